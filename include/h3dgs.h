@@ -1,0 +1,253 @@
+/*
+ * h3dgs.h -- C ABI of the B300 (sm_103a) hierarchical 3D Gaussian render path.
+ *
+ * Method: "A Hierarchical 3D Gaussian Representation for Real-Time Rendering of Very Large
+ * Datasets" (Kerbl, Meuleman, Kopanas, Wimmer, Lanvin, Drettakis; ACM TOG 43(4), 2024).
+ *
+ * Per view, the library selects a cut through a Gaussian hierarchy at a target granularity tau
+ * (Sec. 4.2), interpolates each cut node with its parent (Sec. 4.2, Eq. t_interp and
+ * Eq. alphap), and splats the result with a tile-based rasteriser (Sec. 3.1, Eq. alpha;
+ * EWA low-pass of Sec. 5.1).  It also provides the adjoint used to optimise interior nodes
+ * (Sec. 5.1, Sec. 6.3).
+ *
+ * Conventions shared by every call
+ *   - All attribute, topology, output and gradient buffers are DEVICE pointers unless a
+ *     parameter says "host".  The caller owns them; the library never frees them.
+ *   - Every call is asynchronous on the stream given to h3dgs_create, unless stated otherwise.
+ *     Results are valid once that stream has synchronised.
+ *   - Every call returns an h3dgs_status and never aborts, traps or prints.  On failure,
+ *     h3dgs_last_error() returns a one-line message.  A context is NOT thread-safe.
+ *   - Floating point is fp32 throughout.  Integer decisions (cut membership, tile rectangles,
+ *     depth order) are evaluated in a fixed fp32 operation order documented with each call.
+ */
+#ifndef H3DGS_H
+#define H3DGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    H3DGS_OK = 0,
+    H3DGS_ERR_INVALID_ARG = 1, /* null pointer, bad size or alignment, n_cams out of range    */
+    H3DGS_ERR_OOM = 2,         /* workspace allocation failed                                  */
+    H3DGS_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error)      */
+    H3DGS_ERR_CAPACITY = 4,    /* an output or a fixed workspace was too small (see each call) */
+    H3DGS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                           */
+    H3DGS_ERR_STATE = 6,       /* call order violated (no hierarchy, no saved forward state)   */
+    H3DGS_ERR_NO_DEVICE = 7    /* no CUDA device, or the device is not sm_103                  */
+} h3dgs_status;
+
+typedef struct h3dgs_ctx h3dgs_ctx; /* opaque */
+
+/* Pinhole camera.  World -> camera: x_c = R x_w + T, R row-major; camera axes x right, y down,
+ * z forward.  Pixel (i, j) covers [i, i+1) x [j, j+1) and is sampled at (i + 0.5, j + 0.5):
+ * u = fx x_c/z_c + cx, v = fy y_c/z_c + cy.  Points with z_c <= znear are culled.  tau is the
+ * target granularity in pixels (Sec. 4.2). */
+typedef struct {
+    float R[9];
+    float T[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear;
+    float tau;
+} h3dgs_camera;
+
+/* A Gaussian hierarchy (Sec. 4.1) as device arrays, one row per node, in breadth-first order:
+ * node 0 is the root (parent[0] = -1), the children of a node are contiguous
+ * (child_start .. child_start + child_count - 1), parent < child, leaves have child_count 0.
+ * Attributes are ACTIVATED values: scale > 0 (metres), rot a quaternion (w, x, y, z) (need not
+ * be unit length), opacity >= 0 (interior nodes carry the falloff of Sec. 4.1, which may exceed
+ * 1), sh the 16 degree-3 SH coefficients per colour channel laid out [k*3 + channel].
+ * box_min/box_max: the AABB of the 3-sigma boxes of all leaves below the node (Sec. 4.2); every
+ * parent box must contain its children's boxes.
+ * Alignment: every pointer 16-byte aligned (rot and sh rows are read as float4). */
+typedef struct {
+    int64_t n_nodes;
+    const float* mean;          /* [N,3]  */
+    const float* scale;         /* [N,3]  */
+    const float* rot;           /* [N,4]  */
+    const float* opacity;       /* [N]    */
+    const float* sh;            /* [N,48] */
+    const float* box_min;       /* [N,3]  */
+    const float* box_max;       /* [N,3]  */
+    const int32_t* parent;      /* [N]    */
+    const int32_t* child_start; /* [N]    */
+    const int32_t* child_count; /* [N]    */
+} h3dgs_hierarchy;
+
+/* Gradients of the node attributes, same layouts as h3dgs_hierarchy (device, accumulated +=). */
+typedef struct {
+    float* mean;    /* [N,3]  */
+    float* scale;   /* [N,3]  */
+    float* rot;     /* [N,4]  */
+    float* opacity; /* [N]    */
+    float* sh;      /* [N,48] */
+} h3dgs_grads;
+
+/* Render options.  h3dgs_default_opts() fills the values used by the paper and by 3DGS. */
+typedef struct {
+    int32_t tile_w, tile_h;  /* screen tile in pixels; tile_w * tile_h must be 64, 128 or 256,
+                                tile_w a multiple of 8 (default 16 x 16)                        */
+    float lowpass;           /* screen-space variance added to the 2D covariance, px^2 (0.3)    */
+    float alpha_clamp;       /* alpha upper clamp (0.99, Sec. 6.3)                              */
+    float alpha_floor;       /* alpha below which a splat is skipped (1/255)                   */
+    float t_min;             /* stop before transmittance would drop below this (1e-4)        */
+    int32_t aa_compensate;   /* 1: opacities scaled by sqrt(det S' / det(S' + lowpass I))     */
+    int32_t interpolate;     /* 1: parent/child interpolation (Sec. 4.2); 0: render the cut as is */
+    float bg[3];             /* background colour                                              */
+} h3dgs_render_opts;
+
+/* Counters of the most recent h3dgs_render (read with a stream synchronisation). */
+typedef struct {
+    int64_t n_cut;        /* cut nodes rendered (all cameras)                    */
+    int64_t n_visible;    /* splats surviving culling                            */
+    int64_t n_pairs;      /* (tile, splat) pairs after binning                   */
+    int64_t n_tiles;      /* tiles over all cameras                              */
+    int64_t n_pixels;     /* pixels over all cameras                             */
+    uint32_t device_flags; /* bit 0: pair capacity exceeded (fixed-capacity mode)  */
+} h3dgs_stats;
+
+/* ------------------------------------------------------------------------------ lifecycle */
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  Fails with H3DGS_ERR_NO_DEVICE when no device exists or it
+ * is not compute capability 10.3.  *out receives the context (NULL on failure). */
+h3dgs_status h3dgs_create(h3dgs_ctx** out, int32_t device, void* cuda_stream);
+
+/* Destroy a context and free its workspace (synchronises its stream).  NULL is accepted. */
+h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx);
+
+/* Message of the last failed call on this context (never NULL; "" after success). */
+const char* h3dgs_last_error(const h3dgs_ctx* ctx);
+
+/* Fill *opts with the defaults listed in h3dgs_render_opts. */
+void h3dgs_default_opts(h3dgs_render_opts* opts);
+
+/* Fix the workspace capacities (cut-node splats and tile pairs over all cameras of one render)
+ * and switch the context to fixed-capacity mode: h3dgs_render then never synchronises, so it can
+ * be captured in a CUDA graph.  Overflow sets h3dgs_stats.device_flags bit 0 and the frame is
+ * incomplete.  Passing 0 for both returns to the default mode, in which h3dgs_render reads the
+ * pair count back once per call and grows its workspace as needed.  Synchronous. */
+h3dgs_status h3dgs_reserve(h3dgs_ctx* ctx, int64_t max_splats, int64_t max_pairs);
+
+/* ------------------------------------------------------------------------------ hierarchy */
+
+/* Writable node arrays (device), the layouts of h3dgs_hierarchy, sized for 2L - 1 nodes. */
+typedef struct {
+    float *mean, *scale, *rot, *opacity, *sh, *box_min, *box_max;
+    int32_t *parent, *child_start, *child_count;
+} h3dgs_node_arrays;
+
+/* Build the hierarchy over n_leaves leaf Gaussians on the device (Sec. 4.1): leaf boxes are the
+ * AABBs of the 3-sigma ellipsoids; groups are split top-down at the median of the members'
+ * means projected on the longest axis of the group's box (ties to the lower axis; members
+ * ordered by (projected mean, leaf index); the left child takes floor(n/2)); interior nodes
+ * are merged bottom-up from their two children with Eq. merge, weights w'_i = o_i S_i (S_i the
+ * ellipsoid surface, Thomsen's formula), SH merged with the same weights and the parent
+ * opacity set to the falloff sum(w'_i) / S_p; then, from the root down, each child's axes are
+ * reinterpreted by the proper signed axis permutation minimising its rotation relative to its
+ * parent (orientation matching, Sec. 4.2).  Nodes are numbered breadth-first.  Attributes are
+ * computed in fp64 and rounded to fp32 once.  Inputs are device arrays in the layouts of
+ * h3dgs_hierarchy ([L,3], [L,3], [L,4], [L], [L,48]); `out` receives 2 n_leaves - 1 nodes.
+ * Synchronous; allocates temporary device memory (about 500 bytes per node).
+ * Errors: INVALID_ARG (n_leaves < 1 or > 2^30, NULL or misaligned pointers), OOM, CUDA. */
+h3dgs_status h3dgs_build_hierarchy(h3dgs_ctx* ctx, int64_t n_leaves, const float* mean, const float* scale,
+                                   const float* rot, const float* opacity, const float* sh,
+                                   const h3dgs_node_arrays* out);
+
+/* a0 -- make a hierarchy resident.  The arrays are BORROWED: they must stay allocated, and the
+ * topology and boxes unchanged, until the next upload or h3dgs_destroy.  Attributes (mean, scale,
+ * rot, opacity, sh) may be updated in place between calls (e.g. by an optimiser).  The library
+ * derives a packed 32-byte record per node (box + parent + child count) for the cut kernels.
+ * Errors: INVALID_ARG on NULL pointers, n_nodes < 1 or > 2^31 - 1, misaligned pointers.
+ * The topology is trusted (not validated on the device). */
+h3dgs_status h3dgs_upload_hierarchy(h3dgs_ctx* ctx, const h3dgs_hierarchy* hier);
+
+/* ------------------------------------------------------------------------------ per frame */
+
+/* a1 + a2 -- cut selection and interpolation weights (Sec. 4.2, Fig. gran-cut, Eq. t_interp).
+ * For each camera k (cams: HOST array of n_cams, 1 <= n_cams <= 4096):
+ *   granularity eps(n) = f * size(n) / dist(n), where f = max(fx, fy), size(n) is the largest
+ *   side of the node's box and dist(n) the distance from the camera centre c = -R^T T to the
+ *   closest point of the box (+inf when c is inside the box);
+ *   n is in the cut  <=>  (eps(n) < tau or n is a leaf) and (n is the root or eps(parent) >= tau);
+ *   the parent weight t = (tau - eps(n)) / (eps(parent) - eps(n)) for nodes that passed the test
+ *   with a finite eps(parent), else 0 (root, leaves forced in, camera inside the parent box).
+ * Outputs (device): cut_ids[cut_offsets[k] .. cut_offsets[k+1]) = the cut of camera k in
+ * ascending node order; cut_t (nullable) the matching t; cut_offsets [n_cams + 1] (int64).
+ * At most `capacity` ids are written over all cameras; offsets are clamped to capacity.  If
+ * total_out (host) is non-NULL the call synchronises, stores the untruncated total there and
+ * returns H3DGS_ERR_CAPACITY when it exceeded capacity; with total_out NULL it does not
+ * synchronise and truncation is silent. */
+h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams,
+                              int32_t* cut_ids, float* cut_t, int64_t* cut_offsets, int64_t capacity,
+                              int64_t* total_out);
+
+/* a3 -- export the interpolated attributes of every cut node (Sec. 4.2):
+ *   a = (1 - t) a_n + t a_p  (fp32: fmaf(t, a_p, (1 - t) * a_n))  for mean, scale, rot (then
+ *   normalised), sh;  the opacities o_n, o_p and the parent's child count K are kept separately.
+ * out: device float SoA [62][m_total], rows: mean 0-2, scale 3-5, rot 6-9, sh 10-57, o_n 58,
+ * o_p 59, t 60, K 61.  interpolate = 0 forces t = 0.  m_total must equal cut_offsets[n_cams]
+ * (host value; the caller knows it from h3dgs_select_cut's total_out). */
+h3dgs_status h3dgs_interpolate(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams,
+                               const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets,
+                               int32_t interpolate, float* out, int64_t m_total);
+
+/* a3 .. a7 -- render the cuts of n_cams cameras (HOST array) into `images`: device float,
+ * camera k's image [3, H_k, W_k] (planar RGB) starting at offset 3 * sum_{j<k} H_j W_j.
+ * Stages (all on the device, no host round trip in fixed-capacity mode):
+ *   interpolate + project + SH (EWA: Sigma' = J W Sigma W^T J^T + lowpass I, conic, opacity
+ *   compensation, radius ceil(3 sqrt(lambda_max)), tile rectangle), depth sort, duplication into
+ *   (tile, splat) pairs, stable tile sort, tile ranges, per-tile front-to-back blend with
+ *   alpha = (1 - t) min(c, o_n G) + t alpha'(min(c, o_p G)), alpha' = 1 - (1 - alpha_p)^(1/K)
+ *   (Eq. alphap), skipping alpha < alpha_floor and stopping before T would drop below t_min.
+ * Each tile's list is ordered by (fp32 view depth, cut position).  cut_t may be NULL (t = 0).
+ * save_for_backward = 1 keeps the splats, lists and per-pixel final transmittance for
+ * h3dgs_render_backward (valid until the next render or upload).  The backward re-reads cut_ids,
+ * cut_t and cut_offsets (borrowed): keep them allocated and unchanged until it has run.
+ * Errors: INVALID_ARG (bad cameras/opts), STATE (no hierarchy), OOM, CAPACITY (fixed-capacity
+ * mode only reports it through h3dgs_stats.device_flags). */
+h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams,
+                          const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets,
+                          const h3dgs_render_opts* opts, float* images, int32_t save_for_backward);
+
+/* a8 -- adjoint of the most recent h3dgs_render(save_for_backward = 1) (Sec. 5.1, Sec. 6.3).
+ * dL_dimages: device, same packing as `images`.  Gradients are ACCUMULATED into `grads`:
+ * node n receives (1 - t) of the gradient of its interpolated mean/scale/rot/sh and its parent p
+ * receives t of it (t is a constant); o_n and o_p receive the gradients of their own alpha terms,
+ * including d alpha'/d alpha_p = (1/K)(1 - alpha_p)^(1/K - 1); an opacity gradient is zero where
+ * its alpha is clamped (Sec. 6.3).  freeze_leaves = 1 leaves the rows of leaf nodes untouched
+ * (stop-gradient on leaves, Sec. 6.3).  Errors: STATE if no saved forward state. */
+h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL_dimages, const h3dgs_grads* grads,
+                                   int32_t freeze_leaves);
+
+/* ------------------------------------------------------------------------------ inspection */
+
+/* Counters of the last render (synchronises the stream). */
+h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out);
+
+/* Copy the last render's per-tile lists of camera `cam` to HOST memory (synchronous):
+ * ranges [tiles_x * tiles_y][2] = [start, end) into ids; ids = the NODE id of each list entry.
+ * *n_out (host) receives the number of entries; at most `cap` ids are written (CAPACITY if
+ * more exist). */
+h3dgs_status h3dgs_debug_tile_lists(h3dgs_ctx* ctx, int32_t cam, int32_t* ranges, int32_t* ids, int64_t cap,
+                                    int64_t* n_out);
+
+/* Copy the last render's splat records to HOST memory (synchronous), one row per cut entry in
+ * cut order (all cameras): rec [m][10] = u, v, ca, cb, cc, o_n', o_p', t, K, depth with
+ * (ca, cb, cc) the conic scaled so that the base-2 exponent is ca dx^2 + cb dx dy + cc dy^2;
+ * rect [m][4] = tile x0, x1, y0, y1 (inclusive), all -1 for culled entries; rgb [m][3]. */
+h3dgs_status h3dgs_debug_splats(h3dgs_ctx* ctx, float* rec, int32_t* rect, float* rgb, int64_t m);
+
+/* Copy the last render's per-pixel final transmittance and contributor count (the list position
+ * after the last contributing splat) to HOST memory for all cameras (synchronous). */
+h3dgs_status h3dgs_debug_pixel_state(h3dgs_ctx* ctx, float* T_final, int32_t* n_contrib, int64_t n_pixels);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H3DGS_H */

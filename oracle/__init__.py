@@ -316,7 +316,8 @@ def render(cam, h: Hierarchy, opts: Opts | None = None, a64: Attrs64 | None = No
            cut=None) -> Frame:
     """Cut -> interpolate/project -> tile lists -> blend, all on the CPU."""
     opts = opts or Opts()
-    ids, t = cut if cut is not None else select_cut(cam, h, opts.interpolate)
+    # t is a property of the cut (camera + hierarchy); interpolate = 0 only zeroes it when rendering
+    ids, t = cut if cut is not None else select_cut(cam, h, 1)
     fr = preprocess(cam, h, ids, t, opts, a64)
     tile_lists(cam, fr, opts)
     return blend(cam, fr, opts)

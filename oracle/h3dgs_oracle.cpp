@@ -542,6 +542,7 @@ namespace {
 
 // Interpolated attributes of one cut node.  Layout of the exported row (62 values):
 //   mean 3 | scale 3 | rot 4 (normalised) | sh 48 | o_n | o_p | t | K
+// o_p and K (the parent's opacity and child count) are 0 and 1 when t = 0 (they are unused).
 constexpr int NINTERP = 62;
 
 // fp32 track: a = fmaf(t, a_p, (1 - t) * a_n) for mean, scale, rot (then normalised), sh.
@@ -569,9 +570,9 @@ void interp_f(const OrHier32& h, int64_t n, float t, float out[NINTERP]) {
     for (int c = 0; c < NSH; ++c)
         out[10 + c] = use_p ? lerp(h.sh[(size_t)NSH * n + c], h.sh[(size_t)NSH * p + c]) : h.sh[(size_t)NSH * n + c];
     out[58] = h.opacity[n];
-    out[59] = p >= 0 ? h.opacity[p] : 0.0f;
+    out[59] = use_p ? h.opacity[p] : 0.0f;
     out[60] = t;
-    out[61] = p >= 0 ? (float)h.child_count[p] : 1.0f;
+    out[61] = use_p ? (float)h.child_count[p] : 1.0f;
 }
 
 // fp64 track of the same interpolation (t is the fp32 weight, exactly representable).
@@ -591,9 +592,9 @@ void interp_d(const OrHier32& h, const OrHier64& hd, int64_t n, double t, double
     for (int c = 0; c < NSH; ++c)
         out[10 + c] = use_p ? lerp(hd.sh[(size_t)NSH * n + c], hd.sh[(size_t)NSH * p + c]) : hd.sh[(size_t)NSH * n + c];
     out[58] = hd.opacity[n];
-    out[59] = p >= 0 ? hd.opacity[p] : 0.0;
+    out[59] = use_p ? hd.opacity[p] : 0.0;
     out[60] = t;
-    out[61] = p >= 0 ? (double)h.child_count[p] : 1.0;
+    out[61] = use_p ? (double)h.child_count[p] : 1.0;
 }
 
 // Real spherical harmonics up to degree 3 for a unit direction (x, y, z), orthonormal on the

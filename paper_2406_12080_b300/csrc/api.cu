@@ -1,0 +1,599 @@
+// C ABI of libh3dgs: context, workspace and the orchestration of the per-frame stages.
+// Every stage runs in this library's kernels; host code only validates arguments, does integer
+// bookkeeping (tile grids, offsets) and manages device memory.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace h3dgs;
+
+namespace {
+
+struct DBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+cudaError_t ensure(DBuf& b, size_t bytes) {
+    if (bytes <= b.n && b.p) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    size_t nb = std::max<size_t>(bytes + bytes / 4, 256);
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.n = nb;
+    return cudaSuccess;
+}
+
+template <typename T>
+T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
+
+// device counter block
+enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_COUNT = 8 };
+
+}  // namespace
+
+struct h3dgs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int num_sms = 148;
+    h3dgs_hierarchy hier{};
+    bool has_hier = false;
+    DBuf rec, cams, counters;
+    DBuf cut_mask, cut_bc, cut_tot;
+    DBuf s_rec, s_rect, s_key, s_idx, s_key2, s_idx2, s_tiles, s_poff;
+    DBuf pk0, pv0, pk1, pv1, ranges;
+    DBuf hist, dtot, partial;
+    DBuf T_final, n_contrib, splat_grad;
+    bool fixed = false;
+    int64_t cap_splats = 0, cap_pairs = 0;
+    // state of the last render
+    bool rendered = false, saved = false;
+    std::vector<h3dgs_camera> cams_host;
+    std::vector<int64_t> tile_base, pix_base;
+    std::vector<int32_t> tiles_x, tiles_y;
+    int64_t n_tiles = 0, n_pixels = 0, splat_cap_used = 0, pair_cap_used = 0;
+    DevOpts opts{};
+    const int32_t* cut_ids = nullptr;
+    const float* cut_t = nullptr;
+    const int64_t* cut_offsets = nullptr;
+    bool depth_in_2 = false, pairs_in_1 = false;
+};
+
+namespace {
+
+h3dgs_status fail(h3dgs_ctx* c, h3dgs_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+h3dgs_status cuda_fail(h3dgs_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, e == cudaErrorMemoryAllocation ? H3DGS_ERR_OOM : H3DGS_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                                        \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+h3dgs_status check_cams(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams) {
+    if (!cams || n_cams < 1 || n_cams > MAX_CAMS) return fail(ctx, H3DGS_ERR_INVALID_ARG, "cams: need 1..4096 cameras");
+    for (int i = 0; i < n_cams; ++i) {
+        const h3dgs_camera& c = cams[i];
+        if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
+            return fail(ctx, H3DGS_ERR_INVALID_ARG, "camera " + std::to_string(i) + ": image size out of range");
+        if (!(c.fx > 0) || !(c.fy > 0) || !(c.znear > 0) || !(c.tau >= 0))
+            return fail(ctx, H3DGS_ERR_INVALID_ARG, "camera " + std::to_string(i) + ": fx, fy, znear > 0 and tau >= 0");
+    }
+    return H3DGS_OK;
+}
+
+// Upload cameras with their tile grids; fills the ctx bookkeeping vectors.
+h3dgs_status setup_cameras(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams, int tile_w, int tile_h) {
+    CK(ensure(ctx->cams, sizeof(DevCam) * (size_t)n_cams), "camera buffer");
+    ctx->cams_host.assign(cams, cams + n_cams);
+    ctx->tile_base.resize(n_cams);
+    ctx->pix_base.resize(n_cams);
+    ctx->tiles_x.resize(n_cams);
+    ctx->tiles_y.resize(n_cams);
+    int64_t tb = 0, pb = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        ctx->tiles_x[i] = (cams[i].width + tile_w - 1) / tile_w;
+        ctx->tiles_y[i] = (cams[i].height + tile_h - 1) / tile_h;
+        ctx->tile_base[i] = tb;
+        ctx->pix_base[i] = pb;
+        tb += (int64_t)ctx->tiles_x[i] * ctx->tiles_y[i];
+        pb += (int64_t)cams[i].width * cams[i].height;
+    }
+    ctx->n_tiles = tb;
+    ctx->n_pixels = pb;
+    for (int first = 0; first < n_cams; first += CAM_BATCH) {
+        CamBatch b;
+        std::memset(&b, 0, sizeof(b));
+        b.first = first;
+        b.count = std::min(CAM_BATCH, n_cams - first);
+        for (int i = 0; i < b.count; ++i) {
+            b.cam[i] = cams[first + i];
+            b.tiles_x[i] = ctx->tiles_x[first + i];
+            b.tiles_y[i] = ctx->tiles_y[first + i];
+            b.tile_base[i] = ctx->tile_base[first + i];
+            b.pix_base[i] = ctx->pix_base[first + i];
+        }
+        CK(launch_camera_setup(b, nullptr, P<DevCam>(ctx->cams), ctx->stream), "camera set-up");
+    }
+    return H3DGS_OK;
+}
+
+DevHier dev_hier(h3dgs_ctx* ctx) {
+    DevHier h;
+    h.n = ctx->hier.n_nodes;
+    h.mean = ctx->hier.mean;
+    h.scale = ctx->hier.scale;
+    h.rot = reinterpret_cast<const float4*>(ctx->hier.rot);
+    h.opacity = ctx->hier.opacity;
+    h.sh = reinterpret_cast<const float4*>(ctx->hier.sh);
+    h.parent = ctx->hier.parent;
+    h.child_count = ctx->hier.child_count;
+    h.rec = P<const float4>(ctx->rec);
+    return h;
+}
+
+DevOpts dev_opts(const h3dgs_render_opts& o) {
+    DevOpts d;
+    d.tile_w = o.tile_w; d.tile_h = o.tile_h; d.lowpass = o.lowpass; d.alpha_clamp = o.alpha_clamp;
+    d.alpha_floor = o.alpha_floor; d.t_min = o.t_min; d.aa_compensate = o.aa_compensate;
+    d.interpolate = o.interpolate;
+    for (int i = 0; i < 3; ++i) d.bg[i] = o.bg[i];
+    return d;
+}
+
+bool supported_tile(int w, int h) {
+    return (w == 16 && h == 16) || (w == 8 && h == 8) || (w == 32 && h == 8) || (w == 8 && h == 32) ||
+           (w == 16 && h == 8) || (w == 32 && h == 4);
+}
+
+int bits_for(int64_t n) {
+    int b = 0;
+    while (b < 32 && ((int64_t)1 << b) < n) ++b;
+    return std::max(b, 1);
+}
+
+SortWork sort_work(h3dgs_ctx* ctx) {
+    SortWork w;
+    w.hist = P<uint32_t>(ctx->hist);
+    w.digit_total = P<uint32_t>(ctx->dtot);
+    w.partial = P<uint32_t>(ctx->partial);
+    w.blocks = ctx->num_sms * 4;
+    return w;
+}
+
+}  // namespace
+
+extern "C" {
+
+h3dgs_status h3dgs_create(h3dgs_ctx** out, int32_t device, void* cuda_stream) {
+    if (!out) return H3DGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n <= device || device < 0) {
+        cudaGetLastError();
+        return H3DGS_ERR_NO_DEVICE;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return H3DGS_ERR_NO_DEVICE;
+    if (!(prop.major == 10 && prop.minor == 3)) return H3DGS_ERR_NO_DEVICE;
+    if (cudaSetDevice(device) != cudaSuccess) return H3DGS_ERR_NO_DEVICE;
+    h3dgs_ctx* ctx = new h3dgs_ctx();
+    ctx->device = device;
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    ctx->num_sms = prop.multiProcessorCount;
+    cudaError_t e = ensure(ctx->counters, sizeof(uint32_t) * C_COUNT);
+    if (e == cudaSuccess) e = cudaMemset(ctx->counters.p, 0, sizeof(uint32_t) * C_COUNT);
+    const int G = ctx->num_sms * 4;
+    if (e == cudaSuccess) e = ensure(ctx->hist, sizeof(uint32_t) * 256 * (size_t)G);
+    if (e == cudaSuccess) e = ensure(ctx->dtot, sizeof(uint32_t) * 256);
+    if (e == cudaSuccess) e = ensure(ctx->partial, sizeof(uint32_t) * (size_t)(G + 1));
+    if (e != cudaSuccess) {
+        h3dgs_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? H3DGS_ERR_OOM : H3DGS_ERR_CUDA;
+    }
+    *out = ctx;
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
+    if (!ctx) return H3DGS_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    DBuf* bufs[] = {&ctx->rec, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot,
+                    &ctx->s_rec, &ctx->s_rect, &ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2,
+                    &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1, &ctx->ranges,
+                    &ctx->hist, &ctx->dtot, &ctx->partial, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad};
+    for (DBuf* b : bufs)
+        if (b->p) cudaFree(b->p);
+    delete ctx;
+    return H3DGS_OK;
+}
+
+const char* h3dgs_last_error(const h3dgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void h3dgs_default_opts(h3dgs_render_opts* o) {
+    if (!o) return;
+    o->tile_w = 16;
+    o->tile_h = 16;
+    o->lowpass = 0.3f;
+    o->alpha_clamp = 0.99f;
+    o->alpha_floor = 1.0f / 255.0f;
+    o->t_min = 1e-4f;
+    o->aa_compensate = 1;
+    o->interpolate = 1;
+    o->bg[0] = o->bg[1] = o->bg[2] = 0.0f;
+}
+
+h3dgs_status h3dgs_reserve(h3dgs_ctx* ctx, int64_t max_splats, int64_t max_pairs) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (max_splats < 0 || max_pairs < 0 || max_pairs > 0xffffffffLL || max_splats > 0x7fffffffLL)
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "reserve: capacities out of range");
+    CK(cudaSetDevice(ctx->device), "set device");
+    if (max_splats == 0 && max_pairs == 0) {
+        ctx->fixed = false;
+        return H3DGS_OK;
+    }
+    const size_t M = (size_t)max_splats, Pn = (size_t)max_pairs;
+    CK(ensure(ctx->s_rec, 48 * M), "splat buffer");
+    CK(ensure(ctx->s_rect, 8 * M), "splat buffer");
+    DBuf* m4[] = {&ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2, &ctx->s_tiles, &ctx->s_poff};
+    for (DBuf* b : m4) CK(ensure(*b, 4 * M), "splat buffer");
+    DBuf* p4[] = {&ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1};
+    for (DBuf* b : p4) CK(ensure(*b, 4 * Pn), "pair buffer");
+    CK(cudaDeviceSynchronize(), "reserve");
+    ctx->fixed = true;
+    ctx->cap_splats = max_splats;
+    ctx->cap_pairs = max_pairs;
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_build_hierarchy(h3dgs_ctx* ctx, int64_t L, const float* mean, const float* scale, const float* rot,
+                                   const float* opacity, const float* sh, const h3dgs_node_arrays* out) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (L < 1 || L > (1LL << 30)) return fail(ctx, H3DGS_ERR_INVALID_ARG, "build: n_leaves out of range");
+    if (!out) return fail(ctx, H3DGS_ERR_INVALID_ARG, "build: NULL output");
+    const void* ptrs[] = {mean, scale, rot, opacity, sh, out->mean, out->scale, out->rot, out->opacity, out->sh,
+                          out->box_min, out->box_max, out->parent, out->child_start, out->child_count};
+    for (const void* p : ptrs) {
+        if (!p) return fail(ctx, H3DGS_ERR_INVALID_ARG, "build: NULL array");
+        if (!aligned16(p)) return fail(ctx, H3DGS_ERR_INVALID_ARG, "build: arrays must be 16-byte aligned");
+    }
+    CK(cudaSetDevice(ctx->device), "set device");
+    BuildOut bo{out->mean, out->scale, out->rot, out->opacity, out->sh, out->box_min, out->box_max,
+                out->parent, out->child_start, out->child_count};
+    CK(build_hierarchy(L, mean, scale, rot, opacity, sh, bo, sort_work(ctx), ctx->num_sms, ctx->stream), "build");
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_upload_hierarchy(h3dgs_ctx* ctx, const h3dgs_hierarchy* h) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!h) return fail(ctx, H3DGS_ERR_INVALID_ARG, "hierarchy: NULL");
+    if (h->n_nodes < 1 || h->n_nodes > 0x7fffffffLL) return fail(ctx, H3DGS_ERR_INVALID_ARG, "hierarchy: n_nodes out of range");
+    const void* ptrs[] = {h->mean, h->scale, h->rot, h->opacity, h->sh, h->box_min, h->box_max,
+                          h->parent, h->child_start, h->child_count};
+    for (const void* p : ptrs) {
+        if (!p) return fail(ctx, H3DGS_ERR_INVALID_ARG, "hierarchy: NULL array");
+        if (!aligned16(p)) return fail(ctx, H3DGS_ERR_INVALID_ARG, "hierarchy: arrays must be 16-byte aligned");
+    }
+    CK(cudaSetDevice(ctx->device), "set device");
+    CK(ensure(ctx->rec, sizeof(float4) * 2 * (size_t)h->n_nodes), "record buffer");
+    CK(launch_pack_records(*h, P<float4>(ctx->rec), ctx->stream), "pack records");
+    ctx->hier = *h;
+    ctx->has_hier = true;
+    ctx->rendered = ctx->saved = false;
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams, int32_t* cut_ids,
+                              float* cut_t, int64_t* cut_offsets, int64_t capacity, int64_t* total_out) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_hier) return fail(ctx, H3DGS_ERR_STATE, "select_cut: no hierarchy uploaded");
+    h3dgs_status st = check_cams(ctx, cams, n_cams);
+    if (st != H3DGS_OK) return st;
+    if (!cut_offsets || (capacity > 0 && !cut_ids) || capacity < 0)
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "select_cut: NULL output or negative capacity");
+    CK(cudaSetDevice(ctx->device), "set device");
+    st = setup_cameras(ctx, cams, n_cams, 16, 16);
+    if (st != H3DGS_OK) return st;
+    const int64_t N = ctx->hier.n_nodes;
+    CutWork w;
+    const int64_t max_blocks = (int64_t)ctx->num_sms * 4;
+    w.chunk = ((N + max_blocks - 1) / max_blocks + 255) / 256 * 256;
+    w.blocks = (int)((N + w.chunk - 1) / w.chunk);
+    w.words = (N + 31) / 32;
+    CK(ensure(ctx->cut_mask, sizeof(uint32_t) * (size_t)w.words * n_cams), "cut mask");
+    CK(ensure(ctx->cut_bc, sizeof(uint32_t) * (size_t)w.blocks * n_cams), "cut counts");
+    CK(ensure(ctx->cut_tot, sizeof(int64_t) * (size_t)(n_cams + 1)), "cut totals");
+    w.mask = P<uint32_t>(ctx->cut_mask);
+    w.block_counts = P<uint32_t>(ctx->cut_bc);
+    w.cam_totals = P<int64_t>(ctx->cut_tot);
+    CK(launch_cut(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, w, cut_ids, cut_t, cut_offsets, capacity,
+                  P<uint32_t>(ctx->counters) + C_FLAGS, ctx->stream),
+       "cut kernels");
+    if (total_out) {
+        int64_t tot = 0;
+        CK(cudaMemcpyAsync(&tot, P<int64_t>(ctx->cut_tot) + n_cams, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream),
+           "read cut total");
+        CK(cudaStreamSynchronize(ctx->stream), "select_cut sync");
+        *total_out = tot;
+        if (tot > capacity) return fail(ctx, H3DGS_ERR_CAPACITY, "select_cut: cut larger than capacity");
+    }
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_interpolate(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams, const int32_t* cut_ids,
+                               const float* cut_t, const int64_t* cut_offsets, int32_t interpolate, float* out,
+                               int64_t m_total) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_hier) return fail(ctx, H3DGS_ERR_STATE, "interpolate: no hierarchy uploaded");
+    h3dgs_status st = check_cams(ctx, cams, n_cams);
+    if (st != H3DGS_OK) return st;
+    if (m_total < 0 || (m_total > 0 && (!cut_ids || !out)) || !cut_offsets)
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "interpolate: bad outputs");
+    if (m_total == 0) return H3DGS_OK;
+    CK(cudaSetDevice(ctx->device), "set device");
+    CK(launch_interpolate_export(dev_hier(ctx), n_cams, cut_ids, cut_t, cut_offsets, interpolate, out, m_total,
+                                 ctx->stream),
+       "interpolate");
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams, const int32_t* cut_ids,
+                          const float* cut_t, const int64_t* cut_offsets, const h3dgs_render_opts* opts, float* images,
+                          int32_t save_for_backward) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_hier) return fail(ctx, H3DGS_ERR_STATE, "render: no hierarchy uploaded");
+    h3dgs_status st = check_cams(ctx, cams, n_cams);
+    if (st != H3DGS_OK) return st;
+    if (!opts || !images || !cut_offsets || !cut_ids) return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: NULL argument");
+    if (!supported_tile(opts->tile_w, opts->tile_h))
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: unsupported tile shape");
+    if (!(opts->alpha_clamp > 0 && opts->alpha_clamp < 1) || !(opts->lowpass >= 0) || !(opts->t_min >= 0))
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: bad opts");
+    CK(cudaSetDevice(ctx->device), "set device");
+    st = setup_cameras(ctx, cams, n_cams, opts->tile_w, opts->tile_h);
+    if (st != H3DGS_OK) return st;
+    if (ctx->n_tiles > 0xffffffffLL) return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: too many tiles");
+    cudaStream_t s = ctx->stream;
+    uint32_t* cnt = P<uint32_t>(ctx->counters);
+    // ---- capacities
+    int64_t capM, capP;
+    if (ctx->fixed) {
+        capM = ctx->cap_splats;
+        capP = ctx->cap_pairs;
+    } else {
+        int64_t m = 0;
+        CK(cudaMemcpyAsync(&m, cut_offsets + n_cams, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "read cut size");
+        CK(cudaStreamSynchronize(s), "render sync");
+        if (m < 0 || m > 0x7fffffffLL) return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: bad cut size");
+        capM = std::max<int64_t>(m, 1);
+        const size_t M = (size_t)capM;
+        CK(ensure(ctx->s_rec, 48 * M), "splat buffer");
+        CK(ensure(ctx->s_rect, 8 * M), "splat buffer");
+        DBuf* m4[] = {&ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2, &ctx->s_tiles, &ctx->s_poff};
+        for (DBuf* b : m4) CK(ensure(*b, 4 * M), "splat buffer");
+        capP = 0;
+    }
+    CK(ensure(ctx->ranges, sizeof(int2) * (size_t)ctx->n_tiles), "ranges");
+    CK(ensure(ctx->T_final, sizeof(float) * (size_t)ctx->n_pixels), "pixel state");
+    CK(ensure(ctx->n_contrib, sizeof(int32_t) * (size_t)ctx->n_pixels), "pixel state");
+    CK(cudaMemsetAsync(cnt + C_NVISIBLE, 0, sizeof(uint32_t), s), "memset");
+    CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(int2) * (size_t)ctx->n_tiles, s), "memset");
+    const DevOpts o = dev_opts(*opts);
+    SplatBufs sb;
+    sb.rec = P<float4>(ctx->s_rec);
+    sb.rect = P<uint2>(ctx->s_rect);
+    sb.depth_key = P<uint32_t>(ctx->s_key);
+    sb.tiles = P<uint32_t>(ctx->s_tiles);
+    sb.n_splats = cnt + C_NSPLATS;
+    sb.n_visible = cnt + C_NVISIBLE;
+    const int grid = ctx->num_sms * 8;
+    CK(launch_preprocess(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, o, cut_ids, cut_t, cut_offsets, capM, sb,
+                         cnt + C_FLAGS, grid, s),
+       "preprocess");
+    // depth order of the splats: values start as the identity
+    CK(launch_iota(P<uint32_t>(ctx->s_idx), cnt + C_NSPLATS, grid, s), "iota");
+    SortWork sw = sort_work(ctx);
+    bool in2 = false;
+    CK(radix_sort_pairs(P<uint32_t>(ctx->s_key), P<uint32_t>(ctx->s_idx), P<uint32_t>(ctx->s_key2),
+                        P<uint32_t>(ctx->s_idx2), cnt + C_NSPLATS, 32, sw, &in2, s),
+       "depth sort");
+    const uint32_t* order = in2 ? P<uint32_t>(ctx->s_idx2) : P<uint32_t>(ctx->s_idx);
+    CK(scan_gathered(P<uint32_t>(ctx->s_tiles), order, P<uint32_t>(ctx->s_poff), cnt + C_NSPLATS, cnt + C_NPAIRS, sw, s),
+       "pair scan");
+    if (!ctx->fixed) {
+        uint32_t pn = 0;
+        CK(cudaMemcpyAsync(&pn, cnt + C_NPAIRS, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read pairs");
+        CK(cudaStreamSynchronize(s), "render sync");
+        capP = std::max<int64_t>(pn, 1);
+        DBuf* p4[] = {&ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1};
+        for (DBuf* b : p4) CK(ensure(*b, 4 * (size_t)capP), "pair buffer");
+    }
+    CK(launch_duplicate(P<DevCam>(ctx->cams), n_cams, cut_offsets, sb, order, P<uint32_t>(ctx->s_poff), cnt + C_NPAIRS,
+                        capP, cnt + C_NPAIRS_KEPT, P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), cnt + C_FLAGS, grid, s),
+       "duplicate");
+    bool in1 = false;
+    CK(radix_sort_pairs(P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), P<uint32_t>(ctx->pk1), P<uint32_t>(ctx->pv1),
+                        cnt + C_NPAIRS_KEPT, bits_for(ctx->n_tiles), sw, &in1, s),
+       "tile sort");
+    const uint32_t* keys = in1 ? P<uint32_t>(ctx->pk1) : P<uint32_t>(ctx->pk0);
+    const uint32_t* list = in1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
+    CK(launch_ranges(keys, cnt + C_NPAIRS_KEPT, P<int2>(ctx->ranges), grid, s), "ranges");
+    CK(launch_blend(P<DevCam>(ctx->cams), n_cams, ctx->n_tiles, o, P<int2>(ctx->ranges), list, sb.rec, images,
+                    P<float>(ctx->T_final), P<int32_t>(ctx->n_contrib), s),
+       "blend");
+    ctx->rendered = true;
+    ctx->saved = save_for_backward != 0;
+    ctx->opts = o;
+    ctx->cut_ids = cut_ids;
+    ctx->cut_t = cut_t;
+    ctx->cut_offsets = cut_offsets;
+    ctx->depth_in_2 = in2;
+    ctx->pairs_in_1 = in1;
+    ctx->splat_cap_used = capM;
+    ctx->pair_cap_used = capP;
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL, const h3dgs_grads* g, int32_t freeze_leaves) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->saved || !ctx->has_hier) return fail(ctx, H3DGS_ERR_STATE, "render_backward: no saved forward state");
+    if (!dL || !g || !g->mean || !g->scale || !g->rot || !g->opacity || !g->sh)
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "render_backward: NULL argument");
+    CK(cudaSetDevice(ctx->device), "set device");
+    const int n_cams = (int)ctx->cams_host.size();
+    CK(ensure(ctx->splat_grad, sizeof(float) * 12 * (size_t)ctx->splat_cap_used), "splat gradient buffer");
+    CK(cudaMemsetAsync(ctx->splat_grad.p, 0, sizeof(float) * 12 * (size_t)ctx->splat_cap_used, ctx->stream), "memset");
+    GradBufs gb{g->mean, g->scale, g->rot, g->opacity, g->sh};
+    const uint32_t* list = ctx->pairs_in_1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
+    CK(launch_backward(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, ctx->n_tiles, ctx->opts, ctx->cut_ids, ctx->cut_t,
+                       ctx->cut_offsets, P<int2>(ctx->ranges), list, P<float4>(ctx->s_rec), P<uint2>(ctx->s_rect),
+                       P<uint32_t>(ctx->counters) + C_NSPLATS, ctx->splat_cap_used, P<float>(ctx->T_final),
+                       P<int32_t>(ctx->n_contrib), dL, P<float>(ctx->splat_grad), gb, freeze_leaves,
+                       ctx->num_sms * 8, ctx->stream),
+       "backward");
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out) {
+    if (!ctx || !out) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device), "set device");
+    uint32_t c[C_COUNT];
+    CK(cudaMemcpyAsync(c, ctx->counters.p, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream), "read counters");
+    CK(cudaStreamSynchronize(ctx->stream), "stats sync");
+    out->n_cut = c[C_NSPLATS];
+    out->n_visible = c[C_NVISIBLE];
+    out->n_pairs = c[C_NPAIRS_KEPT];
+    out->n_tiles = ctx->n_tiles;
+    out->n_pixels = ctx->n_pixels;
+    out->device_flags = c[C_FLAGS];
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_debug_tile_lists(h3dgs_ctx* ctx, int32_t cam, int32_t* ranges, int32_t* ids, int64_t cap,
+                                    int64_t* n_out) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->rendered) return fail(ctx, H3DGS_ERR_STATE, "debug: nothing rendered");
+    if (cam < 0 || cam >= (int)ctx->cams_host.size() || !ranges || !n_out)
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "debug: bad camera or NULL output");
+    CK(cudaSetDevice(ctx->device), "set device");
+    cudaStream_t s = ctx->stream;
+    const int64_t nt = (int64_t)ctx->tiles_x[cam] * ctx->tiles_y[cam];
+    std::vector<int2> r(nt);
+    CK(cudaMemcpyAsync(r.data(), P<int2>(ctx->ranges) + ctx->tile_base[cam], sizeof(int2) * nt, cudaMemcpyDeviceToHost, s),
+       "read ranges");
+    uint32_t P_kept = 0;
+    CK(cudaMemcpyAsync(&P_kept, P<uint32_t>(ctx->counters) + C_NPAIRS_KEPT, 4, cudaMemcpyDeviceToHost, s), "read count");
+    CK(cudaStreamSynchronize(s), "debug sync");
+    int64_t lo = INT64_MAX, hi = 0;
+    for (int64_t i = 0; i < nt; ++i)
+        if (r[i].y > r[i].x) { lo = std::min<int64_t>(lo, r[i].x); hi = std::max<int64_t>(hi, r[i].y); }
+    if (lo == INT64_MAX) lo = hi = 0;
+    const int64_t n = hi - lo;
+    *n_out = n;
+    for (int64_t i = 0; i < nt; ++i) {
+        ranges[2 * i] = r[i].y > r[i].x ? (int32_t)(r[i].x - lo) : 0;
+        ranges[2 * i + 1] = r[i].y > r[i].x ? (int32_t)(r[i].y - lo) : 0;
+    }
+    if (n > cap) return fail(ctx, H3DGS_ERR_CAPACITY, "debug: ids capacity too small");
+    if (n == 0) return H3DGS_OK;
+    if (!ids) return fail(ctx, H3DGS_ERR_INVALID_ARG, "debug: NULL ids");
+    std::vector<uint32_t> splat(n);
+    const uint32_t* list = ctx->pairs_in_1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
+    CK(cudaMemcpyAsync(splat.data(), list + lo, 4 * n, cudaMemcpyDeviceToHost, s), "read lists");
+    int64_t m = 0;
+    CK(cudaMemcpyAsync(&m, ctx->cut_offsets + ctx->cams_host.size(), 8, cudaMemcpyDeviceToHost, s), "read cut size");
+    CK(cudaStreamSynchronize(s), "debug sync");
+    std::vector<int32_t> cid(std::max<int64_t>(m, 1));
+    if (m > 0) CK(cudaMemcpyAsync(cid.data(), ctx->cut_ids, 4 * m, cudaMemcpyDeviceToHost, s), "read cut ids");
+    CK(cudaStreamSynchronize(s), "debug sync");
+    for (int64_t i = 0; i < n; ++i) ids[i] = splat[i] < (uint32_t)m ? cid[splat[i]] : -1;
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_debug_splats(h3dgs_ctx* ctx, float* rec, int32_t* rect, float* rgb, int64_t m) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->rendered) return fail(ctx, H3DGS_ERR_STATE, "debug: nothing rendered");
+    if (m < 0 || m > ctx->splat_cap_used) return fail(ctx, H3DGS_ERR_INVALID_ARG, "debug: m out of range");
+    CK(cudaSetDevice(ctx->device), "set device");
+    cudaStream_t s = ctx->stream;
+    std::vector<float4> r(3 * std::max<int64_t>(m, 1));
+    std::vector<uint2> rc(std::max<int64_t>(m, 1));
+    std::vector<uint32_t> key(std::max<int64_t>(m, 1)), idx(std::max<int64_t>(m, 1));
+    // the depth sort leaves (depth key, entry) pairs in depth order: invert it to get each entry's depth
+    const uint32_t* sk = ctx->depth_in_2 ? P<uint32_t>(ctx->s_key2) : P<uint32_t>(ctx->s_key);
+    const uint32_t* si = ctx->depth_in_2 ? P<uint32_t>(ctx->s_idx2) : P<uint32_t>(ctx->s_idx);
+    if (m > 0) {
+        CK(cudaMemcpyAsync(r.data(), ctx->s_rec.p, 48 * m, cudaMemcpyDeviceToHost, s), "read splats");
+        CK(cudaMemcpyAsync(rc.data(), ctx->s_rect.p, 8 * m, cudaMemcpyDeviceToHost, s), "read rects");
+        CK(cudaMemcpyAsync(key.data(), sk, 4 * m, cudaMemcpyDeviceToHost, s), "read depth");
+        CK(cudaMemcpyAsync(idx.data(), si, 4 * m, cudaMemcpyDeviceToHost, s), "read depth order");
+    }
+    CK(cudaStreamSynchronize(s), "debug sync");
+    std::vector<float> depth(std::max<int64_t>(m, 1), 0.0f);
+    for (int64_t i = 0; i < m; ++i)
+        if (idx[i] < (uint32_t)m) {
+            float d;
+            std::memcpy(&d, &key[i], 4);
+            depth[idx[i]] = d;
+        }
+    for (int64_t i = 0; i < m; ++i) {
+        const bool culled = rc[i].x == 0xffffffffu;
+        const float4 a = r[3 * i], b = r[3 * i + 1], c = r[3 * i + 2];
+        if (rec) {
+            float* o = rec + 10 * i;
+            if (culled) { for (int k = 0; k < 10; ++k) o[k] = 0.0f; }
+            else { o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w; o[8] = c.w; o[9] = depth[i]; }
+        }
+        if (rect) {
+            int32_t* q = rect + 4 * i;
+            if (culled) { q[0] = q[1] = q[2] = q[3] = -1; }
+            else { q[0] = rc[i].x & 0xffff; q[1] = rc[i].x >> 16; q[2] = rc[i].y & 0xffff; q[3] = rc[i].y >> 16; }
+        }
+        if (rgb) { rgb[3 * i] = culled ? 0.f : c.x; rgb[3 * i + 1] = culled ? 0.f : c.y; rgb[3 * i + 2] = culled ? 0.f : c.z; }
+    }
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_debug_pixel_state(h3dgs_ctx* ctx, float* T_final, int32_t* n_contrib, int64_t n_pixels) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->rendered) return fail(ctx, H3DGS_ERR_STATE, "debug: nothing rendered");
+    if (n_pixels != ctx->n_pixels) return fail(ctx, H3DGS_ERR_INVALID_ARG, "debug: n_pixels mismatch");
+    CK(cudaSetDevice(ctx->device), "set device");
+    if (T_final) CK(cudaMemcpyAsync(T_final, ctx->T_final.p, 4 * n_pixels, cudaMemcpyDeviceToHost, ctx->stream), "read T");
+    if (n_contrib) CK(cudaMemcpyAsync(n_contrib, ctx->n_contrib.p, 4 * n_pixels, cudaMemcpyDeviceToHost, ctx->stream), "read n");
+    CK(cudaStreamSynchronize(ctx->stream), "debug sync");
+    return H3DGS_OK;
+}
+
+}  // extern "C"

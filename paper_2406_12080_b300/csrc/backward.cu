@@ -1,0 +1,406 @@
+// Adjoint of the render path (a8), used to optimise interior hierarchy nodes (Sec. 5.1).
+//
+// Stage 1, per tile (one CTA, one thread per pixel): walk the tile's list back to front from the
+// last contributor, recomputing each alpha exactly as the forward pass did (same fp32 decisions)
+// and recovering the transmittance before each splat as T / (1 - alpha) from the saved final T, so
+// nothing per (pixel, splat) is stored.  Per splat, the gradient w.r.t. its screen parameters
+// (u, v, conic, o_n', o_p', colour) is summed over the warp with shuffles and added to a per-splat
+// accumulator with one atomic per value per warp.  The alpha' chain uses the derivative of
+// Eq. alphap, d alpha'/d alpha_p = (1/K)(1 - alpha_p)^(1/K - 1); an opacity gradient is zero on a
+// clamped branch (Sec. 6.3).
+//
+// Stage 2, per cut entry: recompute the interpolated Gaussian and its projection and apply the
+// adjoint of SH colour, EWA projection (Sigma' = M M^T, M = J W R(q) diag(s)), the opacity
+// compensation and the quaternion normalisation, then scatter (1 - t) of the result to node n and
+// t to its parent p (t is a constant; Sec. 5.1).  Leaves are skipped when frozen (Sec. 6.3).
+#include "internal.cuh"
+
+namespace h3dgs {
+
+namespace {
+
+constexpr float KH = -0.72134752044448170f;
+constexpr float KL = 1.44269504088896341f;
+constexpr float LN2 = 0.69314718055994531f;
+
+constexpr float SH_C0 = 0.28209479177387814f;
+constexpr float SH_C1 = 0.48860251190291992f;
+constexpr float SH_C2A = 1.0925484305920792f;
+constexpr float SH_C2B = 0.31539156525252005f;
+constexpr float SH_C2C = 0.54627421529603959f;
+constexpr float SH_C3A = 0.59004358992664352f;
+constexpr float SH_C3B = 2.8906114426405538f;
+constexpr float SH_C3C = 0.45704579946446572f;
+constexpr float SH_C3D = 0.37317633259011540f;
+constexpr float SH_C3E = 1.4453057213202769f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float alpha_prime(float ap, float K) {
+    if (K == 2.0f) return __fdividef(ap, 1.0f + sqrtf(1.0f - ap));
+    return 1.0f - ex2_approx(__fdividef(lg2_approx(1.0f - ap), K));
+}
+__device__ __forceinline__ float alpha_prime_grad(float ap, float K) {
+    if (K == 2.0f) return 0.5f * rsqrtf(1.0f - ap);
+    return __fdividef(ex2_approx(lg2_approx(1.0f - ap) * (__fdividef(1.0f, K) - 1.0f)), K);
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
+}
+
+}  // namespace
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
+                                                                 const int2* __restrict__ ranges,
+                                                                 const uint32_t* __restrict__ list,
+                                                                 const float4* __restrict__ splat,
+                                                                 const float* __restrict__ T_final,
+                                                                 const int32_t* __restrict__ n_contrib,
+                                                                 const float* __restrict__ dL,
+                                                                 float* __restrict__ sgrad) {
+    constexpr int NT = TW * TH;
+    __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
+    __shared__ uint32_t s_id[NT];
+    __shared__ int s_max;
+    const int64_t tile = blockIdx.x;
+    int lo = 0, hi = n_cams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cams[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    const DevCam& cam = cams[lo];
+    const int local = (int)(tile - cam.tile_base);
+    const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
+    const int px_i = tx * TW + (threadIdx.x % TW), py_i = ty * TH + (threadIdx.x / TW);
+    const bool inside = px_i < cam.width && py_i < cam.height;
+    const float px = (float)px_i + 0.5f, py = (float)py_i + 0.5f;
+    const int2 r = ranges[tile];
+    float T = 1.0f, g0 = 0, g1 = 0, g2 = 0;
+    int last = 0;
+    if (inside) {
+        const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
+        const int64_t plane = (int64_t)cam.width * cam.height;
+        const float* gp = dL + 3 * cam.pix_base + (int64_t)py_i * cam.width + px_i;
+        g0 = gp[0]; g1 = gp[plane]; g2 = gp[2 * plane];
+        T = T_final[pix];
+        last = n_contrib[pix];
+    }
+    float S0 = T * o.bg[0], S1 = T * o.bg[1], S2 = T * o.bg[2];
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    atomicMax(&s_max, last);
+    __syncthreads();
+    const int count = s_max;
+    const float clampv = o.alpha_clamp, afloor = o.alpha_floor;
+    for (int end = count; end > 0; end -= NT) {
+        const int n = min(NT, end);
+        const int first = end - n;
+        __syncthreads();
+        if ((int)threadIdx.x < n) {
+            const uint32_t s = __ldg(list + r.x + first + threadIdx.x);
+            s_id[threadIdx.x] = s;
+            s_a[threadIdx.x] = __ldg(splat + 3 * (int64_t)s);
+            s_b[threadIdx.x] = __ldg(splat + 3 * (int64_t)s + 1);
+            s_c[threadIdx.x] = __ldg(splat + 3 * (int64_t)s + 2);
+        }
+        __syncthreads();
+        for (int j = n - 1; j >= 0; --j) {
+            const int pos = first + j;
+            float gu = 0, gv = 0, gca = 0, gcb = 0, gcc = 0, gon = 0, gop = 0, gr = 0, gg = 0, gb = 0;
+            bool contrib = false;
+            if (pos < last) {
+                const float4 a = s_a[j], b = s_b[j], c = s_c[j];
+                const float dx = fsub(px, a.x), dy = fsub(py, a.y);
+                const float h = ffma(a.z, dx, fmul(a.w, dy));
+                const float gq = fmul(fmul(b.x, dy), dy);
+                const float p2 = ffma(dx, h, gq);
+                const float G = ex2_approx(p2);
+                const float xn = fmul(b.y, G);
+                const float an = fminf(clampv, xn);
+                float alpha = an, ap = 0.0f, xp = 0.0f;
+                if (b.w != 0.0f) {
+                    xp = fmul(b.z, G);
+                    ap = fminf(clampv, xp);
+                    alpha = ffma(b.w, alpha_prime(ap, c.w), fmul(fsub(1.0f, b.w), an));
+                }
+                if (alpha >= afloor) {
+                    contrib = true;
+                    const float oma = 1.0f - alpha;
+                    T = T / oma;
+                    const float wgt = alpha * T;
+                    gr = g0 * wgt; gg = g1 * wgt; gb = g2 * wgt;
+                    const float dalpha = g0 * (T * c.x - S0 / oma) + g1 * (T * c.y - S1 / oma) + g2 * (T * c.z - S2 / oma);
+                    S0 = fmaf(c.x, wgt, S0); S1 = fmaf(c.y, wgt, S1); S2 = fmaf(c.z, wgt, S2);
+                    float dG = 0.0f;
+                    const float dan = (b.w == 0.0f) ? dalpha : (1.0f - b.w) * dalpha;
+                    if (xn < clampv) { gon = dan * G; dG += dan * b.y; }
+                    if (b.w != 0.0f && xp < clampv) {
+                        const float dap = b.w * dalpha * alpha_prime_grad(ap, c.w);
+                        gop = dap * G;
+                        dG += dap * b.z;
+                    }
+                    const float dp2 = dG * G * LN2;
+                    gca = dp2 * dx * dx;
+                    gcb = dp2 * dx * dy;
+                    gcc = dp2 * dy * dy;
+                    gu = -dp2 * (2.0f * a.z * dx + a.w * dy);
+                    gv = -dp2 * (a.w * dx + 2.0f * b.x * dy);
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                gu = warp_sum(gu); gv = warp_sum(gv); gca = warp_sum(gca); gcb = warp_sum(gcb); gcc = warp_sum(gcc);
+                gon = warp_sum(gon); gop = warp_sum(gop); gr = warp_sum(gr); gg = warp_sum(gg); gb = warp_sum(gb);
+                if ((threadIdx.x & 31) == 0) {
+                    float* d = sgrad + 12 * (int64_t)s_id[j];
+                    atomicAdd(d + 0, gu); atomicAdd(d + 1, gv); atomicAdd(d + 2, gca); atomicAdd(d + 3, gcb);
+                    atomicAdd(d + 4, gcc); atomicAdd(d + 5, gon); atomicAdd(d + 6, gop); atomicAdd(d + 7, gr);
+                    atomicAdd(d + 8, gg); atomicAdd(d + 9, gb);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------- stage 2
+
+__global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const DevCam* __restrict__ cams, int n_cams,
+                                                            DevOpts o, const int32_t* __restrict__ cut_ids,
+                                                            const float* __restrict__ cut_t,
+                                                            const int64_t* __restrict__ cut_offsets,
+                                                            const uint2* __restrict__ rect,
+                                                            const uint32_t* __restrict__ n_splats,
+                                                            const float* __restrict__ sgrad, GradBufs gout,
+                                                            int freeze_leaves) {
+    const uint32_t M = *n_splats;
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        if (rect[m].x == 0xffffffffu) continue;  // culled
+        const float* gs = sgrad + 12 * (int64_t)m;
+        const float gu = gs[0], gv = gs[1], gca = gs[2], gcb = gs[3], gcc = gs[4], gon = gs[5], gop = gs[6];
+        const float grgb[3] = {gs[7], gs[8], gs[9]};
+        const int k = find_cam(cut_offsets, n_cams, m);
+        const DevCam& cam = cams[k];
+        const int32_t n = cut_ids[m];
+        const float t = (o.interpolate && cut_t) ? cut_t[m] : 0.0f;
+        const int32_t p = h.parent[n];
+        const bool use_p = (t != 0.0f) && p >= 0;
+        const float omt = 1.0f - t;
+        // ---- interpolated attributes
+        float mu[3], s[3], ql[4];
+        const float4 qn4 = h.rot[n];
+        float qv[4] = {qn4.x, qn4.y, qn4.z, qn4.w};
+        for (int d = 0; d < 3; ++d) { mu[d] = h.mean[3 * (int64_t)n + d]; s[d] = h.scale[3 * (int64_t)n + d]; }
+        if (use_p) {
+            const float4 qp4 = h.rot[p];
+            const float qpv[4] = {qp4.x, qp4.y, qp4.z, qp4.w};
+            for (int d = 0; d < 3; ++d) {
+                mu[d] = fmaf(t, h.mean[3 * (int64_t)p + d], omt * mu[d]);
+                s[d] = fmaf(t, h.scale[3 * (int64_t)p + d], omt * s[d]);
+            }
+            for (int d = 0; d < 4; ++d) qv[d] = fmaf(t, qpv[d], omt * qv[d]);
+        }
+        for (int d = 0; d < 4; ++d) ql[d] = qv[d];
+        const float qnorm = sqrtf(ql[0] * ql[0] + ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3]);
+        const float q[4] = {ql[0] / qnorm, ql[1] / qnorm, ql[2] / qnorm, ql[3] / qnorm};
+        // ---- forward recompute
+        const float* W = cam.R;
+        float xc[3];
+        for (int i = 0; i < 3; ++i) xc[i] = W[3 * i] * mu[0] + W[3 * i + 1] * mu[1] + W[3 * i + 2] * mu[2] + cam.T[i];
+        const float z = xc[2], iz = 1.0f / z;
+        const float xz = xc[0] * iz, yz = xc[1] * iz;
+        const bool x_in = xz > -cam.limx && xz < cam.limx, y_in = yz > -cam.limy && yz < cam.limy;
+        const float txc = fminf(fmaxf(xz, -cam.limx), cam.limx), tyc = fminf(fmaxf(yz, -cam.limy), cam.limy);
+        const float fx = cam.fx, fy = cam.fy;
+        const float J00 = fx * iz, J02 = -fx * txc * iz, J11 = fy * iz, J12 = -fy * tyc * iz;
+        float A2[2][3];
+        for (int j = 0; j < 3; ++j) {
+            A2[0][j] = J00 * W[j] + J02 * W[6 + j];
+            A2[1][j] = J11 * W[3 + j] + J12 * W[6 + j];
+        }
+        const float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
+        float Rq[3][3];
+        Rq[0][0] = 1.f - 2.f * (qy * qy + qz * qz); Rq[0][1] = 2.f * (qx * qy - qw * qz); Rq[0][2] = 2.f * (qx * qz + qw * qy);
+        Rq[1][0] = 2.f * (qx * qy + qw * qz); Rq[1][1] = 1.f - 2.f * (qx * qx + qz * qz); Rq[1][2] = 2.f * (qy * qz - qw * qx);
+        Rq[2][0] = 2.f * (qx * qz - qw * qy); Rq[2][1] = 2.f * (qy * qz + qw * qx); Rq[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+        float B[2][3], M[2][3];
+        for (int i = 0; i < 2; ++i)
+            for (int kk = 0; kk < 3; ++kk) {
+                B[i][kk] = A2[i][0] * Rq[0][kk] + A2[i][1] * Rq[1][kk] + A2[i][2] * Rq[2][kk];
+                M[i][kk] = B[i][kk] * s[kk];
+            }
+        const float aa = M[0][0] * M[0][0] + M[0][1] * M[0][1] + M[0][2] * M[0][2];
+        const float cc = M[1][0] * M[1][0] + M[1][1] * M[1][1] + M[1][2] * M[1][2];
+        const float bb = M[0][0] * M[1][0] + M[0][1] * M[1][1] + M[0][2] * M[1][2];
+        const float k0 = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+        const float k1 = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+        const float k2 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+        const float det = k0 * k0 + k1 * k1 + k2 * k2;
+        const float lp = o.lowpass;
+        const float af = aa + lp, cf = cc + lp;
+        const float D = det + lp * (aa + cc + lp);
+        const float iD = 1.0f / D;
+        const float comp = o.aa_compensate ? sqrtf(fmaxf(0.0f, det * iD)) : 1.0f;
+        const float ca = cf * iD * KH, cb = bb * iD * KL, cq = af * iD * KH;
+        // ---- opacities
+        const float on = h.opacity[n], op = use_p ? h.opacity[p] : 0.0f;
+        const float d_on = gon * comp, d_op = gop * comp;
+        const float dcomp = gon * on + gop * op;
+        // ---- conic -> (aa, bb, cc)
+        float dD = -(gca * ca + gcb * cb + gcc * cq) * iD;
+        float dcf = gca * KH * iD, daf = gcc * KH * iD, dbb = gcb * KL * iD;
+        float ddet = 0.0f;
+        if (o.aa_compensate && comp > 0.0f) {
+            ddet = dcomp / (2.0f * comp * D);
+            dD += -dcomp * comp / (2.0f * D);
+        }
+        daf += dD * cf; dcf += dD * af; dbb += dD * (-2.0f * bb);
+        const float daa = daf + ddet * cc, dcc = dcf + ddet * aa;
+        dbb += ddet * (-2.0f * bb);
+        float dM[2][3], dB[2][3], ds[3];
+        for (int kk = 0; kk < 3; ++kk) {
+            dM[0][kk] = 2.0f * daa * M[0][kk] + dbb * M[1][kk];
+            dM[1][kk] = 2.0f * dcc * M[1][kk] + dbb * M[0][kk];
+            ds[kk] = dM[0][kk] * B[0][kk] + dM[1][kk] * B[1][kk];
+            dB[0][kk] = dM[0][kk] * s[kk];
+            dB[1][kk] = dM[1][kk] * s[kk];
+        }
+        float dRq[3][3], dA2[2][3];
+        for (int j = 0; j < 3; ++j)
+            for (int kk = 0; kk < 3; ++kk) dRq[j][kk] = A2[0][j] * dB[0][kk] + A2[1][j] * dB[1][kk];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j) dA2[i][j] = dB[i][0] * Rq[j][0] + dB[i][1] * Rq[j][1] + dB[i][2] * Rq[j][2];
+        const float dJ00 = dA2[0][0] * W[0] + dA2[0][1] * W[1] + dA2[0][2] * W[2];
+        const float dJ02 = dA2[0][0] * W[6] + dA2[0][1] * W[7] + dA2[0][2] * W[8];
+        const float dJ11 = dA2[1][0] * W[3] + dA2[1][1] * W[4] + dA2[1][2] * W[5];
+        const float dJ12 = dA2[1][0] * W[6] + dA2[1][1] * W[7] + dA2[1][2] * W[8];
+        const float iz2 = iz * iz;
+        float dz = -dJ00 * fx * iz2 + dJ02 * fx * txc * iz2 - dJ11 * fy * iz2 + dJ12 * fy * tyc * iz2;
+        const float dtxc = -dJ02 * fx * iz, dtyc = -dJ12 * fy * iz;
+        const float dxz = gu * fx + (x_in ? dtxc : 0.0f);
+        const float dyz = gv * fy + (y_in ? dtyc : 0.0f);
+        const float dxc[3] = {dxz * iz, dyz * iz, dz - dxz * xc[0] * iz2 - dyz * xc[1] * iz2};
+        float dmu[3];
+        for (int j = 0; j < 3; ++j) dmu[j] = W[j] * dxc[0] + W[3 + j] * dxc[1] + W[6 + j] * dxc[2];
+        // rotation matrix w.r.t. the unit quaternion
+        float dq[4];
+        dq[0] = 2.f * (-qz * dRq[0][1] + qy * dRq[0][2] + qz * dRq[1][0] - qx * dRq[1][2] - qy * dRq[2][0] + qx * dRq[2][1]);
+        dq[1] = 2.f * (qy * dRq[0][1] + qz * dRq[0][2] + qy * dRq[1][0] - 2.f * qx * dRq[1][1] - qw * dRq[1][2] +
+                       qz * dRq[2][0] + qw * dRq[2][1] - 2.f * qx * dRq[2][2]);
+        dq[2] = 2.f * (-2.f * qy * dRq[0][0] + qx * dRq[0][1] + qw * dRq[0][2] + qx * dRq[1][0] + qz * dRq[1][2] -
+                       qw * dRq[2][0] + qz * dRq[2][1] - 2.f * qy * dRq[2][2]);
+        dq[3] = 2.f * (-2.f * qz * dRq[0][0] - qw * dRq[0][1] + qx * dRq[0][2] + qw * dRq[1][0] - 2.f * qz * dRq[1][1] +
+                       qy * dRq[1][2] + qx * dRq[2][0] + qy * dRq[2][1]);
+        const float qdot = q[0] * dq[0] + q[1] * dq[1] + q[2] * dq[2] + q[3] * dq[3];
+        float dql[4];
+        for (int d = 0; d < 4; ++d) dql[d] = (dq[d] - q[d] * qdot) / qnorm;
+        // ---- colour
+        float dv[3] = {mu[0] - cam.c[0], mu[1] - cam.c[1], mu[2] - cam.c[2]};
+        const float dn = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+        const float x = dv[0] / dn, y = dv[1] / dn, zz = dv[2] / dn;
+        const float xx = x * x, yy = y * y, z2 = zz * zz;
+        float Y[16], dY[16][3];
+        Y[0] = SH_C0;
+        Y[1] = -SH_C1 * y; Y[2] = SH_C1 * zz; Y[3] = -SH_C1 * x;
+        Y[4] = SH_C2A * x * y; Y[5] = -SH_C2A * y * zz; Y[6] = SH_C2B * (2.f * z2 - xx - yy);
+        Y[7] = -SH_C2A * x * zz; Y[8] = SH_C2C * (xx - yy);
+        Y[9] = -SH_C3A * y * (3.f * xx - yy); Y[10] = SH_C3B * x * y * zz;
+        Y[11] = -SH_C3C * y * (4.f * z2 - xx - yy); Y[12] = SH_C3D * zz * (2.f * z2 - 3.f * xx - 3.f * yy);
+        Y[13] = -SH_C3C * x * (4.f * z2 - xx - yy); Y[14] = SH_C3E * zz * (xx - yy);
+        Y[15] = -SH_C3A * x * (xx - 3.f * yy);
+        for (int kk = 0; kk < 16; ++kk) dY[kk][0] = dY[kk][1] = dY[kk][2] = 0.f;
+        dY[1][1] = -SH_C1; dY[2][2] = SH_C1; dY[3][0] = -SH_C1;
+        dY[4][0] = SH_C2A * y; dY[4][1] = SH_C2A * x;
+        dY[5][1] = -SH_C2A * zz; dY[5][2] = -SH_C2A * y;
+        dY[6][0] = -2.f * SH_C2B * x; dY[6][1] = -2.f * SH_C2B * y; dY[6][2] = 4.f * SH_C2B * zz;
+        dY[7][0] = -SH_C2A * zz; dY[7][2] = -SH_C2A * x;
+        dY[8][0] = 2.f * SH_C2C * x; dY[8][1] = -2.f * SH_C2C * y;
+        dY[9][0] = -6.f * SH_C3A * x * y; dY[9][1] = -SH_C3A * (3.f * xx - 3.f * yy);
+        dY[10][0] = SH_C3B * y * zz; dY[10][1] = SH_C3B * x * zz; dY[10][2] = SH_C3B * x * y;
+        dY[11][0] = 2.f * SH_C3C * x * y; dY[11][1] = -SH_C3C * (4.f * z2 - xx - 3.f * yy); dY[11][2] = -8.f * SH_C3C * y * zz;
+        dY[12][0] = -6.f * SH_C3D * x * zz; dY[12][1] = -6.f * SH_C3D * y * zz; dY[12][2] = SH_C3D * (6.f * z2 - 3.f * xx - 3.f * yy);
+        dY[13][0] = -SH_C3C * (4.f * z2 - 3.f * xx - yy); dY[13][1] = 2.f * SH_C3C * x * y; dY[13][2] = -8.f * SH_C3C * x * zz;
+        dY[14][0] = 2.f * SH_C3E * zz * x; dY[14][1] = -2.f * SH_C3E * zz * y; dY[14][2] = SH_C3E * (xx - yy);
+        dY[15][0] = -SH_C3A * (3.f * xx - 3.f * yy); dY[15][1] = 6.f * SH_C3A * x * y;
+        const float* shn = reinterpret_cast<const float*>(h.sh) + (int64_t)NSH * n;
+        const float* shp = reinterpret_cast<const float*>(h.sh) + (int64_t)NSH * (use_p ? p : n);
+        float col[3] = {0.5f, 0.5f, 0.5f};
+        for (int c = 0; c < NSH; ++c) {
+            const float shv = use_p ? fmaf(t, shp[c], omt * shn[c]) : shn[c];
+            col[c % 3] += shv * Y[c / 3];
+        }
+        float ddir[3] = {0.f, 0.f, 0.f};
+        const float wn = use_p ? omt : 1.0f;
+        const bool leaf_n = h.child_count[n] == 0;
+        const bool write_n = !(freeze_leaves && leaf_n);
+        for (int c = 0; c < NSH; ++c) {
+            const int ch = c % 3;
+            if (col[ch] < 0.0f) continue;
+            const float g = grgb[ch] * Y[c / 3];
+            if (write_n && g != 0.0f) atomicAdd(gout.sh + (int64_t)NSH * n + c, wn * g);
+            if (use_p && g != 0.0f) atomicAdd(gout.sh + (int64_t)NSH * p + c, t * g);
+            const float shv = use_p ? fmaf(t, shp[c], omt * shn[c]) : shn[c];
+            for (int j = 0; j < 3; ++j) ddir[j] += grgb[ch] * shv * dY[c / 3][j];
+        }
+        const float dot = ddir[0] * x + ddir[1] * y + ddir[2] * zz;
+        dmu[0] += (ddir[0] - x * dot) / dn;
+        dmu[1] += (ddir[1] - y * dot) / dn;
+        dmu[2] += (ddir[2] - zz * dot) / dn;
+        // ---- scatter to node and parent
+        if (write_n) {
+            for (int d = 0; d < 3; ++d) {
+                atomicAdd(gout.mean + 3 * (int64_t)n + d, wn * dmu[d]);
+                atomicAdd(gout.scale + 3 * (int64_t)n + d, wn * ds[d]);
+            }
+            for (int d = 0; d < 4; ++d) atomicAdd(gout.rot + 4 * (int64_t)n + d, wn * dql[d]);
+            atomicAdd(gout.opacity + n, d_on);
+        }
+        if (use_p) {
+            for (int d = 0; d < 3; ++d) {
+                atomicAdd(gout.mean + 3 * (int64_t)p + d, t * dmu[d]);
+                atomicAdd(gout.scale + 3 * (int64_t)p + d, t * ds[d]);
+            }
+            for (int d = 0; d < 4; ++d) atomicAdd(gout.rot + 4 * (int64_t)p + d, t * dql[d]);
+            atomicAdd(gout.opacity + p, d_op);
+        }
+    }
+}
+
+cudaError_t launch_backward(const DevHier& h, const DevCam* cams, int n_cams, int64_t n_tiles, const DevOpts& o,
+                            const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets, const int2* ranges,
+                            const uint32_t* list, const float4* splat, const uint2* rect, const uint32_t* n_splats,
+                            int64_t cap, const float* T_final, const int32_t* n_contrib, const float* dL,
+                            float* splat_grad, const GradBufs& g, int freeze_leaves, int grid, cudaStream_t s) {
+    (void)cap;
+    if (n_tiles > 0) {
+        const unsigned tg = (unsigned)n_tiles;
+#define BW(TWV, THV)                                                                                          \
+    backward_blend_kernel<TWV, THV><<<tg, TWV * THV, 0, s>>>(cams, n_cams, o, ranges, list, splat, T_final, \
+                                                               n_contrib, dL, splat_grad)
+        if (o.tile_w == 16 && o.tile_h == 16) BW(16, 16);
+        else if (o.tile_w == 8 && o.tile_h == 8) BW(8, 8);
+        else if (o.tile_w == 32 && o.tile_h == 8) BW(32, 8);
+        else if (o.tile_w == 8 && o.tile_h == 32) BW(8, 32);
+        else if (o.tile_w == 16 && o.tile_h == 8) BW(16, 8);
+        else if (o.tile_w == 32 && o.tile_h == 4) BW(32, 4);
+        else return cudaErrorInvalidValue;
+#undef BW
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    backward_splat_kernel<<<grid, 128, 0, s>>>(h, cams, n_cams, o, cut_ids, cut_t, cut_offsets, rect, n_splats, splat_grad,
+                                               g, freeze_leaves);
+    return cudaGetLastError();
+}
+
+}  // namespace h3dgs

@@ -1,0 +1,235 @@
+// Hierarchy residency (a0) and cut selection with interpolation weights (a1, a2).
+//
+// The cut follows the paper's constant-time-per-node rule (Sec. 4.2): node n is selected iff
+// (eps(n) < tau or n is a leaf) and (n is the root or eps(parent) >= tau).  Because a parent's box
+// contains its children's, eps never decreases towards the root, so this per-node test yields
+// exactly one node on every root-to-leaf path.  The kernels scan all nodes (one 32-byte record
+// each, plus the parent's record which is usually an L1/L2 hit for siblings) and test every
+// camera of the batch against each node while it is in registers:
+//   pass 1  one bit per (camera, node) in a mask, a count per (camera, block);
+//   pass 2  scans of the counts (per camera over blocks, then over cameras);
+//   pass 3  ordered compaction: ids in ascending order, t recomputed for the selected nodes.
+#include "internal.cuh"
+
+namespace h3dgs {
+
+// ------------------------------------------------------------------------------------ a0
+
+__global__ void pack_records_kernel(int64_t n, const float* __restrict__ bmin, const float* __restrict__ bmax,
+                                    const int32_t* __restrict__ parent, const int32_t* __restrict__ ccount,
+                                    float4* __restrict__ rec) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        rec[2 * v] = make_float4(bmin[3 * v], bmin[3 * v + 1], bmin[3 * v + 2], __int_as_float(parent[v]));
+        rec[2 * v + 1] = make_float4(bmax[3 * v], bmax[3 * v + 1], bmax[3 * v + 2], __int_as_float(ccount[v]));
+    }
+}
+
+cudaError_t launch_pack_records(const h3dgs_hierarchy& h, float4* rec, cudaStream_t s) {
+    int64_t blocks = (h.n_nodes + 255) / 256;
+    if (blocks > 65535 * 8) blocks = 65535 * 8;
+    pack_records_kernel<<<(unsigned)blocks, 256, 0, s>>>(h.n_nodes, h.box_min, h.box_max, h.parent, h.child_count, rec);
+    return cudaGetLastError();
+}
+
+// Camera set-up: copies the raw cameras and derives, in a fixed fp32 order,
+//   c_j = -(R_0j T_0 + R_1j T_1 + R_2j T_2)  as -fmaf(R_2j, T_2, fmaf(R_1j, T_1, R_0j * T_0)),
+//   f = max(fx, fy),  limx = (0.65 W) / fx,  limy = (0.65 H) / fy.
+__global__ void camera_setup_kernel(CamBatch b, DevCam* __restrict__ out) {
+    const int i = threadIdx.x;
+    if (i >= b.count) return;
+    const h3dgs_camera& c = b.cam[i];
+    DevCam d;
+    for (int k = 0; k < 9; ++k) d.R[k] = c.R[k];
+    for (int k = 0; k < 3; ++k) d.T[k] = c.T[k];
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    d.width = c.width; d.height = c.height; d.znear = c.znear; d.tau = c.tau;
+    for (int j = 0; j < 3; ++j) {
+        float acc = fmul(c.R[j], c.T[0]);
+        acc = ffma(c.R[3 + j], c.T[1], acc);
+        acc = ffma(c.R[6 + j], c.T[2], acc);
+        d.c[j] = -acc;
+    }
+    d.f = fmaxf(c.fx, c.fy);
+    d.limx = fdiv(fmul(0.65f, (float)c.width), c.fx);
+    d.limy = fdiv(fmul(0.65f, (float)c.height), c.fy);
+    d.tiles_x = b.tiles_x[i];
+    d.tiles_y = b.tiles_y[i];
+    d.tile_base = b.tile_base[i];
+    d.pix_base = b.pix_base[i];
+    out[b.first + i] = d;
+}
+
+cudaError_t launch_camera_setup(const CamBatch& b, const DevOpts*, DevCam* cams, cudaStream_t s) {
+    camera_setup_kernel<<<1, CAM_BATCH, 0, s>>>(b, cams);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ a1 + a2
+
+constexpr int CUT_BLOCK = 256;
+
+__device__ __forceinline__ bool cut_test(const DevCam& cam, const float4 lo, const float4 hi, const float4 plo,
+                                         const float4 phi, bool has_parent, float* en_out, float* ep_out) {
+    const float en = granularity(cam, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z);
+    const bool leaf = __float_as_int(hi.w) == 0;
+    float ep = __int_as_float(0x7f800000);
+    bool parent_ok = true;
+    if (has_parent) {
+        ep = granularity(cam, plo.x, plo.y, plo.z, phi.x, phi.y, phi.z);
+        parent_ok = ep >= cam.tau;
+    }
+    *en_out = en;
+    *ep_out = ep;
+    return ((en < cam.tau) || leaf) && parent_ok;
+}
+
+// pass 1: selection bits and per-(camera, block) counts
+__global__ void __launch_bounds__(CUT_BLOCK) cut_mark_kernel(const float4* __restrict__ rec, int64_t n,
+                                                             const DevCam* __restrict__ cams, int n_cams,
+                                                             int64_t chunk, int64_t words,
+                                                             uint32_t* __restrict__ mask,
+                                                             uint32_t* __restrict__ block_counts) {
+    extern __shared__ uint32_t s_count[];  // [n_cams]
+    for (int k = threadIdx.x; k < n_cams; k += blockDim.x) s_count[k] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t base = blockIdx.x * chunk;
+    const int64_t end = min(base + chunk, n);
+    for (int64_t v0 = base; v0 < end; v0 += CUT_BLOCK) {
+        const int64_t v = v0 + threadIdx.x;
+        const bool valid = v < end;
+        float4 lo = make_float4(0, 0, 0, 0), hi = lo, plo = lo, phi = lo;
+        int32_t p = -1;
+        if (valid) {
+            lo = __ldg(rec + 2 * v);
+            hi = __ldg(rec + 2 * v + 1);
+            p = __float_as_int(lo.w);
+            if (p >= 0) {
+                plo = __ldg(rec + 2 * (int64_t)p);
+                phi = __ldg(rec + 2 * (int64_t)p + 1);
+            }
+        }
+        for (int k = 0; k < n_cams; ++k) {
+            float en, ep;
+            const bool sel = valid && cut_test(cams[k], lo, hi, plo, phi, p >= 0, &en, &ep);
+            const uint32_t word = __ballot_sync(0xffffffffu, sel);
+            if (lane == 0) {
+                const int64_t w = (v - lane) >> 5;
+                if (((v - lane) < end) || word) {
+                    if (w < words) mask[(int64_t)k * words + w] = word;
+                }
+                if (word) atomicAdd(&s_count[k], (uint32_t)__popc(word));
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_cams; k += blockDim.x) block_counts[(int64_t)k * gridDim.x + blockIdx.x] = s_count[k];
+}
+
+// pass 2a: per camera, exclusive scan of the block counts (in place) and the camera total
+__global__ void cut_scan_blocks_kernel(uint32_t* __restrict__ block_counts, int G, int64_t* __restrict__ cam_totals) {
+    const int k = blockIdx.x;
+    uint32_t* c = block_counts + (int64_t)k * G;
+    __shared__ uint32_t s_part[1024];
+    // each thread scans a contiguous segment
+    const int per = (G + blockDim.x - 1) / blockDim.x;
+    const int s0 = threadIdx.x * per, s1 = min(G, s0 + per);
+    uint32_t sum = 0;
+    for (int i = s0; i < s1; ++i) sum += c[i];
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) { uint32_t x = s_part[i]; s_part[i] = run; run += x; }
+        cam_totals[k] = run;
+    }
+    __syncthreads();
+    uint32_t run = s_part[threadIdx.x];
+    for (int i = s0; i < s1; ++i) { uint32_t x = c[i]; c[i] = run; run += x; }
+}
+
+// pass 2b: exclusive scan of the camera totals -> raw offsets; clamped offsets for the caller
+__global__ void cut_scan_cams_kernel(int64_t* __restrict__ cam_totals, int n_cams, int64_t capacity,
+                                     int64_t* __restrict__ cut_offsets, uint32_t* __restrict__ flags) {
+    if (threadIdx.x != 0) return;
+    int64_t run = 0;
+    for (int k = 0; k < n_cams; ++k) {
+        const int64_t x = cam_totals[k];
+        cam_totals[k] = run;
+        cut_offsets[k] = run < capacity ? run : capacity;
+        run += x;
+    }
+    cam_totals[n_cams] = run;
+    cut_offsets[n_cams] = run < capacity ? run : capacity;
+    if (run > capacity) atomicOr(flags, FLAG_CUT_TRUNCATED);
+}
+
+// pass 3: ordered compaction and interpolation weights
+__global__ void __launch_bounds__(CUT_BLOCK) cut_write_kernel(const float4* __restrict__ rec, int64_t n,
+                                                              const DevCam* __restrict__ cams, int n_cams,
+                                                              int64_t chunk, int64_t words,
+                                                              const uint32_t* __restrict__ mask,
+                                                              const uint32_t* __restrict__ block_offs,
+                                                              const int64_t* __restrict__ cam_offs,
+                                                              int64_t capacity, int32_t* __restrict__ cut_ids,
+                                                              float* __restrict__ cut_t) {
+    __shared__ uint32_t s_warp[CUT_BLOCK / 32];
+    __shared__ int64_t s_run;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = blockIdx.x * chunk;
+    const int64_t end = min(base + chunk, n);
+    for (int k = 0; k < n_cams; ++k) {
+        const DevCam& cam = cams[k];
+        if (threadIdx.x == 0) s_run = cam_offs[k] + block_offs[(int64_t)k * gridDim.x + blockIdx.x];
+        __syncthreads();
+        for (int64_t v0 = base; v0 < end; v0 += CUT_BLOCK) {
+            const int64_t v = v0 + threadIdx.x;
+            const int64_t w = (v0 >> 5) + warp;
+            const uint32_t word = (v0 + warp * 32 < end && w < words) ? mask[(int64_t)k * words + w] : 0u;
+            const bool sel = (word >> lane) & 1u;
+            if (lane == 0) s_warp[warp] = __popc(word);
+            __syncthreads();
+            uint32_t before = 0, total = 0;
+            for (int i = 0; i < CUT_BLOCK / 32; ++i) {
+                const uint32_t c = s_warp[i];
+                before += (i < warp) ? c : 0u;
+                total += c;
+            }
+            const int64_t pos = s_run + before + __popc(word & ((1u << lane) - 1u));
+            if (sel && pos < capacity) {
+                cut_ids[pos] = (int32_t)v;
+                if (cut_t) {
+                    const float4 lo = __ldg(rec + 2 * v), hi = __ldg(rec + 2 * v + 1);
+                    const int32_t p = __float_as_int(lo.w);
+                    float t = 0.0f;
+                    if (p >= 0) {
+                        const float4 plo = __ldg(rec + 2 * (int64_t)p), phi = __ldg(rec + 2 * (int64_t)p + 1);
+                        const float en = granularity(cam, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z);
+                        const float ep = granularity(cam, plo.x, plo.y, plo.z, phi.x, phi.y, phi.z);
+                        t = parent_weight(cam.tau, en, ep);
+                    }
+                    cut_t[pos] = t;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_run += total;
+            __syncthreads();
+        }
+    }
+}
+
+cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const CutWork& w, int32_t* cut_ids,
+                       float* cut_t, int64_t* cut_offsets, int64_t capacity, uint32_t* flags, cudaStream_t s) {
+    const size_t smem = sizeof(uint32_t) * (size_t)n_cams;
+    cut_mark_kernel<<<w.blocks, CUT_BLOCK, smem, s>>>(h.rec, h.n, cams, n_cams, w.chunk, w.words, w.mask,
+                                                      w.block_counts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cut_scan_blocks_kernel<<<n_cams, 256, 0, s>>>(w.block_counts, w.blocks, w.cam_totals);
+    cut_scan_cams_kernel<<<1, 32, 0, s>>>(w.cam_totals, n_cams, capacity, cut_offsets, flags);
+    cut_write_kernel<<<w.blocks, CUT_BLOCK, 0, s>>>(h.rec, h.n, cams, n_cams, w.chunk, w.words, w.mask, w.block_counts,
+                                                    w.cam_totals, capacity, cut_ids, cut_t);
+    return cudaGetLastError();
+}
+
+}  // namespace h3dgs

@@ -1,0 +1,186 @@
+// Internal declarations shared by the CUDA translation units of libh3dgs (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "h3dgs.h"
+
+namespace h3dgs {
+
+constexpr int NSH = 48;          // degree-3 SH: 16 basis functions x 3 channels, layout [k*3 + ch]
+constexpr int NINTERP = 62;      // exported interpolated row: mean 3, scale 3, rot 4, sh 48, o_n, o_p, t, K
+constexpr int MAX_CAMS = 4096;
+constexpr int CAM_BATCH = 32;    // cameras per set-up launch (passed by value)
+
+// Device flag bits (ctx->d_flags)
+constexpr uint32_t FLAG_PAIRS_OVERFLOW = 1u << 0;
+constexpr uint32_t FLAG_SPLATS_OVERFLOW = 1u << 1;
+constexpr uint32_t FLAG_CUT_TRUNCATED = 1u << 2;
+
+// Per-camera data on the device.  Raw fields come from h3dgs_camera; the derived floats are
+// computed on the device in a fixed fp32 order (camera_setup kernel); integer bookkeeping
+// (tile grid, offsets into the packed tile/pixel spaces) is filled on the host.
+struct DevCam {
+    float R[9];
+    float T[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear, tau;
+    float c[3];        // camera centre  -R^T T
+    float f;           // max(fx, fy)
+    float limx, limy;  // 1.3 tan(half fov): clamp of x/z, y/z in the EWA Jacobian
+    int32_t tiles_x, tiles_y;
+    int64_t tile_base; // first global tile index of this camera
+    int64_t pix_base;  // first pixel of this camera in the packed pixel space
+};
+
+struct CamBatch {
+    int32_t first, count;
+    h3dgs_camera cam[CAM_BATCH];
+    int32_t tiles_x[CAM_BATCH], tiles_y[CAM_BATCH];
+    int64_t tile_base[CAM_BATCH], pix_base[CAM_BATCH];
+};
+
+// Render options as used on the device.
+struct DevOpts {
+    int32_t tile_w, tile_h;
+    float lowpass, alpha_clamp, alpha_floor, t_min;
+    int32_t aa_compensate, interpolate;
+    float bg[3];
+};
+
+// Borrowed hierarchy arrays (device).
+struct DevHier {
+    int64_t n;
+    const float* mean;
+    const float* scale;
+    const float4* rot;
+    const float* opacity;
+    const float4* sh;      // [N][12] float4
+    const int32_t* parent;
+    const int32_t* child_count;
+    const float4* rec;     // packed cut records [N][2]: {box_min.xyz, parent}, {box_max.xyz, child_count}
+};
+
+// ---------------------------------------------------------------- fp32 ops in a fixed order
+// These never contract into FMA (and ffma always is one), so both sides of the parity tests can
+// evaluate integer decisions bit-identically.
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// Granularity (Sec. 4.2): projected size of the node's box, largest side over the distance from the
+// camera centre to the closest point of the box; +inf with the camera inside the box.
+__device__ __forceinline__ float granularity(const DevCam& cam, float lx, float ly, float lz, float hx, float hy,
+                                             float hz) {
+    const float dx = fmaxf(fmaxf(fsub(lx, cam.c[0]), fsub(cam.c[0], hx)), 0.0f);
+    const float dy = fmaxf(fmaxf(fsub(ly, cam.c[1]), fsub(cam.c[1], hy)), 0.0f);
+    const float dz = fmaxf(fmaxf(fsub(lz, cam.c[2]), fsub(cam.c[2], hz)), 0.0f);
+    float d2 = fmul(dx, dx);
+    d2 = ffma(dy, dy, d2);
+    d2 = ffma(dz, dz, d2);
+    const float size = fmaxf(fmaxf(fsub(hx, lx), fsub(hy, ly)), fsub(hz, lz));
+    if (d2 == 0.0f) return __int_as_float(0x7f800000);
+    return fdiv(fmul(cam.f, size), fsqrt(d2));
+}
+
+// Interpolation weight of the parent (Eq. t_interp); 0 unless eps_n < tau <= eps_p < inf.
+__device__ __forceinline__ float parent_weight(float tau, float en, float ep) {
+    if (!(en < tau) || !(ep >= tau) || isinf(ep)) return 0.0f;
+    const float t = fdiv(fsub(tau, en), fsub(ep, en));
+    return fminf(fmaxf(t, 0.0f), 1.0f);
+}
+
+// Camera index of global entry m given the per-camera offsets (binary search, n_cams small).
+__device__ __forceinline__ int find_cam(const int64_t* __restrict__ offs, int n_cams, int64_t m) {
+    int lo = 0, hi = n_cams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(offs + mid) <= m) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- launchers (host side)
+// cut.cu
+cudaError_t launch_pack_records(const h3dgs_hierarchy& h, float4* rec, cudaStream_t s);
+cudaError_t launch_camera_setup(const CamBatch& b, const DevOpts* opts, DevCam* cams, cudaStream_t s);
+struct CutWork {
+    uint32_t* mask;          // [n_cams][words]
+    uint32_t* block_counts;  // [n_cams][G]
+    int64_t* cam_totals;     // [n_cams + 1] raw (untruncated) exclusive offsets
+    int blocks;              // G
+    int64_t chunk;           // nodes per block
+    int64_t words;           // mask words per camera
+};
+cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const CutWork& w, int32_t* cut_ids,
+                       float* cut_t, int64_t* cut_offsets, int64_t capacity, uint32_t* flags, cudaStream_t s);
+
+// preprocess.cu
+struct SplatBufs {
+    float4* rec;           // [cap][3]: {u, v, ca, cb}, {cc, on', op', t}, {r, g, b, K}
+    uint2* rect;           // [cap]: (x0 | x1 << 16, y0 | y1 << 16)
+    uint32_t* depth_key;   // [cap] fp32 depth bits, 0xffffffff when culled
+    uint32_t* tiles;       // [cap] tiles touched (0 when culled)
+    uint32_t* n_splats;    // [1] min(M_total, cap)
+    uint32_t* n_visible;   // [1]
+};
+cudaError_t launch_preprocess(const DevHier& h, const DevCam* cams, int n_cams, const DevOpts& o,
+                              const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets,
+                              int64_t cap, const SplatBufs& sb, uint32_t* flags, int grid, cudaStream_t s);
+cudaError_t launch_interpolate_export(const DevHier& h, int n_cams, const int32_t* cut_ids, const float* cut_t,
+                                      const int64_t* cut_offsets, int interpolate, float* out, int64_t m_total,
+                                      cudaStream_t s);
+
+// sort.cu
+struct SortWork {
+    uint32_t* hist;         // [256][G]
+    uint32_t* digit_total;  // [256]
+    uint32_t* partial;      // [G + 1] scan partials
+    int blocks;             // G
+};
+// Stable LSD radix sort of n (device count) key/value pairs on key bits [0, bits).  Sorts (k0, v0)
+// ping-ponging with (k1, v1); returns via *result_in_1 whether the result is in (k1, v1).
+cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
+                             int bits, const SortWork& w, bool* result_in_1, cudaStream_t s);
+cudaError_t launch_iota(uint32_t* out, const uint32_t* n_dev, int grid, cudaStream_t s);
+// out[i] = exclusive prefix sum of in[idx[i]] over i < n; *total = full sum.
+cudaError_t scan_gathered(const uint32_t* in, const uint32_t* idx, uint32_t* out, const uint32_t* n_dev,
+                          uint32_t* total, const SortWork& w, cudaStream_t s);
+// Also writes *n_pairs_kept = min(*n_pairs, cap_pairs) (the count sorted afterwards).
+cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_offsets, const SplatBufs& sb,
+                             const uint32_t* order, const uint32_t* pair_off, const uint32_t* n_pairs,
+                             int64_t cap_pairs, uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals,
+                             uint32_t* flags, int grid, cudaStream_t s);
+cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_pairs_kept, int2* ranges, int grid, cudaStream_t s);
+
+// blend.cu
+cudaError_t launch_blend(const DevCam* cams, int n_cams, int64_t n_tiles, const DevOpts& o, const int2* ranges,
+                         const uint32_t* list, const float4* splat, float* images, float* T_final,
+                         int32_t* n_contrib, cudaStream_t s);
+
+// builder.cu
+struct BuildOut {
+    float *mean, *scale, *rot, *opacity, *sh, *box_min, *box_max;
+    int32_t *parent, *child_start, *child_count;
+};
+// Builds the 2L - 1 node hierarchy over L leaves (synchronous on stream s).
+cudaError_t build_hierarchy(int64_t L, const float* mean, const float* scale, const float* rot, const float* opacity,
+                            const float* sh, const BuildOut& out, const SortWork& sw, int num_sms, cudaStream_t s);
+
+// backward.cu
+struct GradBufs {
+    float* mean; float* scale; float* rot; float* opacity; float* sh;
+};
+cudaError_t launch_backward(const DevHier& h, const DevCam* cams, int n_cams, int64_t n_tiles, const DevOpts& o,
+                            const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets,
+                            const int2* ranges, const uint32_t* list, const float4* splat, const uint2* rect,
+                            const uint32_t* n_splats, int64_t cap, const float* T_final, const int32_t* n_contrib,
+                            const float* dL, float* splat_grad, const GradBufs& g, int freeze_leaves, int grid,
+                            cudaStream_t s);
+
+}  // namespace h3dgs
