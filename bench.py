@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the hierarchical 3D Gaussian render path on one B300 per rank.
+
+Workload: the street corridor (1M leaf Gaussians, ~2M hierarchy nodes) seen by one 1920x1080
+camera at tau = 6 px.  One step = one frame of the hot path through the C ABI: cut selection with
+interpolation weights, then interpolate + project + SH, depth sort, binning, tile sort, ranges and
+blend.  The hierarchy is built on the device by the library and stays resident (like the paper's
+GPU-resident nodes).  The frame is captured once in a CUDA graph and replayed; L2 is flushed
+(256 MB write) between timed steps, outside the timed events.
+
+Also reported in the same JSON line: fwd+bwd views/s (frame + adjoint), the end-to-end rate with
+the image read back to pinned host memory every step, per-stage times, the roofline fraction of
+the dominant kernel, the SM clocks during the timed region, and the CPU oracle timed on the host
+cores (cpu_baseline).  `--impl reference` times the CPU oracle alone (the deliberately slow
+reference program of this repository).
+
+Multi-GPU: `torchrun --nproc-per-node N bench.py --gpus N`: every rank renders its own replica of
+the workload (views are independent, no collective on the data path); value = frames of all
+ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s (cut+render) & fwd+bwd views/s; % of HBM/FP32 roofline"
+L2_FLUSH_BYTES = 256 << 20
+# FP32 operations per evaluated (pixel, splat) pair in the blend kernel, from its op list:
+#   dx, dy (2 FADD); exponent h = fma(ca, dx, cb dy), g = (cc dy) dy, p2 = fma(dx, h, g) (3 FMUL + 2 FFMA);
+#   alpha_n = min(clamp, o_n G) (FMUL + FMNMX); floor test (FSETP); T (1 - alpha) (FADD + FMUL); stop test
+#   (FSETP); w = alpha T (FMUL); colour (3 FFMA)  -> 22 flops (FFMA = 2) plus one MUFU (ex2).
+#   With t != 0: o_p G, min, 1 - ap, 1 + sqrt, divide, 1 - t, (1 - t) alpha_n, fma(t, a', .) -> +10 flops.
+FLOPS_PER_EVAL = 22
+FLOPS_PER_EVAL_T = 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-leaves", type=int, default=1_000_000)
+    ap.add_argument("--tau", type=float, default=6.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_time(scene, n_frames: int, budget_s: float = 25.0):
+    """Time the CPU oracle (cut + render of the full frame) on the host cores."""
+    import oracle
+    h = oracle.build_tree(scene.leaves)   # offline build, not timed
+    cam = scene.cameras[0]
+    times = []
+    t_start = time.perf_counter()
+    for _ in range(max(1, n_frames)):
+        t0 = time.perf_counter()
+        oracle.render(cam, h, oracle.Opts())
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return {"value": len(times) / float(np.sum(times)), "unit": "frames/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{len(times)} full 1920x1080 frames (cut + interpolate/project/SH + tile lists + blend), "
+                      f"fp64 values with fp32 decisions, OpenMP"}
+
+
+# ----------------------------------------------------------------------------------- our path
+
+def launches_per_frame(n_tiles: int) -> int:
+    tile_bits = max(1, int(np.ceil(np.log2(max(n_tiles, 2)))))
+    cut = 1 + 4                                   # camera set-up, mark, 2 scans, ordered write
+    render = (1 + 1 + 1 + 3 * 4 + 3 + 1 + 3 * ((tile_bits + 7) // 8) + 1 + 1)
+    return cut + render
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2406_12080_b300 import build, h3dgs, synth
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.Stream(dev)
+    scene = synth.corridor_scene(n_leaves=args.n_leaves, tau=args.tau)
+    cam = scene.cameras[0]
+    cams = [cam]
+    ctx = h3dgs.Context(local, stream)
+    with torch.cuda.stream(stream):
+        hier = ctx.build(scene.leaves)
+        ctx.upload(hier)
+        N = hier.n
+        cap = N
+        ids = torch.empty(cap, dtype=torch.int32, device=dev)
+        tt = torch.empty(cap, dtype=torch.float32, device=dev)
+        offs = torch.empty(2, dtype=torch.int64, device=dev)
+        npix = 3 * cam.width * cam.height
+        images = torch.empty(npix, dtype=torch.float32, device=dev)
+        opts = h3dgs.default_opts()
+        carr = h3dgs.camera_array(cams)
+        # first frame in the growing mode, to size the fixed workspace
+        m = h3dgs.h3dgs_select_cut(ctx.ctx, cams, ids, tt, offs, cap)
+        h3dgs.h3dgs_render(ctx.ctx, cams, ids, tt, offs, opts, images, 0)
+        st = h3dgs.h3dgs_get_stats(ctx.ctx)
+        h3dgs.h3dgs_reserve(ctx.ctx, int(m * 1.25) + 1024, int(st["n_pairs"] * 1.25) + 4096)
+
+        def frame():
+            h3dgs.h3dgs_select_cut(ctx.ctx, cams, ids, tt, offs, cap, want_total=False)
+            h3dgs.h3dgs_render(ctx.ctx, cams, ids, tt, offs, opts, images, 0, cam_array=carr)
+
+        frame()
+        ref_img = images.clone()
+        graph = None
+        if not args.no_graph:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                frame()
+            graph.replay()
+            stream.synchronize()
+            assert torch.equal(images, ref_img), "graph replay differs from the direct frame"
+        run = graph.replay if graph is not None else frame
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            run()
+            flush.fill_(1.0)
+        stream.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with ClockSampler(local) as clk:
+            for e0, e1 in evs:
+                e0.record(stream)
+                run()
+                e1.record(stream)
+                flush.fill_(1.0)
+            torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        total_ms = float(np.sum(step_ms))
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+            torch.distributed.barrier()
+        st = h3dgs.h3dgs_get_stats(ctx.ctx)
+        assert st["device_flags"] == 0, f"capacity flags {st['device_flags']}"
+        value = world * args.steps / (total_ms / 1e3)
+
+        # ---- per-stage times (events inside the library, same ABI calls, not graphed)
+        h3dgs.h3dgs_set_profiling(ctx.ctx, 1)
+        stage_acc = {}
+        n_prof = max(3, min(args.steps, 20))
+        for _ in range(n_prof):
+            frame()
+            times = h3dgs.h3dgs_get_stage_times(ctx.ctx)
+            for k, v in times.items():
+                stage_acc[k] = stage_acc.get(k, 0.0) + v
+            flush.fill_(1.0)
+        fwd_stages = {k: v / n_prof for k, v in stage_acc.items() if v > 0}
+        st = h3dgs.h3dgs_get_stats(ctx.ctx)
+
+        # ---- fwd + bwd views/s
+        grads = {k: torch.zeros_like(getattr(hier, k)) for k in ("mean", "scale", "rot", "opacity", "sh")}
+        dl = torch.randn(npix, generator=torch.Generator(device=dev).manual_seed(0), device=dev)
+
+        def fwd_bwd():
+            h3dgs.h3dgs_select_cut(ctx.ctx, cams, ids, tt, offs, cap, want_total=False)
+            h3dgs.h3dgs_render(ctx.ctx, cams, ids, tt, offs, opts, images, 1, cam_array=carr)
+            h3dgs.h3dgs_render_backward(ctx.ctx, dl, grads, 1)
+
+        stage_acc = {}
+        for _ in range(3):
+            fwd_bwd()
+            flush.fill_(1.0)
+        for _ in range(n_prof):
+            fwd_bwd()
+            times = h3dgs.h3dgs_get_stage_times(ctx.ctx)
+            for k, v in times.items():
+                stage_acc[k] = stage_acc.get(k, 0.0) + v
+            flush.fill_(1.0)
+        bwd_stages = {k: v / n_prof for k, v in stage_acc.items() if k.startswith("backward")}
+        h3dgs.h3dgs_set_profiling(ctx.ctx, 0)
+        fb_graph = None
+        if not args.no_graph:
+            fb_graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(fb_graph, stream=stream):
+                fwd_bwd()
+        fb_run = fb_graph.replay if fb_graph is not None else fwd_bwd
+        for _ in range(args.warmup):
+            fb_run()
+            flush.fill_(1.0)
+        torch.cuda.synchronize()
+        fb_ms = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(args.steps):
+            e0.record(stream)
+            fb_run()
+            e1.record(stream)
+            flush.fill_(1.0)
+            e1.synchronize()
+            fb_ms += e0.elapsed_time(e1)
+        fb_value = world * args.steps / (fb_ms / 1e3)
+
+        # ---- end to end through the public API: image read back to pinned host memory every step
+        host_img = torch.empty(npix, dtype=torch.float32, pin_memory=True)
+        for _ in range(args.warmup):
+            frame()
+            host_img.copy_(images, non_blocking=True)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            frame()
+            host_img.copy_(images, non_blocking=True)
+        stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e_value = world * args.steps / e2e_s
+
+    # ---- roofline of the dominant kernel (the blend: FP32/MUFU issue-bound)
+    peaks = measured_peaks()
+    blend_ms = fwd_stages.get("blend", 0.0)
+    n_evals = int(st["n_evals"])
+    flops = n_evals * FLOPS_PER_EVAL
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    fp32_peak_tflops = 148 * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (blend_ms * 1e-3) / 1e12 if blend_ms > 0 else None
+    roofline = {"kernel": "blend_kernel<16,16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": (achieved / fp32_peak_tflops) if achieved else None,
+                "traffic": None,
+                "peak_note": "148 SMs x 128 FP32 lanes x 2 (FFMA) x max SM clock from MEASURED_PEAKS.json",
+                "work_note": f"{FLOPS_PER_EVAL} FP32 flops per evaluated (pixel, splat) pair x {n_evals} pairs"}
+    hbm = float(peaks.get("hbm_gbs", 6442.9))
+    stage_bw = {}
+    M, V, Pn = int(st["n_cut"]), int(st["n_visible"]), int(st["n_pairs"])
+    algo_bytes = {"cut": N * 32 + N * 32 // 2 + M * 8,
+                  "preprocess": M * (236 + 16) + M * 64,
+                  "depth_sort": 4 * M * 20,
+                  "tile_sort": 2 * Pn * 20}
+    for k, b in algo_bytes.items():
+        if fwd_stages.get(k):
+            stage_bw[k] = {"GB/s": b / (fwd_stages[k] * 1e-3) / 1e9, "frac_hbm": b / (fwd_stages[k] * 1e-3) / 1e9 / hbm}
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"street corridor, {args.n_leaves} leaves ({N} nodes), 1920x1080, tau={args.tau:g} px",
+                   "n_leaves": args.n_leaves, "n_nodes": N, "width": cam.width, "height": cam.height, "tau": args.tau,
+                   "cut_size": M, "visible_splats": V, "pairs": Pn, "evals": n_evals,
+                   "l2": "flushed between timed steps (256 MB write, outside the events)",
+                   "cuda_graph": graph is not None, "parallelism": f"{world} independent replicas"},
+        "fwd_bwd": {"value": fb_value, "unit": "views/s", "ms_per_view": fb_ms / args.steps},
+        "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": 76 * len(cams),
+                "d2h_bytes_per_step": npix * 4,
+                "note": "C-ABI calls from Python; camera struct in, image read back to pinned host memory"},
+        "stages_ms": {**fwd_stages, **bwd_stages}, "stage_bandwidth": stage_bw,
+        "roofline": roofline,
+        "gpu_launches": args.steps * launches_per_frame(int(st["n_tiles"])),
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_time(scene, 4)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return out if rank == 0 else None
+
+
+# ----------------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2406_12080_b300 import synth
+    import oracle
+    scene = synth.corridor_scene(n_leaves=args.n_leaves, tau=args.tau)
+    h = oracle.build_tree(scene.leaves)
+    cam = scene.cameras[0]
+    for _ in range(args.warmup):
+        oracle.render(cam, h, oracle.Opts())
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.render(cam, h, oracle.Opts())
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    cores = oracle.num_threads()
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"street corridor, {args.n_leaves} leaves, 1920x1080, tau={args.tau:g} px"},
+            "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": "full frames (cut + render) of the benchmark workload"},
+            "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

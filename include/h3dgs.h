@@ -107,8 +107,25 @@ typedef struct {
     int64_t n_pairs;      /* (tile, splat) pairs after binning                   */
     int64_t n_tiles;      /* tiles over all cameras                              */
     int64_t n_pixels;     /* pixels over all cameras                             */
-    uint32_t device_flags; /* bit 0: pair capacity exceeded (fixed-capacity mode)  */
+    uint32_t device_flags; /* bit 0: pair capacity exceeded, bit 1: splat capacity
+                              exceeded, bit 2: cut truncated to capacity           */
+    int64_t n_evals;      /* (pixel, splat) evaluations performed by the blend   */
 } h3dgs_stats;
+
+/* Per-stage device times of the most recent select_cut / render / render_backward, in ms,
+ * measured with CUDA events on the context's stream while profiling is enabled. */
+typedef enum {
+    H3DGS_STAGE_CUT = 0,        /* a1 + a2: mark, scans, ordered compaction          */
+    H3DGS_STAGE_PREPROCESS,     /* a3 + a4: interpolate, project, SH                 */
+    H3DGS_STAGE_DEPTH_SORT,     /* a5: depth radix sort of the splats                */
+    H3DGS_STAGE_DUPLICATE,      /* a5: pair-offset scan and (tile, splat) emission   */
+    H3DGS_STAGE_TILE_SORT,      /* a5: stable radix sort of the pairs by tile        */
+    H3DGS_STAGE_RANGES,         /* a6: tile ranges                                   */
+    H3DGS_STAGE_BLEND,          /* a7: per-tile blend                                */
+    H3DGS_STAGE_BACKWARD_BLEND, /* a8: reverse per-tile blend                        */
+    H3DGS_STAGE_BACKWARD_SPLAT, /* a8: projection/interpolation adjoint and scatter  */
+    H3DGS_STAGE_COUNT
+} h3dgs_stage;
 
 /* ------------------------------------------------------------------------------ lifecycle */
 
@@ -228,6 +245,14 @@ h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL_dimages, cons
 
 /* Counters of the last render (synchronises the stream). */
 h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out);
+
+/* Enable (1) or disable (0) per-stage event timing.  While enabled every stage is bracketed by
+ * CUDA events on the context's stream (do not capture such calls in a CUDA graph). */
+h3dgs_status h3dgs_set_profiling(h3dgs_ctx* ctx, int32_t enable);
+
+/* Stage times (ms) of the last profiled calls, indexed by h3dgs_stage; ms must hold
+ * H3DGS_STAGE_COUNT floats (host).  Synchronises the stream.  Stages not run report 0. */
+h3dgs_status h3dgs_get_stage_times(h3dgs_ctx* ctx, float* ms);
 
 /* Copy the last render's per-tile lists of camera `cam` to HOST memory (synchronous):
  * ranges [tiles_x * tiles_y][2] = [start, end) into ids; ids = the NODE id of each list entry.

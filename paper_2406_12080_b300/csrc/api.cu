@@ -37,7 +37,8 @@ template <typename T>
 T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
 
 // device counter block
-enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_COUNT = 8 };
+// C_EVALS occupies two words (a 64-bit counter)
+enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_EVALS = 6, C_COUNT = 8 };
 
 }  // namespace
 
@@ -67,6 +68,10 @@ struct h3dgs_ctx {
     const float* cut_t = nullptr;
     const int64_t* cut_offsets = nullptr;
     bool depth_in_2 = false, pairs_in_1 = false;
+    // profiling
+    bool prof = false;
+    cudaEvent_t ev[2 * H3DGS_STAGE_COUNT] = {};
+    bool ev_used[H3DGS_STAGE_COUNT] = {};
 };
 
 namespace {
@@ -79,6 +84,17 @@ h3dgs_status fail(h3dgs_ctx* c, h3dgs_status s, const std::string& msg) {
 h3dgs_status cuda_fail(h3dgs_ctx* c, cudaError_t e, const char* where) {
     return fail(c, e == cudaErrorMemoryAllocation ? H3DGS_ERR_OOM : H3DGS_ERR_CUDA,
                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// stage brackets (only while profiling)
+void stage_begin(h3dgs_ctx* ctx, int st) {
+    if (ctx->prof) cudaEventRecord(ctx->ev[2 * st], ctx->stream);
+}
+void stage_end(h3dgs_ctx* ctx, int st) {
+    if (ctx->prof) {
+        cudaEventRecord(ctx->ev[2 * st + 1], ctx->stream);
+        ctx->ev_used[st] = true;
+    }
 }
 
 #define CK(expr, where)                                        \
@@ -224,6 +240,8 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
                     &ctx->hist, &ctx->dtot, &ctx->partial, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad};
     for (DBuf* b : bufs)
         if (b->p) cudaFree(b->p);
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
     delete ctx;
     return H3DGS_OK;
 }
@@ -330,9 +348,11 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
     w.mask = P<uint32_t>(ctx->cut_mask);
     w.block_counts = P<uint32_t>(ctx->cut_bc);
     w.cam_totals = P<int64_t>(ctx->cut_tot);
+    stage_begin(ctx, H3DGS_STAGE_CUT);
     CK(launch_cut(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, w, cut_ids, cut_t, cut_offsets, capacity,
                   P<uint32_t>(ctx->counters) + C_FLAGS, ctx->stream),
        "cut kernels");
+    stage_end(ctx, H3DGS_STAGE_CUT);
     if (total_out) {
         int64_t tot = 0;
         CK(cudaMemcpyAsync(&tot, P<int64_t>(ctx->cut_tot) + n_cams, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream),
@@ -403,6 +423,7 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
     CK(ensure(ctx->T_final, sizeof(float) * (size_t)ctx->n_pixels), "pixel state");
     CK(ensure(ctx->n_contrib, sizeof(int32_t) * (size_t)ctx->n_pixels), "pixel state");
     CK(cudaMemsetAsync(cnt + C_NVISIBLE, 0, sizeof(uint32_t), s), "memset");
+    CK(cudaMemsetAsync(cnt + C_EVALS, 0, 2 * sizeof(uint32_t), s), "memset");
     CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(int2) * (size_t)ctx->n_tiles, s), "memset");
     const DevOpts o = dev_opts(*opts);
     SplatBufs sb;
@@ -413,17 +434,22 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
     sb.n_splats = cnt + C_NSPLATS;
     sb.n_visible = cnt + C_NVISIBLE;
     const int grid = ctx->num_sms * 8;
+    stage_begin(ctx, H3DGS_STAGE_PREPROCESS);
     CK(launch_preprocess(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, o, cut_ids, cut_t, cut_offsets, capM, sb,
                          cnt + C_FLAGS, grid, s),
        "preprocess");
+    stage_end(ctx, H3DGS_STAGE_PREPROCESS);
     // depth order of the splats: values start as the identity
+    stage_begin(ctx, H3DGS_STAGE_DEPTH_SORT);
     CK(launch_iota(P<uint32_t>(ctx->s_idx), cnt + C_NSPLATS, grid, s), "iota");
     SortWork sw = sort_work(ctx);
     bool in2 = false;
     CK(radix_sort_pairs(P<uint32_t>(ctx->s_key), P<uint32_t>(ctx->s_idx), P<uint32_t>(ctx->s_key2),
                         P<uint32_t>(ctx->s_idx2), cnt + C_NSPLATS, 32, sw, &in2, s),
        "depth sort");
+    stage_end(ctx, H3DGS_STAGE_DEPTH_SORT);
     const uint32_t* order = in2 ? P<uint32_t>(ctx->s_idx2) : P<uint32_t>(ctx->s_idx);
+    stage_begin(ctx, H3DGS_STAGE_DUPLICATE);
     CK(scan_gathered(P<uint32_t>(ctx->s_tiles), order, P<uint32_t>(ctx->s_poff), cnt + C_NSPLATS, cnt + C_NPAIRS, sw, s),
        "pair scan");
     if (!ctx->fixed) {
@@ -437,16 +463,24 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
     CK(launch_duplicate(P<DevCam>(ctx->cams), n_cams, cut_offsets, sb, order, P<uint32_t>(ctx->s_poff), cnt + C_NPAIRS,
                         capP, cnt + C_NPAIRS_KEPT, P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), cnt + C_FLAGS, grid, s),
        "duplicate");
+    stage_end(ctx, H3DGS_STAGE_DUPLICATE);
     bool in1 = false;
+    stage_begin(ctx, H3DGS_STAGE_TILE_SORT);
     CK(radix_sort_pairs(P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), P<uint32_t>(ctx->pk1), P<uint32_t>(ctx->pv1),
                         cnt + C_NPAIRS_KEPT, bits_for(ctx->n_tiles), sw, &in1, s),
        "tile sort");
+    stage_end(ctx, H3DGS_STAGE_TILE_SORT);
     const uint32_t* keys = in1 ? P<uint32_t>(ctx->pk1) : P<uint32_t>(ctx->pk0);
     const uint32_t* list = in1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
+    stage_begin(ctx, H3DGS_STAGE_RANGES);
     CK(launch_ranges(keys, cnt + C_NPAIRS_KEPT, P<int2>(ctx->ranges), grid, s), "ranges");
+    stage_end(ctx, H3DGS_STAGE_RANGES);
+    stage_begin(ctx, H3DGS_STAGE_BLEND);
     CK(launch_blend(P<DevCam>(ctx->cams), n_cams, ctx->n_tiles, o, P<int2>(ctx->ranges), list, sb.rec, images,
-                    P<float>(ctx->T_final), P<int32_t>(ctx->n_contrib), s),
+                    P<float>(ctx->T_final), P<int32_t>(ctx->n_contrib),
+                    reinterpret_cast<unsigned long long*>(cnt + C_EVALS), s),
        "blend");
+    stage_end(ctx, H3DGS_STAGE_BLEND);
     ctx->rendered = true;
     ctx->saved = save_for_backward != 0;
     ctx->opts = o;
@@ -472,12 +506,14 @@ h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL, const h3dgs_
     CK(cudaMemsetAsync(ctx->splat_grad.p, 0, sizeof(float) * 12 * (size_t)ctx->splat_cap_used, ctx->stream), "memset");
     GradBufs gb{g->mean, g->scale, g->rot, g->opacity, g->sh};
     const uint32_t* list = ctx->pairs_in_1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
+    cudaEvent_t* ev = ctx->prof ? ctx->ev + 2 * H3DGS_STAGE_BACKWARD_BLEND : nullptr;
     CK(launch_backward(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, ctx->n_tiles, ctx->opts, ctx->cut_ids, ctx->cut_t,
                        ctx->cut_offsets, P<int2>(ctx->ranges), list, P<float4>(ctx->s_rec), P<uint2>(ctx->s_rect),
                        P<uint32_t>(ctx->counters) + C_NSPLATS, ctx->splat_cap_used, P<float>(ctx->T_final),
                        P<int32_t>(ctx->n_contrib), dL, P<float>(ctx->splat_grad), gb, freeze_leaves,
-                       ctx->num_sms * 8, ctx->stream),
+                       ctx->num_sms * 8, ev, ctx->stream),
        "backward");
+    if (ctx->prof) ctx->ev_used[H3DGS_STAGE_BACKWARD_BLEND] = ctx->ev_used[H3DGS_STAGE_BACKWARD_SPLAT] = true;
     return H3DGS_OK;
 }
 
@@ -494,6 +530,32 @@ h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out) {
     out->n_tiles = ctx->n_tiles;
     out->n_pixels = ctx->n_pixels;
     out->device_flags = c[C_FLAGS];
+    uint64_t ev;
+    std::memcpy(&ev, c + C_EVALS, sizeof(ev));
+    out->n_evals = (int64_t)ev;
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_set_profiling(h3dgs_ctx* ctx, int32_t enable) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device), "set device");
+    if (enable && !ctx->ev[0])
+        for (auto& e : ctx->ev) CK(cudaEventCreate(&e), "event create");
+    ctx->prof = enable != 0;
+    for (bool& u : ctx->ev_used) u = false;
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_get_stage_times(h3dgs_ctx* ctx, float* ms) {
+    if (!ctx || !ms) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device), "set device");
+    CK(cudaStreamSynchronize(ctx->stream), "profile sync");
+    for (int i = 0; i < H3DGS_STAGE_COUNT; ++i) {
+        ms[i] = 0.0f;
+        if (ctx->ev_used[i]) CK(cudaEventElapsedTime(&ms[i], ctx->ev[2 * i], ctx->ev[2 * i + 1]), "event time");
+    }
     return H3DGS_OK;
 }
 

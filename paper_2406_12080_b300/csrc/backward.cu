@@ -380,8 +380,10 @@ cudaError_t launch_backward(const DevHier& h, const DevCam* cams, int n_cams, in
                             const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets, const int2* ranges,
                             const uint32_t* list, const float4* splat, const uint2* rect, const uint32_t* n_splats,
                             int64_t cap, const float* T_final, const int32_t* n_contrib, const float* dL,
-                            float* splat_grad, const GradBufs& g, int freeze_leaves, int grid, cudaStream_t s) {
+                            float* splat_grad, const GradBufs& g, int freeze_leaves, int grid, cudaEvent_t* ev,
+                            cudaStream_t s) {
     (void)cap;
+    if (ev) cudaEventRecord(ev[0], s);
     if (n_tiles > 0) {
         const unsigned tg = (unsigned)n_tiles;
 #define BW(TWV, THV)                                                                                          \
@@ -398,8 +400,13 @@ cudaError_t launch_backward(const DevHier& h, const DevCam* cams, int n_cams, in
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (ev) {
+        cudaEventRecord(ev[1], s);
+        cudaEventRecord(ev[2], s);
+    }
     backward_splat_kernel<<<grid, 128, 0, s>>>(h, cams, n_cams, o, cut_ids, cut_t, cut_offsets, rect, n_splats, splat_grad,
                                                g, freeze_leaves);
+    if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
 

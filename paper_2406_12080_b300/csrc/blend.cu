@@ -35,10 +35,13 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH) blend_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
                                                         const int2* __restrict__ ranges, const uint32_t* __restrict__ list,
                                                         const float4* __restrict__ splat, float* __restrict__ images,
-                                                        float* __restrict__ T_final, int32_t* __restrict__ n_contrib) {
+                                                        float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
+                                                        unsigned long long* __restrict__ n_evals) {
     constexpr int NT = TW * TH;
     __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
+    __shared__ unsigned int s_evals;
     const int64_t tile = blockIdx.x;
+    if (threadIdx.x == 0) s_evals = 0;
     // camera of this tile
     int lo = 0, hi = n_cams - 1;
     while (lo < hi) {
@@ -55,6 +58,7 @@ __global__ void __launch_bounds__(TW * TH) blend_kernel(const DevCam* __restrict
     const float clampv = o.alpha_clamp, afloor = o.alpha_floor, tmin = o.t_min;
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     int last = 0;
+    unsigned int evals = 0;
     bool done = !inside;
     for (int b0 = r.x; b0 < r.y; b0 += NT) {
         if (__syncthreads_count(done) == NT) break;
@@ -68,6 +72,7 @@ __global__ void __launch_bounds__(TW * TH) blend_kernel(const DevCam* __restrict
         __syncthreads();
         if (!done) {
             for (int j = 0; j < n; ++j) {
+                ++evals;
                 const float4 a = s_a[j], b = s_b[j];
                 const float dx = fsub(px, a.x), dy = fsub(py, a.y);
                 const float h = ffma(a.z, dx, fmul(a.w, dy));
@@ -94,6 +99,10 @@ __global__ void __launch_bounds__(TW * TH) blend_kernel(const DevCam* __restrict
             }
         }
     }
+    for (int off = 16; off > 0; off >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_evals, evals);
+    __syncthreads();
+    if (threadIdx.x == 0 && n_evals) atomicAdd(n_evals, (unsigned long long)s_evals);
     if (inside) {
         const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
         const int64_t plane = (int64_t)cam.width * cam.height;
@@ -108,21 +117,21 @@ __global__ void __launch_bounds__(TW * TH) blend_kernel(const DevCam* __restrict
 
 cudaError_t launch_blend(const DevCam* cams, int n_cams, int64_t n_tiles, const DevOpts& o, const int2* ranges,
                          const uint32_t* list, const float4* splat, float* images, float* T_final, int32_t* n_contrib,
-                         cudaStream_t s) {
+                         unsigned long long* n_evals, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)n_tiles;
     if (o.tile_w == 16 && o.tile_h == 16)
-        blend_kernel<16, 16><<<grid, 256, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib);
+        blend_kernel<16, 16><<<grid, 256, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
     else if (o.tile_w == 8 && o.tile_h == 8)
-        blend_kernel<8, 8><<<grid, 64, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib);
+        blend_kernel<8, 8><<<grid, 64, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
     else if (o.tile_w == 32 && o.tile_h == 8)
-        blend_kernel<32, 8><<<grid, 256, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib);
+        blend_kernel<32, 8><<<grid, 256, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
     else if (o.tile_w == 8 && o.tile_h == 32)
-        blend_kernel<8, 32><<<grid, 256, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib);
+        blend_kernel<8, 32><<<grid, 256, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
     else if (o.tile_w == 16 && o.tile_h == 8)
-        blend_kernel<16, 8><<<grid, 128, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib);
+        blend_kernel<16, 8><<<grid, 128, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
     else if (o.tile_w == 32 && o.tile_h == 4)
-        blend_kernel<32, 4><<<grid, 128, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib);
+        blend_kernel<32, 4><<<grid, 128, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -161,7 +161,7 @@ cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_pairs_kept, in
 // blend.cu
 cudaError_t launch_blend(const DevCam* cams, int n_cams, int64_t n_tiles, const DevOpts& o, const int2* ranges,
                          const uint32_t* list, const float4* splat, float* images, float* T_final,
-                         int32_t* n_contrib, cudaStream_t s);
+                         int32_t* n_contrib, unsigned long long* n_evals, cudaStream_t s);
 
 // builder.cu
 struct BuildOut {
@@ -181,6 +181,6 @@ cudaError_t launch_backward(const DevHier& h, const DevCam* cams, int n_cams, in
                             const int2* ranges, const uint32_t* list, const float4* splat, const uint2* rect,
                             const uint32_t* n_splats, int64_t cap, const float* T_final, const int32_t* n_contrib,
                             const float* dL, float* splat_grad, const GradBufs& g, int freeze_leaves, int grid,
-                            cudaStream_t s);
+                            cudaEvent_t* ev /* 4 events or NULL */, cudaStream_t s);
 
 }  // namespace h3dgs

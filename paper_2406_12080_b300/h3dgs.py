@@ -58,7 +58,12 @@ class h3dgs_render_opts(C.Structure):
 
 class h3dgs_stats(C.Structure):
     _fields_ = [("n_cut", C.c_int64), ("n_visible", C.c_int64), ("n_pairs", C.c_int64),
-                ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("device_flags", C.c_uint32)]
+                ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("device_flags", C.c_uint32),
+                ("n_evals", C.c_int64)]
+
+
+STAGES = ["cut", "preprocess", "depth_sort", "duplicate", "tile_sort", "ranges", "blend", "backward_blend",
+          "backward_splat"]
 
 
 _lib = None
@@ -85,6 +90,8 @@ def lib():
             "h3dgs_render": (i32, [vp, C.POINTER(h3dgs_camera), i32, vp, vp, vp, C.POINTER(h3dgs_render_opts), vp, i32]),
             "h3dgs_render_backward": (i32, [vp, vp, C.POINTER(h3dgs_grads), i32]),
             "h3dgs_get_stats": (i32, [vp, C.POINTER(h3dgs_stats)]),
+            "h3dgs_set_profiling": (i32, [vp, i32]),
+            "h3dgs_get_stage_times": (i32, [vp, vp]),
             "h3dgs_debug_tile_lists": (i32, [vp, i32, vp, vp, i64, C.POINTER(i64)]),
             "h3dgs_debug_splats": (i32, [vp, vp, vp, vp, i64]),
             "h3dgs_debug_pixel_state": (i32, [vp, vp, vp, i64]),
@@ -214,6 +221,16 @@ def h3dgs_get_stats(ctx) -> dict:
     s = h3dgs_stats()
     _check(ctx, lib().h3dgs_get_stats(ctx, C.byref(s)))
     return {k: getattr(s, k) for k, _ in h3dgs_stats._fields_}
+
+
+def h3dgs_set_profiling(ctx, enable: int):
+    _check(ctx, lib().h3dgs_set_profiling(ctx, enable))
+
+
+def h3dgs_get_stage_times(ctx) -> dict:
+    ms = np.zeros(len(STAGES), np.float32)
+    _check(ctx, lib().h3dgs_get_stage_times(ctx, ms.ctypes.data))
+    return dict(zip(STAGES, ms.tolist()))
 
 
 def h3dgs_debug_tile_lists(ctx, cam: int, n_tiles: int):
