@@ -46,7 +46,7 @@ FLOPS_PER_EVAL_T = 10
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-leaves", type=int, default=1_000_000)
@@ -78,22 +78,23 @@ class ClockSampler:
     def __enter__(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            if os.path.exists(self.path):
+                os.remove(self.path)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *a):
         if self.proc is not None:
-            self.proc.terminate()
+            self.proc.send_signal(2)
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-            self.f.close()
 
     def summary(self):
         try:
@@ -205,15 +206,15 @@ def run_ours(args, rank, world, local):
             assert torch.equal(images, ref_img), "graph replay differs from the direct frame"
         run = graph.replay if graph is not None else frame
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        for _ in range(args.warmup):
-            run()
-            flush.fill_(1.0)
-        stream.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         with ClockSampler(local) as clk:
+            for _ in range(args.warmup):
+                run()
+                flush.fill_(1.0)
+            stream.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
             for e0, e1 in evs:
                 e0.record(stream)
                 run()
@@ -334,6 +335,8 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "cuda_graph": graph is not None, "parallelism": f"{world} independent replicas"},
         "fwd_bwd": {"value": fb_value, "unit": "views/s", "ms_per_view": fb_ms / args.steps},
+        "blend": {"items": int(st["n_items"]), "tile_chunk": int(opts.blend_chunk), "evals_main": n_evals,
+                  "evals_tpass": int(st["n_evals_tpass"])},
         "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": 76 * len(cams),
                 "d2h_bytes_per_step": npix * 4,
                 "note": "C-ABI calls from Python; camera struct in, image read back to pinned host memory"},

@@ -98,6 +98,9 @@ typedef struct {
     int32_t aa_compensate;   /* 1: opacities scaled by sqrt(det S' / det(S' + lowpass I))     */
     int32_t interpolate;     /* 1: parent/child interpolation (Sec. 4.2); 0: render the cut as is */
     float bg[3];             /* background colour                                              */
+    int32_t blend_chunk;     /* tile lists longer than this many entries are blended in chunks of
+                                this size by separate CTAs (64 .. 65536, default 512); the image
+                                does not depend on it beyond fp32 reassociation of T            */
 } h3dgs_render_opts;
 
 /* Counters of the most recent h3dgs_render (read with a stream synchronisation). */
@@ -109,7 +112,9 @@ typedef struct {
     int64_t n_pixels;     /* pixels over all cameras                             */
     uint32_t device_flags; /* bit 0: pair capacity exceeded, bit 1: splat capacity
                               exceeded, bit 2: cut truncated to capacity           */
-    int64_t n_evals;      /* (pixel, splat) evaluations performed by the blend   */
+    int64_t n_evals;      /* (pixel, splat) evaluations of the blend's main pass */
+    int64_t n_evals_tpass; /* extra evaluations of the transmittance pass of split tiles */
+    int64_t n_items;      /* blend work items (tiles, split tiles count once per chunk) */
 } h3dgs_stats;
 
 /* Per-stage device times of the most recent select_cut / render / render_backward, in ms,

@@ -37,8 +37,9 @@ template <typename T>
 T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
 
 // device counter block
-// C_EVALS occupies two words (a 64-bit counter)
-enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_EVALS = 6, C_COUNT = 8 };
+// C_EVALS and C_EVALS_T occupy two words each (64-bit counters)
+enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NITEMS = 5, C_EVALS = 8,
+       C_EVALS_T = 10, C_COUNT = 12 };
 
 }  // namespace
 
@@ -52,9 +53,11 @@ struct h3dgs_ctx {
     DBuf rec, cams, counters;
     DBuf cut_mask, cut_bc, cut_tot;
     DBuf s_rec, s_rect, s_key, s_idx, s_key2, s_idx2, s_tiles, s_poff;
-    DBuf pk0, pv0, pk1, pv1, ranges;
+    DBuf pk0, pv0, pk1, pv1, ranges, sort_scratch;
     DBuf hist, dtot, partial;
     DBuf T_final, n_contrib, splat_grad;
+    DBuf items, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last;
+    int64_t item_cap = 0;
     bool fixed = false;
     int64_t cap_splats = 0, cap_pairs = 0;
     // state of the last render
@@ -172,6 +175,7 @@ DevOpts dev_opts(const h3dgs_render_opts& o) {
     d.tile_w = o.tile_w; d.tile_h = o.tile_h; d.lowpass = o.lowpass; d.alpha_clamp = o.alpha_clamp;
     d.alpha_floor = o.alpha_floor; d.t_min = o.t_min; d.aa_compensate = o.aa_compensate;
     d.interpolate = o.interpolate;
+    d.chunk = o.blend_chunk > 0 ? o.blend_chunk : 512;
     for (int i = 0; i < 3; ++i) d.bg[i] = o.bg[i];
     return d;
 }
@@ -186,6 +190,37 @@ int bits_for(int64_t n) {
     while (b < 32 && ((int64_t)1 << b) < n) ++b;
     return std::max(b, 1);
 }
+
+}  // namespace
+
+// (outside the anonymous namespace: needs the full context type)
+static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images) {
+    BlendArgs a;
+    a.cams = P<DevCam>(ctx->cams);
+    a.n_cams = n_cams;
+    a.n_tiles = ctx->n_tiles;
+    a.o = ctx->opts;
+    a.ranges = P<int2>(ctx->ranges);
+    a.list = ctx->pairs_in_1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
+    a.splat = P<float4>(ctx->s_rec);
+    a.chunk = ctx->opts.chunk;
+    a.item_cap = ctx->item_cap;
+    a.items = P<int2>(ctx->items);
+    a.tile_item0 = P<int32_t>(ctx->tile_item0);
+    a.tile_nch = P<int32_t>(ctx->tile_nch);
+    a.n_items = P<uint32_t>(ctx->counters) + C_NITEMS;
+    a.scratch_Tc = P<float>(ctx->sc_Tc);
+    a.scratch_C = P<float>(ctx->sc_C);
+    a.scratch_Tend = P<float>(ctx->sc_Tend);
+    a.scratch_last = P<int32_t>(ctx->sc_last);
+    a.images = images;
+    a.T_final = P<float>(ctx->T_final);
+    a.n_contrib = P<int32_t>(ctx->n_contrib);
+    a.n_evals = reinterpret_cast<unsigned long long*>(P<uint32_t>(ctx->counters) + C_EVALS);
+    return a;
+}
+
+namespace {
 
 SortWork sort_work(h3dgs_ctx* ctx) {
     SortWork w;
@@ -236,8 +271,10 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     DBuf* bufs[] = {&ctx->rec, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot,
                     &ctx->s_rec, &ctx->s_rect, &ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2,
-                    &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1, &ctx->ranges,
-                    &ctx->hist, &ctx->dtot, &ctx->partial, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad};
+                    &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1, &ctx->ranges, &ctx->sort_scratch,
+                    &ctx->hist, &ctx->dtot, &ctx->partial, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
+                    &ctx->items, &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
+                    &ctx->sc_last};
     for (DBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& e : ctx->ev)
@@ -259,6 +296,7 @@ void h3dgs_default_opts(h3dgs_render_opts* o) {
     o->aa_compensate = 1;
     o->interpolate = 1;
     o->bg[0] = o->bg[1] = o->bg[2] = 0.0f;
+    o->blend_chunk = 512;
 }
 
 h3dgs_status h3dgs_reserve(h3dgs_ctx* ctx, int64_t max_splats, int64_t max_pairs) {
@@ -395,6 +433,8 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
         return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: unsupported tile shape");
     if (!(opts->alpha_clamp > 0 && opts->alpha_clamp < 1) || !(opts->lowpass >= 0) || !(opts->t_min >= 0))
         return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: bad opts");
+    if (opts->blend_chunk != 0 && (opts->blend_chunk < 64 || opts->blend_chunk > 65536))
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: blend_chunk out of range");
     CK(cudaSetDevice(ctx->device), "set device");
     st = setup_cameras(ctx, cams, n_cams, opts->tile_w, opts->tile_h);
     if (st != H3DGS_OK) return st;
@@ -423,7 +463,7 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
     CK(ensure(ctx->T_final, sizeof(float) * (size_t)ctx->n_pixels), "pixel state");
     CK(ensure(ctx->n_contrib, sizeof(int32_t) * (size_t)ctx->n_pixels), "pixel state");
     CK(cudaMemsetAsync(cnt + C_NVISIBLE, 0, sizeof(uint32_t), s), "memset");
-    CK(cudaMemsetAsync(cnt + C_EVALS, 0, 2 * sizeof(uint32_t), s), "memset");
+    CK(cudaMemsetAsync(cnt + C_EVALS, 0, 4 * sizeof(uint32_t), s), "memset");
     CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(int2) * (size_t)ctx->n_tiles, s), "memset");
     const DevOpts o = dev_opts(*opts);
     SplatBufs sb;
@@ -439,18 +479,10 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
                          cnt + C_FLAGS, grid, s),
        "preprocess");
     stage_end(ctx, H3DGS_STAGE_PREPROCESS);
-    // depth order of the splats: values start as the identity
-    stage_begin(ctx, H3DGS_STAGE_DEPTH_SORT);
-    CK(launch_iota(P<uint32_t>(ctx->s_idx), cnt + C_NSPLATS, grid, s), "iota");
+    // pairs in cut order, stable sort by tile, ranges, then every tile's list by depth in shared memory
     SortWork sw = sort_work(ctx);
-    bool in2 = false;
-    CK(radix_sort_pairs(P<uint32_t>(ctx->s_key), P<uint32_t>(ctx->s_idx), P<uint32_t>(ctx->s_key2),
-                        P<uint32_t>(ctx->s_idx2), cnt + C_NSPLATS, 32, sw, &in2, s),
-       "depth sort");
-    stage_end(ctx, H3DGS_STAGE_DEPTH_SORT);
-    const uint32_t* order = in2 ? P<uint32_t>(ctx->s_idx2) : P<uint32_t>(ctx->s_idx);
     stage_begin(ctx, H3DGS_STAGE_DUPLICATE);
-    CK(scan_gathered(P<uint32_t>(ctx->s_tiles), order, P<uint32_t>(ctx->s_poff), cnt + C_NSPLATS, cnt + C_NPAIRS, sw, s),
+    CK(scan_plain(P<uint32_t>(ctx->s_tiles), P<uint32_t>(ctx->s_poff), cnt + C_NSPLATS, cnt + C_NPAIRS, sw, s),
        "pair scan");
     if (!ctx->fixed) {
         uint32_t pn = 0;
@@ -460,8 +492,10 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
         DBuf* p4[] = {&ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1};
         for (DBuf* b : p4) CK(ensure(*b, 4 * (size_t)capP), "pair buffer");
     }
-    CK(launch_duplicate(P<DevCam>(ctx->cams), n_cams, cut_offsets, sb, order, P<uint32_t>(ctx->s_poff), cnt + C_NPAIRS,
-                        capP, cnt + C_NPAIRS_KEPT, P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), cnt + C_FLAGS, grid, s),
+    CK(ensure(ctx->sort_scratch, 16 * (size_t)capP), "sort scratch");
+    CK(launch_duplicate_plain(P<DevCam>(ctx->cams), n_cams, cut_offsets, sb, P<uint32_t>(ctx->s_poff), cnt + C_NPAIRS,
+                              capP, cnt + C_NPAIRS_KEPT, P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), cnt + C_FLAGS,
+                              grid, s),
        "duplicate");
     stage_end(ctx, H3DGS_STAGE_DUPLICATE);
     bool in1 = false;
@@ -471,23 +505,38 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
        "tile sort");
     stage_end(ctx, H3DGS_STAGE_TILE_SORT);
     const uint32_t* keys = in1 ? P<uint32_t>(ctx->pk1) : P<uint32_t>(ctx->pk0);
-    const uint32_t* list = in1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
+    uint32_t* list = in1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
     stage_begin(ctx, H3DGS_STAGE_RANGES);
     CK(launch_ranges(keys, cnt + C_NPAIRS_KEPT, P<int2>(ctx->ranges), grid, s), "ranges");
     stage_end(ctx, H3DGS_STAGE_RANGES);
+    stage_begin(ctx, H3DGS_STAGE_DEPTH_SORT);
+    CK(launch_tile_depth_sort(P<int2>(ctx->ranges), ctx->n_tiles, P<uint32_t>(ctx->s_key), list,
+                              P<unsigned long long>(ctx->sort_scratch), 2 * capP, s),
+       "tile depth sort");
+    stage_end(ctx, H3DGS_STAGE_DEPTH_SORT);
     stage_begin(ctx, H3DGS_STAGE_BLEND);
-    CK(launch_blend(P<DevCam>(ctx->cams), n_cams, ctx->n_tiles, o, P<int2>(ctx->ranges), list, sb.rec, images,
-                    P<float>(ctx->T_final), P<int32_t>(ctx->n_contrib),
-                    reinterpret_cast<unsigned long long*>(cnt + C_EVALS), s),
-       "blend");
+    {
+        const int NT = o.tile_w * o.tile_h;
+        const int64_t icap = ctx->n_tiles + capP / o.chunk + 1;
+        CK(ensure(ctx->items, sizeof(int2) * (size_t)icap), "blend items");
+        CK(ensure(ctx->tile_item0, sizeof(int32_t) * (size_t)ctx->n_tiles), "blend items");
+        CK(ensure(ctx->tile_nch, sizeof(int32_t) * (size_t)ctx->n_tiles), "blend items");
+        CK(ensure(ctx->sc_Tc, sizeof(float) * (size_t)icap * NT), "blend scratch");
+        CK(ensure(ctx->sc_C, 3 * sizeof(float) * (size_t)icap * NT), "blend scratch");
+        CK(ensure(ctx->sc_Tend, sizeof(float) * (size_t)icap * NT), "blend scratch");
+        CK(ensure(ctx->sc_last, sizeof(int32_t) * (size_t)icap * NT), "blend scratch");
+        ctx->item_cap = icap;
+        ctx->opts = o;
+        ctx->pairs_in_1 = in1;
+        BlendArgs ba = blend_args(ctx, n_cams, images);
+        CK(launch_blend(ba, s), "blend");
+    }
     stage_end(ctx, H3DGS_STAGE_BLEND);
     ctx->rendered = true;
     ctx->saved = save_for_backward != 0;
-    ctx->opts = o;
     ctx->cut_ids = cut_ids;
     ctx->cut_t = cut_t;
     ctx->cut_offsets = cut_offsets;
-    ctx->depth_in_2 = in2;
     ctx->pairs_in_1 = in1;
     ctx->splat_cap_used = capM;
     ctx->pair_cap_used = capP;
@@ -505,12 +554,10 @@ h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL, const h3dgs_
     CK(ensure(ctx->splat_grad, sizeof(float) * 12 * (size_t)ctx->splat_cap_used), "splat gradient buffer");
     CK(cudaMemsetAsync(ctx->splat_grad.p, 0, sizeof(float) * 12 * (size_t)ctx->splat_cap_used, ctx->stream), "memset");
     GradBufs gb{g->mean, g->scale, g->rot, g->opacity, g->sh};
-    const uint32_t* list = ctx->pairs_in_1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
     cudaEvent_t* ev = ctx->prof ? ctx->ev + 2 * H3DGS_STAGE_BACKWARD_BLEND : nullptr;
-    CK(launch_backward(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, ctx->n_tiles, ctx->opts, ctx->cut_ids, ctx->cut_t,
-                       ctx->cut_offsets, P<int2>(ctx->ranges), list, P<float4>(ctx->s_rec), P<uint2>(ctx->s_rect),
-                       P<uint32_t>(ctx->counters) + C_NSPLATS, ctx->splat_cap_used, P<float>(ctx->T_final),
-                       P<int32_t>(ctx->n_contrib), dL, P<float>(ctx->splat_grad), gb, freeze_leaves,
+    BlendArgs ba = blend_args(ctx, n_cams, nullptr);
+    CK(launch_backward(dev_hier(ctx), ba, ctx->cut_ids, ctx->cut_t, ctx->cut_offsets, P<uint2>(ctx->s_rect),
+                       P<uint32_t>(ctx->counters) + C_NSPLATS, dL, P<float>(ctx->splat_grad), gb, freeze_leaves,
                        ctx->num_sms * 8, ev, ctx->stream),
        "backward");
     if (ctx->prof) ctx->ev_used[H3DGS_STAGE_BACKWARD_BLEND] = ctx->ev_used[H3DGS_STAGE_BACKWARD_SPLAT] = true;
@@ -533,6 +580,9 @@ h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out) {
     uint64_t ev;
     std::memcpy(&ev, c + C_EVALS, sizeof(ev));
     out->n_evals = (int64_t)ev;
+    std::memcpy(&ev, c + C_EVALS_T, sizeof(ev));
+    out->n_evals_tpass = (int64_t)ev;
+    out->n_items = c[C_NITEMS];
     return H3DGS_OK;
 }
 
@@ -610,24 +660,15 @@ h3dgs_status h3dgs_debug_splats(h3dgs_ctx* ctx, float* rec, int32_t* rect, float
     cudaStream_t s = ctx->stream;
     std::vector<float4> r(3 * std::max<int64_t>(m, 1));
     std::vector<uint2> rc(std::max<int64_t>(m, 1));
-    std::vector<uint32_t> key(std::max<int64_t>(m, 1)), idx(std::max<int64_t>(m, 1));
-    // the depth sort leaves (depth key, entry) pairs in depth order: invert it to get each entry's depth
-    const uint32_t* sk = ctx->depth_in_2 ? P<uint32_t>(ctx->s_key2) : P<uint32_t>(ctx->s_key);
-    const uint32_t* si = ctx->depth_in_2 ? P<uint32_t>(ctx->s_idx2) : P<uint32_t>(ctx->s_idx);
+    std::vector<uint32_t> key(std::max<int64_t>(m, 1));
     if (m > 0) {
         CK(cudaMemcpyAsync(r.data(), ctx->s_rec.p, 48 * m, cudaMemcpyDeviceToHost, s), "read splats");
         CK(cudaMemcpyAsync(rc.data(), ctx->s_rect.p, 8 * m, cudaMemcpyDeviceToHost, s), "read rects");
-        CK(cudaMemcpyAsync(key.data(), sk, 4 * m, cudaMemcpyDeviceToHost, s), "read depth");
-        CK(cudaMemcpyAsync(idx.data(), si, 4 * m, cudaMemcpyDeviceToHost, s), "read depth order");
+        CK(cudaMemcpyAsync(key.data(), ctx->s_key.p, 4 * m, cudaMemcpyDeviceToHost, s), "read depth");
     }
     CK(cudaStreamSynchronize(s), "debug sync");
     std::vector<float> depth(std::max<int64_t>(m, 1), 0.0f);
-    for (int64_t i = 0; i < m; ++i)
-        if (idx[i] < (uint32_t)m) {
-            float d;
-            std::memcpy(&d, &key[i], 4);
-            depth[idx[i]] = d;
-        }
+    for (int64_t i = 0; i < m; ++i) std::memcpy(&depth[i], &key[i], 4);
     for (int64_t i = 0; i < m; ++i) {
         const bool culled = rc[i].x == 0xffffffffu;
         const float4 a = r[3 * i], b = r[3 * i + 1], c = r[3 * i + 2];

@@ -61,11 +61,21 @@ __device__ __forceinline__ float warp_sum(float x) {
 
 }  // namespace
 
+// One CTA per blend item (tile, chunk).  A single-chunk tile starts from the pixel's final T and
+// contributor count; a chunk of a split tile starts from the T at its end and its last contributor
+// (saved by the forward pass), with the colour behind it = later chunks' colour + T_final bg.
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
                                                                  const int2* __restrict__ ranges,
                                                                  const uint32_t* __restrict__ list,
                                                                  const float4* __restrict__ splat,
+                                                                 const int2* __restrict__ items,
+                                                                 const uint32_t* __restrict__ n_items,
+                                                                 const int32_t* __restrict__ tile_item0,
+                                                                 const int32_t* __restrict__ tile_nch, int chunk,
+                                                                 const float* __restrict__ scC,
+                                                                 const float* __restrict__ scTend,
+                                                                 const int32_t* __restrict__ sclast,
                                                                  const float* __restrict__ T_final,
                                                                  const int32_t* __restrict__ n_contrib,
                                                                  const float* __restrict__ dL,
@@ -74,7 +84,11 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
     __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
     __shared__ uint32_t s_id[NT];
     __shared__ int s_max;
-    const int64_t tile = blockIdx.x;
+    const uint32_t item = blockIdx.x;
+    if (item >= *n_items) return;
+    const int2 it = items[item];
+    const int64_t tile = it.x;
+    const int nch = tile_nch[tile];
     int lo = 0, hi = n_cams - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -87,29 +101,44 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
     const bool inside = px_i < cam.width && py_i < cam.height;
     const float px = (float)px_i + 0.5f, py = (float)py_i + 0.5f;
     const int2 r = ranges[tile];
-    float T = 1.0f, g0 = 0, g1 = 0, g2 = 0;
-    int last = 0;
+    const int begin = r.x + it.y * chunk;     // first list entry of this item
+    float T = 1.0f, g0 = 0, g1 = 0, g2 = 0, S0 = 0, S1 = 0, S2 = 0;
+    int stop = begin;                         // entries [begin, stop) are walked back to front
     if (inside) {
         const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
         const int64_t plane = (int64_t)cam.width * cam.height;
         const float* gp = dL + 3 * cam.pix_base + (int64_t)py_i * cam.width + px_i;
         g0 = gp[0]; g1 = gp[plane]; g2 = gp[2 * plane];
-        T = T_final[pix];
-        last = n_contrib[pix];
+        const float Tf = T_final[pix];
+        S0 = Tf * o.bg[0]; S1 = Tf * o.bg[1]; S2 = Tf * o.bg[2];
+        if (nch == 1) {
+            T = Tf;
+            stop = r.x + n_contrib[pix];
+        } else {
+            const int64_t i0 = tile_item0[tile];
+            const int64_t slot = (int64_t)item * NT + threadIdx.x;
+            T = scTend[slot];
+            const int l = sclast[slot];
+            stop = l < 0 ? begin : r.x + l;
+            for (int c = it.y + 1; c < nch; ++c) {
+                const int64_t sl = (i0 + c) * NT + threadIdx.x;
+                S0 += scC[3 * sl]; S1 += scC[3 * sl + 1]; S2 += scC[3 * sl + 2];
+            }
+        }
     }
-    float S0 = T * o.bg[0], S1 = T * o.bg[1], S2 = T * o.bg[2];
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    atomicMax(&s_max, last);
+    atomicMax(&s_max, stop - begin);
     __syncthreads();
     const int count = s_max;
+    const int last = stop - begin;
     const float clampv = o.alpha_clamp, afloor = o.alpha_floor;
     for (int end = count; end > 0; end -= NT) {
         const int n = min(NT, end);
         const int first = end - n;
         __syncthreads();
         if ((int)threadIdx.x < n) {
-            const uint32_t s = __ldg(list + r.x + first + threadIdx.x);
+            const uint32_t s = __ldg(list + begin + first + threadIdx.x);
             s_id[threadIdx.x] = s;
             s_a[threadIdx.x] = __ldg(splat + 3 * (int64_t)s);
             s_b[threadIdx.x] = __ldg(splat + 3 * (int64_t)s + 1);
@@ -376,19 +405,19 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
     }
 }
 
-cudaError_t launch_backward(const DevHier& h, const DevCam* cams, int n_cams, int64_t n_tiles, const DevOpts& o,
-                            const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets, const int2* ranges,
-                            const uint32_t* list, const float4* splat, const uint2* rect, const uint32_t* n_splats,
-                            int64_t cap, const float* T_final, const int32_t* n_contrib, const float* dL,
+cudaError_t launch_backward(const DevHier& h, const BlendArgs& a, const int32_t* cut_ids, const float* cut_t,
+                            const int64_t* cut_offsets, const uint2* rect, const uint32_t* n_splats, const float* dL,
                             float* splat_grad, const GradBufs& g, int freeze_leaves, int grid, cudaEvent_t* ev,
                             cudaStream_t s) {
-    (void)cap;
     if (ev) cudaEventRecord(ev[0], s);
-    if (n_tiles > 0) {
-        const unsigned tg = (unsigned)n_tiles;
-#define BW(TWV, THV)                                                                                          \
-    backward_blend_kernel<TWV, THV><<<tg, TWV * THV, 0, s>>>(cams, n_cams, o, ranges, list, splat, T_final, \
-                                                               n_contrib, dL, splat_grad)
+    if (a.n_tiles > 0) {
+        const unsigned ig = (unsigned)a.item_cap;
+#define BW(TWV, THV)                                                                                              \
+    backward_blend_kernel<TWV, THV><<<ig, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat,    \
+                                                             a.items, a.n_items, a.tile_item0, a.tile_nch, a.chunk, \
+                                                             a.scratch_C, a.scratch_Tend, a.scratch_last, a.T_final, \
+                                                             a.n_contrib, dL, splat_grad)
+        const DevOpts& o = a.o;
         if (o.tile_w == 16 && o.tile_h == 16) BW(16, 16);
         else if (o.tile_w == 8 && o.tile_h == 8) BW(8, 8);
         else if (o.tile_w == 32 && o.tile_h == 8) BW(32, 8);
@@ -404,8 +433,8 @@ cudaError_t launch_backward(const DevHier& h, const DevCam* cams, int n_cams, in
         cudaEventRecord(ev[1], s);
         cudaEventRecord(ev[2], s);
     }
-    backward_splat_kernel<<<grid, 128, 0, s>>>(h, cams, n_cams, o, cut_ids, cut_t, cut_offsets, rect, n_splats, splat_grad,
-                                               g, freeze_leaves);
+    backward_splat_kernel<<<grid, 128, 0, s>>>(h, a.cams, a.n_cams, a.o, cut_ids, cut_t, cut_offsets, rect, n_splats,
+                                               splat_grad, g, freeze_leaves);
     if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }

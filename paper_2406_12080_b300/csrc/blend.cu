@@ -1,15 +1,25 @@
-// Per-tile front-to-back blending (a7).
+// Per-tile front-to-back blending (a7), with long tile lists split into chunks.
 //
-// One CTA per screen tile, one thread per pixel.  The tile's splat list is consumed in batches
-// staged through shared memory (one 48-byte record per thread per batch); every pixel walks the
-// batch in order:
+// Per pixel and splat, in list order (tile list = (depth, cut position) order):
 //   G = 2^(ca dx^2 + cb dx dy + cc dy^2)                (conic pre-scaled by -log2(e)/2)
 //   alpha_n = min(c, o_n G),  alpha_p = min(c, o_p G)
 //   alpha'  = 1 - (1 - alpha_p)^(1/K)                   (Eq. alphap; K = 2: alpha_p / (1 + sqrt(1 - alpha_p)))
 //   alpha   = (1 - t) alpha_n + t alpha'                (t = parent weight; t = 0 skips alpha')
 //   skip alpha < alpha_floor; stop before T (1 - alpha) < t_min; C += colour alpha T.
-// The per-pixel decision quantities (dx, dy, exponent, alpha, T) use a fixed fp32 order; the
-// exponential and alpha' use the fast hardware approximations.
+// The per-pixel decision quantities (dx, dy, exponent, alpha, T) use a fixed fp32 order.
+//
+// Street scenes put thousands of splats behind some pixels (near the vanishing point), so a
+// one-CTA-per-tile blend is bounded by its longest list.  Lists longer than `chunk` entries are
+// cut into chunks that run as separate CTAs ("items"):
+//   pass T    (split tiles only) each chunk computes the product of (1 - alpha) over its
+//             contributors, without the stop rule, giving every chunk its incoming transmittance
+//             T_in as a product of the earlier chunks' products;
+//   pass main every item walks its entries from T_in with the exact skip/stop rules; single-chunk
+//             tiles write the pixel directly, chunks of split tiles write (colour, T at the end,
+//             last contributor) to a per-(item, pixel) scratch kept for the adjoint;
+//   combine   per pixel of a split tile: colour = sum of its chunks, T_final and the last
+//             contributor from the chunk where the walk stopped.
+// A chunk whose T_in is already below t_min adds nothing (the walk stopped in an earlier chunk).
 #include "internal.cuh"
 
 namespace h3dgs {
@@ -31,38 +41,131 @@ __device__ __forceinline__ float alpha_prime(float ap, float K) {
     return 1.0f - ex2_approx(__fdividef(lg2_approx(1.0f - ap), K));
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) blend_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
-                                                        const int2* __restrict__ ranges, const uint32_t* __restrict__ list,
-                                                        const float4* __restrict__ splat, float* __restrict__ images,
-                                                        float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
-                                                        unsigned long long* __restrict__ n_evals) {
-    constexpr int NT = TW * TH;
-    __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
-    __shared__ unsigned int s_evals;
-    const int64_t tile = blockIdx.x;
-    if (threadIdx.x == 0) s_evals = 0;
-    // camera of this tile
+// alpha of one (pixel, splat) pair, fixed fp32 order
+__device__ __forceinline__ float pair_alpha(float px, float py, const float4 a, const float4 b, float Kc, float clampv) {
+    const float dx = fsub(px, a.x), dy = fsub(py, a.y);
+    const float h = ffma(a.z, dx, fmul(a.w, dy));
+    const float g = fmul(fmul(b.x, dy), dy);
+    const float p2 = ffma(dx, h, g);
+    const float G = ex2_approx(p2);
+    const float an = fminf(clampv, fmul(b.y, G));
+    if (b.w == 0.0f) return an;
+    const float ap = fminf(clampv, fmul(b.z, G));
+    return ffma(b.w, alpha_prime(ap, Kc), fmul(fsub(1.0f, b.w), an));
+}
+
+struct TileGeom {
+    int px_i, py_i;
+    bool inside;
+    float px, py;
+    const DevCam* cam;
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const DevCam* __restrict__ cams, int n_cams, int64_t tile, int TW, int TH) {
     int lo = 0, hi = n_cams - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (cams[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
     }
-    const DevCam& cam = cams[lo];
-    const int local = (int)(tile - cam.tile_base);
-    const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
-    const int px_i = tx * TW + (threadIdx.x % TW), py_i = ty * TH + (threadIdx.x / TW);
-    const bool inside = px_i < cam.width && py_i < cam.height;
-    const float px = (float)px_i + 0.5f, py = (float)py_i + 0.5f;
+    TileGeom g;
+    g.cam = cams + lo;
+    const int local = (int)(tile - g.cam->tile_base);
+    const int tx = local % g.cam->tiles_x, ty = local / g.cam->tiles_x;
+    g.px_i = tx * TW + (threadIdx.x % TW);
+    g.py_i = ty * TH + (threadIdx.x / TW);
+    g.inside = g.px_i < g.cam->width && g.py_i < g.cam->height;
+    g.px = (float)g.px_i + 0.5f;
+    g.py = (float)g.py_i + 0.5f;
+    return g;
+}
+
+// ------------------------------------------------------------------------------------ plan
+
+// Single block: chunk counts per tile, their exclusive scan, and the (tile, chunk) item list.
+__global__ void __launch_bounds__(1024) blend_plan_kernel(const int2* __restrict__ ranges, int64_t n_tiles, int chunk,
+                                                          int32_t* __restrict__ tile_item0, int32_t* __restrict__ tile_nch,
+                                                          int2* __restrict__ items, int64_t item_cap,
+                                                          uint32_t* __restrict__ n_items) {
+    __shared__ int32_t s_part[1024];
+    const int64_t per = (n_tiles + blockDim.x - 1) / blockDim.x;
+    const int64_t t0 = threadIdx.x * per, t1 = min(n_tiles, t0 + per);
+    int32_t sum = 0;
+    for (int64_t t = t0; t < t1; ++t) {
+        const int len = ranges[t].y - ranges[t].x;
+        sum += len <= chunk ? 1 : (len + chunk - 1) / chunk;
+    }
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const int32_t x = (int)threadIdx.x >= off ? s_part[threadIdx.x - off] : 0;
+        __syncthreads();
+        s_part[threadIdx.x] += x;
+        __syncthreads();
+    }
+    int32_t run = s_part[threadIdx.x] - sum;
+    if (threadIdx.x == blockDim.x - 1) *n_items = (uint32_t)min((int64_t)s_part[threadIdx.x], item_cap);
+    for (int64_t t = t0; t < t1; ++t) {
+        const int len = ranges[t].y - ranges[t].x;
+        const int nch = len <= chunk ? 1 : (len + chunk - 1) / chunk;
+        tile_item0[t] = run;
+        tile_nch[t] = nch;
+        for (int c = 0; c < nch; ++c)
+            if (run + c < item_cap) items[run + c] = make_int2((int)t, c);
+        run += nch;
+    }
+}
+
+// ------------------------------------------------------------------------------------ passes
+
+// Scratch per (item, pixel), struct-of-arrays over pixels: Tc, C0, C1, C2, Tend, last.
+struct Scratch {
+    float* Tc;     // product of (1 - alpha) over the chunk (pass T)
+    float* C;      // [3] colour of the chunk
+    float* Tend;   // T after the chunk's walk (stop applied)
+    int32_t* last; // list position (within the tile) after the chunk's last contributor, or -1
+};
+
+template <int TW, int TH, bool MAIN>
+__global__ void __launch_bounds__(TW * TH) blend_items_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
+                                                              const int2* __restrict__ ranges,
+                                                              const uint32_t* __restrict__ list,
+                                                              const float4* __restrict__ splat,
+                                                              const int2* __restrict__ items,
+                                                              const uint32_t* __restrict__ n_items,
+                                                              const int32_t* __restrict__ tile_item0,
+                                                              const int32_t* __restrict__ tile_nch, int chunk,
+                                                              Scratch sc, float* __restrict__ images,
+                                                              float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
+                                                              unsigned long long* __restrict__ n_evals) {
+    constexpr int NT = TW * TH;
+    __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
+    __shared__ unsigned int s_evals;
+    const uint32_t item = blockIdx.x;
+    if (item >= *n_items) return;
+    const int2 it = items[item];
+    const int64_t tile = it.x;
+    const int nch = tile_nch[tile];
+    if (!MAIN && nch == 1) return;                      // pass T only for split tiles
+    if (threadIdx.x == 0) s_evals = 0;
+    const TileGeom g = tile_geom(cams, n_cams, tile, TW, TH);
     const int2 r = ranges[tile];
+    const int begin = r.x + it.y * chunk;
+    const int end = nch == 1 ? r.y : min(r.y, begin + chunk);
+    const int64_t slot = (int64_t)item * NT + threadIdx.x;
     const float clampv = o.alpha_clamp, afloor = o.alpha_floor, tmin = o.t_min;
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    int last = 0;
+    float T = 1.0f;
+    if (MAIN && nch > 1) {
+        // incoming transmittance: product of the earlier chunks' (1 - alpha) products
+        const int64_t i0 = tile_item0[tile];
+        for (int c = 0; c < it.y; ++c) T = fmul(T, sc.Tc[(i0 + c) * NT + threadIdx.x]);
+    }
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    int last = -1;
     unsigned int evals = 0;
-    bool done = !inside;
-    for (int b0 = r.x; b0 < r.y; b0 += NT) {
+    bool done = !g.inside || (MAIN && T < tmin);
+    for (int b0 = begin; b0 < end; b0 += NT) {
         if (__syncthreads_count(done) == NT) break;
-        const int n = min(NT, r.y - b0);
+        const int n = min(NT, end - b0);
         if ((int)threadIdx.x < n) {
             const uint32_t s = __ldg(list + b0 + threadIdx.x);
             s_a[threadIdx.x] = __ldg(splat + 3 * (int64_t)s);
@@ -73,21 +176,14 @@ __global__ void __launch_bounds__(TW * TH) blend_kernel(const DevCam* __restrict
         if (!done) {
             for (int j = 0; j < n; ++j) {
                 ++evals;
-                const float4 a = s_a[j], b = s_b[j];
-                const float dx = fsub(px, a.x), dy = fsub(py, a.y);
-                const float h = ffma(a.z, dx, fmul(a.w, dy));
-                const float g = fmul(fmul(b.x, dy), dy);
-                const float p2 = ffma(dx, h, g);
-                const float G = ex2_approx(p2);
-                const float an = fminf(clampv, fmul(b.y, G));
-                float alpha = an;
-                if (b.w != 0.0f) {
-                    const float ap = fminf(clampv, fmul(b.z, G));
-                    const float apr = alpha_prime(ap, s_c[j].w);
-                    alpha = ffma(b.w, apr, fmul(fsub(1.0f, b.w), an));
-                }
+                const float alpha = pair_alpha(g.px, g.py, s_a[j], s_b[j], s_c[j].w, clampv);
                 if (alpha < afloor) continue;
                 const float Tn = fmul(T, fsub(1.0f, alpha));
+                if (!MAIN) {                            // pass T: no stop, but nothing matters below t_min
+                    T = Tn;
+                    if (T < tmin) { done = true; break; }
+                    continue;
+                }
                 if (Tn < tmin) { done = true; break; }
                 const float w = alpha * T;
                 const float4 c = s_c[j];
@@ -103,37 +199,102 @@ __global__ void __launch_bounds__(TW * TH) blend_kernel(const DevCam* __restrict
     if ((threadIdx.x & 31) == 0) atomicAdd(&s_evals, evals);
     __syncthreads();
     if (threadIdx.x == 0 && n_evals) atomicAdd(n_evals, (unsigned long long)s_evals);
-    if (inside) {
-        const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
+    if (!MAIN) {
+        sc.Tc[slot] = T;
+        return;
+    }
+    if (nch > 1) {
+        sc.C[3 * slot + 0] = C0;
+        sc.C[3 * slot + 1] = C1;
+        sc.C[3 * slot + 2] = C2;
+        sc.Tend[slot] = T;
+        sc.last[slot] = last;
+        return;
+    }
+    if (g.inside) {
+        const DevCam& cam = *g.cam;
+        const int64_t pix = cam.pix_base + (int64_t)g.py_i * cam.width + g.px_i;
         const int64_t plane = (int64_t)cam.width * cam.height;
-        float* img = images + 3 * cam.pix_base + (int64_t)py_i * cam.width + px_i;
+        float* img = images + 3 * cam.pix_base + (int64_t)g.py_i * cam.width + g.px_i;
         img[0] = fmaf(T, o.bg[0], C0);
         img[plane] = fmaf(T, o.bg[1], C1);
         img[2 * plane] = fmaf(T, o.bg[2], C2);
         if (T_final) T_final[pix] = T;
-        if (n_contrib) n_contrib[pix] = last;
+        if (n_contrib) n_contrib[pix] = last < 0 ? 0 : last;
     }
 }
 
-cudaError_t launch_blend(const DevCam* cams, int n_cams, int64_t n_tiles, const DevOpts& o, const int2* ranges,
-                         const uint32_t* list, const float4* splat, float* images, float* T_final, int32_t* n_contrib,
-                         unsigned long long* n_evals, cudaStream_t s) {
-    if (n_tiles <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)n_tiles;
-    if (o.tile_w == 16 && o.tile_h == 16)
-        blend_kernel<16, 16><<<grid, 256, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
-    else if (o.tile_w == 8 && o.tile_h == 8)
-        blend_kernel<8, 8><<<grid, 64, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
-    else if (o.tile_w == 32 && o.tile_h == 8)
-        blend_kernel<32, 8><<<grid, 256, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
-    else if (o.tile_w == 8 && o.tile_h == 32)
-        blend_kernel<8, 32><<<grid, 256, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
-    else if (o.tile_w == 16 && o.tile_h == 8)
-        blend_kernel<16, 8><<<grid, 128, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
-    else if (o.tile_w == 32 && o.tile_h == 4)
-        blend_kernel<32, 4><<<grid, 128, 0, s>>>(cams, n_cams, o, ranges, list, splat, images, T_final, n_contrib, n_evals);
-    else
-        return cudaErrorInvalidValue;
+// Split tiles: per pixel, sum the chunks' colours; T_final and the last contributor come from the
+// last chunk whose walk ran (a chunk with T_in below t_min did not run).
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
+                                                                int64_t n_tiles, const int32_t* __restrict__ tile_item0,
+                                                                const int32_t* __restrict__ tile_nch, Scratch sc,
+                                                                float* __restrict__ images, float* __restrict__ T_final,
+                                                                int32_t* __restrict__ n_contrib) {
+    constexpr int NT = TW * TH;
+    const int64_t tile = blockIdx.x;
+    if (tile >= n_tiles) return;
+    const int nch = tile_nch[tile];
+    if (nch == 1) return;
+    const TileGeom g = tile_geom(cams, n_cams, tile, TW, TH);
+    if (!g.inside) return;
+    const int64_t i0 = tile_item0[tile];
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f, Tin = 1.0f;
+    int last = 0;
+    for (int c = 0; c < nch; ++c) {
+        const int64_t slot = (i0 + c) * NT + threadIdx.x;
+        if (!(Tin < o.t_min)) {
+            C0 += sc.C[3 * slot + 0];
+            C1 += sc.C[3 * slot + 1];
+            C2 += sc.C[3 * slot + 2];
+            T = sc.Tend[slot];
+            if (sc.last[slot] >= 0) last = sc.last[slot];
+        }
+        Tin = fmul(Tin, sc.Tc[slot]);
+    }
+    const DevCam& cam = *g.cam;
+    const int64_t pix = cam.pix_base + (int64_t)g.py_i * cam.width + g.px_i;
+    const int64_t plane = (int64_t)cam.width * cam.height;
+    float* img = images + 3 * cam.pix_base + (int64_t)g.py_i * cam.width + g.px_i;
+    img[0] = fmaf(T, o.bg[0], C0);
+    img[plane] = fmaf(T, o.bg[1], C1);
+    img[2 * plane] = fmaf(T, o.bg[2], C2);
+    if (T_final) T_final[pix] = T;
+    if (n_contrib) n_contrib[pix] = last;
+}
+
+cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
+    if (a.n_tiles <= 0) return cudaSuccess;
+    blend_plan_kernel<<<1, 1024, 0, s>>>(a.ranges, a.n_tiles, a.chunk, a.tile_item0, a.tile_nch, a.items, a.item_cap,
+                                         a.n_items);
+    Scratch sc{a.scratch_Tc, a.scratch_C, a.scratch_Tend, a.scratch_last};
+    unsigned long long* ev_main = a.n_evals;
+    unsigned long long* ev_tpass = a.n_evals ? a.n_evals + 1 : nullptr;
+    const unsigned grid = (unsigned)a.item_cap;
+    const unsigned tg = (unsigned)a.n_tiles;
+#define BL(TWV, THV)                                                                                                  \
+    do {                                                                                                              \
+        blend_items_kernel<TWV, THV, false><<<grid, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list,       \
+                                                                       a.splat, a.items, a.n_items, a.tile_item0,     \
+                                                                       a.tile_nch, a.chunk, sc, a.images, a.T_final,  \
+                                                                       a.n_contrib, ev_tpass);                        \
+        blend_items_kernel<TWV, THV, true><<<grid, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list,        \
+                                                                      a.splat, a.items, a.n_items, a.tile_item0,      \
+                                                                      a.tile_nch, a.chunk, sc, a.images, a.T_final,   \
+                                                                      a.n_contrib, ev_main);                          \
+        blend_combine_kernel<TWV, THV><<<tg, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.n_tiles, a.tile_item0,       \
+                                                                a.tile_nch, sc, a.images, a.T_final, a.n_contrib);    \
+    } while (0)
+    const DevOpts& o = a.o;
+    if (o.tile_w == 16 && o.tile_h == 16) BL(16, 16);
+    else if (o.tile_w == 8 && o.tile_h == 8) BL(8, 8);
+    else if (o.tile_w == 32 && o.tile_h == 8) BL(32, 8);
+    else if (o.tile_w == 8 && o.tile_h == 32) BL(8, 32);
+    else if (o.tile_w == 16 && o.tile_h == 8) BL(16, 8);
+    else if (o.tile_w == 32 && o.tile_h == 4) BL(32, 4);
+    else return cudaErrorInvalidValue;
+#undef BL
     return cudaGetLastError();
 }
 

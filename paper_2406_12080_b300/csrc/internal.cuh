@@ -44,7 +44,7 @@ struct CamBatch {
 
 // Render options as used on the device.
 struct DevOpts {
-    int32_t tile_w, tile_h;
+    int32_t tile_w, tile_h, chunk;
     float lowpass, alpha_clamp, alpha_floor, t_min;
     int32_t aa_compensate, interpolate;
     float bg[3];
@@ -157,11 +157,46 @@ cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_
                              int64_t cap_pairs, uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals,
                              uint32_t* flags, int grid, cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_pairs_kept, int2* ranges, int grid, cudaStream_t s);
+// Plain exclusive scan (no gather).
+cudaError_t scan_plain(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t* total, const SortWork& w,
+                       cudaStream_t s);
+// Pairs emitted in cut order (splat m's tiles in row-major order).
+cudaError_t launch_duplicate_plain(const DevCam* cams, int n_cams, const int64_t* cut_offsets, const SplatBufs& sb,
+                                   const uint32_t* pair_off, const uint32_t* n_pairs, int64_t cap_pairs,
+                                   uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* flags, int grid,
+                                   cudaStream_t s);
+// Orders every tile's list by (depth key, cut position); scratch: 64-bit, >= 2 * pairs entries.
+cudaError_t launch_tile_depth_sort(const int2* ranges, int64_t n_tiles, const uint32_t* depth_key, uint32_t* list,
+                                   unsigned long long* scratch, int64_t scratch_cap, cudaStream_t s);
 
 // blend.cu
-cudaError_t launch_blend(const DevCam* cams, int n_cams, int64_t n_tiles, const DevOpts& o, const int2* ranges,
-                         const uint32_t* list, const float4* splat, float* images, float* T_final,
-                         int32_t* n_contrib, unsigned long long* n_evals, cudaStream_t s);
+// Everything the chunked blend and its adjoint share.  Items are (tile, chunk) pairs; tiles with at
+// most `chunk` list entries are one item.  Scratch holds, per (item, pixel), the chunk's (1 - alpha)
+// product, colour, end transmittance and last contributor (split tiles only).
+struct BlendArgs {
+    const DevCam* cams;
+    int n_cams;
+    int64_t n_tiles;
+    DevOpts o;
+    const int2* ranges;
+    const uint32_t* list;
+    const float4* splat;
+    int chunk;
+    int64_t item_cap;
+    int2* items;
+    int32_t* tile_item0;
+    int32_t* tile_nch;
+    uint32_t* n_items;
+    float* scratch_Tc;
+    float* scratch_C;
+    float* scratch_Tend;
+    int32_t* scratch_last;
+    float* images;
+    float* T_final;
+    int32_t* n_contrib;
+    unsigned long long* n_evals;  // [2]: main-pass evaluations, transmittance-pass evaluations
+};
+cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
 
 // builder.cu
 struct BuildOut {
@@ -176,11 +211,9 @@ cudaError_t build_hierarchy(int64_t L, const float* mean, const float* scale, co
 struct GradBufs {
     float* mean; float* scale; float* rot; float* opacity; float* sh;
 };
-cudaError_t launch_backward(const DevHier& h, const DevCam* cams, int n_cams, int64_t n_tiles, const DevOpts& o,
-                            const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets,
-                            const int2* ranges, const uint32_t* list, const float4* splat, const uint2* rect,
-                            const uint32_t* n_splats, int64_t cap, const float* T_final, const int32_t* n_contrib,
-                            const float* dL, float* splat_grad, const GradBufs& g, int freeze_leaves, int grid,
+cudaError_t launch_backward(const DevHier& h, const BlendArgs& a, const int32_t* cut_ids, const float* cut_t,
+                            const int64_t* cut_offsets, const uint2* rect, const uint32_t* n_splats, const float* dL,
+                            float* splat_grad, const GradBufs& g, int freeze_leaves, int grid,
                             cudaEvent_t* ev /* 4 events or NULL */, cudaStream_t s);
 
 }  // namespace h3dgs

@@ -257,11 +257,25 @@ __global__ void __launch_bounds__(SC_BLOCK) scan_reduce_kernel(const uint32_t* _
     if (threadIdx.x == 0) partial[blockIdx.x] = total;
 }
 
-__global__ void scan_partials_kernel(uint32_t* __restrict__ partial, int G, uint32_t* __restrict__ total_out) {
-    if (threadIdx.x != 0) return;
-    uint32_t run = 0;
-    for (int b = 0; b < G; ++b) { const uint32_t x = partial[b]; partial[b] = run; run += x; }
-    *total_out = run;
+// exclusive scan of the G block partials in place (one block of 1024 threads), total to *total_out
+__global__ void __launch_bounds__(1024) scan_partials_kernel(uint32_t* __restrict__ partial, int G,
+                                                             uint32_t* __restrict__ total_out) {
+    __shared__ uint32_t s[1024];
+    const int per = (G + 1023) / 1024;
+    const int i0 = threadIdx.x * per, i1 = min(G, i0 + per);
+    uint32_t sum = 0;
+    for (int i = i0; i < i1; ++i) sum += partial[i];
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint32_t x = (int)threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
+        __syncthreads();
+        s[threadIdx.x] += x;
+        __syncthreads();
+    }
+    uint32_t run = s[threadIdx.x] - sum;
+    for (int i = i0; i < i1; ++i) { const uint32_t x = partial[i]; partial[i] = run; run += x; }
+    if (threadIdx.x == 1023) *total_out = s[1023];
 }
 
 __global__ void __launch_bounds__(SC_BLOCK) scan_down_kernel(const uint32_t* __restrict__ in,
@@ -286,7 +300,7 @@ __global__ void __launch_bounds__(SC_BLOCK) scan_down_kernel(const uint32_t* __r
 cudaError_t scan_gathered(const uint32_t* in, const uint32_t* idx, uint32_t* out, const uint32_t* n_dev,
                           uint32_t* total, const SortWork& w, cudaStream_t s) {
     scan_reduce_kernel<<<w.blocks, SC_BLOCK, 0, s>>>(in, idx, n_dev, w.partial);
-    scan_partials_kernel<<<1, 32, 0, s>>>(w.partial, w.blocks, total);
+    scan_partials_kernel<<<1, 1024, 0, s>>>(w.partial, w.blocks, total);
     scan_down_kernel<<<w.blocks, SC_BLOCK, 0, s>>>(in, idx, n_dev, w.partial, out);
     return cudaGetLastError();
 }
@@ -350,6 +364,199 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint32_t* __restrict_
 
 cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_pairs_kept, int2* ranges, int grid, cudaStream_t s) {
     ranges_kernel<<<grid, 256, 0, s>>>(keys, n_pairs_kept, ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace h3dgs
+
+namespace h3dgs {
+
+// ------------------------------------------------------------------------------ per-tile depth sort
+//
+// After the stable sort of the pairs by tile, every tile's entries are in cut-position order.  The
+// tile's list is then ordered by (fp32 depth, cut position) with a bitonic network on 64-bit keys
+// (depth bits << 32 | cut position; unique) held in shared memory.  Lists are classed by length:
+// up to SORT_SMALL entries (16 KB of keys, many CTAs per SM), up to SORT_LARGE (128 KB, one CTA per
+// SM), and longer lists sorted in place in a global 64-bit scratch by the same network.
+
+constexpr int SORT_SMALL = 2048;
+constexpr int SORT_LARGE = 16384;
+
+__device__ __forceinline__ void bitonic_smem(unsigned long long* s, int N) {
+    for (int k = 2; k <= N; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = threadIdx.x; p < (N >> 1); p += blockDim.x) {
+                const int pos = 2 * j * (p / j) + (p % j);
+                const int q = pos + j;
+                const bool up = (pos & k) == 0;
+                const unsigned long long a = s[pos], b = s[q];
+                if ((a > b) == up) { s[pos] = b; s[q] = a; }
+            }
+            __syncthreads();
+        }
+}
+
+template <int CAP>
+__global__ void tile_depth_sort_kernel(const int2* __restrict__ ranges, int64_t n_tiles, const uint32_t* __restrict__ depth_key,
+                                       uint32_t* __restrict__ list, int lo_exclusive) {
+    extern __shared__ unsigned long long s_key[];
+    const int64_t tile = blockIdx.x;
+    if (tile >= n_tiles) return;
+    const int2 r = ranges[tile];
+    const int n = r.y - r.x;
+    if (n <= lo_exclusive || n > CAP || n < 2) return;
+    int N = 1;
+    while (N < n) N <<= 1;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        if (i < n) {
+            const uint32_t m = list[r.x + i];
+            s_key[i] = ((unsigned long long)__ldg(depth_key + m) << 32) | m;
+        } else {
+            s_key[i] = ~0ull;
+        }
+    }
+    __syncthreads();
+    bitonic_smem(s_key, N);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) list[r.x + i] = (uint32_t)(s_key[i] & 0xffffffffu);
+}
+
+// lists longer than SORT_LARGE: the same network over a global scratch (rare; one CTA per tile)
+__global__ void __launch_bounds__(1024) tile_depth_sort_global_kernel(const int2* __restrict__ ranges, int64_t n_tiles,
+                                                                      const uint32_t* __restrict__ depth_key,
+                                                                      uint32_t* __restrict__ list,
+                                                                      unsigned long long* __restrict__ scratch,
+                                                                      int64_t scratch_cap) {
+    const int64_t tile = blockIdx.x;
+    if (tile >= n_tiles) return;
+    const int2 r = ranges[tile];
+    const int n = r.y - r.x;
+    if (n <= SORT_LARGE) return;
+    int N = 1;
+    while (N < n) N <<= 1;
+    // the tile's padded segment lives at [2 r.x, 2 r.x + N) of the scratch (room for pad: N < 2n)
+    const int64_t base = 2 * (int64_t)r.x;
+    if (base + N > scratch_cap) return;
+    unsigned long long* s = scratch + base;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        if (i < n) {
+            const uint32_t m = list[r.x + i];
+            s[i] = ((unsigned long long)__ldg(depth_key + m) << 32) | m;
+        } else {
+            s[i] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= N; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = threadIdx.x; p < (N >> 1); p += blockDim.x) {
+                const int pos = 2 * j * (p / j) + (p % j);
+                const int q = pos + j;
+                const bool up = (pos & k) == 0;
+                const unsigned long long a = s[pos], b = s[q];
+                if ((a > b) == up) { s[pos] = b; s[q] = a; }
+            }
+            __threadfence_block();
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) list[r.x + i] = (uint32_t)(s[i] & 0xffffffffu);
+}
+
+cudaError_t launch_tile_depth_sort(const int2* ranges, int64_t n_tiles, const uint32_t* depth_key, uint32_t* list,
+                                   unsigned long long* scratch, int64_t scratch_cap, cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(tile_depth_sort_kernel<SORT_LARGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SORT_LARGE * 8);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const unsigned g = (unsigned)n_tiles;
+    tile_depth_sort_kernel<SORT_SMALL><<<g, 256, SORT_SMALL * 8, s>>>(ranges, n_tiles, depth_key, list, 0);
+    tile_depth_sort_kernel<SORT_LARGE><<<g, 1024, SORT_LARGE * 8, s>>>(ranges, n_tiles, depth_key, list, SORT_SMALL);
+    tile_depth_sort_global_kernel<<<g, 1024, 0, s>>>(ranges, n_tiles, depth_key, list, scratch, scratch_cap);
+    return cudaGetLastError();
+}
+
+// plain exclusive scan of in[0, n) (no gather): out, *total
+__global__ void __launch_bounds__(SC_BLOCK) scan_reduce_plain_kernel(const uint32_t* __restrict__ in,
+                                                                     const uint32_t* __restrict__ n_dev,
+                                                                     uint32_t* __restrict__ partial) {
+    __shared__ uint32_t s_warp[SC_BLOCK / 32];
+    uint32_t begin, end;
+    scan_range(*n_dev, gridDim.x, blockIdx.x, &begin, &end);
+    uint32_t sum = 0;
+    for (uint32_t i = begin + threadIdx.x; i < end; i += SC_BLOCK) sum += __ldg(in + i);
+    uint32_t total;
+    block_exclusive_scan(sum, s_warp, &total);
+    if (threadIdx.x == 0) partial[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SC_BLOCK) scan_down_plain_kernel(const uint32_t* __restrict__ in,
+                                                                   const uint32_t* __restrict__ n_dev,
+                                                                   const uint32_t* __restrict__ partial,
+                                                                   uint32_t* __restrict__ out) {
+    __shared__ uint32_t s_warp[SC_BLOCK / 32];
+    uint32_t begin, end;
+    scan_range(*n_dev, gridDim.x, blockIdx.x, &begin, &end);
+    uint32_t run = partial[blockIdx.x];
+    for (uint32_t i0 = begin; i0 < end; i0 += SC_BLOCK) {
+        const uint32_t i = i0 + threadIdx.x;
+        const uint32_t x = i < end ? __ldg(in + i) : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(x, s_warp, &total);
+        if (i < end) out[i] = run + ex;
+        run += total;
+    }
+}
+
+cudaError_t scan_plain(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t* total, const SortWork& w,
+                       cudaStream_t s) {
+    scan_reduce_plain_kernel<<<w.blocks, SC_BLOCK, 0, s>>>(in, n_dev, w.partial);
+    scan_partials_kernel<<<1, 1024, 0, s>>>(w.partial, w.blocks, total);
+    scan_down_plain_kernel<<<w.blocks, SC_BLOCK, 0, s>>>(in, n_dev, w.partial, out);
+    return cudaGetLastError();
+}
+
+// Pairs in cut order: for splat m, one (global tile id, m) pair per covered tile (row-major).
+__global__ void __launch_bounds__(256) duplicate_plain_kernel(const DevCam* __restrict__ cams, int n_cams,
+                                                              const int64_t* __restrict__ cut_offsets, SplatBufs sb,
+                                                              const uint32_t* __restrict__ pair_off,
+                                                              const uint32_t* __restrict__ n_pairs, int64_t cap_pairs,
+                                                              uint32_t* __restrict__ n_pairs_kept,
+                                                              uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                              uint32_t* __restrict__ flags) {
+    const uint32_t M = *sb.n_splats;
+    const uint32_t P = *n_pairs;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if ((int64_t)P > cap_pairs) atomicOr(flags, FLAG_PAIRS_OVERFLOW);
+        *n_pairs_kept = (int64_t)P > cap_pairs ? (uint32_t)cap_pairs : P;
+    }
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        const uint32_t nt = sb.tiles[m];
+        if (nt == 0) continue;
+        const uint2 r = sb.rect[m];
+        const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+        const int k = find_cam(cut_offsets, n_cams, m);
+        const int64_t tb = cams[k].tile_base;
+        const int TX = cams[k].tiles_x;
+        int64_t off = pair_off[m];
+        for (int y = y0; y <= y1; ++y)
+            for (int x = x0; x <= x1; ++x, ++off) {
+                if (off < cap_pairs) {
+                    keys[off] = (uint32_t)(tb + (int64_t)y * TX + x);
+                    vals[off] = m;
+                }
+            }
+    }
+}
+
+cudaError_t launch_duplicate_plain(const DevCam* cams, int n_cams, const int64_t* cut_offsets, const SplatBufs& sb,
+                                   const uint32_t* pair_off, const uint32_t* n_pairs, int64_t cap_pairs,
+                                   uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* flags, int grid,
+                                   cudaStream_t s) {
+    duplicate_plain_kernel<<<grid, 256, 0, s>>>(cams, n_cams, cut_offsets, sb, pair_off, n_pairs, cap_pairs, n_pairs_kept,
+                                                keys, vals, flags);
     return cudaGetLastError();
 }
 

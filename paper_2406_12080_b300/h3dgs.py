@@ -53,13 +53,14 @@ class h3dgs_grads(C.Structure):
 class h3dgs_render_opts(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("lowpass", C.c_float),
                 ("alpha_clamp", C.c_float), ("alpha_floor", C.c_float), ("t_min", C.c_float),
-                ("aa_compensate", C.c_int32), ("interpolate", C.c_int32), ("bg", C.c_float * 3)]
+                ("aa_compensate", C.c_int32), ("interpolate", C.c_int32), ("bg", C.c_float * 3),
+                ("blend_chunk", C.c_int32)]
 
 
 class h3dgs_stats(C.Structure):
     _fields_ = [("n_cut", C.c_int64), ("n_visible", C.c_int64), ("n_pairs", C.c_int64),
                 ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("device_flags", C.c_uint32),
-                ("n_evals", C.c_int64)]
+                ("n_evals", C.c_int64), ("n_evals_tpass", C.c_int64), ("n_items", C.c_int64)]
 
 
 STAGES = ["cut", "preprocess", "depth_sort", "duplicate", "tile_sort", "ranges", "blend", "backward_blend",

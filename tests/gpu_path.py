@@ -40,19 +40,20 @@ def upload(hier):
     return dh
 
 
-def opts_from(o) -> h3dgs.h3dgs_render_opts:
-    """Library options equal to the oracle's Opts `o`."""
+def opts_from(o, chunk=None) -> h3dgs.h3dgs_render_opts:
+    """Library options equal to the oracle's Opts `o` (plus the blend chunk, which the oracle lacks)."""
+    kw = {} if chunk is None else {"blend_chunk": chunk}
     return h3dgs.default_opts(tile_w=o.tile_w, tile_h=o.tile_h, lowpass=o.lowpass, alpha_clamp=o.alpha_clamp,
                               alpha_floor=o.alpha_floor, t_min=o.t_min, aa_compensate=o.aa_compensate,
-                              interpolate=o.interpolate, bg=o.bg)
+                              interpolate=o.interpolate, bg=o.bg, **kw)
 
 
-def run(hier_dev, cams, oopts, debug=True, capacity=None) -> GpuFrame:
+def run(hier_dev, cams, oopts, debug=True, capacity=None, chunk=None) -> GpuFrame:
     import torch
     ctx = context()
     cut = ctx.select_cut(cams, capacity)
     ids, t, offs = cut
-    opts = opts_from(oopts)
+    opts = opts_from(oopts, chunk)
     images = ctx.render(cams, cut, opts, save_for_backward=1)
     torch.cuda.synchronize()
     fr = GpuFrame(ids.cpu().numpy(), t.cpu().numpy(), offs.cpu().numpy(),

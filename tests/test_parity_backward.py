@@ -26,9 +26,9 @@ def _cuda():
     build.build()
 
 
-def _gpu_grads(dh, cam, opts, w, freeze=0):
+def _gpu_grads(dh, cam, opts, w, freeze=0, chunk=None):
     import torch
-    fr = gpu_path.run(dh, [cam], opts, debug=False)   # keeps the cut buffers alive: the backward re-reads them
+    fr = gpu_path.run(dh, [cam], opts, debug=False, chunk=chunk)  # keeps the cut buffers alive (re-read by the backward)
     grads = {k: torch.zeros_like(getattr(dh, k)) for k in ("mean", "scale", "rot", "opacity", "sh")}
     dl = torch.from_numpy(np.ascontiguousarray(w, np.float32).reshape(-1)).cuda()
     h3dgs.h3dgs_render_backward(gpu_path.context().ctx, dl, grads, freeze)
@@ -72,8 +72,8 @@ def test_backward_small_interpolated_scene(freeze):
         assert np.all(gg[h.child_count == 0] == 0)
 
 
-@pytest.mark.parametrize("tau", [0.0, 6.0, 30.0])
-def test_backward_tiny_scene(tau):
+@pytest.mark.parametrize("tau,chunk", [(0.0, None), (6.0, None), (30.0, None), (2.0, 64), (6.0, 100)])
+def test_backward_tiny_scene(tau, chunk):
     sc, h = scenes.tiny()
     cam = synth.with_tau(sc.cameras[0], tau)
     opts = oracle.Opts()
@@ -81,7 +81,7 @@ def test_backward_tiny_scene(tau):
     fr = oracle.render(cam, h, opts)
     w = np.random.default_rng(1).normal(size=fr.image.shape)
     og = oracle.backward(cam, h, fr, w, opts)
-    gg = _gpu_grads(dh, cam, opts, w)
+    gg = _gpu_grads(dh, cam, opts, w, chunk=chunk)
     _check(gg, og)
 
 

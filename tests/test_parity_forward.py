@@ -27,9 +27,9 @@ def _cuda():
     build.build()
 
 
-def _compare(cam, h, dh, opts, cams_index=0, full_rec=True):
+def _compare(cam, h, dh, opts, cams_index=0, chunk=None):
     ofr = oracle.render(cam, h, opts)
-    g = gpu_path.run(dh, [cam], opts)
+    g = gpu_path.run(dh, [cam], opts, chunk=chunk)
     # a1/a2: cut ids and weights bit-exact
     np.testing.assert_array_equal(g.cut_ids, ofr.ids)
     np.testing.assert_array_equal(g.cut_t.view(np.uint32), ofr.t.view(np.uint32))
@@ -144,10 +144,21 @@ def test_interpolate_export_bit_exact():
     np.testing.assert_allclose(out.cpu().numpy(), o64, atol=1e-6, rtol=1e-6)
 
 
-@pytest.mark.parametrize("tau", [0.0, 3.0, 6.0, 15.0])
-def test_street_corridor_full_size(tau):
+@pytest.mark.parametrize("chunk", [64, 100, 150])
+def test_split_tiles_small_chunks(chunk):
+    """Tile lists longer than the blend chunk are blended by several CTAs and recombined."""
+    sc, h = scenes.tiny()
+    dh = gpu_path.upload(h)
+    ofr, g = _compare(synth.with_tau(sc.cameras[0], 2.0), h, dh, oracle.Opts(), chunk=chunk)
+    lengths = ofr.ranges[:, 1] - ofr.ranges[:, 0]
+    expected_items = int(np.sum(np.where(lengths <= chunk, 1, (lengths + chunk - 1) // chunk)))
+    assert g.stats["n_items"] == expected_items
+
+
+@pytest.mark.parametrize("tau,chunk", [(0.0, None), (3.0, None), (6.0, None), (15.0, None), (6.0, 64), (6.0, 4096)])
+def test_street_corridor_full_size(tau, chunk):
     """1M leaves (2M nodes) at 1920x1080: the workload the benchmark times."""
     sc, h = scenes.corridor()
     dh = gpu_path.upload(h)
     cam = synth.with_tau(sc.cameras[0], tau)
-    _compare(cam, h, dh, oracle.Opts())
+    _compare(cam, h, dh, oracle.Opts(), chunk=chunk)
