@@ -53,7 +53,7 @@ struct h3dgs_ctx {
     DBuf rec, cams, counters;
     DBuf cut_mask, cut_bc, cut_tot;
     DBuf s_rec, s_rect, s_key, s_idx, s_key2, s_idx2, s_tiles, s_poff;
-    DBuf pk0, pv0, pk1, pv1, ranges, sort_scratch;
+    DBuf pk0, pv0, pk1, pv1, ranges, sort_scratch, tile_work;
     DBuf hist, dtot, partial;
     DBuf T_final, n_contrib, splat_grad;
     DBuf items, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last;
@@ -271,7 +271,7 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     DBuf* bufs[] = {&ctx->rec, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot,
                     &ctx->s_rec, &ctx->s_rect, &ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2,
-                    &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1, &ctx->ranges, &ctx->sort_scratch,
+                    &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1, &ctx->ranges, &ctx->sort_scratch, &ctx->tile_work,
                     &ctx->hist, &ctx->dtot, &ctx->partial, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
                     &ctx->items, &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
                     &ctx->sc_last};
@@ -310,7 +310,7 @@ h3dgs_status h3dgs_reserve(h3dgs_ctx* ctx, int64_t max_splats, int64_t max_pairs
         return H3DGS_OK;
     }
     const size_t M = (size_t)max_splats, Pn = (size_t)max_pairs;
-    CK(ensure(ctx->s_rec, 48 * M), "splat buffer");
+    CK(ensure(ctx->s_rec, 16 * SPLAT_F4 * M), "splat buffer");
     CK(ensure(ctx->s_rect, 8 * M), "splat buffer");
     DBuf* m4[] = {&ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2, &ctx->s_tiles, &ctx->s_poff};
     for (DBuf* b : m4) CK(ensure(*b, 4 * M), "splat buffer");
@@ -453,7 +453,7 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
         if (m < 0 || m > 0x7fffffffLL) return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: bad cut size");
         capM = std::max<int64_t>(m, 1);
         const size_t M = (size_t)capM;
-        CK(ensure(ctx->s_rec, 48 * M), "splat buffer");
+        CK(ensure(ctx->s_rec, 16 * SPLAT_F4 * M), "splat buffer");
         CK(ensure(ctx->s_rect, 8 * M), "splat buffer");
         DBuf* m4[] = {&ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2, &ctx->s_tiles, &ctx->s_poff};
         for (DBuf* b : m4) CK(ensure(*b, 4 * M), "splat buffer");
@@ -510,8 +510,10 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
     CK(launch_ranges(keys, cnt + C_NPAIRS_KEPT, P<int2>(ctx->ranges), grid, s), "ranges");
     stage_end(ctx, H3DGS_STAGE_RANGES);
     stage_begin(ctx, H3DGS_STAGE_DEPTH_SORT);
+    CK(ensure(ctx->tile_work, sizeof(uint32_t) * (size_t)(2 * ctx->n_tiles + 2)), "tile sort work");
     CK(launch_tile_depth_sort(P<int2>(ctx->ranges), ctx->n_tiles, P<uint32_t>(ctx->s_key), list,
-                              P<unsigned long long>(ctx->sort_scratch), 2 * capP, s),
+                              P<uint32_t>(ctx->tile_work), P<unsigned long long>(ctx->sort_scratch), 2 * capP,
+                              ctx->num_sms, s),
        "tile depth sort");
     stage_end(ctx, H3DGS_STAGE_DEPTH_SORT);
     stage_begin(ctx, H3DGS_STAGE_BLEND);
@@ -658,11 +660,11 @@ h3dgs_status h3dgs_debug_splats(h3dgs_ctx* ctx, float* rec, int32_t* rect, float
     if (m < 0 || m > ctx->splat_cap_used) return fail(ctx, H3DGS_ERR_INVALID_ARG, "debug: m out of range");
     CK(cudaSetDevice(ctx->device), "set device");
     cudaStream_t s = ctx->stream;
-    std::vector<float4> r(3 * std::max<int64_t>(m, 1));
+    std::vector<float4> r(SPLAT_F4 * std::max<int64_t>(m, 1));
     std::vector<uint2> rc(std::max<int64_t>(m, 1));
     std::vector<uint32_t> key(std::max<int64_t>(m, 1));
     if (m > 0) {
-        CK(cudaMemcpyAsync(r.data(), ctx->s_rec.p, 48 * m, cudaMemcpyDeviceToHost, s), "read splats");
+        CK(cudaMemcpyAsync(r.data(), ctx->s_rec.p, 16 * SPLAT_F4 * m, cudaMemcpyDeviceToHost, s), "read splats");
         CK(cudaMemcpyAsync(rc.data(), ctx->s_rect.p, 8 * m, cudaMemcpyDeviceToHost, s), "read rects");
         CK(cudaMemcpyAsync(key.data(), ctx->s_key.p, 4 * m, cudaMemcpyDeviceToHost, s), "read depth");
     }
@@ -671,7 +673,7 @@ h3dgs_status h3dgs_debug_splats(h3dgs_ctx* ctx, float* rec, int32_t* rect, float
     for (int64_t i = 0; i < m; ++i) std::memcpy(&depth[i], &key[i], 4);
     for (int64_t i = 0; i < m; ++i) {
         const bool culled = rc[i].x == 0xffffffffu;
-        const float4 a = r[3 * i], b = r[3 * i + 1], c = r[3 * i + 2];
+        const float4 a = r[SPLAT_F4 * i], b = r[SPLAT_F4 * i + 1], c = r[SPLAT_F4 * i + 2];
         if (rec) {
             float* o = rec + 10 * i;
             if (culled) { for (int k = 0; k < 10; ++k) o[k] = 0.0f; }

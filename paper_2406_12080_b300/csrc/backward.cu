@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
                                                                  float* __restrict__ sgrad) {
     constexpr int NT = TW * TH;
     __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
-    __shared__ uint32_t s_id[NT];
+    __shared__ uint32_t s_id[NT], s_m[NT];
     __shared__ int s_max;
     const uint32_t item = blockIdx.x;
     if (item >= *n_items) return;
@@ -96,10 +96,13 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
     }
     const DevCam& cam = cams[lo];
     const int local = (int)(tile - cam.tile_base);
-    const int tx = local % cam.tiles_x, ty = local / cam.tiles_x;
-    const int px_i = tx * TW + (threadIdx.x % TW), py_i = ty * TH + (threadIdx.x / TW);
+    const int ox = (local % cam.tiles_x) * TW, oy = (local / cam.tiles_x) * TH;
+    int lx, ly;
+    tile_pixel<TW, TH>(threadIdx.x, lx, ly);
+    const int px_i = ox + lx, py_i = oy + ly;
     const bool inside = px_i < cam.width && py_i < cam.height;
     const float px = (float)px_i + 0.5f, py = (float)py_i + 0.5f;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 r = ranges[tile];
     const int begin = r.x + it.y * chunk;     // first list entry of this item
     float T = 1.0f, g0 = 0, g1 = 0, g2 = 0, S0 = 0, S1 = 0, S2 = 0;
@@ -139,13 +142,23 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
         __syncthreads();
         if ((int)threadIdx.x < n) {
             const uint32_t s = __ldg(list + begin + first + threadIdx.x);
+            const float4 a = __ldg(splat + SPLAT_F4 * (int64_t)s);
+            const float4 d = __ldg(splat + SPLAT_F4 * (int64_t)s + 3);
             s_id[threadIdx.x] = s;
-            s_a[threadIdx.x] = __ldg(splat + 3 * (int64_t)s);
-            s_b[threadIdx.x] = __ldg(splat + 3 * (int64_t)s + 1);
-            s_c[threadIdx.x] = __ldg(splat + 3 * (int64_t)s + 2);
+            s_a[threadIdx.x] = a;
+            s_b[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
+            s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
+            s_m[threadIdx.x] = warp_mask<TW, TH>(a.x, a.y, d.x, d.y, ox, oy);
         }
         __syncthreads();
-        for (int j = n - 1; j >= 0; --j) {
+        // back to front over the splats whose alpha-floor box reaches this warp's pixels
+        for (int base = ((n - 1) >> 5) << 5; base >= 0; base -= 32) {
+          const uint32_t mm = (base + lane < n) ? s_m[base + lane] : 0u;
+          uint32_t bits = __ballot_sync(0xffffffffu, (mm >> warp) & 1u);
+          while (bits) {
+            const int hb = 31 - __clz(bits);
+            bits &= ~(1u << hb);
+            const int j = base + hb;
             const int pos = first + j;
             float gu = 0, gv = 0, gca = 0, gcb = 0, gcc = 0, gon = 0, gop = 0, gr = 0, gg = 0, gb = 0;
             bool contrib = false;
@@ -198,6 +211,7 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
                     atomicAdd(d + 8, gg); atomicAdd(d + 9, gb);
                 }
             }
+          }
         }
     }
 }

@@ -54,25 +54,31 @@ __device__ __forceinline__ float pair_alpha(float px, float py, const float4 a, 
     return ffma(b.w, alpha_prime(ap, Kc), fmul(fsub(1.0f, b.w), an));
 }
 
+template <int TW, int TH>
 struct TileGeom {
-    int px_i, py_i;
+    int px_i, py_i;   // this thread's pixel
+    int ox, oy;       // tile's pixel origin
     bool inside;
     float px, py;
     const DevCam* cam;
 };
 
-__device__ __forceinline__ TileGeom tile_geom(const DevCam* __restrict__ cams, int n_cams, int64_t tile, int TW, int TH) {
+template <int TW, int TH>
+__device__ __forceinline__ TileGeom<TW, TH> tile_geom(const DevCam* __restrict__ cams, int n_cams, int64_t tile) {
     int lo = 0, hi = n_cams - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (cams[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
     }
-    TileGeom g;
+    TileGeom<TW, TH> g;
     g.cam = cams + lo;
     const int local = (int)(tile - g.cam->tile_base);
-    const int tx = local % g.cam->tiles_x, ty = local / g.cam->tiles_x;
-    g.px_i = tx * TW + (threadIdx.x % TW);
-    g.py_i = ty * TH + (threadIdx.x / TW);
+    g.ox = (local % g.cam->tiles_x) * TW;
+    g.oy = (local / g.cam->tiles_x) * TH;
+    int lx, ly;
+    tile_pixel<TW, TH>(threadIdx.x, lx, ly);
+    g.px_i = g.ox + lx;
+    g.py_i = g.oy + ly;
     g.inside = g.px_i < g.cam->width && g.py_i < g.cam->height;
     g.px = (float)g.px_i + 0.5f;
     g.py = (float)g.py_i + 0.5f;
@@ -139,19 +145,22 @@ __global__ void __launch_bounds__(TW * TH) blend_items_kernel(const DevCam* __re
                                                               unsigned long long* __restrict__ n_evals) {
     constexpr int NT = TW * TH;
     __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
+    __shared__ uint32_t s_m[NT];
     __shared__ unsigned int s_evals;
     const uint32_t item = blockIdx.x;
     if (item >= *n_items) return;
     const int2 it = items[item];
     const int64_t tile = it.x;
     const int nch = tile_nch[tile];
-    if (!MAIN && nch == 1) return;                      // pass T only for split tiles
+    // pass T only for split tiles, and not for their last chunk (nobody reads its product)
+    if (!MAIN && (nch == 1 || it.y == nch - 1)) return;
     if (threadIdx.x == 0) s_evals = 0;
-    const TileGeom g = tile_geom(cams, n_cams, tile, TW, TH);
+    const TileGeom<TW, TH> g = tile_geom<TW, TH>(cams, n_cams, tile);
     const int2 r = ranges[tile];
     const int begin = r.x + it.y * chunk;
     const int end = nch == 1 ? r.y : min(r.y, begin + chunk);
     const int64_t slot = (int64_t)item * NT + threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float clampv = o.alpha_clamp, afloor = o.alpha_floor, tmin = o.t_min;
     float T = 1.0f;
     if (MAIN && nch > 1) {
@@ -168,35 +177,46 @@ __global__ void __launch_bounds__(TW * TH) blend_items_kernel(const DevCam* __re
         const int n = min(NT, end - b0);
         if ((int)threadIdx.x < n) {
             const uint32_t s = __ldg(list + b0 + threadIdx.x);
-            s_a[threadIdx.x] = __ldg(splat + 3 * (int64_t)s);
-            s_b[threadIdx.x] = __ldg(splat + 3 * (int64_t)s + 1);
-            s_c[threadIdx.x] = __ldg(splat + 3 * (int64_t)s + 2);
+            const float4 a = __ldg(splat + SPLAT_F4 * (int64_t)s);
+            const float4 d = __ldg(splat + SPLAT_F4 * (int64_t)s + 3);
+            s_a[threadIdx.x] = a;
+            s_b[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
+            s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
+            s_m[threadIdx.x] = warp_mask<TW, TH>(a.x, a.y, d.x, d.y, g.ox, g.oy);
         }
         __syncthreads();
-        if (!done) {
-            for (int j = 0; j < n; ++j) {
-                ++evals;
-                const float alpha = pair_alpha(g.px, g.py, s_a[j], s_b[j], s_c[j].w, clampv);
-                if (alpha < afloor) continue;
-                const float Tn = fmul(T, fsub(1.0f, alpha));
-                if (!MAIN) {                            // pass T: no stop, but nothing matters below t_min
+        if (__any_sync(0xffffffffu, !done)) {
+            for (int base = 0; base < n; base += 32) {
+                const uint32_t mm = (base + lane < n) ? s_m[base + lane] : 0u;
+                uint32_t bits = __ballot_sync(0xffffffffu, (mm >> warp) & 1u);
+                while (bits) {
+                    const int j = base + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (done) continue;
+                    ++evals;
+                    const float alpha = pair_alpha(g.px, g.py, s_a[j], s_b[j], s_c[j].w, clampv);
+                    if (alpha < afloor) continue;
+                    const float Tn = fmul(T, fsub(1.0f, alpha));
+                    if (!MAIN) {                            // pass T: no stop, but nothing matters below t_min
+                        T = Tn;
+                        if (T < tmin) done = true;
+                        continue;
+                    }
+                    if (Tn < tmin) { done = true; continue; }
+                    const float w = alpha * T;
+                    const float4 c = s_c[j];
+                    C0 = fmaf(c.x, w, C0);
+                    C1 = fmaf(c.y, w, C1);
+                    C2 = fmaf(c.z, w, C2);
                     T = Tn;
-                    if (T < tmin) { done = true; break; }
-                    continue;
+                    last = b0 + j + 1 - r.x;
                 }
-                if (Tn < tmin) { done = true; break; }
-                const float w = alpha * T;
-                const float4 c = s_c[j];
-                C0 = fmaf(c.x, w, C0);
-                C1 = fmaf(c.y, w, C1);
-                C2 = fmaf(c.z, w, C2);
-                T = Tn;
-                last = b0 + j + 1 - r.x;
+                if (__all_sync(0xffffffffu, done)) break;
             }
         }
     }
     for (int off = 16; off > 0; off >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&s_evals, evals);
+    if (lane == 0) atomicAdd(&s_evals, evals);
     __syncthreads();
     if (threadIdx.x == 0 && n_evals) atomicAdd(n_evals, (unsigned long long)s_evals);
     if (!MAIN) {
@@ -237,7 +257,7 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
     if (tile >= n_tiles) return;
     const int nch = tile_nch[tile];
     if (nch == 1) return;
-    const TileGeom g = tile_geom(cams, n_cams, tile, TW, TH);
+    const TileGeom<TW, TH> g = tile_geom<TW, TH>(cams, n_cams, tile);
     if (!g.inside) return;
     const int64_t i0 = tile_item0[tile];
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f, Tin = 1.0f;
@@ -251,7 +271,7 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
             T = sc.Tend[slot];
             if (sc.last[slot] >= 0) last = sc.last[slot];
         }
-        Tin = fmul(Tin, sc.Tc[slot]);
+        if (c + 1 < nch) Tin = fmul(Tin, sc.Tc[slot]);
     }
     const DevCam& cam = *g.cam;
     const int64_t pix = cam.pix_base + (int64_t)g.py_i * cam.width + g.px_i;

@@ -95,6 +95,34 @@ __device__ __forceinline__ float parent_weight(float tau, float en, float ep) {
     return fminf(fmaxf(t, 0.0f), 1.0f);
 }
 
+// Pixel of thread `tid` inside a TW x TH tile: each warp owns an 8 x 4 block of pixels, so a warp
+// can skip every splat whose alpha-floor box misses its block.
+template <int TW, int TH>
+__device__ __forceinline__ void tile_pixel(int tid, int& lx, int& ly) {
+    constexpr int WX = TW / 8;
+    const int w = tid >> 5, l = tid & 31;
+    lx = (w % WX) * 8 + (l & 7);
+    ly = (w / WX) * 4 + (l >> 3);
+}
+
+// Bit w set iff the splat's alpha-floor box [u +- hx] x [v +- hy] reaches a pixel centre of warp w's
+// block in the tile with pixel origin (ox, oy).  Outside the box alpha < alpha_floor for every
+// pixel (the box is the inflated bounding box of the level set o_max G = alpha_floor), so a warp
+// whose bit is clear would skip the splat anyway.  hx < 0 marks a splat that never reaches the floor.
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t warp_mask(float u, float v, float hx, float hy, int ox, int oy) {
+    if (!(hx >= 0.0f)) return 0u;
+    constexpr int NW = TW * TH / 32, WX = TW / 8;
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const float x0 = (float)(ox + (w % WX) * 8) + 0.5f, x1 = x0 + 7.0f;
+        const float y0 = (float)(oy + (w / WX) * 4) + 0.5f, y1 = y0 + 3.0f;
+        if (u + hx >= x0 && u - hx <= x1 && v + hy >= y0 && v - hy <= y1) m |= 1u << w;
+    }
+    return m;
+}
+
 // Camera index of global entry m given the per-camera offsets (binary search, n_cams small).
 __device__ __forceinline__ int find_cam(const int64_t* __restrict__ offs, int n_cams, int64_t m) {
     int lo = 0, hi = n_cams - 1;
@@ -121,8 +149,9 @@ cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const C
                        float* cut_t, int64_t* cut_offsets, int64_t capacity, uint32_t* flags, cudaStream_t s);
 
 // preprocess.cu
+constexpr int SPLAT_F4 = 4;      // float4 per splat record
 struct SplatBufs {
-    float4* rec;           // [cap][3]: {u, v, ca, cb}, {cc, on', op', t}, {r, g, b, K}
+    float4* rec;           // [cap][4]: {u, v, ca, cb}, {cc, on', op', t}, {r, g, b, K}, {hx, hy, 0, 0}
     uint2* rect;           // [cap]: (x0 | x1 << 16, y0 | y1 << 16)
     uint32_t* depth_key;   // [cap] fp32 depth bits, 0xffffffff when culled
     uint32_t* tiles;       // [cap] tiles touched (0 when culled)
@@ -165,9 +194,11 @@ cudaError_t launch_duplicate_plain(const DevCam* cams, int n_cams, const int64_t
                                    const uint32_t* pair_off, const uint32_t* n_pairs, int64_t cap_pairs,
                                    uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* flags, int grid,
                                    cudaStream_t s);
-// Orders every tile's list by (depth key, cut position); scratch: 64-bit, >= 2 * pairs entries.
+// Orders every tile's list by (depth key, cut position).  work: 2 n_tiles + 2 words; scratch:
+// 64-bit, >= 2 * pairs entries (only lists longer than 16384 entries use it).
 cudaError_t launch_tile_depth_sort(const int2* ranges, int64_t n_tiles, const uint32_t* depth_key, uint32_t* list,
-                                   unsigned long long* scratch, int64_t scratch_cap, cudaStream_t s);
+                                   uint32_t* work, unsigned long long* scratch, int64_t scratch_cap, int num_sms,
+                                   cudaStream_t s);
 
 // blend.cu
 // Everything the chunked blend and its adjoint share.  Items are (tile, chunk) pairs; tiles with at

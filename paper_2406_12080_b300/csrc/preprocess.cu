@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
         }
         const float z = xc[2];
         bool vis = z > cam.znear;
-        float u = 0, v = 0, ca = 0, cb = 0, cc = 0, comp = 0;
+        float u = 0, v = 0, ca = 0, cb = 0, cc = 0, comp = 0, sxx = 0, syy = 0;
         int rx0 = 0, rx1 = -1, ry0 = 0, ry1 = -1;
         if (vis) {
             const float xz = fdiv(xc[0], z), yz = fdiv(xc[1], z);
@@ -179,6 +179,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
             const float af = fadd(ca2, lp), cf = fadd(cc2, lp);
             const float detf = ffma(lp, fadd(fadd(ca2, cc2), lp), det);
             vis = detf > 0.0f;
+            sxx = af;
+            syy = cf;
             if (vis) {
                 comp = o.aa_compensate ? fsqrt(fmaxf(0.0f, fdiv(det, detf))) : 1.0f;
                 ca = fmul(fdiv(cf, detf), KH);
@@ -238,9 +240,20 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
         const float on = fmul(__ldg(h.opacity + n), comp);
         const float op = use_p ? fmul(__ldg(h.opacity + p), comp) : 0.0f;
         const float K = use_p ? (float)__ldg(h.child_count + p) : 1.0f;
-        sb.rec[3 * m + 0] = make_float4(u, v, ca, cb);
-        sb.rec[3 * m + 1] = make_float4(cc, on, op, t);
-        sb.rec[3 * m + 2] = make_float4(fmaxf(rgb[0], 0.0f), fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), K);
+        // alpha-floor box: alpha <= o_max G, and o_max G >= floor only inside the ellipse
+        // d^T Sigma'_f^-1 d <= 2 ln(o_max / floor), whose bounding box has half-widths
+        // sqrt(2 ln(o_max / floor) Sigma'_f,xx) and likewise in y; inflated by 1% + 0.01 px
+        const float omax = fmaxf(on, op);
+        float hx = -1.0f, hy = -1.0f;
+        if (omax > o.alpha_floor) {
+            const float r2 = 2.0f * logf(omax / o.alpha_floor);
+            hx = sqrtf(r2 * sxx) * 1.01f + 0.01f;
+            hy = sqrtf(r2 * syy) * 1.01f + 0.01f;
+        }
+        sb.rec[SPLAT_F4 * m + 0] = make_float4(u, v, ca, cb);
+        sb.rec[SPLAT_F4 * m + 1] = make_float4(cc, on, op, t);
+        sb.rec[SPLAT_F4 * m + 2] = make_float4(fmaxf(rgb[0], 0.0f), fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), K);
+        sb.rec[SPLAT_F4 * m + 3] = make_float4(hx, hy, 0.0f, 0.0f);
         sb.rect[m] = make_uint2((uint32_t)rx0 | ((uint32_t)rx1 << 16), (uint32_t)ry0 | ((uint32_t)ry1 << 16));
         sb.depth_key[m] = __float_as_uint(z);
         sb.tiles[m] = (uint32_t)((rx1 - rx0 + 1) * (ry1 - ry0 + 1));

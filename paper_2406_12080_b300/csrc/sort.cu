@@ -383,6 +383,7 @@ constexpr int SORT_SMALL = 2048;
 constexpr int SORT_LARGE = 16384;
 
 __device__ __forceinline__ void bitonic_smem(unsigned long long* s, int N) {
+    // N is a power of two <= the block's key capacity; ends with a barrier
     for (int k = 2; k <= N; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int p = threadIdx.x; p < (N >> 1); p += blockDim.x) {
@@ -396,15 +397,10 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long* s, int N) {
         }
 }
 
-template <int CAP>
-__global__ void tile_depth_sort_kernel(const int2* __restrict__ ranges, int64_t n_tiles, const uint32_t* __restrict__ depth_key,
-                                       uint32_t* __restrict__ list, int lo_exclusive) {
-    extern __shared__ unsigned long long s_key[];
-    const int64_t tile = blockIdx.x;
-    if (tile >= n_tiles) return;
-    const int2 r = ranges[tile];
+// Sorts one tile's list [r.x, r.y) in shared memory (n <= CAP entries).
+__device__ __forceinline__ void sort_tile_smem(unsigned long long* s_key, int2 r, const uint32_t* __restrict__ depth_key,
+                                               uint32_t* __restrict__ list) {
     const int n = r.y - r.x;
-    if (n <= lo_exclusive || n > CAP || n < 2) return;
     int N = 1;
     while (N < n) N <<= 1;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -418,63 +414,106 @@ __global__ void tile_depth_sort_kernel(const int2* __restrict__ ranges, int64_t 
     __syncthreads();
     bitonic_smem(s_key, N);
     for (int i = threadIdx.x; i < n; i += blockDim.x) list[r.x + i] = (uint32_t)(s_key[i] & 0xffffffffu);
+    __syncthreads();
 }
 
-// lists longer than SORT_LARGE: the same network over a global scratch (rare; one CTA per tile)
-__global__ void __launch_bounds__(1024) tile_depth_sort_global_kernel(const int2* __restrict__ ranges, int64_t n_tiles,
-                                                                      const uint32_t* __restrict__ depth_key,
-                                                                      uint32_t* __restrict__ list,
-                                                                      unsigned long long* __restrict__ scratch,
-                                                                      int64_t scratch_cap) {
+// lists of 2 .. SORT_SMALL entries: one CTA per tile; longer lists are appended to the large/huge
+// work lists for the persistent kernels below
+__global__ void __launch_bounds__(256) tile_sort_small_kernel(const int2* __restrict__ ranges, int64_t n_tiles,
+                                                              const uint32_t* __restrict__ depth_key,
+                                                              uint32_t* __restrict__ list, uint32_t* __restrict__ large,
+                                                              uint32_t* __restrict__ n_large, uint32_t* __restrict__ huge,
+                                                              uint32_t* __restrict__ n_huge) {
+    __shared__ unsigned long long s_key[SORT_SMALL];
     const int64_t tile = blockIdx.x;
     if (tile >= n_tiles) return;
     const int2 r = ranges[tile];
     const int n = r.y - r.x;
-    if (n <= SORT_LARGE) return;
-    int N = 1;
-    while (N < n) N <<= 1;
-    // the tile's padded segment lives at [2 r.x, 2 r.x + N) of the scratch (room for pad: N < 2n)
-    const int64_t base = 2 * (int64_t)r.x;
-    if (base + N > scratch_cap) return;
-    unsigned long long* s = scratch + base;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        if (i < n) {
-            const uint32_t m = list[r.x + i];
-            s[i] = ((unsigned long long)__ldg(depth_key + m) << 32) | m;
-        } else {
-            s[i] = ~0ull;
+    if (n < 2) return;
+    if (n > SORT_SMALL) {
+        if (threadIdx.x == 0) {
+            if (n > SORT_LARGE) huge[atomicAdd(n_huge, 1u)] = (uint32_t)tile;
+            else large[atomicAdd(n_large, 1u)] = (uint32_t)tile;
         }
+        return;
     }
-    __syncthreads();
-    for (int k = 2; k <= N; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int p = threadIdx.x; p < (N >> 1); p += blockDim.x) {
-                const int pos = 2 * j * (p / j) + (p % j);
-                const int q = pos + j;
-                const bool up = (pos & k) == 0;
-                const unsigned long long a = s[pos], b = s[q];
-                if ((a > b) == up) { s[pos] = b; s[q] = a; }
+    sort_tile_smem(s_key, r, depth_key, list);
+}
+
+// lists of SORT_SMALL .. SORT_LARGE entries: persistent CTAs of 1024 threads with 128 KB of keys
+__global__ void __launch_bounds__(1024) tile_sort_large_kernel(const int2* __restrict__ ranges,
+                                                               const uint32_t* __restrict__ depth_key,
+                                                               uint32_t* __restrict__ list,
+                                                               const uint32_t* __restrict__ large,
+                                                               const uint32_t* __restrict__ n_large) {
+    extern __shared__ unsigned long long s_key[];
+    const uint32_t cnt = *n_large;
+    for (uint32_t i = blockIdx.x; i < cnt; i += gridDim.x) sort_tile_smem(s_key, ranges[large[i]], depth_key, list);
+}
+
+// lists longer than SORT_LARGE: the same network over a global 64-bit scratch (rare)
+__global__ void __launch_bounds__(1024) tile_sort_huge_kernel(const int2* __restrict__ ranges,
+                                                              const uint32_t* __restrict__ depth_key,
+                                                              uint32_t* __restrict__ list,
+                                                              const uint32_t* __restrict__ huge,
+                                                              const uint32_t* __restrict__ n_huge,
+                                                              unsigned long long* __restrict__ scratch,
+                                                              int64_t scratch_cap) {
+    const uint32_t cnt = *n_huge;
+    for (uint32_t ti = blockIdx.x; ti < cnt; ti += gridDim.x) {
+        const int2 r = ranges[huge[ti]];
+        const int n = r.y - r.x;
+        int N = 1;
+        while (N < n) N <<= 1;
+        // the tile's padded segment lives at [2 r.x, 2 r.x + N) of the scratch (N < 2n: disjoint)
+        const int64_t base = 2 * (int64_t)r.x;
+        if (base + N > scratch_cap) continue;
+        unsigned long long* s = scratch + base;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            if (i < n) {
+                const uint32_t m = list[r.x + i];
+                s[i] = ((unsigned long long)__ldg(depth_key + m) << 32) | m;
+            } else {
+                s[i] = ~0ull;
             }
-            __threadfence_block();
-            __syncthreads();
         }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) list[r.x + i] = (uint32_t)(s[i] & 0xffffffffu);
+        __syncthreads();
+        for (int k = 2; k <= N; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int p = threadIdx.x; p < (N >> 1); p += blockDim.x) {
+                    const int pos = 2 * j * (p / j) + (p % j);
+                    const int q = pos + j;
+                    const bool up = (pos & k) == 0;
+                    const unsigned long long a = s[pos], b = s[q];
+                    if ((a > b) == up) { s[pos] = b; s[q] = a; }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) list[r.x + i] = (uint32_t)(s[i] & 0xffffffffu);
+        __syncthreads();
+    }
 }
 
 cudaError_t launch_tile_depth_sort(const int2* ranges, int64_t n_tiles, const uint32_t* depth_key, uint32_t* list,
-                                   unsigned long long* scratch, int64_t scratch_cap, cudaStream_t s) {
+                                   uint32_t* work /*2 n_tiles + 2*/, unsigned long long* scratch, int64_t scratch_cap,
+                                   int num_sms, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tile_depth_sort_kernel<SORT_LARGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(tile_sort_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SORT_LARGE * 8);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const unsigned g = (unsigned)n_tiles;
-    tile_depth_sort_kernel<SORT_SMALL><<<g, 256, SORT_SMALL * 8, s>>>(ranges, n_tiles, depth_key, list, 0);
-    tile_depth_sort_kernel<SORT_LARGE><<<g, 1024, SORT_LARGE * 8, s>>>(ranges, n_tiles, depth_key, list, SORT_SMALL);
-    tile_depth_sort_global_kernel<<<g, 1024, 0, s>>>(ranges, n_tiles, depth_key, list, scratch, scratch_cap);
+    uint32_t* n_large = work;
+    uint32_t* n_huge = work + 1;
+    uint32_t* large = work + 2;
+    uint32_t* huge = work + 2 + n_tiles;
+    cudaError_t e = cudaMemsetAsync(work, 0, 2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    tile_sort_small_kernel<<<(unsigned)n_tiles, 256, 0, s>>>(ranges, n_tiles, depth_key, list, large, n_large, huge, n_huge);
+    tile_sort_large_kernel<<<num_sms, 1024, SORT_LARGE * 8, s>>>(ranges, depth_key, list, large, n_large);
+    tile_sort_huge_kernel<<<16, 1024, 0, s>>>(ranges, depth_key, list, huge, n_huge, scratch, scratch_cap);
     return cudaGetLastError();
 }
 

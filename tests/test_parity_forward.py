@@ -162,3 +162,24 @@ def test_street_corridor_full_size(tau, chunk):
     dh = gpu_path.upload(h)
     cam = synth.with_tau(sc.cameras[0], tau)
     _compare(cam, h, dh, oracle.Opts(), chunk=chunk)
+
+
+def test_one_tile_with_twenty_thousand_splats():
+    """A tile list longer than 16384 entries takes the global-scratch sort path and many blend chunks."""
+    rng = np.random.default_rng(21)
+    n, f = 20000, 100.0
+    z = rng.uniform(5.0, 50.0, n)
+    u = rng.uniform(18.0, 30.0, n)
+    v = rng.uniform(18.0, 30.0, n)
+    mean = np.stack([(u - 32.0) * z / f, (v - 32.0) * z / f, z], 1)
+    scale = (0.3 * z / f)[:, None] * np.exp(rng.normal(0, 0.2, (n, 3)))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    op = rng.uniform(0.02, 0.2, n)
+    lv = scenes.leaves_from(mean, scale, q, op, rng.normal(0, 0.3, (n, 48)))
+    h = oracle.build_tree(lv)
+    dh = gpu_path.upload(h)
+    cam = scenes.axis_camera(64, 64, f, tau=0.0)
+    ofr, g = _compare(cam, h, dh, oracle.Opts())
+    lengths = ofr.ranges[:, 1] - ofr.ranges[:, 0]
+    assert lengths.max() > 16384
