@@ -208,6 +208,28 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
                               int32_t* cut_ids, float* cut_t, int64_t* cut_offsets, int64_t capacity,
                               int64_t* total_out);
 
+/* Cut selection that allocates nothing (the paper has no counterpart; this is a deployment aid).
+ * For callers that cannot call cudaMalloc: code running under another framework's memory budget or
+ * allocator, real-time loops that must not enter the driver's allocator (it may synchronise the
+ * device), or processes whose device memory is partitioned up front.  Same rule and outputs as
+ * h3dgs_select_cut for ONE camera (cam: host pointer), but it needs no context: it reads the
+ * caller's box_min, box_max, parent and child_count arrays directly (other hierarchy fields are
+ * ignored) and keeps its scratch in a fixed device array of about 2 MB inside the library.
+ *   - hier->n_nodes must be at most H3DGS_NOALLOC_MAX_NODES; larger trees return
+ *     H3DGS_ERR_CAPACITY without launching anything.
+ *   - The first call on each device looks up the scratch array's device address; make that first
+ *     call before any CUDA stream capture on that device.
+ *   - All calls in the process share the scratch array: calls whose work overlaps on the GPU
+ *     (other streams or host threads) race and must be serialised by the caller.
+ *   - Work is issued on `cuda_stream` (cudaStream_t, NULL = legacy default stream) of the current
+ *     device.  cut_offsets is device int64[2]; with total_out non-NULL the call synchronises the
+ *     stream, stores the untruncated cut size and returns H3DGS_ERR_CAPACITY if it exceeds capacity.
+ * No cudaMalloc, cudaFree or other allocating call is made. */
+#define H3DGS_NOALLOC_MAX_NODES (1LL << 24)
+h3dgs_status h3dgs_select_cut_noalloc(const h3dgs_hierarchy* hier, const h3dgs_camera* cam, int32_t* cut_ids,
+                                      float* cut_t, int64_t* cut_offsets, int64_t capacity, int64_t* total_out,
+                                      void* cuda_stream);
+
 /* a3 -- export the interpolated attributes of every cut node (Sec. 4.2):
  *   a = (1 - t) a_n + t a_p  (fp32: fmaf(t, a_p, (1 - t) * a_n))  for mean, scale, rot (then
  *   normalised), sh;  the opacities o_n, o_p and the parent's child count K are kept separately.

@@ -88,6 +88,8 @@ def lib():
             "h3dgs_build_hierarchy": (i32, [vp, i64, vp, vp, vp, vp, vp, C.POINTER(h3dgs_node_arrays)]),
             "h3dgs_select_cut": (i32, [vp, C.POINTER(h3dgs_camera), i32, vp, vp, vp, i64, C.POINTER(i64)]),
             "h3dgs_interpolate": (i32, [vp, C.POINTER(h3dgs_camera), i32, vp, vp, vp, i32, vp, i64]),
+            "h3dgs_select_cut_noalloc": (i32, [C.POINTER(h3dgs_hierarchy), C.POINTER(h3dgs_camera), vp, vp, vp, i64,
+                                               C.POINTER(i64), vp]),
             "h3dgs_render": (i32, [vp, C.POINTER(h3dgs_camera), i32, vp, vp, vp, C.POINTER(h3dgs_render_opts), vp, i32]),
             "h3dgs_render_backward": (i32, [vp, vp, C.POINTER(h3dgs_grads), i32]),
             "h3dgs_get_stats": (i32, [vp, C.POINTER(h3dgs_stats)]),
@@ -195,6 +197,26 @@ def h3dgs_select_cut(ctx, cams, cut_ids, cut_t, cut_offsets, capacity: int, want
     st = lib().h3dgs_select_cut(ctx, arr, len(cams), _ptr(cut_ids), _ptr(cut_t), _ptr(cut_offsets), capacity,
                                 C.byref(tot) if want_total else None)
     _check(ctx, st)
+    return int(tot.value) if want_total else None
+
+
+def h3dgs_select_cut_noalloc(hier: "DeviceHierarchy", cam, cut_ids, cut_t, cut_offsets, capacity: int,
+                             stream: int | None = None, want_total: bool = True, n_nodes: int | None = None):
+    """One camera's cut with no allocation anywhere (scratch in a fixed device array of the library).
+
+    For callers that cannot allocate device memory; see include/h3dgs.h.  Returns the cut size
+    (synchronising) when want_total, else None.  n_nodes overrides the node count (tests only).
+    """
+    h = h3dgs_hierarchy()
+    h.n_nodes = hier.n if n_nodes is None else n_nodes
+    for k in ("mean", "scale", "rot", "opacity", "sh", "box_min", "box_max", "parent", "child_start",
+              "child_count"):
+        setattr(h, k, _ptr(getattr(hier, k)))
+    tot = C.c_int64(-1)
+    st = lib().h3dgs_select_cut_noalloc(C.byref(h), C.byref(camera_struct(cam)), _ptr(cut_ids), _ptr(cut_t),
+                                        _ptr(cut_offsets), capacity, C.byref(tot) if want_total else None, stream)
+    if st != H3DGS_OK:
+        raise H3dgsError(st, "h3dgs_select_cut_noalloc failed")
     return int(tot.value) if want_total else None
 
 
