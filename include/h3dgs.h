@@ -111,7 +111,9 @@ typedef struct {
     int64_t n_tiles;      /* tiles over all cameras                              */
     int64_t n_pixels;     /* pixels over all cameras                             */
     uint32_t device_flags; /* bit 0: pair capacity exceeded, bit 1: splat capacity
-                              exceeded, bit 2: cut truncated to capacity           */
+                              exceeded, bit 2: cut truncated to capacity, bit 3: a
+                              sort's wait on an earlier tile timed out (frame
+                              invalid; the context stays usable)                  */
     int64_t n_evals;      /* (pixel, splat) evaluations of the blend's main pass */
     int64_t n_evals_tpass; /* extra evaluations of the transmittance pass of split tiles */
     int64_t n_items;      /* blend work items (tiles, split tiles count once per chunk) */

@@ -80,3 +80,16 @@ class HierarchyParams(torch.nn.Module):
 def sample_tau(tau_min: float, tau_max: float, xi: float) -> float:
     """Target granularity for one optimisation step: tau = tau_max^xi tau_min^(1 - xi) (Sec. 5.1)."""
     return float(tau_max ** xi * tau_min ** (1.0 - xi))
+
+
+def l1_step(params: HierarchyParams, context, topology, cams, targets, optimizer, opts=None, capacity=None,
+            freeze_leaves: bool = True):
+    """One hierarchy-optimisation step (Sec. 5.1): render the views at their own tau, mean L1 against the
+    target images (packed like the render's output), back-propagate through the adjoint, step."""
+    optimizer.zero_grad(set_to_none=True)
+    images = render(context, topology, *params.activated(), cams, opts, freeze_leaves=freeze_leaves,
+                    capacity=capacity)
+    loss = (images - targets).abs().mean()
+    loss.backward()
+    optimizer.step()
+    return loss.detach()

@@ -38,8 +38,9 @@ T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
 
 // device counter block
 // C_EVALS and C_EVALS_T occupy two words each (64-bit counters)
-enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NITEMS = 5, C_EVALS = 8,
-       C_EVALS_T = 10, C_COUNT = 12 };
+// C_NSORTED: splats kept by the depth sort (the visible ones); C_NTSORT: pairs sorted by tile
+enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NITEMS = 5, C_NSORTED = 6,
+       C_NTSORT = 7, C_EVALS = 8, C_EVALS_T = 10, C_COUNT = 12 };
 
 }  // namespace
 
@@ -52,9 +53,9 @@ struct h3dgs_ctx {
     bool has_hier = false;
     DBuf rec, cams, counters;
     DBuf cut_mask, cut_bc, cut_tot;
-    DBuf s_rec, s_rect, s_key, s_idx, s_key2, s_idx2, s_tiles, s_poff;
-    DBuf pk0, pv0, pk1, pv1, ranges, sort_scratch, tile_work;
-    DBuf hist, dtot, partial;
+    DBuf s_rec, s_rect, s_key, s_idx, s_key2, s_idx2, s_key3, s_tiles, s_poff;
+    DBuf pk0, pv0, pk1, pv1, ranges;
+    DBuf sortw, partial;
     DBuf T_final, n_contrib, splat_grad;
     DBuf items, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last;
     int64_t item_cap = 0;
@@ -70,7 +71,7 @@ struct h3dgs_ctx {
     const int32_t* cut_ids = nullptr;
     const float* cut_t = nullptr;
     const int64_t* cut_offsets = nullptr;
-    bool depth_in_2 = false, pairs_in_1 = false;
+    bool pairs_in_1 = false;
     // profiling
     bool prof = false;
     cudaEvent_t ev[2 * H3DGS_STAGE_COUNT] = {};
@@ -185,11 +186,6 @@ bool supported_tile(int w, int h) {
            (w == 16 && h == 8) || (w == 32 && h == 4);
 }
 
-int bits_for(int64_t n) {
-    int b = 0;
-    while (b < 32 && ((int64_t)1 << b) < n) ++b;
-    return std::max(b, 1);
-}
 
 }  // namespace
 
@@ -222,13 +218,18 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images) {
 
 namespace {
 
-SortWork sort_work(h3dgs_ctx* ctx) {
-    SortWork w;
-    w.hist = P<uint32_t>(ctx->hist);
-    w.digit_total = P<uint32_t>(ctx->dtot);
-    w.partial = P<uint32_t>(ctx->partial);
-    w.blocks = ctx->num_sms * 4;
-    return w;
+// Sort and scan workspace for sorts of up to n_cap keys (grown here; no growth once reserved).
+cudaError_t sort_work(h3dgs_ctx* ctx, int64_t n_cap, SortWork* w) {
+    const size_t words = radix_work_words(n_cap);
+    cudaError_t e = ensure(ctx->sortw, sizeof(uint32_t) * words);
+    if (e != cudaSuccess) return e;
+    w->work = P<uint32_t>(ctx->sortw);
+    w->words = ctx->sortw.n / sizeof(uint32_t);
+    w->partial = P<uint32_t>(ctx->partial);
+    w->scan_blocks = ctx->num_sms * 4;
+    w->num_sms = ctx->num_sms;
+    w->flags = P<uint32_t>(ctx->counters) + C_FLAGS;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -254,8 +255,6 @@ h3dgs_status h3dgs_create(h3dgs_ctx** out, int32_t device, void* cuda_stream) {
     cudaError_t e = ensure(ctx->counters, sizeof(uint32_t) * C_COUNT);
     if (e == cudaSuccess) e = cudaMemset(ctx->counters.p, 0, sizeof(uint32_t) * C_COUNT);
     const int G = ctx->num_sms * 4;
-    if (e == cudaSuccess) e = ensure(ctx->hist, sizeof(uint32_t) * 256 * (size_t)G);
-    if (e == cudaSuccess) e = ensure(ctx->dtot, sizeof(uint32_t) * 256);
     if (e == cudaSuccess) e = ensure(ctx->partial, sizeof(uint32_t) * (size_t)(G + 1));
     if (e != cudaSuccess) {
         h3dgs_destroy(ctx);
@@ -271,8 +270,8 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     DBuf* bufs[] = {&ctx->rec, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot,
                     &ctx->s_rec, &ctx->s_rect, &ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2,
-                    &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1, &ctx->ranges, &ctx->sort_scratch, &ctx->tile_work,
-                    &ctx->hist, &ctx->dtot, &ctx->partial, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
+                    &ctx->s_key3, &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1,
+                    &ctx->ranges, &ctx->sortw, &ctx->partial, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
                     &ctx->items, &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
                     &ctx->sc_last};
     for (DBuf* b : bufs)
@@ -312,10 +311,12 @@ h3dgs_status h3dgs_reserve(h3dgs_ctx* ctx, int64_t max_splats, int64_t max_pairs
     const size_t M = (size_t)max_splats, Pn = (size_t)max_pairs;
     CK(ensure(ctx->s_rec, 16 * SPLAT_F4 * M), "splat buffer");
     CK(ensure(ctx->s_rect, 8 * M), "splat buffer");
-    DBuf* m4[] = {&ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2, &ctx->s_tiles, &ctx->s_poff};
+    DBuf* m4[] = {&ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2, &ctx->s_key3, &ctx->s_tiles, &ctx->s_poff};
     for (DBuf* b : m4) CK(ensure(*b, 4 * M), "splat buffer");
     DBuf* p4[] = {&ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1};
     for (DBuf* b : p4) CK(ensure(*b, 4 * Pn), "pair buffer");
+    SortWork w;
+    CK(sort_work(ctx, std::max<int64_t>(max_splats, max_pairs), &w), "sort workspace");
     CK(cudaDeviceSynchronize(), "reserve");
     ctx->fixed = true;
     ctx->cap_splats = max_splats;
@@ -338,7 +339,9 @@ h3dgs_status h3dgs_build_hierarchy(h3dgs_ctx* ctx, int64_t L, const float* mean,
     CK(cudaSetDevice(ctx->device), "set device");
     BuildOut bo{out->mean, out->scale, out->rot, out->opacity, out->sh, out->box_min, out->box_max,
                 out->parent, out->child_start, out->child_count};
-    CK(build_hierarchy(L, mean, scale, rot, opacity, sh, bo, sort_work(ctx), ctx->num_sms, ctx->stream), "build");
+    SortWork sw;
+    CK(sort_work(ctx, L, &sw), "sort workspace");
+    CK(build_hierarchy(L, mean, scale, rot, opacity, sh, bo, sw, ctx->num_sms, ctx->stream), "build");
     return H3DGS_OK;
 }
 
@@ -455,7 +458,8 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
         const size_t M = (size_t)capM;
         CK(ensure(ctx->s_rec, 16 * SPLAT_F4 * M), "splat buffer");
         CK(ensure(ctx->s_rect, 8 * M), "splat buffer");
-        DBuf* m4[] = {&ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2, &ctx->s_tiles, &ctx->s_poff};
+        DBuf* m4[] = {&ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2, &ctx->s_key3, &ctx->s_tiles,
+                      &ctx->s_poff};
         for (DBuf* b : m4) CK(ensure(*b, 4 * M), "splat buffer");
         capP = 0;
     }
@@ -479,10 +483,20 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
                          cnt + C_FLAGS, grid, s),
        "preprocess");
     stage_end(ctx, H3DGS_STAGE_PREPROCESS);
-    // pairs in cut order, stable sort by tile, ranges, then every tile's list by depth in shared memory
-    SortWork sw = sort_work(ctx);
+    // visible splats by depth (culled ones dropped), pair offsets in that order, pairs, stable sort
+    // of the pairs by tile id, ranges
+    SortWork sw;
+    CK(sort_work(ctx, std::max<int64_t>(capM, ctx->fixed ? capP : 0), &sw), "sort workspace");
+    bool in_a = false;
+    stage_begin(ctx, H3DGS_STAGE_DEPTH_SORT);
+    CK(radix_sort_pairs(P<uint32_t>(ctx->s_key), nullptr, P<uint32_t>(ctx->s_key2), P<uint32_t>(ctx->s_idx2),
+                        P<uint32_t>(ctx->s_key3), P<uint32_t>(ctx->s_idx), cnt + C_NSPLATS, capM, 32, true,
+                        cnt + C_NSORTED, sw, &in_a, s),
+       "depth sort");
+    stage_end(ctx, H3DGS_STAGE_DEPTH_SORT);
+    const uint32_t* order = in_a ? P<uint32_t>(ctx->s_idx2) : P<uint32_t>(ctx->s_idx);
     stage_begin(ctx, H3DGS_STAGE_DUPLICATE);
-    CK(scan_plain(P<uint32_t>(ctx->s_tiles), P<uint32_t>(ctx->s_poff), cnt + C_NSPLATS, cnt + C_NPAIRS, sw, s),
+    CK(scan_gathered(P<uint32_t>(ctx->s_tiles), order, P<uint32_t>(ctx->s_poff), cnt + C_NSORTED, cnt + C_NPAIRS, sw, s),
        "pair scan");
     if (!ctx->fixed) {
         uint32_t pn = 0;
@@ -491,31 +505,26 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
         capP = std::max<int64_t>(pn, 1);
         DBuf* p4[] = {&ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1};
         for (DBuf* b : p4) CK(ensure(*b, 4 * (size_t)capP), "pair buffer");
+        CK(sort_work(ctx, std::max<int64_t>(capM, capP), &sw), "sort workspace");
     }
-    CK(ensure(ctx->sort_scratch, 16 * (size_t)capP), "sort scratch");
-    CK(launch_duplicate_plain(P<DevCam>(ctx->cams), n_cams, cut_offsets, sb, P<uint32_t>(ctx->s_poff), cnt + C_NPAIRS,
-                              capP, cnt + C_NPAIRS_KEPT, P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), cnt + C_FLAGS,
-                              grid, s),
+    CK(launch_duplicate(P<DevCam>(ctx->cams), n_cams, cut_offsets, sb, order, cnt + C_NSORTED, P<uint32_t>(ctx->s_poff),
+                        cnt + C_NPAIRS, capP, cnt + C_NPAIRS_KEPT, P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0),
+                        cnt + C_FLAGS, grid, s),
        "duplicate");
     stage_end(ctx, H3DGS_STAGE_DUPLICATE);
-    bool in1 = false;
     stage_begin(ctx, H3DGS_STAGE_TILE_SORT);
+    int tbits = 1;
+    while (tbits < 32 && ((int64_t)1 << tbits) < ctx->n_tiles) ++tbits;
     CK(radix_sort_pairs(P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), P<uint32_t>(ctx->pk1), P<uint32_t>(ctx->pv1),
-                        cnt + C_NPAIRS_KEPT, bits_for(ctx->n_tiles), sw, &in1, s),
+                        P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), cnt + C_NPAIRS_KEPT, capP, tbits, false,
+                        cnt + C_NTSORT, sw, &in_a, s),
        "tile sort");
     stage_end(ctx, H3DGS_STAGE_TILE_SORT);
-    const uint32_t* keys = in1 ? P<uint32_t>(ctx->pk1) : P<uint32_t>(ctx->pk0);
-    uint32_t* list = in1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
+    const bool in1 = in_a;
+    const uint32_t* tile_keys = in1 ? P<uint32_t>(ctx->pk1) : P<uint32_t>(ctx->pk0);
     stage_begin(ctx, H3DGS_STAGE_RANGES);
-    CK(launch_ranges(keys, cnt + C_NPAIRS_KEPT, P<int2>(ctx->ranges), grid, s), "ranges");
+    CK(launch_ranges(tile_keys, cnt + C_NPAIRS_KEPT, ctx->n_tiles, P<int2>(ctx->ranges), grid, s), "ranges");
     stage_end(ctx, H3DGS_STAGE_RANGES);
-    stage_begin(ctx, H3DGS_STAGE_DEPTH_SORT);
-    CK(ensure(ctx->tile_work, sizeof(uint32_t) * (size_t)(2 * ctx->n_tiles + 2)), "tile sort work");
-    CK(launch_tile_depth_sort(P<int2>(ctx->ranges), ctx->n_tiles, P<uint32_t>(ctx->s_key), list,
-                              P<uint32_t>(ctx->tile_work), P<unsigned long long>(ctx->sort_scratch), 2 * capP,
-                              ctx->num_sms, s),
-       "tile depth sort");
-    stage_end(ctx, H3DGS_STAGE_DEPTH_SORT);
     stage_begin(ctx, H3DGS_STAGE_BLEND);
     {
         const int NT = o.tile_w * o.tile_h;

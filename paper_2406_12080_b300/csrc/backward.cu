@@ -53,10 +53,33 @@ __device__ __forceinline__ float alpha_prime_grad(float ap, float K) {
     return __fdividef(ex2_approx(lg2_approx(1.0f - ap) * (__fdividef(1.0f, K) - 1.0f)), K);
 }
 
-__device__ __forceinline__ float warp_sum(float x) {
+// Warp reduce-scatter of 16 per-lane values (the last 6 are zero padding): after it, lanes 2k and
+// 2k+1 both hold the warp-wide sum of value k.  16 shuffles instead of 16 x 5.
+__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    return x;
+    for (int i = 0; i < 8; ++i) {
+        const bool hi = lane & 16;
+        const float send = hi ? v[i] : v[8 + i], keep = hi ? v[8 + i] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 8;
+        const float send = hi ? v[i] : v[4 + i], keep = hi ? v[4 + i] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 4;
+        const float send = hi ? v[i] : v[2 + i], keep = hi ? v[2 + i] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool hi = lane & 2;
+        const float send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 }  // namespace
@@ -202,14 +225,10 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                gu = warp_sum(gu); gv = warp_sum(gv); gca = warp_sum(gca); gcb = warp_sum(gcb); gcc = warp_sum(gcc);
-                gon = warp_sum(gon); gop = warp_sum(gop); gr = warp_sum(gr); gg = warp_sum(gg); gb = warp_sum(gb);
-                if ((threadIdx.x & 31) == 0) {
-                    float* d = sgrad + 12 * (int64_t)s_id[j];
-                    atomicAdd(d + 0, gu); atomicAdd(d + 1, gv); atomicAdd(d + 2, gca); atomicAdd(d + 3, gcb);
-                    atomicAdd(d + 4, gcc); atomicAdd(d + 5, gon); atomicAdd(d + 6, gop); atomicAdd(d + 7, gr);
-                    atomicAdd(d + 8, gg); atomicAdd(d + 9, gb);
-                }
+                float v[16] = {gu, gv, gca, gcb, gcc, gon, gop, gr, gg, gb, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const float sum = warp_reduce_scatter16(v, lane);
+                const int k = (lane >> 1) & 15;
+                if (!(lane & 1) && k < 10) atomicAdd(sgrad + 12 * (int64_t)s_id[j] + k, sum);
             }
           }
         }

@@ -41,8 +41,9 @@ __device__ __forceinline__ float alpha_prime(float ap, float K) {
     return 1.0f - ex2_approx(__fdividef(lg2_approx(1.0f - ap), K));
 }
 
-// alpha of one (pixel, splat) pair, fixed fp32 order
-__device__ __forceinline__ float pair_alpha(float px, float py, const float4 a, const float4 b, float Kc, float clampv) {
+// alpha of one (pixel, splat) pair, fixed fp32 order; K (child count) is read only when t != 0
+__device__ __forceinline__ float pair_alpha(float px, float py, const float4 a, const float4 b, const float4* c,
+                                            float clampv) {
     const float dx = fsub(px, a.x), dy = fsub(py, a.y);
     const float h = ffma(a.z, dx, fmul(a.w, dy));
     const float g = fmul(fmul(b.x, dy), dy);
@@ -51,7 +52,7 @@ __device__ __forceinline__ float pair_alpha(float px, float py, const float4 a, 
     const float an = fminf(clampv, fmul(b.y, G));
     if (b.w == 0.0f) return an;
     const float ap = fminf(clampv, fmul(b.z, G));
-    return ffma(b.w, alpha_prime(ap, Kc), fmul(fsub(1.0f, b.w), an));
+    return ffma(b.w, alpha_prime(ap, c->w), fmul(fsub(1.0f, b.w), an));
 }
 
 template <int TW, int TH>
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(TW * TH) blend_items_kernel(const DevCam* __re
                     bits &= bits - 1;
                     if (done) continue;
                     ++evals;
-                    const float alpha = pair_alpha(g.px, g.py, s_a[j], s_b[j], s_c[j].w, clampv);
+                    const float alpha = pair_alpha(g.px, g.py, s_a[j], s_b[j], &s_c[j], clampv);
                     if (alpha < afloor) continue;
                     const float Tn = fmul(T, fsub(1.0f, alpha));
                     if (!MAIN) {                            // pass T: no stop, but nothing matters below t_min

@@ -511,7 +511,7 @@ cudaError_t build_hierarchy(int64_t L, const float* mean, const float* scale, co
     BR(mem.alloc(&k1, (size_t)L));
     BR(mem.alloc(&v1, (size_t)L));
     BR(mem.alloc(&ebox, 6 * (size_t)N));
-    BR(mem.alloc(&n_dev, 1));
+    BR(mem.alloc(&n_dev, 2));   // [0] leaf count, [1] kept count of the sorts
     BR(mem.alloc(&d_nodes, maxG));
     BR(mem.alloc(&d_cnt, maxG));
     BR(mem.alloc(&d_next, 2 * maxG));
@@ -558,7 +558,7 @@ cudaError_t build_hierarchy(int64_t L, const float* mean, const float* scale, co
         group_axis_kernel<<<grid, 256, 0, st>>>(G, d_nodes, ebox, d_axis);
         split_keys_kernel<<<grid, 256, 0, st>>>(L, mean, seg, d_axis, k0, v0);
         bool in1 = false;
-        BR(radix_sort_pairs(k0, v0, k1, v1, n_dev, 32, sw, &in1, st));
+        BR(radix_sort_pairs(k0, v0, k1, v1, k0, v0, n_dev, L, 32, false, n_dev + 1, sw, &in1, st));
         uint32_t* va = in1 ? v1 : v0;   // leaves in (mean on axis, leaf index) order
         uint32_t* kb = in1 ? k0 : k1;   // free key buffer
         uint32_t* kc = in1 ? k1 : k0;   // keys of the first sort, no longer needed
@@ -567,7 +567,7 @@ cudaError_t build_hierarchy(int64_t L, const float* mean, const float* scale, co
         int bits = 1;
         while (bits < 32 && ((int64_t)1 << bits) < G + 1) ++bits;
         bool in1b = false;
-        BR(radix_sort_pairs(kb, va, kc, vb, n_dev, bits, sw, &in1b, st));
+        BR(radix_sort_pairs(kb, va, kc, vb, kb, va, n_dev, L, bits, false, n_dev + 1, sw, &in1b, st));
         const uint32_t* gk = in1b ? kc : kb;
         const uint32_t* gv = in1b ? vb : va;
         assign_kernel<<<grid, 256, 0, st>>>(n_active, gk, gv, d_start, d_cnt, d_next, seg, leaf_of_node);

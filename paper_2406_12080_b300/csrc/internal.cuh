@@ -17,6 +17,7 @@ constexpr int CAM_BATCH = 32;    // cameras per set-up launch (passed by value)
 constexpr uint32_t FLAG_PAIRS_OVERFLOW = 1u << 0;
 constexpr uint32_t FLAG_SPLATS_OVERFLOW = 1u << 1;
 constexpr uint32_t FLAG_CUT_TRUNCATED = 1u << 2;
+constexpr uint32_t FLAG_SORT_TIMEOUT = 1u << 3;   // a radix-sort look-back wait gave up (result invalid)
 
 // Per-camera data on the device.  Raw fields come from h3dgs_camera; the derived floats are
 // computed on the device in a fixed fp32 order (camera_setup kernel); integer bookkeeping
@@ -166,39 +167,34 @@ cudaError_t launch_interpolate_export(const DevHier& h, int n_cams, const int32_
                                       cudaStream_t s);
 
 // sort.cu
+constexpr size_t RADIX_HEADER_WORDS = 2048;   // tickets, kept count, pass histograms
 struct SortWork {
-    uint32_t* hist;         // [256][G]
-    uint32_t* digit_total;  // [256]
-    uint32_t* partial;      // [G + 1] scan partials
-    int blocks;             // G
+    uint32_t* work;         // radix_work_words(n_cap) words: header, then look-back words per pass and tile
+    size_t words;
+    uint32_t* partial;      // [scan_blocks + 1] scan partials
+    int scan_blocks;
+    int num_sms;
+    uint32_t* flags;        // device flag word (FLAG_SORT_TIMEOUT)
 };
-// Stable LSD radix sort of n (device count) key/value pairs on key bits [0, bits).  Sorts (k0, v0)
-// ping-ponging with (k1, v1); returns via *result_in_1 whether the result is in (k1, v1).
-cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev,
-                             int bits, const SortWork& w, bool* result_in_1, cudaStream_t s);
-cudaError_t launch_iota(uint32_t* out, const uint32_t* n_dev, int grid, cudaStream_t s);
-// out[i] = exclusive prefix sum of in[idx[i]] over i < n; *total = full sum.
+size_t radix_work_words(int64_t n_cap);
+// Stable LSD radix sort of n = *n_dev <= n_cap key/value pairs on key bits [0, bits).  The first pass
+// reads (kin, vin) (vin NULL: values are the input positions), later passes alternate between (ka, va)
+// and (kb, vb); *result_in_a tells which pair holds the result (kin/vin may alias kb/vb).  With
+// drop_max, keys equal to 0xffffffff are left out; *n_kept (device) receives the number sorted.
+cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ka, uint32_t* va, uint32_t* kb,
+                             uint32_t* vb, const uint32_t* n_dev, int64_t n_cap, int bits, bool drop_max,
+                             uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s);
+// out[i] = exclusive prefix sum over j < i of in[idx[j]] (in[j] if idx is NULL), i < *n_dev; *total = sum.
 cudaError_t scan_gathered(const uint32_t* in, const uint32_t* idx, uint32_t* out, const uint32_t* n_dev,
                           uint32_t* total, const SortWork& w, cudaStream_t s);
-// Also writes *n_pairs_kept = min(*n_pairs, cap_pairs) (the count sorted afterwards).
+// Pairs (tile id, cut position) of the depth-ordered splats order[0, *n_order) at their scanned
+// offsets; *n_pairs_kept = min(*n_pairs, cap_pairs).
 cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_offsets, const SplatBufs& sb,
-                             const uint32_t* order, const uint32_t* pair_off, const uint32_t* n_pairs,
-                             int64_t cap_pairs, uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals,
-                             uint32_t* flags, int grid, cudaStream_t s);
-cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_pairs_kept, int2* ranges, int grid, cudaStream_t s);
-// Plain exclusive scan (no gather).
-cudaError_t scan_plain(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t* total, const SortWork& w,
-                       cudaStream_t s);
-// Pairs emitted in cut order (splat m's tiles in row-major order).
-cudaError_t launch_duplicate_plain(const DevCam* cams, int n_cams, const int64_t* cut_offsets, const SplatBufs& sb,
-                                   const uint32_t* pair_off, const uint32_t* n_pairs, int64_t cap_pairs,
-                                   uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* flags, int grid,
-                                   cudaStream_t s);
-// Orders every tile's list by (depth key, cut position).  work: 2 n_tiles + 2 words; scratch:
-// 64-bit, >= 2 * pairs entries (only lists longer than 16384 entries use it).
-cudaError_t launch_tile_depth_sort(const int2* ranges, int64_t n_tiles, const uint32_t* depth_key, uint32_t* list,
-                                   uint32_t* work, unsigned long long* scratch, int64_t scratch_cap, int num_sms,
-                                   cudaStream_t s);
+                             const uint32_t* order, const uint32_t* n_order, const uint32_t* pair_off,
+                             const uint32_t* n_pairs, int64_t cap_pairs, uint32_t* n_pairs_kept, uint32_t* keys,
+                             uint32_t* vals, uint32_t* flags, int grid, cudaStream_t s);
+cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n_tiles, int2* ranges, int grid,
+                          cudaStream_t s);
 
 // blend.cu
 // Everything the chunked blend and its adjoint share.  Items are (tile, chunk) pairs; tiles with at

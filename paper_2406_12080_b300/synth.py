@@ -186,6 +186,21 @@ def corridor_scene(seed: int = 1, n_leaves: int = 1_000_000, width: int = 1920,
     return Scene("corridor", leaves, [corridor_camera(line, s_cam, width, height, tau)])
 
 
+def corridor_views(seed: int = 1, n_views: int = 32,
+                   resolutions=((1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)),
+                   taus=(3.0, 6.0, 15.0), hfov_deg: float = 60.0):
+    """Views along the corridor polyline: resolutions in equal groups, tau cycling over `taus`."""
+    line = corridor_polyline(seed)
+    rng = np.random.default_rng([seed, 6])
+    s = np.sort(rng.uniform(50.0, line.length - 50.0, n_views))
+    per = max(1, n_views // len(resolutions))
+    cams = []
+    for i, si in enumerate(s):
+        w, h = resolutions[min(i // per, len(resolutions) - 1)]
+        cams.append(corridor_camera(line, si, w, h, taus[i % len(taus)], hfov_deg))
+    return cams
+
+
 def optimisation_views(seed: int = 3, n_views: int = 8, width: int = 1280, height: int = 720,
                        tau_min: float = 3.0, tau_max: float = 640.0):
     """Views for the hierarchy-optimisation workload on the corridor.
