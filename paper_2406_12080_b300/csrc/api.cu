@@ -55,7 +55,7 @@ struct h3dgs_ctx {
     DBuf cut_mask, cut_bc, cut_tot;
     DBuf s_rec, s_rect, s_key, s_idx, s_key2, s_idx2, s_key3, s_tiles, s_poff;
     DBuf pk0, pv0, pk1, pv1, ranges;
-    DBuf sortw, partial;
+    DBuf sortw, seg_start;
     DBuf T_final, n_contrib, splat_grad;
     DBuf items, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last;
     int64_t item_cap = 0;
@@ -213,6 +213,9 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images) {
     a.T_final = P<float>(ctx->T_final);
     a.n_contrib = P<int32_t>(ctx->n_contrib);
     a.n_evals = reinterpret_cast<unsigned long long*>(P<uint32_t>(ctx->counters) + C_EVALS);
+    a.work = P<uint32_t>(ctx->sortw);
+    a.work_words = ctx->sortw.n / sizeof(uint32_t);
+    a.flags = P<uint32_t>(ctx->counters) + C_FLAGS;
     return a;
 }
 
@@ -225,8 +228,6 @@ cudaError_t sort_work(h3dgs_ctx* ctx, int64_t n_cap, SortWork* w) {
     if (e != cudaSuccess) return e;
     w->work = P<uint32_t>(ctx->sortw);
     w->words = ctx->sortw.n / sizeof(uint32_t);
-    w->partial = P<uint32_t>(ctx->partial);
-    w->scan_blocks = ctx->num_sms * 4;
     w->num_sms = ctx->num_sms;
     w->flags = P<uint32_t>(ctx->counters) + C_FLAGS;
     return cudaSuccess;
@@ -254,8 +255,6 @@ h3dgs_status h3dgs_create(h3dgs_ctx** out, int32_t device, void* cuda_stream) {
     ctx->num_sms = prop.multiProcessorCount;
     cudaError_t e = ensure(ctx->counters, sizeof(uint32_t) * C_COUNT);
     if (e == cudaSuccess) e = cudaMemset(ctx->counters.p, 0, sizeof(uint32_t) * C_COUNT);
-    const int G = ctx->num_sms * 4;
-    if (e == cudaSuccess) e = ensure(ctx->partial, sizeof(uint32_t) * (size_t)(G + 1));
     if (e != cudaSuccess) {
         h3dgs_destroy(ctx);
         return e == cudaErrorMemoryAllocation ? H3DGS_ERR_OOM : H3DGS_ERR_CUDA;
@@ -271,7 +270,7 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
     DBuf* bufs[] = {&ctx->rec, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot,
                     &ctx->s_rec, &ctx->s_rect, &ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2,
                     &ctx->s_key3, &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1,
-                    &ctx->ranges, &ctx->sortw, &ctx->partial, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
+                    &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
                     &ctx->items, &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
                     &ctx->sc_last};
     for (DBuf* b : bufs)
@@ -317,6 +316,7 @@ h3dgs_status h3dgs_reserve(h3dgs_ctx* ctx, int64_t max_splats, int64_t max_pairs
     for (DBuf* b : p4) CK(ensure(*b, 4 * Pn), "pair buffer");
     SortWork w;
     CK(sort_work(ctx, std::max<int64_t>(max_splats, max_pairs), &w), "sort workspace");
+    CK(ensure(ctx->seg_start, sizeof(uint32_t) * (size_t)(Pn / DUP_SEG + 2)), "pair segments");
     CK(cudaDeviceSynchronize(), "reserve");
     ctx->fixed = true;
     ctx->cap_splats = max_splats;
@@ -496,8 +496,11 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
     stage_end(ctx, H3DGS_STAGE_DEPTH_SORT);
     const uint32_t* order = in_a ? P<uint32_t>(ctx->s_idx2) : P<uint32_t>(ctx->s_idx);
     stage_begin(ctx, H3DGS_STAGE_DUPLICATE);
-    CK(scan_gathered(P<uint32_t>(ctx->s_tiles), order, P<uint32_t>(ctx->s_poff), cnt + C_NSORTED, cnt + C_NPAIRS, sw, s),
-       "pair scan");
+    const int64_t seg_cap0 = ctx->fixed ? capP / DUP_SEG + 2 : 0;
+    if (ctx->fixed) CK(ensure(ctx->seg_start, sizeof(uint32_t) * (size_t)seg_cap0), "pair segments");
+    CK(launch_pair_offsets(P<uint32_t>(ctx->s_tiles), order, cnt + C_NSORTED, capM, P<uint32_t>(ctx->s_poff),
+                           P<uint32_t>(ctx->seg_start), seg_cap0, cnt + C_NPAIRS, sw, s),
+       "pair offsets");
     if (!ctx->fixed) {
         uint32_t pn = 0;
         CK(cudaMemcpyAsync(&pn, cnt + C_NPAIRS, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read pairs");
@@ -506,10 +509,15 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
         DBuf* p4[] = {&ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1};
         for (DBuf* b : p4) CK(ensure(*b, 4 * (size_t)capP), "pair buffer");
         CK(sort_work(ctx, std::max<int64_t>(capM, capP), &sw), "sort workspace");
+        const int64_t seg_cap = capP / DUP_SEG + 2;
+        CK(ensure(ctx->seg_start, sizeof(uint32_t) * (size_t)seg_cap), "pair segments");
+        CK(launch_pair_segments(P<uint32_t>(ctx->s_tiles), order, cnt + C_NSORTED, P<uint32_t>(ctx->s_poff),
+                                P<uint32_t>(ctx->seg_start), seg_cap, grid, s),
+           "pair segments");
     }
     CK(launch_duplicate(P<DevCam>(ctx->cams), n_cams, cut_offsets, sb, order, cnt + C_NSORTED, P<uint32_t>(ctx->s_poff),
-                        cnt + C_NPAIRS, capP, cnt + C_NPAIRS_KEPT, P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0),
-                        cnt + C_FLAGS, grid, s),
+                        P<uint32_t>(ctx->seg_start), cnt + C_NPAIRS, capP, cnt + C_NPAIRS_KEPT, P<uint32_t>(ctx->pk0),
+                        P<uint32_t>(ctx->pv0), cnt + C_FLAGS, s),
        "duplicate");
     stage_end(ctx, H3DGS_STAGE_DUPLICATE);
     stage_begin(ctx, H3DGS_STAGE_TILE_SORT);

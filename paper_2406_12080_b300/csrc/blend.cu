@@ -21,6 +21,7 @@
 //             contributor from the chunk where the walk stopped.
 // A chunk whose T_in is already below t_min adds nothing (the walk stopped in an earlier chunk).
 #include "internal.cuh"
+#include "lookback.cuh"
 
 namespace h3dgs {
 
@@ -88,37 +89,49 @@ __device__ __forceinline__ TileGeom<TW, TH> tile_geom(const DevCam* __restrict__
 
 // ------------------------------------------------------------------------------------ plan
 
-// Single block: chunk counts per tile, their exclusive scan, and the (tile, chunk) item list.
-__global__ void __launch_bounds__(1024) blend_plan_kernel(const int2* __restrict__ ranges, int64_t n_tiles, int chunk,
-                                                          int32_t* __restrict__ tile_item0, int32_t* __restrict__ tile_nch,
-                                                          int2* __restrict__ items, int64_t item_cap,
-                                                          uint32_t* __restrict__ n_items) {
-    __shared__ int32_t s_part[1024];
-    const int64_t per = (n_tiles + blockDim.x - 1) / blockDim.x;
-    const int64_t t0 = threadIdx.x * per, t1 = min(n_tiles, t0 + per);
-    int32_t sum = 0;
-    for (int64_t t = t0; t < t1; ++t) {
-        const int len = ranges[t].y - ranges[t].x;
-        sum += len <= chunk ? 1 : (len + chunk - 1) / chunk;
+// Chunk counts per tile, their exclusive scan (single pass, decoupled look-back) and the (tile, chunk)
+// item list.  Block b takes tiles [b PL_TILE, (b + 1) PL_TILE), PL_IPT contiguous tiles per thread.
+constexpr int PL_THREADS = 256;
+constexpr int PL_IPT = 4;
+constexpr int PL_TILE = PL_THREADS * PL_IPT;
+
+__global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __restrict__ ranges, int64_t n_tiles,
+                                                                int chunk, int32_t* __restrict__ tile_item0,
+                                                                int32_t* __restrict__ tile_nch,
+                                                                int2* __restrict__ items, int64_t item_cap,
+                                                                uint32_t* __restrict__ n_items, Lookback lb) {
+    __shared__ uint32_t s_ticket;
+    __shared__ unsigned long long s_slot, s_warp[PL_THREADS / 32];
+    const uint32_t b = lb_ticket(lb, &s_ticket);
+    const int64_t base = (int64_t)b * PL_TILE;
+    if (base >= n_tiles) return;
+    int nch[PL_IPT];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int q = 0; q < PL_IPT; ++q) {
+        const int64_t t = base + (int64_t)threadIdx.x * PL_IPT + q;
+        nch[q] = 0;
+        if (t < n_tiles) {
+            const int2 r = ranges[t];
+            const int len = r.y - r.x;
+            nch[q] = len <= chunk ? 1 : (len + chunk - 1) / chunk;
+        }
+        sum += nch[q];
     }
-    s_part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        const int32_t x = (int)threadIdx.x >= off ? s_part[threadIdx.x - off] : 0;
-        __syncthreads();
-        s_part[threadIdx.x] += x;
-        __syncthreads();
-    }
-    int32_t run = s_part[threadIdx.x] - sum;
-    if (threadIdx.x == blockDim.x - 1) *n_items = (uint32_t)min((int64_t)s_part[threadIdx.x], item_cap);
-    for (int64_t t = t0; t < t1; ++t) {
-        const int len = ranges[t].y - ranges[t].x;
-        const int nch = len <= chunk ? 1 : (len + chunk - 1) / chunk;
-        tile_item0[t] = run;
-        tile_nch[t] = nch;
-        for (int c = 0; c < nch; ++c)
-            if (run + c < item_cap) items[run + c] = make_int2((int)t, c);
-        run += nch;
+    unsigned long long agg;
+    const unsigned long long before = lb_block_scan<PL_THREADS>(sum, s_warp, &agg);
+    unsigned long long off = lb_prefix(lb, b, agg, &s_slot) + before;
+#pragma unroll
+    for (int q = 0; q < PL_IPT; ++q) {
+        const int64_t t = base + (int64_t)threadIdx.x * PL_IPT + q;
+        if (t < n_tiles) {
+            tile_item0[t] = (int32_t)off;
+            tile_nch[t] = nch[q];
+            for (int c = 0; c < nch[q]; ++c)
+                if ((int64_t)off + c < item_cap) items[off + c] = make_int2((int)t, c);
+            if (t + 1 == n_tiles) *n_items = (uint32_t)min((long long)(off + nch[q]), (long long)item_cap);
+        }
+        off += nch[q];
     }
 }
 
@@ -287,8 +300,13 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
 
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     if (a.n_tiles <= 0) return cudaSuccess;
-    blend_plan_kernel<<<1, 1024, 0, s>>>(a.ranges, a.n_tiles, a.chunk, a.tile_item0, a.tile_nch, a.items, a.item_cap,
-                                         a.n_items);
+    const int64_t pblocks = (a.n_tiles + PL_TILE - 1) / PL_TILE;
+    if ((size_t)(LB_HEADER_WORDS + 2 * pblocks) > a.work_words) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)pblocks), s);
+    if (e != cudaSuccess) return e;
+    Lookback lb{reinterpret_cast<unsigned long long*>(a.work + LB_HEADER_WORDS), a.work, a.flags};
+    blend_plan_kernel<<<(unsigned)pblocks, PL_THREADS, 0, s>>>(a.ranges, a.n_tiles, a.chunk, a.tile_item0, a.tile_nch,
+                                                               a.items, a.item_cap, a.n_items, lb);
     Scratch sc{a.scratch_Tc, a.scratch_C, a.scratch_Tend, a.scratch_last};
     unsigned long long* ev_main = a.n_evals;
     unsigned long long* ev_tpass = a.n_evals ? a.n_evals + 1 : nullptr;

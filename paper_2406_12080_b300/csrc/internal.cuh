@@ -171,8 +171,6 @@ constexpr size_t RADIX_HEADER_WORDS = 2048;   // tickets, kept count, pass histo
 struct SortWork {
     uint32_t* work;         // radix_work_words(n_cap) words: header, then look-back words per pass and tile
     size_t words;
-    uint32_t* partial;      // [scan_blocks + 1] scan partials
-    int scan_blocks;
     int num_sms;
     uint32_t* flags;        // device flag word (FLAG_SORT_TIMEOUT)
 };
@@ -184,15 +182,21 @@ size_t radix_work_words(int64_t n_cap);
 cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ka, uint32_t* va, uint32_t* kb,
                              uint32_t* vb, const uint32_t* n_dev, int64_t n_cap, int bits, bool drop_max,
                              uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s);
-// out[i] = exclusive prefix sum over j < i of in[idx[j]] (in[j] if idx is NULL), i < *n_dev; *total = sum.
-cudaError_t scan_gathered(const uint32_t* in, const uint32_t* idx, uint32_t* out, const uint32_t* n_dev,
-                          uint32_t* total, const SortWork& w, cudaStream_t s);
-// Pairs (tile id, cut position) of the depth-ordered splats order[0, *n_order) at their scanned
-// offsets; *n_pairs_kept = min(*n_pairs, cap_pairs).
+// Pair offsets of the depth order: pair_off[i] = sum of tiles[order[j]] over j < i (i < *n_dev <= n_cap),
+// *total = the sum; seg_start[s] = the entry holding pair s DUP_SEG (for s < seg_cap).
+constexpr int DUP_SEG = 1024;         // pairs per duplication block
+constexpr size_t LB_HEADER_WORDS = 64;
+cudaError_t launch_pair_offsets(const uint32_t* tiles, const uint32_t* order, const uint32_t* n_dev, int64_t n_cap,
+                                uint32_t* pair_off, uint32_t* seg_start, int64_t seg_cap, uint32_t* total,
+                                const SortWork& w, cudaStream_t s);
+cudaError_t launch_pair_segments(const uint32_t* tiles, const uint32_t* order, const uint32_t* n_dev,
+                                 const uint32_t* pair_off, uint32_t* seg_start, int64_t seg_cap, int grid,
+                                 cudaStream_t s);
+// Pairs (tile id, cut position) of the depth-ordered splats; *n_pairs_kept = min(*n_pairs, cap_pairs).
 cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_offsets, const SplatBufs& sb,
                              const uint32_t* order, const uint32_t* n_order, const uint32_t* pair_off,
-                             const uint32_t* n_pairs, int64_t cap_pairs, uint32_t* n_pairs_kept, uint32_t* keys,
-                             uint32_t* vals, uint32_t* flags, int grid, cudaStream_t s);
+                             const uint32_t* seg_start, const uint32_t* n_pairs, int64_t cap_pairs,
+                             uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* flags, cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n_tiles, int2* ranges, int grid,
                           cudaStream_t s);
 
@@ -222,6 +226,9 @@ struct BlendArgs {
     float* T_final;
     int32_t* n_contrib;
     unsigned long long* n_evals;  // [2]: main-pass evaluations, transmittance-pass evaluations
+    uint32_t* work;               // look-back workspace of the plan (LB_HEADER_WORDS + 2 per 1024 tiles)
+    size_t work_words;
+    uint32_t* flags;              // device flag word
 };
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
 

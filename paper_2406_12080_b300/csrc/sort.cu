@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "lookback.cuh"
 
 namespace h3dgs {
 
@@ -32,7 +33,8 @@ constexpr int OS_TILE = OS_THREADS * OS_IPT;    // 3840 keys per tile
 constexpr uint32_t ST_AGG = 1u << 30;           // look-back word: tile's own digit count
 constexpr uint32_t ST_INC = 2u << 30;           // look-back word: count of this and all earlier tiles
 constexpr uint32_t ST_VAL = (1u << 30) - 1u;
-constexpr int OS_SPIN_LIMIT = 1 << 20;
+constexpr int OS_SPIN_LIMIT = 1 << 20;       // re-reads of one look-back word before giving up
+constexpr int OS_LOOKBACK = 8;               // look-back words loaded per step
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
     uint32_t v;
@@ -67,7 +69,9 @@ __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t x, uint32_t
 }
 
 // Digit histograms of every pass over keys[0, n); with `drop`, keys equal to 0xffffffff are left out.
-// n_kept gets the number of keys counted.  hist and n_kept start at zero.
+// n_kept gets the number of keys counted.  hist and n_kept start at zero.  Lanes of a warp holding the
+// same digit are grouped (8 ballots) and their leader adds the group's size, so skewed digits (the
+// top byte of depth keys takes a handful of values) cost one shared atomic per group.
 __global__ void __launch_bounds__(OS_THREADS) radix_histogram_kernel(const uint32_t* __restrict__ keys,
                                                                      const uint32_t* __restrict__ n_dev, int passes,
                                                                      int drop, uint32_t* __restrict__ hist,
@@ -78,15 +82,30 @@ __global__ void __launch_bounds__(OS_THREADS) radix_histogram_kernel(const uint3
     if (threadIdx.x == 0) s_kept = 0;
     __syncthreads();
     const uint32_t n = *n_dev;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lmask = lanemask_lt();
     uint32_t kept = 0;
-    for (uint32_t i = blockIdx.x * OS_THREADS + threadIdx.x; i < n; i += gridDim.x * OS_THREADS) {
-        const uint32_t k = __ldg(keys + i);
-        if (drop && k == 0xffffffffu) continue;
-        ++kept;
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(k >> (8 * p)) & 255u], 1u);
+    // whole warps iterate together (the ballots need every lane)
+    for (uint32_t i0 = (blockIdx.x * OS_THREADS + threadIdx.x) & ~31u; i0 < n; i0 += gridDim.x * OS_THREADS) {
+        const uint32_t i = i0 + lane;
+        const uint32_t k = i < n ? __ldg(keys + i) : 0xffffffffu;
+        const bool ok = i < n && !(drop && k == 0xffffffffu);
+        kept += ok;
+        const uint32_t valid = __ballot_sync(0xffffffffu, ok);
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = (k >> (8 * p)) & 255u;
+            uint32_t peers = valid;
+#pragma unroll
+            for (int bit = 0; bit < 8; ++bit) {
+                const bool on = (d >> bit) & 1u;
+                const uint32_t m = __ballot_sync(0xffffffffu, on);
+                peers &= on ? m : ~m;
+            }
+            if (ok && (peers & lmask) == 0) atomicAdd(&s_h[p][d], (uint32_t)__popc(peers));
+        }
     }
     kept = __reduce_add_sync(0xffffffffu, kept);
-    if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&s_kept, kept);
+    if (lane == 0 && kept) atomicAdd(&s_kept, kept);
     __syncthreads();
     for (int i = threadIdx.x; i < passes * 256; i += OS_THREADS) {
         const uint32_t c = (&s_h[0][0])[i];
@@ -168,22 +187,34 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
     s_lstart[d] = lstart;
     // global start of digit d over the whole input (exclusive scan of the pass histogram)
     const uint32_t gstart = block_exclusive_scan256(hist[d], s_warp);
-    // ---- decoupled look-back over earlier tiles for digit d
+    // ---- decoupled look-back over earlier tiles for digit d: OS_LOOKBACK status words are loaded at
+    // once, then summed newest first until an inclusive one; a word not yet published is re-read
     uint32_t excl = 0;
-    for (int64_t j = (int64_t)tile - 1; j >= 0; --j) {
-        const uint32_t* p = status + (uint64_t)j * 256 + d;
-        uint32_t v = ld_relaxed(p);
-        int spins = 0;
-        while ((v & (ST_AGG | ST_INC)) == 0 && spins < OS_SPIN_LIMIT) {
-            if (++spins > 32) __nanosleep(64);
-            v = ld_relaxed(p);
+    bool found = false;
+    for (int64_t j = (int64_t)tile - 1; j >= 0 && !found; j -= OS_LOOKBACK) {
+        uint32_t v[OS_LOOKBACK];
+#pragma unroll
+        for (int q = 0; q < OS_LOOKBACK; ++q) v[q] = (j - q >= 0) ? ld_relaxed(status + (uint64_t)(j - q) * 256 + d) : 0u;
+#pragma unroll
+        for (int q = 0; q < OS_LOOKBACK; ++q) {
+            if (found || j - q < 0) {
+                found = true;
+                continue;
+            }
+            uint32_t x = v[q];
+            int spins = 0;
+            while ((x & (ST_AGG | ST_INC)) == 0 && spins < OS_SPIN_LIMIT) {
+                if (++spins > 32) __nanosleep(64);
+                x = ld_relaxed(status + (uint64_t)(j - q) * 256 + d);
+            }
+            if ((x & (ST_AGG | ST_INC)) == 0) {   // gave up: the result is wrong, the flag says so
+                atomicOr(flags, FLAG_SORT_TIMEOUT);
+                found = true;
+                continue;
+            }
+            excl += x & ST_VAL;
+            if (x & ST_INC) found = true;
         }
-        if ((v & (ST_AGG | ST_INC)) == 0) {   // gave up: the result is wrong, the flag says so
-            atomicOr(flags, FLAG_SORT_TIMEOUT);
-            break;
-        }
-        excl += v & ST_VAL;
-        if (v & ST_INC) break;
     }
     if (tile > 0) st_relaxed(st + d, ST_INC | (excl + cnt));
     s_gdst[d] = gstart + excl;
@@ -248,192 +279,159 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------ scan
+// ------------------------------------------------------------------------------ pair offsets
+//
+// One pass over the depth order: entry i (splat order[i]) gets its first pair slot pair_off[i] =
+// sum of the tile counts of the entries before it (single-pass scan with decoupled look-back), and
+// every segment of DUP_SEG pairs records the entry holding its first pair (seg_start), which is
+// what the duplication uses to balance pairs over blocks.
 
-constexpr int SC_BLOCK = 256;
+constexpr int PO_THREADS = 256;
+constexpr int PO_IPT = 8;
+constexpr int PO_TILE = PO_THREADS * PO_IPT;
 
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* s_warp, uint32_t* total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t inc = x;
+__global__ void __launch_bounds__(PO_THREADS) pair_offsets_kernel(const uint32_t* __restrict__ tiles,
+                                                                  const uint32_t* __restrict__ order,
+                                                                  const uint32_t* __restrict__ n_dev,
+                                                                  uint32_t* __restrict__ pair_off,
+                                                                  uint32_t* __restrict__ seg_start, uint32_t seg_cap,
+                                                                  uint32_t* __restrict__ total, Lookback lb) {
+    __shared__ uint32_t s_ticket;
+    __shared__ unsigned long long s_slot, s_warp[PO_THREADS / 32];
+    const uint32_t b = lb_ticket(lb, &s_ticket);
+    const uint32_t n = *n_dev;
+    const uint64_t base = (uint64_t)b * PO_TILE;
+    if (base >= n && b > 0) return;   // block 0 always runs, so that an empty input still gets total = 0
+    // thread t owns entries base + t IPT + q, q < IPT (contiguous, so its running sum is in order)
+    uint32_t x[PO_IPT];
+    unsigned long long sum = 0;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
-        if (lane >= off) inc += y;
+    for (int q = 0; q < PO_IPT; ++q) {
+        const uint64_t i = base + (uint64_t)threadIdx.x * PO_IPT + q;
+        x[q] = i < n ? __ldg(tiles + __ldg(order + i)) : 0u;
+        sum += x[q];
     }
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < SC_BLOCK / 32 ? s_warp[lane] : 0u;
+    unsigned long long agg;
+    const unsigned long long before = lb_block_scan<PO_THREADS>(sum, s_warp, &agg);
+    const unsigned long long prefix = lb_prefix(lb, b, agg, &s_slot);
+    unsigned long long off = prefix + before;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
-            if (lane >= off) w += y;
+    for (int q = 0; q < PO_IPT; ++q) {
+        const uint64_t i = base + (uint64_t)threadIdx.x * PO_IPT + q;
+        if (i < n) {
+            pair_off[i] = (uint32_t)off;
+            if (x[q]) {   // segments whose first pair lies in [off, off + x)
+                const uint64_t s0 = (off + DUP_SEG - 1) / DUP_SEG, s1 = (off + x[q] - 1) / DUP_SEG;
+                for (uint64_t sg = s0; sg <= s1 && sg < seg_cap; ++sg) seg_start[sg] = (uint32_t)i;
+            }
+            if (i + 1 == n) *total = (uint32_t)min(off + x[q], (unsigned long long)0xffffffffu);
         }
-        if (lane < SC_BLOCK / 32) s_warp[lane] = w;
+        off += x[q];
     }
-    __syncthreads();
-    const uint32_t wprefix = warp ? s_warp[warp - 1] : 0u;
-    *total = s_warp[SC_BLOCK / 32 - 1];
-    __syncthreads();
-    return wprefix + inc - x;
+    if (n == 0 && threadIdx.x == 0) *total = 0;
 }
 
-__device__ __forceinline__ void scan_range(uint32_t n, int G, int b, uint32_t* begin, uint32_t* end) {
-    const uint32_t per = ((n + G - 1) / G + SC_BLOCK - 1) / SC_BLOCK * SC_BLOCK;
-    const uint64_t b0 = (uint64_t)b * per, b1 = b0 + per;
-    *begin = (uint32_t)(b0 < n ? b0 : n);
-    *end = (uint32_t)(b1 < n ? b1 : n);
+cudaError_t launch_pair_offsets(const uint32_t* tiles, const uint32_t* order, const uint32_t* n_dev, int64_t n_cap,
+                                uint32_t* pair_off, uint32_t* seg_start, int64_t seg_cap, uint32_t* total,
+                                const SortWork& w, cudaStream_t s) {
+    const int64_t blocks = std::max<int64_t>(1, (n_cap + PO_TILE - 1) / PO_TILE);
+    if ((size_t)(LB_HEADER_WORDS + 2 * blocks) > w.words) return cudaErrorInvalidValue;
+    Lookback lb{reinterpret_cast<unsigned long long*>(w.work + LB_HEADER_WORDS), w.work, w.flags};
+    cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)blocks), s);
+    if (e != cudaSuccess) return e;
+    pair_offsets_kernel<<<(unsigned)blocks, PO_THREADS, 0, s>>>(tiles, order, n_dev, pair_off, seg_start,
+                                                                (uint32_t)std::min<int64_t>(seg_cap, 0xffffffffLL),
+                                                                total, lb);
+    return cudaGetLastError();
 }
 
-__device__ __forceinline__ uint32_t scan_item(const uint32_t* __restrict__ in, const uint32_t* __restrict__ idx,
-                                              uint32_t i) {
-    return __ldg(in + (idx ? __ldg(idx + i) : i));
-}
-
-__global__ void __launch_bounds__(SC_BLOCK) scan_reduce_kernel(const uint32_t* __restrict__ in,
-                                                               const uint32_t* __restrict__ idx,
-                                                               const uint32_t* __restrict__ n_dev,
-                                                               uint32_t* __restrict__ partial) {
-    __shared__ uint32_t s_warp[SC_BLOCK / 32];
-    uint32_t begin, end;
-    scan_range(*n_dev, gridDim.x, blockIdx.x, &begin, &end);
-    uint32_t sum = 0;
-    for (uint32_t i = begin + threadIdx.x; i < end; i += SC_BLOCK) sum += scan_item(in, idx, i);
-    uint32_t total;
-    block_exclusive_scan(sum, s_warp, &total);
-    if (threadIdx.x == 0) partial[blockIdx.x] = total;
-}
-
-// exclusive scan of the G block partials in place (one block of 1024 threads), total to *total_out
-__global__ void __launch_bounds__(1024) scan_partials_kernel(uint32_t* __restrict__ partial, int G,
-                                                             uint32_t* __restrict__ total_out) {
-    __shared__ uint32_t s_w[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int per = (G + 1023) / 1024;
-    const int i0 = threadIdx.x * per, i1 = min(G, i0 + per);
-    uint32_t sum = 0;
-    for (int i = i0; i < i1; ++i) sum += partial[i];
-    uint32_t inc = sum;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
-        if (lane >= off) inc += y;
-    }
-    if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t x = s_w[lane];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
-            if (lane >= off) x += y;
-        }
-        s_w[lane] = x;
-    }
-    __syncthreads();
-    uint32_t run = (warp ? s_w[warp - 1] : 0u) + inc - sum;
-    for (int i = i0; i < i1; ++i) { const uint32_t x = partial[i]; partial[i] = run; run += x; }
-    if (threadIdx.x == 1023) *total_out = s_w[31];
-}
-
-__global__ void __launch_bounds__(SC_BLOCK) scan_down_kernel(const uint32_t* __restrict__ in,
-                                                             const uint32_t* __restrict__ idx,
-                                                             const uint32_t* __restrict__ n_dev,
-                                                             const uint32_t* __restrict__ partial,
-                                                             uint32_t* __restrict__ out) {
-    __shared__ uint32_t s_warp[SC_BLOCK / 32];
-    uint32_t begin, end;
-    scan_range(*n_dev, gridDim.x, blockIdx.x, &begin, &end);
-    uint32_t run = partial[blockIdx.x];
-    for (uint32_t i0 = begin; i0 < end; i0 += SC_BLOCK) {
-        const uint32_t i = i0 + threadIdx.x;
-        const uint32_t x = i < end ? scan_item(in, idx, i) : 0u;
-        uint32_t total;
-        const uint32_t ex = block_exclusive_scan(x, s_warp, &total);
-        if (i < end) out[i] = run + ex;
-        run += total;
+// seg_start from finished pair offsets (used when the segment array had to grow after the scan)
+__global__ void pair_segments_kernel(const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ order,
+                                     const uint32_t* __restrict__ n_dev, const uint32_t* __restrict__ pair_off,
+                                     uint32_t* __restrict__ seg_start, uint32_t seg_cap) {
+    const uint32_t n = *n_dev;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t off = __ldg(pair_off + i), x = __ldg(tiles + __ldg(order + i));
+        if (!x) continue;
+        const uint64_t s0 = (off + DUP_SEG - 1) / DUP_SEG, s1 = (off + x - 1) / DUP_SEG;
+        for (uint64_t sg = s0; sg <= s1 && sg < seg_cap; ++sg) seg_start[sg] = i;
     }
 }
 
-cudaError_t scan_gathered(const uint32_t* in, const uint32_t* idx, uint32_t* out, const uint32_t* n_dev,
-                          uint32_t* total, const SortWork& w, cudaStream_t s) {
-    scan_reduce_kernel<<<w.scan_blocks, SC_BLOCK, 0, s>>>(in, idx, n_dev, w.partial);
-    scan_partials_kernel<<<1, 1024, 0, s>>>(w.partial, w.scan_blocks, total);
-    scan_down_kernel<<<w.scan_blocks, SC_BLOCK, 0, s>>>(in, idx, n_dev, w.partial, out);
+cudaError_t launch_pair_segments(const uint32_t* tiles, const uint32_t* order, const uint32_t* n_dev,
+                                 const uint32_t* pair_off, uint32_t* seg_start, int64_t seg_cap, int grid,
+                                 cudaStream_t s) {
+    pair_segments_kernel<<<grid, 256, 0, s>>>(tiles, order, n_dev, pair_off, seg_start,
+                                              (uint32_t)std::min<int64_t>(seg_cap, 0xffffffffLL));
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------ duplication
 //
-// Entry i of the depth order (splat m = order[i]) writes its pairs at [pair_off[i], pair_off[i] +
-// tiles[m]): key = global tile id, value = m, tiles in row-major order.  A warp takes 32 consecutive
-// entries and walks each entry's tiles with all its lanes (a few splats cover thousands of tiles).
+// Block b writes pairs [b DUP_SEG, (b + 1) DUP_SEG) (key = global tile id, value = cut position; a
+// splat's tiles in row-major order), fully coalesced.  The entries covering the segment are
+// seg_start[b] .. seg_start[b + 1] (the last one may continue into the next segment); they are
+// staged in shared memory and every pair finds its entry by binary search over their offsets.
+
 __global__ void __launch_bounds__(256) duplicate_kernel(const DevCam* __restrict__ cams, int n_cams,
                                                         const int64_t* __restrict__ cut_offsets, SplatBufs sb,
                                                         const uint32_t* __restrict__ order,
                                                         const uint32_t* __restrict__ n_order,
                                                         const uint32_t* __restrict__ pair_off,
+                                                        const uint32_t* __restrict__ seg_start,
                                                         const uint32_t* __restrict__ n_pairs, int64_t cap_pairs,
                                                         uint32_t* __restrict__ n_pairs_kept,
                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                         uint32_t* __restrict__ flags) {
-    const uint32_t V = *n_order;
-    const int lane = threadIdx.x & 31;
-    const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    __shared__ uint32_t s_off[DUP_SEG + 1], s_m[DUP_SEG + 1], s_xy[DUP_SEG + 1], s_wtx[DUP_SEG + 1],
+        s_tb[DUP_SEG + 1];
+    const uint32_t P = *n_pairs;
+    const uint32_t Pk = (int64_t)P > cap_pairs ? (uint32_t)cap_pairs : P;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const uint32_t P = *n_pairs;
-        *n_pairs_kept = (int64_t)P > cap_pairs ? (uint32_t)cap_pairs : P;
+        *n_pairs_kept = Pk;
         if ((int64_t)P > cap_pairs) atomicOr(flags, FLAG_PAIRS_OVERFLOW);
     }
-    for (uint32_t i0 = warp_global * 32; i0 < V; i0 += n_warps * 32) {
-        const uint32_t i = i0 + lane;
-        uint32_t nt = 0, rx = 0, ry = 0, m = 0, off = 0;
-        int64_t tb = 0;
-        int TX = 0;
-        if (i < V) {
-            m = __ldg(order + i);
-            nt = __ldg(sb.tiles + m);
-            off = __ldg(pair_off + i);
-            if (nt) {
-                const uint2 r = sb.rect[m];
-                rx = r.x;
-                ry = r.y;
-                const int k = find_cam(cut_offsets, n_cams, m);
-                tb = cams[k].tile_base;
-                TX = cams[k].tiles_x;
-            }
+    const uint64_t p0 = (uint64_t)blockIdx.x * DUP_SEG;
+    if (p0 >= Pk) return;
+    const uint64_t p1 = min((uint64_t)Pk, p0 + DUP_SEG);
+    const uint32_t V = *n_order;
+    const uint32_t e0 = seg_start[blockIdx.x];
+    const uint32_t e1 = p1 < Pk ? seg_start[blockIdx.x + 1] : V - 1;
+    if (e0 >= V || e1 < e0) return;   // only after a failed scan (flagged)
+    const int ne = (int)min(min(e1 - e0 + 1, (uint32_t)DUP_SEG + 1), V - e0);
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const uint32_t i = e0 + e;
+        const uint32_t m = __ldg(order + i);
+        const uint2 r = sb.rect[m];
+        const int k = find_cam(cut_offsets, n_cams, m);
+        s_off[e] = __ldg(pair_off + i);
+        s_m[e] = m;
+        s_xy[e] = (r.x & 0xffffu) | (r.y << 16);                                // x0 | y0 << 16
+        s_wtx[e] = ((r.x >> 16) - (r.x & 0xffffu) + 1) | ((uint32_t)cams[k].tiles_x << 16);
+        s_tb[e] = (uint32_t)cams[k].tile_base;
+    }
+    __syncthreads();
+    for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        int lo = 0, hi = ne - 1;   // last entry whose first pair is <= p
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
         }
-        uint32_t todo = __ballot_sync(0xffffffffu, nt != 0);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t snt = __shfl_sync(0xffffffffu, nt, src);
-            const uint32_t srx = __shfl_sync(0xffffffffu, rx, src);
-            const uint32_t sry = __shfl_sync(0xffffffffu, ry, src);
-            const uint32_t sm = __shfl_sync(0xffffffffu, m, src);
-            const uint32_t soff = __shfl_sync(0xffffffffu, off, src);
-            const int64_t stb = __shfl_sync(0xffffffffu, tb, src);
-            const int sTX = __shfl_sync(0xffffffffu, TX, src);
-            const int x0 = srx & 0xffff, x1 = srx >> 16, y0 = sry & 0xffff;
-            const uint32_t w = (uint32_t)(x1 - x0 + 1);
-            for (uint32_t k = lane; k < snt; k += 32) {
-                const uint32_t slot = soff + k;
-                if ((int64_t)slot >= cap_pairs) break;
-                const uint32_t ty = k / w, tx = k - ty * w;
-                keys[slot] = (uint32_t)(stb + (int64_t)(y0 + (int)ty) * sTX + x0 + (int)tx);
-                vals[slot] = sm;
-            }
-        }
+        const uint32_t k = (uint32_t)(p - s_off[lo]);
+        const uint32_t wtx = s_wtx[lo], xy = s_xy[lo];
+        const uint32_t w = wtx & 0xffffu, ty = k / w, tx = k - ty * w;
+        keys[p] = s_tb[lo] + ((xy >> 16) + ty) * (wtx >> 16) + (xy & 0xffffu) + tx;
+        vals[p] = s_m[lo];
     }
 }
 
 cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_offsets, const SplatBufs& sb,
                              const uint32_t* order, const uint32_t* n_order, const uint32_t* pair_off,
-                             const uint32_t* n_pairs, int64_t cap_pairs, uint32_t* n_pairs_kept, uint32_t* keys,
-                             uint32_t* vals, uint32_t* flags, int grid, cudaStream_t s) {
-    duplicate_kernel<<<grid, 256, 0, s>>>(cams, n_cams, cut_offsets, sb, order, n_order, pair_off, n_pairs, cap_pairs,
-                                          n_pairs_kept, keys, vals, flags);
+                             const uint32_t* seg_start, const uint32_t* n_pairs, int64_t cap_pairs,
+                             uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* flags, cudaStream_t s) {
+    const int64_t blocks = std::max<int64_t>(1, (cap_pairs + DUP_SEG - 1) / DUP_SEG);
+    duplicate_kernel<<<(unsigned)blocks, 256, 0, s>>>(cams, n_cams, cut_offsets, sb, order, n_order, pair_off,
+                                                      seg_start, n_pairs, cap_pairs, n_pairs_kept, keys, vals, flags);
     return cudaGetLastError();
 }
 
