@@ -112,8 +112,9 @@ typedef struct {
     int64_t n_pixels;     /* pixels over all cameras                             */
     uint32_t device_flags; /* bit 0: pair capacity exceeded, bit 1: splat capacity
                               exceeded, bit 2: cut truncated to capacity, bit 3: a
-                              sort's wait on an earlier tile timed out (frame
-                              invalid; the context stays usable)                  */
+                              bounded wait of one thread block on another (sort,
+                              scan or blend queue) gave up: the frame is invalid,
+                              the context stays usable                            */
     int64_t n_evals;      /* (pixel, splat) evaluations of the blend's main pass */
     int64_t n_evals_tpass; /* extra evaluations of the transmittance pass of split tiles */
     int64_t n_items;      /* blend work items (tiles, split tiles count once per chunk) */
@@ -266,7 +267,9 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
  * receives t of it (t is a constant); o_n and o_p receive the gradients of their own alpha terms,
  * including d alpha'/d alpha_p = (1/K)(1 - alpha_p)^(1/K - 1); an opacity gradient is zero where
  * its alpha is clamped (Sec. 6.3).  freeze_leaves = 1 leaves the rows of leaf nodes untouched
- * (stop-gradient on leaves, Sec. 6.3).  Errors: STATE if no saved forward state. */
+ * (stop-gradient on leaves, Sec. 6.3).  grads->rot and grads->sh must be 16-byte aligned (they are
+ * updated with 4-float vector reductions).  Errors: STATE if no saved forward state, INVALID_ARG for
+ * NULL or misaligned gradient arrays. */
 h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL_dimages, const h3dgs_grads* grads,
                                    int32_t freeze_leaves);
 

@@ -39,8 +39,9 @@ T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
 // device counter block
 // C_EVALS and C_EVALS_T occupy two words each (64-bit counters)
 // C_NSORTED: splats kept by the depth sort (the visible ones); C_NTSORT: pairs sorted by tile
-enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NITEMS = 5, C_NSORTED = 6,
-       C_NTSORT = 7, C_EVALS = 8, C_EVALS_T = 10, C_COUNT = 12 };
+// C_NITEMS: 3 words (all items, launch list A, launch list B)
+enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NSORTED = 6,
+       C_NTSORT = 7, C_EVALS = 8, C_EVALS_T = 10, C_NITEMS = 12, C_COUNT = 16 };
 
 }  // namespace
 
@@ -52,12 +53,12 @@ struct h3dgs_ctx {
     h3dgs_hierarchy hier{};
     bool has_hier = false;
     DBuf rec, cams, counters;
-    DBuf cut_mask, cut_bc, cut_tot;
+    DBuf cut_mask, cut_bc, cut_tot, cut_lb;
     DBuf s_rec, s_rect, s_key, s_idx, s_key2, s_idx2, s_key3, s_tiles, s_poff;
     DBuf pk0, pv0, pk1, pv1, ranges;
     DBuf sortw, seg_start;
     DBuf T_final, n_contrib, splat_grad;
-    DBuf items, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last;
+    DBuf items, q_prod, q_single, q_cons, queue_sync, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last;
     int64_t item_cap = 0;
     bool fixed = false;
     int64_t cap_splats = 0, cap_pairs = 0;
@@ -202,6 +203,10 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images) {
     a.chunk = ctx->opts.chunk;
     a.item_cap = ctx->item_cap;
     a.items = P<int2>(ctx->items);
+    a.q_prod = P<uint32_t>(ctx->q_prod);
+    a.q_single = P<uint32_t>(ctx->q_single);
+    a.q_cons = P<uint32_t>(ctx->q_cons);
+    a.queue_sync = P<uint32_t>(ctx->queue_sync);
     a.tile_item0 = P<int32_t>(ctx->tile_item0);
     a.tile_nch = P<int32_t>(ctx->tile_nch);
     a.n_items = P<uint32_t>(ctx->counters) + C_NITEMS;
@@ -267,11 +272,12 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
     if (!ctx) return H3DGS_OK;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    DBuf* bufs[] = {&ctx->rec, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot,
+    DBuf* bufs[] = {&ctx->rec, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot, &ctx->cut_lb,
                     &ctx->s_rec, &ctx->s_rect, &ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2,
                     &ctx->s_key3, &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1,
                     &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
-                    &ctx->items, &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
+                    &ctx->items, &ctx->q_prod, &ctx->q_single, &ctx->q_cons, &ctx->queue_sync,
+                    &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
                     &ctx->sc_last};
     for (DBuf* b : bufs)
         if (b->p) cudaFree(b->p);
@@ -386,6 +392,9 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
     CK(ensure(ctx->cut_mask, sizeof(uint32_t) * (size_t)w.words * n_cams), "cut mask");
     CK(ensure(ctx->cut_bc, sizeof(uint32_t) * (size_t)w.blocks * n_cams), "cut counts");
     CK(ensure(ctx->cut_tot, sizeof(int64_t) * (size_t)(n_cams + 1)), "cut totals");
+    w.lb_words = (int64_t)LB_HEADER_WORDS + 2 * ((N + 2047) / 2048) + 64;
+    CK(ensure(ctx->cut_lb, sizeof(uint32_t) * (size_t)w.lb_words), "cut look-back");
+    w.lb_work = P<uint32_t>(ctx->cut_lb);
     w.mask = P<uint32_t>(ctx->cut_mask);
     w.block_counts = P<uint32_t>(ctx->cut_bc);
     w.cam_totals = P<int64_t>(ctx->cut_tot);
@@ -538,6 +547,10 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
         const int NT = o.tile_w * o.tile_h;
         const int64_t icap = ctx->n_tiles + capP / o.chunk + 1;
         CK(ensure(ctx->items, sizeof(int2) * (size_t)icap), "blend items");
+        CK(ensure(ctx->q_prod, sizeof(uint32_t) * (size_t)icap), "blend queue");
+        CK(ensure(ctx->q_cons, sizeof(uint32_t) * (size_t)icap), "blend queue");
+        CK(ensure(ctx->q_single, sizeof(uint32_t) * (size_t)ctx->n_tiles), "blend queue");
+        CK(ensure(ctx->queue_sync, sizeof(uint32_t) * (size_t)(ctx->n_tiles + 1)), "blend queue");
         CK(ensure(ctx->tile_item0, sizeof(int32_t) * (size_t)ctx->n_tiles), "blend items");
         CK(ensure(ctx->tile_nch, sizeof(int32_t) * (size_t)ctx->n_tiles), "blend items");
         CK(ensure(ctx->sc_Tc, sizeof(float) * (size_t)icap * NT), "blend scratch");
@@ -568,6 +581,8 @@ h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL, const h3dgs_
     if (!ctx->saved || !ctx->has_hier) return fail(ctx, H3DGS_ERR_STATE, "render_backward: no saved forward state");
     if (!dL || !g || !g->mean || !g->scale || !g->rot || !g->opacity || !g->sh)
         return fail(ctx, H3DGS_ERR_INVALID_ARG, "render_backward: NULL argument");
+    if (!aligned16(g->rot) || !aligned16(g->sh))
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "render_backward: rot and sh gradients must be 16-byte aligned");
     CK(cudaSetDevice(ctx->device), "set device");
     const int n_cams = (int)ctx->cams_host.size();
     CK(ensure(ctx->splat_grad, sizeof(float) * 12 * (size_t)ctx->splat_cap_used), "splat gradient buffer");

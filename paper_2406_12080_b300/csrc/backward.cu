@@ -169,9 +169,10 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
             const float4 d = __ldg(splat + SPLAT_F4 * (int64_t)s + 3);
             s_id[threadIdx.x] = s;
             s_a[threadIdx.x] = a;
-            s_b[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
+            const float4 bb = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
+            s_b[threadIdx.x] = bb;
             s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
-            s_m[threadIdx.x] = warp_mask<TW, TH>(a.x, a.y, d.x, d.y, ox, oy);
+            s_m[threadIdx.x] = warp_mask<TW, TH>(a, bb.x, d, ox, oy);
         }
         __syncthreads();
         // back to front over the splats whose alpha-floor box reaches this warp's pixels
@@ -202,11 +203,12 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
                 }
                 if (alpha >= afloor) {
                     contrib = true;
-                    const float oma = 1.0f - alpha;
-                    T = T / oma;
+                    // one approximate reciprocal instead of four divisions (values, not decisions)
+                    const float inv = __fdividef(1.0f, 1.0f - alpha);
+                    T = T * inv;
                     const float wgt = alpha * T;
                     gr = g0 * wgt; gg = g1 * wgt; gb = g2 * wgt;
-                    const float dalpha = g0 * (T * c.x - S0 / oma) + g1 * (T * c.y - S1 / oma) + g2 * (T * c.z - S2 / oma);
+                    const float dalpha = g0 * (T * c.x - S0 * inv) + g1 * (T * c.y - S1 * inv) + g2 * (T * c.z - S2 * inv);
                     S0 = fmaf(c.x, wgt, S0); S1 = fmaf(c.y, wgt, S1); S2 = fmaf(c.z, wgt, S2);
                     float dG = 0.0f;
                     const float dan = (b.w == 0.0f) ? dalpha : (1.0f - b.w) * dalpha;
@@ -236,6 +238,12 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
 }
 
 // ---------------------------------------------------------------------------------------- stage 2
+
+// Vector reduction of 4 floats (16-byte aligned address) into global memory.
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
 
 __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const DevCam* __restrict__ cams, int n_cams,
                                                             DevOpts o, const int32_t* __restrict__ cut_ids,
@@ -405,14 +413,23 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         const float wn = use_p ? omt : 1.0f;
         const bool leaf_n = h.child_count[n] == 0;
         const bool write_n = !(freeze_leaves && leaf_n);
-        for (int c = 0; c < NSH; ++c) {
-            const int ch = c % 3;
-            if (col[ch] < 0.0f) continue;
-            const float g = grgb[ch] * Y[c / 3];
-            if (write_n && g != 0.0f) atomicAdd(gout.sh + (int64_t)NSH * n + c, wn * g);
-            if (use_p && g != 0.0f) atomicAdd(gout.sh + (int64_t)NSH * p + c, t * g);
-            const float shv = use_p ? fmaf(t, shp[c], omt * shn[c]) : shn[c];
-            for (int j = 0; j < 3; ++j) ddir[j] += grgb[ch] * shv * dY[c / 3][j];
+        // SH gradient in groups of 4 coefficients, one vector reduction per group and row
+        for (int c0 = 0; c0 < NSH; c0 += 4) {
+            float g4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u, ch = c % 3;
+                const bool live = !(col[ch] < 0.0f);
+                g4[u] = live ? grgb[ch] * Y[c / 3] : 0.0f;
+                if (live) {
+                    const float shv = use_p ? fmaf(t, shp[c], omt * shn[c]) : shn[c];
+                    for (int j = 0; j < 3; ++j) ddir[j] += grgb[ch] * shv * dY[c / 3][j];
+                }
+            }
+            if (g4[0] != 0.0f || g4[1] != 0.0f || g4[2] != 0.0f || g4[3] != 0.0f) {
+                if (write_n) red_add_v4(gout.sh + (int64_t)NSH * n + c0, wn * g4[0], wn * g4[1], wn * g4[2], wn * g4[3]);
+                if (use_p) red_add_v4(gout.sh + (int64_t)NSH * p + c0, t * g4[0], t * g4[1], t * g4[2], t * g4[3]);
+            }
         }
         const float dot = ddir[0] * x + ddir[1] * y + ddir[2] * zz;
         dmu[0] += (ddir[0] - x * dot) / dn;
@@ -424,7 +441,7 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
                 atomicAdd(gout.mean + 3 * (int64_t)n + d, wn * dmu[d]);
                 atomicAdd(gout.scale + 3 * (int64_t)n + d, wn * ds[d]);
             }
-            for (int d = 0; d < 4; ++d) atomicAdd(gout.rot + 4 * (int64_t)n + d, wn * dql[d]);
+            red_add_v4(gout.rot + 4 * (int64_t)n, wn * dql[0], wn * dql[1], wn * dql[2], wn * dql[3]);
             atomicAdd(gout.opacity + n, d_on);
         }
         if (use_p) {
@@ -432,7 +449,7 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
                 atomicAdd(gout.mean + 3 * (int64_t)p + d, t * dmu[d]);
                 atomicAdd(gout.scale + 3 * (int64_t)p + d, t * ds[d]);
             }
-            for (int d = 0; d < 4; ++d) atomicAdd(gout.rot + 4 * (int64_t)p + d, t * dql[d]);
+            red_add_v4(gout.rot + 4 * (int64_t)p, t * dql[0], t * dql[1], t * dql[2], t * dql[3]);
             atomicAdd(gout.opacity + p, d_op);
         }
     }

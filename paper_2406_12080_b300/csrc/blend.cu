@@ -20,6 +20,8 @@
 //   combine   per pixel of a split tile: colour = sum of its chunks, T_final and the last
 //             contributor from the chunk where the walk stopped.
 // A chunk whose T_in is already below t_min adds nothing (the walk stopped in an earlier chunk).
+#include <algorithm>
+
 #include "internal.cuh"
 #include "lookback.cuh"
 
@@ -89,8 +91,14 @@ __device__ __forceinline__ TileGeom<TW, TH> tile_geom(const DevCam* __restrict__
 
 // ------------------------------------------------------------------------------------ plan
 
-// Chunk counts per tile, their exclusive scan (single pass, decoupled look-back) and the (tile, chunk)
-// item list.  Block b takes tiles [b PL_TILE, (b + 1) PL_TILE), PL_IPT contiguous tiles per thread.
+// The plan: chunk counts per tile, their exclusive scan (single pass, decoupled look-back), the full
+// (tile, chunk) item list (used by the combine and the adjoint) and the work queue of the blend:
+//   producers  chunks 0 .. nch - 2 of split tiles: chunk 0 is blended from T = 1 and hands on its
+//              (1 - alpha) product, the middle chunks compute their product only (transmittance pass);
+//   singles    tiles of one chunk;
+//   consumers  chunks 1 .. nch - 1 of split tiles, blended from the product of the earlier chunks.
+// Per tile the scan carries X = nch - 1 (split tiles) and Y = [nch == 1] packed in one word; the item
+// offset is t + prefix(X), the producer and consumer offsets prefix(X), the single offset prefix(Y).
 constexpr int PL_THREADS = 256;
 constexpr int PL_IPT = 4;
 constexpr int PL_TILE = PL_THREADS * PL_IPT;
@@ -99,7 +107,11 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __re
                                                                 int chunk, int32_t* __restrict__ tile_item0,
                                                                 int32_t* __restrict__ tile_nch,
                                                                 int2* __restrict__ items, int64_t item_cap,
-                                                                uint32_t* __restrict__ n_items, Lookback lb) {
+                                                                uint32_t* __restrict__ q_prod,
+                                                                uint32_t* __restrict__ q_single,
+                                                                uint32_t* __restrict__ q_cons,
+                                                                uint32_t* __restrict__ counts /* items, X, Y */,
+                                                                Lookback lb) {
     __shared__ uint32_t s_ticket;
     __shared__ unsigned long long s_slot, s_warp[PL_THREADS / 32];
     const uint32_t b = lb_ticket(lb, &s_ticket);
@@ -115,23 +127,42 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __re
             const int2 r = ranges[t];
             const int len = r.y - r.x;
             nch[q] = len <= chunk ? 1 : (len + chunk - 1) / chunk;
+            sum += ((unsigned long long)(nch[q] - 1) << 31) | (unsigned long long)(nch[q] == 1);
         }
-        sum += nch[q];
     }
     unsigned long long agg;
     const unsigned long long before = lb_block_scan<PL_THREADS>(sum, s_warp, &agg);
-    unsigned long long off = lb_prefix(lb, b, agg, &s_slot) + before;
+    const unsigned long long pre = lb_prefix(lb, b, agg, &s_slot) + before;
+    int64_t offX = (int64_t)(pre >> 31), offY = (int64_t)(pre & 0x7fffffffull);
 #pragma unroll
     for (int q = 0; q < PL_IPT; ++q) {
         const int64_t t = base + (int64_t)threadIdx.x * PL_IPT + q;
         if (t < n_tiles) {
-            tile_item0[t] = (int32_t)off;
-            tile_nch[t] = nch[q];
-            for (int c = 0; c < nch[q]; ++c)
-                if ((int64_t)off + c < item_cap) items[off + c] = make_int2((int)t, c);
-            if (t + 1 == n_tiles) *n_items = (uint32_t)min((long long)(off + nch[q]), (long long)item_cap);
+            const int n = nch[q];
+            const int64_t offF = t + offX;
+            tile_item0[t] = (int32_t)offF;
+            tile_nch[t] = n;
+            for (int c = 0; c < n; ++c) {
+                const int64_t it = offF + c;
+                if (it >= item_cap) break;
+                items[it] = make_int2((int)t, c);
+                if (n == 1) q_single[offY] = (uint32_t)it;
+                else {
+                    if (c < n - 1) q_prod[offX + c] = (uint32_t)it;
+                    if (c >= 1) q_cons[offX + c - 1] = (uint32_t)it;
+                }
+            }
+            if (t + 1 == n_tiles) {
+                const int64_t X = offX + n - 1, Y = offY + (n == 1);
+                const int64_t F = n_tiles + X;
+                const bool fits = F <= item_cap;
+                counts[0] = (uint32_t)min(F, item_cap);
+                counts[1] = fits ? (uint32_t)X : 0u;   // an overflowing plan blends nothing (flagged)
+                counts[2] = fits ? (uint32_t)Y : 0u;
+            }
+            offX += n - 1;
+            offY += (n == 1);
         }
-        off += nch[q];
     }
 }
 
@@ -139,64 +170,36 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __re
 
 // Scratch per (item, pixel), struct-of-arrays over pixels: Tc, C0, C1, C2, Tend, last.
 struct Scratch {
-    float* Tc;     // product of (1 - alpha) over the chunk (pass T)
+    float* Tc;     // product of (1 - alpha) over the chunk's contributors (0 once the walk stopped)
     float* C;      // [3] colour of the chunk
     float* Tend;   // T after the chunk's walk (stop applied)
     int32_t* last; // list position (within the tile) after the chunk's last contributor, or -1
 };
 
+// Walk of one item over list entries [begin, end).  MAIN: the exact skip/stop rules with colour;
+// otherwise the transmittance pass (product of (1 - alpha) over contributors, no colour; a pixel is
+// finished once T < t_min, after which nothing it could add matters).  Branch-free per entry: the
+// alpha of every live lane is computed and applied through selects.
 template <int TW, int TH, bool MAIN>
-__global__ void __launch_bounds__(TW * TH) blend_items_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
-                                                              const int2* __restrict__ ranges,
-                                                              const uint32_t* __restrict__ list,
-                                                              const float4* __restrict__ splat,
-                                                              const int2* __restrict__ items,
-                                                              const uint32_t* __restrict__ n_items,
-                                                              const int32_t* __restrict__ tile_item0,
-                                                              const int32_t* __restrict__ tile_nch, int chunk,
-                                                              Scratch sc, float* __restrict__ images,
-                                                              float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
-                                                              unsigned long long* __restrict__ n_evals) {
+__device__ __forceinline__ void blend_walk(const TileGeom<TW, TH>& g, const uint32_t* __restrict__ list,
+                                           const float4* __restrict__ splat, int begin, int end, int list0,
+                                           float clampv, float afloor, float tmin, float4* s_a, float4* s_b,
+                                           float4* s_c, uint32_t* s_m, float& T, float& C0, float& C1, float& C2,
+                                           int& last, bool& done, unsigned int& evals) {
     constexpr int NT = TW * TH;
-    __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
-    __shared__ uint32_t s_m[NT];
-    __shared__ unsigned int s_evals;
-    const uint32_t item = blockIdx.x;
-    if (item >= *n_items) return;
-    const int2 it = items[item];
-    const int64_t tile = it.x;
-    const int nch = tile_nch[tile];
-    // pass T only for split tiles, and not for their last chunk (nobody reads its product)
-    if (!MAIN && (nch == 1 || it.y == nch - 1)) return;
-    if (threadIdx.x == 0) s_evals = 0;
-    const TileGeom<TW, TH> g = tile_geom<TW, TH>(cams, n_cams, tile);
-    const int2 r = ranges[tile];
-    const int begin = r.x + it.y * chunk;
-    const int end = nch == 1 ? r.y : min(r.y, begin + chunk);
-    const int64_t slot = (int64_t)item * NT + threadIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float clampv = o.alpha_clamp, afloor = o.alpha_floor, tmin = o.t_min;
-    float T = 1.0f;
-    if (MAIN && nch > 1) {
-        // incoming transmittance: product of the earlier chunks' (1 - alpha) products
-        const int64_t i0 = tile_item0[tile];
-        for (int c = 0; c < it.y; ++c) T = fmul(T, sc.Tc[(i0 + c) * NT + threadIdx.x]);
-    }
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    int last = -1;
-    unsigned int evals = 0;
-    bool done = !g.inside || (MAIN && T < tmin);
     for (int b0 = begin; b0 < end; b0 += NT) {
         if (__syncthreads_count(done) == NT) break;
         const int n = min(NT, end - b0);
         if ((int)threadIdx.x < n) {
             const uint32_t s = __ldg(list + b0 + threadIdx.x);
             const float4 a = __ldg(splat + SPLAT_F4 * (int64_t)s);
+            const float4 bb = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
             const float4 d = __ldg(splat + SPLAT_F4 * (int64_t)s + 3);
             s_a[threadIdx.x] = a;
-            s_b[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
+            s_b[threadIdx.x] = bb;
             s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
-            s_m[threadIdx.x] = warp_mask<TW, TH>(a.x, a.y, d.x, d.y, g.ox, g.oy);
+            s_m[threadIdx.x] = warp_mask<TW, TH>(a, bb.x, d, g.ox, g.oy);
         }
         __syncthreads();
         if (__any_sync(0xffffffffu, !done)) {
@@ -206,37 +209,130 @@ __global__ void __launch_bounds__(TW * TH) blend_items_kernel(const DevCam* __re
                 while (bits) {
                     const int j = base + __ffs(bits) - 1;
                     bits &= bits - 1;
-                    if (done) continue;
-                    ++evals;
+                    evals += !done;
                     const float alpha = pair_alpha(g.px, g.py, s_a[j], s_b[j], &s_c[j], clampv);
-                    if (alpha < afloor) continue;
+                    const bool live = !done && alpha >= afloor;
                     const float Tn = fmul(T, fsub(1.0f, alpha));
-                    if (!MAIN) {                            // pass T: no stop, but nothing matters below t_min
-                        T = Tn;
-                        if (T < tmin) done = true;
-                        continue;
+                    if (!__any_sync(0xffffffffu, live)) continue;   // no lane of the warp takes it
+                    if (MAIN) {
+                        const bool stop = live && Tn < tmin;
+                        const bool apply = live && !stop;
+                        done = done || stop;
+                        const float w = apply ? alpha * T : 0.0f;
+                        const float4 c = s_c[j];
+                        C0 = fmaf(c.x, w, C0);
+                        C1 = fmaf(c.y, w, C1);
+                        C2 = fmaf(c.z, w, C2);
+                        T = apply ? Tn : T;
+                        last = apply ? b0 + j + 1 - list0 : last;
+                    } else {
+                        T = live ? Tn : T;
+                        done = done || (live && Tn < tmin);
                     }
-                    if (Tn < tmin) { done = true; continue; }
-                    const float w = alpha * T;
-                    const float4 c = s_c[j];
-                    C0 = fmaf(c.x, w, C0);
-                    C1 = fmaf(c.y, w, C1);
-                    C2 = fmaf(c.z, w, C2);
-                    T = Tn;
-                    last = b0 + j + 1 - r.x;
                 }
                 if (__all_sync(0xffffffffu, done)) break;
             }
         }
     }
-    for (int off = 16; off > 0; off >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, off);
-    if (lane == 0) atomicAdd(&s_evals, evals);
+}
+
+// The blend: one CTA per queue entry, in ticket order (a CTA holding ticket k is running, and every
+// entry before k has been taken by a running CTA).  Producers never wait; a consumer waits until the
+// producers of its tile have published their products (per-tile counter, bounded wait), which were
+// all taken before it.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH) blend_queue_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
+                                                              const int2* __restrict__ ranges,
+                                                              const uint32_t* __restrict__ list,
+                                                              const float4* __restrict__ splat,
+                                                              const int2* __restrict__ items,
+                                                              const uint32_t* __restrict__ q_prod,
+                                                              const uint32_t* __restrict__ q_single,
+                                                              const uint32_t* __restrict__ q_cons,
+                                                              const uint32_t* __restrict__ counts,
+                                                              const int32_t* __restrict__ tile_item0,
+                                                              const int32_t* __restrict__ tile_nch, int chunk,
+                                                              Scratch sc, uint32_t* __restrict__ ticket,
+                                                              uint32_t* __restrict__ tile_done,
+                                                              float* __restrict__ images,
+                                                              float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
+                                                              unsigned long long* __restrict__ n_evals,
+                                                              uint32_t* __restrict__ flags) {
+    constexpr int NT = TW * TH;
+    __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
+    __shared__ uint32_t s_m[NT];
+    __shared__ unsigned int s_evals[2];
+    __shared__ uint32_t s_k;
+    if (threadIdx.x == 0) s_k = atomicAdd(ticket, 1u);
+    if (threadIdx.x < 2) s_evals[threadIdx.x] = 0;
     __syncthreads();
-    if (threadIdx.x == 0 && n_evals) atomicAdd(n_evals, (unsigned long long)s_evals);
-    if (!MAIN) {
-        sc.Tc[slot] = T;
-        return;
+    const uint32_t k = s_k;
+    const uint32_t X = counts[1], Y = counts[2];
+    int role;   // 0: producer, 1: single, 2: consumer
+    uint32_t item;
+    if (k < X) { role = 0; item = q_prod[k]; }
+    else if (k < X + Y) { role = 1; item = q_single[k - X]; }
+    else if (k < 2 * X + Y) { role = 2; item = q_cons[k - X - Y]; }
+    else return;
+    const int2 it = items[item];
+    const int64_t tile = it.x;
+    const int nch = tile_nch[tile];
+    const bool main_pass = role != 0 || it.y == 0;
+    const TileGeom<TW, TH> g = tile_geom<TW, TH>(cams, n_cams, tile);
+    const int2 r = ranges[tile];
+    const int begin = r.x + it.y * chunk;
+    const int end = nch == 1 ? r.y : min(r.y, begin + chunk);
+    const int64_t slot = (int64_t)item * NT + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    float T = 1.0f;
+    if (role == 2) {
+        // wait for the tile's nch - 1 producers, then T_in = product of the earlier chunks' products
+        if (threadIdx.x == 0) {
+            const uint32_t want = (uint32_t)(nch - 1);
+            uint32_t v;
+            int spins = 0;
+            do {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(tile_done + tile) : "memory");
+                if (v >= want) break;
+                if (++spins > 32) __nanosleep(128);
+            } while (spins < QUEUE_SPIN_LIMIT);
+            if (v < want) atomicOr(flags, FLAG_WAIT_TIMEOUT);
+        }
+        __syncthreads();
+        const int64_t i0 = tile_item0[tile];
+        for (int c = 0; c < it.y; ++c) T = fmul(T, __ldcg(sc.Tc + (i0 + c) * NT + threadIdx.x));
     }
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    int last = -1;
+    unsigned int evals = 0;
+    bool done = !g.inside || T < o.t_min;
+    if (main_pass)
+        blend_walk<TW, TH, true>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min, s_a, s_b,
+                                 s_c, s_m, T, C0, C1, C2, last, done, evals);
+    else
+        blend_walk<TW, TH, false>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min, s_a, s_b,
+                                  s_c, s_m, T, C0, C1, C2, last, done, evals);
+    for (int off = 16; off > 0; off >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, off);
+    if (lane == 0) atomicAdd(&s_evals[main_pass ? 0 : 1], evals);
+    if (role == 0) {
+        // the product handed to the later chunks: 0 once the first chunk's walk stopped
+        if (!main_pass) sc.Tc[slot] = T;
+        else {
+            sc.C[3 * slot + 0] = C0;
+            sc.C[3 * slot + 1] = C1;
+            sc.C[3 * slot + 2] = C2;
+            sc.Tend[slot] = T;
+            sc.last[slot] = last;
+            sc.Tc[slot] = (done && g.inside) ? 0.0f : T;
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(tile_done + tile, 1u);
+    } else {
+        __syncthreads();
+    }
+    if (threadIdx.x < 2 && n_evals && s_evals[threadIdx.x]) atomicAdd(n_evals + threadIdx.x, (unsigned long long)s_evals[threadIdx.x]);
+    if (role == 0) return;
     if (nch > 1) {
         sc.C[3 * slot + 0] = C0;
         sc.C[3 * slot + 1] = C1;
@@ -306,22 +402,21 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     Lookback lb{reinterpret_cast<unsigned long long*>(a.work + LB_HEADER_WORDS), a.work, a.flags};
     blend_plan_kernel<<<(unsigned)pblocks, PL_THREADS, 0, s>>>(a.ranges, a.n_tiles, a.chunk, a.tile_item0, a.tile_nch,
-                                                               a.items, a.item_cap, a.n_items, lb);
+                                                               a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons, a.n_items,
+                                                               lb);
     Scratch sc{a.scratch_Tc, a.scratch_C, a.scratch_Tend, a.scratch_last};
-    unsigned long long* ev_main = a.n_evals;
-    unsigned long long* ev_tpass = a.n_evals ? a.n_evals + 1 : nullptr;
-    const unsigned grid = (unsigned)a.item_cap;
+    e = cudaMemsetAsync(a.queue_sync, 0, sizeof(uint32_t) * (size_t)(a.n_tiles + 1), s);
+    if (e != cudaSuccess) return e;
+    // queue length 2 X + Y <= 2 item_cap - n_tiles
+    const unsigned gq = (unsigned)std::max<int64_t>(1, 2 * a.item_cap - a.n_tiles);
     const unsigned tg = (unsigned)a.n_tiles;
 #define BL(TWV, THV)                                                                                                  \
     do {                                                                                                              \
-        blend_items_kernel<TWV, THV, false><<<grid, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list,       \
-                                                                       a.splat, a.items, a.n_items, a.tile_item0,     \
-                                                                       a.tile_nch, a.chunk, sc, a.images, a.T_final,  \
-                                                                       a.n_contrib, ev_tpass);                        \
-        blend_items_kernel<TWV, THV, true><<<grid, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list,        \
-                                                                      a.splat, a.items, a.n_items, a.tile_item0,      \
-                                                                      a.tile_nch, a.chunk, sc, a.images, a.T_final,   \
-                                                                      a.n_contrib, ev_main);                          \
+        blend_queue_kernel<TWV, THV><<<gq, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat,       \
+                                                              a.items, a.q_prod, a.q_single, a.q_cons, a.n_items,     \
+                                                              a.tile_item0, a.tile_nch, a.chunk, sc, a.queue_sync,    \
+                                                              a.queue_sync + 1, a.images, a.T_final, a.n_contrib,     \
+                                                              a.n_evals, a.flags);                                    \
         blend_combine_kernel<TWV, THV><<<tg, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.n_tiles, a.tile_item0,       \
                                                                 a.tile_nch, sc, a.images, a.T_final, a.n_contrib);    \
     } while (0)

@@ -10,6 +10,7 @@
 //   pass 2  scans of the counts (per camera over blocks, then over cameras);
 //   pass 3  ordered compaction: ids in ascending order, t recomputed for the selected nodes.
 #include "internal.cuh"
+#include "lookback.cuh"
 
 namespace h3dgs {
 
@@ -218,8 +219,90 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_write_kernel(const float4* __re
     }
 }
 
+// One camera: a single pass with decoupled look-back.  Block b (ticket order) tests nodes
+// [b CS_TILE, (b + 1) CS_TILE), CS_IPT per thread at stride CUT_BLOCK (coalesced), counts the
+// selected ones per (step, warp), obtains the count of all earlier blocks and writes its ids in
+// ascending order with their weights.  The last block writes the offsets and the total.
+constexpr int CS_IPT = 8;
+constexpr int CS_TILE = CUT_BLOCK * CS_IPT;
+
+__global__ void __launch_bounds__(CUT_BLOCK) cut_single_kernel(const float4* __restrict__ rec, int64_t n,
+                                                               const DevCam* __restrict__ cams, int64_t capacity,
+                                                               int32_t* __restrict__ cut_ids, float* __restrict__ cut_t,
+                                                               int64_t* __restrict__ cut_offsets,
+                                                               int64_t* __restrict__ cam_totals,
+                                                               uint32_t* __restrict__ flags, Lookback lb) {
+    __shared__ uint32_t s_ticket;
+    __shared__ unsigned long long s_slot, s_warp[CUT_BLOCK / 32];
+    __shared__ uint32_t s_cnt[CS_IPT][CUT_BLOCK / 32];
+    const uint32_t b = lb_ticket(lb, &s_ticket);
+    const int64_t base = (int64_t)b * CS_TILE;
+    if (base >= n) return;
+    const DevCam cam = cams[0];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t word[CS_IPT];
+    float tw[CS_IPT];
+#pragma unroll
+    for (int q = 0; q < CS_IPT; ++q) {
+        const int64_t v = base + q * CUT_BLOCK + threadIdx.x;
+        bool sel = false;
+        tw[q] = 0.0f;
+        if (v < n) {
+            const float4 lo = __ldg(rec + 2 * v), hi = __ldg(rec + 2 * v + 1);
+            const int32_t p = __float_as_int(lo.w);
+            float4 plo = lo, phi = hi;
+            if (p >= 0) {
+                plo = __ldg(rec + 2 * (int64_t)p);
+                phi = __ldg(rec + 2 * (int64_t)p + 1);
+            }
+            float en, ep;
+            sel = cut_test(cam, lo, hi, plo, phi, p >= 0, &en, &ep);
+            if (sel && p >= 0) tw[q] = parent_weight(cam.tau, en, ep);
+        }
+        word[q] = __ballot_sync(0xffffffffu, sel);
+        if (lane == 0) s_cnt[q][warp] = __popc(word[q]);
+    }
+    __syncthreads();
+    // exclusive scan of the (step, warp) counts in step-major order = ascending node order
+    unsigned long long mine = 0;
+    if (threadIdx.x < CS_IPT * (CUT_BLOCK / 32)) mine = (&s_cnt[0][0])[threadIdx.x];
+    unsigned long long agg;
+    const unsigned long long ex = lb_block_scan<CUT_BLOCK>(mine, s_warp, &agg);
+    if (threadIdx.x < CS_IPT * (CUT_BLOCK / 32)) (&s_cnt[0][0])[threadIdx.x] = (uint32_t)ex;
+    const unsigned long long prefix = lb_prefix(lb, b, agg, &s_slot);   // ends with a barrier
+    const uint32_t lmask = (1u << lane) - 1u;
+#pragma unroll
+    for (int q = 0; q < CS_IPT; ++q) {
+        if ((word[q] >> lane) & 1u) {
+            const int64_t pos = (int64_t)(prefix + s_cnt[q][warp]) + __popc(word[q] & lmask);
+            if (pos < capacity) {
+                cut_ids[pos] = (int32_t)(base + q * CUT_BLOCK + threadIdx.x);
+                if (cut_t) cut_t[pos] = tw[q];
+            }
+        }
+    }
+    if (base + CS_TILE >= n && threadIdx.x == 0) {   // the last block: offsets and total
+        const int64_t total = (int64_t)(prefix + agg);
+        cam_totals[0] = 0;
+        cam_totals[1] = total;
+        cut_offsets[0] = 0;
+        cut_offsets[1] = total < capacity ? total : capacity;
+        if (total > capacity) atomicOr(flags, FLAG_CUT_TRUNCATED);
+    }
+}
+
 cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const CutWork& w, int32_t* cut_ids,
                        float* cut_t, int64_t* cut_offsets, int64_t capacity, uint32_t* flags, cudaStream_t s) {
+    if (n_cams == 1 && w.lb_work) {
+        const int64_t blocks = (h.n + CS_TILE - 1) / CS_TILE;
+        if ((int64_t)LB_HEADER_WORDS + 2 * blocks > w.lb_words) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(w.lb_work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)blocks), s);
+        if (e != cudaSuccess) return e;
+        Lookback lb{reinterpret_cast<unsigned long long*>(w.lb_work + LB_HEADER_WORDS), w.lb_work, flags};
+        cut_single_kernel<<<(unsigned)blocks, CUT_BLOCK, 0, s>>>(h.rec, h.n, cams, capacity, cut_ids, cut_t, cut_offsets,
+                                                                 w.cam_totals, flags, lb);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(uint32_t) * (size_t)n_cams;
     cut_mark_kernel<<<w.blocks, CUT_BLOCK, smem, s>>>(h.rec, h.n, cams, n_cams, w.chunk, w.words, w.mask,
                                                       w.block_counts);

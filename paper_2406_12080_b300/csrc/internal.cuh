@@ -12,12 +12,14 @@ constexpr int NSH = 48;          // degree-3 SH: 16 basis functions x 3 channels
 constexpr int NINTERP = 62;      // exported interpolated row: mean 3, scale 3, rot 4, sh 48, o_n, o_p, t, K
 constexpr int MAX_CAMS = 4096;
 constexpr int CAM_BATCH = 32;    // cameras per set-up launch (passed by value)
+constexpr size_t LB_HEADER_WORDS = 64;   // look-back workspaces: ticket word(s), then 2 words per block
 
 // Device flag bits (ctx->d_flags)
 constexpr uint32_t FLAG_PAIRS_OVERFLOW = 1u << 0;
 constexpr uint32_t FLAG_SPLATS_OVERFLOW = 1u << 1;
 constexpr uint32_t FLAG_CUT_TRUNCATED = 1u << 2;
-constexpr uint32_t FLAG_SORT_TIMEOUT = 1u << 3;   // a radix-sort look-back wait gave up (result invalid)
+constexpr uint32_t FLAG_WAIT_TIMEOUT = 1u << 3;   // a bounded wait on another block gave up (frame invalid)
+constexpr int QUEUE_SPIN_LIMIT = 1 << 22;          // polls of the blend queue's per-tile counter
 
 // Per-camera data on the device.  Raw fields come from h3dgs_camera; the derived floats are
 // computed on the device in a fixed fp32 order (camera_setup kernel); integer bookkeeping
@@ -106,20 +108,51 @@ __device__ __forceinline__ void tile_pixel(int tid, int& lx, int& ly) {
     ly = (w / WX) * 4 + (l >> 3);
 }
 
-// Bit w set iff the splat's alpha-floor box [u +- hx] x [v +- hy] reaches a pixel centre of warp w's
-// block in the tile with pixel origin (ox, oy).  Outside the box alpha < alpha_floor for every
-// pixel (the box is the inflated bounding box of the level set o_max G = alpha_floor), so a warp
-// whose bit is clear would skip the splat anyway.  hx < 0 marks a splat that never reaches the floor.
+// Bit w set if the splat can reach alpha_floor at a pixel centre of warp w's 8x4 block in the tile
+// with pixel origin (ox, oy); a clear bit means alpha < alpha_floor at every pixel of the block, so
+// the warp would skip the splat anyway.  a = {u, v, ca, cb}, cc = the third conic term (pre-scaled:
+// the exponent is p2 = ca dx^2 + cb dx dy + cc dy^2), d = {hx, hy, rz, 0}: hx, hy are the inflated
+// half-widths of the bounding box of the level set o_max 2^p2 = alpha_floor and rz = log2(o_max /
+// alpha_floor) inflated by 2% + 0.02; hx < 0 marks a splat that never reaches the floor.  A block
+// passing the box test is kept only if the minimum of q = -p2 over the block (a convex quadratic:
+// the centre if inside, else the best point of the four edges) is at most rz.
 template <int TW, int TH>
-__device__ __forceinline__ uint32_t warp_mask(float u, float v, float hx, float hy, int ox, int oy) {
+__device__ __forceinline__ uint32_t warp_mask(const float4 a, float cc, const float4 d, int ox, int oy) {
+    const float hx = d.x, hy = d.y;
     if (!(hx >= 0.0f)) return 0u;
     constexpr int NW = TW * TH / 32, WX = TW / 8;
+    const float u = a.x, v = a.y;
+    const float qa = -a.z, qb = -a.w, qc = -cc, rz = d.z;
+    // edge minimisers use approximate reciprocals: a slightly moved point on the edge changes q only
+    // to second order, far inside the 2% margin of rz
+    const float kx = -qb * __fdividef(0.5f, qc), ky = -qb * __fdividef(0.5f, qa);
     uint32_t m = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         const float x0 = (float)(ox + (w % WX) * 8) + 0.5f, x1 = x0 + 7.0f;
         const float y0 = (float)(oy + (w / WX) * 4) + 0.5f, y1 = y0 + 3.0f;
-        if (u + hx >= x0 && u - hx <= x1 && v + hy >= y0 && v - hy <= y1) m |= 1u << w;
+        if (!(u + hx >= x0 && u - hx <= x1 && v + hy >= y0 && v - hy <= y1)) continue;
+        if (u >= x0 && u <= x1 && v >= y0 && v <= y1) {
+            m |= 1u << w;
+            continue;
+        }
+        const float dx0 = x0 - u, dx1 = x1 - u, dy0 = y0 - v, dy1 = y1 - v;
+        float qmin = __int_as_float(0x7f800000);
+        // vertical edges x = x0, x1: best dy = clamp(-qb dx / (2 qc))
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float dx = e ? dx1 : dx0;
+            const float dy = fminf(fmaxf(kx * dx, dy0), dy1);
+            qmin = fminf(qmin, qa * dx * dx + qb * dx * dy + qc * dy * dy);
+        }
+        // horizontal edges y = y0, y1: best dx = clamp(-qb dy / (2 qa))
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float dy = e ? dy1 : dy0;
+            const float dx = fminf(fmaxf(ky * dy, dx0), dx1);
+            qmin = fminf(qmin, qa * dx * dx + qb * dx * dy + qc * dy * dy);
+        }
+        if (!(qmin > rz)) m |= 1u << w;   // NaN keeps the block
     }
     return m;
 }
@@ -145,6 +178,8 @@ struct CutWork {
     int blocks;              // G
     int64_t chunk;           // nodes per block
     int64_t words;           // mask words per camera
+    uint32_t* lb_work;       // single-camera pass: look-back workspace (NULL: use the three-pass path)
+    int64_t lb_words;
 };
 cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const CutWork& w, int32_t* cut_ids,
                        float* cut_t, int64_t* cut_offsets, int64_t capacity, uint32_t* flags, cudaStream_t s);
@@ -152,7 +187,7 @@ cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const C
 // preprocess.cu
 constexpr int SPLAT_F4 = 4;      // float4 per splat record
 struct SplatBufs {
-    float4* rec;           // [cap][4]: {u, v, ca, cb}, {cc, on', op', t}, {r, g, b, K}, {hx, hy, 0, 0}
+    float4* rec;           // [cap][4]: {u, v, ca, cb}, {cc, on', op', t}, {r, g, b, K}, {hx, hy, rz, 0}
     uint2* rect;           // [cap]: (x0 | x1 << 16, y0 | y1 << 16)
     uint32_t* depth_key;   // [cap] fp32 depth bits, 0xffffffff when culled
     uint32_t* tiles;       // [cap] tiles touched (0 when culled)
@@ -172,7 +207,7 @@ struct SortWork {
     uint32_t* work;         // radix_work_words(n_cap) words: header, then look-back words per pass and tile
     size_t words;
     int num_sms;
-    uint32_t* flags;        // device flag word (FLAG_SORT_TIMEOUT)
+    uint32_t* flags;        // device flag word (FLAG_WAIT_TIMEOUT)
 };
 size_t radix_work_words(int64_t n_cap);
 // Stable LSD radix sort of n = *n_dev <= n_cap key/value pairs on key bits [0, bits).  The first pass
@@ -185,7 +220,6 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
 // Pair offsets of the depth order: pair_off[i] = sum of tiles[order[j]] over j < i (i < *n_dev <= n_cap),
 // *total = the sum; seg_start[s] = the entry holding pair s DUP_SEG (for s < seg_cap).
 constexpr int DUP_SEG = 1024;         // pairs per duplication block
-constexpr size_t LB_HEADER_WORDS = 64;
 cudaError_t launch_pair_offsets(const uint32_t* tiles, const uint32_t* order, const uint32_t* n_dev, int64_t n_cap,
                                 uint32_t* pair_off, uint32_t* seg_start, int64_t seg_cap, uint32_t* total,
                                 const SortWork& w, cudaStream_t s);
@@ -211,13 +245,17 @@ struct BlendArgs {
     DevOpts o;
     const int2* ranges;
     const uint32_t* list;
+    uint32_t* q_prod;             // blend queue: producer items (chunks 0 .. nch - 2 of split tiles)
+    uint32_t* q_single;           // blend queue: single-chunk tiles
+    uint32_t* q_cons;             // blend queue: consumer items (chunks 1 .. nch - 1 of split tiles)
+    uint32_t* queue_sync;         // [1 + n_tiles]: queue ticket, per-tile finished-producer counters
     const float4* splat;
     int chunk;
     int64_t item_cap;
     int2* items;
     int32_t* tile_item0;
     int32_t* tile_nch;
-    uint32_t* n_items;
+    uint32_t* n_items;            // [3]: items, producers X, singles Y
     float* scratch_Tc;
     float* scratch_C;
     float* scratch_Tend;

@@ -5,7 +5,7 @@
 // a ticket earlier and are therefore running.  Each block publishes its aggregate, then warp 0 reads
 // the status words of up to 32 earlier blocks at a time, newest first, until it meets an inclusive
 // prefix.  Every wait on a word that is not yet published is bounded; a wait that gives up sets
-// FLAG_SORT_TIMEOUT in the device flag word and the result is invalid (the context stays usable).
+// FLAG_WAIT_TIMEOUT in the device flag word and the result is invalid (the context stays usable).
 #pragma once
 
 #include "internal.cuh"
@@ -60,7 +60,7 @@ __device__ __forceinline__ unsigned long long lb_prefix(const Lookback& lb, uint
                     v = lb_load(lb.status + k);
                 }
                 if ((v >> 62) == 0) {
-                    atomicOr(lb.flags, FLAG_SORT_TIMEOUT);
+                    atomicOr(lb.flags, FLAG_WAIT_TIMEOUT);
                     v = LB_INC;
                 }
             }

@@ -243,17 +243,19 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
         // alpha-floor box: alpha <= o_max G, and o_max G >= floor only inside the ellipse
         // d^T Sigma'_f^-1 d <= 2 ln(o_max / floor), whose bounding box has half-widths
         // sqrt(2 ln(o_max / floor) Sigma'_f,xx) and likewise in y; inflated by 1% + 0.01 px
+        // in the blend's log2 units the same level set is -p2 = log2(o_max / floor) = r2 log2(e) / 2
         const float omax = fmaxf(on, op);
-        float hx = -1.0f, hy = -1.0f;
+        float hx = -1.0f, hy = -1.0f, rz = -1.0f;
         if (omax > o.alpha_floor) {
             const float r2 = 2.0f * logf(omax / o.alpha_floor);
             hx = sqrtf(r2 * sxx) * 1.01f + 0.01f;
             hy = sqrtf(r2 * syy) * 1.01f + 0.01f;
+            rz = r2 * (0.5f * 1.44269504f) * 1.02f + 0.02f;
         }
         sb.rec[SPLAT_F4 * m + 0] = make_float4(u, v, ca, cb);
         sb.rec[SPLAT_F4 * m + 1] = make_float4(cc, on, op, t);
         sb.rec[SPLAT_F4 * m + 2] = make_float4(fmaxf(rgb[0], 0.0f), fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), K);
-        sb.rec[SPLAT_F4 * m + 3] = make_float4(hx, hy, 0.0f, 0.0f);
+        sb.rec[SPLAT_F4 * m + 3] = make_float4(hx, hy, rz, 0.0f);
         sb.rect[m] = make_uint2((uint32_t)rx0 | ((uint32_t)rx1 << 16), (uint32_t)ry0 | ((uint32_t)ry1 << 16));
         sb.depth_key[m] = __float_as_uint(z);
         sb.tiles[m] = (uint32_t)((rx1 - rx0 + 1) * (ry1 - ry0 + 1));

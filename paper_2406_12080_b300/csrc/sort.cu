@@ -35,6 +35,7 @@ constexpr uint32_t ST_INC = 2u << 30;           // look-back word: count of this
 constexpr uint32_t ST_VAL = (1u << 30) - 1u;
 constexpr int OS_SPIN_LIMIT = 1 << 20;       // re-reads of one look-back word before giving up
 constexpr int OS_LOOKBACK = 8;               // look-back words loaded per step
+constexpr int HG_IPT = 4;                    // keys per thread of the histogram kernel
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
     uint32_t v;
@@ -82,26 +83,37 @@ __global__ void __launch_bounds__(OS_THREADS) radix_histogram_kernel(const uint3
     if (threadIdx.x == 0) s_kept = 0;
     __syncthreads();
     const uint32_t n = *n_dev;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lmask = lanemask_lt();
     uint32_t kept = 0;
-    // whole warps iterate together (the ballots need every lane)
-    for (uint32_t i0 = (blockIdx.x * OS_THREADS + threadIdx.x) & ~31u; i0 < n; i0 += gridDim.x * OS_THREADS) {
-        const uint32_t i = i0 + lane;
-        const uint32_t k = i < n ? __ldg(keys + i) : 0xffffffffu;
-        const bool ok = i < n && !(drop && k == 0xffffffffu);
-        kept += ok;
-        const uint32_t valid = __ballot_sync(0xffffffffu, ok);
-        for (int p = 0; p < passes; ++p) {
-            const uint32_t d = (k >> (8 * p)) & 255u;
-            uint32_t peers = valid;
+    // HG_IPT keys per thread, all loads issued before any ranking; a warp covers 32 HG_IPT
+    // consecutive keys (whole warps iterate together: the ballots need every lane)
+    for (uint64_t w0 = ((uint64_t)blockIdx.x * OS_WARPS + warp) * 32 * HG_IPT; w0 < n;
+         w0 += (uint64_t)gridDim.x * OS_WARPS * 32 * HG_IPT) {
+        uint32_t kk[HG_IPT];
 #pragma unroll
-            for (int bit = 0; bit < 8; ++bit) {
-                const bool on = (d >> bit) & 1u;
-                const uint32_t m = __ballot_sync(0xffffffffu, on);
-                peers &= on ? m : ~m;
+        for (int q = 0; q < HG_IPT; ++q) {
+            const uint64_t i = w0 + q * 32 + lane;
+            kk[q] = i < n ? __ldg(keys + i) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int q = 0; q < HG_IPT; ++q) {
+            const uint64_t i = w0 + q * 32 + lane;
+            const uint32_t k = kk[q];
+            const bool ok = i < n && !(drop && k == 0xffffffffu);
+            kept += ok;
+            const uint32_t valid = __ballot_sync(0xffffffffu, ok);
+            for (int p = 0; p < passes; ++p) {
+                const uint32_t d = (k >> (8 * p)) & 255u;
+                uint32_t peers = valid;
+#pragma unroll
+                for (int bit = 0; bit < 8; ++bit) {
+                    const bool on = (d >> bit) & 1u;
+                    const uint32_t m = __ballot_sync(0xffffffffu, on);
+                    peers &= on ? m : ~m;
+                }
+                if (ok && (peers & lmask) == 0) atomicAdd(&s_h[p][d], (uint32_t)__popc(peers));
             }
-            if (ok && (peers & lmask) == 0) atomicAdd(&s_h[p][d], (uint32_t)__popc(peers));
         }
     }
     kept = __reduce_add_sync(0xffffffffu, kept);
@@ -208,7 +220,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
                 x = ld_relaxed(status + (uint64_t)(j - q) * 256 + d);
             }
             if ((x & (ST_AGG | ST_INC)) == 0) {   // gave up: the result is wrong, the flag says so
-                atomicOr(flags, FLAG_SORT_TIMEOUT);
+                atomicOr(flags, FLAG_WAIT_TIMEOUT);
                 found = true;
                 continue;
             }
@@ -264,7 +276,9 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
     cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * (RADIX_HEADER_WORDS + (size_t)passes * tiles * 256), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const unsigned hg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_cap + 4095) / 4096, 4 * (int64_t)w.num_sms));
+    const int64_t per_block = (int64_t)OS_THREADS * HG_IPT;
+    const unsigned hg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_cap + per_block - 1) / per_block,
+                                                                         16 * (int64_t)w.num_sms));
     radix_histogram_kernel<<<hg, OS_THREADS, 0, s>>>(kin, n_dev, passes, drop_max ? 1 : 0, hist, n_kept);
     // pass p reads (kin, vin) for p = 0, then alternates (ka, va) -> (kb, vb) -> (ka, va) ...
     for (int p = 0; p < passes; ++p) {

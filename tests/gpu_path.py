@@ -64,7 +64,7 @@ def run(hier_dev, cams, oopts, debug=True, capacity=None, chunk=None) -> GpuFram
         npix = sum(c.width * c.height for c in cams)
         fr.T_final, fr.n_contrib = h3dgs.h3dgs_debug_pixel_state(ctx.ctx, npix)
         fr.stats = h3dgs.h3dgs_get_stats(ctx.ctx)
-        assert fr.stats["device_flags"] & 0x8 == 0, "a sort look-back wait timed out"
+        assert fr.stats["device_flags"] & 0x8 == 0, "a bounded inter-block wait timed out"
     fr._images_dev = images
     fr._cut = cut
     return fr
