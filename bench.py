@@ -57,6 +57,15 @@ def parse():
     ap.add_argument("--chunk", type=int, default=512, help="blend chunk (list entries per CTA)")
     ap.add_argument("--tile", default="16x16", help="screen tile WxH")
     ap.add_argument("--batch-views", type=int, default=32, help="cameras of the batched multi-view section (0: skip)")
+    ap.add_argument("--opt-leaves", type=int, default=2_000_000,
+                    help="leaves of the hierarchy-optimisation section (0: skip)")
+    ap.add_argument("--opt-steps", type=int, default=20)
+    ap.add_argument("--workload", choices=["corridor", "city"], default="corridor",
+                    help="corridor: 1M-leaf street corridor, one 1080p view; city: 50M-leaf chunked city, "
+                         "256-pose loop (and the batched views on it)")
+    ap.add_argument("--city-leaves", type=int, default=50_000_000)
+    ap.add_argument("--city-grid", type=int, default=20, help="chunks per side (50 m each)")
+    ap.add_argument("--city-poses", type=int, default=256)
     return ap.parse_args()
 
 
@@ -340,6 +349,7 @@ def run_ours(args, rank, world, local):
         e2e_value = world * args.steps / e2e_s
 
         batched = run_batched(args, ctx, hier, flush, dev, stream) if args.batch_views > 0 else None
+        optimisation = run_optimisation(args, dev, stream) if args.opt_leaves > 0 else None
 
     # ---- roofline of the dominant kernel (the blend: FP32/MUFU issue-bound)
     peaks = measured_peaks()
@@ -379,6 +389,7 @@ def run_ours(args, rank, world, local):
                    "cut_size": M, "visible_splats": V, "pairs": Pn, "evals": n_evals,
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "cuda_graph": graph is not None, "parallelism": f"{world} independent replicas"},
+        "gaussians_per_s": M * value,
         "fwd_bwd": {"value": fb_value, "unit": "views/s", "ms_per_view": fb_ms / args.steps},
         "blend": {"items": int(st["n_items"]), "tile_chunk": int(opts.blend_chunk), "evals_main": n_evals,
                   "evals_tpass": int(st["n_evals_tpass"])},
@@ -394,6 +405,8 @@ def run_ours(args, rank, world, local):
     }
     if batched is not None:
         out["batched"] = batched
+    if optimisation is not None:
+        out["optimisation"] = optimisation
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_time(scene, 4)
     if world > 1:
@@ -402,21 +415,26 @@ def run_ours(args, rank, world, local):
     return out if rank == 0 else None
 
 
-def run_batched(args, ctx, hier, flush, dev, stream):
+def run_batched(args, ctx, hier, flush, dev, stream, cams=None, scene="street corridor 1M leaves"):
     """Many cameras of mixed resolution and tau in one launch per stage vs one frame per view."""
     import torch
     from paper_2406_12080_b300 import autotune, h3dgs, synth
-    cams = synth.corridor_views(n_views=args.batch_views)
+    cams = cams if cams is not None else synth.corridor_views(n_views=args.batch_views)
     n = len(cams)
     N = hier.n
-    cap = N * n
+    h3dgs.h3dgs_reserve(ctx.ctx, 0, 0)
+    ids = torch.empty(N, dtype=torch.int32, device=dev)
+    tt = torch.empty(N, dtype=torch.float32, device=dev)
+    offs = torch.empty(2, dtype=torch.int64, device=dev)
+    sizes = [h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids, tt, offs, N) for c in cams]
+    cap = int(sum(sizes) * 1.02) + 1024
+    del ids, tt
     ids = torch.empty(cap, dtype=torch.int32, device=dev)
     tt = torch.empty(cap, dtype=torch.float32, device=dev)
     offs = torch.empty(n + 1, dtype=torch.int64, device=dev)
     npix = sum(3 * c.width * c.height for c in cams)
     img_b = torch.empty(npix, dtype=torch.float32, device=dev)
     img_v = torch.empty(npix, dtype=torch.float32, device=dev)
-    h3dgs.h3dgs_reserve(ctx.ctx, 0, 0)
     m = h3dgs.h3dgs_select_cut(ctx.ctx, cams, ids, tt, offs, cap)
     opts0 = h3dgs.default_opts()
     h3dgs.h3dgs_render(ctx.ctx, cams, ids, tt, offs, opts0, img_b, 0)
@@ -492,7 +510,7 @@ def run_batched(args, ctx, hier, flush, dev, stream):
         tot += e0.elapsed_time(e1)
     fb_ms = tot / reps
     res = sorted({f"{c.width}x{c.height}" for c in cams})
-    return {"workload": f"{n} cameras ({', '.join(res)}), tau in (3, 6, 15), street corridor 1M leaves",
+    return {"workload": f"{n} cameras ({', '.join(res)}), tau in (3, 6, 15), {scene}",
             "views": n, "pixels": npix // 3, "cut_total": int(st["n_cut"]), "pairs": int(st["n_pairs"]),
             "batched_ms": times["batched"], "per_view_ms": times["per_view"],
             "batched_views_per_s": n / (times["batched"] * 1e-3),
@@ -501,6 +519,151 @@ def run_batched(args, ctx, hier, flush, dev, stream):
             "fwd_bwd_views_per_s": n / (fb_ms * 1e-3),
             "autotune": {"tile": f"{opts.tile_w}x{opts.tile_h}", "chunk": int(opts.blend_chunk),
                          "table_ms": table}}
+
+
+def run_optimisation(args, dev, stream):
+    """Hierarchy optimisation: L1 against leaf renders, 8 views at 1280x720, autograd + Adam per step."""
+    import torch
+    from paper_2406_12080_b300 import autograd, h3dgs, synth
+    scene = synth.corridor_scene(seed=3, n_leaves=args.opt_leaves)
+    _, views = synth.optimisation_views(seed=3)
+    ctx = h3dgs.Context(dev.index, stream)
+    hier = ctx.build(scene.leaves)
+    ctx.upload(hier)
+    leaf_views = [synth.with_tau(c, 0.0) for c in views]
+    targets = ctx.render(leaf_views, ctx.select_cut(leaf_views)).clone()
+    params = autograd.HierarchyParams(hier)
+    opt = torch.optim.Adam(params.parameters(), lr=1e-3)
+    for _ in range(2):
+        autograd.l1_step(params, ctx, hier, views, targets, opt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    losses = []
+    e0.record(stream)
+    for _ in range(args.opt_steps):
+        losses.append(autograd.l1_step(params, ctx, hier, views, targets, opt))
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.opt_steps
+    st = h3dgs.h3dgs_get_stats(ctx.ctx)
+    losses = [float(x) for x in losses]
+    out = {"workload": f"street corridor {args.opt_leaves} leaves ({hier.n} nodes), {len(views)} views "
+                       f"1280x720, tau log-uniform in [3, 640) px, L1 vs leaf renders, Adam",
+           "ms_per_step": ms, "steps_per_s": 1e3 / ms, "views_per_s": len(views) * 1e3 / ms,
+           "loss_first": losses[0], "loss_last": losses[-1], "cut_total": int(st["n_cut"]),
+           "note": "each step: activations, upload, cut, render (save), adjoint, Adam; host syncs for "
+                   "the cut size and pair count (not graph-captured)"}
+    ctx.close()
+    return out
+
+
+def _city_chunk(a):
+    """One chunk of the city (worker of the generation pool)."""
+    from paper_2406_12080_b300 import synth
+    seed, c, grid, per = a
+    lv = synth.city_chunk_leaves(seed, c % grid, c // grid, per)
+    return c, lv
+
+
+def build_city(args, ctx, dev):
+    """The chunked city on the device: leaves generated chunk by chunk on the host cores, then the
+    consolidated hierarchy (per-chunk trees joined by a top tree) built by the library."""
+    import multiprocessing as mp
+    import torch
+    K = args.city_grid * args.city_grid
+    per = args.city_leaves // K
+    L = K * per
+    f = lambda *shape: torch.empty(shape, dtype=torch.float32, device=dev)
+    leaves = {"mean": f(L, 3), "scale": f(L, 3), "rot": f(L, 4), "opacity": f(L), "sh": f(L, 48)}
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        for c, lv in pool.imap(_city_chunk, [(2, c, args.city_grid, per) for c in range(K)], chunksize=4):
+            sl = slice(c * per, (c + 1) * per)
+            for k in leaves:
+                leaves[k][sl].copy_(torch.from_numpy(getattr(lv, k)))
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hier = ctx.build_chunked(leaves, np.arange(K + 1, dtype=np.int64) * per)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    del leaves
+    torch.cuda.empty_cache()
+    return hier, L, t_gen, t_build
+
+
+def run_city(args, rank, world, local):
+    import torch
+    from paper_2406_12080_b300 import build, h3dgs, synth
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    ctx = h3dgs.Context(local, stream)
+    with torch.cuda.stream(stream):
+        hier, L, t_gen, t_build = build_city(args, ctx, dev)
+        ctx.upload(hier)
+        N = hier.n
+        poses = synth.city_path(2, args.city_poses)
+        ids = torch.empty(N, dtype=torch.int32, device=dev)
+        tt = torch.empty(N, dtype=torch.float32, device=dev)
+        offs = torch.empty(2, dtype=torch.int64, device=dev)
+        npix = 3 * poses[0].width * poses[0].height
+        images = torch.empty(npix, dtype=torch.float32, device=dev)
+        opts = h3dgs.default_opts()
+        # size the fixed workspace from every 8th pose, then time every pose with events
+        h3dgs.h3dgs_reserve(ctx.ctx, 0, 0)
+        mmax = pmax = 0
+        for c in poses[::8]:
+            mmax = max(mmax, h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids, tt, offs, N))
+            h3dgs.h3dgs_render(ctx.ctx, [c], ids, tt, offs, opts, images, 0)
+            pmax = max(pmax, h3dgs.h3dgs_get_stats(ctx.ctx)["n_pairs"])
+        h3dgs.h3dgs_reserve(ctx.ctx, int(mmax * 1.3) + 4096, int(pmax * 1.3) + 65536)
+        arrs = [h3dgs.camera_array([c]) for c in poses]
+        for c, a in zip(poses[:args.warmup], arrs):
+            h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids, tt, offs, N, want_total=False)
+            h3dgs.h3dgs_render(ctx.ctx, [c], ids, tt, offs, opts, images, 0, cam_array=a)
+        torch.cuda.synchronize()
+        cut_ms, render_ms, sizes, pairs = [], [], [], []
+        with ClockSampler(local) as clk:
+            for c, a in zip(poses, arrs):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+                h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids, tt, offs, N, want_total=False)
+                e[1].record(stream)
+                h3dgs.h3dgs_render(ctx.ctx, [c], ids, tt, offs, opts, images, 0, cam_array=a)
+                e[2].record(stream)
+                st = h3dgs.h3dgs_get_stats(ctx.ctx)   # synchronises
+                assert st["device_flags"] == 0, f"device flags {st['device_flags']}"
+                cut_ms.append(e[0].elapsed_time(e[1]))
+                render_ms.append(e[1].elapsed_time(e[2]))
+                sizes.append(int(st["n_cut"]))
+                pairs.append(int(st["n_pairs"]))
+        frame_ms = np.array(cut_ms) + np.array(render_ms)
+        value = len(poses) / (frame_ms.sum() * 1e-3)
+        batched = None
+        if args.batch_views > 0:
+            flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+            batched = run_batched(args, ctx, hier, flush, dev, stream, cams=synth.city_views(2, args.batch_views),
+                                  scene=f"chunked city {L} leaves")
+    out = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": len(poses),
+        "warmup": args.warmup, "ms_per_step": float(frame_ms.mean()), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"chunked city, {L} leaves ({N} nodes) in {args.city_grid}x{args.city_grid} chunks of "
+                               f"50 m, {len(poses)}-pose loop at 1920x1080, tau=6 px",
+                   "n_leaves": L, "n_nodes": N, "l2": "working set (3.2 GB of node records) far above L2"},
+        "per_frame": {"cut_size_mean": float(np.mean(sizes)), "cut_size_max": int(np.max(sizes)),
+                      "pairs_mean": float(np.mean(pairs)), "cut_ms_mean": float(np.mean(cut_ms)),
+                      "cut_ms_max": float(np.max(cut_ms)), "render_ms_mean": float(np.mean(render_ms)),
+                      "render_ms_max": float(np.max(render_ms)), "frame_ms_p50": float(np.median(frame_ms)),
+                      "frame_ms_max": float(frame_ms.max())},
+        "gaussians_per_s": float(np.sum(sizes) / (frame_ms.sum() * 1e-3)),
+        "build": {"host_generation_s": t_gen, "device_build_s": t_build},
+        "clocks": clk.summary(),
+    }
+    if batched is not None:
+        out["batched"] = batched
+    return out if rank == 0 else None
 
 
 # ----------------------------------------------------------------------------------- reference arm
@@ -543,6 +706,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "city":
+        out = run_city(args, rank, world, local)
     else:
         out = run_ours(args, rank, world, local)
     if out is not None:

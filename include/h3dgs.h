@@ -183,6 +183,22 @@ h3dgs_status h3dgs_build_hierarchy(h3dgs_ctx* ctx, int64_t n_leaves, const float
                                    const float* rot, const float* opacity, const float* sh,
                                    const h3dgs_node_arrays* out);
 
+/* Consolidated hierarchy over a chunked scene (the chunk-wise build and consolidation of large
+ * captures, Sec. 5): the leaves are grouped into n_chunks chunks (chunk c = leaves
+ * [chunk_offsets[c], chunk_offsets[c + 1]), host array of n_chunks + 1 ascending offsets starting at
+ * 0); every chunk gets its own hierarchy exactly as h3dgs_build_hierarchy builds it from the chunk's
+ * leaves alone, and a top tree built the same way over the chunk roots joins them (its leaf boxes
+ * are the chunks' leaf-union boxes, its leaves are the chunk roots; the chunk roots keep their own
+ * frames, i.e. orientation matching stops at the chunk boundary).  Node order: the top tree's
+ * 2 n_chunks - 1 nodes breadth-first, then chunk after chunk that chunk's nodes except its root in
+ * the chunk's own breadth-first order; every parent precedes its children and children are
+ * contiguous.  `out` receives 2 L - 1 nodes for L leaves in total.  Synchronous; allocates
+ * temporary device memory.  Errors: INVALID_ARG (bad offsets, an empty chunk, NULL or misaligned
+ * pointers), OOM, CUDA. */
+h3dgs_status h3dgs_build_hierarchy_chunked(h3dgs_ctx* ctx, int32_t n_chunks, const int64_t* chunk_offsets,
+                                           const float* mean, const float* scale, const float* rot,
+                                           const float* opacity, const float* sh, const h3dgs_node_arrays* out);
+
 /* a0 -- make a hierarchy resident.  The arrays are BORROWED: they must stay allocated, and the
  * topology and boxes unchanged, until the next upload or h3dgs_destroy.  Attributes (mean, scale,
  * rot, opacity, sh) may be updated in place between calls (e.g. by an optimiser).  The library

@@ -351,6 +351,35 @@ h3dgs_status h3dgs_build_hierarchy(h3dgs_ctx* ctx, int64_t L, const float* mean,
     return H3DGS_OK;
 }
 
+h3dgs_status h3dgs_build_hierarchy_chunked(h3dgs_ctx* ctx, int32_t n_chunks, const int64_t* off, const float* mean,
+                                           const float* scale, const float* rot, const float* opacity, const float* sh,
+                                           const h3dgs_node_arrays* out) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (n_chunks < 1 || !off || off[0] != 0) return fail(ctx, H3DGS_ERR_INVALID_ARG, "build_chunked: bad chunk offsets");
+    int64_t Lmax = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+        if (off[c + 1] <= off[c]) return fail(ctx, H3DGS_ERR_INVALID_ARG, "build_chunked: empty or unordered chunk");
+        Lmax = std::max<int64_t>(Lmax, off[c + 1] - off[c]);
+    }
+    if (off[n_chunks] > (1LL << 30)) return fail(ctx, H3DGS_ERR_INVALID_ARG, "build_chunked: too many leaves");
+    if (!out) return fail(ctx, H3DGS_ERR_INVALID_ARG, "build_chunked: NULL output");
+    const void* ptrs[] = {mean, scale, rot, opacity, sh, out->mean, out->scale, out->rot, out->opacity, out->sh,
+                          out->box_min, out->box_max, out->parent, out->child_start, out->child_count};
+    for (const void* p : ptrs) {
+        if (!p) return fail(ctx, H3DGS_ERR_INVALID_ARG, "build_chunked: NULL array");
+        if (!aligned16(p)) return fail(ctx, H3DGS_ERR_INVALID_ARG, "build_chunked: arrays must be 16-byte aligned");
+    }
+    CK(cudaSetDevice(ctx->device), "set device");
+    BuildOut bo{out->mean, out->scale, out->rot, out->opacity, out->sh, out->box_min, out->box_max,
+                out->parent, out->child_start, out->child_count};
+    SortWork sw;
+    CK(sort_work(ctx, std::max<int64_t>(Lmax, n_chunks), &sw), "sort workspace");
+    CK(build_hierarchy_chunked(n_chunks, off, mean, scale, rot, opacity, sh, bo, sw, ctx->num_sms, ctx->stream),
+       "build chunked");
+    return H3DGS_OK;
+}
+
 h3dgs_status h3dgs_upload_hierarchy(h3dgs_ctx* ctx, const h3dgs_hierarchy* h) {
     if (!ctx) return H3DGS_ERR_INVALID_ARG;
     ctx->err.clear();

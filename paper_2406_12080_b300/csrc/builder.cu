@@ -129,9 +129,16 @@ __device__ void eigen_sym(D3 A, double lam[3], D3& V) {
 // ---------------------------------------------------------------------------------------- kernels
 
 __global__ void leaf_init_kernel(int64_t L, const float* __restrict__ mean, const float* __restrict__ scale,
-                                 const float* __restrict__ rot, float* __restrict__ lbox /*[L][6]*/,
-                                 int32_t* __restrict__ seg, uint32_t* __restrict__ perm) {
+                                 const float* __restrict__ rot, const float* __restrict__ given_box,
+                                 float* __restrict__ lbox /*[L][6]*/, int32_t* __restrict__ seg,
+                                 uint32_t* __restrict__ perm) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
+        seg[i] = 0;
+        perm[i] = (uint32_t)i;
+        if (given_box) {   // explicit leaf boxes (min xyz, max xyz)
+            for (int k = 0; k < 6; ++k) lbox[6 * i + k] = given_box[6 * i + k];
+            continue;
+        }
         const double q[4] = {rot[4 * i], rot[4 * i + 1], rot[4 * i + 2], rot[4 * i + 3]};
         const double s[3] = {scale[3 * i], scale[3 * i + 1], scale[3 * i + 2]};
         const D3 R = rot_of(q);
@@ -146,9 +153,14 @@ __global__ void leaf_init_kernel(int64_t L, const float* __restrict__ mean, cons
             lbox[6 * i + j] = __double2float_rn(__dsub_rn(m, h));
             lbox[6 * i + 3 + j] = __double2float_rn(__dadd_rn(m, h));
         }
-        seg[i] = 0;
-        perm[i] = (uint32_t)i;
     }
+}
+
+// node id of every leaf (inverse of leaf_of_node over the leaf nodes)
+__global__ void leaf_node_kernel(int64_t N, const int32_t* __restrict__ child_count,
+                                 const int32_t* __restrict__ leaf_of_node, int32_t* __restrict__ leaf_node) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x)
+        if (child_count[v] == 0) leaf_node[leaf_of_node[v]] = (int32_t)v;
 }
 
 __global__ void box_reset_kernel(int64_t n, uint32_t* __restrict__ ebox) {
@@ -334,12 +346,13 @@ __constant__ int8_t c_perm[24][3];
 __constant__ int8_t c_sign[24][3];
 
 __global__ void orient_kernel(int64_t n, const int32_t* __restrict__ level_nodes, const int32_t* __restrict__ child_start,
-                              const int32_t* __restrict__ child_count, double* __restrict__ work) {
+                              const int32_t* __restrict__ child_count, double* __restrict__ work, int orient_leaves) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = level_nodes[r];
         const double* par = work + NA * v;
         const D3 Rp = rot_of(par + 6);
         for (int ci = 0; ci < child_count[v]; ++ci) {
+            if (!orient_leaves && child_count[(int64_t)child_start[v] + ci] == 0) continue;
             double* ch = work + NA * ((int64_t)child_start[v] + ci);
             const D3 Rc = rot_of(ch + 6);
             int best = 0;
@@ -478,7 +491,8 @@ cudaError_t upload_perms() {
     } while (0)
 
 cudaError_t build_hierarchy(int64_t L, const float* mean, const float* scale, const float* rot, const float* opacity,
-                            const float* sh, const BuildOut& out, const SortWork& sw, int num_sms, cudaStream_t st) {
+                            const float* sh, const BuildOut& out, const SortWork& sw, int num_sms, cudaStream_t st,
+                            const BuildExtra& ex) {
     BR(upload_perms());
     const int64_t N = 2 * L - 1;
     BuildShape shape;
@@ -524,7 +538,7 @@ cudaError_t build_hierarchy(int64_t L, const float* mean, const float* scale, co
     BR(cudaMemcpyAsync(out.parent, shape.parent.data(), 4 * N, cudaMemcpyHostToDevice, st));
     BR(cudaMemcpyAsync(out.child_start, shape.child_start.data(), 4 * N, cudaMemcpyHostToDevice, st));
     BR(cudaMemcpyAsync(out.child_count, shape.child_count.data(), 4 * N, cudaMemcpyHostToDevice, st));
-    leaf_init_kernel<<<grid, 256, 0, st>>>(L, mean, scale, rot, lbox, seg, perm);
+    leaf_init_kernel<<<grid, 256, 0, st>>>(L, mean, scale, rot, ex.leaf_box, lbox, seg, perm);
     box_reset_kernel<<<grid, 256, 0, st>>>(N, ebox);
     const int32_t zero = 0;
     if (L == 1) BR(cudaMemcpyAsync(leaf_of_node, &zero, 4, cudaMemcpyHostToDevice, st));
@@ -591,12 +605,132 @@ cudaError_t build_hierarchy(int64_t L, const float* mean, const float* scale, co
         if (G == 0) continue;
         BR(cudaMemcpyAsync(d_nodes, lvl_nodes[d].data(), 4 * G, cudaMemcpyHostToDevice, st));
         orient_kernel<<<(unsigned)std::min<int64_t>((G + 127) / 128, grid), 128, 0, st>>>(G, d_nodes, out.child_start,
-                                                                                      out.child_count, work);
+                                                                                      out.child_count, work,
+                                                                                      ex.orient_leaves ? 1 : 0);
         BR(cudaGetLastError());
         BR(cudaStreamSynchronize(st));
     }
     output_kernel<<<grid, 256, 0, st>>>(N, work, ebox, out.mean, out.scale, out.rot, out.opacity, out.sh, out.box_min,
                                         out.box_max);
+    if (ex.leaf_node) leaf_node_kernel<<<grid, 256, 0, st>>>(N, out.child_count, leaf_of_node, ex.leaf_node);
+    BR(cudaGetLastError());
+    BR(cudaStreamSynchronize(st));
+    return cudaSuccess;
+}
+
+namespace {
+
+// local node j >= 1 of a chunk's hierarchy -> global node base + j - 1; the root's children keep
+// parent -1 until the top tree is known (patched by chunk_root_kernel)
+__global__ void chunk_copy_kernel(int64_t Nc, BuildOut src, BuildOut dst, int64_t base) {
+    for (int64_t j = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < Nc; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = base + j - 1;
+        for (int k = 0; k < 3; ++k) {
+            dst.mean[3 * g + k] = src.mean[3 * j + k];
+            dst.scale[3 * g + k] = src.scale[3 * j + k];
+            dst.box_min[3 * g + k] = src.box_min[3 * j + k];
+            dst.box_max[3 * g + k] = src.box_max[3 * j + k];
+        }
+        for (int k = 0; k < 4; ++k) dst.rot[4 * g + k] = src.rot[4 * j + k];
+        dst.opacity[g] = src.opacity[j];
+        for (int c = 0; c < NSH; ++c) dst.sh[NSH * g + c] = src.sh[NSH * j + c];
+        const int32_t p = src.parent[j], cs = src.child_start[j];
+        dst.parent[g] = p == 0 ? -1 : (int32_t)(base + p - 1);
+        dst.child_start[g] = cs >= 0 ? (int32_t)(base + cs - 1) : -1;
+        dst.child_count[g] = src.child_count[j];
+    }
+}
+
+// the chunk root as a leaf of the top tree: its attributes and leaf-union box
+__global__ void chunk_root_out_kernel(BuildOut src, int64_t c, float* mean, float* scale, float* rot, float* opacity,
+                                      float* sh, float* box) {
+    const int k = threadIdx.x;
+    if (k < 3) {
+        mean[3 * c + k] = src.mean[k];
+        scale[3 * c + k] = src.scale[k];
+        box[6 * c + k] = src.box_min[k];
+        box[6 * c + 3 + k] = src.box_max[k];
+    }
+    if (k < 4) rot[4 * c + k] = src.rot[k];
+    if (k == 0) opacity[c] = src.opacity[0];
+    if (k < NSH) sh[NSH * c + k] = src.sh[k];
+}
+
+// link every chunk's root (a leaf of the top tree) with the chunk's first nodes
+__global__ void chunk_root_kernel(int K, const int64_t* __restrict__ base, const int32_t* __restrict__ root_children,
+                                  const int32_t* __restrict__ top_node, BuildOut dst) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) {
+        const int32_t v = top_node[c], nc = root_children[c];
+        if (nc == 0) continue;
+        dst.child_start[v] = (int32_t)base[c];
+        dst.child_count[v] = nc;
+        for (int i = 0; i < nc; ++i) dst.parent[base[c] + i] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t build_hierarchy_chunked(int K, const int64_t* off, const float* mean, const float* scale, const float* rot,
+                                    const float* opacity, const float* sh, const BuildOut& out, const SortWork& sw,
+                                    int num_sms, cudaStream_t st) {
+    int64_t Lmax = 0;
+    for (int c = 0; c < K; ++c) Lmax = std::max<int64_t>(Lmax, off[c + 1] - off[c]);
+    const int64_t Nmax = 2 * Lmax - 1;
+    DevMem mem;
+    BuildOut scr;
+    BR(mem.alloc(&scr.mean, 3 * (size_t)Nmax));
+    BR(mem.alloc(&scr.scale, 3 * (size_t)Nmax));
+    BR(mem.alloc(&scr.rot, 4 * (size_t)Nmax));
+    BR(mem.alloc(&scr.opacity, (size_t)Nmax));
+    BR(mem.alloc(&scr.sh, (size_t)NSH * Nmax));
+    BR(mem.alloc(&scr.box_min, 3 * (size_t)Nmax));
+    BR(mem.alloc(&scr.box_max, 3 * (size_t)Nmax));
+    BR(mem.alloc(&scr.parent, (size_t)Nmax));
+    BR(mem.alloc(&scr.child_start, (size_t)Nmax));
+    BR(mem.alloc(&scr.child_count, (size_t)Nmax));
+    float *tm, *ts, *tr, *to, *tsh, *tb;
+    int32_t *top_node, *root_children;
+    int64_t* d_base;
+    BR(mem.alloc(&tm, 3 * (size_t)K));
+    BR(mem.alloc(&ts, 3 * (size_t)K));
+    BR(mem.alloc(&tr, 4 * (size_t)K));
+    BR(mem.alloc(&to, (size_t)K));
+    BR(mem.alloc(&tsh, (size_t)NSH * K));
+    BR(mem.alloc(&tb, 6 * (size_t)K));
+    BR(mem.alloc(&top_node, (size_t)K));
+    BR(mem.alloc(&root_children, (size_t)K));
+    BR(mem.alloc(&d_base, (size_t)K));
+    const int64_t Ntop = 2 * (int64_t)K - 1;
+    std::vector<int64_t> base(K);
+    std::vector<int32_t> rc(K);
+    int64_t next = Ntop;
+    const int grid = num_sms * 8;
+    for (int c = 0; c < K; ++c) {
+        const int64_t Lc = off[c + 1] - off[c];
+        const int64_t o = off[c];
+        BR(build_hierarchy(Lc, mean + 3 * o, scale + 3 * o, rot + 4 * o, opacity + o, sh + (int64_t)NSH * o, scr, sw,
+                           num_sms, st));
+        chunk_root_out_kernel<<<1, 64, 0, st>>>(scr, c, tm, ts, tr, to, tsh, tb);
+        base[c] = next;
+        rc[c] = Lc >= 2 ? 2 : 0;
+        const int64_t Nc = 2 * Lc - 1;
+        if (Nc > 1) {
+            BuildOut dst = out;
+            chunk_copy_kernel<<<(unsigned)std::min<int64_t>((Nc + 255) / 256, grid), 256, 0, st>>>(Nc, scr, dst, base[c]);
+        }
+        next += Nc - 1;
+        BR(cudaGetLastError());
+    }
+    // the top tree over the chunk roots: leaf boxes are the chunks' leaf-union boxes, and the chunk
+    // roots keep their own frames (no orientation matching at the chunk boundary)
+    BuildExtra ex;
+    ex.leaf_box = tb;
+    ex.orient_leaves = false;
+    ex.leaf_node = top_node;
+    BR(build_hierarchy(K, tm, ts, tr, to, tsh, out, sw, num_sms, st, ex));
+    BR(cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, st));
+    BR(cudaMemcpyAsync(root_children, rc.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, st));
+    chunk_root_kernel<<<(K + 255) / 256, 256, 0, st>>>(K, d_base, root_children, top_node, out);
     BR(cudaGetLastError());
     BR(cudaStreamSynchronize(st));
     return cudaSuccess;

@@ -275,9 +275,24 @@ struct BuildOut {
     float *mean, *scale, *rot, *opacity, *sh, *box_min, *box_max;
     int32_t *parent, *child_start, *child_count;
 };
+// Options of one build: explicit leaf boxes ([L][6] min xyz, max xyz; NULL: the 3-sigma boxes of the
+// leaf Gaussians), whether leaves take part in orientation matching, and an optional output of the
+// node id of every leaf ([L]).
+struct BuildExtra {
+    const float* leaf_box = nullptr;
+    bool orient_leaves = true;
+    int32_t* leaf_node = nullptr;
+};
 // Builds the 2L - 1 node hierarchy over L leaves (synchronous on stream s).
 cudaError_t build_hierarchy(int64_t L, const float* mean, const float* scale, const float* rot, const float* opacity,
-                            const float* sh, const BuildOut& out, const SortWork& sw, int num_sms, cudaStream_t s);
+                            const float* sh, const BuildOut& out, const SortWork& sw, int num_sms, cudaStream_t s,
+                            const BuildExtra& ex = BuildExtra());
+// Consolidated hierarchy of K chunks (leaves of chunk c: [off[c], off[c + 1]), host offsets):
+// nodes [0, 2K - 1) are the top tree over the chunk roots (breadth-first; its leaves are the chunk
+// roots), followed by every chunk's own hierarchy without its root, chunk after chunk.
+cudaError_t build_hierarchy_chunked(int K, const int64_t* off, const float* mean, const float* scale, const float* rot,
+                                    const float* opacity, const float* sh, const BuildOut& out, const SortWork& sw,
+                                    int num_sms, cudaStream_t s);
 
 // backward.cu
 struct GradBufs {

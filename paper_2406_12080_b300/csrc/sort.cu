@@ -30,20 +30,20 @@ constexpr int OS_THREADS = 256;                 // one thread per digit in the l
 constexpr int OS_WARPS = OS_THREADS / 32;
 constexpr int OS_IPT = 15;                      // keys per thread
 constexpr int OS_TILE = OS_THREADS * OS_IPT;    // 3840 keys per tile
-constexpr uint32_t ST_AGG = 1u << 30;           // look-back word: tile's own digit count
-constexpr uint32_t ST_INC = 2u << 30;           // look-back word: count of this and all earlier tiles
-constexpr uint32_t ST_VAL = (1u << 30) - 1u;
+constexpr unsigned long long ST_AGG = 1ull << 62;   // look-back word: tile's own digit count
+constexpr unsigned long long ST_INC = 2ull << 62;   // look-back word: count of this and all earlier tiles
+constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
 constexpr int OS_SPIN_LIMIT = 1 << 20;       // re-reads of one look-back word before giving up
 constexpr int OS_LOOKBACK = 8;               // look-back words loaded per step
 constexpr int HG_IPT = 4;                    // keys per thread of the histogram kernel
 
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
                                                                     const uint32_t* __restrict__ n_dev,
                                                                     const uint32_t* __restrict__ n_out, int shift,
                                                                     int drop, const uint32_t* __restrict__ hist,
-                                                                    uint32_t* __restrict__ status,
+                                                                    unsigned long long* __restrict__ status,
                                                                     uint32_t* __restrict__ ticket,
                                                                     uint32_t* __restrict__ flags) {
     __shared__ uint32_t s_wcnt[OS_WARPS][256];
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
         s_wcnt[w][d] = cnt;
         cnt += c;
     }
-    uint32_t* st = status + (uint64_t)tile * 256;
+    unsigned long long* st = status + (uint64_t)tile * 256;
     if (tile == 0) st_relaxed(st + d, ST_INC | cnt);
     else st_relaxed(st + d, ST_AGG | cnt);
     const uint32_t lstart = block_exclusive_scan256(cnt, s_warp);
@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
     const uint32_t gstart = block_exclusive_scan256(hist[d], s_warp);
     // ---- decoupled look-back over earlier tiles for digit d: OS_LOOKBACK status words are loaded at
     // once, then summed newest first until an inclusive one; a word not yet published is re-read
-    uint32_t excl = 0;
+    unsigned long long excl = 0;
     bool found = false;
     for (int64_t j = (int64_t)tile - 1; j >= 0 && !found; j -= OS_LOOKBACK) {
-        uint32_t v[OS_LOOKBACK];
+        unsigned long long v[OS_LOOKBACK];
 #pragma unroll
         for (int q = 0; q < OS_LOOKBACK; ++q) v[q] = (j - q >= 0) ? ld_relaxed(status + (uint64_t)(j - q) * 256 + d) : 0u;
 #pragma unroll
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
                 found = true;
                 continue;
             }
-            uint32_t x = v[q];
+            unsigned long long x = v[q];
             int spins = 0;
             while ((x & (ST_AGG | ST_INC)) == 0 && spins < OS_SPIN_LIMIT) {
                 if (++spins > 32) __nanosleep(64);
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
         }
     }
     if (tile > 0) st_relaxed(st + d, ST_INC | (excl + cnt));
-    s_gdst[d] = gstart + excl;
+    s_gdst[d] = (uint32_t)(gstart + excl);
     if (d == 255) s_cnt255 = cnt;
     __syncthreads();
     // ---- stage by digit in shared memory, then write runs out
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
 
 size_t radix_work_words(int64_t n_cap) {
     const int64_t tiles = std::max<int64_t>(1, (n_cap + OS_TILE - 1) / OS_TILE);
-    return (size_t)(RADIX_HEADER_WORDS + 4 * tiles * 256);
+    return (size_t)(RADIX_HEADER_WORDS + 2 * 4 * tiles * 256);   // 64-bit look-back words
 }
 
 cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ka, uint32_t* va, uint32_t* kb,
@@ -266,14 +266,15 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
                              uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s) {
     *result_in_a = false;
     if (n_cap <= 0) return cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s);
-    if (n_cap >= (1LL << 30) || bits < 1 || bits > 32) return cudaErrorInvalidValue;
+    if (n_cap > 0xffffffffLL || bits < 1 || bits > 32) return cudaErrorInvalidValue;
     const int passes = (bits + 7) / 8;
     const int64_t tiles = (n_cap + OS_TILE - 1) / OS_TILE;
     if (radix_work_words(n_cap) > w.words) return cudaErrorInvalidValue;
     uint32_t* tickets = w.work;            // [4]
     uint32_t* hist = w.work + 64;          // [4][256]
-    uint32_t* status = w.work + RADIX_HEADER_WORDS;
-    cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * (RADIX_HEADER_WORDS + (size_t)passes * tiles * 256), s);
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(w.work + RADIX_HEADER_WORDS);
+    cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * RADIX_HEADER_WORDS +
+                                                   sizeof(unsigned long long) * (size_t)passes * tiles * 256, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const int64_t per_block = (int64_t)OS_THREADS * HG_IPT;

@@ -86,6 +86,8 @@ def lib():
             "h3dgs_reserve": (i32, [vp, i64, i64]),
             "h3dgs_upload_hierarchy": (i32, [vp, C.POINTER(h3dgs_hierarchy)]),
             "h3dgs_build_hierarchy": (i32, [vp, i64, vp, vp, vp, vp, vp, C.POINTER(h3dgs_node_arrays)]),
+            "h3dgs_build_hierarchy_chunked": (i32, [vp, i32, C.POINTER(C.c_int64), vp, vp, vp, vp, vp,
+                                                    C.POINTER(h3dgs_node_arrays)]),
             "h3dgs_select_cut": (i32, [vp, C.POINTER(h3dgs_camera), i32, vp, vp, vp, i64, C.POINTER(i64)]),
             "h3dgs_interpolate": (i32, [vp, C.POINTER(h3dgs_camera), i32, vp, vp, vp, i32, vp, i64]),
             "h3dgs_select_cut_noalloc": (i32, [C.POINTER(h3dgs_hierarchy), C.POINTER(h3dgs_camera), vp, vp, vp, i64,
@@ -189,6 +191,18 @@ def h3dgs_build_hierarchy(ctx, leaves: dict, out: "DeviceHierarchy"):
     L = int(leaves["mean"].shape[0])
     _check(ctx, lib().h3dgs_build_hierarchy(ctx, L, *[_ptr(leaves[k]) for k in ("mean", "scale", "rot", "opacity", "sh")],
                                             C.byref(a)))
+
+
+def h3dgs_build_hierarchy_chunked(ctx, leaves: dict, chunk_offsets, out: "DeviceHierarchy"):
+    """Consolidated hierarchy over chunks; chunk_offsets: n_chunks + 1 ascending leaf offsets from 0."""
+    a = h3dgs_node_arrays()
+    for k in ("mean", "scale", "rot", "opacity", "sh", "box_min", "box_max", "parent", "child_start",
+              "child_count"):
+        setattr(a, k, _ptr(getattr(out, k)))
+    off = np.ascontiguousarray(chunk_offsets, np.int64)
+    _check(ctx, lib().h3dgs_build_hierarchy_chunked(ctx, len(off) - 1, off.ctypes.data_as(C.POINTER(C.c_int64)),
+                                                    *[_ptr(leaves[k]) for k in ("mean", "scale", "rot", "opacity",
+                                                                                 "sh")], C.byref(a)))
 
 
 def h3dgs_select_cut(ctx, cams, cut_ids, cut_t, cut_offsets, capacity: int, want_total: bool = True):
@@ -344,6 +358,17 @@ class Context:
         i = lambda n: torch.empty(n, dtype=torch.int32, device=self.device)
         out = DeviceHierarchy(f(N, 3), f(N, 3), f(N, 4), f(N), f(N, 48), f(N, 3), f(N, 3), i(N), i(N), i(N))
         h3dgs_build_hierarchy(self.ctx, leaves, out)
+        return out
+
+    def build_chunked(self, leaves: dict, chunk_offsets) -> DeviceHierarchy:
+        """Consolidated hierarchy over chunks (leaves: dict of device tensors, chunks contiguous)."""
+        import torch
+        L = int(leaves["mean"].shape[0])
+        N = 2 * L - 1
+        f = lambda *shape: torch.empty(shape, dtype=torch.float32, device=self.device)
+        i = lambda n: torch.empty(n, dtype=torch.int32, device=self.device)
+        out = DeviceHierarchy(f(N, 3), f(N, 3), f(N, 4), f(N), f(N, 48), f(N, 3), f(N, 3), i(N), i(N), i(N))
+        h3dgs_build_hierarchy_chunked(self.ctx, leaves, chunk_offsets, out)
         return out
 
     def upload(self, hier: DeviceHierarchy):

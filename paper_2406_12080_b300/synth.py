@@ -224,9 +224,8 @@ def city_chunk_leaves(seed: int, cx: int, cy: int, per_chunk: int, chunk: float 
     return _leaves(np.column_stack([xy, h]), rng)
 
 
-def city_path(seed: int, n_poses: int, extent: float = 1000.0, width: int = 1920,
-              height: int = 1080, tau: float = 6.0):
-    """Closed loop of camera poses at eye height over the city grid."""
+def city_poses(seed: int, n_poses: int, extent: float = 1000.0):
+    """Closed loop of (position, forward) pairs at eye height over the city grid."""
     rng = np.random.default_rng([seed, 5])
     k = np.arange(n_poses) / n_poses * 2 * np.pi
     wob = rng.uniform(-0.08, 0.08, size=4)
@@ -234,9 +233,30 @@ def city_path(seed: int, n_poses: int, extent: float = 1000.0, width: int = 1920
     cx = cy = 0.5 * extent
     pts = np.stack([cx + rad * np.cos(k), cy + rad * np.sin(k)], axis=1)
     nxt = np.roll(pts, -1, axis=0)
+    return [([p[0], p[1], 1.7], [q[0] - p[0], q[1] - p[1], 0.0]) for p, q in zip(pts, nxt)]
+
+
+def city_path(seed: int, n_poses: int, extent: float = 1000.0, width: int = 1920,
+              height: int = 1080, tau: float = 6.0):
+    """Closed loop of camera poses at eye height over the city grid."""
+    return [look_camera(pos, fwd, [0, 0, 1], width, height, 60.0, tau)
+            for pos, fwd in city_poses(seed, n_poses, extent)]
+
+
+def city_views(seed: int = 2, n_views: int = 32,
+               resolutions=((1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)),
+               taus=(3.0, 6.0, 15.0), extent: float = 1000.0):
+    """Views on the city loop: resolutions in equal groups, tau cycling over `taus`."""
+    per = max(1, n_views // len(resolutions))
     cams = []
-    for p, q in zip(pts, nxt):
-        d = q - p
-        cams.append(look_camera([p[0], p[1], 1.7], [d[0], d[1], 0.0], [0, 0, 1], width,
-                                height, 60.0, tau))
+    for i, (pos, fwd) in enumerate(city_poses(seed, n_views, extent)):
+        w, h = resolutions[min(i // per, len(resolutions) - 1)]
+        cams.append(look_camera(pos, fwd, [0, 0, 1], w, h, 60.0, taus[i % len(taus)]))
     return cams
+
+
+def city_chunks(seed: int = 2, grid: int = 20, per_chunk: int = 125_000, chunk: float = 50.0):
+    """The large-scene workload chunk by chunk: grid x grid chunks of chunk x chunk metres, each drawn
+    like the corridor (uniform in the chunk's xy, heights ~ Exp(5 m)).  Yields (index, Leaves)."""
+    for c in range(grid * grid):
+        yield c, city_chunk_leaves(seed, c % grid, c // grid, per_chunk, chunk)

@@ -54,3 +54,25 @@ def corridor(n_leaves=1_000_000):
     import oracle
     sc = synth.corridor_scene(n_leaves=n_leaves)
     return sc, oracle.build_tree(sc.leaves)
+
+
+def _city_chunk(a):
+    seed, c, grid, per = a
+    return c, synth.city_chunk_leaves(seed, c % grid, c // grid, per)
+
+
+def city_device(ctx, grid=20, per=125_000, seed=2):
+    """The chunked city (grid x grid chunks of `per` leaves) as device leaf tensors, generated on the
+    host cores chunk by chunk (spawned workers: the parent already holds a CUDA context)."""
+    import multiprocessing as mp
+    import os
+    import torch
+    K = grid * grid
+    L = K * per
+    f = lambda *shape: torch.empty(shape, dtype=torch.float32, device="cuda")
+    leaves = {"mean": f(L, 3), "scale": f(L, 3), "rot": f(L, 4), "opacity": f(L), "sh": f(L, 48)}
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        for c, lv in pool.imap(_city_chunk, [(seed, c, grid, per) for c in range(K)], chunksize=4):
+            for k in leaves:
+                leaves[k][c * per:(c + 1) * per].copy_(torch.from_numpy(getattr(lv, k)))
+    return leaves, np.arange(K + 1, dtype=np.int64) * per

@@ -1,0 +1,127 @@
+"""The large-scene workload at full size: 50M leaves in 20 x 20 chunks of 50 m, one hierarchy per chunk
+joined by a top tree over the chunk roots (h3dgs_build_hierarchy_chunked), about 100M nodes.
+
+The oracle cannot build the whole scene in a test's time, so parity is checked where the oracle can
+work one chunk at a time: for sampled chunks the oracle builds the chunk's hierarchy from the chunk's
+leaves alone, and the device's nodes of that chunk must match it (topology, boxes bit-exact, attributes
+within fp32 rounding), and the device cut of full-size frames must hold exactly the chunk nodes the
+oracle's cut rule selects, with identical weights (every chunk node but the root has its parent inside
+the chunk, so its decision is local).  Properties that hold at any size are checked on the whole
+scene: the cut is an antichain meeting every root-to-leaf path exactly once, and the images, final
+transmittances and contributor counts are in range."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_12080_b300 import h3dgs, synth
+from tests import gpu_path, scenes
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+GRID, PER = 20, 125_000
+CHUNKS = (0, 137, 399)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_12080_b300 import build
+    build.build()
+
+
+@functools.lru_cache(maxsize=None)
+def _city():
+    import torch
+    ctx = gpu_path.context()
+    leaves, off = scenes.city_device(ctx, GRID, PER)
+    dh = ctx.build_chunked(leaves, off)
+    del leaves
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return dh
+
+
+def _chunk_nodes(dh, c):
+    """Global node ids of chunk c's local nodes 0 .. 2 PER - 2 (local 0 = the chunk root)."""
+    n_top = 2 * GRID * GRID - 1
+    base = n_top + c * (2 * PER - 2)
+    cs = dh.child_start[:n_top].cpu().numpy()
+    root = int(np.nonzero(cs == base)[0][0])
+    return np.concatenate([[root], base + np.arange(2 * PER - 2)]), base
+
+
+def test_chunk_hierarchies_equal_the_oracle_build():
+    dh = _city()
+    assert dh.n == 2 * GRID * GRID * PER - 1
+    for c in CHUNKS:
+        ho = oracle.build_tree(synth.city_chunk_leaves(2, c % GRID, c // GRID, PER))
+        g, base = _chunk_nodes(dh, c)
+        gid = lambda local: np.where(local < 0, -1, np.where(local == 0, g[0], base + local - 1))
+        par = dh.parent[g].cpu().numpy()
+        np.testing.assert_array_equal(par[1:], gid(ho.parent[1:]))
+        cs = dh.child_start[g].cpu().numpy()
+        np.testing.assert_array_equal(cs, gid(ho.child_start))
+        np.testing.assert_array_equal(dh.child_count[g].cpu().numpy(), ho.child_count)
+        for k in ("box_min", "box_max"):
+            np.testing.assert_array_equal(getattr(dh, k)[g].cpu().numpy(), getattr(ho, k), err_msg=k)
+        np.testing.assert_allclose(dh.mean[g].cpu().numpy(), ho.mean, rtol=1e-6, atol=1e-5)
+        np.testing.assert_allclose(dh.opacity[g].cpu().numpy(), ho.opacity, rtol=1e-5, atol=1e-7)
+        np.testing.assert_allclose(dh.sh[g].cpu().numpy(), ho.sh, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("pose", [0, 97, 200])
+def test_full_size_frame_cut_and_render(pose):
+    import torch
+    dh = _city()
+    ctx = gpu_path.context()
+    ctx.upload(dh)
+    cam = synth.city_path(2, 256)[pose]
+    cut = ctx.select_cut([cam], dh.n)
+    ids, t, _ = cut
+    ids_h, t_h = ids.cpu().numpy(), t.cpu().numpy()
+    assert np.all(np.diff(ids_h) > 0)
+    assert np.all((t_h >= 0) & (t_h <= 1))
+    # antichain meeting every root-to-leaf path once, level by level (parents precede children)
+    parent = dh.parent.cpu().numpy()
+    cstart = dh.child_start.cpu().numpy()
+    ccount = dh.child_count.cpu().numpy()
+    assert set(np.unique(ccount)) <= {0, 2}
+    in_cut = np.zeros(dh.n, bool)
+    in_cut[ids_h] = True
+    covered = in_cut.copy()    # some node on the path from the root down to v (inclusive) is in the cut
+    above = np.zeros(dh.n, bool)
+    frontier = np.array([0])
+    while len(frontier):
+        kids = frontier[ccount[frontier] > 0]
+        ch = (cstart[kids][:, None] + np.arange(2)[None, :]).ravel()
+        assert np.all(parent[ch] == np.repeat(kids, 2))
+        above[ch] = covered[parent[ch]]
+        covered[ch] |= covered[parent[ch]]
+        frontier = ch
+    assert not np.any(in_cut & above), "a cut node has a cut ancestor"
+    assert np.all(covered[ccount == 0]), "a leaf is not covered by the cut"
+    # the sampled chunks: the oracle's cut rule on its own chunk build
+    for c in CHUNKS:
+        ho = oracle.build_tree(synth.city_chunk_leaves(2, c % GRID, c // GRID, PER))
+        oid, ot = oracle.select_cut(cam, ho, 1)
+        keep = oid > 0
+        g, base = _chunk_nodes(dh, c)
+        want = base + oid[keep] - 1
+        lo, hi = base, base + 2 * PER - 2
+        sel = (ids_h >= lo) & (ids_h < hi)
+        np.testing.assert_array_equal(ids_h[sel], want)
+        np.testing.assert_array_equal(t_h[sel].view(np.uint32), ot[keep].view(np.uint32))
+    # render: values in range
+    images = ctx.render([cam], cut, save_for_backward=0)
+    torch.cuda.synchronize()
+    st = h3dgs.h3dgs_get_stats(ctx.ctx)
+    assert st["device_flags"] == 0
+    im = images.cpu().numpy()
+    assert np.all(np.isfinite(im)) and im.min() >= 0
+    npix = cam.width * cam.height
+    Tf, nc = h3dgs.h3dgs_debug_pixel_state(ctx.ctx, npix)
+    assert np.all((Tf >= 0) & (Tf <= 1)) and np.all(nc >= 0)
+    assert st["n_cut"] == len(ids_h) and st["n_visible"] > 0
