@@ -89,8 +89,8 @@ typedef struct {
 
 /* Render options.  h3dgs_default_opts() fills the values used by the paper and by 3DGS. */
 typedef struct {
-    int32_t tile_w, tile_h;  /* screen tile in pixels; tile_w * tile_h must be 64, 128 or 256,
-                                tile_w a multiple of 8 (default 16 x 16)                        */
+    int32_t tile_w, tile_h;  /* screen tile in pixels: 16x16 (default), 8x8, 32x8, 8x32 or 16x8
+                                (both sides multiples of 8: a warp blends 8x8 pixels)          */
     float lowpass;           /* screen-space variance added to the 2D covariance, px^2 (0.3)    */
     float alpha_clamp;       /* alpha upper clamp (0.99, Sec. 6.3)                              */
     float alpha_floor;       /* alpha below which a splat is skipped (1/255)                   */

@@ -184,7 +184,7 @@ DevOpts dev_opts(const h3dgs_render_opts& o) {
 
 bool supported_tile(int w, int h) {
     return (w == 16 && h == 16) || (w == 8 && h == 8) || (w == 32 && h == 8) || (w == 8 && h == 32) ||
-           (w == 16 && h == 8) || (w == 32 && h == 4);
+           (w == 16 && h == 8);
 }
 
 

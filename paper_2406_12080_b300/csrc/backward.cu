@@ -142,12 +142,12 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
             stop = r.x + n_contrib[pix];
         } else {
             const int64_t i0 = tile_item0[tile];
-            const int64_t slot = (int64_t)item * NT + threadIdx.x;
+            const int64_t slot = (int64_t)item * NT + ly * TW + lx;   // the scratch is row-major per tile
             T = scTend[slot];
             const int l = sclast[slot];
             stop = l < 0 ? begin : r.x + l;
             for (int c = it.y + 1; c < nch; ++c) {
-                const int64_t sl = (i0 + c) * NT + threadIdx.x;
+                const int64_t sl = (i0 + c) * NT + ly * TW + lx;
                 S0 += scC[3 * sl]; S1 += scC[3 * sl + 1]; S2 += scC[3 * sl + 2];
             }
         }
@@ -473,7 +473,6 @@ cudaError_t launch_backward(const DevHier& h, const BlendArgs& a, const int32_t*
         else if (o.tile_w == 32 && o.tile_h == 8) BW(32, 8);
         else if (o.tile_w == 8 && o.tile_h == 32) BW(8, 32);
         else if (o.tile_w == 16 && o.tile_h == 8) BW(16, 8);
-        else if (o.tile_w == 32 && o.tile_h == 4) BW(32, 4);
         else return cudaErrorInvalidValue;
 #undef BW
         cudaError_t e = cudaGetLastError();

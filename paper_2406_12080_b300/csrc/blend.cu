@@ -58,34 +58,61 @@ __device__ __forceinline__ float pair_alpha(float px, float py, const float4 a, 
     return ffma(b.w, alpha_prime(ap, c->w), fmul(fsub(1.0f, b.w), an));
 }
 
+// alpha of two pixels of the same column (rows py.x, py.y) for one splat, in the same fixed fp32 order
+// as pair_alpha per pixel (the paired instructions round every element like the scalar ones)
+__device__ __forceinline__ float2 pair_alpha2(float px, float2 py, const float4 a, const float4 b, const float4* c,
+                                              float clampv) {
+    const float dx = fsub(px, a.x);
+    const float2 dy = __fadd2_rn(py, make_float2(-a.y, -a.y));
+    const float2 h = __ffma2_rn(make_float2(a.z, a.z), make_float2(dx, dx), __fmul2_rn(make_float2(a.w, a.w), dy));
+    const float2 g = __fmul2_rn(__fmul2_rn(make_float2(b.x, b.x), dy), dy);
+    const float2 p2 = __ffma2_rn(make_float2(dx, dx), h, g);
+    const float2 G = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
+    const float2 xn = __fmul2_rn(make_float2(b.y, b.y), G);
+    const float2 an = make_float2(fminf(clampv, xn.x), fminf(clampv, xn.y));
+    if (b.w == 0.0f) return an;
+    const float2 xp = __fmul2_rn(make_float2(b.z, b.z), G);
+    const float K = c->w;
+    const float2 apr = make_float2(alpha_prime(fminf(clampv, xp.x), K), alpha_prime(fminf(clampv, xp.y), K));
+    const float omw = fsub(1.0f, b.w);
+    return __ffma2_rn(make_float2(b.w, b.w), apr, __fmul2_rn(make_float2(omw, omw), an));
+}
+
+// This thread's two pixels of the tile and the tile's camera.
 template <int TW, int TH>
-struct TileGeom {
-    int px_i, py_i;   // this thread's pixel
-    int ox, oy;       // tile's pixel origin
-    bool inside;
-    float px, py;
+struct TileGeom2 {
+    int ox, oy;                 // tile's pixel origin
+    int px_i, py_i0, py_i1;     // the two pixels (same column)
+    int slot0, slot1;           // their indices in the tile (row-major), for the per-pixel scratch
+    bool in0, in1;
+    float px;
+    float2 py;
     const DevCam* cam;
 };
 
 template <int TW, int TH>
-__device__ __forceinline__ TileGeom<TW, TH> tile_geom(const DevCam* __restrict__ cams, int n_cams, int64_t tile) {
+__device__ __forceinline__ TileGeom2<TW, TH> tile_geom2(const DevCam* __restrict__ cams, int n_cams, int64_t tile) {
     int lo = 0, hi = n_cams - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (cams[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
     }
-    TileGeom<TW, TH> g;
+    TileGeom2<TW, TH> g;
     g.cam = cams + lo;
     const int local = (int)(tile - g.cam->tile_base);
     g.ox = (local % g.cam->tiles_x) * TW;
     g.oy = (local / g.cam->tiles_x) * TH;
-    int lx, ly;
-    tile_pixel<TW, TH>(threadIdx.x, lx, ly);
+    int lx, ly0;
+    tile_pixel2<TW, TH>(threadIdx.x, lx, ly0);
     g.px_i = g.ox + lx;
-    g.py_i = g.oy + ly;
-    g.inside = g.px_i < g.cam->width && g.py_i < g.cam->height;
+    g.py_i0 = g.oy + ly0;
+    g.py_i1 = g.py_i0 + 4;
+    g.slot0 = ly0 * TW + lx;
+    g.slot1 = (ly0 + 4) * TW + lx;
+    g.in0 = g.px_i < g.cam->width && g.py_i0 < g.cam->height;
+    g.in1 = g.px_i < g.cam->width && g.py_i1 < g.cam->height;
     g.px = (float)g.px_i + 0.5f;
-    g.py = (float)g.py_i + 0.5f;
+    g.py = make_float2((float)g.py_i0 + 0.5f, (float)g.py_i1 + 0.5f);
     return g;
 }
 
@@ -176,21 +203,22 @@ struct Scratch {
     int32_t* last; // list position (within the tile) after the chunk's last contributor, or -1
 };
 
-// Walk of one item over list entries [begin, end).  MAIN: the exact skip/stop rules with colour;
-// otherwise the transmittance pass (product of (1 - alpha) over contributors, no colour; a pixel is
-// finished once T < t_min, after which nothing it could add matters).  Branch-free per entry: the
-// alpha of every live lane is computed and applied through selects.
+// Walk of one item over list entries [begin, end) for this thread's two pixels.  MAIN: the exact
+// skip/stop rules with colour; otherwise the transmittance pass (product of (1 - alpha) over
+// contributors, no colour; a pixel is finished once T < t_min, after which nothing it could add
+// matters).  Branch-free per entry: the alpha of every live pixel is computed and applied through
+// selects; the paired fp32 instructions evaluate both pixels at once.
 template <int TW, int TH, bool MAIN>
-__device__ __forceinline__ void blend_walk(const TileGeom<TW, TH>& g, const uint32_t* __restrict__ list,
-                                           const float4* __restrict__ splat, int begin, int end, int list0,
-                                           float clampv, float afloor, float tmin, float4* s_a, float4* s_b,
-                                           float4* s_c, uint32_t* s_m, float& T, float& C0, float& C1, float& C2,
-                                           int& last, bool& done, unsigned int& evals) {
-    constexpr int NT = TW * TH;
+__device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const uint32_t* __restrict__ list,
+                                            const float4* __restrict__ splat, int begin, int end, int list0,
+                                            float clampv, float afloor, float tmin, float4* s_a, float4* s_b,
+                                            float4* s_c, uint32_t* s_m, float2& T, float2& C0, float2& C1,
+                                            float2& C2, int2& last, bool& done0, bool& done1, unsigned int& evals) {
+    constexpr int NT2 = TW * TH / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int b0 = begin; b0 < end; b0 += NT) {
-        if (__syncthreads_count(done) == NT) break;
-        const int n = min(NT, end - b0);
+    for (int b0 = begin; b0 < end; b0 += NT2) {
+        if (__syncthreads_count(done0 && done1) == NT2) break;
+        const int n = min(NT2, end - b0);
         if ((int)threadIdx.x < n) {
             const uint32_t s = __ldg(list + b0 + threadIdx.x);
             const float4 a = __ldg(splat + SPLAT_F4 * (int64_t)s);
@@ -199,38 +227,42 @@ __device__ __forceinline__ void blend_walk(const TileGeom<TW, TH>& g, const uint
             s_a[threadIdx.x] = a;
             s_b[threadIdx.x] = bb;
             s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
-            s_m[threadIdx.x] = warp_mask<TW, TH>(a, bb.x, d, g.ox, g.oy);
+            s_m[threadIdx.x] = warp_mask<TW, TH, 8>(a, bb.x, d, g.ox, g.oy);
         }
         __syncthreads();
-        if (__any_sync(0xffffffffu, !done)) {
+        if (__any_sync(0xffffffffu, !(done0 && done1))) {
             for (int base = 0; base < n; base += 32) {
                 const uint32_t mm = (base + lane < n) ? s_m[base + lane] : 0u;
                 uint32_t bits = __ballot_sync(0xffffffffu, (mm >> warp) & 1u);
                 while (bits) {
                     const int j = base + __ffs(bits) - 1;
                     bits &= bits - 1;
-                    evals += !done;
-                    const float alpha = pair_alpha(g.px, g.py, s_a[j], s_b[j], &s_c[j], clampv);
-                    const bool live = !done && alpha >= afloor;
-                    const float Tn = fmul(T, fsub(1.0f, alpha));
-                    if (!__any_sync(0xffffffffu, live)) continue;   // no lane of the warp takes it
+                    evals += (unsigned)!done0 + (unsigned)!done1;
+                    const float2 alpha = pair_alpha2(g.px, g.py, s_a[j], s_b[j], &s_c[j], clampv);
+                    const bool live0 = !done0 && alpha.x >= afloor, live1 = !done1 && alpha.y >= afloor;
+                    if (!__any_sync(0xffffffffu, live0 || live1)) continue;   // no pixel of the warp takes it
+                    const float2 Tn = __fmul2_rn(T, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-alpha.x, -alpha.y)));
                     if (MAIN) {
-                        const bool stop = live && Tn < tmin;
-                        const bool apply = live && !stop;
-                        done = done || stop;
-                        const float w = apply ? alpha * T : 0.0f;
+                        const bool stop0 = live0 && Tn.x < tmin, stop1 = live1 && Tn.y < tmin;
+                        const bool app0 = live0 && !stop0, app1 = live1 && !stop1;
+                        done0 = done0 || stop0;
+                        done1 = done1 || stop1;
+                        const float2 wt = __fmul2_rn(alpha, T);
+                        const float2 w = make_float2(app0 ? wt.x : 0.0f, app1 ? wt.y : 0.0f);
                         const float4 c = s_c[j];
-                        C0 = fmaf(c.x, w, C0);
-                        C1 = fmaf(c.y, w, C1);
-                        C2 = fmaf(c.z, w, C2);
-                        T = apply ? Tn : T;
-                        last = apply ? b0 + j + 1 - list0 : last;
+                        C0 = __ffma2_rn(make_float2(c.x, c.x), w, C0);
+                        C1 = __ffma2_rn(make_float2(c.y, c.y), w, C1);
+                        C2 = __ffma2_rn(make_float2(c.z, c.z), w, C2);
+                        T = make_float2(app0 ? Tn.x : T.x, app1 ? Tn.y : T.y);
+                        const int pos = b0 + j + 1 - list0;
+                        last = make_int2(app0 ? pos : last.x, app1 ? pos : last.y);
                     } else {
-                        T = live ? Tn : T;
-                        done = done || (live && Tn < tmin);
+                        T = make_float2(live0 ? Tn.x : T.x, live1 ? Tn.y : T.y);
+                        done0 = done0 || (live0 && Tn.x < tmin);
+                        done1 = done1 || (live1 && Tn.y < tmin);
                     }
                 }
-                if (__all_sync(0xffffffffu, done)) break;
+                if (__all_sync(0xffffffffu, done0 && done1)) break;
             }
         }
     }
@@ -239,28 +271,29 @@ __device__ __forceinline__ void blend_walk(const TileGeom<TW, TH>& g, const uint
 // The blend: one CTA per queue entry, in ticket order (a CTA holding ticket k is running, and every
 // entry before k has been taken by a running CTA).  Producers never wait; a consumer waits until the
 // producers of its tile have published their products (per-tile counter, bounded wait), which were
-// all taken before it.
+// all taken before it.  TW x TH / 2 threads, two pixels each.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) blend_queue_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
-                                                              const int2* __restrict__ ranges,
-                                                              const uint32_t* __restrict__ list,
-                                                              const float4* __restrict__ splat,
-                                                              const int2* __restrict__ items,
-                                                              const uint32_t* __restrict__ q_prod,
-                                                              const uint32_t* __restrict__ q_single,
-                                                              const uint32_t* __restrict__ q_cons,
-                                                              const uint32_t* __restrict__ counts,
-                                                              const int32_t* __restrict__ tile_item0,
-                                                              const int32_t* __restrict__ tile_nch, int chunk,
-                                                              Scratch sc, uint32_t* __restrict__ ticket,
-                                                              uint32_t* __restrict__ tile_done,
-                                                              float* __restrict__ images,
-                                                              float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
-                                                              unsigned long long* __restrict__ n_evals,
-                                                              uint32_t* __restrict__ flags) {
-    constexpr int NT = TW * TH;
-    __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
-    __shared__ uint32_t s_m[NT];
+__global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
+                                                                  const int2* __restrict__ ranges,
+                                                                  const uint32_t* __restrict__ list,
+                                                                  const float4* __restrict__ splat,
+                                                                  const int2* __restrict__ items,
+                                                                  const uint32_t* __restrict__ q_prod,
+                                                                  const uint32_t* __restrict__ q_single,
+                                                                  const uint32_t* __restrict__ q_cons,
+                                                                  const uint32_t* __restrict__ counts,
+                                                                  const int32_t* __restrict__ tile_item0,
+                                                                  const int32_t* __restrict__ tile_nch, int chunk,
+                                                                  Scratch sc, uint32_t* __restrict__ ticket,
+                                                                  uint32_t* __restrict__ tile_done,
+                                                                  float* __restrict__ images,
+                                                                  float* __restrict__ T_final,
+                                                                  int32_t* __restrict__ n_contrib,
+                                                                  unsigned long long* __restrict__ n_evals,
+                                                                  uint32_t* __restrict__ flags) {
+    constexpr int NT = TW * TH, NT2 = NT / 2;
+    __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];
+    __shared__ uint32_t s_m[NT2];
     __shared__ unsigned int s_evals[2];
     __shared__ uint32_t s_k;
     if (threadIdx.x == 0) s_k = atomicAdd(ticket, 1u);
@@ -278,13 +311,13 @@ __global__ void __launch_bounds__(TW * TH) blend_queue_kernel(const DevCam* __re
     const int64_t tile = it.x;
     const int nch = tile_nch[tile];
     const bool main_pass = role != 0 || it.y == 0;
-    const TileGeom<TW, TH> g = tile_geom<TW, TH>(cams, n_cams, tile);
+    const TileGeom2<TW, TH> g = tile_geom2<TW, TH>(cams, n_cams, tile);
     const int2 r = ranges[tile];
     const int begin = r.x + it.y * chunk;
     const int end = nch == 1 ? r.y : min(r.y, begin + chunk);
-    const int64_t slot = (int64_t)item * NT + threadIdx.x;
+    const int64_t s0 = (int64_t)item * NT + g.slot0, s1 = (int64_t)item * NT + g.slot1;
     const int lane = threadIdx.x & 31;
-    float T = 1.0f;
+    float2 T = make_float2(1.0f, 1.0f);
     if (role == 2) {
         // wait for the tile's nch - 1 producers, then T_in = product of the earlier chunks' products
         if (threadIdx.x == 0) {
@@ -300,30 +333,35 @@ __global__ void __launch_bounds__(TW * TH) blend_queue_kernel(const DevCam* __re
         }
         __syncthreads();
         const int64_t i0 = tile_item0[tile];
-        for (int c = 0; c < it.y; ++c) T = fmul(T, __ldcg(sc.Tc + (i0 + c) * NT + threadIdx.x));
+        for (int c = 0; c < it.y; ++c)
+            T = __fmul2_rn(T, make_float2(__ldcg(sc.Tc + (i0 + c) * NT + g.slot0), __ldcg(sc.Tc + (i0 + c) * NT + g.slot1)));
     }
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    int last = -1;
+    float2 C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0;
+    int2 last = make_int2(-1, -1);
     unsigned int evals = 0;
-    bool done = !g.inside || T < o.t_min;
+    bool done0 = !g.in0 || T.x < o.t_min, done1 = !g.in1 || T.y < o.t_min;
     if (main_pass)
-        blend_walk<TW, TH, true>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min, s_a, s_b,
-                                 s_c, s_m, T, C0, C1, C2, last, done, evals);
+        blend_walk2<TW, TH, true>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min, s_a, s_b,
+                                  s_c, s_m, T, C0, C1, C2, last, done0, done1, evals);
     else
-        blend_walk<TW, TH, false>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min, s_a, s_b,
-                                  s_c, s_m, T, C0, C1, C2, last, done, evals);
+        blend_walk2<TW, TH, false>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min, s_a, s_b,
+                                   s_c, s_m, T, C0, C1, C2, last, done0, done1, evals);
     for (int off = 16; off > 0; off >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, off);
     if (lane == 0) atomicAdd(&s_evals[main_pass ? 0 : 1], evals);
     if (role == 0) {
         // the product handed to the later chunks: 0 once the first chunk's walk stopped
-        if (!main_pass) sc.Tc[slot] = T;
-        else {
-            sc.C[3 * slot + 0] = C0;
-            sc.C[3 * slot + 1] = C1;
-            sc.C[3 * slot + 2] = C2;
-            sc.Tend[slot] = T;
-            sc.last[slot] = last;
-            sc.Tc[slot] = (done && g.inside) ? 0.0f : T;
+        if (!main_pass) {
+            sc.Tc[s0] = T.x;
+            sc.Tc[s1] = T.y;
+        } else {
+            sc.C[3 * s0 + 0] = C0.x; sc.C[3 * s0 + 1] = C1.x; sc.C[3 * s0 + 2] = C2.x;
+            sc.C[3 * s1 + 0] = C0.y; sc.C[3 * s1 + 1] = C1.y; sc.C[3 * s1 + 2] = C2.y;
+            sc.Tend[s0] = T.x;
+            sc.Tend[s1] = T.y;
+            sc.last[s0] = last.x;
+            sc.last[s1] = last.y;
+            sc.Tc[s0] = (done0 && g.in0) ? 0.0f : T.x;
+            sc.Tc[s1] = (done1 && g.in1) ? 0.0f : T.y;
         }
         __threadfence();
         __syncthreads();
@@ -334,23 +372,33 @@ __global__ void __launch_bounds__(TW * TH) blend_queue_kernel(const DevCam* __re
     if (threadIdx.x < 2 && n_evals && s_evals[threadIdx.x]) atomicAdd(n_evals + threadIdx.x, (unsigned long long)s_evals[threadIdx.x]);
     if (role == 0) return;
     if (nch > 1) {
-        sc.C[3 * slot + 0] = C0;
-        sc.C[3 * slot + 1] = C1;
-        sc.C[3 * slot + 2] = C2;
-        sc.Tend[slot] = T;
-        sc.last[slot] = last;
+        sc.C[3 * s0 + 0] = C0.x; sc.C[3 * s0 + 1] = C1.x; sc.C[3 * s0 + 2] = C2.x;
+        sc.C[3 * s1 + 0] = C0.y; sc.C[3 * s1 + 1] = C1.y; sc.C[3 * s1 + 2] = C2.y;
+        sc.Tend[s0] = T.x;
+        sc.Tend[s1] = T.y;
+        sc.last[s0] = last.x;
+        sc.last[s1] = last.y;
         return;
     }
-    if (g.inside) {
-        const DevCam& cam = *g.cam;
-        const int64_t pix = cam.pix_base + (int64_t)g.py_i * cam.width + g.px_i;
-        const int64_t plane = (int64_t)cam.width * cam.height;
-        float* img = images + 3 * cam.pix_base + (int64_t)g.py_i * cam.width + g.px_i;
-        img[0] = fmaf(T, o.bg[0], C0);
-        img[plane] = fmaf(T, o.bg[1], C1);
-        img[2 * plane] = fmaf(T, o.bg[2], C2);
-        if (T_final) T_final[pix] = T;
-        if (n_contrib) n_contrib[pix] = last < 0 ? 0 : last;
+    const DevCam& cam = *g.cam;
+    const int64_t plane = (int64_t)cam.width * cam.height;
+    if (g.in0) {
+        const int64_t pix = cam.pix_base + (int64_t)g.py_i0 * cam.width + g.px_i;
+        float* img = images + 3 * cam.pix_base + (int64_t)g.py_i0 * cam.width + g.px_i;
+        img[0] = fmaf(T.x, o.bg[0], C0.x);
+        img[plane] = fmaf(T.x, o.bg[1], C1.x);
+        img[2 * plane] = fmaf(T.x, o.bg[2], C2.x);
+        if (T_final) T_final[pix] = T.x;
+        if (n_contrib) n_contrib[pix] = last.x < 0 ? 0 : last.x;
+    }
+    if (g.in1) {
+        const int64_t pix = cam.pix_base + (int64_t)g.py_i1 * cam.width + g.px_i;
+        float* img = images + 3 * cam.pix_base + (int64_t)g.py_i1 * cam.width + g.px_i;
+        img[0] = fmaf(T.y, o.bg[0], C0.y);
+        img[plane] = fmaf(T.y, o.bg[1], C1.y);
+        img[2 * plane] = fmaf(T.y, o.bg[2], C2.y);
+        if (T_final) T_final[pix] = T.y;
+        if (n_contrib) n_contrib[pix] = last.y < 0 ? 0 : last.y;
     }
 }
 
@@ -367,8 +415,17 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
     if (tile >= n_tiles) return;
     const int nch = tile_nch[tile];
     if (nch == 1) return;
-    const TileGeom<TW, TH> g = tile_geom<TW, TH>(cams, n_cams, tile);
-    if (!g.inside) return;
+    // one pixel per thread, row-major in the tile (the scratch's pixel order)
+    int lo = 0, hi = n_cams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cams[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    const DevCam& cam = cams[lo];
+    const int local = (int)(tile - cam.tile_base);
+    const int px_i = (local % cam.tiles_x) * TW + (int)threadIdx.x % TW;
+    const int py_i = (local / cam.tiles_x) * TH + (int)threadIdx.x / TW;
+    if (px_i >= cam.width || py_i >= cam.height) return;
     const int64_t i0 = tile_item0[tile];
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f, Tin = 1.0f;
     int last = 0;
@@ -383,10 +440,9 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
         }
         if (c + 1 < nch) Tin = fmul(Tin, sc.Tc[slot]);
     }
-    const DevCam& cam = *g.cam;
-    const int64_t pix = cam.pix_base + (int64_t)g.py_i * cam.width + g.px_i;
+    const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
     const int64_t plane = (int64_t)cam.width * cam.height;
-    float* img = images + 3 * cam.pix_base + (int64_t)g.py_i * cam.width + g.px_i;
+    float* img = images + 3 * cam.pix_base + (int64_t)py_i * cam.width + px_i;
     img[0] = fmaf(T, o.bg[0], C0);
     img[plane] = fmaf(T, o.bg[1], C1);
     img[2 * plane] = fmaf(T, o.bg[2], C2);
@@ -412,7 +468,7 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     const unsigned tg = (unsigned)a.n_tiles;
 #define BL(TWV, THV)                                                                                                  \
     do {                                                                                                              \
-        blend_queue_kernel<TWV, THV><<<gq, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat,       \
+        blend_queue_kernel<TWV, THV><<<gq, TWV * THV / 2, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat,       \
                                                               a.items, a.q_prod, a.q_single, a.q_cons, a.n_items,     \
                                                               a.tile_item0, a.tile_nch, a.chunk, sc, a.queue_sync,    \
                                                               a.queue_sync + 1, a.images, a.T_final, a.n_contrib,     \
@@ -426,7 +482,6 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     else if (o.tile_w == 32 && o.tile_h == 8) BL(32, 8);
     else if (o.tile_w == 8 && o.tile_h == 32) BL(8, 32);
     else if (o.tile_w == 16 && o.tile_h == 8) BL(16, 8);
-    else if (o.tile_w == 32 && o.tile_h == 4) BL(32, 4);
     else return cudaErrorInvalidValue;
 #undef BL
     return cudaGetLastError();

@@ -108,7 +108,17 @@ __device__ __forceinline__ void tile_pixel(int tid, int& lx, int& ly) {
     ly = (w / WX) * 4 + (l >> 3);
 }
 
-// Bit w set if the splat can reach alpha_floor at a pixel centre of warp w's 8x4 block in the tile
+// Two pixels per thread: warp w owns the 8x8 block (w % (TW/8), w / (TW/8)) of the tile, lane l the
+// pixels (l % 8, l / 8) and (l % 8, l / 8 + 4) of it.
+template <int TW, int TH>
+__device__ __forceinline__ void tile_pixel2(int tid, int& lx, int& ly0) {
+    constexpr int WX = TW / 8;
+    const int w = tid >> 5, l = tid & 31;
+    lx = (w % WX) * 8 + (l & 7);
+    ly0 = (w / WX) * 8 + (l >> 3);
+}
+
+// Bit w set if the splat can reach alpha_floor at a pixel centre of warp w's 8 x BH block in the tile
 // with pixel origin (ox, oy); a clear bit means alpha < alpha_floor at every pixel of the block, so
 // the warp would skip the splat anyway.  a = {u, v, ca, cb}, cc = the third conic term (pre-scaled:
 // the exponent is p2 = ca dx^2 + cb dx dy + cc dy^2), d = {hx, hy, rz, 0}: hx, hy are the inflated
@@ -116,11 +126,11 @@ __device__ __forceinline__ void tile_pixel(int tid, int& lx, int& ly) {
 // alpha_floor) inflated by 2% + 0.02; hx < 0 marks a splat that never reaches the floor.  A block
 // passing the box test is kept only if the minimum of q = -p2 over the block (a convex quadratic:
 // the centre if inside, else the best point of the four edges) is at most rz.
-template <int TW, int TH>
+template <int TW, int TH, int BH = 4>
 __device__ __forceinline__ uint32_t warp_mask(const float4 a, float cc, const float4 d, int ox, int oy) {
     const float hx = d.x, hy = d.y;
     if (!(hx >= 0.0f)) return 0u;
-    constexpr int NW = TW * TH / 32, WX = TW / 8;
+    constexpr int NW = TW * TH / (8 * BH), WX = TW / 8;
     const float u = a.x, v = a.y;
     const float qa = -a.z, qb = -a.w, qc = -cc, rz = d.z;
     // edge minimisers use approximate reciprocals: a slightly moved point on the edge changes q only
@@ -130,7 +140,7 @@ __device__ __forceinline__ uint32_t warp_mask(const float4 a, float cc, const fl
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         const float x0 = (float)(ox + (w % WX) * 8) + 0.5f, x1 = x0 + 7.0f;
-        const float y0 = (float)(oy + (w / WX) * 4) + 0.5f, y1 = y0 + 3.0f;
+        const float y0 = (float)(oy + (w / WX) * BH) + 0.5f, y1 = y0 + (float)(BH - 1);
         if (!(u + hx >= x0 && u - hx <= x1 && v + hy >= y0 && v - hy <= y1)) continue;
         if (u >= x0 && u <= x1 && v >= y0 && v <= y1) {
             m |= 1u << w;
