@@ -84,28 +84,39 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
 
 }  // namespace
 
-// One CTA per blend item (tile, chunk).  A single-chunk tile starts from the pixel's final T and
-// contributor count; a chunk of a split tile starts from the T at its end and its last contributor
-// (saved by the forward pass), with the colour behind it = later chunks' colour + T_final bg.
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sel2(bool p0, bool p1, float2 a, float2 b) {
+    return make_float2(p0 ? a.x : b.x, p1 ? a.y : b.y);
+}
+
+// One CTA per blend item (tile, chunk), TW x TH / 2 threads with two pixels each (the forward's
+// layout: warp w owns an 8x8 block, lane l the pixels (l % 8, l / 8) and (l % 8, l / 8 + 4)).  A
+// single-chunk tile starts from the pixel's final T and contributor count; a chunk of a split tile
+// starts from the T at its end and its last contributor (saved by the forward pass), with the colour
+// behind it = later chunks' colour + T_final bg.  Per splat the two pixels' gradients are added in
+// registers before the warp reduction, and the arithmetic runs on pixel pairs.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
-                                                                 const int2* __restrict__ ranges,
-                                                                 const uint32_t* __restrict__ list,
-                                                                 const float4* __restrict__ splat,
-                                                                 const int2* __restrict__ items,
-                                                                 const uint32_t* __restrict__ n_items,
-                                                                 const int32_t* __restrict__ tile_item0,
-                                                                 const int32_t* __restrict__ tile_nch, int chunk,
-                                                                 const float* __restrict__ scC,
-                                                                 const float* __restrict__ scTend,
-                                                                 const int32_t* __restrict__ sclast,
-                                                                 const float* __restrict__ T_final,
-                                                                 const int32_t* __restrict__ n_contrib,
-                                                                 const float* __restrict__ dL,
-                                                                 float* __restrict__ sgrad) {
-    constexpr int NT = TW * TH;
-    __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
-    __shared__ uint32_t s_id[NT], s_m[NT];
+__global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCam* __restrict__ cams, int n_cams,
+                                                                     DevOpts o, const int2* __restrict__ ranges,
+                                                                     const uint32_t* __restrict__ list,
+                                                                     const float4* __restrict__ splat,
+                                                                     const int2* __restrict__ items,
+                                                                     const uint32_t* __restrict__ n_items,
+                                                                     const int32_t* __restrict__ tile_item0,
+                                                                     const int32_t* __restrict__ tile_nch, int chunk,
+                                                                     const float* __restrict__ scC,
+                                                                     const float* __restrict__ scTend,
+                                                                     const int32_t* __restrict__ sclast,
+                                                                     const float* __restrict__ T_final,
+                                                                     const int32_t* __restrict__ n_contrib,
+                                                                     const float* __restrict__ dL,
+                                                                     float* __restrict__ sgrad) {
+    constexpr int NT = TW * TH, NT2 = NT / 2;
+    __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];
+    __shared__ uint32_t s_id[NT2], s_m[NT2];
     __shared__ int s_max;
     const uint32_t item = blockIdx.x;
     if (item >= *n_items) return;
@@ -120,47 +131,56 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
     const DevCam& cam = cams[lo];
     const int local = (int)(tile - cam.tile_base);
     const int ox = (local % cam.tiles_x) * TW, oy = (local / cam.tiles_x) * TH;
-    int lx, ly;
-    tile_pixel<TW, TH>(threadIdx.x, lx, ly);
-    const int px_i = ox + lx, py_i = oy + ly;
-    const bool inside = px_i < cam.width && py_i < cam.height;
-    const float px = (float)px_i + 0.5f, py = (float)py_i + 0.5f;
+    int lx, ly0;
+    tile_pixel2<TW, TH>(threadIdx.x, lx, ly0);
+    const int px_i = ox + lx;
+    const int pyi[2] = {oy + ly0, oy + ly0 + 4};
+    const int lyk[2] = {ly0, ly0 + 4};
+    const bool in_[2] = {px_i < cam.width && pyi[0] < cam.height, px_i < cam.width && pyi[1] < cam.height};
+    const float px = (float)px_i + 0.5f;
+    const float2 py = make_float2((float)pyi[0] + 0.5f, (float)pyi[1] + 0.5f);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 r = ranges[tile];
     const int begin = r.x + it.y * chunk;     // first list entry of this item
-    float T = 1.0f, g0 = 0, g1 = 0, g2 = 0, S0 = 0, S1 = 0, S2 = 0;
-    int stop = begin;                         // entries [begin, stop) are walked back to front
-    if (inside) {
-        const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
-        const int64_t plane = (int64_t)cam.width * cam.height;
-        const float* gp = dL + 3 * cam.pix_base + (int64_t)py_i * cam.width + px_i;
-        g0 = gp[0]; g1 = gp[plane]; g2 = gp[2 * plane];
+    float Tk[2] = {1.0f, 1.0f}, gk[2][3] = {{0, 0, 0}, {0, 0, 0}}, Sk[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    int stop[2] = {begin, begin};             // entries [begin, stop) are walked back to front
+    const int64_t plane = (int64_t)cam.width * cam.height;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (!in_[k]) continue;
+        const int64_t pix = cam.pix_base + (int64_t)pyi[k] * cam.width + px_i;
+        const float* gp = dL + 3 * cam.pix_base + (int64_t)pyi[k] * cam.width + px_i;
+        gk[k][0] = gp[0]; gk[k][1] = gp[plane]; gk[k][2] = gp[2 * plane];
         const float Tf = T_final[pix];
-        S0 = Tf * o.bg[0]; S1 = Tf * o.bg[1]; S2 = Tf * o.bg[2];
+        for (int ch = 0; ch < 3; ++ch) Sk[k][ch] = Tf * o.bg[ch];
         if (nch == 1) {
-            T = Tf;
-            stop = r.x + n_contrib[pix];
+            Tk[k] = Tf;
+            stop[k] = r.x + n_contrib[pix];
         } else {
             const int64_t i0 = tile_item0[tile];
-            const int64_t slot = (int64_t)item * NT + ly * TW + lx;   // the scratch is row-major per tile
-            T = scTend[slot];
+            const int64_t slot = (int64_t)item * NT + lyk[k] * TW + lx;   // the scratch is row-major per tile
+            Tk[k] = scTend[slot];
             const int l = sclast[slot];
-            stop = l < 0 ? begin : r.x + l;
+            stop[k] = l < 0 ? begin : r.x + l;
             for (int c = it.y + 1; c < nch; ++c) {
-                const int64_t sl = (i0 + c) * NT + ly * TW + lx;
-                S0 += scC[3 * sl]; S1 += scC[3 * sl + 1]; S2 += scC[3 * sl + 2];
+                const int64_t sl = (i0 + c) * NT + lyk[k] * TW + lx;
+                for (int ch = 0; ch < 3; ++ch) Sk[k][ch] += scC[3 * sl + ch];
             }
         }
     }
+    float2 T = make_float2(Tk[0], Tk[1]);
+    const float2 g0 = make_float2(gk[0][0], gk[1][0]), g1 = make_float2(gk[0][1], gk[1][1]),
+                 g2 = make_float2(gk[0][2], gk[1][2]);
+    float2 S0 = make_float2(Sk[0][0], Sk[1][0]), S1 = make_float2(Sk[0][1], Sk[1][1]), S2 = make_float2(Sk[0][2], Sk[1][2]);
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    atomicMax(&s_max, stop - begin);
+    atomicMax(&s_max, max(stop[0], stop[1]) - begin);
     __syncthreads();
     const int count = s_max;
-    const int last = stop - begin;
+    const int last0 = stop[0] - begin, last1 = stop[1] - begin;
     const float clampv = o.alpha_clamp, afloor = o.alpha_floor;
-    for (int end = count; end > 0; end -= NT) {
-        const int n = min(NT, end);
+    for (int end = count; end > 0; end -= NT2) {
+        const int n = min(NT2, end);
         const int first = end - n;
         __syncthreads();
         if ((int)threadIdx.x < n) {
@@ -172,10 +192,10 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
             const float4 bb = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
             s_b[threadIdx.x] = bb;
             s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
-            s_m[threadIdx.x] = warp_mask<TW, TH>(a, bb.x, d, ox, oy);
+            s_m[threadIdx.x] = warp_mask<TW, TH, 8>(a, bb.x, d, ox, oy);
         }
         __syncthreads();
-        // back to front over the splats whose alpha-floor box reaches this warp's pixels
+        // back to front over the splats that reach this warp's pixels
         for (int base = ((n - 1) >> 5) << 5; base >= 0; base -= 32) {
           const uint32_t mm = (base + lane < n) ? s_m[base + lane] : 0u;
           uint32_t bits = __ballot_sync(0xffffffffu, (mm >> warp) & 1u);
@@ -184,54 +204,63 @@ __global__ void __launch_bounds__(TW * TH) backward_blend_kernel(const DevCam* _
             bits &= ~(1u << hb);
             const int j = base + hb;
             const int pos = first + j;
-            float gu = 0, gv = 0, gca = 0, gcb = 0, gcc = 0, gon = 0, gop = 0, gr = 0, gg = 0, gb = 0;
-            bool contrib = false;
-            if (pos < last) {
-                const float4 a = s_a[j], b = s_b[j], c = s_c[j];
-                const float dx = fsub(px, a.x), dy = fsub(py, a.y);
-                const float h = ffma(a.z, dx, fmul(a.w, dy));
-                const float gq = fmul(fmul(b.x, dy), dy);
-                const float p2 = ffma(dx, h, gq);
-                const float G = ex2_approx(p2);
-                const float xn = fmul(b.y, G);
-                const float an = fminf(clampv, xn);
-                float alpha = an, ap = 0.0f, xp = 0.0f;
-                if (b.w != 0.0f) {
-                    xp = fmul(b.z, G);
-                    ap = fminf(clampv, xp);
-                    alpha = ffma(b.w, alpha_prime(ap, c.w), fmul(fsub(1.0f, b.w), an));
-                }
-                if (alpha >= afloor) {
-                    contrib = true;
-                    // one approximate reciprocal instead of four divisions (values, not decisions)
-                    const float inv = __fdividef(1.0f, 1.0f - alpha);
-                    T = T * inv;
-                    const float wgt = alpha * T;
-                    gr = g0 * wgt; gg = g1 * wgt; gb = g2 * wgt;
-                    const float dalpha = g0 * (T * c.x - S0 * inv) + g1 * (T * c.y - S1 * inv) + g2 * (T * c.z - S2 * inv);
-                    S0 = fmaf(c.x, wgt, S0); S1 = fmaf(c.y, wgt, S1); S2 = fmaf(c.z, wgt, S2);
-                    float dG = 0.0f;
-                    const float dan = (b.w == 0.0f) ? dalpha : (1.0f - b.w) * dalpha;
-                    if (xn < clampv) { gon = dan * G; dG += dan * b.y; }
-                    if (b.w != 0.0f && xp < clampv) {
-                        const float dap = b.w * dalpha * alpha_prime_grad(ap, c.w);
-                        gop = dap * G;
-                        dG += dap * b.z;
-                    }
-                    const float dp2 = dG * G * LN2;
-                    gca = dp2 * dx * dx;
-                    gcb = dp2 * dx * dy;
-                    gcc = dp2 * dy * dy;
-                    gu = -dp2 * (2.0f * a.z * dx + a.w * dy);
-                    gv = -dp2 * (a.w * dx + 2.0f * b.x * dy);
-                }
+            const bool act0 = pos < last0, act1 = pos < last1;
+            if (!__any_sync(0xffffffffu, act0 || act1)) continue;
+            const float4 a = s_a[j], b = s_b[j], c = s_c[j];
+            // alpha exactly as the forward pass computed it (same fp32 order, paired per element)
+            const float dx = fsub(px, a.x);
+            const float2 dy = add2(py, f2(-a.y));
+            const float2 h = fma2(f2(a.z), f2(dx), mul2(f2(a.w), dy));
+            const float2 gq = mul2(mul2(f2(b.x), dy), dy);
+            const float2 p2 = fma2(f2(dx), h, gq);
+            const float2 G = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
+            const float2 xn = mul2(f2(b.y), G);
+            const float2 an = make_float2(fminf(clampv, xn.x), fminf(clampv, xn.y));
+            float2 alpha = an, ap = f2(0.0f), xp = f2(0.0f);
+            const bool interp = b.w != 0.0f;   // uniform over the warp
+            if (interp) {
+                xp = mul2(f2(b.z), G);
+                ap = make_float2(fminf(clampv, xp.x), fminf(clampv, xp.y));
+                const float omw = fsub(1.0f, b.w);
+                alpha = fma2(f2(b.w), make_float2(alpha_prime(ap.x, c.w), alpha_prime(ap.y, c.w)), mul2(f2(omw), an));
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                float v[16] = {gu, gv, gca, gcb, gcc, gon, gop, gr, gg, gb, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                const float sum = warp_reduce_scatter16(v, lane);
-                const int k = (lane >> 1) & 15;
-                if (!(lane & 1) && k < 10) atomicAdd(sgrad + 12 * (int64_t)s_id[j] + k, sum);
+            const bool con0 = act0 && alpha.x >= afloor, con1 = act1 && alpha.y >= afloor;
+            if (!__any_sync(0xffffffffu, con0 || con1)) continue;
+            // one approximate reciprocal per pixel instead of four divisions (values, not decisions)
+            const float2 inv = make_float2(__fdividef(1.0f, 1.0f - alpha.x), __fdividef(1.0f, 1.0f - alpha.y));
+            T = sel2(con0, con1, mul2(T, inv), T);
+            const float2 wgt = mul2(alpha, T);
+            const float2 gr = mul2(g0, wgt), gg = mul2(g1, wgt), gb = mul2(g2, wgt);
+            float2 dal = mul2(g0, fma2(T, f2(c.x), mul2(f2(-1.0f), mul2(S0, inv))));
+            dal = fma2(g1, fma2(T, f2(c.y), mul2(f2(-1.0f), mul2(S1, inv))), dal);
+            dal = fma2(g2, fma2(T, f2(c.z), mul2(f2(-1.0f), mul2(S2, inv))), dal);
+            S0 = sel2(con0, con1, fma2(f2(c.x), wgt, S0), S0);
+            S1 = sel2(con0, con1, fma2(f2(c.y), wgt, S1), S1);
+            S2 = sel2(con0, con1, fma2(f2(c.z), wgt, S2), S2);
+            const float2 dan = interp ? mul2(f2(1.0f - b.w), dal) : dal;
+            const bool nl0 = xn.x < clampv, nl1 = xn.y < clampv;
+            const float2 gon = sel2(nl0, nl1, mul2(dan, G), f2(0.0f));
+            float2 dG = sel2(nl0, nl1, mul2(dan, f2(b.y)), f2(0.0f));
+            float2 gop = f2(0.0f);
+            if (interp) {
+                const bool pl0 = xp.x < clampv, pl1 = xp.y < clampv;
+                const float2 dap = mul2(mul2(f2(b.w), dal),
+                                        make_float2(alpha_prime_grad(ap.x, c.w), alpha_prime_grad(ap.y, c.w)));
+                gop = sel2(pl0, pl1, mul2(dap, G), f2(0.0f));
+                dG = sel2(pl0, pl1, fma2(dap, f2(b.z), dG), dG);
             }
+            const float2 dp2 = mul2(mul2(dG, G), f2(LN2));
+            const float2 dxx = f2(dx * dx);
+            const float2 gca = mul2(dp2, dxx), gcb = mul2(mul2(dp2, f2(dx)), dy), gcc = mul2(mul2(dp2, dy), dy);
+            const float2 gu = mul2(f2(-1.0f), mul2(dp2, fma2(f2(2.0f * a.z), f2(dx), mul2(f2(a.w), dy))));
+            const float2 gv = mul2(f2(-1.0f), mul2(dp2, fma2(f2(a.w), f2(dx), mul2(f2(2.0f * b.x), dy))));
+            // both pixels' contributions of this splat (a pixel that does not take it adds zero)
+            auto sum2 = [&](float2 x) { return (con0 ? x.x : 0.0f) + (con1 ? x.y : 0.0f); };
+            float v[16] = {sum2(gu), sum2(gv), sum2(gca), sum2(gcb), sum2(gcc), sum2(gon), sum2(gop), sum2(gr),
+                           sum2(gg), sum2(gb), 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float sum = warp_reduce_scatter16(v, lane);
+            const int kk = (lane >> 1) & 15;
+            if (!(lane & 1) && kk < 10) atomicAdd(sgrad + 12 * (int64_t)s_id[j] + kk, sum);
           }
         }
     }
@@ -463,7 +492,7 @@ cudaError_t launch_backward(const DevHier& h, const BlendArgs& a, const int32_t*
     if (a.n_tiles > 0) {
         const unsigned ig = (unsigned)a.item_cap;
 #define BW(TWV, THV)                                                                                              \
-    backward_blend_kernel<TWV, THV><<<ig, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat,    \
+    backward_blend_kernel<TWV, THV><<<ig, TWV * THV / 2, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat,    \
                                                              a.items, a.n_items, a.tile_item0, a.tile_nch, a.chunk, \
                                                              a.scratch_C, a.scratch_Tend, a.scratch_last, a.T_final, \
                                                              a.n_contrib, dL, splat_grad)
