@@ -42,6 +42,9 @@ REF_BUDGET_S = 120.0
 #   With t != 0: o_p G, min, 1 - ap, 1 + sqrt, divide, 1 - t, (1 - t) alpha_n, fma(t, a', .) -> +10 flops.
 FLOPS_PER_EVAL = 22
 FLOPS_PER_EVAL_T = 10
+# DRAM bytes (read + write) of one launch of the blend's main kernel at the 1080p corridor frame
+# (16x16 tiles, chunk 512), from an ncu capture of the current kernel; None once the kernel changes
+BLEND_TRAFFIC_BYTES = 31.163904e6 + 8.637696e6
 
 
 def parse():
@@ -351,19 +354,22 @@ def run_ours(args, rank, world, local):
         batched = run_batched(args, ctx, hier, flush, dev, stream) if args.batch_views > 0 else None
         optimisation = run_optimisation(args, dev, stream) if args.opt_leaves > 0 else None
 
-    # ---- roofline of the dominant kernel (the blend: FP32/MUFU issue-bound)
+    # ---- roofline of the dominant kernel: the blend's main kernel (FP32 issue-bound)
     peaks = measured_peaks()
-    blend_ms = fwd_stages.get("blend", 0.0)
+    queue_ms = fwd_stages.get("blend_queue", 0.0)   # events around that kernel alone, on its stream
     n_evals = int(st["n_evals"])
     flops = n_evals * FLOPS_PER_EVAL
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     fp32_peak_tflops = 148 * 128 * 2 * sm_max * 1e6 / 1e12
-    achieved = flops / (blend_ms * 1e-3) / 1e12 if blend_ms > 0 else None
-    roofline = {"kernel": "blend_kernel<16,16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+    achieved = flops / (queue_ms * 1e-3) / 1e12 if queue_ms > 0 else None
+    roofline = {"kernel": "blend_queue_kernel<16,16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": (achieved / fp32_peak_tflops) if achieved else None,
-                "traffic": None,
+                "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk == 512) else None,
+                "kernel_ms": queue_ms,
                 "peak_note": "148 SMs x 128 FP32 lanes x 2 (FFMA) x max SM clock from MEASURED_PEAKS.json",
-                "work_note": f"{FLOPS_PER_EVAL} FP32 flops per evaluated (pixel, splat) pair x {n_evals} pairs"}
+                "work_note": f"{FLOPS_PER_EVAL} FP32 flops per main-pass (pixel, splat) evaluation x {n_evals}; the "
+                             f"{int(st['n_evals_tpass'])} transmittance-pass evaluations of split tiles are not counted",
+                "traffic_note": "DRAM read + write of one launch from an ncu capture of this kernel at this workload"}
     hbm = float(peaks.get("hbm_gbs", 6442.9))
     stage_bw = {}
     M, V, Pn = int(st["n_cut"]), int(st["n_visible"]), int(st["n_pairs"])

@@ -132,6 +132,7 @@ typedef enum {
     H3DGS_STAGE_BLEND,          /* a7: per-tile blend                                */
     H3DGS_STAGE_BACKWARD_BLEND, /* a8: reverse per-tile blend                        */
     H3DGS_STAGE_BACKWARD_SPLAT, /* a8: projection/interpolation adjoint and scatter  */
+    H3DGS_STAGE_BLEND_QUEUE,    /* a7: the blend's main kernel alone (inside BLEND)  */
     H3DGS_STAGE_COUNT
 } h3dgs_stage;
 

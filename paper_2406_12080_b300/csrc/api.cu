@@ -221,6 +221,7 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images) {
     a.work = P<uint32_t>(ctx->sortw);
     a.work_words = ctx->sortw.n / sizeof(uint32_t);
     a.flags = P<uint32_t>(ctx->counters) + C_FLAGS;
+    a.ev_queue = nullptr;
     return a;
 }
 
@@ -590,6 +591,10 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
         ctx->opts = o;
         ctx->pairs_in_1 = in1;
         BlendArgs ba = blend_args(ctx, n_cams, images);
+        if (ctx->prof) {
+            ba.ev_queue = ctx->ev + 2 * H3DGS_STAGE_BLEND_QUEUE;
+            ctx->ev_used[H3DGS_STAGE_BLEND_QUEUE] = true;
+        }
         CK(launch_blend(ba, s), "blend");
     }
     stage_end(ctx, H3DGS_STAGE_BLEND);

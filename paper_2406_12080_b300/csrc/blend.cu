@@ -468,11 +468,13 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     const unsigned tg = (unsigned)a.n_tiles;
 #define BL(TWV, THV)                                                                                                  \
     do {                                                                                                              \
+        if (a.ev_queue) cudaEventRecord(a.ev_queue[0], s);                                                            \
         blend_queue_kernel<TWV, THV><<<gq, TWV * THV / 2, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat,       \
                                                               a.items, a.q_prod, a.q_single, a.q_cons, a.n_items,     \
                                                               a.tile_item0, a.tile_nch, a.chunk, sc, a.queue_sync,    \
                                                               a.queue_sync + 1, a.images, a.T_final, a.n_contrib,     \
                                                               a.n_evals, a.flags);                                    \
+        if (a.ev_queue) cudaEventRecord(a.ev_queue[1], s);                                                            \
         blend_combine_kernel<TWV, THV><<<tg, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.n_tiles, a.tile_item0,       \
                                                                 a.tile_nch, sc, a.images, a.T_final, a.n_contrib);    \
     } while (0)

@@ -277,6 +277,7 @@ struct BlendArgs {
     uint32_t* work;               // look-back workspace of the plan (LB_HEADER_WORDS + 2 per 1024 tiles)
     size_t work_words;
     uint32_t* flags;              // device flag word
+    cudaEvent_t* ev_queue;        // 2 events around the main blend kernel (profiling), or NULL
 };
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
 

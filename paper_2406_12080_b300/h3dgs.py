@@ -64,7 +64,7 @@ class h3dgs_stats(C.Structure):
 
 
 STAGES = ["cut", "preprocess", "depth_sort", "duplicate", "tile_sort", "ranges", "blend", "backward_blend",
-          "backward_splat"]
+          "backward_splat", "blend_queue"]
 
 
 _lib = None
