@@ -282,7 +282,11 @@ def run_ours(args, rank, world, local):
             launches = launches_per_frame(int(st["n_tiles"]))
             launch_src = f"launch sites ({type(e).__name__})"
 
-        # ---- per-stage times (events inside the library, same ABI calls, not graphed)
+        # ---- evaluation counts (profiling level 2), then per-stage times (level 1: events inside the
+        # library around the same ABI calls, not graphed)
+        h3dgs.h3dgs_set_profiling(ctx.ctx, 2)
+        frame()
+        st_counts = h3dgs.h3dgs_get_stats(ctx.ctx)
         h3dgs.h3dgs_set_profiling(ctx.ctx, 1)
         stage_acc = {}
         n_prof = max(3, min(args.steps, 20))
@@ -293,7 +297,8 @@ def run_ours(args, rank, world, local):
                 stage_acc[k] = stage_acc.get(k, 0.0) + v
             flush.fill_(1.0)
         fwd_stages = {k: v / n_prof for k, v in stage_acc.items() if v > 0}
-        st = h3dgs.h3dgs_get_stats(ctx.ctx)
+        st = dict(h3dgs.h3dgs_get_stats(ctx.ctx))
+        st["n_evals"], st["n_evals_tpass"] = st_counts["n_evals"], st_counts["n_evals_tpass"]
 
         # ---- fwd + bwd views/s
         grads = {k: torch.zeros_like(getattr(hier, k)) for k in ("mean", "scale", "rot", "opacity", "sh")}

@@ -115,8 +115,10 @@ typedef struct {
                               bounded wait of one thread block on another (sort,
                               scan or blend queue) gave up: the frame is invalid,
                               the context stays usable                            */
-    int64_t n_evals;      /* (pixel, splat) evaluations of the blend's main pass */
-    int64_t n_evals_tpass; /* extra evaluations of the transmittance pass of split tiles */
+    int64_t n_evals;      /* (pixel, splat) evaluations of the blend's main pass
+                             (counted only at profiling level 2, else 0)        */
+    int64_t n_evals_tpass; /* extra evaluations of the transmittance pass of split tiles
+                             (likewise)                                          */
     int64_t n_items;      /* blend work items (tiles, split tiles count once per chunk) */
 } h3dgs_stats;
 
@@ -295,8 +297,9 @@ h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL_dimages, cons
 /* Counters of the last render (synchronises the stream). */
 h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out);
 
-/* Enable (1) or disable (0) per-stage event timing.  While enabled every stage is bracketed by
- * CUDA events on the context's stream (do not capture such calls in a CUDA graph). */
+/* Profiling level: 0 off; 1 per-stage event timing (every stage bracketed by CUDA events on the
+ * context's stream; do not capture such calls in a CUDA graph); 2 timing plus the blend's
+ * evaluation counters of h3dgs_stats (which slow the blend down: time with level 1). */
 h3dgs_status h3dgs_set_profiling(h3dgs_ctx* ctx, int32_t enable);
 
 /* Stage times (ms) of the last profiled calls, indexed by h3dgs_stage; ms must hold

@@ -44,15 +44,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
-    objs = []
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
-    for src in SOURCES:
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
-        if verbose:
+    objs = [os.path.join(BUILD_DIR, src.replace(".cu", ".o")) for src in SOURCES]
+    cmds = [[nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj] for src, obj in zip(SOURCES, objs)]
+    if verbose:
+        for cmd in cmds:
             print(" ".join(cmd), flush=True)
-        subprocess.check_call(cmd)
-        objs.append(obj)
+    # translation units compile independently: run them side by side
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
+        list(ex.map(subprocess.check_call, cmds))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     if verbose:

@@ -75,6 +75,7 @@ struct h3dgs_ctx {
     bool pairs_in_1 = false;
     // profiling
     bool prof = false;
+    bool count = false;   // blend evaluation counters (profiling level 2)
     cudaEvent_t ev[2 * H3DGS_STAGE_COUNT] = {};
     bool ev_used[H3DGS_STAGE_COUNT] = {};
 };
@@ -217,7 +218,8 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images) {
     a.images = images;
     a.T_final = P<float>(ctx->T_final);
     a.n_contrib = P<int32_t>(ctx->n_contrib);
-    a.n_evals = reinterpret_cast<unsigned long long*>(P<uint32_t>(ctx->counters) + C_EVALS);
+    // evaluation counters only at profiling level 2 (counting costs instructions in the blend's inner loop)
+    a.n_evals = ctx->count ? reinterpret_cast<unsigned long long*>(P<uint32_t>(ctx->counters) + C_EVALS) : nullptr;
     a.work = P<uint32_t>(ctx->sortw);
     a.work_words = ctx->sortw.n / sizeof(uint32_t);
     a.flags = P<uint32_t>(ctx->counters) + C_FLAGS;
@@ -661,6 +663,7 @@ h3dgs_status h3dgs_set_profiling(h3dgs_ctx* ctx, int32_t enable) {
     if (enable && !ctx->ev[0])
         for (auto& e : ctx->ev) CK(cudaEventCreate(&e), "event create");
     ctx->prof = enable != 0;
+    ctx->count = enable >= 2;
     for (bool& u : ctx->ev_used) u = false;
     return H3DGS_OK;
 }

@@ -115,9 +115,8 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
                                                                      const float* __restrict__ dL,
                                                                      float* __restrict__ sgrad) {
     constexpr int NT = TW * TH, NT2 = NT / 2;
-    __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];
-    __shared__ uint32_t s_id[NT2], s_m[NT2];
-    __shared__ int s_max;
+    __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];   // one 32-entry slice per warp
+    __shared__ uint32_t s_id[NT2];
     const uint32_t item = blockIdx.x;
     if (item >= *n_items) return;
     const int2 it = items[item];
@@ -172,41 +171,44 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
     const float2 g0 = make_float2(gk[0][0], gk[1][0]), g1 = make_float2(gk[0][1], gk[1][1]),
                  g2 = make_float2(gk[0][2], gk[1][2]);
     float2 S0 = make_float2(Sk[0][0], Sk[1][0]), S1 = make_float2(Sk[0][1], Sk[1][1]), S2 = make_float2(Sk[0][2], Sk[1][2]);
-    if (threadIdx.x == 0) s_max = 0;
-    __syncthreads();
-    atomicMax(&s_max, max(stop[0], stop[1]) - begin);
-    __syncthreads();
-    const int count = s_max;
+    // every warp walks its own pipeline back to front from the last entry any of its pixels took
+    int count = max(stop[0], stop[1]) - begin;
+    count = __reduce_max_sync(0xffffffffu, count);
     const int last0 = stop[0] - begin, last1 = stop[1] - begin;
     const float clampv = o.alpha_clamp, afloor = o.alpha_floor;
-    for (int end = count; end > 0; end -= NT2) {
-        const int n = min(NT2, end);
-        const int first = end - n;
-        __syncthreads();
-        if ((int)threadIdx.x < n) {
-            const uint32_t s = __ldg(list + begin + first + threadIdx.x);
+    constexpr int WX = TW / 8;
+    float4* wa = s_a + 32 * warp;
+    float4* wb = s_b + 32 * warp;
+    float4* wc = s_c + 32 * warp;
+    uint32_t* wid = s_id + 32 * warp;
+    const float bx0 = (float)(ox + (warp % WX) * 8) + 0.5f, by0 = (float)(oy + (warp / WX) * 8) + 0.5f;
+    for (int end = count; end > 0; end -= 32) {
+        const int first = max(0, end - 32);
+        bool hit = false;
+        if (first + lane < end) {
+            const uint32_t s = __ldg(list + begin + first + lane);
             const float4 a = __ldg(splat + SPLAT_F4 * (int64_t)s);
-            const float4 d = __ldg(splat + SPLAT_F4 * (int64_t)s + 3);
-            s_id[threadIdx.x] = s;
-            s_a[threadIdx.x] = a;
             const float4 bb = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
-            s_b[threadIdx.x] = bb;
-            s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
-            s_m[threadIdx.x] = warp_mask<TW, TH, 8>(a, bb.x, d, ox, oy);
+            const float4 d = __ldg(splat + SPLAT_F4 * (int64_t)s + 3);
+            hit = block_reach<8, 8>(a, bb.x, d, bx0, by0);
+            if (hit) {
+                wid[lane] = s;
+                wa[lane] = a;
+                wb[lane] = bb;
+                wc[lane] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
+            }
         }
-        __syncthreads();
+        uint32_t bits = __ballot_sync(0xffffffffu, hit);
+        __syncwarp();
         // back to front over the splats that reach this warp's pixels
-        for (int base = ((n - 1) >> 5) << 5; base >= 0; base -= 32) {
-          const uint32_t mm = (base + lane < n) ? s_m[base + lane] : 0u;
-          uint32_t bits = __ballot_sync(0xffffffffu, (mm >> warp) & 1u);
           while (bits) {
             const int hb = 31 - __clz(bits);
             bits &= ~(1u << hb);
-            const int j = base + hb;
+            const int j = hb;
             const int pos = first + j;
             const bool act0 = pos < last0, act1 = pos < last1;
             if (!__any_sync(0xffffffffu, act0 || act1)) continue;
-            const float4 a = s_a[j], b = s_b[j], c = s_c[j];
+            const float4 a = wa[j], b = wb[j], c = wc[j];
             // alpha exactly as the forward pass computed it (same fp32 order, paired per element)
             const float dx = fsub(px, a.x);
             const float2 dy = add2(py, f2(-a.y));
@@ -260,9 +262,9 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
                            sum2(gg), sum2(gb), 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const float sum = warp_reduce_scatter16(v, lane);
             const int kk = (lane >> 1) & 15;
-            if (!(lane & 1) && kk < 10) atomicAdd(sgrad + 12 * (int64_t)s_id[j] + kk, sum);
+            if (!(lane & 1) && kk < 10) atomicAdd(sgrad + 12 * (int64_t)wid[j] + kk, sum);
           }
-        }
+        __syncwarp();   // the slice is refilled by the next round
     }
 }
 
@@ -431,33 +433,50 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         dY[13][0] = -SH_C3C * (4.f * z2 - 3.f * xx - yy); dY[13][1] = 2.f * SH_C3C * x * y; dY[13][2] = -8.f * SH_C3C * x * zz;
         dY[14][0] = 2.f * SH_C3E * zz * x; dY[14][1] = -2.f * SH_C3E * zz * y; dY[14][2] = SH_C3E * (xx - yy);
         dY[15][0] = -SH_C3A * (3.f * xx - 3.f * yy); dY[15][1] = 6.f * SH_C3A * x * y;
-        const float* shn = reinterpret_cast<const float*>(h.sh) + (int64_t)NSH * n;
-        const float* shp = reinterpret_cast<const float*>(h.sh) + (int64_t)NSH * (use_p ? p : n);
+        // SH rows as float4 (12 per node); loops fully unrolled so every Y / dY index is a constant
+        const float4* shn4 = h.sh + (int64_t)12 * n;
+        const float4* shp4 = h.sh + (int64_t)12 * (use_p ? p : n);
         float col[3] = {0.5f, 0.5f, 0.5f};
-        for (int c = 0; c < NSH; ++c) {
-            const float shv = use_p ? fmaf(t, shp[c], omt * shn[c]) : shn[c];
-            col[c % 3] += shv * Y[c / 3];
+#pragma unroll
+        for (int j4 = 0; j4 < 12; ++j4) {
+            const float4 a4 = __ldg(shn4 + j4);
+            float4 v4 = a4;
+            if (use_p) {
+                const float4 b4 = __ldg(shp4 + j4);
+                v4 = make_float4(fmaf(t, b4.x, omt * a4.x), fmaf(t, b4.y, omt * a4.y), fmaf(t, b4.z, omt * a4.z),
+                                 fmaf(t, b4.w, omt * a4.w));
+            }
+            const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) col[(4 * j4 + e) % 3] += vv[e] * Y[(4 * j4 + e) / 3];
         }
         float ddir[3] = {0.f, 0.f, 0.f};
         const float wn = use_p ? omt : 1.0f;
         const bool leaf_n = h.child_count[n] == 0;
         const bool write_n = !(freeze_leaves && leaf_n);
         // SH gradient in groups of 4 coefficients, one vector reduction per group and row
-        for (int c0 = 0; c0 < NSH; c0 += 4) {
+#pragma unroll
+        for (int j4 = 0; j4 < 12; ++j4) {
+            const float4 a4 = __ldg(shn4 + j4);
+            float4 v4 = a4;
+            if (use_p) {
+                const float4 b4 = __ldg(shp4 + j4);
+                v4 = make_float4(fmaf(t, b4.x, omt * a4.x), fmaf(t, b4.y, omt * a4.y), fmaf(t, b4.z, omt * a4.z),
+                                 fmaf(t, b4.w, omt * a4.w));
+            }
+            const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
             float g4[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = c0 + u, ch = c % 3;
+            for (int e = 0; e < 4; ++e) {
+                const int c = 4 * j4 + e, ch = c % 3;
                 const bool live = !(col[ch] < 0.0f);
-                g4[u] = live ? grgb[ch] * Y[c / 3] : 0.0f;
-                if (live) {
-                    const float shv = use_p ? fmaf(t, shp[c], omt * shn[c]) : shn[c];
-                    for (int j = 0; j < 3; ++j) ddir[j] += grgb[ch] * shv * dY[c / 3][j];
-                }
+                g4[e] = live ? grgb[ch] * Y[c / 3] : 0.0f;
+                if (live)
+                    for (int jj = 0; jj < 3; ++jj) ddir[jj] += grgb[ch] * vv[e] * dY[c / 3][jj];
             }
             if (g4[0] != 0.0f || g4[1] != 0.0f || g4[2] != 0.0f || g4[3] != 0.0f) {
-                if (write_n) red_add_v4(gout.sh + (int64_t)NSH * n + c0, wn * g4[0], wn * g4[1], wn * g4[2], wn * g4[3]);
-                if (use_p) red_add_v4(gout.sh + (int64_t)NSH * p + c0, t * g4[0], t * g4[1], t * g4[2], t * g4[3]);
+                if (write_n) red_add_v4(gout.sh + (int64_t)NSH * n + 4 * j4, wn * g4[0], wn * g4[1], wn * g4[2], wn * g4[3]);
+                if (use_p) red_add_v4(gout.sh + (int64_t)NSH * p + 4 * j4, t * g4[0], t * g4[1], t * g4[2], t * g4[3]);
             }
         }
         const float dot = ddir[0] * x + ddir[1] * y + ddir[2] * zz;

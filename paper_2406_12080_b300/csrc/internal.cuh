@@ -118,52 +118,52 @@ __device__ __forceinline__ void tile_pixel2(int tid, int& lx, int& ly0) {
     ly0 = (w / WX) * 8 + (l >> 3);
 }
 
+// Whether the splat can reach alpha_floor at a pixel centre of the block [x0, x0 + BW - 1] x
+// [y0, y0 + BH - 1] (pixel-centre coordinates): the box test, then the minimum of q = -p2 over the
+// block (the centre if inside, else the best point of the four edges) against rz.
+template <int BW, int BH>
+__device__ __forceinline__ bool block_reach(const float4 a, float cc, const float4 d, float x0, float y0) {
+    const float hx = d.x, hy = d.y;
+    if (!(hx >= 0.0f)) return false;
+    const float u = a.x, v = a.y;
+    const float x1 = x0 + (float)(BW - 1), y1 = y0 + (float)(BH - 1);
+    if (!(u + hx >= x0 && u - hx <= x1 && v + hy >= y0 && v - hy <= y1)) return false;
+    if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return true;
+    const float qa = -a.z, qb = -a.w, qc = -cc, rz = d.z;
+    // edge minimisers use approximate reciprocals: a slightly moved point on the edge changes q only
+    // to second order, far inside the 2% margin of rz
+    const float kx = -qb * __fdividef(0.5f, qc), ky = -qb * __fdividef(0.5f, qa);
+    const float dx0 = x0 - u, dx1 = x1 - u, dy0 = y0 - v, dy1 = y1 - v;
+    float qmin = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {   // vertical edges: best dy = clamp(-qb dx / (2 qc))
+        const float dx = e ? dx1 : dx0;
+        const float dy = fminf(fmaxf(kx * dx, dy0), dy1);
+        qmin = fminf(qmin, qa * dx * dx + qb * dx * dy + qc * dy * dy);
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {   // horizontal edges: best dx = clamp(-qb dy / (2 qa))
+        const float dy = e ? dy1 : dy0;
+        const float dx = fminf(fmaxf(ky * dy, dx0), dx1);
+        qmin = fminf(qmin, qa * dx * dx + qb * dx * dy + qc * dy * dy);
+    }
+    return !(qmin > rz);   // NaN keeps the block
+}
+
 // Bit w set if the splat can reach alpha_floor at a pixel centre of warp w's 8 x BH block in the tile
 // with pixel origin (ox, oy); a clear bit means alpha < alpha_floor at every pixel of the block, so
 // the warp would skip the splat anyway.  a = {u, v, ca, cb}, cc = the third conic term (pre-scaled:
 // the exponent is p2 = ca dx^2 + cb dx dy + cc dy^2), d = {hx, hy, rz, 0}: hx, hy are the inflated
 // half-widths of the bounding box of the level set o_max 2^p2 = alpha_floor and rz = log2(o_max /
-// alpha_floor) inflated by 2% + 0.02; hx < 0 marks a splat that never reaches the floor.  A block
-// passing the box test is kept only if the minimum of q = -p2 over the block (a convex quadratic:
-// the centre if inside, else the best point of the four edges) is at most rz.
+// alpha_floor) inflated by 2% + 0.02; hx < 0 marks a splat that never reaches the floor.
 template <int TW, int TH, int BH = 4>
 __device__ __forceinline__ uint32_t warp_mask(const float4 a, float cc, const float4 d, int ox, int oy) {
-    const float hx = d.x, hy = d.y;
-    if (!(hx >= 0.0f)) return 0u;
     constexpr int NW = TW * TH / (8 * BH), WX = TW / 8;
-    const float u = a.x, v = a.y;
-    const float qa = -a.z, qb = -a.w, qc = -cc, rz = d.z;
-    // edge minimisers use approximate reciprocals: a slightly moved point on the edge changes q only
-    // to second order, far inside the 2% margin of rz
-    const float kx = -qb * __fdividef(0.5f, qc), ky = -qb * __fdividef(0.5f, qa);
     uint32_t m = 0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        const float x0 = (float)(ox + (w % WX) * 8) + 0.5f, x1 = x0 + 7.0f;
-        const float y0 = (float)(oy + (w / WX) * BH) + 0.5f, y1 = y0 + (float)(BH - 1);
-        if (!(u + hx >= x0 && u - hx <= x1 && v + hy >= y0 && v - hy <= y1)) continue;
-        if (u >= x0 && u <= x1 && v >= y0 && v <= y1) {
+    for (int w = 0; w < NW; ++w)
+        if (block_reach<8, BH>(a, cc, d, (float)(ox + (w % WX) * 8) + 0.5f, (float)(oy + (w / WX) * BH) + 0.5f))
             m |= 1u << w;
-            continue;
-        }
-        const float dx0 = x0 - u, dx1 = x1 - u, dy0 = y0 - v, dy1 = y1 - v;
-        float qmin = __int_as_float(0x7f800000);
-        // vertical edges x = x0, x1: best dy = clamp(-qb dx / (2 qc))
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float dx = e ? dx1 : dx0;
-            const float dy = fminf(fmaxf(kx * dx, dy0), dy1);
-            qmin = fminf(qmin, qa * dx * dx + qb * dx * dy + qc * dy * dy);
-        }
-        // horizontal edges y = y0, y1: best dx = clamp(-qb dy / (2 qa))
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float dy = e ? dy1 : dy0;
-            const float dx = fminf(fmaxf(ky * dy, dx0), dx1);
-            qmin = fminf(qmin, qa * dx * dx + qb * dx * dy + qc * dy * dy);
-        }
-        if (!(qmin > rz)) m |= 1u << w;   // NaN keeps the block
-    }
     return m;
 }
 
