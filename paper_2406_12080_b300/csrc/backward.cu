@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
                                                                      const float* __restrict__ dL,
                                                                      float* __restrict__ sgrad) {
     constexpr int NT = TW * TH, NT2 = NT / 2;
-    __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];   // one 32-entry slice per warp
-    __shared__ uint32_t s_id[NT2];
+    __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];
+    __shared__ uint32_t s_id[NT2], s_m[NT2];
+    __shared__ int s_max;
     const uint32_t item = blockIdx.x;
     if (item >= *n_items) return;
     const int2 it = items[item];
@@ -171,44 +172,41 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
     const float2 g0 = make_float2(gk[0][0], gk[1][0]), g1 = make_float2(gk[0][1], gk[1][1]),
                  g2 = make_float2(gk[0][2], gk[1][2]);
     float2 S0 = make_float2(Sk[0][0], Sk[1][0]), S1 = make_float2(Sk[0][1], Sk[1][1]), S2 = make_float2(Sk[0][2], Sk[1][2]);
-    // every warp walks its own pipeline back to front from the last entry any of its pixels took
-    int count = max(stop[0], stop[1]) - begin;
-    count = __reduce_max_sync(0xffffffffu, count);
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    atomicMax(&s_max, max(stop[0], stop[1]) - begin);
+    __syncthreads();
+    const int count = s_max;
     const int last0 = stop[0] - begin, last1 = stop[1] - begin;
     const float clampv = o.alpha_clamp, afloor = o.alpha_floor;
-    constexpr int WX = TW / 8;
-    float4* wa = s_a + 32 * warp;
-    float4* wb = s_b + 32 * warp;
-    float4* wc = s_c + 32 * warp;
-    uint32_t* wid = s_id + 32 * warp;
-    const float bx0 = (float)(ox + (warp % WX) * 8) + 0.5f, by0 = (float)(oy + (warp / WX) * 8) + 0.5f;
-    for (int end = count; end > 0; end -= 32) {
-        const int first = max(0, end - 32);
-        bool hit = false;
-        if (first + lane < end) {
-            const uint32_t s = __ldg(list + begin + first + lane);
+    for (int end = count; end > 0; end -= NT2) {
+        const int n = min(NT2, end);
+        const int first = end - n;
+        __syncthreads();
+        if ((int)threadIdx.x < n) {
+            const uint32_t s = __ldg(list + begin + first + threadIdx.x);
             const float4 a = __ldg(splat + SPLAT_F4 * (int64_t)s);
-            const float4 bb = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
             const float4 d = __ldg(splat + SPLAT_F4 * (int64_t)s + 3);
-            hit = block_reach<8, 8>(a, bb.x, d, bx0, by0);
-            if (hit) {
-                wid[lane] = s;
-                wa[lane] = a;
-                wb[lane] = bb;
-                wc[lane] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
-            }
+            s_id[threadIdx.x] = s;
+            s_a[threadIdx.x] = a;
+            const float4 bb = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
+            s_b[threadIdx.x] = bb;
+            s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
+            s_m[threadIdx.x] = warp_mask<TW, TH, 8>(a, bb.x, d, ox, oy);
         }
-        uint32_t bits = __ballot_sync(0xffffffffu, hit);
-        __syncwarp();
+        __syncthreads();
         // back to front over the splats that reach this warp's pixels
+        for (int base = ((n - 1) >> 5) << 5; base >= 0; base -= 32) {
+          const uint32_t mm = (base + lane < n) ? s_m[base + lane] : 0u;
+          uint32_t bits = __ballot_sync(0xffffffffu, (mm >> warp) & 1u);
           while (bits) {
             const int hb = 31 - __clz(bits);
             bits &= ~(1u << hb);
-            const int j = hb;
+            const int j = base + hb;
             const int pos = first + j;
             const bool act0 = pos < last0, act1 = pos < last1;
             if (!__any_sync(0xffffffffu, act0 || act1)) continue;
-            const float4 a = wa[j], b = wb[j], c = wc[j];
+            const float4 a = s_a[j], b = s_b[j], c = s_c[j];
             // alpha exactly as the forward pass computed it (same fp32 order, paired per element)
             const float dx = fsub(px, a.x);
             const float2 dy = add2(py, f2(-a.y));
@@ -262,9 +260,9 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
                            sum2(gg), sum2(gb), 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const float sum = warp_reduce_scatter16(v, lane);
             const int kk = (lane >> 1) & 15;
-            if (!(lane & 1) && kk < 10) atomicAdd(sgrad + 12 * (int64_t)wid[j] + kk, sum);
+            if (!(lane & 1) && kk < 10) atomicAdd(sgrad + 12 * (int64_t)s_id[j] + kk, sum);
           }
-        __syncwarp();   // the slice is refilled by the next round
+        }
     }
 }
 

@@ -203,71 +203,68 @@ struct Scratch {
     int32_t* last; // list position (within the tile) after the chunk's last contributor, or -1
 };
 
-// Walk of one item over list entries [begin, end) for this thread's two pixels.  Every warp runs its
-// own pipeline over the list: its lanes load 32 entries, test them against the warp's 8x8 block,
-// stage the hits in the warp's slice of shared memory and the warp blends them in list order; no
-// barrier couples the warps of a tile, so a warp with few hits moves on.  MAIN: the exact skip/stop
-// rules with colour; otherwise the transmittance pass (product of (1 - alpha) over contributors, no
-// colour; a pixel is finished once T < t_min, after which nothing it could add matters).  Per entry
-// the update is branch-free (selects) and the paired fp32 instructions evaluate both pixels at once.
+// Walk of one item over list entries [begin, end) for this thread's two pixels.  MAIN: the exact
+// skip/stop rules with colour; otherwise the transmittance pass (product of (1 - alpha) over
+// contributors, no colour; a pixel is finished once T < t_min, after which nothing it could add
+// matters).  Branch-free per entry: the alpha of every live pixel is computed and applied through
+// selects; the paired fp32 instructions evaluate both pixels at once.
 template <int TW, int TH, bool MAIN, bool COUNT>
 __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const uint32_t* __restrict__ list,
                                             const float4* __restrict__ splat, int begin, int end, int list0,
                                             float clampv, float afloor, float tmin, float4* s_a, float4* s_b,
-                                            float4* s_c, float2& T, float2& C0, float2& C1, float2& C2, int2& last,
-                                            bool& done0, bool& done1, unsigned int& evals) {
-    constexpr int WX = TW / 8;
+                                            float4* s_c, uint32_t* s_m, float2& T, float2& C0, float2& C1,
+                                            float2& C2, int2& last, bool& done0, bool& done1, unsigned int& evals) {
+    constexpr int NT2 = TW * TH / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* wa = s_a + 32 * warp;
-    float4* wb = s_b + 32 * warp;
-    float4* wc = s_c + 32 * warp;
-    const float bx0 = (float)(g.ox + (warp % WX) * 8) + 0.5f, by0 = (float)(g.oy + (warp / WX) * 8) + 0.5f;
-    for (int b0 = begin; b0 < end; b0 += 32) {
-        if (__all_sync(0xffffffffu, done0 && done1)) break;
-        bool hit = false;
-        if (b0 + lane < end) {
-            const uint32_t s = __ldg(list + b0 + lane);
+    for (int b0 = begin; b0 < end; b0 += NT2) {
+        if (__syncthreads_count(done0 && done1) == NT2) break;
+        const int n = min(NT2, end - b0);
+        if ((int)threadIdx.x < n) {
+            const uint32_t s = __ldg(list + b0 + threadIdx.x);
             const float4 a = __ldg(splat + SPLAT_F4 * (int64_t)s);
             const float4 bb = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
             const float4 d = __ldg(splat + SPLAT_F4 * (int64_t)s + 3);
-            hit = block_reach<8, 8>(a, bb.x, d, bx0, by0);
-            if (hit) {
-                wa[lane] = a;
-                wb[lane] = bb;
-                wc[lane] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
+            s_a[threadIdx.x] = a;
+            s_b[threadIdx.x] = bb;
+            s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
+            s_m[threadIdx.x] = warp_mask<TW, TH, 8>(a, bb.x, d, g.ox, g.oy);
+        }
+        __syncthreads();
+        if (__any_sync(0xffffffffu, !(done0 && done1))) {
+            for (int base = 0; base < n; base += 32) {
+                const uint32_t mm = (base + lane < n) ? s_m[base + lane] : 0u;
+                uint32_t bits = __ballot_sync(0xffffffffu, (mm >> warp) & 1u);
+                while (bits) {
+                    const int j = base + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (COUNT) evals += (unsigned)!done0 + (unsigned)!done1;
+                    const float2 alpha = pair_alpha2(g.px, g.py, s_a[j], s_b[j], &s_c[j], clampv);
+                    const bool live0 = !done0 && alpha.x >= afloor, live1 = !done1 && alpha.y >= afloor;
+                    if (!__any_sync(0xffffffffu, live0 || live1)) continue;   // no pixel of the warp takes it
+                    const float2 Tn = __fmul2_rn(T, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-alpha.x, -alpha.y)));
+                    if (MAIN) {
+                        const bool stop0 = live0 && Tn.x < tmin, stop1 = live1 && Tn.y < tmin;
+                        const bool app0 = live0 && !stop0, app1 = live1 && !stop1;
+                        done0 = done0 || stop0;
+                        done1 = done1 || stop1;
+                        const float2 wt = __fmul2_rn(alpha, T);
+                        const float2 w = make_float2(app0 ? wt.x : 0.0f, app1 ? wt.y : 0.0f);
+                        const float4 c = s_c[j];
+                        C0 = __ffma2_rn(make_float2(c.x, c.x), w, C0);
+                        C1 = __ffma2_rn(make_float2(c.y, c.y), w, C1);
+                        C2 = __ffma2_rn(make_float2(c.z, c.z), w, C2);
+                        T = make_float2(app0 ? Tn.x : T.x, app1 ? Tn.y : T.y);
+                        const int pos = b0 + j + 1 - list0;
+                        last = make_int2(app0 ? pos : last.x, app1 ? pos : last.y);
+                    } else {
+                        T = make_float2(live0 ? Tn.x : T.x, live1 ? Tn.y : T.y);
+                        done0 = done0 || (live0 && Tn.x < tmin);
+                        done1 = done1 || (live1 && Tn.y < tmin);
+                    }
+                }
+                if (__all_sync(0xffffffffu, done0 && done1)) break;
             }
         }
-        uint32_t bits = __ballot_sync(0xffffffffu, hit);
-        __syncwarp();
-        while (bits) {
-            const int j = __ffs(bits) - 1;
-            bits &= bits - 1;
-            if (COUNT) evals += (unsigned)!done0 + (unsigned)!done1;
-            const float2 alpha = pair_alpha2(g.px, g.py, wa[j], wb[j], &wc[j], clampv);
-            const bool live0 = !done0 && alpha.x >= afloor, live1 = !done1 && alpha.y >= afloor;
-            if (!__any_sync(0xffffffffu, live0 || live1)) continue;   // no pixel of the warp takes it
-            const float2 Tn = __fmul2_rn(T, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-alpha.x, -alpha.y)));
-            if (MAIN) {
-                const bool stop0 = live0 && Tn.x < tmin, stop1 = live1 && Tn.y < tmin;
-                const bool app0 = live0 && !stop0, app1 = live1 && !stop1;
-                done0 = done0 || stop0;
-                done1 = done1 || stop1;
-                const float2 wt = __fmul2_rn(alpha, T);
-                const float2 w = make_float2(app0 ? wt.x : 0.0f, app1 ? wt.y : 0.0f);
-                const float4 c = wc[j];
-                C0 = __ffma2_rn(make_float2(c.x, c.x), w, C0);
-                C1 = __ffma2_rn(make_float2(c.y, c.y), w, C1);
-                C2 = __ffma2_rn(make_float2(c.z, c.z), w, C2);
-                T = make_float2(app0 ? Tn.x : T.x, app1 ? Tn.y : T.y);
-                const int pos = b0 + j + 1 - list0;
-                last = make_int2(app0 ? pos : last.x, app1 ? pos : last.y);
-            } else {
-                T = make_float2(live0 ? Tn.x : T.x, live1 ? Tn.y : T.y);
-                done0 = done0 || (live0 && Tn.x < tmin);
-                done1 = done1 || (live1 && Tn.y < tmin);
-            }
-        }
-        __syncwarp();   // the slice is refilled by the next round
     }
 }
 
@@ -296,7 +293,8 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
                                                                   unsigned long long* __restrict__ n_evals,
                                                                   uint32_t* __restrict__ flags) {
     constexpr int NT = TW * TH, NT2 = NT / 2;
-    __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];   // one 32-entry slice per warp
+    __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];
+    __shared__ uint32_t s_m[NT2];
     __shared__ unsigned int s_evals[2];
     __shared__ uint32_t s_k;
     if (threadIdx.x == 0) s_k = atomicAdd(ticket, 1u);
@@ -345,10 +343,10 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     bool done0 = !g.in0 || T.x < o.t_min, done1 = !g.in1 || T.y < o.t_min;
     if (main_pass)
         blend_walk2<TW, TH, true, COUNT>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min, s_a,
-                                         s_b, s_c, T, C0, C1, C2, last, done0, done1, evals);
+                                         s_b, s_c, s_m, T, C0, C1, C2, last, done0, done1, evals);
     else
         blend_walk2<TW, TH, false, COUNT>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min, s_a,
-                                          s_b, s_c, T, C0, C1, C2, last, done0, done1, evals);
+                                          s_b, s_c, s_m, T, C0, C1, C2, last, done0, done1, evals);
     if (COUNT) {
         for (int off = 16; off > 0; off >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, off);
         if (lane == 0) atomicAdd(&s_evals[main_pass ? 0 : 1], evals);
