@@ -28,8 +28,10 @@ namespace h3dgs {
 
 constexpr int OS_THREADS = 256;                 // one thread per digit in the look-back
 constexpr int OS_WARPS = OS_THREADS / 32;
-constexpr int OS_IPT = 15;                      // keys per thread
-constexpr int OS_TILE = OS_THREADS * OS_IPT;    // 3840 keys per tile
+constexpr int OS_IPT_SMALL = 8;                 // keys per thread when all tiles fit one wave
+constexpr int OS_IPT_LARGE = 15;                // keys per thread otherwise
+constexpr int OS_TILE_SMALL = OS_THREADS * OS_IPT_SMALL;   // 2048 keys per tile
+constexpr int OS_TILE_LARGE = OS_THREADS * OS_IPT_LARGE;   // 3840 keys per tile
 constexpr unsigned long long ST_AGG = 1ull << 62;   // look-back word: tile's own digit count
 constexpr unsigned long long ST_INC = 2ull << 62;   // look-back word: count of this and all earlier tiles
 constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
@@ -128,6 +130,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_histogram_kernel(const uint3
 
 // One LSD pass.  n = *n_dev keys are read (dropping 0xffffffff keys if `drop`), the kept ones written;
 // without vin the values are the input positions.
+template <int OS_IPT>
 __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32_t* __restrict__ kin,
                                                                     const uint32_t* __restrict__ vin,
                                                                     uint32_t* __restrict__ kout,
@@ -141,6 +144,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
     __shared__ uint32_t s_wcnt[OS_WARPS][256];
     __shared__ uint32_t s_lstart[256];    // first staging slot of each digit in this tile
     __shared__ uint32_t s_gdst[256];      // global destination of each digit's first key of this tile
+    constexpr int OS_TILE = OS_THREADS * OS_IPT;
     __shared__ uint32_t s_keys[OS_TILE];
     __shared__ uint32_t s_vals[OS_TILE];
     __shared__ uint32_t s_warp[OS_WARPS];
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
 }
 
 size_t radix_work_words(int64_t n_cap) {
-    const int64_t tiles = std::max<int64_t>(1, (n_cap + OS_TILE - 1) / OS_TILE);
+    const int64_t tiles = std::max<int64_t>(1, (n_cap + OS_TILE_SMALL - 1) / OS_TILE_SMALL);
     return (size_t)(RADIX_HEADER_WORDS + 2 * 4 * tiles * 256);   // 64-bit look-back words
 }
 
@@ -268,7 +272,11 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
     if (n_cap <= 0) return cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s);
     if (n_cap > 0xffffffffLL || bits < 1 || bits > 32) return cudaErrorInvalidValue;
     const int passes = (bits + 7) / 8;
-    const int64_t tiles = (n_cap + OS_TILE - 1) / OS_TILE;
+    // small tiles (a shorter serial ranking chain per tile) while every tile of a pass fits one wave of
+    // resident blocks, larger tiles beyond
+    const bool small = (n_cap + OS_TILE_SMALL - 1) / OS_TILE_SMALL <= 3 * (int64_t)w.num_sms;
+    const int64_t tile_keys = small ? OS_TILE_SMALL : OS_TILE_LARGE;
+    const int64_t tiles = (n_cap + tile_keys - 1) / tile_keys;
     if (radix_work_words(n_cap) > w.words) return cudaErrorInvalidValue;
     uint32_t* tickets = w.work;            // [4]
     uint32_t* hist = w.work + 64;          // [4][256]
@@ -286,9 +294,14 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
         const bool to_a = (p % 2) == 0;
         const uint32_t* ki = p == 0 ? kin : (to_a ? kb : ka);
         const uint32_t* vi = p == 0 ? vin : (to_a ? vb : va);
-        radix_onesweep_kernel<<<(unsigned)tiles, OS_THREADS, 0, s>>>(
-            ki, vi, to_a ? ka : kb, to_a ? va : vb, p == 0 ? n_dev : n_kept, n_kept, 8 * p, (p == 0 && drop_max) ? 1 : 0,
-            hist + 256 * p, status + (size_t)p * tiles * 256, tickets + p, w.flags);
+        if (small)
+            radix_onesweep_kernel<OS_IPT_SMALL><<<(unsigned)tiles, OS_THREADS, 0, s>>>(
+                ki, vi, to_a ? ka : kb, to_a ? va : vb, p == 0 ? n_dev : n_kept, n_kept, 8 * p,
+                (p == 0 && drop_max) ? 1 : 0, hist + 256 * p, status + (size_t)p * tiles * 256, tickets + p, w.flags);
+        else
+            radix_onesweep_kernel<OS_IPT_LARGE><<<(unsigned)tiles, OS_THREADS, 0, s>>>(
+                ki, vi, to_a ? ka : kb, to_a ? va : vb, p == 0 ? n_dev : n_kept, n_kept, 8 * p,
+                (p == 0 && drop_max) ? 1 : 0, hist + 256 * p, status + (size_t)p * tiles * 256, tickets + p, w.flags);
     }
     *result_in_a = (passes % 2) == 1;
     return cudaGetLastError();
