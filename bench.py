@@ -274,6 +274,7 @@ def run_ours(args, rank, world, local):
             torch.distributed.barrier()
         st = h3dgs.h3dgs_get_stats(ctx.ctx)
         assert st["device_flags"] == 0, f"device flags {st['device_flags']}"
+        M_cut = int(st["n_cut"])
         value = world * args.steps / (total_ms / 1e3)
         try:
             launches = graph_kernel_count(frame, stream)
@@ -356,6 +357,17 @@ def run_ours(args, rank, world, local):
         e2e_s = time.perf_counter() - t0
         e2e_value = world * args.steps / e2e_s
 
+        # ---- quality of the tau = 6 frame against the leaves-only (tau = 0) render of the same view
+        # (after every use of the captured graphs: the leaves-only cut needs larger buffers)
+        h3dgs.h3dgs_reserve(ctx.ctx, 0, 0)
+        frame()
+        img_tau = images.clone()
+        leaf_cam = [synth.with_tau(cam, 0.0)]
+        m0 = h3dgs.h3dgs_select_cut(ctx.ctx, leaf_cam, ids, tt, offs, cap)
+        h3dgs.h3dgs_render(ctx.ctx, leaf_cam, ids, tt, offs, opts, images, 0)
+        mse = float(((img_tau - images) ** 2).mean().item())
+        quality = {"psnr_vs_leaves_db": 10.0 * np.log10(1.0 / max(mse, 1e-20)), "cut_tau": M_cut,
+                   "cut_leaves": int(m0), "note": "image range ~[0, 1]; leaves = the tau = 0 render"}
         batched = run_batched(args, ctx, hier, flush, dev, stream) if args.batch_views > 0 else None
         optimisation = run_optimisation(args, dev, stream) if args.opt_leaves > 0 else None
 
@@ -414,6 +426,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches_per_step": launches, "gpu_launches_source": launch_src,
         "clocks": clocks,
     }
+    out["quality"] = quality
     if batched is not None:
         out["batched"] = batched
     if optimisation is not None:
@@ -672,6 +685,7 @@ def run_city(args, rank, world, local):
         "build": {"host_generation_s": t_gen, "device_build_s": t_build},
         "clocks": clk.summary(),
     }
+    out["quality"] = quality
     if batched is not None:
         out["batched"] = batched
     return out if rank == 0 else None

@@ -321,6 +321,14 @@ h3dgs_status h3dgs_debug_splats(h3dgs_ctx* ctx, float* rec, int32_t* rect, float
 
 /* Copy the last render's per-pixel final transmittance and contributor count (the list position
  * after the last contributing splat) to HOST memory for all cameras (synchronous). */
+/* Test hook for the failure path of the library's bounded waits between thread blocks (the
+ * radix-sort and scan look-backs, the blend queue): runs one wait, with the same loop, on a device
+ * word that nothing sets, giving up after `polls` polls (1 .. 2^20; each poll sleeps about 0.1 us
+ * after the first 32).  Giving up sets bit 3 of h3dgs_stats.device_flags, as a real timeout would;
+ * the context stays usable (the next render clears the flag).  Asynchronous on the context's stream.
+ * Errors: INVALID_ARG for polls out of range. */
+h3dgs_status h3dgs_debug_wait_timeout(h3dgs_ctx* ctx, int32_t polls);
+
 h3dgs_status h3dgs_debug_pixel_state(h3dgs_ctx* ctx, float* T_final, int32_t* n_contrib, int64_t n_pixels);
 
 #ifdef __cplusplus

@@ -39,9 +39,10 @@ T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
 // device counter block
 // C_EVALS and C_EVALS_T occupy two words each (64-bit counters)
 // C_NSORTED: splats kept by the depth sort (the visible ones); C_NTSORT: pairs sorted by tile
-// C_NITEMS: 3 words (all items, launch list A, launch list B)
+// C_NITEMS: 3 words (items, producers, singles).  C_FLAGS: render flags (cleared by every render);
+// C_CUTFLAGS: cut flags (cleared by every cut); the stats report both.
 enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NSORTED = 6,
-       C_NTSORT = 7, C_EVALS = 8, C_EVALS_T = 10, C_NITEMS = 12, C_COUNT = 16 };
+       C_NTSORT = 7, C_EVALS = 8, C_EVALS_T = 10, C_NITEMS = 12, C_CUTFLAGS = 15, C_COUNT = 16 };
 
 }  // namespace
 
@@ -241,6 +242,16 @@ cudaError_t sort_work(h3dgs_ctx* ctx, int64_t n_cap, SortWork* w) {
     return cudaSuccess;
 }
 
+// A build is synchronous: a sort wait that gave up is reported as its status.
+h3dgs_status check_build_flags(h3dgs_ctx* ctx) {
+    uint32_t f = 0;
+    CK(cudaMemcpyAsync(&f, P<uint32_t>(ctx->counters) + C_FLAGS, sizeof(f), cudaMemcpyDeviceToHost, ctx->stream),
+       "read flags");
+    CK(cudaStreamSynchronize(ctx->stream), "build sync");
+    if (f & FLAG_WAIT_TIMEOUT) return fail(ctx, H3DGS_ERR_TIMEOUT, "build: a bounded wait between blocks gave up");
+    return H3DGS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -350,8 +361,9 @@ h3dgs_status h3dgs_build_hierarchy(h3dgs_ctx* ctx, int64_t L, const float* mean,
                 out->parent, out->child_start, out->child_count};
     SortWork sw;
     CK(sort_work(ctx, L, &sw), "sort workspace");
+    CK(cudaMemsetAsync(P<uint32_t>(ctx->counters) + C_FLAGS, 0, sizeof(uint32_t), ctx->stream), "memset");
     CK(build_hierarchy(L, mean, scale, rot, opacity, sh, bo, sw, ctx->num_sms, ctx->stream), "build");
-    return H3DGS_OK;
+    return check_build_flags(ctx);
 }
 
 h3dgs_status h3dgs_build_hierarchy_chunked(h3dgs_ctx* ctx, int32_t n_chunks, const int64_t* off, const float* mean,
@@ -378,9 +390,10 @@ h3dgs_status h3dgs_build_hierarchy_chunked(h3dgs_ctx* ctx, int32_t n_chunks, con
                 out->parent, out->child_start, out->child_count};
     SortWork sw;
     CK(sort_work(ctx, std::max<int64_t>(Lmax, n_chunks), &sw), "sort workspace");
+    CK(cudaMemsetAsync(P<uint32_t>(ctx->counters) + C_FLAGS, 0, sizeof(uint32_t), ctx->stream), "memset");
     CK(build_hierarchy_chunked(n_chunks, off, mean, scale, rot, opacity, sh, bo, sw, ctx->num_sms, ctx->stream),
        "build chunked");
-    return H3DGS_OK;
+    return check_build_flags(ctx);
 }
 
 h3dgs_status h3dgs_upload_hierarchy(h3dgs_ctx* ctx, const h3dgs_hierarchy* h) {
@@ -430,9 +443,10 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
     w.mask = P<uint32_t>(ctx->cut_mask);
     w.block_counts = P<uint32_t>(ctx->cut_bc);
     w.cam_totals = P<int64_t>(ctx->cut_tot);
+    CK(cudaMemsetAsync(P<uint32_t>(ctx->counters) + C_CUTFLAGS, 0, sizeof(uint32_t), ctx->stream), "memset");
     stage_begin(ctx, H3DGS_STAGE_CUT);
     CK(launch_cut(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, w, cut_ids, cut_t, cut_offsets, capacity,
-                  P<uint32_t>(ctx->counters) + C_FLAGS, ctx->stream),
+                  P<uint32_t>(ctx->counters) + C_CUTFLAGS, ctx->stream),
        "cut kernels");
     stage_end(ctx, H3DGS_STAGE_CUT);
     if (total_out) {
@@ -507,6 +521,7 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
     CK(ensure(ctx->ranges, sizeof(int2) * (size_t)ctx->n_tiles), "ranges");
     CK(ensure(ctx->T_final, sizeof(float) * (size_t)ctx->n_pixels), "pixel state");
     CK(ensure(ctx->n_contrib, sizeof(int32_t) * (size_t)ctx->n_pixels), "pixel state");
+    CK(cudaMemsetAsync(cnt + C_FLAGS, 0, sizeof(uint32_t), s), "memset");
     CK(cudaMemsetAsync(cnt + C_NVISIBLE, 0, sizeof(uint32_t), s), "memset");
     CK(cudaMemsetAsync(cnt + C_EVALS, 0, 4 * sizeof(uint32_t), s), "memset");
     CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(int2) * (size_t)ctx->n_tiles, s), "memset");
@@ -646,7 +661,7 @@ h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out) {
     out->n_pairs = c[C_NPAIRS_KEPT];
     out->n_tiles = ctx->n_tiles;
     out->n_pixels = ctx->n_pixels;
-    out->device_flags = c[C_FLAGS];
+    out->device_flags = c[C_FLAGS] | c[C_CUTFLAGS];
     uint64_t ev;
     std::memcpy(&ev, c + C_EVALS, sizeof(ev));
     out->n_evals = (int64_t)ev;
@@ -755,6 +770,20 @@ h3dgs_status h3dgs_debug_splats(h3dgs_ctx* ctx, float* rec, int32_t* rect, float
         }
         if (rgb) { rgb[3 * i] = culled ? 0.f : c.x; rgb[3 * i + 1] = culled ? 0.f : c.y; rgb[3 * i + 2] = culled ? 0.f : c.z; }
     }
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_debug_wait_timeout(h3dgs_ctx* ctx, int32_t polls) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (polls < 1 || polls > (1 << 20)) return fail(ctx, H3DGS_ERR_INVALID_ARG, "debug: polls out of range");
+    CK(cudaSetDevice(ctx->device), "set device");
+    uint32_t* cnt = P<uint32_t>(ctx->counters);
+    CK(cudaMemsetAsync(cnt + C_FLAGS, 0, sizeof(uint32_t), ctx->stream), "memset");
+    // the word waited on is one that nothing sets during the call (the render's item counter slot is
+    // reused as a zero word: cleared here, read only)
+    CK(cudaMemsetAsync(cnt + C_NSORTED, 0, sizeof(uint32_t), ctx->stream), "memset");
+    CK(launch_wait_probe(cnt + C_NSORTED, polls, cnt + C_FLAGS, ctx->stream), "wait probe");
     return H3DGS_OK;
 }
 

@@ -321,17 +321,7 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     float2 T = make_float2(1.0f, 1.0f);
     if (role == 2) {
         // wait for the tile's nch - 1 producers, then T_in = product of the earlier chunks' products
-        if (threadIdx.x == 0) {
-            const uint32_t want = (uint32_t)(nch - 1);
-            uint32_t v;
-            int spins = 0;
-            do {
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(tile_done + tile) : "memory");
-                if (v >= want) break;
-                if (++spins > 32) __nanosleep(128);
-            } while (spins < QUEUE_SPIN_LIMIT);
-            if (v < want) atomicOr(flags, FLAG_WAIT_TIMEOUT);
-        }
+        if (threadIdx.x == 0) wait_geq(tile_done + tile, (uint32_t)(nch - 1), QUEUE_SPIN_LIMIT, flags);
         __syncthreads();
         const int64_t i0 = tile_item0[tile];
         for (int c = 0; c < it.y; ++c)
@@ -452,6 +442,15 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
     img[2 * plane] = fmaf(T, o.bg[2], C2);
     if (T_final) T_final[pix] = T;
     if (n_contrib) n_contrib[pix] = last;
+}
+
+__global__ void wait_probe_kernel(const uint32_t* word, int polls, uint32_t* flags) {
+    if (threadIdx.x == 0) wait_geq(word, 1u, polls, flags);
+}
+
+cudaError_t launch_wait_probe(const uint32_t* word, int polls, uint32_t* flags, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(word, polls, flags);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {

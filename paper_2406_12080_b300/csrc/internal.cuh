@@ -167,6 +167,21 @@ __device__ __forceinline__ uint32_t warp_mask(const float4 a, float cc, const fl
     return m;
 }
 
+// Bounded wait of one thread until *p >= want (acquire): at most `limit` polls, sleeping between
+// polls after the first few.  Giving up sets FLAG_WAIT_TIMEOUT in *flags and returns false; the
+// caller then goes on with what it has (its result is invalid and flagged), so no wait can hang.
+__device__ __forceinline__ bool wait_geq(const uint32_t* p, uint32_t want, int limit, uint32_t* flags) {
+    uint32_t v;
+    int spins = 0;
+    do {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+        if (v >= want) return true;
+        if (++spins > 32) __nanosleep(128);
+    } while (spins < limit);
+    atomicOr(flags, FLAG_WAIT_TIMEOUT);
+    return false;
+}
+
 // Camera index of global entry m given the per-camera offsets (binary search, n_cams small).
 __device__ __forceinline__ int find_cam(const int64_t* __restrict__ offs, int n_cams, int64_t m) {
     int lo = 0, hi = n_cams - 1;
@@ -280,6 +295,8 @@ struct BlendArgs {
     cudaEvent_t* ev_queue;        // 2 events around the main blend kernel (profiling), or NULL
 };
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
+// Test hook: one thread waits with wait_geq on *word (which nothing sets) for `polls` polls.
+cudaError_t launch_wait_probe(const uint32_t* word, int polls, uint32_t* flags, cudaStream_t s);
 
 // builder.cu
 struct BuildOut {

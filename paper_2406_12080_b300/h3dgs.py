@@ -96,6 +96,7 @@ def lib():
             "h3dgs_render_backward": (i32, [vp, vp, C.POINTER(h3dgs_grads), i32]),
             "h3dgs_get_stats": (i32, [vp, C.POINTER(h3dgs_stats)]),
             "h3dgs_set_profiling": (i32, [vp, i32]),
+            "h3dgs_debug_wait_timeout": (i32, [vp, i32]),
             "h3dgs_get_stage_times": (i32, [vp, vp]),
             "h3dgs_debug_tile_lists": (i32, [vp, i32, vp, vp, i64, C.POINTER(i64)]),
             "h3dgs_debug_splats": (i32, [vp, vp, vp, vp, i64]),
@@ -258,6 +259,10 @@ def h3dgs_get_stats(ctx) -> dict:
     s = h3dgs_stats()
     _check(ctx, lib().h3dgs_get_stats(ctx, C.byref(s)))
     return {k: getattr(s, k) for k, _ in h3dgs_stats._fields_}
+
+
+def h3dgs_debug_wait_timeout(ctx, polls: int):
+    _check(ctx, lib().h3dgs_debug_wait_timeout(ctx, polls))
 
 
 def h3dgs_set_profiling(ctx, enable: int):
