@@ -64,6 +64,7 @@ def lib():
         _lib.or_build_tree.restype = C.c_int64
         _lib.or_select_cut.restype = C.c_int64
         _lib.or_select_cut_descent.restype = C.c_int64
+        _lib.or_compact.restype = C.c_int64
         _lib.or_tile_lists.restype = C.c_int64
         _lib.or_weighted_image_sum.restype = C.c_double
         _lib.or_rotation_angle.restype = C.c_double
@@ -231,6 +232,26 @@ def select_cut_descent(cam, h: Hierarchy):
     m = lib().or_select_cut_descent(C.byref(camera(cam)), C.byref(h.c32()), _p(ids, C.c_int32),
                                     C.c_int64(h.n))
     return ids[:m].copy()
+
+
+def compact(cams, h: Hierarchy, tau_min: float, tau_max: float):
+    """Compacted hierarchy (Sec. 5.2) over the training cameras `cams`.
+
+    Returns (Hierarchy, old_of_new): the kept nodes renumbered breadth-first with their attribute
+    rows and boxes unchanged, and the old index of every new node."""
+    N = h.n
+    oc = (OrCamera * max(len(cams), 1))(*[camera(c) for c in cams])
+    old = np.empty(N, np.int32)
+    par, cs, cc = np.empty(N, np.int32), np.empty(N, np.int32), np.empty(N, np.int32)
+    m = lib().or_compact(oc, C.c_int32(len(cams)), C.byref(h.c32()), C.c_float(tau_min), C.c_float(tau_max),
+                         _p(old, C.c_int32), _p(par, C.c_int32), _p(cs, C.c_int32), _p(cc, C.c_int32))
+    if m < 0:
+        raise ValueError("compact: tau_min must be > 0 and tau_max finite")
+    o = old[:m].copy()
+    g = lambda a: np.ascontiguousarray(a[o])
+    out = Hierarchy(g(h.mean), g(h.scale), g(h.rot), g(h.opacity), g(h.sh), g(h.box_min), g(h.box_max),
+                    par[:m].copy(), cs[:m].copy(), cc[:m].copy())
+    return out, o
 
 
 # --------------------------------------------------------------------------------- render

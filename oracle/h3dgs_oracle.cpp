@@ -532,6 +532,73 @@ int64_t or_select_cut_descent(const OrCamera* cam, const OrHier32* h, int32_t* i
     return (int64_t)out.size();
 }
 
+// Hierarchy compaction (Sec. 5.2), step by step as the paper describes it.
+//   * The leaves start out marked as relevant.
+//   * For tau = tau_min, 2 tau_min, 4 tau_min, ... (doubled in fp32) while tau <= tau_max:
+//       U = the union over the training views of their cuts at tau;
+//       B = the bottom-most members of U (no member of U strictly below them);
+//       every node strictly below a node of B that is not yet marked is removed;
+//       the nodes of B are marked.
+//   * A kept node's new parent is its closest kept ancestor (a node can now have K > 2 children).
+//   * Kept nodes are renumbered breadth-first from the root; siblings keep their old relative order.
+// Outputs are indexed by the new numbering; old_of_new[i] is the old index of new node i.
+// Returns the number of kept nodes, or -1 for tau_min <= 0 or a non-finite tau_max.
+int64_t or_compact(const OrCamera* cams, int32_t n_cams, const OrHier32* h, float tau_min, float tau_max,
+                   int32_t* old_of_new, int32_t* new_parent, int32_t* new_child_start, int32_t* new_child_count) {
+    if (!(tau_min > 0.0f) || !std::isfinite(tau_max)) return -1;
+    const int64_t N = h->n;
+    std::vector<char> marked(N), removed(N, 0), in_union(N), has_below(N), bottom(N), below(N);
+    for (int64_t v = 0; v < N; ++v) marked[v] = h->child_count[v] == 0;
+    std::vector<int32_t> ids(N);
+    for (float tau = tau_min; tau <= tau_max; tau = tau * 2.0f) {
+        std::fill(in_union.begin(), in_union.end(), 0);
+        for (int32_t k = 0; k < n_cams; ++k) {
+            OrCamera c = cams[k];
+            c.tau = tau;
+            const int64_t m = or_select_cut(&c, h, 0, ids.data(), nullptr, N);
+            for (int64_t i = 0; i < m; ++i) in_union[ids[i]] = 1;
+        }
+        // children come after their parent, so one backward sweep sees every subtree before its root
+        std::fill(has_below.begin(), has_below.end(), 0);
+        for (int64_t v = N - 1; v > 0; --v)
+            if (in_union[v] || has_below[v]) has_below[h->parent[v]] = 1;
+        for (int64_t v = 0; v < N; ++v) bottom[v] = in_union[v] && !has_below[v];
+        below[0] = 0;
+        for (int64_t v = 1; v < N; ++v) {
+            const int32_t p = h->parent[v];
+            below[v] = bottom[p] || below[p];
+        }
+        for (int64_t v = 0; v < N; ++v)
+            if (below[v] && !marked[v]) removed[v] = 1;
+        for (int64_t v = 0; v < N; ++v)
+            if (bottom[v]) marked[v] = 1;
+    }
+    std::vector<int32_t> up(N, -1);
+    std::vector<std::vector<int32_t>> kids(N);
+    for (int64_t v = 1; v < N; ++v) {
+        if (removed[v]) continue;
+        int32_t p = h->parent[v];
+        while (removed[p]) p = h->parent[p];
+        up[v] = p;
+        kids[p].push_back((int32_t)v);
+    }
+    std::vector<int32_t> order = {0}, new_of_old(N, -1);
+    new_of_old[0] = 0;
+    for (size_t i = 0; i < order.size(); ++i)
+        for (int32_t c : kids[order[i]]) {
+            new_of_old[c] = (int32_t)order.size();
+            order.push_back(c);
+        }
+    for (size_t i = 0; i < order.size(); ++i) {
+        const int32_t o = order[i];
+        old_of_new[i] = o;
+        new_parent[i] = i == 0 ? -1 : new_of_old[up[o]];
+        new_child_count[i] = (int32_t)kids[o].size();
+        new_child_start[i] = kids[o].empty() ? -1 : new_of_old[kids[o][0]];
+    }
+    return (int64_t)order.size();
+}
+
 }  // extern "C"
 
 // ==========================================================================================

@@ -114,6 +114,21 @@ def look_camera(pos, forward, up, width, height, hfov_deg, tau) -> Camera:
                   float(tau))
 
 
+def orbit_views(center, radius: float, n_views: int, width: int, height: int, hfov_deg: float = 60.0,
+                tau: float = 6.0, elevation: float = 0.3, seed: int = 0):
+    """n_views cameras on a ring around `center` (z up), each looking at it; a seeded jitter of the
+    ring angle and radius keeps the views distinct."""
+    rng = np.random.default_rng([seed, 7])
+    c = np.asarray(center, np.float64)
+    cams = []
+    for i in range(n_views):
+        a = 2 * math.pi * (i + rng.uniform(-0.3, 0.3)) / n_views
+        r = radius * rng.uniform(0.6, 1.4)
+        pos = c + np.array([r * math.cos(a), r * math.sin(a), elevation * r])
+        cams.append(look_camera(pos, c - pos, [0, 0, 1], width, height, hfov_deg, tau))
+    return cams
+
+
 def with_tau(cam: Camera, tau: float) -> Camera:
     return Camera(cam.R, cam.T, cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height,
                   float(tau), cam.znear)
