@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--opt-leaves", type=int, default=2_000_000,
                     help="leaves of the hierarchy-optimisation section (0: skip)")
     ap.add_argument("--opt-steps", type=int, default=20)
+    ap.add_argument("--compact-views", type=int, default=256,
+                    help="training views of the hierarchy-compaction section (0: skip)")
     ap.add_argument("--workload", choices=["corridor", "city"], default="corridor",
                     help="corridor: 1M-leaf street corridor, one 1080p view; city: 50M-leaf chunked city, "
                          "256-pose loop (and the batched views on it)")
@@ -370,6 +372,7 @@ def run_ours(args, rank, world, local):
                    "cut_leaves": int(m0), "note": "image range ~[0, 1]; leaves = the tau = 0 render"}
         batched = run_batched(args, ctx, hier, flush, dev, stream) if args.batch_views > 0 else None
         optimisation = run_optimisation(args, dev, stream) if args.opt_leaves > 0 else None
+        compaction = run_compaction(args, ctx, hier, stream) if args.compact_views > 0 else None
 
     # ---- roofline of the dominant kernel: the blend's main kernel (FP32 issue-bound)
     peaks = measured_peaks()
@@ -431,6 +434,8 @@ def run_ours(args, rank, world, local):
         out["batched"] = batched
     if optimisation is not None:
         out["optimisation"] = optimisation
+    if compaction is not None:
+        out["compaction"] = compaction
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_time(scene, 4)
     if world > 1:
@@ -579,6 +584,39 @@ def run_optimisation(args, dev, stream):
                    "the cut size and pair count (not graph-captured)"}
     ctx.close()
     return out
+
+
+def run_compaction(args, ctx, hier, stream, reps: int = 3):
+    """Hierarchy compaction (Sec. 5.2) of the resident hierarchy for training views along the street.
+
+    The call is synchronous (one host read per level of the new tree) and allocates its scratch, so
+    it is timed on the host clock around the whole call."""
+    import time
+    import torch
+    from paper_2406_12080_b300 import h3dgs, synth
+    views = synth.corridor_views(seed=1, n_views=args.compact_views, resolutions=((1920, 1080),))
+    tau_min, tau_max = 3.0, 960.0
+    N = hier.n
+    f = lambda *shape: torch.empty(shape, dtype=torch.float32, device=hier.mean.device)
+    i = lambda n: torch.empty(n, dtype=torch.int32, device=hier.mean.device)
+    out = h3dgs.DeviceHierarchy(f(N, 3), f(N, 3), f(N, 4), f(N), f(N, 48), f(N, 3), f(N, 3), i(N), i(N), i(N))
+    old = i(N)
+    m = h3dgs.h3dgs_compact_hierarchy(ctx.ctx, views, tau_min, tau_max, out, old)
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = h3dgs.h3dgs_compact_hierarchy(ctx.ctx, views, tau_min, tau_max, out, old)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * min(times)
+    cc = out.child_count[:m]
+    return {"workload": f"street corridor hierarchy ({N} nodes), {len(views)} training views 1920x1080 along the "
+                        f"street, tau levels {tau_min:g} x 2^k <= {tau_max:g} px",
+            "ms": ms, "nodes_per_s": N / (ms * 1e-3), "view_node_tests_per_s": N * len(views) / (ms * 1e-3),
+            "n_in": N, "n_out": int(m), "max_children": int(cc.max().item()),
+            "wide_nodes": int((cc > 2).sum().item()),
+            "note": "host clock around the synchronous call (best of 3), including its scratch allocation"}
 
 
 def _city_chunk(a):

@@ -202,6 +202,26 @@ h3dgs_status h3dgs_build_hierarchy_chunked(h3dgs_ctx* ctx, int32_t n_chunks, con
                                            const float* mean, const float* scale, const float* rot,
                                            const float* opacity, const float* sh, const h3dgs_node_arrays* out);
 
+/* Compaction of the resident hierarchy (Sec. 5.2) for a set of training views.  The leaves start
+ * out marked; for tau = tau_min, 2 tau_min, 4 tau_min, ... (doubled in fp32) while tau <= tau_max,
+ * the bottom-most nodes of the union of the views' cuts at tau (the cut rule of h3dgs_select_cut,
+ * with each camera's own tau ignored) are marked and every unmarked node strictly below them is
+ * removed.  A kept node's parent becomes its closest kept ancestor, so nodes may end up with
+ * K > 2 children (the transition opacity then uses 1 - (1 - alpha_p)^(1/K)).  The kept nodes are
+ * renumbered breadth-first from the root, siblings in their old relative order; attributes and
+ * boxes are copied unchanged.  cams: HOST array of 1 .. 2^20 cameras (only R, T, fx, fy are used).
+ * out: device arrays with room for `capacity` nodes, 16-byte aligned, not overlapping the resident
+ * hierarchy; old_index (device, nullable, [capacity]) receives the old index of every new node;
+ * *n_out (host) the number of kept nodes.  The resident hierarchy is not changed (upload the
+ * result to use it).  Requires nested boxes (a parent's box contains its children's), as built by
+ * h3dgs_build_hierarchy.  Synchronous; allocates temporary device memory (about 40 bytes per node).
+ * Errors: STATE (no hierarchy), INVALID_ARG (tau_min <= 0, a non-finite tau, more than 64 levels,
+ * bad cameras, NULL, misaligned or overlapping arrays, a parent index not below its child's),
+ * CAPACITY (*n_out > capacity; nothing written), TIMEOUT, OOM, CUDA. */
+h3dgs_status h3dgs_compact_hierarchy(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams, float tau_min,
+                                     float tau_max, const h3dgs_node_arrays* out, int64_t capacity,
+                                     int32_t* old_index, int64_t* n_out);
+
 /* a0 -- make a hierarchy resident.  The arrays are BORROWED: they must stay allocated, and the
  * topology and boxes unchanged, until the next upload or h3dgs_destroy.  Attributes (mean, scale,
  * rot, opacity, sh) may be updated in place between calls (e.g. by an optimiser).  The library

@@ -2,6 +2,7 @@
 // Every stage runs in this library's kernels; host code only validates arguments, does integer
 // bookkeeping (tile grids, offsets) and manages device memory.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -394,6 +395,65 @@ h3dgs_status h3dgs_build_hierarchy_chunked(h3dgs_ctx* ctx, int32_t n_chunks, con
     CK(build_hierarchy_chunked(n_chunks, off, mean, scale, rot, opacity, sh, bo, sw, ctx->num_sms, ctx->stream),
        "build chunked");
     return check_build_flags(ctx);
+}
+
+h3dgs_status h3dgs_compact_hierarchy(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams, float tau_min,
+                                     float tau_max, const h3dgs_node_arrays* out, int64_t capacity, int32_t* old_index,
+                                     int64_t* n_out) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_hier) return fail(ctx, H3DGS_ERR_STATE, "compact: no hierarchy uploaded");
+    if (!cams || n_cams < 1 || n_cams > (1 << 20)) return fail(ctx, H3DGS_ERR_INVALID_ARG, "compact: need 1..2^20 cameras");
+    for (int i = 0; i < n_cams; ++i)
+        if (!(cams[i].fx > 0) || !(cams[i].fy > 0) || !std::isfinite(cams[i].fx) || !std::isfinite(cams[i].fy))
+            return fail(ctx, H3DGS_ERR_INVALID_ARG, "compact: camera " + std::to_string(i) + " needs finite fx, fy > 0");
+    if (!(tau_min > 0) || !std::isfinite(tau_min) || !std::isfinite(tau_max))
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "compact: need tau_min > 0 and a finite tau_max");
+    std::vector<float> levels;
+    for (float t = tau_min; t <= tau_max; t = t * 2.0f) {
+        if (levels.size() == 64) return fail(ctx, H3DGS_ERR_INVALID_ARG, "compact: more than 64 levels");
+        levels.push_back(t);
+    }
+    if (!out || !n_out || capacity < 1) return fail(ctx, H3DGS_ERR_INVALID_ARG, "compact: NULL output or capacity < 1");
+    const h3dgs_hierarchy& h = ctx->hier;
+    const int64_t N = h.n_nodes;
+    const size_t n = (size_t)N;
+    struct Range { const void* p; size_t bytes; };
+    const Range in[] = {{h.mean, 12 * n}, {h.scale, 12 * n}, {h.rot, 16 * n}, {h.opacity, 4 * n},
+                        {h.sh, 192 * n}, {h.box_min, 12 * n}, {h.box_max, 12 * n}, {h.parent, 4 * n},
+                        {h.child_start, 4 * n}, {h.child_count, 4 * n}};
+    const size_t cap = (size_t)capacity;
+    const Range outs[] = {{out->mean, 12 * cap}, {out->scale, 12 * cap}, {out->rot, 16 * cap},
+                          {out->opacity, 4 * cap}, {out->sh, 192 * cap}, {out->box_min, 12 * cap},
+                          {out->box_max, 12 * cap}, {out->parent, 4 * cap}, {out->child_start, 4 * cap},
+                          {out->child_count, 4 * cap}, {old_index, old_index ? 4 * cap : 0}};
+    for (const Range& o : outs) {
+        if (!o.p && &o != &outs[10]) return fail(ctx, H3DGS_ERR_INVALID_ARG, "compact: NULL output array");
+        if (o.p && !aligned16(o.p)) return fail(ctx, H3DGS_ERR_INVALID_ARG, "compact: arrays must be 16-byte aligned");
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(o.p), a1 = a0 + o.bytes;
+        for (const Range& i : in) {
+            const uintptr_t b0 = reinterpret_cast<uintptr_t>(i.p), b1 = b0 + i.bytes;
+            if (o.p && a0 < b1 && b0 < a1)
+                return fail(ctx, H3DGS_ERR_INVALID_ARG, "compact: an output overlaps the resident hierarchy");
+        }
+    }
+    CK(cudaSetDevice(ctx->device), "set device");
+    SortWork sw;
+    CK(sort_work(ctx, N, &sw), "sort workspace");
+    CK(cudaMemsetAsync(P<uint32_t>(ctx->counters) + C_FLAGS, 0, sizeof(uint32_t), ctx->stream), "memset");
+    BuildOut bo{out->mean, out->scale, out->rot, out->opacity, out->sh, out->box_min, out->box_max,
+                out->parent, out->child_start, out->child_count};
+    CK(compact_hierarchy(h, P<const float4>(ctx->rec), cams, n_cams, levels.data(), (int)levels.size(), bo, capacity,
+                         old_index, n_out, sw, ctx->num_sms, ctx->stream),
+       "compact");
+    uint32_t f = 0;
+    CK(cudaMemcpyAsync(&f, P<uint32_t>(ctx->counters) + C_FLAGS, sizeof(f), cudaMemcpyDeviceToHost, ctx->stream),
+       "read flags");
+    CK(cudaStreamSynchronize(ctx->stream), "compact sync");
+    if (f & FLAG_WAIT_TIMEOUT) return fail(ctx, H3DGS_ERR_TIMEOUT, "compact: a bounded wait between blocks gave up");
+    if (f & FLAG_BAD_TOPOLOGY) return fail(ctx, H3DGS_ERR_INVALID_ARG, "compact: a parent index is not below its child's");
+    if (*n_out > capacity) return fail(ctx, H3DGS_ERR_CAPACITY, "compact: more kept nodes than capacity");
+    return H3DGS_OK;
 }
 
 h3dgs_status h3dgs_upload_hierarchy(h3dgs_ctx* ctx, const h3dgs_hierarchy* h) {

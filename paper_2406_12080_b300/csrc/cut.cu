@@ -44,12 +44,7 @@ __global__ void camera_setup_kernel(CamBatch b, DevCam* __restrict__ out) {
     for (int k = 0; k < 3; ++k) d.T[k] = c.T[k];
     d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
     d.width = c.width; d.height = c.height; d.znear = c.znear; d.tau = c.tau;
-    for (int j = 0; j < 3; ++j) {
-        float acc = fmul(c.R[j], c.T[0]);
-        acc = ffma(c.R[3 + j], c.T[1], acc);
-        acc = ffma(c.R[6 + j], c.T[2], acc);
-        d.c[j] = -acc;
-    }
+    camera_centre(c, d.c);
     d.f = fmaxf(c.fx, c.fy);
     d.limx = fdiv(fmul(0.65f, (float)c.width), c.fx);
     d.limy = fdiv(fmul(0.65f, (float)c.height), c.fy);

@@ -32,12 +32,7 @@ static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
 // Derived camera values in the same fixed fp32 order as the context path's set-up kernel.
 __device__ __forceinline__ DevCam na_camera(const h3dgs_camera& c) {
     DevCam d;
-    for (int j = 0; j < 3; ++j) {
-        float acc = fmul(c.R[j], c.T[0]);
-        acc = ffma(c.R[3 + j], c.T[1], acc);
-        acc = ffma(c.R[6 + j], c.T[2], acc);
-        d.c[j] = -acc;
-    }
+    camera_centre(c, d.c);
     d.f = fmaxf(c.fx, c.fy);
     d.tau = c.tau;
     return d;

@@ -19,6 +19,7 @@ constexpr uint32_t FLAG_PAIRS_OVERFLOW = 1u << 0;
 constexpr uint32_t FLAG_SPLATS_OVERFLOW = 1u << 1;
 constexpr uint32_t FLAG_CUT_TRUNCATED = 1u << 2;
 constexpr uint32_t FLAG_WAIT_TIMEOUT = 1u << 3;   // a bounded wait on another block gave up (frame invalid)
+constexpr uint32_t FLAG_BAD_TOPOLOGY = 1u << 4;   // a parent index not below its child's (compaction)
 constexpr int QUEUE_SPIN_LIMIT = 1 << 22;          // polls of the blend queue's per-tile counter
 
 // Per-camera data on the device.  Raw fields come from h3dgs_camera; the derived floats are
@@ -78,17 +79,32 @@ __device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf
 
 // Granularity (Sec. 4.2): projected size of the node's box, largest side over the distance from the
 // camera centre to the closest point of the box; +inf with the camera inside the box.
-__device__ __forceinline__ float granularity(const DevCam& cam, float lx, float ly, float lz, float hx, float hy,
-                                             float hz) {
-    const float dx = fmaxf(fmaxf(fsub(lx, cam.c[0]), fsub(cam.c[0], hx)), 0.0f);
-    const float dy = fmaxf(fmaxf(fsub(ly, cam.c[1]), fsub(cam.c[1], hy)), 0.0f);
-    const float dz = fmaxf(fmaxf(fsub(lz, cam.c[2]), fsub(cam.c[2], hz)), 0.0f);
+// c = the camera centre, f = max(fx, fy).
+__device__ __forceinline__ float granularity(float c0, float c1, float c2, float f, float lx, float ly, float lz,
+                                             float hx, float hy, float hz) {
+    const float dx = fmaxf(fmaxf(fsub(lx, c0), fsub(c0, hx)), 0.0f);
+    const float dy = fmaxf(fmaxf(fsub(ly, c1), fsub(c1, hy)), 0.0f);
+    const float dz = fmaxf(fmaxf(fsub(lz, c2), fsub(c2, hz)), 0.0f);
     float d2 = fmul(dx, dx);
     d2 = ffma(dy, dy, d2);
     d2 = ffma(dz, dz, d2);
     const float size = fmaxf(fmaxf(fsub(hx, lx), fsub(hy, ly)), fsub(hz, lz));
     if (d2 == 0.0f) return __int_as_float(0x7f800000);
-    return fdiv(fmul(cam.f, size), fsqrt(d2));
+    return fdiv(fmul(f, size), fsqrt(d2));
+}
+__device__ __forceinline__ float granularity(const DevCam& cam, float lx, float ly, float lz, float hx, float hy,
+                                             float hz) {
+    return granularity(cam.c[0], cam.c[1], cam.c[2], cam.f, lx, ly, lz, hx, hy, hz);
+}
+
+// Camera centre c = -R^T T, component j as -fmaf(R_2j, T_2, fmaf(R_1j, T_1, R_0j * T_0)).
+__device__ __forceinline__ void camera_centre(const h3dgs_camera& cam, float c[3]) {
+    for (int j = 0; j < 3; ++j) {
+        float acc = fmul(cam.R[j], cam.T[0]);
+        acc = ffma(cam.R[3 + j], cam.T[1], acc);
+        acc = ffma(cam.R[6 + j], cam.T[2], acc);
+        c[j] = -acc;
+    }
 }
 
 // Interpolation weight of the parent (Eq. t_interp); 0 unless eps_n < tau <= eps_p < inf.
@@ -321,6 +337,14 @@ cudaError_t build_hierarchy(int64_t L, const float* mean, const float* scale, co
 cudaError_t build_hierarchy_chunked(int K, const int64_t* off, const float* mean, const float* scale, const float* rot,
                                     const float* opacity, const float* sh, const BuildOut& out, const SortWork& sw,
                                     int num_sms, cudaStream_t s);
+
+// compact.cu
+// Compaction of the resident hierarchy (h, rec) over the training cameras cams_host (host array).
+// Writes *n_out = the number of kept nodes; when it exceeds `capacity` nothing else is written.
+// Synchronous on stream s; allocates temporary device memory.
+cudaError_t compact_hierarchy(const h3dgs_hierarchy& h, const float4* rec, const h3dgs_camera* cams_host,
+                              int n_cams, const float* levels, int n_levels, const BuildOut& out, int64_t capacity,
+                              int32_t* old_index, int64_t* n_out, const SortWork& sw, int num_sms, cudaStream_t s);
 
 // backward.cu
 struct GradBufs {

@@ -88,6 +88,8 @@ def lib():
             "h3dgs_build_hierarchy": (i32, [vp, i64, vp, vp, vp, vp, vp, C.POINTER(h3dgs_node_arrays)]),
             "h3dgs_build_hierarchy_chunked": (i32, [vp, i32, C.POINTER(C.c_int64), vp, vp, vp, vp, vp,
                                                     C.POINTER(h3dgs_node_arrays)]),
+            "h3dgs_compact_hierarchy": (i32, [vp, C.POINTER(h3dgs_camera), i32, C.c_float, C.c_float,
+                                              C.POINTER(h3dgs_node_arrays), i64, vp, C.POINTER(i64)]),
             "h3dgs_select_cut": (i32, [vp, C.POINTER(h3dgs_camera), i32, vp, vp, vp, i64, C.POINTER(i64)]),
             "h3dgs_interpolate": (i32, [vp, C.POINTER(h3dgs_camera), i32, vp, vp, vp, i32, vp, i64]),
             "h3dgs_select_cut_noalloc": (i32, [C.POINTER(h3dgs_hierarchy), C.POINTER(h3dgs_camera), vp, vp, vp, i64,
@@ -192,6 +194,18 @@ def h3dgs_build_hierarchy(ctx, leaves: dict, out: "DeviceHierarchy"):
     L = int(leaves["mean"].shape[0])
     _check(ctx, lib().h3dgs_build_hierarchy(ctx, L, *[_ptr(leaves[k]) for k in ("mean", "scale", "rot", "opacity", "sh")],
                                             C.byref(a)))
+
+
+def h3dgs_compact_hierarchy(ctx, cams, tau_min: float, tau_max: float, out: "DeviceHierarchy", old_index=None) -> int:
+    """Compacts the resident hierarchy into `out` (capacity = out.n); returns the kept node count."""
+    a = h3dgs_node_arrays()
+    for k in ("mean", "scale", "rot", "opacity", "sh", "box_min", "box_max", "parent", "child_start",
+              "child_count"):
+        setattr(a, k, _ptr(getattr(out, k)))
+    n = C.c_int64(0)
+    _check(ctx, lib().h3dgs_compact_hierarchy(ctx, camera_array(cams), len(cams), tau_min, tau_max, C.byref(a),
+                                              out.n, _ptr(old_index), C.byref(n)))
+    return n.value
 
 
 def h3dgs_build_hierarchy_chunked(ctx, leaves: dict, chunk_offsets, out: "DeviceHierarchy"):
@@ -375,6 +389,20 @@ class Context:
         out = DeviceHierarchy(f(N, 3), f(N, 3), f(N, 4), f(N), f(N, 48), f(N, 3), f(N, 3), i(N), i(N), i(N))
         h3dgs_build_hierarchy_chunked(self.ctx, leaves, chunk_offsets, out)
         return out
+
+    def compact(self, cams, tau_min: float, tau_max: float):
+        """Compacted copy of the resident hierarchy (Sec. 5.2) for the training cameras `cams`.
+        Returns (DeviceHierarchy, old index of every new node)."""
+        import torch
+        N = self.hier.n
+        f = lambda *shape: torch.empty(shape, dtype=torch.float32, device=self.device)
+        i = lambda n: torch.empty(n, dtype=torch.int32, device=self.device)
+        out = DeviceHierarchy(f(N, 3), f(N, 3), f(N, 4), f(N), f(N, 48), f(N, 3), f(N, 3), i(N), i(N), i(N))
+        old = i(N)
+        m = h3dgs_compact_hierarchy(self.ctx, cams, tau_min, tau_max, out, old)
+        trim = DeviceHierarchy(*[getattr(out, k)[:m] for k in ("mean", "scale", "rot", "opacity", "sh", "box_min",
+                                                             "box_max", "parent", "child_start", "child_count")])
+        return trim, old[:m]
 
     def upload(self, hier: DeviceHierarchy):
         h3dgs_upload_hierarchy(self.ctx, hier)
