@@ -20,6 +20,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 NSH = 48
 NATTR = 59
 NINTERP = 62
+NVAL = 13
 
 
 def build(force: bool = False) -> str:
@@ -273,13 +274,14 @@ class Frame:
     t: np.ndarray
     rec32: np.ndarray      # [M, 10] u v ca cb cc on op t K depth (fp32 decision track)
     rect: np.ndarray       # [M, 4]  x0 x1 y0 y1, -1 if culled
-    val64: np.ndarray      # [M, 12] u v A B C on op t K r g b (fp64 value track)
+    val64: np.ndarray      # [M, 13] u v A B C on op t K r g b z (fp64 value track)
     ranges: np.ndarray | None = None   # [tiles, 2]
     lists: np.ndarray | None = None    # [P] splat indices (cut positions)
     image: np.ndarray | None = None    # [3, H, W] fp64
     T_final: np.ndarray | None = None
     n_contrib: np.ndarray | None = None
     ambiguous: np.ndarray | None = None
+    depth: np.ndarray | None = None    # [H, W] expected depth sum(T alpha z), fp64
 
 
 def preprocess(cam, h: Hierarchy, ids, t, opts: Opts, a64: Attrs64 | None = None) -> Frame:
@@ -288,7 +290,7 @@ def preprocess(cam, h: Hierarchy, ids, t, opts: Opts, a64: Attrs64 | None = None
     ids, t = np.ascontiguousarray(ids, np.int32), _f32(t)
     rec = np.empty((M, 10), np.float32)
     rect = np.empty((M, 4), np.int32)
-    val = np.empty((M, 12), np.float64)
+    val = np.empty((M, NVAL), np.float64)
     lib().or_preprocess(C.byref(camera(cam)), C.byref(opts.c()), C.byref(h.c32()),
                         C.byref(a64.c64()), C.c_int64(M), _p(ids, C.c_int32), _p(t, C.c_float),
                         _p(rec, C.c_float), _p(rect, C.c_int32), _p(val, C.c_double))
@@ -311,17 +313,22 @@ def tile_lists(cam, fr: Frame, opts: Opts):
     return fr
 
 
-def blend(cam, fr: Frame, opts: Opts):
+def blend(cam, fr: Frame, opts: Opts, exposure=None):
+    """Image (exposure = the camera's 3x4 affine, row-major, applied when given), expected depth,
+    final transmittance, contributor counts and the ambiguity flags."""
     H, W = cam.height, cam.width
     img = np.empty((3, H, W), np.float64)
+    dep = np.empty((H, W), np.float64)
     Tf = np.empty((H, W), np.float64)
     nc = np.empty((H, W), np.int32)
     amb = np.empty((H, W), np.uint8)
     lists = fr.lists if len(fr.lists) else np.zeros(1, np.int32)
+    E = None if exposure is None else np.ascontiguousarray(exposure, np.float32).reshape(12)
     lib().or_blend(C.byref(camera(cam)), C.byref(opts.c()), _p(fr.rec32, C.c_float), _p(fr.val64, C.c_double),
-                   _p(fr.ranges, C.c_int32), _p(lists, C.c_int32), _p(img, C.c_double),
-                   _p(Tf, C.c_double), _p(nc, C.c_int32), _p(amb, C.c_uint8))
-    fr.image, fr.T_final, fr.n_contrib, fr.ambiguous = img, Tf, nc, amb.astype(bool)
+                   _p(fr.ranges, C.c_int32), _p(lists, C.c_int32), None if E is None else _p(E, C.c_float),
+                   _p(img, C.c_double), _p(dep, C.c_double), _p(Tf, C.c_double), _p(nc, C.c_int32),
+                   _p(amb, C.c_uint8))
+    fr.image, fr.depth, fr.T_final, fr.n_contrib, fr.ambiguous = img, dep, Tf, nc, amb.astype(bool)
     return fr
 
 
@@ -334,45 +341,53 @@ def blend_bruteforce(cam, fr: Frame, opts: Opts) -> np.ndarray:
 
 
 def render(cam, h: Hierarchy, opts: Opts | None = None, a64: Attrs64 | None = None,
-           cut=None) -> Frame:
+           cut=None, exposure=None) -> Frame:
     """Cut -> interpolate/project -> tile lists -> blend, all on the CPU."""
     opts = opts or Opts()
     # t is a property of the cut (camera + hierarchy); interpolate = 0 only zeroes it when rendering
     ids, t = cut if cut is not None else select_cut(cam, h, 1)
     fr = preprocess(cam, h, ids, t, opts, a64)
     tile_lists(cam, fr, opts)
-    return blend(cam, fr, opts)
+    return blend(cam, fr, opts, exposure)
 
 
 def backward(cam, h: Hierarchy, fr: Frame, dL_dimage: np.ndarray, opts: Opts,
-             a64: Attrs64 | None = None, freeze_leaves: int = 0) -> np.ndarray:
-    """Gradient [N, 59] of sum(dL_dimage * image) w.r.t. node attributes (fp64)."""
+             a64: Attrs64 | None = None, freeze_leaves: int = 0, dL_ddepth=None, exposure=None) -> np.ndarray:
+    """Gradient [N, 59] of sum(dL_dimage * image) + sum(dL_ddepth * depth) w.r.t. node attributes
+    (fp64); the image carries the exposure when given."""
     a64 = a64 or Attrs64.of(h)
     g = np.empty((h.n, NATTR), np.float64)
     dl = _f64(dL_dimage)
+    dd = None if dL_ddepth is None else _f64(dL_ddepth)
+    E = None if exposure is None else np.ascontiguousarray(exposure, np.float32).reshape(12)
     lists = fr.lists if len(fr.lists) else np.zeros(1, np.int32)
     lib().or_backward(C.byref(camera(cam)), C.byref(opts.c()), C.byref(h.c32()), C.byref(a64.c64()),
                       C.c_int64(len(fr.ids)), _p(fr.ids, C.c_int32), _p(fr.t, C.c_float),
                       _p(fr.rec32, C.c_float), _p(fr.rect, C.c_int32), _p(fr.val64, C.c_double),
                       _p(fr.ranges, C.c_int32), _p(lists, C.c_int32), _p(dl, C.c_double),
+                      None if dd is None else _p(dd, C.c_double), None if E is None else _p(E, C.c_float),
                       C.c_int32(freeze_leaves), _p(g, C.c_double))
     return g
 
 
-def weighted_image_sum(cam, h: Hierarchy, fr: Frame, w: np.ndarray, opts: Opts, a64: Attrs64) -> float:
-    """sum(w * image) of the fp64 track with the decisions of `fr` held fixed."""
+def weighted_image_sum(cam, h: Hierarchy, fr: Frame, w: np.ndarray, opts: Opts, a64: Attrs64,
+                       w_depth=None, exposure=None) -> float:
+    """sum(w * image) + sum(w_depth * depth) of the fp64 track with the decisions of `fr` held fixed."""
     M = len(fr.ids)
-    val = np.empty((M, 12), np.float64)
+    val = np.empty((M, NVAL), np.float64)
     rec = np.empty((M, 10), np.float32)
     rect = np.empty((M, 4), np.int32)
     lib().or_preprocess(C.byref(camera(cam)), C.byref(opts.c()), C.byref(h.c32()), C.byref(a64.c64()),
                         C.c_int64(M), _p(fr.ids, C.c_int32), _p(fr.t, C.c_float), _p(rec, C.c_float),
                         _p(rect, C.c_int32), _p(val, C.c_double))
     w = _f64(w)
+    wd = None if w_depth is None else _f64(w_depth)
+    E = None if exposure is None else np.ascontiguousarray(exposure, np.float32).reshape(12)
     lists = fr.lists if len(fr.lists) else np.zeros(1, np.int32)
     return lib().or_weighted_image_sum(C.byref(camera(cam)), C.byref(opts.c()), _p(fr.rec32, C.c_float),
                                        _p(val, C.c_double), _p(fr.ranges, C.c_int32), _p(lists, C.c_int32),
-                                       _p(w, C.c_double))
+                                       None if E is None else _p(E, C.c_float), _p(w, C.c_double),
+                                       None if wd is None else _p(wd, C.c_double))
 
 
 def ellipsoid_area(s) -> float:

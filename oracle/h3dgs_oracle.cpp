@@ -37,6 +37,7 @@ namespace {
 
 constexpr int NSH = 48;          // 16 SH basis functions x 3 colour channels, layout [k*3 + ch]
 constexpr int NATTR = 59;        // mean 3, scale 3, rot 4, opacity 1, sh 48
+constexpr int NVAL = 13;         // value-track splat row: u v A B C on op t K r g b z
 constexpr double PI = 3.14159265358979323846;
 
 // ------------------------------------------------------------------------------------------
@@ -796,7 +797,7 @@ SplatF project_f(const OrCamera& cam, const OrOpts& o, const float a[NINTERP]) {
 }
 
 // One splat, fp64 value track: natural-exponent conic (A, B, C), opacities, colour.
-struct SplatD { double u, v, A, B, C, on, op, t, K, rgb[3]; bool clamped[3]; };
+struct SplatD { double u, v, A, B, C, on, op, t, K, rgb[3], z; bool clamped[3]; };
 
 SplatD project_d(const OrCamera& cam, const OrOpts& o, const double a[NINTERP]) {
     SplatD s{};
@@ -806,6 +807,7 @@ SplatD project_d(const OrCamera& cam, const OrOpts& o, const double a[NINTERP]) 
     double xc[3];
     for (int i = 0; i < 3; ++i) xc[i] = W[3 * i] * a[0] + W[3 * i + 1] * a[1] + W[3 * i + 2] * a[2] + T[i];
     double z = xc[2];
+    s.z = z;
     double xz = xc[0] / z, yz = xc[1] / z;
     s.u = (double)cam.fx * xz + cam.cx;
     s.v = (double)cam.fy * yz + cam.cy;
@@ -874,7 +876,7 @@ void or_interpolate(const OrHier32* h, const OrHier64* hd, int64_t M, const int3
 // Splat records of every cut node.
 //   rec32 [M][10]: u v ca cb cc on op t K depth   (fp32 decision track)
 //   rect  [M][4] : x0 x1 y0 y1 (tiles, inclusive), all -1 if culled
-//   val64 [M][12]: u v A B C on op t K r g b       (fp64 value track)
+//   val64 [M][13]: u v A B C on op t K r g b z     (fp64 value track; z = view depth of the mean)
 void or_preprocess(const OrCamera* cam, const OrOpts* o, const OrHier32* h, const OrHier64* hd, int64_t M,
                    const int32_t* ids, const float* t, float* rec32, int32_t* rect, double* val64) {
 #pragma omp parallel for schedule(static)
@@ -890,16 +892,16 @@ void or_preprocess(const OrCamera* cam, const OrOpts* o, const OrHier32* h, cons
         if (!sf.visible) {
             for (int k = 0; k < 10; ++k) r[k] = 0;
             rc[0] = rc[1] = rc[2] = rc[3] = -1;
-            for (int k = 0; k < 12; ++k) val64[12 * i + k] = 0;
+            for (int k = 0; k < NVAL; ++k) val64[NVAL * i + k] = 0;
             continue;
         }
         r[0] = sf.u; r[1] = sf.v; r[2] = sf.ca; r[3] = sf.cb; r[4] = sf.cc;
         r[5] = sf.on; r[6] = sf.op; r[7] = sf.t; r[8] = sf.K; r[9] = sf.depth;
         for (int k = 0; k < 4; ++k) rc[k] = sf.rect[k];
         SplatD sd = project_d(*cam, *o, b);
-        double* v = val64 + 12 * i;
+        double* v = val64 + NVAL * i;
         v[0] = sd.u; v[1] = sd.v; v[2] = sd.A; v[3] = sd.B; v[4] = sd.C; v[5] = sd.on; v[6] = sd.op;
-        v[7] = sd.t; v[8] = sd.K; v[9] = sd.rgb[0]; v[10] = sd.rgb[1]; v[11] = sd.rgb[2];
+        v[7] = sd.t; v[8] = sd.K; v[9] = sd.rgb[0]; v[10] = sd.rgb[1]; v[11] = sd.rgb[2]; v[12] = sd.z;
     }
 }
 
@@ -968,15 +970,16 @@ double alpha_d(const double* v, double px, double py, double clamp, bool* cn = n
 
 // Blend one pixel over an ordered list of splat indices.  Decisions (skip below the alpha floor,
 // stop when the transmittance would fall below t_min) are taken in the fp32 track; the colour is
-// accumulated in the fp64 track.  Returns the list position just after the last contributing
-// splat (0 if none contributed).
+// accumulated in the fp64 track, and so is the expected depth sum(T alpha z) of the depth
+// regulariser (the splat's colour replaced by the view depth of its mean; no background term).
+// Returns the list position just after the last contributing splat (0 if none contributed).
 int32_t blend_pixel(const OrOpts& o, const float* rec32, const double* val64, const int32_t* L, int32_t n,
-                    double px, double py, double out[3], double& Tfin, bool& ambiguous,
+                    double px, double py, double out[3], double& depth, double& Tfin, bool& ambiguous,
                     std::vector<PixelRec>* contrib) {
     const float pxf = (float)px, pyf = (float)py;
     const float afl = o.alpha_floor, tmin = o.t_min;
     float T32 = 1.0f;
-    double T = 1.0, C[3] = {0, 0, 0};
+    double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
     int32_t last = 0;
     ambiguous = false;
     for (int32_t k = 0; k < n; ++k) {
@@ -988,28 +991,39 @@ int32_t blend_pixel(const OrOpts& o, const float* rec32, const double* val64, co
         if (std::fabs(Tn32 - tmin) <= 1e-5f * tmin) ambiguous = true;
         if (Tn32 < tmin) break;
         last = k + 1;
-        const double* v = val64 + 12 * s;
+        const double* v = val64 + NVAL * s;
         double a = alpha_d(v, px, py, (double)o.alpha_clamp);
         if (contrib) contrib->push_back({k, a, T});
         for (int ch = 0; ch < 3; ++ch) C[ch] += v[9 + ch] * a * T;
+        D += v[12] * a * T;
         T *= (1.0 - a);
         T32 = Tn32;
     }
     for (int ch = 0; ch < 3; ++ch) out[ch] = C[ch] + T * (double)o.bg[ch];
+    depth = D;
     Tfin = T;
     return last;
+}
+
+// Exposure compensation (appendix, exposure optimisation): the camera's 3x4 affine E (row-major)
+// applied to the rendered colour, out = E [C | 1].  E = NULL: the identity.
+void expose(const float* E, const double in[3], double out[3]) {
+    for (int c = 0; c < 3; ++c)
+        out[c] = E ? (double)E[4 * c] * in[0] + (double)E[4 * c + 1] * in[1] + (double)E[4 * c + 2] * in[2]
+                         + (double)E[4 * c + 3]
+                   : in[c];
 }
 
 }  // namespace
 
 extern "C" {
 
-// Tiled blend: image [3][H][W] (fp64), final transmittance, the list position after the last
-// contributing splat per pixel, and a per-pixel flag for decisions that fell within the fp32
-// ambiguity band.
+// Tiled blend: image [3][H][W] (fp64, exposure applied when E is given), expected depth [H][W]
+// (nullable), final transmittance, the list position after the last contributing splat per pixel,
+// and a per-pixel flag for decisions that fell within the fp32 ambiguity band.
 void or_blend(const OrCamera* cam, const OrOpts* o, const float* rec32, const double* val64,
-              const int32_t* ranges, const int32_t* list, double* image, double* T_final, int32_t* n_contrib,
-              uint8_t* ambiguous) {
+              const int32_t* ranges, const int32_t* list, const float* E, double* image, double* depth,
+              double* T_final, int32_t* n_contrib, uint8_t* ambiguous) {
     const int W = cam->width, H = cam->height;
     const int TX = (W + o->tile_w - 1) / o->tile_w;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -1017,10 +1031,12 @@ void or_blend(const OrCamera* cam, const OrOpts* o, const float* rec32, const do
         int x = (int)(pix % W), y = (int)(pix / W);
         int tile = (y / o->tile_h) * TX + (x / o->tile_w);
         int32_t s = ranges[2 * tile], e = ranges[2 * tile + 1];
-        double out[3], Tf;
+        double out[3], ex[3], D, Tf;
         bool amb;
-        int32_t c = blend_pixel(*o, rec32, val64, list + s, e - s, x + 0.5, y + 0.5, out, Tf, amb, nullptr);
-        for (int ch = 0; ch < 3; ++ch) image[(int64_t)ch * W * H + pix] = out[ch];
+        int32_t c = blend_pixel(*o, rec32, val64, list + s, e - s, x + 0.5, y + 0.5, out, D, Tf, amb, nullptr);
+        expose(E, out, ex);
+        for (int ch = 0; ch < 3; ++ch) image[(int64_t)ch * W * H + pix] = ex[ch];
+        if (depth) depth[pix] = D;
         if (T_final) T_final[pix] = Tf;
         if (n_contrib) n_contrib[pix] = c;
         if (ambiguous) ambiguous[pix] = amb;
@@ -1045,9 +1061,9 @@ void or_blend_bruteforce(const OrCamera* cam, const OrOpts* o, int64_t M, const 
             float da = rec32[10 * a + 9], db = rec32[10 * b + 9];
             return da < db || (da == db && a < b);
         });
-        double out[3], Tf;
+        double out[3], D, Tf;
         bool amb;
-        blend_pixel(*o, rec32, val64, L.data(), (int32_t)L.size(), x + 0.5, y + 0.5, out, Tf, amb, nullptr);
+        blend_pixel(*o, rec32, val64, L.data(), (int32_t)L.size(), x + 0.5, y + 0.5, out, D, Tf, amb, nullptr);
         for (int ch = 0; ch < 3; ++ch) image[(int64_t)ch * W * H + pix] = out[ch];
     }
 }
@@ -1061,7 +1077,7 @@ void or_blend_bruteforce(const OrCamera* cam, const OrOpts* o, int64_t M, const 
 namespace {
 
 // Per-splat gradient accumulator of the value-track parameters.
-struct SplatGrad { double u, v, A, B, C, on, op, rgb[3]; };
+struct SplatGrad { double u, v, A, B, C, on, op, rgb[3], z; };
 
 // Backward of the interpolation + projection of one splat: from the splat-parameter gradient to
 // the interpolated attributes (mean 3, scale 3, rot 4 (pre-normalisation), sh 48, o_n, o_p).
@@ -1144,7 +1160,8 @@ void project_backward(const OrCamera& cam, const OrOpts& o, const double a[NINTE
     double dtxc = dJ[0][2] * (-fx / z), dtyc = dJ[1][2] * (-fy / z);
     double dxz = g.u * fx + (cx_in ? dtxc : 0.0);
     double dyz = g.v * fy + (cy_in ? dtyc : 0.0);
-    double dxc[3] = {dxz / z, dyz / z, dz - dxz * xc[0] / (z * z) - dyz * xc[1] / (z * z)};
+    // g.z: the expected-depth channel reads the view depth z = xc[2] directly
+    double dxc[3] = {dxz / z, dyz / z, dz + g.z - dxz * xc[0] / (z * z) - dyz * xc[1] / (z * z)};
     for (int j = 0; j < 3; ++j) da[j] = W[j] * dxc[0] + W[3 + j] * dxc[1] + W[6 + j] * dxc[2];
     // rotation matrix of the (unit) quaternion w.r.t. its components
     const double w = q[0], x = q[1], y = q[2], zq = q[3];
@@ -1182,7 +1199,8 @@ void project_backward(const OrCamera& cam, const OrOpts& o, const double a[NINTE
 
 extern "C" {
 
-// Gradient of L = sum(dL_dimage * image) w.r.t. the value-track node attributes.
+// Gradient of L = sum(dL_dimage * image) + sum(dL_ddepth * depth) w.r.t. the value-track node
+// attributes (image with the camera's exposure E applied when given; dL_ddepth nullable).
 // grad [N][59] (mean 3, scale 3, rot 4, opacity 1, sh 48) is OVERWRITTEN.  Node n receives
 // (1 - t) of its interpolated attributes' gradient and the parent p receives t of it (t is a
 // constant); o_n and o_p receive the gradients of their own opacity terms; the opacity gradient
@@ -1190,7 +1208,8 @@ extern "C" {
 void or_backward(const OrCamera* cam, const OrOpts* o, const OrHier32* h, const OrHier64* hd, int64_t M,
                  const int32_t* ids, const float* t, const float* rec32, const int32_t* rect, const double* val64,
                  const int32_t* ranges,
-                 const int32_t* list, const double* dL_dimage, int32_t freeze_leaves, double* grad) {
+                 const int32_t* list, const double* dL_dimage, const double* dL_ddepth, const float* E,
+                 int32_t freeze_leaves, double* grad) {
     const int Wd = cam->width, Ht = cam->height;
     const int TX = (Wd + o->tile_w - 1) / o->tile_w, TY = (Ht + o->tile_h - 1) / o->tile_h;
     const double clampv = o->alpha_clamp;
@@ -1213,19 +1232,24 @@ void or_backward(const OrCamera* cam, const OrOpts* o, const OrHier32* h, const 
         for (int y = ty * o->tile_h; y < std::min(Ht, (ty + 1) * o->tile_h); ++y)
             for (int x = tx * o->tile_w; x < std::min(Wd, (tx + 1) * o->tile_w); ++x) {
                 rec.clear();
-                double out[3], Tf;
+                double out[3], D, Tf;
                 bool amb;
                 const double px = x + 0.5, py = y + 0.5;
-                blend_pixel(*o, rec32, val64, L, n, px, py, out, Tf, amb, &rec);
+                blend_pixel(*o, rec32, val64, L, n, px, py, out, D, Tf, amb, &rec);
                 const int64_t pix = (int64_t)y * Wd + x;
-                double gpix[3];
-                for (int ch = 0; ch < 3; ++ch) gpix[ch] = dL_dimage[(int64_t)ch * Wd * Ht + pix];
-                // S = colour accumulated behind the current splat, plus the background term
-                double S[3];
+                double gout[3], gpix[3];
+                for (int ch = 0; ch < 3; ++ch) gout[ch] = dL_dimage[(int64_t)ch * Wd * Ht + pix];
+                // through the exposure: dL/dC_k = sum_c E[c][k] dL/dout_c
+                for (int k = 0; k < 3; ++k)
+                    gpix[k] = E ? (double)E[k] * gout[0] + (double)E[4 + k] * gout[1] + (double)E[8 + k] * gout[2]
+                                : gout[k];
+                const double gD = dL_ddepth ? dL_ddepth[pix] : 0.0;
+                // S = colour accumulated behind the current splat, plus the background term; SD the depth
+                double S[3], SD = 0.0;
                 for (int ch = 0; ch < 3; ++ch) S[ch] = Tf * o->bg[ch];
                 for (int r = (int)rec.size() - 1; r >= 0; --r) {
                     const int32_t s = L[rec[r].k];
-                    const double* v = val64 + 12 * s;
+                    const double* v = val64 + NVAL * s;
                     const double a = rec[r].alpha, Tk = rec[r].T;
                     SplatGrad& gs = G[s];
                     double dalpha = 0;
@@ -1233,7 +1257,10 @@ void or_backward(const OrCamera* cam, const OrOpts* o, const OrHier32* h, const 
                         gs.rgb[ch] += gpix[ch] * a * Tk;
                         dalpha += gpix[ch] * (Tk * v[9 + ch] - S[ch] / (1.0 - a));
                     }
+                    gs.z += gD * a * Tk;
+                    dalpha += gD * (Tk * v[12] - SD / (1.0 - a));
                     for (int ch = 0; ch < 3; ++ch) S[ch] += v[9 + ch] * a * Tk;
+                    SD += v[12] * a * Tk;
                     // alpha = (1 - t) an + t a'(ap);  an = min(c, on G);  ap = min(c, op G)
                     const double dx = px - v[0], dy = py - v[1];
                     const double pw = -0.5 * (v[2] * dx * dx + v[4] * dy * dy) - v[3] * dx * dy;
@@ -1267,7 +1294,7 @@ void or_backward(const OrCamera* cam, const OrOpts* o, const OrHier32* h, const 
         for (int64_t s = 0; s < M; ++s) {
             const SplatGrad& a = acc[th][s];
             SplatGrad& b = tot[s];
-            b.u += a.u; b.v += a.v; b.A += a.A; b.B += a.B; b.C += a.C; b.on += a.on; b.op += a.op;
+            b.u += a.u; b.v += a.v; b.A += a.A; b.B += a.B; b.C += a.C; b.on += a.on; b.op += a.op; b.z += a.z;
             for (int ch = 0; ch < 3; ++ch) b.rgb[ch] += a.rgb[ch];
         }
     std::fill(grad, grad + (size_t)h->n * NATTR, 0.0);
@@ -1310,14 +1337,18 @@ void or_backward(const OrCamera* cam, const OrOpts* o, const OrHier32* h, const 
             if (h->child_count[v] == 0) std::fill(grad + (size_t)v * NATTR, grad + (size_t)(v + 1) * NATTR, 0.0);
 }
 
-// Loss value L = sum(w * image) of the fp64 track with fixed decisions (for finite differences).
+// Loss value L = sum(w * image) + sum(w_depth * depth) of the fp64 track with fixed decisions (for
+// finite differences); E and w_depth nullable.
 double or_weighted_image_sum(const OrCamera* cam, const OrOpts* o, const float* rec32, const double* val64,
-                             const int32_t* ranges, const int32_t* list, const double* w) {
+                             const int32_t* ranges, const int32_t* list, const float* E, const double* w,
+                             const double* w_depth) {
     const int W = cam->width, H = cam->height;
-    std::vector<double> img((size_t)3 * W * H);
-    or_blend(cam, o, rec32, val64, ranges, list, img.data(), nullptr, nullptr, nullptr);
+    std::vector<double> img((size_t)3 * W * H), dep((size_t)W * H);
+    or_blend(cam, o, rec32, val64, ranges, list, E, img.data(), dep.data(), nullptr, nullptr, nullptr);
     double s = 0;
     for (size_t i = 0; i < img.size(); ++i) s += w[i] * img[i];
+    if (w_depth)
+        for (size_t i = 0; i < dep.size(); ++i) s += w_depth[i] * dep[i];
     return s;
 }
 
