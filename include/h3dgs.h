@@ -312,6 +312,28 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
 h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL_dimages, const h3dgs_grads* grads,
                                    int32_t freeze_leaves);
 
+/* h3dgs_render with the optional outputs of the appendix's depth regularisation and exposure
+ * compensation (h3dgs_render is this call with depth = exposure = NULL):
+ *   depth     device float, camera k's [H_k, W_k] at offset sum_{j<k} H_j W_j, or NULL: the expected
+ *             depth sum_i T_i alpha_i z_i over the pixel's contributors, z_i the view depth of the
+ *             (interpolated) mean, with the same blend decisions as the colour and no background;
+ *   exposure  device float [n_cams][12], or NULL: camera k's row-major 3x4 affine E_k, applied to
+ *             the pixel colour: image = E_k [C + T bg | 1] (the library keeps a copy for the adjoint).
+ * Both must be 4-byte aligned.  Errors as h3dgs_render. */
+h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams,
+                             const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets,
+                             const h3dgs_render_opts* opts, float* images, float* depth, const float* exposure,
+                             int32_t save_for_backward);
+
+/* h3dgs_render_backward for a forward made with h3dgs_render_ex: dL_dimages is the gradient of the
+ * exposed image (taken back through E_k; E_k itself gets no gradient, it is held fixed as in the
+ * paper's hierarchy optimisation) and dL_ddepth (device, the packing of `depth`, or NULL) the
+ * gradient of the expected depth, which reaches each splat's alpha and the view depth of its mean.
+ * Errors as h3dgs_render_backward, plus STATE when dL_ddepth is given and the forward rendered no
+ * depth. */
+h3dgs_status h3dgs_render_backward_ex(h3dgs_ctx* ctx, const float* dL_dimages, const float* dL_ddepth,
+                                      const h3dgs_grads* grads, int32_t freeze_leaves);
+
 /* ------------------------------------------------------------------------------ inspection */
 
 /* Counters of the last render (synchronises the stream). */

@@ -52,6 +52,45 @@ class H3dgsRender(torch.autograd.Function):
                 None, None, None, None, None, None)
 
 
+class H3dgsRenderDepth(torch.autograd.Function):
+    """(images, depth) = render with the expected-depth output and optional per-camera exposure
+    affines (the appendix's depth regularisation and exposure compensation).  `exposure`: device
+    tensor [n_cams, 3, 4] or None; it is held fixed (no gradient), as in hierarchy optimisation."""
+
+    @staticmethod
+    def forward(fctx, mean, scale, rot, opacity, sh, context: h3dgs.Context, topology: h3dgs.DeviceHierarchy,
+                cams, opts, freeze_leaves: bool, capacity, exposure):
+        attrs = [t.contiguous() for t in (mean, scale, rot, opacity, sh)]
+        hier = h3dgs.DeviceHierarchy(*attrs, topology.box_min, topology.box_max, topology.parent,
+                                     topology.child_start, topology.child_count)
+        context.upload(hier)
+        cut = context.select_cut(cams, capacity)
+        images, depth = context.render(cams, cut, opts, save_for_backward=1, depth=True,
+                                       exposure=None if exposure is None else exposure.contiguous())
+        fctx.context = context
+        fctx.hier = hier
+        fctx.cut = cut
+        fctx.freeze = int(bool(freeze_leaves))
+        return images, depth
+
+    @staticmethod
+    def backward(fctx, dimages, ddepth):
+        hier = fctx.hier
+        grads = {k: torch.zeros_like(getattr(hier, k)) for k in ATTRS}
+        dimages = torch.zeros_like(ddepth).repeat(3) if dimages is None else dimages.contiguous()
+        h3dgs.h3dgs_render_backward_ex(fctx.context.ctx, dimages, None if ddepth is None else ddepth.contiguous(),
+                                       grads, fctx.freeze)
+        return (grads["mean"], grads["scale"], grads["rot"], grads["opacity"], grads["sh"],
+                None, None, None, None, None, None, None)
+
+
+def render_depth(context, topology, mean, scale, rot, opacity, sh, cams, opts=None, freeze_leaves=True,
+                 capacity=None, exposure=None):
+    opts = opts or h3dgs.default_opts()
+    return H3dgsRenderDepth.apply(mean, scale, rot, opacity, sh, context, topology, cams, opts, freeze_leaves,
+                                  capacity, exposure)
+
+
 def render(context, topology, mean, scale, rot, opacity, sh, cams, opts=None, freeze_leaves=True, capacity=None):
     opts = opts or h3dgs.default_opts()
     return H3dgsRender.apply(mean, scale, rot, opacity, sh, context, topology, cams, opts, freeze_leaves, capacity)

@@ -60,12 +60,13 @@ struct h3dgs_ctx {
     DBuf pk0, pv0, pk1, pv1, ranges;
     DBuf sortw, seg_start;
     DBuf T_final, n_contrib, splat_grad;
-    DBuf items, q_prod, q_single, q_cons, queue_sync, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last;
+    DBuf items, q_prod, q_single, q_cons, queue_sync, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last, sc_D;
+    DBuf exposure;   // copy of the last render's exposure affines [n_cams][12]
     int64_t item_cap = 0;
     bool fixed = false;
     int64_t cap_splats = 0, cap_pairs = 0;
     // state of the last render
-    bool rendered = false, saved = false;
+    bool rendered = false, saved = false, saved_depth = false, has_exposure = false;
     std::vector<h3dgs_camera> cams_host;
     std::vector<int64_t> tile_base, pix_base;
     std::vector<int32_t> tiles_x, tiles_y;
@@ -194,7 +195,7 @@ bool supported_tile(int w, int h) {
 }  // namespace
 
 // (outside the anonymous namespace: needs the full context type)
-static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images) {
+static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images, float* depth) {
     BlendArgs a;
     a.cams = P<DevCam>(ctx->cams);
     a.n_cams = n_cams;
@@ -218,6 +219,9 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images) {
     a.scratch_Tend = P<float>(ctx->sc_Tend);
     a.scratch_last = P<int32_t>(ctx->sc_last);
     a.images = images;
+    a.depth = depth;
+    a.exposure = ctx->has_exposure ? P<const float>(ctx->exposure) : nullptr;
+    a.scratch_D = P<float>(ctx->sc_D);
     a.T_final = P<float>(ctx->T_final);
     a.n_contrib = P<int32_t>(ctx->n_contrib);
     // evaluation counters only at profiling level 2 (counting costs instructions in the blend's inner loop)
@@ -293,7 +297,7 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
                     &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
                     &ctx->items, &ctx->q_prod, &ctx->q_single, &ctx->q_cons, &ctx->queue_sync,
                     &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
-                    &ctx->sc_last};
+                    &ctx->sc_last, &ctx->sc_D, &ctx->exposure};
     for (DBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& e : ctx->ev)
@@ -541,6 +545,13 @@ h3dgs_status h3dgs_interpolate(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t
 h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams, const int32_t* cut_ids,
                           const float* cut_t, const int64_t* cut_offsets, const h3dgs_render_opts* opts, float* images,
                           int32_t save_for_backward) {
+    return h3dgs_render_ex(ctx, cams, n_cams, cut_ids, cut_t, cut_offsets, opts, images, nullptr, nullptr,
+                           save_for_backward);
+}
+
+h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams, const int32_t* cut_ids,
+                             const float* cut_t, const int64_t* cut_offsets, const h3dgs_render_opts* opts,
+                             float* images, float* depth, const float* exposure, int32_t save_for_backward) {
     if (!ctx) return H3DGS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (!ctx->has_hier) return fail(ctx, H3DGS_ERR_STATE, "render: no hierarchy uploaded");
@@ -553,6 +564,8 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
         return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: bad opts");
     if (opts->blend_chunk != 0 && (opts->blend_chunk < 64 || opts->blend_chunk > 65536))
         return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: blend_chunk out of range");
+    if ((reinterpret_cast<uintptr_t>(exposure) & 3u) || (reinterpret_cast<uintptr_t>(depth) & 3u))
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: misaligned depth or exposure array");
     CK(cudaSetDevice(ctx->device), "set device");
     st = setup_cameras(ctx, cams, n_cams, opts->tile_w, opts->tile_h);
     if (st != H3DGS_OK) return st;
@@ -664,10 +677,17 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
         CK(ensure(ctx->sc_C, 3 * sizeof(float) * (size_t)icap * NT), "blend scratch");
         CK(ensure(ctx->sc_Tend, sizeof(float) * (size_t)icap * NT), "blend scratch");
         CK(ensure(ctx->sc_last, sizeof(int32_t) * (size_t)icap * NT), "blend scratch");
+        if (depth) CK(ensure(ctx->sc_D, sizeof(float) * (size_t)icap * NT), "blend scratch");
+        ctx->has_exposure = exposure != nullptr;
+        if (exposure) {
+            CK(ensure(ctx->exposure, sizeof(float) * 12 * (size_t)n_cams), "exposure");
+            CK(cudaMemcpyAsync(ctx->exposure.p, exposure, sizeof(float) * 12 * (size_t)n_cams, cudaMemcpyDeviceToDevice, s),
+               "exposure copy");
+        }
         ctx->item_cap = icap;
         ctx->opts = o;
         ctx->pairs_in_1 = in1;
-        BlendArgs ba = blend_args(ctx, n_cams, images);
+        BlendArgs ba = blend_args(ctx, n_cams, images, depth);
         if (ctx->prof) {
             ba.ev_queue = ctx->ev + 2 * H3DGS_STAGE_BLEND_QUEUE;
             ctx->ev_used[H3DGS_STAGE_BLEND_QUEUE] = true;
@@ -677,6 +697,7 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
     stage_end(ctx, H3DGS_STAGE_BLEND);
     ctx->rendered = true;
     ctx->saved = save_for_backward != 0;
+    ctx->saved_depth = ctx->saved && depth != nullptr;
     ctx->cut_ids = cut_ids;
     ctx->cut_t = cut_t;
     ctx->cut_offsets = cut_offsets;
@@ -687,9 +708,16 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
 }
 
 h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL, const h3dgs_grads* g, int32_t freeze_leaves) {
+    return h3dgs_render_backward_ex(ctx, dL, nullptr, g, freeze_leaves);
+}
+
+h3dgs_status h3dgs_render_backward_ex(h3dgs_ctx* ctx, const float* dL, const float* dL_ddepth, const h3dgs_grads* g,
+                                      int32_t freeze_leaves) {
     if (!ctx) return H3DGS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (!ctx->saved || !ctx->has_hier) return fail(ctx, H3DGS_ERR_STATE, "render_backward: no saved forward state");
+    if (dL_ddepth && !ctx->saved_depth)
+        return fail(ctx, H3DGS_ERR_STATE, "render_backward: a depth gradient needs a forward that rendered depth");
     if (!dL || !g || !g->mean || !g->scale || !g->rot || !g->opacity || !g->sh)
         return fail(ctx, H3DGS_ERR_INVALID_ARG, "render_backward: NULL argument");
     if (!aligned16(g->rot) || !aligned16(g->sh))
@@ -700,10 +728,10 @@ h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL, const h3dgs_
     CK(cudaMemsetAsync(ctx->splat_grad.p, 0, sizeof(float) * 12 * (size_t)ctx->splat_cap_used, ctx->stream), "memset");
     GradBufs gb{g->mean, g->scale, g->rot, g->opacity, g->sh};
     cudaEvent_t* ev = ctx->prof ? ctx->ev + 2 * H3DGS_STAGE_BACKWARD_BLEND : nullptr;
-    BlendArgs ba = blend_args(ctx, n_cams, nullptr);
+    BlendArgs ba = blend_args(ctx, n_cams, nullptr, nullptr);
     CK(launch_backward(dev_hier(ctx), ba, ctx->cut_ids, ctx->cut_t, ctx->cut_offsets, P<uint2>(ctx->s_rect),
-                       P<uint32_t>(ctx->counters) + C_NSPLATS, dL, P<float>(ctx->splat_grad), gb, freeze_leaves,
-                       ctx->num_sms * 8, ev, ctx->stream),
+                       P<uint32_t>(ctx->counters) + C_NSPLATS, dL, dL_ddepth, P<float>(ctx->splat_grad), gb,
+                       freeze_leaves, ctx->num_sms * 8, ev, ctx->stream),
        "backward");
     if (ctx->prof) ctx->ev_used[H3DGS_STAGE_BACKWARD_BLEND] = ctx->ev_used[H3DGS_STAGE_BACKWARD_SPLAT] = true;
     return H3DGS_OK;

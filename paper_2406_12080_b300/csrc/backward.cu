@@ -97,8 +97,10 @@ __device__ __forceinline__ float2 sel2(bool p0, bool p1, float2 a, float2 b) {
 // single-chunk tile starts from the pixel's final T and contributor count; a chunk of a split tile
 // starts from the T at its end and its last contributor (saved by the forward pass), with the colour
 // behind it = later chunks' colour + T_final bg.  Per splat the two pixels' gradients are added in
-// registers before the warp reduction, and the arithmetic runs on pixel pairs.
-template <int TW, int TH>
+// registers before the warp reduction, and the arithmetic runs on pixel pairs.  The incoming
+// gradient is taken back through the camera's exposure affine (dL/dC = E^T dL/dout); DEPTH adds the
+// expected-depth channel (gradient dLdepth, the splat's view depth as its colour, no background).
+template <int TW, int TH, bool DEPTH>
 __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCam* __restrict__ cams, int n_cams,
                                                                      DevOpts o, const int2* __restrict__ ranges,
                                                                      const uint32_t* __restrict__ list,
@@ -113,10 +115,14 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
                                                                      const float* __restrict__ T_final,
                                                                      const int32_t* __restrict__ n_contrib,
                                                                      const float* __restrict__ dL,
+                                                                     const float* __restrict__ dLdepth,
+                                                                     const float* __restrict__ exposure,
+                                                                     const float* __restrict__ scD,
                                                                      float* __restrict__ sgrad) {
     constexpr int NT = TW * TH, NT2 = NT / 2;
     __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];
     __shared__ uint32_t s_id[NT2], s_m[NT2];
+    __shared__ float s_dz[DEPTH ? NT2 : 1];
     __shared__ int s_max;
     const uint32_t item = blockIdx.x;
     if (item >= *n_items) return;
@@ -143,14 +149,22 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
     const int2 r = ranges[tile];
     const int begin = r.x + it.y * chunk;     // first list entry of this item
     float Tk[2] = {1.0f, 1.0f}, gk[2][3] = {{0, 0, 0}, {0, 0, 0}}, Sk[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    float gdk[2] = {0.0f, 0.0f}, SDk[2] = {0.0f, 0.0f};
     int stop[2] = {begin, begin};             // entries [begin, stop) are walked back to front
     const int64_t plane = (int64_t)cam.width * cam.height;
+    const float* E = exposure ? exposure + 12 * lo : nullptr;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         if (!in_[k]) continue;
         const int64_t pix = cam.pix_base + (int64_t)pyi[k] * cam.width + px_i;
         const float* gp = dL + 3 * cam.pix_base + (int64_t)pyi[k] * cam.width + px_i;
-        gk[k][0] = gp[0]; gk[k][1] = gp[plane]; gk[k][2] = gp[2 * plane];
+        const float go0 = gp[0], go1 = gp[plane], go2 = gp[2 * plane];
+        if (E) {
+            for (int ch = 0; ch < 3; ++ch) gk[k][ch] = fmaf(E[ch], go0, fmaf(E[4 + ch], go1, E[8 + ch] * go2));
+        } else {
+            gk[k][0] = go0; gk[k][1] = go1; gk[k][2] = go2;
+        }
+        if (DEPTH) gdk[k] = dLdepth[pix];
         const float Tf = T_final[pix];
         for (int ch = 0; ch < 3; ++ch) Sk[k][ch] = Tf * o.bg[ch];
         if (nch == 1) {
@@ -165,6 +179,7 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
             for (int c = it.y + 1; c < nch; ++c) {
                 const int64_t sl = (i0 + c) * NT + lyk[k] * TW + lx;
                 for (int ch = 0; ch < 3; ++ch) Sk[k][ch] += scC[3 * sl + ch];
+                if (DEPTH) SDk[k] += scD[sl];
             }
         }
     }
@@ -172,6 +187,8 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
     const float2 g0 = make_float2(gk[0][0], gk[1][0]), g1 = make_float2(gk[0][1], gk[1][1]),
                  g2 = make_float2(gk[0][2], gk[1][2]);
     float2 S0 = make_float2(Sk[0][0], Sk[1][0]), S1 = make_float2(Sk[0][1], Sk[1][1]), S2 = make_float2(Sk[0][2], Sk[1][2]);
+    const float2 gd2 = make_float2(gdk[0], gdk[1]);
+    float2 SD = make_float2(SDk[0], SDk[1]);
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
     atomicMax(&s_max, max(stop[0], stop[1]) - begin);
@@ -193,6 +210,7 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
             s_b[threadIdx.x] = bb;
             s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
             s_m[threadIdx.x] = warp_mask<TW, TH, 8>(a, bb.x, d, ox, oy);
+            if (DEPTH) s_dz[threadIdx.x] = d.w;
         }
         __syncthreads();
         // back to front over the splats that reach this warp's pixels
@@ -237,6 +255,13 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
             S0 = sel2(con0, con1, fma2(f2(c.x), wgt, S0), S0);
             S1 = sel2(con0, con1, fma2(f2(c.y), wgt, S1), S1);
             S2 = sel2(con0, con1, fma2(f2(c.z), wgt, S2), S2);
+            float2 gz = f2(0.0f);
+            if (DEPTH) {
+                const float zj = s_dz[j];
+                dal = fma2(gd2, fma2(T, f2(zj), mul2(f2(-1.0f), mul2(SD, inv))), dal);
+                gz = mul2(gd2, wgt);
+                SD = sel2(con0, con1, fma2(f2(zj), wgt, SD), SD);
+            }
             const float2 dan = interp ? mul2(f2(1.0f - b.w), dal) : dal;
             const bool nl0 = xn.x < clampv, nl1 = xn.y < clampv;
             const float2 gon = sel2(nl0, nl1, mul2(dan, G), f2(0.0f));
@@ -257,10 +282,10 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
             // both pixels' contributions of this splat (a pixel that does not take it adds zero)
             auto sum2 = [&](float2 x) { return (con0 ? x.x : 0.0f) + (con1 ? x.y : 0.0f); };
             float v[16] = {sum2(gu), sum2(gv), sum2(gca), sum2(gcb), sum2(gcc), sum2(gon), sum2(gop), sum2(gr),
-                           sum2(gg), sum2(gb), 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                           sum2(gg), sum2(gb), DEPTH ? sum2(gz) : 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const float sum = warp_reduce_scatter16(v, lane);
             const int kk = (lane >> 1) & 15;
-            if (!(lane & 1) && kk < 10) atomicAdd(sgrad + 12 * (int64_t)s_id[j] + kk, sum);
+            if (!(lane & 1) && kk < (DEPTH ? 11 : 10)) atomicAdd(sgrad + 12 * (int64_t)s_id[j] + kk, sum);
           }
         }
     }
@@ -287,6 +312,7 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         if (rect[m].x == 0xffffffffu) continue;  // culled
         const float* gs = sgrad + 12 * (int64_t)m;
         const float gu = gs[0], gv = gs[1], gca = gs[2], gcb = gs[3], gcc = gs[4], gon = gs[5], gop = gs[6];
+        const float gz = gs[10];   // expected-depth channel: d L / d (view depth of the mean)
         const float grgb[3] = {gs[7], gs[8], gs[9]};
         const int k = find_cam(cut_offsets, n_cams, m);
         const DevCam& cam = cams[k];
@@ -388,7 +414,7 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         const float dtxc = -dJ02 * fx * iz, dtyc = -dJ12 * fy * iz;
         const float dxz = gu * fx + (x_in ? dtxc : 0.0f);
         const float dyz = gv * fy + (y_in ? dtyc : 0.0f);
-        const float dxc[3] = {dxz * iz, dyz * iz, dz - dxz * xc[0] * iz2 - dyz * xc[1] * iz2};
+        const float dxc[3] = {dxz * iz, dyz * iz, dz + gz - dxz * xc[0] * iz2 - dyz * xc[1] * iz2};
         float dmu[3];
         for (int j = 0; j < 3; ++j) dmu[j] = W[j] * dxc[0] + W[3 + j] * dxc[1] + W[6 + j] * dxc[2];
         // rotation matrix w.r.t. the unit quaternion
@@ -503,16 +529,20 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
 
 cudaError_t launch_backward(const DevHier& h, const BlendArgs& a, const int32_t* cut_ids, const float* cut_t,
                             const int64_t* cut_offsets, const uint2* rect, const uint32_t* n_splats, const float* dL,
-                            float* splat_grad, const GradBufs& g, int freeze_leaves, int grid, cudaEvent_t* ev,
-                            cudaStream_t s) {
+                            const float* dLdepth, float* splat_grad, const GradBufs& g, int freeze_leaves, int grid,
+                            cudaEvent_t* ev, cudaStream_t s) {
     if (ev) cudaEventRecord(ev[0], s);
     if (a.n_tiles > 0) {
         const unsigned ig = (unsigned)a.item_cap;
-#define BW(TWV, THV)                                                                                              \
-    backward_blend_kernel<TWV, THV><<<ig, TWV * THV / 2, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat,    \
-                                                             a.items, a.n_items, a.tile_item0, a.tile_nch, a.chunk, \
-                                                             a.scratch_C, a.scratch_Tend, a.scratch_last, a.T_final, \
-                                                             a.n_contrib, dL, splat_grad)
+#define BWD(TWV, THV, DEP)                                                                                          \
+    backward_blend_kernel<TWV, THV, DEP><<<ig, TWV * THV / 2, 0, s>>>(                                              \
+        a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.items, a.n_items, a.tile_item0, a.tile_nch, a.chunk,      \
+        a.scratch_C, a.scratch_Tend, a.scratch_last, a.T_final, a.n_contrib, dL, dLdepth, a.exposure, a.scratch_D,    \
+        splat_grad)
+#define BW(TWV, THV)                                                                                                \
+    do {                                                                                                            \
+        if (dLdepth) BWD(TWV, THV, true); else BWD(TWV, THV, false);                                                \
+    } while (0)
         const DevOpts& o = a.o;
         if (o.tile_w == 16 && o.tile_h == 16) BW(16, 16);
         else if (o.tile_w == 8 && o.tile_h == 8) BW(8, 8);
@@ -521,6 +551,7 @@ cudaError_t launch_backward(const DevHier& h, const BlendArgs& a, const int32_t*
         else if (o.tile_w == 16 && o.tile_h == 8) BW(16, 8);
         else return cudaErrorInvalidValue;
 #undef BW
+#undef BWD
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

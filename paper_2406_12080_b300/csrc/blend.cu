@@ -20,6 +20,11 @@
 //   combine   per pixel of a split tile: colour = sum of its chunks, T_final and the last
 //             contributor from the chunk where the walk stopped.
 // A chunk whose T_in is already below t_min adds nothing (the walk stopped in an earlier chunk).
+//
+// Optional outputs (appendix, depth regularisation and exposure optimisation): the expected depth
+// sum(T alpha z), accumulated like a fourth colour channel with the splat's view depth z and no
+// background term, and the camera's 3x4 exposure affine applied to the pixel colour,
+// out = E [C + T bg | 1].
 #include <algorithm>
 
 #include "internal.cuh"
@@ -201,19 +206,37 @@ struct Scratch {
     float* C;      // [3] colour of the chunk
     float* Tend;   // T after the chunk's walk (stop applied)
     int32_t* last; // list position (within the tile) after the chunk's last contributor, or -1
+    float* D;      // expected depth of the chunk (depth output only)
 };
+
+// One pixel's colour C + T bg, through the camera's exposure affine E (row-major 3x4) when given.
+__device__ __forceinline__ void write_pixel(float* img, int64_t plane, float T, float C0, float C1, float C2,
+                                            const DevOpts& o, const float* __restrict__ E) {
+    const float r = fmaf(T, o.bg[0], C0), g = fmaf(T, o.bg[1], C1), b = fmaf(T, o.bg[2], C2);
+    if (E) {
+        img[0] = fmaf(E[0], r, fmaf(E[1], g, fmaf(E[2], b, E[3])));
+        img[plane] = fmaf(E[4], r, fmaf(E[5], g, fmaf(E[6], b, E[7])));
+        img[2 * plane] = fmaf(E[8], r, fmaf(E[9], g, fmaf(E[10], b, E[11])));
+    } else {
+        img[0] = r;
+        img[plane] = g;
+        img[2 * plane] = b;
+    }
+}
 
 // Walk of one item over list entries [begin, end) for this thread's two pixels.  MAIN: the exact
 // skip/stop rules with colour; otherwise the transmittance pass (product of (1 - alpha) over
 // contributors, no colour; a pixel is finished once T < t_min, after which nothing it could add
 // matters).  Branch-free per entry: the alpha of every live pixel is computed and applied through
-// selects; the paired fp32 instructions evaluate both pixels at once.
-template <int TW, int TH, bool MAIN, bool COUNT>
+// selects; the paired fp32 instructions evaluate both pixels at once.  DEPTH: the expected depth Dp
+// is accumulated as a fourth channel.
+template <int TW, int TH, bool MAIN, bool COUNT, bool DEPTH>
 __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const uint32_t* __restrict__ list,
                                             const float4* __restrict__ splat, int begin, int end, int list0,
                                             float clampv, float afloor, float tmin, float4* s_a, float4* s_b,
-                                            float4* s_c, uint32_t* s_m, float2& T, float2& C0, float2& C1,
-                                            float2& C2, int2& last, bool& done0, bool& done1, unsigned int& evals) {
+                                            float4* s_c, uint32_t* s_m, float* s_d, float2& T, float2& C0,
+                                            float2& C1, float2& C2, float2& Dp, int2& last, bool& done0, bool& done1,
+                                            unsigned int& evals) {
     constexpr int NT2 = TW * TH / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int b0 = begin; b0 < end; b0 += NT2) {
@@ -228,6 +251,7 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
             s_b[threadIdx.x] = bb;
             s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
             s_m[threadIdx.x] = warp_mask<TW, TH, 8>(a, bb.x, d, g.ox, g.oy);
+            if (DEPTH) s_d[threadIdx.x] = d.w;
         }
         __syncthreads();
         if (__any_sync(0xffffffffu, !(done0 && done1))) {
@@ -253,6 +277,7 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
                         C0 = __ffma2_rn(make_float2(c.x, c.x), w, C0);
                         C1 = __ffma2_rn(make_float2(c.y, c.y), w, C1);
                         C2 = __ffma2_rn(make_float2(c.z, c.z), w, C2);
+                        if (DEPTH) Dp = __ffma2_rn(make_float2(s_d[j], s_d[j]), w, Dp);
                         T = make_float2(app0 ? Tn.x : T.x, app1 ? Tn.y : T.y);
                         const int pos = b0 + j + 1 - list0;
                         last = make_int2(app0 ? pos : last.x, app1 ? pos : last.y);
@@ -273,7 +298,8 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
 // producers of its tile have published their products (per-tile counter, bounded wait), which were
 // all taken before it.  TW x TH / 2 threads, two pixels each.  COUNT: count the (pixel, splat)
 // evaluations into n_evals (profiling only; the count costs instructions in the innermost loop).
-template <int TW, int TH, bool COUNT>
+// DEPTH: also the expected depth (depth != NULL).
+template <int TW, int TH, bool COUNT, bool DEPTH>
 __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
                                                                   const int2* __restrict__ ranges,
                                                                   const uint32_t* __restrict__ list,
@@ -288,6 +314,8 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
                                                                   Scratch sc, uint32_t* __restrict__ ticket,
                                                                   uint32_t* __restrict__ tile_done,
                                                                   float* __restrict__ images,
+                                                                  float* __restrict__ depth,
+                                                                  const float* __restrict__ exposure,
                                                                   float* __restrict__ T_final,
                                                                   int32_t* __restrict__ n_contrib,
                                                                   unsigned long long* __restrict__ n_evals,
@@ -295,6 +323,7 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     constexpr int NT = TW * TH, NT2 = NT / 2;
     __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];
     __shared__ uint32_t s_m[NT2];
+    __shared__ float s_d[DEPTH ? NT2 : 1];
     __shared__ unsigned int s_evals[2];
     __shared__ uint32_t s_k;
     if (threadIdx.x == 0) s_k = atomicAdd(ticket, 1u);
@@ -327,16 +356,17 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
         for (int c = 0; c < it.y; ++c)
             T = __fmul2_rn(T, make_float2(__ldcg(sc.Tc + (i0 + c) * NT + g.slot0), __ldcg(sc.Tc + (i0 + c) * NT + g.slot1)));
     }
-    float2 C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0;
+    float2 C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0, Dp = C0;
     int2 last = make_int2(-1, -1);
     unsigned int evals = 0;
     bool done0 = !g.in0 || T.x < o.t_min, done1 = !g.in1 || T.y < o.t_min;
     if (main_pass)
-        blend_walk2<TW, TH, true, COUNT>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min, s_a,
-                                         s_b, s_c, s_m, T, C0, C1, C2, last, done0, done1, evals);
+        blend_walk2<TW, TH, true, COUNT, DEPTH>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min,
+                                                s_a, s_b, s_c, s_m, s_d, T, C0, C1, C2, Dp, last, done0, done1, evals);
     else
-        blend_walk2<TW, TH, false, COUNT>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min, s_a,
-                                          s_b, s_c, s_m, T, C0, C1, C2, last, done0, done1, evals);
+        blend_walk2<TW, TH, false, COUNT, false>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
+                                                 o.t_min, s_a, s_b, s_c, s_m, s_d, T, C0, C1, C2, Dp, last, done0,
+                                                 done1, evals);
     if (COUNT) {
         for (int off = 16; off > 0; off >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, off);
         if (lane == 0) atomicAdd(&s_evals[main_pass ? 0 : 1], evals);
@@ -353,6 +383,10 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
             sc.Tend[s1] = T.y;
             sc.last[s0] = last.x;
             sc.last[s1] = last.y;
+            if (DEPTH) {
+                sc.D[s0] = Dp.x;
+                sc.D[s1] = Dp.y;
+            }
             sc.Tc[s0] = (done0 && g.in0) ? 0.0f : T.x;
             sc.Tc[s1] = (done1 && g.in1) ? 0.0f : T.y;
         }
@@ -372,25 +406,26 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
         sc.Tend[s1] = T.y;
         sc.last[s0] = last.x;
         sc.last[s1] = last.y;
+        if (DEPTH) {
+            sc.D[s0] = Dp.x;
+            sc.D[s1] = Dp.y;
+        }
         return;
     }
     const DevCam& cam = *g.cam;
     const int64_t plane = (int64_t)cam.width * cam.height;
+    const float* E = exposure ? exposure + 12 * (g.cam - cams) : nullptr;
     if (g.in0) {
         const int64_t pix = cam.pix_base + (int64_t)g.py_i0 * cam.width + g.px_i;
-        float* img = images + 3 * cam.pix_base + (int64_t)g.py_i0 * cam.width + g.px_i;
-        img[0] = fmaf(T.x, o.bg[0], C0.x);
-        img[plane] = fmaf(T.x, o.bg[1], C1.x);
-        img[2 * plane] = fmaf(T.x, o.bg[2], C2.x);
+        write_pixel(images + 3 * cam.pix_base + (int64_t)g.py_i0 * cam.width + g.px_i, plane, T.x, C0.x, C1.x, C2.x, o, E);
+        if (DEPTH) depth[pix] = Dp.x;
         if (T_final) T_final[pix] = T.x;
         if (n_contrib) n_contrib[pix] = last.x < 0 ? 0 : last.x;
     }
     if (g.in1) {
         const int64_t pix = cam.pix_base + (int64_t)g.py_i1 * cam.width + g.px_i;
-        float* img = images + 3 * cam.pix_base + (int64_t)g.py_i1 * cam.width + g.px_i;
-        img[0] = fmaf(T.y, o.bg[0], C0.y);
-        img[plane] = fmaf(T.y, o.bg[1], C1.y);
-        img[2 * plane] = fmaf(T.y, o.bg[2], C2.y);
+        write_pixel(images + 3 * cam.pix_base + (int64_t)g.py_i1 * cam.width + g.px_i, plane, T.y, C0.y, C1.y, C2.y, o, E);
+        if (DEPTH) depth[pix] = Dp.y;
         if (T_final) T_final[pix] = T.y;
         if (n_contrib) n_contrib[pix] = last.y < 0 ? 0 : last.y;
     }
@@ -402,7 +437,9 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
                                                                 int64_t n_tiles, const int32_t* __restrict__ tile_item0,
                                                                 const int32_t* __restrict__ tile_nch, Scratch sc,
-                                                                float* __restrict__ images, float* __restrict__ T_final,
+                                                                float* __restrict__ images, float* __restrict__ depth,
+                                                                const float* __restrict__ exposure,
+                                                                float* __restrict__ T_final,
                                                                 int32_t* __restrict__ n_contrib) {
     constexpr int NT = TW * TH;
     const int64_t tile = blockIdx.x;
@@ -421,7 +458,7 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
     const int py_i = (local / cam.tiles_x) * TH + (int)threadIdx.x / TW;
     if (px_i >= cam.width || py_i >= cam.height) return;
     const int64_t i0 = tile_item0[tile];
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f, Tin = 1.0f;
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f, T = 1.0f, Tin = 1.0f;
     int last = 0;
     for (int c = 0; c < nch; ++c) {
         const int64_t slot = (i0 + c) * NT + threadIdx.x;
@@ -429,6 +466,7 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
             C0 += sc.C[3 * slot + 0];
             C1 += sc.C[3 * slot + 1];
             C2 += sc.C[3 * slot + 2];
+            if (depth) D += sc.D[slot];
             T = sc.Tend[slot];
             if (sc.last[slot] >= 0) last = sc.last[slot];
         }
@@ -436,10 +474,9 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
     }
     const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
     const int64_t plane = (int64_t)cam.width * cam.height;
-    float* img = images + 3 * cam.pix_base + (int64_t)py_i * cam.width + px_i;
-    img[0] = fmaf(T, o.bg[0], C0);
-    img[plane] = fmaf(T, o.bg[1], C1);
-    img[2 * plane] = fmaf(T, o.bg[2], C2);
+    write_pixel(images + 3 * cam.pix_base + (int64_t)py_i * cam.width + px_i, plane, T, C0, C1, C2, o,
+                exposure ? exposure + 12 * lo : nullptr);
+    if (depth) depth[pix] = D;
     if (T_final) T_final[pix] = T;
     if (n_contrib) n_contrib[pix] = last;
 }
@@ -463,25 +500,29 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     blend_plan_kernel<<<(unsigned)pblocks, PL_THREADS, 0, s>>>(a.ranges, a.n_tiles, a.chunk, a.tile_item0, a.tile_nch,
                                                                a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons, a.n_items,
                                                                lb);
-    Scratch sc{a.scratch_Tc, a.scratch_C, a.scratch_Tend, a.scratch_last};
+    Scratch sc{a.scratch_Tc, a.scratch_C, a.scratch_Tend, a.scratch_last, a.scratch_D};
     e = cudaMemsetAsync(a.queue_sync, 0, sizeof(uint32_t) * (size_t)(a.n_tiles + 1), s);
     if (e != cudaSuccess) return e;
     // queue length 2 X + Y <= 2 item_cap - n_tiles
     const unsigned gq = (unsigned)std::max<int64_t>(1, 2 * a.item_cap - a.n_tiles);
     const unsigned tg = (unsigned)a.n_tiles;
-#define QUEUE(TWV, THV, CNT)                                                                                          \
-    blend_queue_kernel<TWV, THV, CNT><<<gq, TWV * THV / 2, 0, s>>>(a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat,  \
-                                                                   a.items, a.q_prod, a.q_single, a.q_cons,           \
-                                                                   a.n_items, a.tile_item0, a.tile_nch, a.chunk, sc,  \
-                                                                   a.queue_sync, a.queue_sync + 1, a.images,          \
-                                                                   a.T_final, a.n_contrib, a.n_evals, a.flags)
+#define QUEUE(TWV, THV, CNT, DEP)                                                                                     \
+    blend_queue_kernel<TWV, THV, CNT, DEP><<<gq, TWV * THV / 2, 0, s>>>(                                              \
+        a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.items, a.q_prod, a.q_single, a.q_cons, a.n_items,         \
+        a.tile_item0, a.tile_nch, a.chunk, sc, a.queue_sync, a.queue_sync + 1, a.images, a.depth, a.exposure,         \
+        a.T_final, a.n_contrib, a.n_evals, a.flags)
 #define BL(TWV, THV)                                                                                                  \
     do {                                                                                                              \
         if (a.ev_queue) cudaEventRecord(a.ev_queue[0], s);                                                            \
-        if (a.n_evals) QUEUE(TWV, THV, true); else QUEUE(TWV, THV, false);                                            \
+        if (a.depth) {                                                                                                \
+            if (a.n_evals) QUEUE(TWV, THV, true, true); else QUEUE(TWV, THV, false, true);                            \
+        } else {                                                                                                      \
+            if (a.n_evals) QUEUE(TWV, THV, true, false); else QUEUE(TWV, THV, false, false);                          \
+        }                                                                                                             \
         if (a.ev_queue) cudaEventRecord(a.ev_queue[1], s);                                                            \
         blend_combine_kernel<TWV, THV><<<tg, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.n_tiles, a.tile_item0,       \
-                                                                a.tile_nch, sc, a.images, a.T_final, a.n_contrib);    \
+                                                                a.tile_nch, sc, a.images, a.depth, a.exposure,        \
+                                                                a.T_final, a.n_contrib);                              \
     } while (0)
     const DevOpts& o = a.o;
     if (o.tile_w == 16 && o.tile_h == 16) BL(16, 16);

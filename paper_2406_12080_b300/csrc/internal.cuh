@@ -169,7 +169,7 @@ __device__ __forceinline__ bool block_reach(const float4 a, float cc, const floa
 // Bit w set if the splat can reach alpha_floor at a pixel centre of warp w's 8 x BH block in the tile
 // with pixel origin (ox, oy); a clear bit means alpha < alpha_floor at every pixel of the block, so
 // the warp would skip the splat anyway.  a = {u, v, ca, cb}, cc = the third conic term (pre-scaled:
-// the exponent is p2 = ca dx^2 + cb dx dy + cc dy^2), d = {hx, hy, rz, 0}: hx, hy are the inflated
+// the exponent is p2 = ca dx^2 + cb dx dy + cc dy^2), d = {hx, hy, rz, z}: hx, hy are the inflated
 // half-widths of the bounding box of the level set o_max 2^p2 = alpha_floor and rz = log2(o_max /
 // alpha_floor) inflated by 2% + 0.02; hx < 0 marks a splat that never reaches the floor.
 template <int TW, int TH, int BH = 4>
@@ -228,7 +228,7 @@ cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const C
 // preprocess.cu
 constexpr int SPLAT_F4 = 4;      // float4 per splat record
 struct SplatBufs {
-    float4* rec;           // [cap][4]: {u, v, ca, cb}, {cc, on', op', t}, {r, g, b, K}, {hx, hy, rz, 0}
+    float4* rec;           // [cap][4]: {u, v, ca, cb}, {cc, on', op', t}, {r, g, b, K}, {hx, hy, rz, z} (z = view depth)
     uint2* rect;           // [cap]: (x0 | x1 << 16, y0 | y1 << 16)
     uint32_t* depth_key;   // [cap] fp32 depth bits, 0xffffffff when culled
     uint32_t* tiles;       // [cap] tiles touched (0 when culled)
@@ -302,6 +302,9 @@ struct BlendArgs {
     float* scratch_Tend;
     int32_t* scratch_last;
     float* images;
+    float* depth;                 // expected depth per pixel, or NULL (not computed)
+    const float* exposure;        // [n_cams][12] row-major 3x4 exposure affines, or NULL (identity)
+    float* scratch_D;             // per (item, pixel) expected depth of split tiles' chunks (depth only)
     float* T_final;
     int32_t* n_contrib;
     unsigned long long* n_evals;  // [2]: main-pass evaluations, transmittance-pass evaluations
@@ -352,7 +355,7 @@ struct GradBufs {
 };
 cudaError_t launch_backward(const DevHier& h, const BlendArgs& a, const int32_t* cut_ids, const float* cut_t,
                             const int64_t* cut_offsets, const uint2* rect, const uint32_t* n_splats, const float* dL,
-                            float* splat_grad, const GradBufs& g, int freeze_leaves, int grid,
-                            cudaEvent_t* ev /* 4 events or NULL */, cudaStream_t s);
+                            const float* dLdepth /* NULL: no depth gradient */, float* splat_grad, const GradBufs& g,
+                            int freeze_leaves, int grid, cudaEvent_t* ev /* 4 events or NULL */, cudaStream_t s);
 
 }  // namespace h3dgs

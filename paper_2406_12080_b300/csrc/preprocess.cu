@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
         sb.rec[SPLAT_F4 * m + 0] = make_float4(u, v, ca, cb);
         sb.rec[SPLAT_F4 * m + 1] = make_float4(cc, on, op, t);
         sb.rec[SPLAT_F4 * m + 2] = make_float4(fmaxf(rgb[0], 0.0f), fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), K);
-        sb.rec[SPLAT_F4 * m + 3] = make_float4(hx, hy, rz, 0.0f);
+        sb.rec[SPLAT_F4 * m + 3] = make_float4(hx, hy, rz, z);
         sb.rect[m] = make_uint2((uint32_t)rx0 | ((uint32_t)rx1 << 16), (uint32_t)ry0 | ((uint32_t)ry1 << 16));
         sb.depth_key[m] = __float_as_uint(z);
         sb.tiles[m] = (uint32_t)((rx1 - rx0 + 1) * (ry1 - ry0 + 1));

@@ -96,6 +96,9 @@ def lib():
                                                C.POINTER(i64), vp]),
             "h3dgs_render": (i32, [vp, C.POINTER(h3dgs_camera), i32, vp, vp, vp, C.POINTER(h3dgs_render_opts), vp, i32]),
             "h3dgs_render_backward": (i32, [vp, vp, C.POINTER(h3dgs_grads), i32]),
+            "h3dgs_render_ex": (i32, [vp, C.POINTER(h3dgs_camera), i32, vp, vp, vp, C.POINTER(h3dgs_render_opts), vp,
+                                      vp, vp, i32]),
+            "h3dgs_render_backward_ex": (i32, [vp, vp, vp, C.POINTER(h3dgs_grads), i32]),
             "h3dgs_get_stats": (i32, [vp, C.POINTER(h3dgs_stats)]),
             "h3dgs_set_profiling": (i32, [vp, i32]),
             "h3dgs_debug_wait_timeout": (i32, [vp, i32]),
@@ -269,6 +272,21 @@ def h3dgs_render_backward(ctx, dL_dimages, grads: dict, freeze_leaves: int = 0):
     _check(ctx, lib().h3dgs_render_backward(ctx, _ptr(dL_dimages), C.byref(g), freeze_leaves))
 
 
+def h3dgs_render_ex(ctx, cams, cut_ids, cut_t, cut_offsets, opts: h3dgs_render_opts, images, depth=None,
+                    exposure=None, save_for_backward: int = 0, cam_array=None):
+    """depth: device [sum H_k W_k] or None; exposure: device [n_cams, 3, 4] or None."""
+    arr = cam_array if cam_array is not None else camera_array(cams)
+    _check(ctx, lib().h3dgs_render_ex(ctx, arr, len(cams), _ptr(cut_ids), _ptr(cut_t), _ptr(cut_offsets),
+                                      C.byref(opts), _ptr(images), _ptr(depth), _ptr(exposure), save_for_backward))
+
+
+def h3dgs_render_backward_ex(ctx, dL_dimages, dL_ddepth, grads: dict, freeze_leaves: int = 0):
+    g = h3dgs_grads()
+    for k in ("mean", "scale", "rot", "opacity", "sh"):
+        setattr(g, k, _ptr(grads[k]))
+    _check(ctx, lib().h3dgs_render_backward_ex(ctx, _ptr(dL_dimages), _ptr(dL_ddepth), C.byref(g), freeze_leaves))
+
+
 def h3dgs_get_stats(ctx) -> dict:
     s = h3dgs_stats()
     _check(ctx, lib().h3dgs_get_stats(ctx, C.byref(s)))
@@ -418,15 +436,23 @@ class Context:
         tot = h3dgs_select_cut(self.ctx, cams, ids, t, offs, cap)
         return ids[:tot], t[:tot], offs
 
-    def render(self, cams, cut, opts=None, save_for_backward=0, images=None):
+    def render(self, cams, cut, opts=None, save_for_backward=0, images=None, depth=False, exposure=None):
+        """Packed images; with depth=True (or a depth tensor) returns (images, depth).  exposure: device
+        tensor [n_cams, 3, 4] of per-camera affines applied to the colour."""
         import torch
         opts = opts or default_opts()
         npix = sum(3 * c.width * c.height for c in cams)
         if images is None:
             images = torch.empty(npix, dtype=torch.float32, device=self.device)
         ids, t, offs = cut
-        h3dgs_render(self.ctx, cams, ids, t, offs, opts, images, save_for_backward)
-        return images
+        if depth is False and exposure is None:
+            h3dgs_render(self.ctx, cams, ids, t, offs, opts, images, save_for_backward)
+            return images
+        d = depth if depth is not False and depth is not True else None
+        if depth is True:
+            d = torch.empty(npix // 3, dtype=torch.float32, device=self.device)
+        h3dgs_render_ex(self.ctx, cams, ids, t, offs, opts, images, d, exposure, save_for_backward)
+        return (images, d) if depth is not False else images
 
     def split_images(self, images, cams):
         out, o = [], 0
