@@ -345,6 +345,53 @@ def run_ours(args, rank, world, local):
             fb_ms += e0.elapsed_time(e1)
         fb_value = world * args.steps / (fb_ms / 1e3)
 
+        # ---- expected-depth output and exposure affine (appendix): forward frame, and forward + adjoint
+        # with a depth gradient, both graph-captured like the frames above
+        depth_buf = torch.empty(npix // 3, dtype=torch.float32, device=dev)
+        expo = torch.tensor([[1.05, 0.02, 0.0, 0.01], [0.0, 0.97, 0.03, 0.0], [0.01, 0.0, 1.02, -0.01]],
+                            dtype=torch.float32, device=dev).reshape(1, 3, 4).contiguous()
+        ddep = torch.randn(npix // 3, generator=torch.Generator(device=dev).manual_seed(1), device=dev)
+
+        def frame_de():
+            h3dgs.h3dgs_select_cut(ctx.ctx, cams, ids, tt, offs, cap, want_total=False)
+            h3dgs.h3dgs_render_ex(ctx.ctx, cams, ids, tt, offs, opts, images, depth_buf, expo, 0, cam_array=carr)
+
+        def fwd_bwd_de():
+            h3dgs.h3dgs_select_cut(ctx.ctx, cams, ids, tt, offs, cap, want_total=False)
+            h3dgs.h3dgs_render_ex(ctx.ctx, cams, ids, tt, offs, opts, images, depth_buf, expo, 1, cam_array=carr)
+            h3dgs.h3dgs_render_backward_ex(ctx.ctx, dl, ddep, grads, 1)
+
+        def time_steps(fn):
+            fn()
+            g = None
+            if not args.no_graph:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    fn()
+            r = g.replay if g is not None else fn
+            for _ in range(args.warmup):
+                r()
+                flush.fill_(1.0)
+            torch.cuda.synchronize()
+            acc = 0.0
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for _ in range(args.steps):
+                a0.record(stream)
+                r()
+                a1.record(stream)
+                flush.fill_(1.0)
+                a1.synchronize()
+                acc += a0.elapsed_time(a1)
+            return acc / args.steps
+
+        de_frame_ms = time_steps(frame_de)
+        de_fb_ms = time_steps(fwd_bwd_de)
+        assert h3dgs.h3dgs_get_stats(ctx.ctx)["device_flags"] == 0
+        depth_exposure = {"frame_ms": de_frame_ms, "frames_per_s": 1e3 / de_frame_ms,
+                          "fwd_bwd_ms": de_fb_ms, "fwd_bwd_views_per_s": 1e3 / de_fb_ms,
+                          "note": "cut + render with the expected-depth output and a 3x4 exposure affine; the "
+                                  "adjoint also takes a depth gradient"}
+
         # ---- end to end through the public API: image read back to pinned host memory every step
         host_img = torch.empty(npix, dtype=torch.float32, pin_memory=True)
         for _ in range(args.warmup):
@@ -436,6 +483,7 @@ def run_ours(args, rank, world, local):
         out["optimisation"] = optimisation
     if compaction is not None:
         out["compaction"] = compaction
+    out["depth_exposure"] = depth_exposure
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_time(scene, 4)
     if world > 1:
