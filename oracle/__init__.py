@@ -255,6 +255,35 @@ def compact(cams, h: Hierarchy, tau_min: float, tau_max: float):
     return out, o
 
 
+def stream_trace(cams, h: Hierarchy, update_every: int = 2, cleanup_every: int = 100, max_age: int = 100,
+                 interpolate: int = 1):
+    """Node residency of streamed rendering along a camera path (Sec. 5.3: the cut is updated every
+    few frames by transferring the nodes it needs from CPU RAM to the GPU; a cleanup runs every 100
+    frames).  Frame f = 0, 1, ...:
+      * if f % update_every == 0: the cut of cams[f]; the needed nodes are its nodes and the parents
+        of its entries with t != 0; the ones not resident are transferred; all needed are stamped f;
+      * the frame renders that cut;
+      * if (f + 1) % cleanup_every == 0: every resident node with f - stamp > max_age is evicted.
+    Returns (transfers per update, resident count after each cleanup, resident count at the end)."""
+    resident = np.zeros(h.n, bool)
+    stamp = np.full(h.n, -1, np.int64)
+    transfers, after_cleanup = [], []
+    for f, cam in enumerate(cams):
+        if f % update_every == 0:
+            ids, t = select_cut(cam, h, interpolate)
+            par = h.parent[ids]
+            need = np.zeros(h.n, bool)
+            need[ids] = True
+            need[par[(t != 0) & (par >= 0)]] = True
+            transfers.append(int(np.sum(need & ~resident)))
+            resident |= need
+            stamp[need] = f
+        if (f + 1) % cleanup_every == 0:
+            resident &= ~(f - stamp > max_age)
+            after_cleanup.append(int(resident.sum()))
+    return transfers, after_cleanup, int(resident.sum())
+
+
 # --------------------------------------------------------------------------------- render
 
 def interpolate(h: Hierarchy, ids, t, a64: Attrs64 | None = None):
