@@ -230,6 +230,33 @@ h3dgs_status h3dgs_compact_hierarchy(h3dgs_ctx* ctx, const h3dgs_camera* cams, i
  * The topology is trusted (not validated on the device). */
 h3dgs_status h3dgs_upload_hierarchy(h3dgs_ctx* ctx, const h3dgs_hierarchy* hier);
 
+/* Streamed (out-of-core) hierarchy (Sec. 5.3: the cut is updated every few frames by transferring
+ * the nodes it needs from CPU RAM to the GPU; a cleanup runs every 100 frames).  Like
+ * h3dgs_upload_hierarchy, but the attribute arrays (mean, scale, rot, opacity, sh) are PAGE-LOCKED
+ * HOST arrays (cudaHostAlloc / cudaHostRegister; borrowed, same layouts) while the boxes and the
+ * topology are device arrays.  The library keeps the 32-byte cut records of every node on the
+ * device and a cache of `cache_nodes` attribute rows (236 bytes each).  h3dgs_select_cut works as
+ * usual; before a cut is rendered, h3dgs_stream_update must have made its nodes resident.  Renders
+ * read attributes from the cache and are bit-identical to a resident hierarchy's; a cut node that
+ * is not resident is left out of the frame and sets bit 5 (0x20) of h3dgs_stats.device_flags.
+ * h3dgs_render_backward and h3dgs_compact_hierarchy return STATE on a streamed hierarchy; any
+ * upload replaces it.  Errors: INVALID_ARG (host attributes not page-locked, boxes/topology not
+ * device memory, sizes), OOM, CUDA. */
+h3dgs_status h3dgs_upload_hierarchy_streamed(h3dgs_ctx* ctx, const h3dgs_hierarchy* hier, int64_t cache_nodes);
+
+/* Makes every node of a cut (as returned by h3dgs_select_cut for n_cams cameras) and the parent of
+ * every entry with t != 0 resident, stamped with `frame`: absent nodes get free cache rows and are
+ * copied from host memory by a device gather over the host link.  *n_transferred (host, nullable;
+ * when given the call synchronises) = the number of nodes copied.  When the free rows run out the
+ * remaining nodes stay absent, bit 6 (0x40) of device_flags is set and, if n_transferred is given,
+ * the call returns CAPACITY.  Asynchronous and graph-capturable when n_transferred is NULL. */
+h3dgs_status h3dgs_stream_update(h3dgs_ctx* ctx, int32_t n_cams, const int32_t* cut_ids, const float* cut_t,
+                                 const int64_t* cut_offsets, int32_t frame, int64_t* n_transferred);
+
+/* Cleanup: frees the cache row of every resident node whose last update stamp s has
+ * frame - s > max_age.  *n_resident (host, nullable; synchronises) = the rows still in use. */
+h3dgs_status h3dgs_stream_cleanup(h3dgs_ctx* ctx, int32_t frame, int32_t max_age, int64_t* n_resident);
+
 /* ------------------------------------------------------------------------------ per frame */
 
 /* a1 + a2 -- cut selection and interpolation weights (Sec. 4.2, Fig. gran-cut, Eq. t_interp).

@@ -62,6 +62,10 @@ struct h3dgs_ctx {
     DBuf T_final, n_contrib, splat_grad;
     DBuf items, q_prod, q_single, q_cons, queue_sync, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last, sc_D;
     DBuf exposure;   // copy of the last render's exposure affines [n_cams][12]
+    // streamed hierarchy (attributes in host memory, a device cache of rows)
+    bool streamed = false;
+    StreamState st{};
+    DBuf st_mean, st_scale, st_rot, st_opacity, st_sh, st_slot_of, st_node_of, st_stamp, st_free, st_missing, st_count;
     int64_t item_cap = 0;
     bool fixed = false;
     int64_t cap_splats = 0, cap_pairs = 0;
@@ -173,6 +177,15 @@ DevHier dev_hier(h3dgs_ctx* ctx) {
     h.parent = ctx->hier.parent;
     h.child_count = ctx->hier.child_count;
     h.rec = P<const float4>(ctx->rec);
+    h.row_of = nullptr;
+    if (ctx->streamed) {
+        h.mean = ctx->st.mean;
+        h.scale = ctx->st.scale;
+        h.rot = reinterpret_cast<const float4*>(ctx->st.rot);
+        h.opacity = ctx->st.opacity;
+        h.sh = reinterpret_cast<const float4*>(ctx->st.sh);
+        h.row_of = ctx->st.slot_of;
+    }
     return h;
 }
 
@@ -297,7 +310,9 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
                     &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
                     &ctx->items, &ctx->q_prod, &ctx->q_single, &ctx->q_cons, &ctx->queue_sync,
                     &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
-                    &ctx->sc_last, &ctx->sc_D, &ctx->exposure};
+                    &ctx->sc_last, &ctx->sc_D, &ctx->exposure, &ctx->st_mean, &ctx->st_scale, &ctx->st_rot,
+                    &ctx->st_opacity, &ctx->st_sh, &ctx->st_slot_of, &ctx->st_node_of, &ctx->st_stamp,
+                    &ctx->st_free, &ctx->st_missing, &ctx->st_count};
     for (DBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& e : ctx->ev)
@@ -407,6 +422,7 @@ h3dgs_status h3dgs_compact_hierarchy(h3dgs_ctx* ctx, const h3dgs_camera* cams, i
     if (!ctx) return H3DGS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (!ctx->has_hier) return fail(ctx, H3DGS_ERR_STATE, "compact: no hierarchy uploaded");
+    if (ctx->streamed) return fail(ctx, H3DGS_ERR_STATE, "compact: not available for a streamed hierarchy");
     if (!cams || n_cams < 1 || n_cams > (1 << 20)) return fail(ctx, H3DGS_ERR_INVALID_ARG, "compact: need 1..2^20 cameras");
     for (int i = 0; i < n_cams; ++i)
         if (!(cams[i].fx > 0) || !(cams[i].fy > 0) || !std::isfinite(cams[i].fx) || !std::isfinite(cams[i].fy))
@@ -476,7 +492,102 @@ h3dgs_status h3dgs_upload_hierarchy(h3dgs_ctx* ctx, const h3dgs_hierarchy* h) {
     CK(launch_pack_records(*h, P<float4>(ctx->rec), ctx->stream), "pack records");
     ctx->hier = *h;
     ctx->has_hier = true;
+    ctx->streamed = false;
     ctx->rendered = ctx->saved = false;
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_upload_hierarchy_streamed(h3dgs_ctx* ctx, const h3dgs_hierarchy* h, int64_t cache_nodes) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!h) return fail(ctx, H3DGS_ERR_INVALID_ARG, "hierarchy: NULL");
+    if (h->n_nodes < 1 || h->n_nodes > 0x7fffffffLL) return fail(ctx, H3DGS_ERR_INVALID_ARG, "hierarchy: n_nodes out of range");
+    if (cache_nodes < 1 || cache_nodes > 0x7fffffffLL) return fail(ctx, H3DGS_ERR_INVALID_ARG, "stream: cache_nodes out of range");
+    CK(cudaSetDevice(ctx->device), "set device");
+    const void* dev_ptrs[] = {h->box_min, h->box_max, h->parent, h->child_start, h->child_count};
+    for (const void* p : dev_ptrs) {
+        cudaPointerAttributes a{};
+        if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeDevice)
+            return fail(ctx, H3DGS_ERR_INVALID_ARG, "stream: boxes and topology must be device arrays");
+        if (!aligned16(p)) return fail(ctx, H3DGS_ERR_INVALID_ARG, "hierarchy: arrays must be 16-byte aligned");
+    }
+    const float* host[5] = {h->mean, h->scale, h->rot, h->opacity, h->sh};
+    const float* mapped[5];
+    for (int k = 0; k < 5; ++k) {
+        cudaPointerAttributes a{};
+        if (!host[k] || cudaPointerGetAttributes(&a, host[k]) != cudaSuccess || a.type != cudaMemoryTypeHost)
+            return fail(ctx, H3DGS_ERR_INVALID_ARG, "stream: attributes must be page-locked host arrays");
+        void* d = nullptr;
+        if (cudaHostGetDevicePointer(&d, const_cast<float*>(host[k]), 0) != cudaSuccess || !d)
+            return fail(ctx, H3DGS_ERR_INVALID_ARG, "stream: attributes not mapped into the device address space");
+        mapped[k] = static_cast<const float*>(d);
+    }
+    const size_t C = (size_t)cache_nodes, N = (size_t)h->n_nodes;
+    CK(ensure(ctx->st_mean, 12 * C), "stream cache");
+    CK(ensure(ctx->st_scale, 12 * C), "stream cache");
+    CK(ensure(ctx->st_rot, 16 * C), "stream cache");
+    CK(ensure(ctx->st_opacity, 4 * C), "stream cache");
+    CK(ensure(ctx->st_sh, 192 * C), "stream cache");
+    CK(ensure(ctx->st_node_of, 4 * C), "stream cache");
+    CK(ensure(ctx->st_stamp, 4 * C), "stream cache");
+    CK(ensure(ctx->st_free, 4 * C), "stream cache");
+    CK(ensure(ctx->st_slot_of, 4 * N), "stream tables");
+    CK(ensure(ctx->st_missing, 4 * N), "stream tables");
+    CK(ensure(ctx->st_count, 16), "stream tables");
+    CK(ensure(ctx->rec, sizeof(float4) * 2 * N), "record buffer");
+    CK(launch_pack_records(*h, P<float4>(ctx->rec), ctx->stream), "pack records");
+    StreamState& st = ctx->st;
+    st.n_nodes = h->n_nodes;
+    st.cap = cache_nodes;
+    st.h_mean = mapped[0]; st.h_scale = mapped[1]; st.h_rot = mapped[2]; st.h_opacity = mapped[3]; st.h_sh = mapped[4];
+    st.mean = P<float>(ctx->st_mean); st.scale = P<float>(ctx->st_scale); st.rot = P<float>(ctx->st_rot);
+    st.opacity = P<float>(ctx->st_opacity); st.sh = P<float>(ctx->st_sh);
+    st.slot_of = P<int32_t>(ctx->st_slot_of); st.node_of = P<int32_t>(ctx->st_node_of);
+    st.stamp = P<int32_t>(ctx->st_stamp); st.free_list = P<int32_t>(ctx->st_free);
+    st.missing = P<int32_t>(ctx->st_missing); st.count = P<uint32_t>(ctx->st_count);
+    CK(stream_init(st, ctx->num_sms, ctx->stream), "stream init");
+    ctx->hier = *h;
+    ctx->has_hier = true;
+    ctx->streamed = true;
+    ctx->rendered = ctx->saved = false;
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_stream_update(h3dgs_ctx* ctx, int32_t n_cams, const int32_t* cut_ids, const float* cut_t,
+                                 const int64_t* cut_offsets, int32_t frame, int64_t* n_transferred) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_hier || !ctx->streamed) return fail(ctx, H3DGS_ERR_STATE, "stream_update: no streamed hierarchy");
+    if (n_cams < 1 || n_cams > MAX_CAMS || !cut_ids || !cut_offsets)
+        return fail(ctx, H3DGS_ERR_INVALID_ARG, "stream_update: bad cut");
+    CK(cudaSetDevice(ctx->device), "set device");
+    CK(stream_update(ctx->st, ctx->hier.parent, n_cams, cut_ids, cut_t, cut_offsets, frame,
+                     P<uint32_t>(ctx->counters) + C_CUTFLAGS, ctx->num_sms, ctx->stream),
+       "stream update");
+    if (n_transferred) {
+        uint32_t c[4];
+        CK(cudaMemcpyAsync(c, ctx->st.count, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream), "read stream counts");
+        CK(cudaStreamSynchronize(ctx->stream), "stream sync");
+        *n_transferred = c[2];
+        if (c[3] > c[2]) return fail(ctx, H3DGS_ERR_CAPACITY, "stream_update: cache full (run a cleanup or enlarge it)");
+    }
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_stream_cleanup(h3dgs_ctx* ctx, int32_t frame, int32_t max_age, int64_t* n_resident) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->has_hier || !ctx->streamed) return fail(ctx, H3DGS_ERR_STATE, "stream_cleanup: no streamed hierarchy");
+    if (max_age < 0) return fail(ctx, H3DGS_ERR_INVALID_ARG, "stream_cleanup: max_age < 0");
+    CK(cudaSetDevice(ctx->device), "set device");
+    CK(stream_cleanup(ctx->st, frame, max_age, ctx->num_sms, ctx->stream), "stream cleanup");
+    if (n_resident) {
+        uint32_t free_rows = 0;
+        CK(cudaMemcpyAsync(&free_rows, ctx->st.count, sizeof(free_rows), cudaMemcpyDeviceToHost, ctx->stream),
+           "read stream counts");
+        CK(cudaStreamSynchronize(ctx->stream), "stream sync");
+        *n_resident = ctx->st.cap - (int64_t)free_rows;
+    }
     return H3DGS_OK;
 }
 
@@ -716,6 +827,7 @@ h3dgs_status h3dgs_render_backward_ex(h3dgs_ctx* ctx, const float* dL, const flo
     if (!ctx) return H3DGS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (!ctx->saved || !ctx->has_hier) return fail(ctx, H3DGS_ERR_STATE, "render_backward: no saved forward state");
+    if (ctx->streamed) return fail(ctx, H3DGS_ERR_STATE, "render_backward: not available for a streamed hierarchy");
     if (dL_ddepth && !ctx->saved_depth)
         return fail(ctx, H3DGS_ERR_STATE, "render_backward: a depth gradient needs a forward that rendered depth");
     if (!dL || !g || !g->mean || !g->scale || !g->rot || !g->opacity || !g->sh)

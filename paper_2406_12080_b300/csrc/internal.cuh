@@ -20,6 +20,8 @@ constexpr uint32_t FLAG_SPLATS_OVERFLOW = 1u << 1;
 constexpr uint32_t FLAG_CUT_TRUNCATED = 1u << 2;
 constexpr uint32_t FLAG_WAIT_TIMEOUT = 1u << 3;   // a bounded wait on another block gave up (frame invalid)
 constexpr uint32_t FLAG_BAD_TOPOLOGY = 1u << 4;   // a parent index not below its child's (compaction)
+constexpr uint32_t FLAG_NOT_RESIDENT = 1u << 5;   // streamed hierarchy: a cut node's attributes not in the cache
+constexpr uint32_t FLAG_CACHE_FULL = 1u << 6;     // streamed hierarchy: too few free cache slots for an update
 constexpr int QUEUE_SPIN_LIMIT = 1 << 22;          // polls of the blend queue's per-tile counter
 
 // Per-camera data on the device.  Raw fields come from h3dgs_camera; the derived floats are
@@ -65,6 +67,8 @@ struct DevHier {
     const int32_t* parent;
     const int32_t* child_count;
     const float4* rec;     // packed cut records [N][2]: {box_min.xyz, parent}, {box_max.xyz, child_count}
+    const int32_t* row_of; // attribute row of each node (streamed hierarchy: its cache slot, -1 if absent), or
+                           // NULL: the node id
 };
 
 // ---------------------------------------------------------------- fp32 ops in a fixed order
@@ -348,6 +352,24 @@ cudaError_t build_hierarchy_chunked(int K, const int64_t* off, const float* mean
 cudaError_t compact_hierarchy(const h3dgs_hierarchy& h, const float4* rec, const h3dgs_camera* cams_host,
                               int n_cams, const float* levels, int n_levels, const BuildOut& out, int64_t capacity,
                               int32_t* old_index, int64_t* n_out, const SortWork& sw, int num_sms, cudaStream_t s);
+
+// stream.cu -- streamed hierarchy: attributes in page-locked host memory, a device cache of rows
+struct StreamState {
+    int64_t n_nodes, cap;                                     // nodes; cache rows
+    const float *h_mean, *h_scale, *h_rot, *h_opacity, *h_sh;  // device mappings of the host arrays
+    float *mean, *scale, *rot, *opacity, *sh;                  // cache rows [cap] (hierarchy layouts)
+    int32_t* slot_of;    // [n_nodes] cache row, -1 absent (-2 while claimed by an update)
+    int32_t* node_of;    // [cap] node of the row, -1 free
+    int32_t* stamp;      // [cap] frame of the last update that needed the row
+    int32_t* free_list;  // [cap] stack of free rows
+    int32_t* missing;    // [n_nodes] nodes to transfer in the current update
+    uint32_t* count;     // [4] free rows, listed nodes, transferred by the last update, requested by it
+};
+cudaError_t stream_init(const StreamState& st, int num_sms, cudaStream_t s);
+cudaError_t stream_update(const StreamState& st, const int32_t* parent, int n_cams, const int32_t* cut_ids,
+                          const float* cut_t, const int64_t* cut_offsets, int32_t frame, uint32_t* flags, int num_sms,
+                          cudaStream_t s);
+cudaError_t stream_cleanup(const StreamState& st, int32_t frame, int32_t max_age, int num_sms, cudaStream_t s);
 
 // backward.cu
 struct GradBufs {

@@ -107,7 +107,17 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
         const float t = (o.interpolate && cut_t) ? __ldg(cut_t + m) : 0.0f;
         const int32_t p = __ldg(h.parent + n);
         const bool use_p = (t != 0.0f) && p >= 0;
-        const Interp a = interp_geometry(h, n, p, use_p, t);
+        // attribute rows: the node ids, or the cache slots of a streamed hierarchy
+        const int32_t rn = h.row_of ? __ldg(h.row_of + n) : n;
+        const int32_t rp = (h.row_of && use_p) ? __ldg(h.row_of + p) : p;
+        if (rn < 0 || (use_p && rp < 0)) {   // not resident: flagged, left out of the frame
+            atomicOr(flags, FLAG_NOT_RESIDENT);
+            sb.tiles[m] = 0;
+            sb.depth_key[m] = 0xffffffffu;
+            sb.rect[m] = make_uint2(0xffffffffu, 0xffffffffu);
+            continue;
+        }
+        const Interp a = interp_geometry(h, rn, rp, use_p, t);
         // ---- view transform
         const float* W = cam.R;
         float xc[3];
@@ -220,8 +230,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
         float Y[16];
         sh_basis(dx, dy, dz, Y);
         float rgb[3] = {0.5f, 0.5f, 0.5f};
-        const float4* shn = h.sh + 12 * (int64_t)n;
-        const float4* shp = h.sh + 12 * (int64_t)(use_p ? p : n);
+        const float4* shn = h.sh + 12 * (int64_t)rn;
+        const float4* shp = h.sh + 12 * (int64_t)(use_p ? rp : rn);
 #pragma unroll
         for (int j = 0; j < 12; ++j) {
             float4 s4 = __ldg(shn + j);
@@ -237,8 +247,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
                 rgb[c % 3] = fmaf(sv[e], Y[c / 3], rgb[c % 3]);
             }
         }
-        const float on = fmul(__ldg(h.opacity + n), comp);
-        const float op = use_p ? fmul(__ldg(h.opacity + p), comp) : 0.0f;
+        const float on = fmul(__ldg(h.opacity + rn), comp);
+        const float op = use_p ? fmul(__ldg(h.opacity + rp), comp) : 0.0f;
         const float K = use_p ? (float)__ldg(h.child_count + p) : 1.0f;
         // alpha-floor box: alpha <= o_max G, and o_max G >= floor only inside the ellipse
         // d^T Sigma'_f^-1 d <= 2 ln(o_max / floor), whose bounding box has half-widths
@@ -284,19 +294,25 @@ __global__ void __launch_bounds__(256) interpolate_export_kernel(DevHier h, int 
         const float t = (interpolate && cut_t) ? cut_t[m] : 0.0f;
         const int32_t p = h.parent[n];
         const bool use_p = (t != 0.0f) && p >= 0;
-        const Interp a = interp_geometry(h, n, p, use_p, t);
+        const int32_t rn = h.row_of ? h.row_of[n] : n;
+        const int32_t rp = (h.row_of && use_p) ? h.row_of[p] : p;
+        if (rn < 0 || (use_p && rp < 0)) {   // not resident
+            for (int r = 0; r < NINTERP; ++r) out[(int64_t)r * m_total + m] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const Interp a = interp_geometry(h, rn, rp, use_p, t);
         for (int d = 0; d < 3; ++d) {
             out[(int64_t)d * m_total + m] = a.mean[d];
             out[(int64_t)(3 + d) * m_total + m] = a.scale[d];
         }
         for (int d = 0; d < 4; ++d) out[(int64_t)(6 + d) * m_total + m] = a.q[d];
         const float omt = fsub(1.0f, t);
-        const float* shn = reinterpret_cast<const float*>(h.sh) + (int64_t)NSH * n;
-        const float* shp = reinterpret_cast<const float*>(h.sh) + (int64_t)NSH * (use_p ? p : n);
+        const float* shn = reinterpret_cast<const float*>(h.sh) + (int64_t)NSH * rn;
+        const float* shp = reinterpret_cast<const float*>(h.sh) + (int64_t)NSH * (use_p ? rp : rn);
         for (int c = 0; c < NSH; ++c)
             out[(int64_t)(10 + c) * m_total + m] = use_p ? lerp_c(t, omt, shn[c], shp[c]) : shn[c];
-        out[(int64_t)58 * m_total + m] = h.opacity[n];
-        out[(int64_t)59 * m_total + m] = use_p ? h.opacity[p] : 0.0f;
+        out[(int64_t)58 * m_total + m] = h.opacity[rn];
+        out[(int64_t)59 * m_total + m] = use_p ? h.opacity[rp] : 0.0f;
         out[(int64_t)60 * m_total + m] = t;
         out[(int64_t)61 * m_total + m] = use_p ? (float)h.child_count[p] : 1.0f;
     }

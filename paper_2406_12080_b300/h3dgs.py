@@ -85,6 +85,9 @@ def lib():
             "h3dgs_default_opts": (None, [C.POINTER(h3dgs_render_opts)]),
             "h3dgs_reserve": (i32, [vp, i64, i64]),
             "h3dgs_upload_hierarchy": (i32, [vp, C.POINTER(h3dgs_hierarchy)]),
+            "h3dgs_upload_hierarchy_streamed": (i32, [vp, C.POINTER(h3dgs_hierarchy), i64]),
+            "h3dgs_stream_update": (i32, [vp, i32, vp, vp, vp, i32, C.POINTER(i64)]),
+            "h3dgs_stream_cleanup": (i32, [vp, i32, i32, C.POINTER(i64)]),
             "h3dgs_build_hierarchy": (i32, [vp, i64, vp, vp, vp, vp, vp, C.POINTER(h3dgs_node_arrays)]),
             "h3dgs_build_hierarchy_chunked": (i32, [vp, i32, C.POINTER(C.c_int64), vp, vp, vp, vp, vp,
                                                     C.POINTER(h3dgs_node_arrays)]),
@@ -209,6 +212,29 @@ def h3dgs_compact_hierarchy(ctx, cams, tau_min: float, tau_max: float, out: "Dev
     _check(ctx, lib().h3dgs_compact_hierarchy(ctx, camera_array(cams), len(cams), tau_min, tau_max, C.byref(a),
                                               out.n, _ptr(old_index), C.byref(n)))
     return n.value
+
+
+def h3dgs_upload_hierarchy_streamed(ctx, hier: "DeviceHierarchy", cache_nodes: int):
+    """hier: attributes as page-locked CPU tensors, boxes and topology as CUDA tensors."""
+    h = h3dgs_hierarchy()
+    h.n_nodes = hier.n
+    for k in ("mean", "scale", "rot", "opacity", "sh", "box_min", "box_max", "parent", "child_start",
+              "child_count"):
+        setattr(h, k, _ptr(getattr(hier, k)))
+    _check(ctx, lib().h3dgs_upload_hierarchy_streamed(ctx, C.byref(h), cache_nodes))
+
+
+def h3dgs_stream_update(ctx, n_cams: int, cut_ids, cut_t, cut_offsets, frame: int, want_count: bool = True):
+    n = C.c_int64(0)
+    _check(ctx, lib().h3dgs_stream_update(ctx, n_cams, _ptr(cut_ids), _ptr(cut_t), _ptr(cut_offsets), frame,
+                                          C.byref(n) if want_count else None))
+    return n.value if want_count else None
+
+
+def h3dgs_stream_cleanup(ctx, frame: int, max_age: int, want_count: bool = True):
+    n = C.c_int64(0)
+    _check(ctx, lib().h3dgs_stream_cleanup(ctx, frame, max_age, C.byref(n) if want_count else None))
+    return n.value if want_count else None
 
 
 def h3dgs_build_hierarchy_chunked(ctx, leaves: dict, chunk_offsets, out: "DeviceHierarchy"):
@@ -421,6 +447,18 @@ class Context:
         trim = DeviceHierarchy(*[getattr(out, k)[:m] for k in ("mean", "scale", "rot", "opacity", "sh", "box_min",
                                                              "box_max", "parent", "child_start", "child_count")])
         return trim, old[:m]
+
+    def upload_streamed(self, hier: DeviceHierarchy, cache_nodes: int) -> DeviceHierarchy:
+        """Streamed hierarchy: `hier`'s attributes are moved to page-locked host memory (the boxes and
+        topology stay on the device); returns the hierarchy as the library now borrows it."""
+        import torch
+        host = lambda t: t.detach().to("cpu").contiguous().pin_memory()
+        h = DeviceHierarchy(host(hier.mean), host(hier.scale), host(hier.rot), host(hier.opacity), host(hier.sh),
+                            hier.box_min, hier.box_max, hier.parent, hier.child_start, hier.child_count)
+        torch.cuda.synchronize()
+        h3dgs_upload_hierarchy_streamed(self.ctx, h, cache_nodes)
+        self.hier = h
+        return h
 
     def upload(self, hier: DeviceHierarchy):
         h3dgs_upload_hierarchy(self.ctx, hier)
