@@ -39,7 +39,7 @@ T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
 
 // device counter block
 // C_EVALS and C_EVALS_T occupy two words each (64-bit counters)
-// C_NSORTED: splats kept by the depth sort (the visible ones); C_NTSORT: pairs sorted by tile
+// C_NSORTED: a zero word (the bounded-wait probe); C_NTSORT: unused
 // C_NITEMS: 3 words (items, producers, singles).  C_FLAGS: render flags (cleared by every render);
 // C_CUTFLAGS: cut flags (cleared by every cut); the stats report both.
 enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NSORTED = 6,
@@ -58,7 +58,7 @@ struct h3dgs_ctx {
     DBuf cut_mask, cut_bc, cut_tot, cut_lb;
     DBuf s_rec, s_rect, s_key, s_idx, s_key2, s_idx2, s_key3, s_tiles, s_poff;
     DBuf pk0, pv0, pk1, pv1, ranges;
-    DBuf sortw, seg_start;
+    DBuf sortw, seg_start, hists;   // hists: [2][4][256] digit histograms of the depth and tile keys
     DBuf T_final, n_contrib, splat_grad;
     DBuf items, q_prod, q_single, q_cons, queue_sync, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last, sc_D;
     DBuf exposure;   // copy of the last render's exposure affines [n_cams][12]
@@ -307,7 +307,7 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
     DBuf* bufs[] = {&ctx->rec, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot, &ctx->cut_lb,
                     &ctx->s_rec, &ctx->s_rect, &ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2,
                     &ctx->s_key3, &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1,
-                    &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
+                    &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->hists, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
                     &ctx->items, &ctx->q_prod, &ctx->q_single, &ctx->q_cons, &ctx->queue_sync,
                     &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
                     &ctx->sc_last, &ctx->sc_D, &ctx->exposure, &ctx->st_mean, &ctx->st_scale, &ctx->st_rot,
@@ -709,6 +709,10 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
     CK(cudaMemsetAsync(cnt + C_NVISIBLE, 0, sizeof(uint32_t), s), "memset");
     CK(cudaMemsetAsync(cnt + C_EVALS, 0, 4 * sizeof(uint32_t), s), "memset");
     CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(int2) * (size_t)ctx->n_tiles, s), "memset");
+    CK(ensure(ctx->hists, sizeof(uint32_t) * 2 * 4 * 256), "histograms");
+    CK(cudaMemsetAsync(ctx->hists.p, 0, sizeof(uint32_t) * 2 * 4 * 256, s), "memset");
+    uint32_t* depth_hist = P<uint32_t>(ctx->hists);
+    uint32_t* tile_hist = depth_hist + 4 * 256;
     const DevOpts o = dev_opts(*opts);
     SplatBufs sb;
     sb.rec = P<float4>(ctx->s_rec);
@@ -717,6 +721,7 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
     sb.tiles = P<uint32_t>(ctx->s_tiles);
     sb.n_splats = cnt + C_NSPLATS;
     sb.n_visible = cnt + C_NVISIBLE;
+    sb.depth_hist = depth_hist;
     const int grid = ctx->num_sms * 8;
     stage_begin(ctx, H3DGS_STAGE_PREPROCESS);
     CK(launch_preprocess(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, o, cut_ids, cut_t, cut_offsets, capM, sb,
@@ -729,16 +734,17 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
     CK(sort_work(ctx, std::max<int64_t>(capM, ctx->fixed ? capP : 0), &sw), "sort workspace");
     bool in_a = false;
     stage_begin(ctx, H3DGS_STAGE_DEPTH_SORT);
+    // the histograms and the kept count (the visible splats) come from the preprocess kernel
     CK(radix_sort_pairs(P<uint32_t>(ctx->s_key), nullptr, P<uint32_t>(ctx->s_key2), P<uint32_t>(ctx->s_idx2),
                         P<uint32_t>(ctx->s_key3), P<uint32_t>(ctx->s_idx), cnt + C_NSPLATS, capM, 32, true,
-                        cnt + C_NSORTED, sw, &in_a, s),
+                        cnt + C_NVISIBLE, sw, &in_a, s, depth_hist),
        "depth sort");
     stage_end(ctx, H3DGS_STAGE_DEPTH_SORT);
     const uint32_t* order = in_a ? P<uint32_t>(ctx->s_idx2) : P<uint32_t>(ctx->s_idx);
     stage_begin(ctx, H3DGS_STAGE_DUPLICATE);
     const int64_t seg_cap0 = ctx->fixed ? capP / DUP_SEG + 2 : 0;
     if (ctx->fixed) CK(ensure(ctx->seg_start, sizeof(uint32_t) * (size_t)seg_cap0), "pair segments");
-    CK(launch_pair_offsets(P<uint32_t>(ctx->s_tiles), order, cnt + C_NSORTED, capM, P<uint32_t>(ctx->s_poff),
+    CK(launch_pair_offsets(P<uint32_t>(ctx->s_tiles), order, cnt + C_NVISIBLE, capM, P<uint32_t>(ctx->s_poff),
                            P<uint32_t>(ctx->seg_start), seg_cap0, cnt + C_NPAIRS, sw, s),
        "pair offsets");
     if (!ctx->fixed) {
@@ -751,21 +757,22 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
         CK(sort_work(ctx, std::max<int64_t>(capM, capP), &sw), "sort workspace");
         const int64_t seg_cap = capP / DUP_SEG + 2;
         CK(ensure(ctx->seg_start, sizeof(uint32_t) * (size_t)seg_cap), "pair segments");
-        CK(launch_pair_segments(P<uint32_t>(ctx->s_tiles), order, cnt + C_NSORTED, P<uint32_t>(ctx->s_poff),
+        CK(launch_pair_segments(P<uint32_t>(ctx->s_tiles), order, cnt + C_NVISIBLE, P<uint32_t>(ctx->s_poff),
                                 P<uint32_t>(ctx->seg_start), seg_cap, grid, s),
            "pair segments");
     }
-    CK(launch_duplicate(P<DevCam>(ctx->cams), n_cams, cut_offsets, sb, order, cnt + C_NSORTED, P<uint32_t>(ctx->s_poff),
+    int tbits = 1;
+    while (tbits < 32 && ((int64_t)1 << tbits) < ctx->n_tiles) ++tbits;
+    CK(launch_duplicate(P<DevCam>(ctx->cams), n_cams, cut_offsets, sb, order, cnt + C_NVISIBLE, P<uint32_t>(ctx->s_poff),
                         P<uint32_t>(ctx->seg_start), cnt + C_NPAIRS, capP, cnt + C_NPAIRS_KEPT, P<uint32_t>(ctx->pk0),
-                        P<uint32_t>(ctx->pv0), cnt + C_FLAGS, s),
+                        P<uint32_t>(ctx->pv0), tile_hist, (tbits + 7) / 8, cnt + C_FLAGS, s),
        "duplicate");
     stage_end(ctx, H3DGS_STAGE_DUPLICATE);
     stage_begin(ctx, H3DGS_STAGE_TILE_SORT);
-    int tbits = 1;
-    while (tbits < 32 && ((int64_t)1 << tbits) < ctx->n_tiles) ++tbits;
+    // histograms counted by the duplication; every pair is kept
     CK(radix_sort_pairs(P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), P<uint32_t>(ctx->pk1), P<uint32_t>(ctx->pv1),
                         P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), cnt + C_NPAIRS_KEPT, capP, tbits, false,
-                        cnt + C_NTSORT, sw, &in_a, s),
+                        cnt + C_NPAIRS_KEPT, sw, &in_a, s, tile_hist),
        "tile sort");
     stage_end(ctx, H3DGS_STAGE_TILE_SORT);
     const bool in1 = in_a;

@@ -235,6 +235,7 @@ struct SplatBufs {
     float4* rec;           // [cap][4]: {u, v, ca, cb}, {cc, on', op', t}, {r, g, b, K}, {hx, hy, rz, z} (z = view depth)
     uint2* rect;           // [cap]: (x0 | x1 << 16, y0 | y1 << 16)
     uint32_t* depth_key;   // [cap] fp32 depth bits, 0xffffffff when culled
+    uint32_t* depth_hist;  // [4][256] digit histograms of the visible splats' depth keys (zeroed by the caller)
     uint32_t* tiles;       // [cap] tiles touched (0 when culled)
     uint32_t* n_splats;    // [1] min(M_total, cap)
     uint32_t* n_visible;   // [1]
@@ -259,9 +260,13 @@ size_t radix_work_words(int64_t n_cap);
 // reads (kin, vin) (vin NULL: values are the input positions), later passes alternate between (ka, va)
 // and (kb, vb); *result_in_a tells which pair holds the result (kin/vin may alias kb/vb).  With
 // drop_max, keys equal to 0xffffffff are left out; *n_kept (device) receives the number sorted.
+// hist_pre: the digit histograms of every pass ([passes][256], 8-bit digits from the low end) already
+// counted by the producer of the keys, with *n_kept already holding the number of kept keys; NULL:
+// the sort counts them itself.
 cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ka, uint32_t* va, uint32_t* kb,
                              uint32_t* vb, const uint32_t* n_dev, int64_t n_cap, int bits, bool drop_max,
-                             uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s);
+                             uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s,
+                             const uint32_t* hist_pre = nullptr);
 // Pair offsets of the depth order: pair_off[i] = sum of tiles[order[j]] over j < i (i < *n_dev <= n_cap),
 // *total = the sum; seg_start[s] = the entry holding pair s DUP_SEG (for s < seg_cap).
 constexpr int DUP_SEG = 1024;         // pairs per duplication block
@@ -272,10 +277,12 @@ cudaError_t launch_pair_segments(const uint32_t* tiles, const uint32_t* order, c
                                  const uint32_t* pair_off, uint32_t* seg_start, int64_t seg_cap, int grid,
                                  cudaStream_t s);
 // Pairs (tile id, cut position) of the depth-ordered splats; *n_pairs_kept = min(*n_pairs, cap_pairs).
+// hist (nullable, zeroed by the caller): the tile keys' digit histograms for hist_passes (<= 4) passes.
 cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_offsets, const SplatBufs& sb,
                              const uint32_t* order, const uint32_t* n_order, const uint32_t* pair_off,
                              const uint32_t* seg_start, const uint32_t* n_pairs, int64_t cap_pairs,
-                             uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* flags, cudaStream_t s);
+                             uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* hist, int hist_passes,
+                             uint32_t* flags, cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n_tiles, int2* ranges, int grid,
                           cudaStream_t s);
 

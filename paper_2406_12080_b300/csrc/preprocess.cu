@@ -93,6 +93,11 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
                                                          const float* __restrict__ cut_t,
                                                          const int64_t* __restrict__ cut_offsets, int64_t cap,
                                                          SplatBufs sb, uint32_t* __restrict__ flags) {
+    __shared__ uint32_t s_hist[4][256];   // digit histograms of the depth keys, for the depth sort
+    if (sb.depth_hist) {
+        for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+        __syncthreads();
+    }
     const int64_t m_raw = cut_offsets[n_cams];
     const int64_t M = m_raw < cap ? m_raw : cap;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -267,12 +272,24 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
         sb.rec[SPLAT_F4 * m + 2] = make_float4(fmaxf(rgb[0], 0.0f), fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), K);
         sb.rec[SPLAT_F4 * m + 3] = make_float4(hx, hy, rz, z);
         sb.rect[m] = make_uint2((uint32_t)rx0 | ((uint32_t)rx1 << 16), (uint32_t)ry0 | ((uint32_t)ry1 << 16));
-        sb.depth_key[m] = __float_as_uint(z);
+        const uint32_t key = __float_as_uint(z);
+        sb.depth_key[m] = key;
         sb.tiles[m] = (uint32_t)((rx1 - rx0 + 1) * (ry1 - ry0 + 1));
+        if (sb.depth_hist) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 255u], 1u);
+        }
     }
     // block-reduce the visible count
     for (int off = 16; off > 0; off >>= 1) visible += __shfl_down_sync(0xffffffffu, visible, off);
     if ((threadIdx.x & 31) == 0 && visible) atomicAdd(sb.n_visible, visible);
+    if (sb.depth_hist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+            const uint32_t c = (&s_hist[0][0])[i];
+            if (c) atomicAdd(sb.depth_hist + i, c);
+        }
+    }
 }
 
 cudaError_t launch_preprocess(const DevHier& h, const DevCam* cams, int n_cams, const DevOpts& o,

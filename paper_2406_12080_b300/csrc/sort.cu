@@ -267,9 +267,10 @@ size_t radix_work_words(int64_t n_cap) {
 
 cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ka, uint32_t* va, uint32_t* kb,
                              uint32_t* vb, const uint32_t* n_dev, int64_t n_cap, int bits, bool drop_max,
-                             uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s) {
+                             uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s,
+                             const uint32_t* hist_pre) {
     *result_in_a = false;
-    if (n_cap <= 0) return cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s);
+    if (n_cap <= 0) return hist_pre ? cudaSuccess : cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s);
     if (n_cap > 0xffffffffLL || bits < 1 || bits > 32) return cudaErrorInvalidValue;
     const int passes = (bits + 7) / 8;
     // small tiles (a shorter serial ranking chain per tile) while every tile of a pass fits one wave of
@@ -283,12 +284,17 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
     unsigned long long* status = reinterpret_cast<unsigned long long*>(w.work + RADIX_HEADER_WORDS);
     cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * RADIX_HEADER_WORDS +
                                                    sizeof(unsigned long long) * (size_t)passes * tiles * 256, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const int64_t per_block = (int64_t)OS_THREADS * HG_IPT;
-    const unsigned hg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_cap + per_block - 1) / per_block,
-                                                                         16 * (int64_t)w.num_sms));
-    radix_histogram_kernel<<<hg, OS_THREADS, 0, s>>>(kin, n_dev, passes, drop_max ? 1 : 0, hist, n_kept);
+    if (hist_pre) {
+        hist = const_cast<uint32_t*>(hist_pre);   // counted by the producer of the keys, with *n_kept
+    } else {
+        e = cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s);
+        if (e != cudaSuccess) return e;
+        const int64_t per_block = (int64_t)OS_THREADS * HG_IPT;
+        const unsigned hg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_cap + per_block - 1) / per_block,
+                                                                             16 * (int64_t)w.num_sms));
+        radix_histogram_kernel<<<hg, OS_THREADS, 0, s>>>(kin, n_dev, passes, drop_max ? 1 : 0, hist, n_kept);
+    }
     // pass p reads (kin, vin) for p = 0, then alternates (ka, va) -> (kb, vb) -> (ka, va) ...
     for (int p = 0; p < passes; ++p) {
         const bool to_a = (p % 2) == 0;
@@ -410,9 +416,11 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const DevCam* __restrict
                                                         const uint32_t* __restrict__ n_pairs, int64_t cap_pairs,
                                                         uint32_t* __restrict__ n_pairs_kept,
                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                        uint32_t* __restrict__ hist, int hist_passes,
                                                         uint32_t* __restrict__ flags) {
     __shared__ uint32_t s_off[DUP_SEG + 1], s_m[DUP_SEG + 1], s_xy[DUP_SEG + 1], s_wtx[DUP_SEG + 1],
         s_tb[DUP_SEG + 1];
+    __shared__ uint32_t s_hist[4][256];   // digit histograms of the tile keys for the tile sort
     const uint32_t P = *n_pairs;
     const uint32_t Pk = (int64_t)P > cap_pairs ? (uint32_t)cap_pairs : P;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -426,6 +434,8 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const DevCam* __restrict
     const uint32_t e0 = seg_start[blockIdx.x];
     const uint32_t e1 = p1 < Pk ? seg_start[blockIdx.x + 1] : V - 1;
     if (e0 >= V || e1 < e0) return;   // only after a failed scan (flagged)
+    if (hist)
+        for (int i = threadIdx.x; i < hist_passes * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     const int ne = (int)min(min(e1 - e0 + 1, (uint32_t)DUP_SEG + 1), V - e0);
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
         const uint32_t i = e0 + e;
@@ -448,18 +458,31 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const DevCam* __restrict
         const uint32_t k = (uint32_t)(p - s_off[lo]);
         const uint32_t wtx = s_wtx[lo], xy = s_xy[lo];
         const uint32_t w = wtx & 0xffffu, ty = k / w, tx = k - ty * w;
-        keys[p] = s_tb[lo] + ((xy >> 16) + ty) * (wtx >> 16) + (xy & 0xffffu) + tx;
+        const uint32_t key = s_tb[lo] + ((xy >> 16) + ty) * (wtx >> 16) + (xy & 0xffffu) + tx;
+        keys[p] = key;
         vals[p] = s_m[lo];
+        if (hist)
+            for (int q = 0; q < hist_passes; ++q) atomicAdd(&s_hist[q][(key >> (8 * q)) & 255u], 1u);
+    }
+    if (hist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < hist_passes * 256; i += blockDim.x) {
+            const uint32_t c = (&s_hist[0][0])[i];
+            if (c) atomicAdd(hist + i, c);
+        }
     }
 }
 
 cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_offsets, const SplatBufs& sb,
                              const uint32_t* order, const uint32_t* n_order, const uint32_t* pair_off,
                              const uint32_t* seg_start, const uint32_t* n_pairs, int64_t cap_pairs,
-                             uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* flags, cudaStream_t s) {
+                             uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* hist, int hist_passes,
+                             uint32_t* flags, cudaStream_t s) {
     const int64_t blocks = std::max<int64_t>(1, (cap_pairs + DUP_SEG - 1) / DUP_SEG);
+    if (hist_passes < 0 || hist_passes > 4) return cudaErrorInvalidValue;
     duplicate_kernel<<<(unsigned)blocks, 256, 0, s>>>(cams, n_cams, cut_offsets, sb, order, n_order, pair_off,
-                                                      seg_start, n_pairs, cap_pairs, n_pairs_kept, keys, vals, flags);
+                                                      seg_start, n_pairs, cap_pairs, n_pairs_kept, keys, vals, hist,
+                                                      hist_passes, flags);
     return cudaGetLastError();
 }
 
