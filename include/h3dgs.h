@@ -389,7 +389,8 @@ h3dgs_status h3dgs_debug_tile_lists(h3dgs_ctx* ctx, int32_t cam, int32_t* ranges
 h3dgs_status h3dgs_debug_splats(h3dgs_ctx* ctx, float* rec, int32_t* rect, float* rgb, int64_t m);
 
 /* Copy the last render's per-pixel final transmittance and contributor count (the list position
- * after the last contributing splat) to HOST memory for all cameras (synchronous). */
+ * after the last contributing splat) to HOST memory for all cameras (synchronous).  Only a render
+ * with save_for_backward = 1 keeps this state. */
 /* Test hook for the failure path of the library's bounded waits between thread blocks (the
  * radix-sort and scan look-backs, the blend queue): runs one wait, with the same loop, on a device
  * word that nothing sets, giving up after `polls` polls (1 .. 2^20; each poll sleeps about 0.1 us

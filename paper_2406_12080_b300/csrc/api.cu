@@ -806,6 +806,10 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
         ctx->opts = o;
         ctx->pairs_in_1 = in1;
         BlendArgs ba = blend_args(ctx, n_cams, images, depth);
+        if (!save_for_backward) {   // the adjoint's per-pixel state is not kept
+            ba.T_final = nullptr;
+            ba.n_contrib = nullptr;
+        }
         if (ctx->prof) {
             ba.ev_queue = ctx->ev + 2 * H3DGS_STAGE_BLEND_QUEUE;
             ctx->ev_used[H3DGS_STAGE_BLEND_QUEUE] = true;

@@ -229,8 +229,8 @@ __device__ __forceinline__ void write_pixel(float* img, int64_t plane, float T, 
 // contributors, no colour; a pixel is finished once T < t_min, after which nothing it could add
 // matters).  Branch-free per entry: the alpha of every live pixel is computed and applied through
 // selects; the paired fp32 instructions evaluate both pixels at once.  DEPTH: the expected depth Dp
-// is accumulated as a fourth channel.
-template <int TW, int TH, bool MAIN, bool COUNT, bool DEPTH>
+// is accumulated as a fourth channel.  SAVE: track the last contributor (kept for the adjoint).
+template <int TW, int TH, bool MAIN, bool COUNT, bool DEPTH, bool SAVE>
 __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const uint32_t* __restrict__ list,
                                             const float4* __restrict__ splat, int begin, int end, int list0,
                                             float clampv, float afloor, float tmin, float4* s_a, float4* s_b,
@@ -279,8 +279,10 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
                         C2 = __ffma2_rn(make_float2(c.z, c.z), w, C2);
                         if (DEPTH) Dp = __ffma2_rn(make_float2(s_d[j], s_d[j]), w, Dp);
                         T = make_float2(app0 ? Tn.x : T.x, app1 ? Tn.y : T.y);
-                        const int pos = b0 + j + 1 - list0;
-                        last = make_int2(app0 ? pos : last.x, app1 ? pos : last.y);
+                        if (SAVE) {
+                            const int pos = b0 + j + 1 - list0;
+                            last = make_int2(app0 ? pos : last.x, app1 ? pos : last.y);
+                        }
                     } else {
                         T = make_float2(live0 ? Tn.x : T.x, live1 ? Tn.y : T.y);
                         done0 = done0 || (live0 && Tn.x < tmin);
@@ -298,8 +300,9 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
 // producers of its tile have published their products (per-tile counter, bounded wait), which were
 // all taken before it.  TW x TH / 2 threads, two pixels each.  COUNT: count the (pixel, splat)
 // evaluations into n_evals (profiling only; the count costs instructions in the innermost loop).
-// DEPTH: also the expected depth (depth != NULL).
-template <int TW, int TH, bool COUNT, bool DEPTH>
+// DEPTH: also the expected depth (depth != NULL).  SAVE: also the per-pixel state the adjoint reads
+// (final transmittance, contributor count; T_final and n_contrib != NULL).
+template <int TW, int TH, bool COUNT, bool DEPTH, bool SAVE>
 __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
                                                                   const int2* __restrict__ ranges,
                                                                   const uint32_t* __restrict__ list,
@@ -361,12 +364,13 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     unsigned int evals = 0;
     bool done0 = !g.in0 || T.x < o.t_min, done1 = !g.in1 || T.y < o.t_min;
     if (main_pass)
-        blend_walk2<TW, TH, true, COUNT, DEPTH>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor, o.t_min,
-                                                s_a, s_b, s_c, s_m, s_d, T, C0, C1, C2, Dp, last, done0, done1, evals);
+        blend_walk2<TW, TH, true, COUNT, DEPTH, SAVE>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
+                                                      o.t_min, s_a, s_b, s_c, s_m, s_d, T, C0, C1, C2, Dp, last, done0,
+                                                      done1, evals);
     else
-        blend_walk2<TW, TH, false, COUNT, false>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
-                                                 o.t_min, s_a, s_b, s_c, s_m, s_d, T, C0, C1, C2, Dp, last, done0,
-                                                 done1, evals);
+        blend_walk2<TW, TH, false, COUNT, false, false>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
+                                                        o.t_min, s_a, s_b, s_c, s_m, s_d, T, C0, C1, C2, Dp, last,
+                                                        done0, done1, evals);
     if (COUNT) {
         for (int off = 16; off > 0; off >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, off);
         if (lane == 0) atomicAdd(&s_evals[main_pass ? 0 : 1], evals);
@@ -381,8 +385,10 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
             sc.C[3 * s1 + 0] = C0.y; sc.C[3 * s1 + 1] = C1.y; sc.C[3 * s1 + 2] = C2.y;
             sc.Tend[s0] = T.x;
             sc.Tend[s1] = T.y;
-            sc.last[s0] = last.x;
-            sc.last[s1] = last.y;
+            if (SAVE) {
+                sc.last[s0] = last.x;
+                sc.last[s1] = last.y;
+            }
             if (DEPTH) {
                 sc.D[s0] = Dp.x;
                 sc.D[s1] = Dp.y;
@@ -404,8 +410,10 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
         sc.C[3 * s1 + 0] = C0.y; sc.C[3 * s1 + 1] = C1.y; sc.C[3 * s1 + 2] = C2.y;
         sc.Tend[s0] = T.x;
         sc.Tend[s1] = T.y;
-        sc.last[s0] = last.x;
-        sc.last[s1] = last.y;
+        if (SAVE) {
+            sc.last[s0] = last.x;
+            sc.last[s1] = last.y;
+        }
         if (DEPTH) {
             sc.D[s0] = Dp.x;
             sc.D[s1] = Dp.y;
@@ -419,15 +427,19 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
         const int64_t pix = cam.pix_base + (int64_t)g.py_i0 * cam.width + g.px_i;
         write_pixel(images + 3 * cam.pix_base + (int64_t)g.py_i0 * cam.width + g.px_i, plane, T.x, C0.x, C1.x, C2.x, o, E);
         if (DEPTH) depth[pix] = Dp.x;
-        if (T_final) T_final[pix] = T.x;
-        if (n_contrib) n_contrib[pix] = last.x < 0 ? 0 : last.x;
+        if (SAVE) {
+            T_final[pix] = T.x;
+            n_contrib[pix] = last.x < 0 ? 0 : last.x;
+        }
     }
     if (g.in1) {
         const int64_t pix = cam.pix_base + (int64_t)g.py_i1 * cam.width + g.px_i;
         write_pixel(images + 3 * cam.pix_base + (int64_t)g.py_i1 * cam.width + g.px_i, plane, T.y, C0.y, C1.y, C2.y, o, E);
         if (DEPTH) depth[pix] = Dp.y;
-        if (T_final) T_final[pix] = T.y;
-        if (n_contrib) n_contrib[pix] = last.y < 0 ? 0 : last.y;
+        if (SAVE) {
+            T_final[pix] = T.y;
+            n_contrib[pix] = last.y < 0 ? 0 : last.y;
+        }
     }
 }
 
@@ -468,7 +480,7 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
             C2 += sc.C[3 * slot + 2];
             if (depth) D += sc.D[slot];
             T = sc.Tend[slot];
-            if (sc.last[slot] >= 0) last = sc.last[slot];
+            if (n_contrib && sc.last[slot] >= 0) last = sc.last[slot];
         }
         if (c + 1 < nch) Tin = fmul(Tin, sc.Tc[slot]);
     }
@@ -506,8 +518,8 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     // queue length 2 X + Y <= 2 item_cap - n_tiles
     const unsigned gq = (unsigned)std::max<int64_t>(1, 2 * a.item_cap - a.n_tiles);
     const unsigned tg = (unsigned)a.n_tiles;
-#define QUEUE(TWV, THV, CNT, DEP)                                                                                     \
-    blend_queue_kernel<TWV, THV, CNT, DEP><<<gq, TWV * THV / 2, 0, s>>>(                                              \
+#define QUEUE(TWV, THV, CNT, DEP, SAV)                                                                                \
+    blend_queue_kernel<TWV, THV, CNT, DEP, SAV><<<gq, TWV * THV / 2, 0, s>>>(                                         \
         a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.items, a.q_prod, a.q_single, a.q_cons, a.n_items,         \
         a.tile_item0, a.tile_nch, a.chunk, sc, a.queue_sync, a.queue_sync + 1, a.images, a.depth, a.exposure,         \
         a.T_final, a.n_contrib, a.n_evals, a.flags)
@@ -515,9 +527,11 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     do {                                                                                                              \
         if (a.ev_queue) cudaEventRecord(a.ev_queue[0], s);                                                            \
         if (a.depth) {                                                                                                \
-            if (a.n_evals) QUEUE(TWV, THV, true, true); else QUEUE(TWV, THV, false, true);                            \
+            if (save) QUEUE(TWV, THV, false, true, true); else QUEUE(TWV, THV, false, true, false);                   \
+        } else if (a.n_evals) {                                                                                       \
+            if (save) QUEUE(TWV, THV, true, false, true); else QUEUE(TWV, THV, true, false, false);                   \
         } else {                                                                                                      \
-            if (a.n_evals) QUEUE(TWV, THV, true, false); else QUEUE(TWV, THV, false, false);                          \
+            if (save) QUEUE(TWV, THV, false, false, true); else QUEUE(TWV, THV, false, false, false);                 \
         }                                                                                                             \
         if (a.ev_queue) cudaEventRecord(a.ev_queue[1], s);                                                            \
         blend_combine_kernel<TWV, THV><<<tg, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.n_tiles, a.tile_item0,       \
@@ -525,6 +539,8 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
                                                                 a.T_final, a.n_contrib);                              \
     } while (0)
     const DevOpts& o = a.o;
+    const bool save = a.T_final && a.n_contrib;   // per-pixel state for the adjoint (evaluations are not
+                                                  // counted together with the depth output)
     if (o.tile_w == 16 && o.tile_h == 16) BL(16, 16);
     else if (o.tile_w == 8 && o.tile_h == 8) BL(8, 8);
     else if (o.tile_w == 32 && o.tile_h == 8) BL(32, 8);
