@@ -44,7 +44,7 @@ FLOPS_PER_EVAL = 22
 FLOPS_PER_EVAL_T = 10
 # DRAM bytes (read + write) of one launch of the blend's main kernel at the 1080p corridor frame
 # (16x16 tiles, chunk 512), from an ncu capture of the current kernel; None once the kernel changes
-BLEND_TRAFFIC_BYTES = 31.163904e6 + 8.637696e6
+BLEND_TRAFFIC_BYTES = 28.638464e6 + 2.040320e6
 
 
 def parse():
