@@ -371,6 +371,12 @@ h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out);
  * evaluation counters of h3dgs_stats (which slow the blend down: time with level 1). */
 h3dgs_status h3dgs_set_profiling(h3dgs_ctx* ctx, int32_t enable);
 
+/* Calibration of the roofline denominators of the arithmetic-bound kernels on this GPU: chain
+ * kernels filling every SM measure the fp32 fused multiply-add rate of the paired instruction the
+ * blend uses (*fp32_tflops, 2 flops per FMA) and the exp2 approximation rate (*ex2_gops, results per
+ * second / 1e9).  Synchronous, about 20 ms.  Errors: INVALID_ARG (NULL outputs), CUDA. */
+h3dgs_status h3dgs_measure_peaks(h3dgs_ctx* ctx, float* fp32_tflops, float* ex2_gops);
+
 /* Stage times (ms) of the last profiled calls, indexed by h3dgs_stage; ms must hold
  * H3DGS_STAGE_COUNT floats (host).  Synchronises the stream.  Stages not run report 0. */
 h3dgs_status h3dgs_get_stage_times(h3dgs_ctx* ctx, float* ms);

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libh3dgs.so")
 BUILD_DIR = os.path.join(PKG, "_build")
 
-SOURCES = ["api.cu", "cut.cu", "preprocess.cu", "sort.cu", "blend.cu", "backward.cu", "builder.cu", "cut_noalloc.cu", "compact.cu", "stream.cu"]
+SOURCES = ["api.cu", "cut.cu", "preprocess.cu", "sort.cu", "blend.cu", "backward.cu", "builder.cu", "cut_noalloc.cu", "compact.cu", "stream.cu", "calib.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -860,6 +860,15 @@ h3dgs_status h3dgs_render_backward_ex(h3dgs_ctx* ctx, const float* dL, const flo
     return H3DGS_OK;
 }
 
+h3dgs_status h3dgs_measure_peaks(h3dgs_ctx* ctx, float* fp32_tflops, float* ex2_gops) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!fp32_tflops || !ex2_gops) return fail(ctx, H3DGS_ERR_INVALID_ARG, "measure_peaks: NULL output");
+    CK(cudaSetDevice(ctx->device), "set device");
+    CK(measure_peaks(ctx->num_sms, fp32_tflops, ex2_gops, ctx->stream), "measure peaks");
+    return H3DGS_OK;
+}
+
 h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out) {
     if (!ctx || !out) return H3DGS_ERR_INVALID_ARG;
     ctx->err.clear();

@@ -378,6 +378,9 @@ cudaError_t stream_update(const StreamState& st, const int32_t* parent, int n_ca
                           cudaStream_t s);
 cudaError_t stream_cleanup(const StreamState& st, int32_t frame, int32_t max_age, int num_sms, cudaStream_t s);
 
+// calib.cu: FP32 (paired FFMA) and exp2 (MUFU) rates of the running GPU, from chain kernels
+cudaError_t measure_peaks(int num_sms, float* fp32_tflops, float* ex2_gops, cudaStream_t s);
+
 // backward.cu
 struct GradBufs {
     float* mean; float* scale; float* rot; float* opacity; float* sh;

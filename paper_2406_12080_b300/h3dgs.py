@@ -103,6 +103,7 @@ def lib():
                                       vp, vp, i32]),
             "h3dgs_render_backward_ex": (i32, [vp, vp, vp, C.POINTER(h3dgs_grads), i32]),
             "h3dgs_get_stats": (i32, [vp, C.POINTER(h3dgs_stats)]),
+            "h3dgs_measure_peaks": (i32, [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
             "h3dgs_set_profiling": (i32, [vp, i32]),
             "h3dgs_debug_wait_timeout": (i32, [vp, i32]),
             "h3dgs_get_stage_times": (i32, [vp, vp]),
@@ -317,6 +318,13 @@ def h3dgs_get_stats(ctx) -> dict:
     s = h3dgs_stats()
     _check(ctx, lib().h3dgs_get_stats(ctx, C.byref(s)))
     return {k: getattr(s, k) for k, _ in h3dgs_stats._fields_}
+
+
+def h3dgs_measure_peaks(ctx) -> dict:
+    """Measured fp32 (paired FFMA) TFLOP/s and exp2 Gop/s of this GPU."""
+    f, x = C.c_float(0), C.c_float(0)
+    _check(ctx, lib().h3dgs_measure_peaks(ctx, C.byref(f), C.byref(x)))
+    return {"fp32_tflops": f.value, "ex2_gops": x.value}
 
 
 def h3dgs_debug_wait_timeout(ctx, polls: int):
