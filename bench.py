@@ -43,8 +43,8 @@ REF_BUDGET_S = 120.0
 FLOPS_PER_EVAL = 22
 FLOPS_PER_EVAL_T = 10
 # DRAM bytes (read + write) of one launch of the blend's main kernel at the 1080p corridor frame
-# (16x16 tiles, chunk 512), from an ncu capture of the current kernel; None once the kernel changes
-BLEND_TRAFFIC_BYTES = 28.638464e6 + 2.040320e6
+# (16x16 tiles, chunk 384), from an ncu capture of the current kernel; None once the kernel changes
+BLEND_TRAFFIC_BYTES = 28.804352e6 + 2.989568e6
 
 
 def parse():
@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--tau", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--chunk", type=int, default=512, help="blend chunk (list entries per CTA)")
+    ap.add_argument("--chunk", type=int, default=384, help="blend chunk (list entries per CTA)")
     ap.add_argument("--tile", default="16x16", help="screen tile WxH")
     ap.add_argument("--batch-views", type=int, default=32, help="cameras of the batched multi-view section (0: skip)")
     ap.add_argument("--opt-leaves", type=int, default=2_000_000,
@@ -435,7 +435,7 @@ def run_ours(args, rank, world, local):
     achieved = flops / (queue_ms * 1e-3) / 1e12 if queue_ms > 0 else None
     roofline = {"kernel": "blend_queue_kernel<16,16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": (achieved / fp32_peak_tflops) if achieved else None,
-                "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk == 512) else None,
+                "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk == 384) else None,
                 "kernel_ms": queue_ms,
                 "peak_note": "148 SMs x 128 FP32 lanes x 2 (FFMA) x max SM clock from MEASURED_PEAKS.json",
                 "work_note": f"{FLOPS_PER_EVAL} FP32 flops per main-pass (pixel, splat) evaluation x {n_evals}; the "
