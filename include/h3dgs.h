@@ -99,7 +99,7 @@ typedef struct {
     int32_t interpolate;     /* 1: parent/child interpolation (Sec. 4.2); 0: render the cut as is */
     float bg[3];             /* background colour                                              */
     int32_t blend_chunk;     /* tile lists longer than this many entries are blended in chunks of
-                                this size by separate CTAs (64 .. 65536, default 512); the image
+                                this size by separate CTAs (64 .. 65536, default 384); the image
                                 does not depend on it beyond fp32 reassociation of T            */
 } h3dgs_render_opts;
 

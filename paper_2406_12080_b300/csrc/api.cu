@@ -194,7 +194,7 @@ DevOpts dev_opts(const h3dgs_render_opts& o) {
     d.tile_w = o.tile_w; d.tile_h = o.tile_h; d.lowpass = o.lowpass; d.alpha_clamp = o.alpha_clamp;
     d.alpha_floor = o.alpha_floor; d.t_min = o.t_min; d.aa_compensate = o.aa_compensate;
     d.interpolate = o.interpolate;
-    d.chunk = o.blend_chunk > 0 ? o.blend_chunk : 512;
+    d.chunk = o.blend_chunk > 0 ? o.blend_chunk : 384;
     for (int i = 0; i < 3; ++i) d.bg[i] = o.bg[i];
     return d;
 }
@@ -334,7 +334,7 @@ void h3dgs_default_opts(h3dgs_render_opts* o) {
     o->aa_compensate = 1;
     o->interpolate = 1;
     o->bg[0] = o->bg[1] = o->bg[2] = 0.0f;
-    o->blend_chunk = 512;
+    o->blend_chunk = 384;
 }
 
 h3dgs_status h3dgs_reserve(h3dgs_ctx* ctx, int64_t max_splats, int64_t max_pairs) {
@@ -601,10 +601,13 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
     if (!cut_offsets || (capacity > 0 && !cut_ids) || capacity < 0)
         return fail(ctx, H3DGS_ERR_INVALID_ARG, "select_cut: NULL output or negative capacity");
     CK(cudaSetDevice(ctx->device), "set device");
-    st = setup_cameras(ctx, cams, n_cams, 16, 16);
-    if (st != H3DGS_OK) return st;
+    if (n_cams > 1) {   // the one-camera pass derives its camera values itself (no set-up launch)
+        st = setup_cameras(ctx, cams, n_cams, 16, 16);
+        if (st != H3DGS_OK) return st;
+    }
     const int64_t N = ctx->hier.n_nodes;
     CutWork w;
+    w.cam0 = cams[0];
     const int64_t max_blocks = (int64_t)ctx->num_sms * 4;
     w.chunk = ((N + max_blocks - 1) / max_blocks + 255) / 256 * 256;
     w.blocks = (int)((N + w.chunk - 1) / w.chunk);

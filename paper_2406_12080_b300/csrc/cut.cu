@@ -223,7 +223,7 @@ constexpr int CS_GRP = 2;   // nodes whose loads are in flight together (2 measu
 constexpr int CS_TILE = CUT_BLOCK * CS_IPT;
 
 __global__ void __launch_bounds__(CUT_BLOCK) cut_single_kernel(const float4* __restrict__ rec, int64_t n,
-                                                               const DevCam* __restrict__ cams, int64_t capacity,
+                                                               const h3dgs_camera raw, int64_t capacity,
                                                                int32_t* __restrict__ cut_ids, float* __restrict__ cut_t,
                                                                int64_t* __restrict__ cut_offsets,
                                                                int64_t* __restrict__ cam_totals,
@@ -234,7 +234,10 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_single_kernel(const float4* __r
     const uint32_t b = lb_ticket(lb, &s_ticket);
     const int64_t base = (int64_t)b * CS_TILE;
     if (base >= n) return;
-    const DevCam cam = cams[0];
+    DevCam cam;   // only the centre, f and tau are used; derived as the set-up kernel does
+    camera_centre(raw, cam.c);
+    cam.f = fmaxf(raw.fx, raw.fy);
+    cam.tau = raw.tau;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t word[CS_IPT];
     float tw[CS_IPT];
@@ -308,7 +311,7 @@ cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const C
         cudaError_t e = cudaMemsetAsync(w.lb_work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)blocks), s);
         if (e != cudaSuccess) return e;
         Lookback lb{reinterpret_cast<unsigned long long*>(w.lb_work + LB_HEADER_WORDS), w.lb_work, flags};
-        cut_single_kernel<<<(unsigned)blocks, CUT_BLOCK, 0, s>>>(h.rec, h.n, cams, capacity, cut_ids, cut_t, cut_offsets,
+        cut_single_kernel<<<(unsigned)blocks, CUT_BLOCK, 0, s>>>(h.rec, h.n, w.cam0, capacity, cut_ids, cut_t, cut_offsets,
                                                                  w.cam_totals, flags, lb);
         return cudaGetLastError();
     }

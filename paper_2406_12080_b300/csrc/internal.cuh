@@ -225,6 +225,7 @@ struct CutWork {
     int64_t words;           // mask words per camera
     uint32_t* lb_work;       // single-camera pass: look-back workspace (NULL: use the three-pass path)
     int64_t lb_words;
+    h3dgs_camera cam0;       // single-camera pass: the raw camera (its derived values are computed in the kernel)
 };
 cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const CutWork& w, int32_t* cut_ids,
                        float* cut_t, int64_t* cut_offsets, int64_t capacity, uint32_t* flags, cudaStream_t s);
