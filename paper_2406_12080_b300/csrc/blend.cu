@@ -132,7 +132,7 @@ __device__ __forceinline__ TileGeom2<TW, TH> tile_geom2(const DevCam* __restrict
 // Per tile the scan carries X = nch - 1 (split tiles) and Y = [nch == 1] packed in one word; the item
 // offset is t + prefix(X), the producer and consumer offsets prefix(X), the single offset prefix(Y).
 constexpr int PL_THREADS = 256;
-constexpr int PL_IPT = 4;
+constexpr int PL_IPT = 1;   // one tile per thread: 32 blocks at 1080p (4 tiles per thread left 8 blocks)
 constexpr int PL_TILE = PL_THREADS * PL_IPT;
 
 __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __restrict__ ranges, int64_t n_tiles,
@@ -472,17 +472,27 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
     const int64_t i0 = tile_item0[tile];
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f, T = 1.0f, Tin = 1.0f;
     int last = 0;
+    // every chunk's scratch is read whether or not it is used, so the loads of successive chunks do
+    // not wait on each other through the running transmittance
+#pragma unroll 4
     for (int c = 0; c < nch; ++c) {
         const int64_t slot = (i0 + c) * NT + threadIdx.x;
-        if (!(Tin < o.t_min)) {
-            C0 += sc.C[3 * slot + 0];
-            C1 += sc.C[3 * slot + 1];
-            C2 += sc.C[3 * slot + 2];
-            if (depth) D += sc.D[slot];
-            T = sc.Tend[slot];
-            if (n_contrib && sc.last[slot] >= 0) last = sc.last[slot];
+        const float c0 = sc.C[3 * slot + 0], c1 = sc.C[3 * slot + 1], c2 = sc.C[3 * slot + 2];
+        const float te = sc.Tend[slot], tc = sc.Tc[slot];   // Tc of the last chunk is not used
+        const bool run = !(Tin < o.t_min);
+        C0 += run ? c0 : 0.0f;
+        C1 += run ? c1 : 0.0f;
+        C2 += run ? c2 : 0.0f;
+        T = run ? te : T;
+        if (depth) {
+            const float dd = sc.D[slot];
+            D += run ? dd : 0.0f;
         }
-        if (c + 1 < nch) Tin = fmul(Tin, sc.Tc[slot]);
+        if (n_contrib) {
+            const int32_t l = sc.last[slot];
+            if (run && l >= 0) last = l;
+        }
+        if (c + 1 < nch) Tin = fmul(Tin, tc);
     }
     const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
     const int64_t plane = (int64_t)cam.width * cam.height;
