@@ -174,13 +174,13 @@ def cpu_oracle_time(scene, n_frames: int, budget_s: float = 25.0):
 def launches_per_frame(n_tiles: int) -> int:
     """Kernels of one frame, from the pipeline's launch sites (used when the graph cannot be read)."""
     tile_bits = max(1, int(np.ceil(np.log2(max(n_tiles, 2)))))
-    cut = 1 + 4                       # camera set-up; mark, block scan, camera scan, ordered write
-    render = (1 + 1                   # camera set-up, preprocess
-              + 1 + 4                 # depth sort: histograms, 4 onesweep passes
-              + 3 + 1                 # pair-offset scan, duplicate
-              + 1 + (tile_bits + 7) // 8   # tile sort: histograms, passes
+    cut = 1                           # one-camera cut (single pass, camera derived in the kernel)
+    render = (1 + 1                   # camera set-up, preprocess (also counts the depth-key digits)
+              + 4                     # depth sort: 4 onesweep passes
+              + 1 + 1                 # pair-offset scan, duplicate (also counts the tile-key digits)
+              + (tile_bits + 7) // 8  # tile sort passes
               + 1                     # ranges
-              + 4)                    # blend: plan, transmittance pass, main pass, combine
+              + 3)                    # blend: plan, queue, combine
     return cut + render
 
 
@@ -452,13 +452,13 @@ def run_ours(args, rank, world, local):
     M, V, Pn = int(st["n_cut"]), int(st["n_visible"]), int(st["n_pairs"])
     # algorithmic bytes: cut reads 32 B of records per node (+ the parent's, half of them cached) and writes
     # 8 B per cut entry; preprocess reads the node and parent attributes (236 + 16 B) and writes 64 B of
-    # record + 16 B of key/count/rect per entry; each radix pass reads and writes 8 B per key/value pair
-    # (+ 4 B read by the histograms); duplicate reads 16 B per visible splat and writes 8 B per pair
+    # record + 16 B of key/count/rect per entry; each radix pass reads and writes 8 B per key/value pair;
+    # duplicate reads 16 B per visible splat and writes 8 B per pair
     algo_bytes = {"cut": N * 32 + N * 32 // 2 + M * 8,
                   "preprocess": M * (236 + 16) + M * 80,
-                  "depth_sort": M * 4 + 4 * V * 16,
+                  "depth_sort": 4 * V * 16,
                   "duplicate": V * 16 + Pn * 8,
-                  "tile_sort": Pn * 4 + 2 * Pn * 16}
+                  "tile_sort": 2 * Pn * 16}
     for k, b in algo_bytes.items():
         if fwd_stages.get(k):
             stage_bw[k] = {"GB/s": b / (fwd_stages[k] * 1e-3) / 1e9, "frac_hbm": b / (fwd_stages[k] * 1e-3) / 1e9 / hbm}
