@@ -852,7 +852,6 @@ def run_city(args, rank, world, local):
         "build": {"host_generation_s": t_gen, "device_build_s": t_build},
         "clocks": clk.summary(),
     }
-    out["quality"] = quality
     if batched is not None:
         out["batched"] = batched
     return out if rank == 0 else None
