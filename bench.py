@@ -462,6 +462,14 @@ def run_ours(args, rank, world, local):
     for k, b in algo_bytes.items():
         if fwd_stages.get(k):
             stage_bw[k] = {"GB/s": b / (fwd_stages[k] * 1e-3) / 1e9, "frac_hbm": b / (fwd_stages[k] * 1e-3) / 1e9 / hbm}
+    # frame-level roofline: the time every stage would take at its binding peak (HBM stages at the
+    # measured copy bandwidth, the blend at the unit-count FP32 peak), summed, over the frame time
+    ideal_ms = sum(b / (hbm * 1e9) * 1e3 for b in algo_bytes.values())
+    ideal_ms += FLOPS_PER_EVAL * n_evals / (fp32_peak_tflops * 1e12) * 1e3
+    frame_ms = total_ms / args.steps
+    frame_roofline = {"frac": ideal_ms / frame_ms, "ideal_ms": ideal_ms, "frame_ms": frame_ms,
+                      "note": "sum over cut, preprocess, sorts, duplication (algorithmic bytes at the measured HBM "
+                              "copy rate) and blend (main-pass flops at the FP32 peak), divided by the frame time"}
     clocks = clk.summary()
     out = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -481,6 +489,7 @@ def run_ours(args, rank, world, local):
                 "note": "C-ABI calls from Python; camera struct in, image read back to pinned host memory"},
         "stages_ms": {**fwd_stages, **bwd_stages}, "stage_bandwidth": stage_bw,
         "roofline": roofline,
+        "frame_roofline": frame_roofline,
         "tile": args.tile,
         "gpu_launches": args.steps * launches,
         "gpu_launches_per_step": launches, "gpu_launches_source": launch_src,

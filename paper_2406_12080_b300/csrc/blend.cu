@@ -234,12 +234,27 @@ template <int TW, int TH, bool MAIN, bool COUNT, bool DEPTH, bool SAVE>
 __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const uint32_t* __restrict__ list,
                                             const float4* __restrict__ splat, int begin, int end, int list0,
                                             float clampv, float afloor, float tmin, float4* s_a, float4* s_b,
-                                            float4* s_c, uint32_t* s_m, float* s_d, float2& T, float2& C0,
+                                            float4* s_c, uint32_t* s_m, float* s_d, float4* s_box, float2& T, float2& C0,
                                             float2& C1, float2& C2, float2& Dp, int2& last, bool& done0, bool& done1,
                                             unsigned int& evals) {
-    constexpr int NT2 = TW * TH / 2;
+    constexpr int NT2 = TW * TH / 2, NW = NT2 / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int b0 = begin; b0 < end; b0 += NT2) {
+        // the warp's live pixels' bounding box (pixel centres): entries that cannot reach alpha_floor
+        // inside it are skipped by the warp mask (its stopped pixels no longer matter)
+        {
+            const bool any_live = !(done0 && done1);
+            const int ix = g.px_i;
+            const int iy_lo = !done0 ? g.py_i0 : g.py_i1, iy_hi = !done1 ? g.py_i1 : g.py_i0;
+            const int xmin = __reduce_min_sync(0xffffffffu, any_live ? ix : 0x7fffffff);
+            const int xmax = __reduce_max_sync(0xffffffffu, any_live ? ix : -1);
+            const int ymin = __reduce_min_sync(0xffffffffu, any_live ? iy_lo : 0x7fffffff);
+            const int ymax = __reduce_max_sync(0xffffffffu, any_live ? iy_hi : -1);
+            if (lane == 0)
+                s_box[warp] = xmax < 0 ? make_float4(1.0f, 1.0f, -1.0f, -1.0f)
+                                       : make_float4((float)xmin + 0.5f, (float)ymin + 0.5f, (float)xmax + 0.5f,
+                                                     (float)ymax + 0.5f);
+        }
         if (__syncthreads_count(done0 && done1) == NT2) break;
         const int n = min(NT2, end - b0);
         if ((int)threadIdx.x < n) {
@@ -250,7 +265,13 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
             s_a[threadIdx.x] = a;
             s_b[threadIdx.x] = bb;
             s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
-            s_m[threadIdx.x] = warp_mask<TW, TH, 8>(a, bb.x, d, g.ox, g.oy);
+            uint32_t wm = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const float4 bx = s_box[w];
+                if (bx.x <= bx.z && rect_reach(a, bb.x, d, bx.x, bx.y, bx.z, bx.w)) wm |= 1u << w;
+            }
+            s_m[threadIdx.x] = wm;
             if (DEPTH) s_d[threadIdx.x] = d.w;
         }
         __syncthreads();
@@ -327,6 +348,7 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];
     __shared__ uint32_t s_m[NT2];
     __shared__ float s_d[DEPTH ? NT2 : 1];
+    __shared__ float4 s_box[NT2 / 32];
     __shared__ unsigned int s_evals[2];
     __shared__ uint32_t s_k;
     if (threadIdx.x == 0) s_k = atomicAdd(ticket, 1u);
@@ -365,12 +387,12 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     bool done0 = !g.in0 || T.x < o.t_min, done1 = !g.in1 || T.y < o.t_min;
     if (main_pass)
         blend_walk2<TW, TH, true, COUNT, DEPTH, SAVE>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
-                                                      o.t_min, s_a, s_b, s_c, s_m, s_d, T, C0, C1, C2, Dp, last, done0,
-                                                      done1, evals);
+                                                      o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp, last,
+                                                      done0, done1, evals);
     else
         blend_walk2<TW, TH, false, COUNT, false, false>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
-                                                        o.t_min, s_a, s_b, s_c, s_m, s_d, T, C0, C1, C2, Dp, last,
-                                                        done0, done1, evals);
+                                                        o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp,
+                                                        last, done0, done1, evals);
     if (COUNT) {
         for (int off = 16; off > 0; off >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, off);
         if (lane == 0) atomicAdd(&s_evals[main_pass ? 0 : 1], evals);

@@ -138,15 +138,15 @@ __device__ __forceinline__ void tile_pixel2(int tid, int& lx, int& ly0) {
     ly0 = (w / WX) * 8 + (l >> 3);
 }
 
-// Whether the splat can reach alpha_floor at a pixel centre of the block [x0, x0 + BW - 1] x
-// [y0, y0 + BH - 1] (pixel-centre coordinates): the box test, then the minimum of q = -p2 over the
-// block (the centre if inside, else the best point of the four edges) against rz.
-template <int BW, int BH>
-__device__ __forceinline__ bool block_reach(const float4 a, float cc, const float4 d, float x0, float y0) {
+// Whether the splat can reach alpha_floor at a pixel centre of the rectangle [x0, x1] x [y0, y1]
+// (pixel-centre coordinates): the box test, then the minimum of q = -p2 over the rectangle (the
+// centre if inside, else the best point of the four edges) against rz.  block_reach: the block
+// [x0, x0 + BW - 1] x [y0, y0 + BH - 1].
+__device__ __forceinline__ bool rect_reach(const float4 a, float cc, const float4 d, float x0, float y0, float x1,
+                                           float y1) {
     const float hx = d.x, hy = d.y;
     if (!(hx >= 0.0f)) return false;
     const float u = a.x, v = a.y;
-    const float x1 = x0 + (float)(BW - 1), y1 = y0 + (float)(BH - 1);
     if (!(u + hx >= x0 && u - hx <= x1 && v + hy >= y0 && v - hy <= y1)) return false;
     if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return true;
     const float qa = -a.z, qb = -a.w, qc = -cc, rz = d.z;
@@ -168,6 +168,10 @@ __device__ __forceinline__ bool block_reach(const float4 a, float cc, const floa
         qmin = fminf(qmin, qa * dx * dx + qb * dx * dy + qc * dy * dy);
     }
     return !(qmin > rz);   // NaN keeps the block
+}
+template <int BW, int BH>
+__device__ __forceinline__ bool block_reach(const float4 a, float cc, const float4 d, float x0, float y0) {
+    return rect_reach(a, cc, d, x0, y0, x0 + (float)(BW - 1), y0 + (float)(BH - 1));
 }
 
 // Bit w set if the splat can reach alpha_floor at a pixel centre of warp w's 8 x BH block in the tile
