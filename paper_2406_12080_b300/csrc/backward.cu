@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
     __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];
     __shared__ uint32_t s_id[NT2], s_m[NT2];
     __shared__ float s_dz[DEPTH ? NT2 : 1];
+    __shared__ float4 s_box[NT2 / 32];
     __shared__ int s_max;
     const uint32_t item = blockIdx.x;
     if (item >= *n_items) return;
@@ -199,6 +200,20 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
     for (int end = count; end > 0; end -= NT2) {
         const int n = min(NT2, end);
         const int first = end - n;
+        // bounding box of the warp's pixels that take part in this batch (their last contributor lies
+        // beyond its first entry): the warp mask tests entries against it
+        {
+            const bool l0 = last0 > first, l1 = last1 > first, any_l = l0 || l1;
+            const int iy_lo = l0 ? pyi[0] : pyi[1], iy_hi = l1 ? pyi[1] : pyi[0];
+            const int xmin = __reduce_min_sync(0xffffffffu, any_l ? px_i : 0x7fffffff);
+            const int xmax = __reduce_max_sync(0xffffffffu, any_l ? px_i : -1);
+            const int ymin = __reduce_min_sync(0xffffffffu, any_l ? iy_lo : 0x7fffffff);
+            const int ymax = __reduce_max_sync(0xffffffffu, any_l ? iy_hi : -1);
+            if (lane == 0)
+                s_box[warp] = xmax < 0 ? make_float4(1.0f, 1.0f, -1.0f, -1.0f)
+                                       : make_float4((float)xmin + 0.5f, (float)ymin + 0.5f, (float)xmax + 0.5f,
+                                                     (float)ymax + 0.5f);
+        }
         __syncthreads();
         if ((int)threadIdx.x < n) {
             const uint32_t s = __ldg(list + begin + first + threadIdx.x);
@@ -209,7 +224,13 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
             const float4 bb = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
             s_b[threadIdx.x] = bb;
             s_c[threadIdx.x] = __ldg(splat + SPLAT_F4 * (int64_t)s + 2);
-            s_m[threadIdx.x] = warp_mask<TW, TH, 8>(a, bb.x, d, ox, oy);
+            uint32_t wm = 0;
+#pragma unroll
+            for (int w = 0; w < NT2 / 32; ++w) {
+                const float4 bx = s_box[w];
+                if (bx.x <= bx.z && rect_reach(a, bb.x, d, bx.x, bx.y, bx.z, bx.w)) wm |= 1u << w;
+            }
+            s_m[threadIdx.x] = wm;
             if (DEPTH) s_dz[threadIdx.x] = d.w;
         }
         __syncthreads();
