@@ -59,6 +59,7 @@ struct h3dgs_ctx {
     DBuf s_rec, s_rect, s_key, s_idx, s_key2, s_idx2, s_key3, s_tiles, s_poff;
     DBuf pk0, pv0, pk1, pv1, ranges;
     DBuf sortw, seg_start, hists;   // hists: [2][4][256] digit histograms of the depth and tile keys
+    DBuf fw;                        // fixed-capacity frame workspace (all cleared by one launch per render)
     DBuf T_final, n_contrib, splat_grad;
     DBuf items, q_prod, q_single, q_cons, queue_sync, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last, sc_D;
     DBuf exposure;   // copy of the last render's exposure affines [n_cams][12]
@@ -243,6 +244,7 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images, float* de
     a.work_words = ctx->sortw.n / sizeof(uint32_t);
     a.flags = P<uint32_t>(ctx->counters) + C_FLAGS;
     a.ev_queue = nullptr;
+    a.pre_zeroed = false;
     return a;
 }
 
@@ -307,7 +309,7 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
     DBuf* bufs[] = {&ctx->rec, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot, &ctx->cut_lb,
                     &ctx->s_rec, &ctx->s_rect, &ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2,
                     &ctx->s_key3, &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1,
-                    &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->hists, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
+                    &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->hists, &ctx->fw, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
                     &ctx->items, &ctx->q_prod, &ctx->q_single, &ctx->q_cons, &ctx->queue_sync,
                     &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
                     &ctx->sc_last, &ctx->sc_D, &ctx->exposure, &ctx->st_mean, &ctx->st_scale, &ctx->st_rot,
@@ -708,14 +710,49 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
     CK(ensure(ctx->ranges, sizeof(int2) * (size_t)ctx->n_tiles), "ranges");
     CK(ensure(ctx->T_final, sizeof(float) * (size_t)ctx->n_pixels), "pixel state");
     CK(ensure(ctx->n_contrib, sizeof(int32_t) * (size_t)ctx->n_pixels), "pixel state");
-    CK(cudaMemsetAsync(cnt + C_FLAGS, 0, sizeof(uint32_t), s), "memset");
-    CK(cudaMemsetAsync(cnt + C_NVISIBLE, 0, sizeof(uint32_t), s), "memset");
-    CK(cudaMemsetAsync(cnt + C_EVALS, 0, 4 * sizeof(uint32_t), s), "memset");
-    CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(int2) * (size_t)ctx->n_tiles, s), "memset");
-    CK(ensure(ctx->hists, sizeof(uint32_t) * 2 * 4 * 256), "histograms");
-    CK(cudaMemsetAsync(ctx->hists.p, 0, sizeof(uint32_t) * 2 * 4 * 256, s), "memset");
-    uint32_t* depth_hist = P<uint32_t>(ctx->hists);
-    uint32_t* tile_hist = depth_hist + 4 * 256;
+    // Per-frame clears.  With fixed capacities every workspace the frame clears (the sorts' and scans'
+    // look-back words, the blend queue's counters, the digit histograms) has its own region of one
+    // buffer, and a single launch clears them with the counters and the tile ranges; otherwise (sizes
+    // found on the way) they are cleared where they are used.
+    const bool prezero = ctx->fixed;
+    uint32_t *depth_hist, *tile_hist, *plan_work = nullptr, *qsync = nullptr;
+    SortWork sw_d, sw_t, sw_po;
+    size_t plan_words = 0;
+    if (prezero) {
+        auto r64 = [](size_t w) { return (w + 63) / 64 * 64; };
+        const size_t wd = r64(radix_work_words(capM)), wt = r64(radix_work_words(capP));
+        const size_t wpo = r64(pair_offsets_work_words(capM)), wpl = r64(blend_plan_work_words(ctx->n_tiles));
+        const size_t wq = r64((size_t)ctx->n_tiles + 1), wh = 2 * 4 * 256;
+        const size_t total = wd + wt + wpo + wpl + wq + wh;
+        CK(ensure(ctx->fw, sizeof(uint32_t) * total), "frame workspace");
+        uint32_t* base = P<uint32_t>(ctx->fw);
+        uint32_t* flags = cnt + C_FLAGS;
+        sw_d = SortWork{base, wd, ctx->num_sms, flags};
+        sw_t = SortWork{base + wd, wt, ctx->num_sms, flags};
+        sw_po = SortWork{base + wd + wt, wpo, ctx->num_sms, flags};
+        plan_work = base + wd + wt + wpo;
+        plan_words = wpl;
+        qsync = plan_work + wpl;
+        depth_hist = qsync + wq;
+        tile_hist = depth_hist + 4 * 256;
+        ResetList rl;
+        rl.n = 5;
+        rl.p[0] = cnt + C_FLAGS;    rl.words[0] = 1;
+        rl.p[1] = cnt + C_NVISIBLE; rl.words[1] = 1;
+        rl.p[2] = cnt + C_EVALS;    rl.words[2] = 4;
+        rl.p[3] = P<uint32_t>(ctx->ranges); rl.words[3] = 2 * (uint64_t)ctx->n_tiles;
+        rl.p[4] = base;             rl.words[4] = total;
+        CK(launch_reset(rl, ctx->num_sms, s), "frame reset");
+    } else {
+        CK(cudaMemsetAsync(cnt + C_FLAGS, 0, sizeof(uint32_t), s), "memset");
+        CK(cudaMemsetAsync(cnt + C_NVISIBLE, 0, sizeof(uint32_t), s), "memset");
+        CK(cudaMemsetAsync(cnt + C_EVALS, 0, 4 * sizeof(uint32_t), s), "memset");
+        CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(int2) * (size_t)ctx->n_tiles, s), "memset");
+        CK(ensure(ctx->hists, sizeof(uint32_t) * 2 * 4 * 256), "histograms");
+        CK(cudaMemsetAsync(ctx->hists.p, 0, sizeof(uint32_t) * 2 * 4 * 256, s), "memset");
+        depth_hist = P<uint32_t>(ctx->hists);
+        tile_hist = depth_hist + 4 * 256;
+    }
     const DevOpts o = dev_opts(*opts);
     SplatBufs sb;
     sb.rec = P<float4>(ctx->s_rec);
@@ -735,12 +772,13 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
     // of the pairs by tile id, ranges
     SortWork sw;
     CK(sort_work(ctx, std::max<int64_t>(capM, ctx->fixed ? capP : 0), &sw), "sort workspace");
+    if (!prezero) sw_d = sw_t = sw_po = sw;
     bool in_a = false;
     stage_begin(ctx, H3DGS_STAGE_DEPTH_SORT);
     // the histograms and the kept count (the visible splats) come from the preprocess kernel
     CK(radix_sort_pairs(P<uint32_t>(ctx->s_key), nullptr, P<uint32_t>(ctx->s_key2), P<uint32_t>(ctx->s_idx2),
                         P<uint32_t>(ctx->s_key3), P<uint32_t>(ctx->s_idx), cnt + C_NSPLATS, capM, 32, true,
-                        cnt + C_NVISIBLE, sw, &in_a, s, depth_hist),
+                        cnt + C_NVISIBLE, sw_d, &in_a, s, depth_hist, prezero),
        "depth sort");
     stage_end(ctx, H3DGS_STAGE_DEPTH_SORT);
     const uint32_t* order = in_a ? P<uint32_t>(ctx->s_idx2) : P<uint32_t>(ctx->s_idx);
@@ -748,7 +786,7 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
     const int64_t seg_cap0 = ctx->fixed ? capP / DUP_SEG + 2 : 0;
     if (ctx->fixed) CK(ensure(ctx->seg_start, sizeof(uint32_t) * (size_t)seg_cap0), "pair segments");
     CK(launch_pair_offsets(P<uint32_t>(ctx->s_tiles), order, cnt + C_NVISIBLE, capM, P<uint32_t>(ctx->s_poff),
-                           P<uint32_t>(ctx->seg_start), seg_cap0, cnt + C_NPAIRS, sw, s),
+                           P<uint32_t>(ctx->seg_start), seg_cap0, cnt + C_NPAIRS, sw_po, s, prezero),
        "pair offsets");
     if (!ctx->fixed) {
         uint32_t pn = 0;
@@ -758,6 +796,7 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
         DBuf* p4[] = {&ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1};
         for (DBuf* b : p4) CK(ensure(*b, 4 * (size_t)capP), "pair buffer");
         CK(sort_work(ctx, std::max<int64_t>(capM, capP), &sw), "sort workspace");
+        sw_d = sw_t = sw_po = sw;
         const int64_t seg_cap = capP / DUP_SEG + 2;
         CK(ensure(ctx->seg_start, sizeof(uint32_t) * (size_t)seg_cap), "pair segments");
         CK(launch_pair_segments(P<uint32_t>(ctx->s_tiles), order, cnt + C_NVISIBLE, P<uint32_t>(ctx->s_poff),
@@ -775,7 +814,7 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
     // histograms counted by the duplication; every pair is kept
     CK(radix_sort_pairs(P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), P<uint32_t>(ctx->pk1), P<uint32_t>(ctx->pv1),
                         P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), cnt + C_NPAIRS_KEPT, capP, tbits, false,
-                        cnt + C_NPAIRS_KEPT, sw, &in_a, s, tile_hist),
+                        cnt + C_NPAIRS_KEPT, sw_t, &in_a, s, tile_hist, prezero),
        "tile sort");
     stage_end(ctx, H3DGS_STAGE_TILE_SORT);
     const bool in1 = in_a;
@@ -812,6 +851,12 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
         if (!save_for_backward) {   // the adjoint's per-pixel state is not kept
             ba.T_final = nullptr;
             ba.n_contrib = nullptr;
+        }
+        if (prezero) {
+            ba.work = plan_work;
+            ba.work_words = plan_words;
+            ba.queue_sync = qsync;
+            ba.pre_zeroed = true;
         }
         if (ctx->prof) {
             ba.ev_queue = ctx->ev + 2 * H3DGS_STAGE_BLEND_QUEUE;

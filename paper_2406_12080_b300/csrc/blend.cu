@@ -534,18 +534,23 @@ cudaError_t launch_wait_probe(const uint32_t* word, int polls, uint32_t* flags, 
     return cudaGetLastError();
 }
 
+size_t blend_plan_work_words(int64_t n_tiles) {
+    return LB_HEADER_WORDS + 2 * (size_t)std::max<int64_t>(1, (n_tiles + PL_TILE - 1) / PL_TILE);
+}
+
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     if (a.n_tiles <= 0) return cudaSuccess;
     const int64_t pblocks = (a.n_tiles + PL_TILE - 1) / PL_TILE;
     if ((size_t)(LB_HEADER_WORDS + 2 * pblocks) > a.work_words) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)pblocks), s);
+    cudaError_t e = cudaSuccess;
+    if (!a.pre_zeroed) e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)pblocks), s);
     if (e != cudaSuccess) return e;
     Lookback lb{reinterpret_cast<unsigned long long*>(a.work + LB_HEADER_WORDS), a.work, a.flags};
     blend_plan_kernel<<<(unsigned)pblocks, PL_THREADS, 0, s>>>(a.ranges, a.n_tiles, a.chunk, a.tile_item0, a.tile_nch,
                                                                a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons, a.n_items,
                                                                lb);
     Scratch sc{a.scratch_Tc, a.scratch_C, a.scratch_Tend, a.scratch_last, a.scratch_D};
-    e = cudaMemsetAsync(a.queue_sync, 0, sizeof(uint32_t) * (size_t)(a.n_tiles + 1), s);
+    if (!a.pre_zeroed) e = cudaMemsetAsync(a.queue_sync, 0, sizeof(uint32_t) * (size_t)(a.n_tiles + 1), s);
     if (e != cudaSuccess) return e;
     // queue length 2 X + Y <= 2 item_cap - n_tiles
     const unsigned gq = (unsigned)std::max<int64_t>(1, 2 * a.item_cap - a.n_tiles);

@@ -268,16 +268,25 @@ size_t radix_work_words(int64_t n_cap);
 // hist_pre: the digit histograms of every pass ([passes][256], 8-bit digits from the low end) already
 // counted by the producer of the keys, with *n_kept already holding the number of kept keys; NULL:
 // the sort counts them itself.
+// pre_zeroed: the workspace (radix_work_words(n_cap) words) was cleared by the caller.
 cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ka, uint32_t* va, uint32_t* kb,
                              uint32_t* vb, const uint32_t* n_dev, int64_t n_cap, int bits, bool drop_max,
                              uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s,
-                             const uint32_t* hist_pre = nullptr);
+                             const uint32_t* hist_pre = nullptr, bool pre_zeroed = false);
+// Zeroes up to 8 regions of 32-bit words in one launch (the per-frame clears of the render).
+struct ResetList {
+    int n = 0;
+    uint32_t* p[8];
+    uint64_t words[8];
+};
+cudaError_t launch_reset(const ResetList& r, int num_sms, cudaStream_t s);
+size_t pair_offsets_work_words(int64_t n_cap);
 // Pair offsets of the depth order: pair_off[i] = sum of tiles[order[j]] over j < i (i < *n_dev <= n_cap),
 // *total = the sum; seg_start[s] = the entry holding pair s DUP_SEG (for s < seg_cap).
 constexpr int DUP_SEG = 1024;         // pairs per duplication block
 cudaError_t launch_pair_offsets(const uint32_t* tiles, const uint32_t* order, const uint32_t* n_dev, int64_t n_cap,
                                 uint32_t* pair_off, uint32_t* seg_start, int64_t seg_cap, uint32_t* total,
-                                const SortWork& w, cudaStream_t s);
+                                const SortWork& w, cudaStream_t s, bool pre_zeroed = false);
 cudaError_t launch_pair_segments(const uint32_t* tiles, const uint32_t* order, const uint32_t* n_dev,
                                  const uint32_t* pair_off, uint32_t* seg_start, int64_t seg_cap, int grid,
                                  cudaStream_t s);
@@ -328,7 +337,9 @@ struct BlendArgs {
     size_t work_words;
     uint32_t* flags;              // device flag word
     cudaEvent_t* ev_queue;        // 2 events around the main blend kernel (profiling), or NULL
+    bool pre_zeroed;              // work (the plan's look-back words) and queue_sync already cleared
 };
+size_t blend_plan_work_words(int64_t n_tiles);
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
 // Test hook: one thread waits with wait_geq on *word (which nothing sets) for `polls` polls.
 cudaError_t launch_wait_probe(const uint32_t* word, int polls, uint32_t* flags, cudaStream_t s);

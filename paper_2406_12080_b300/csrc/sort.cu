@@ -265,10 +265,31 @@ size_t radix_work_words(int64_t n_cap) {
     return (size_t)(RADIX_HEADER_WORDS + 2 * 4 * tiles * 256);   // 64-bit look-back words
 }
 
+__global__ void reset_kernel(ResetList r) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (int k = 0; k < r.n; ++k) {
+        uint32_t* p = r.p[k];
+        const uint64_t n = r.words[k];
+        if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {   // 16-byte stores, then the tail
+            uint4* q = reinterpret_cast<uint4*>(p);
+            for (uint64_t i = t0; i < n / 4; i += stride) q[i] = make_uint4(0u, 0u, 0u, 0u);
+            for (uint64_t i = (n / 4) * 4 + t0; i < n; i += stride) p[i] = 0u;
+        } else {
+            for (uint64_t i = t0; i < n; i += stride) p[i] = 0u;
+        }
+    }
+}
+
+cudaError_t launch_reset(const ResetList& r, int num_sms, cudaStream_t s) {
+    if (r.n < 0 || r.n > 8) return cudaErrorInvalidValue;
+    reset_kernel<<<num_sms * 4, 256, 0, s>>>(r);
+    return cudaGetLastError();
+}
+
 cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ka, uint32_t* va, uint32_t* kb,
                              uint32_t* vb, const uint32_t* n_dev, int64_t n_cap, int bits, bool drop_max,
                              uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s,
-                             const uint32_t* hist_pre) {
+                             const uint32_t* hist_pre, bool pre_zeroed) {
     *result_in_a = false;
     if (n_cap <= 0) return hist_pre ? cudaSuccess : cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s);
     if (n_cap > 0xffffffffLL || bits < 1 || bits > 32) return cudaErrorInvalidValue;
@@ -282,8 +303,10 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
     uint32_t* tickets = w.work;            // [4]
     uint32_t* hist = w.work + 64;          // [4][256]
     unsigned long long* status = reinterpret_cast<unsigned long long*>(w.work + RADIX_HEADER_WORDS);
-    cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * RADIX_HEADER_WORDS +
-                                                   sizeof(unsigned long long) * (size_t)passes * tiles * 256, s);
+    cudaError_t e = cudaSuccess;
+    if (!pre_zeroed)
+        e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * RADIX_HEADER_WORDS +
+                                           sizeof(unsigned long long) * (size_t)passes * tiles * 256, s);
     if (e != cudaSuccess) return e;
     if (hist_pre) {
         hist = const_cast<uint32_t*>(hist_pre);   // counted by the producer of the keys, with *n_kept
@@ -365,14 +388,20 @@ __global__ void __launch_bounds__(PO_THREADS) pair_offsets_kernel(const uint32_t
     if (n == 0 && threadIdx.x == 0) *total = 0;
 }
 
+size_t pair_offsets_work_words(int64_t n_cap) {
+    return LB_HEADER_WORDS + 2 * (size_t)std::max<int64_t>(1, (n_cap + PO_TILE - 1) / PO_TILE);
+}
+
 cudaError_t launch_pair_offsets(const uint32_t* tiles, const uint32_t* order, const uint32_t* n_dev, int64_t n_cap,
                                 uint32_t* pair_off, uint32_t* seg_start, int64_t seg_cap, uint32_t* total,
-                                const SortWork& w, cudaStream_t s) {
+                                const SortWork& w, cudaStream_t s, bool pre_zeroed) {
     const int64_t blocks = std::max<int64_t>(1, (n_cap + PO_TILE - 1) / PO_TILE);
     if ((size_t)(LB_HEADER_WORDS + 2 * blocks) > w.words) return cudaErrorInvalidValue;
     Lookback lb{reinterpret_cast<unsigned long long*>(w.work + LB_HEADER_WORDS), w.work, w.flags};
-    cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)blocks), s);
-    if (e != cudaSuccess) return e;
+    if (!pre_zeroed) {
+        cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)blocks), s);
+        if (e != cudaSuccess) return e;
+    }
     pair_offsets_kernel<<<(unsigned)blocks, PO_THREADS, 0, s>>>(tiles, order, n_dev, pair_off, seg_start,
                                                                 (uint32_t)std::min<int64_t>(seg_cap, 0xffffffffLL),
                                                                 total, lb);
