@@ -34,20 +34,6 @@ constexpr float SH_C3C = 0.45704579946446572f;
 constexpr float SH_C3D = 0.37317633259011540f;
 constexpr float SH_C3E = 1.4453057213202769f;
 
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float lg2_approx(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float alpha_prime(float ap, float K) {
-    if (K == 2.0f) return __fdividef(ap, 1.0f + sqrtf(1.0f - ap));
-    return 1.0f - ex2_approx(__fdividef(lg2_approx(1.0f - ap), K));
-}
 __device__ __forceinline__ float alpha_prime_grad(float ap, float K) {
     if (K == 2.0f) return 0.5f * rsqrtf(1.0f - ap);
     return __fdividef(ex2_approx(lg2_approx(1.0f - ap) * (__fdividef(1.0f, K) - 1.0f)), K);

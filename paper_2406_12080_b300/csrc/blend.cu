@@ -32,23 +32,6 @@
 
 namespace h3dgs {
 
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float lg2_approx(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// alpha' of a K-child transition given the clamped parent alpha
-__device__ __forceinline__ float alpha_prime(float ap, float K) {
-    if (K == 2.0f) return __fdividef(ap, 1.0f + sqrtf(1.0f - ap));
-    return 1.0f - ex2_approx(__fdividef(lg2_approx(1.0f - ap), K));
-}
-
 // alpha of one (pixel, splat) pair, fixed fp32 order; K (child count) is read only when t != 0
 __device__ __forceinline__ float pair_alpha(float px, float py, const float4 a, const float4 b, const float4* c,
                                             float clampv) {

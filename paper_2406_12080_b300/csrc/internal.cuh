@@ -191,6 +191,36 @@ __device__ __forceinline__ uint32_t warp_mask(const float4 a, float cc, const fl
     return m;
 }
 
+// Hardware approximations (PTX .approx instructions) used by the blend and its adjoint; both take
+// every per-pixel decision through these same definitions.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// alpha' = 1 - (1 - ap)^(1/K) of a K-child transition given the clamped parent alpha ap (Eq. alphap);
+// K = 2 in the cancellation-free form ap / (1 + sqrt(1 - ap)).  ap <= alpha_clamp < 1.
+__device__ __forceinline__ float alpha_prime(float ap, float K) {
+    if (K == 2.0f) return ap * rcp_approx(1.0f + sqrt_approx(1.0f - ap));
+    return 1.0f - ex2_approx(__fdividef(lg2_approx(1.0f - ap), K));
+}
+
 // Bounded wait of one thread until *p >= want (acquire): at most `limit` polls, sleeping between
 // polls after the first few.  Giving up sets FLAG_WAIT_TIMEOUT in *flags and returns false; the
 // caller then goes on with what it has (its result is invalid and flagged), so no wait can hang.
