@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_histogram_kernel(const uint3
 // One LSD pass.  n = *n_dev keys are read (dropping 0xffffffff keys if `drop`), the kept ones written;
 // without vin the values are the input positions.
 template <int OS_IPT>
-__global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32_t* __restrict__ kin,
+__global__ void __launch_bounds__(OS_THREADS, 3) radix_onesweep_kernel(const uint32_t* __restrict__ kin,
                                                                     const uint32_t* __restrict__ vin,
                                                                     uint32_t* __restrict__ kout,
                                                                     uint32_t* __restrict__ vout,
@@ -151,22 +151,30 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
     __shared__ uint32_t s_tile, s_cnt255;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    // loads that do not depend on the tile overlap the ticket
+    const uint32_t n = *n_dev;
+    const uint32_t n_written = *n_out;   // destinations stay below it even if a look-back gave up
+    const uint32_t hist_d = hist[threadIdx.x];
     for (int i = threadIdx.x; i < OS_WARPS * 256; i += OS_THREADS) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
     const uint32_t tile = s_tile;
-    const uint32_t n = *n_dev;
     const uint64_t base = (uint64_t)tile * OS_TILE;
     if (base >= n) return;   // every tile below this one is in range, so nobody waits for it
     // ---- load and rank: warp w holds keys [base + 32 IPT w, base + 32 IPT (w + 1)), key i of a lane at
-    // offset 32 i + lane, ranked in (i, lane) order, i.e. in input order
+    // offset 32 i + lane, ranked in (i, lane) order, i.e. in input order.  All loads are issued first.
     const uint32_t lmask = lanemask_lt();
     uint32_t key[OS_IPT], val[OS_IPT], loc[OS_IPT];
 #pragma unroll
     for (int i = 0; i < OS_IPT; ++i) {
         const uint64_t g = base + (uint64_t)warp * 32 * OS_IPT + i * 32 + lane;
-        bool ok = g < n;
+        const bool ok = g < n;
         key[i] = ok ? __ldg(kin + g) : 0xffffffffu;
         val[i] = ok ? (vin ? __ldg(vin + g) : (uint32_t)g) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < OS_IPT; ++i) {
+        const uint64_t g = base + (uint64_t)warp * 32 * OS_IPT + i * 32 + lane;
+        bool ok = g < n;
         if (drop && key[i] == 0xffffffffu) ok = false;
         const uint32_t d = (key[i] >> shift) & 255u;
         uint32_t peers = __ballot_sync(0xffffffffu, ok);
@@ -202,7 +210,7 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
     const uint32_t lstart = block_exclusive_scan256(cnt, s_warp);
     s_lstart[d] = lstart;
     // global start of digit d over the whole input (exclusive scan of the pass histogram)
-    const uint32_t gstart = block_exclusive_scan256(hist[d], s_warp);
+    const uint32_t gstart = block_exclusive_scan256(hist_d, s_warp);
     // ---- decoupled look-back over earlier tiles for digit d: OS_LOOKBACK status words are loaded at
     // once, then summed newest first until an inclusive one; a word not yet published is re-read
     unsigned long long excl = 0;
@@ -248,7 +256,6 @@ __global__ void __launch_bounds__(OS_THREADS) radix_onesweep_kernel(const uint32
     }
     __syncthreads();
     const uint32_t kept = s_lstart[255] + s_cnt255;
-    const uint32_t n_written = *n_out;   // destinations stay below it even if a look-back gave up
     for (uint32_t j = threadIdx.x; j < kept; j += OS_THREADS) {
         const uint32_t k = s_keys[j];
         const uint32_t dd = (k >> shift) & 255u;
