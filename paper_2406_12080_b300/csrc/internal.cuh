@@ -191,6 +191,29 @@ __device__ __forceinline__ uint32_t warp_mask(const float4 a, float cc, const fl
     return m;
 }
 
+// Programmatic dependent launch: a kernel launched with launch_dependent() may start while the
+// previous kernel of the stream is still running.  Such a kernel calls griddep_wait() (in every
+// block, before any early exit) before it reads anything an earlier kernel wrote or writes anything
+// an earlier kernel reads; griddep_launch_dependents() lets the next kernel start early.  Both are
+// no-ops for a kernel launched normally.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Hardware approximations (PTX .approx instructions) used by the blend and its adjoint; both take
 // every per-pixel decision through these same definitions.
 __device__ __forceinline__ float ex2_approx(float x) {

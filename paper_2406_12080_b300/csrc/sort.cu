@@ -150,12 +150,14 @@ __global__ void __launch_bounds__(OS_THREADS, 3) radix_onesweep_kernel(const uin
     __shared__ uint32_t s_warp[OS_WARPS];
     __shared__ uint32_t s_tile, s_cnt255;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    griddep_launch_dependents();
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);   // tickets are cleared before the frame
+    for (int i = threadIdx.x; i < OS_WARPS * 256; i += OS_THREADS) (&s_wcnt[0][0])[i] = 0;
+    griddep_wait();
     // loads that do not depend on the tile overlap the ticket
     const uint32_t n = *n_dev;
     const uint32_t n_written = *n_out;   // destinations stay below it even if a look-back gave up
     const uint32_t hist_d = hist[threadIdx.x];
-    for (int i = threadIdx.x; i < OS_WARPS * 256; i += OS_THREADS) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t base = (uint64_t)tile * OS_TILE;
@@ -330,14 +332,11 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
         const bool to_a = (p % 2) == 0;
         const uint32_t* ki = p == 0 ? kin : (to_a ? kb : ka);
         const uint32_t* vi = p == 0 ? vin : (to_a ? vb : va);
-        if (small)
-            radix_onesweep_kernel<OS_IPT_SMALL><<<(unsigned)tiles, OS_THREADS, 0, s>>>(
-                ki, vi, to_a ? ka : kb, to_a ? va : vb, p == 0 ? n_dev : n_kept, n_kept, 8 * p,
-                (p == 0 && drop_max) ? 1 : 0, hist + 256 * p, status + (size_t)p * tiles * 256, tickets + p, w.flags);
-        else
-            radix_onesweep_kernel<OS_IPT_LARGE><<<(unsigned)tiles, OS_THREADS, 0, s>>>(
-                ki, vi, to_a ? ka : kb, to_a ? va : vb, p == 0 ? n_dev : n_kept, n_kept, 8 * p,
-                (p == 0 && drop_max) ? 1 : 0, hist + 256 * p, status + (size_t)p * tiles * 256, tickets + p, w.flags);
+        e = launch_dependent(small ? radix_onesweep_kernel<OS_IPT_SMALL> : radix_onesweep_kernel<OS_IPT_LARGE>,
+                             dim3((unsigned)tiles), dim3(OS_THREADS), s, ki, vi, to_a ? ka : kb, to_a ? va : vb,
+                             p == 0 ? n_dev : n_kept, n_kept, 8 * p, (p == 0 && drop_max) ? 1 : 0, hist + 256 * p,
+                             status + (size_t)p * tiles * 256, tickets + p, w.flags);
+        if (e != cudaSuccess) return e;
     }
     *result_in_a = (passes % 2) == 1;
     return cudaGetLastError();
