@@ -40,10 +40,10 @@ T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
 // device counter block
 // C_EVALS and C_EVALS_T occupy two words each (64-bit counters)
 // C_NSORTED: a zero word (the bounded-wait probe); C_NTSORT: unused
-// C_NITEMS: 3 words (items, producers, singles).  C_FLAGS: render flags (cleared by every render);
+// C_NITEMS: 4 words (items, producers, singles, split tiles).  C_FLAGS: render flags (cleared by every render);
 // C_CUTFLAGS: cut flags (cleared by every cut); the stats report both.
 enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NSORTED = 6,
-       C_NTSORT = 7, C_EVALS = 8, C_EVALS_T = 10, C_NITEMS = 12, C_CUTFLAGS = 15, C_COUNT = 16 };
+       C_NTSORT = 7, C_EVALS = 8, C_EVALS_T = 10, C_NITEMS = 12, C_CUTFLAGS = 16, C_COUNT = 17 };
 
 }  // namespace
 
@@ -61,7 +61,7 @@ struct h3dgs_ctx {
     DBuf sortw, seg_start, hists;   // hists: [2][4][256] digit histograms of the depth and tile keys
     DBuf fw;                        // fixed-capacity frame workspace (all cleared by one launch per render)
     DBuf T_final, n_contrib, splat_grad;
-    DBuf items, q_prod, q_single, q_cons, queue_sync, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last, sc_D;
+    DBuf items, q_prod, q_single, q_cons, queue_sync, tile_item0, tile_nch, tile_split, sc_Tc, sc_C, sc_Tend, sc_last, sc_D;
     DBuf exposure;   // copy of the last render's exposure affines [n_cams][12]
     // streamed hierarchy (attributes in host memory, a device cache of rows)
     bool streamed = false;
@@ -227,6 +227,8 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images, float* de
     a.queue_sync = P<uint32_t>(ctx->queue_sync);
     a.tile_item0 = P<int32_t>(ctx->tile_item0);
     a.tile_nch = P<int32_t>(ctx->tile_nch);
+    a.tile_split = P<int32_t>(ctx->tile_split);
+    a.num_sms = ctx->num_sms;
     a.n_items = P<uint32_t>(ctx->counters) + C_NITEMS;
     a.scratch_Tc = P<float>(ctx->sc_Tc);
     a.scratch_C = P<float>(ctx->sc_C);
@@ -311,7 +313,7 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
                     &ctx->s_key3, &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1,
                     &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->hists, &ctx->fw, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
                     &ctx->items, &ctx->q_prod, &ctx->q_single, &ctx->q_cons, &ctx->queue_sync,
-                    &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
+                    &ctx->tile_item0, &ctx->tile_nch, &ctx->tile_split, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
                     &ctx->sc_last, &ctx->sc_D, &ctx->exposure, &ctx->st_mean, &ctx->st_scale, &ctx->st_rot,
                     &ctx->st_opacity, &ctx->st_sh, &ctx->st_slot_of, &ctx->st_node_of, &ctx->st_stamp,
                     &ctx->st_free, &ctx->st_missing, &ctx->st_count};
@@ -833,6 +835,7 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
         CK(ensure(ctx->queue_sync, sizeof(uint32_t) * (size_t)(ctx->n_tiles + 1)), "blend queue");
         CK(ensure(ctx->tile_item0, sizeof(int32_t) * (size_t)ctx->n_tiles), "blend items");
         CK(ensure(ctx->tile_nch, sizeof(int32_t) * (size_t)ctx->n_tiles), "blend items");
+        CK(ensure(ctx->tile_split, sizeof(int32_t) * (size_t)ctx->n_tiles), "blend items");
         CK(ensure(ctx->sc_Tc, sizeof(float) * (size_t)icap * NT), "blend scratch");
         CK(ensure(ctx->sc_C, 3 * sizeof(float) * (size_t)icap * NT), "blend scratch");
         CK(ensure(ctx->sc_Tend, sizeof(float) * (size_t)icap * NT), "blend scratch");

@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __re
                                                                 uint32_t* __restrict__ q_prod,
                                                                 uint32_t* __restrict__ q_single,
                                                                 uint32_t* __restrict__ q_cons,
-                                                                uint32_t* __restrict__ counts /* items, X, Y */,
+                                                                int32_t* __restrict__ tile_split,
+                                                                uint32_t* __restrict__ counts /* items, X, Y, Z */,
                                                                 Lookback lb) {
     __shared__ uint32_t s_ticket;
     __shared__ unsigned long long s_slot, s_warp[PL_THREADS / 32];
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __re
             const int64_t offF = t + offX;
             tile_item0[t] = (int32_t)offF;
             tile_nch[t] = n;
+            if (n > 1) tile_split[t - offY] = (int32_t)t;   // offY singles before t
             for (int c = 0; c < n; ++c) {
                 const int64_t it = offF + c;
                 if (it >= item_cap) break;
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __re
                 counts[0] = (uint32_t)min(F, item_cap);
                 counts[1] = fits ? (uint32_t)X : 0u;   // an overflowing plan blends nothing (flagged)
                 counts[2] = fits ? (uint32_t)Y : 0u;
+                counts[3] = fits ? (uint32_t)(n_tiles - Y) : 0u;
             }
             offX += n - 1;
             offY += (n == 1);
@@ -449,63 +452,67 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
 }
 
 // Split tiles: per pixel, sum the chunks' colours; T_final and the last contributor come from the
-// last chunk whose walk ran (a chunk with T_in below t_min did not run).
+// last chunk whose walk ran (a chunk with T_in below t_min did not run).  One wave of blocks walks
+// the plan's list of split tiles (counts[3] of them), one pixel per thread.
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
-                                                                int64_t n_tiles, const int32_t* __restrict__ tile_item0,
+                                                                const uint32_t* __restrict__ counts,
+                                                                const int32_t* __restrict__ tile_split,
+                                                                const int32_t* __restrict__ tile_item0,
                                                                 const int32_t* __restrict__ tile_nch, Scratch sc,
                                                                 float* __restrict__ images, float* __restrict__ depth,
                                                                 const float* __restrict__ exposure,
                                                                 float* __restrict__ T_final,
                                                                 int32_t* __restrict__ n_contrib) {
     constexpr int NT = TW * TH;
-    const int64_t tile = blockIdx.x;
-    if (tile >= n_tiles) return;
-    const int nch = tile_nch[tile];
-    if (nch == 1) return;
-    // one pixel per thread, row-major in the tile (the scratch's pixel order)
-    int lo = 0, hi = n_cams - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (cams[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
-    }
-    const DevCam& cam = cams[lo];
-    const int local = (int)(tile - cam.tile_base);
-    const int px_i = (local % cam.tiles_x) * TW + (int)threadIdx.x % TW;
-    const int py_i = (local / cam.tiles_x) * TH + (int)threadIdx.x / TW;
-    if (px_i >= cam.width || py_i >= cam.height) return;
-    const int64_t i0 = tile_item0[tile];
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f, T = 1.0f, Tin = 1.0f;
-    int last = 0;
-    // every chunk's scratch is read whether or not it is used, so the loads of successive chunks do
-    // not wait on each other through the running transmittance
+    const uint32_t Z = counts[3];
+    for (uint32_t z = blockIdx.x; z < Z; z += gridDim.x) {
+        const int64_t tile = tile_split[z];
+        const int nch = tile_nch[tile];
+        // one pixel per thread, row-major in the tile (the scratch's pixel order)
+        int lo = 0, hi = n_cams - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cams[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+        }
+        const DevCam& cam = cams[lo];
+        const int local = (int)(tile - cam.tile_base);
+        const int px_i = (local % cam.tiles_x) * TW + (int)threadIdx.x % TW;
+        const int py_i = (local / cam.tiles_x) * TH + (int)threadIdx.x / TW;
+        if (px_i >= cam.width || py_i >= cam.height) continue;
+        const int64_t i0 = tile_item0[tile];
+        float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f, T = 1.0f, Tin = 1.0f;
+        int last = 0;
+        // every chunk's scratch is read whether or not it is used, so the loads of successive chunks
+        // do not wait on each other through the running transmittance
 #pragma unroll 4
-    for (int c = 0; c < nch; ++c) {
-        const int64_t slot = (i0 + c) * NT + threadIdx.x;
-        const float c0 = sc.C[3 * slot + 0], c1 = sc.C[3 * slot + 1], c2 = sc.C[3 * slot + 2];
-        const float te = sc.Tend[slot], tc = sc.Tc[slot];   // Tc of the last chunk is not used
-        const bool run = !(Tin < o.t_min);
-        C0 += run ? c0 : 0.0f;
-        C1 += run ? c1 : 0.0f;
-        C2 += run ? c2 : 0.0f;
-        T = run ? te : T;
-        if (depth) {
-            const float dd = sc.D[slot];
-            D += run ? dd : 0.0f;
+        for (int c = 0; c < nch; ++c) {
+            const int64_t slot = (i0 + c) * NT + threadIdx.x;
+            const float c0 = sc.C[3 * slot + 0], c1 = sc.C[3 * slot + 1], c2 = sc.C[3 * slot + 2];
+            const float te = sc.Tend[slot], tc = sc.Tc[slot];   // Tc of the last chunk is not used
+            const bool run = !(Tin < o.t_min);
+            C0 += run ? c0 : 0.0f;
+            C1 += run ? c1 : 0.0f;
+            C2 += run ? c2 : 0.0f;
+            T = run ? te : T;
+            if (depth) {
+                const float dd = sc.D[slot];
+                D += run ? dd : 0.0f;
+            }
+            if (n_contrib) {
+                const int32_t l = sc.last[slot];
+                if (run && l >= 0) last = l;
+            }
+            if (c + 1 < nch) Tin = fmul(Tin, tc);
         }
-        if (n_contrib) {
-            const int32_t l = sc.last[slot];
-            if (run && l >= 0) last = l;
-        }
-        if (c + 1 < nch) Tin = fmul(Tin, tc);
+        const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
+        const int64_t plane = (int64_t)cam.width * cam.height;
+        write_pixel(images + 3 * cam.pix_base + (int64_t)py_i * cam.width + px_i, plane, T, C0, C1, C2, o,
+                    exposure ? exposure + 12 * lo : nullptr);
+        if (depth) depth[pix] = D;
+        if (T_final) T_final[pix] = T;
+        if (n_contrib) n_contrib[pix] = last;
     }
-    const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
-    const int64_t plane = (int64_t)cam.width * cam.height;
-    write_pixel(images + 3 * cam.pix_base + (int64_t)py_i * cam.width + px_i, plane, T, C0, C1, C2, o,
-                exposure ? exposure + 12 * lo : nullptr);
-    if (depth) depth[pix] = D;
-    if (T_final) T_final[pix] = T;
-    if (n_contrib) n_contrib[pix] = last;
 }
 
 __global__ void wait_probe_kernel(const uint32_t* word, int polls, uint32_t* flags) {
@@ -530,14 +537,16 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     Lookback lb{reinterpret_cast<unsigned long long*>(a.work + LB_HEADER_WORDS), a.work, a.flags};
     blend_plan_kernel<<<(unsigned)pblocks, PL_THREADS, 0, s>>>(a.ranges, a.n_tiles, a.chunk, a.tile_item0, a.tile_nch,
-                                                               a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons, a.n_items,
+                                                               a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons,
+                                                               a.tile_split, a.n_items,
                                                                lb);
     Scratch sc{a.scratch_Tc, a.scratch_C, a.scratch_Tend, a.scratch_last, a.scratch_D};
     if (!a.pre_zeroed) e = cudaMemsetAsync(a.queue_sync, 0, sizeof(uint32_t) * (size_t)(a.n_tiles + 1), s);
     if (e != cudaSuccess) return e;
     // queue length 2 X + Y <= 2 item_cap - n_tiles
     const unsigned gq = (unsigned)std::max<int64_t>(1, 2 * a.item_cap - a.n_tiles);
-    const unsigned tg = (unsigned)a.n_tiles;
+    // combine: one wave of blocks (a few per SM) over the split tiles
+    const unsigned tg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.n_tiles, 8 * (int64_t)a.num_sms));
 #define QUEUE(TWV, THV, CNT, DEP, SAV)                                                                                \
     blend_queue_kernel<TWV, THV, CNT, DEP, SAV><<<gq, TWV * THV / 2, 0, s>>>(                                         \
         a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.items, a.q_prod, a.q_single, a.q_cons, a.n_items,         \
@@ -554,9 +563,9 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
             if (save) QUEUE(TWV, THV, false, false, true); else QUEUE(TWV, THV, false, false, false);                 \
         }                                                                                                             \
         if (a.ev_queue) cudaEventRecord(a.ev_queue[1], s);                                                            \
-        blend_combine_kernel<TWV, THV><<<tg, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.n_tiles, a.tile_item0,       \
-                                                                a.tile_nch, sc, a.images, a.depth, a.exposure,        \
-                                                                a.T_final, a.n_contrib);                              \
+        blend_combine_kernel<TWV, THV><<<tg, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.n_items, a.tile_split,       \
+                                                                a.tile_item0, a.tile_nch, sc, a.images, a.depth,      \
+                                                                a.exposure, a.T_final, a.n_contrib);                  \
     } while (0)
     const DevOpts& o = a.o;
     const bool save = a.T_final && a.n_contrib;   // per-pixel state for the adjoint (evaluations are not

@@ -374,7 +374,8 @@ struct BlendArgs {
     int2* items;
     int32_t* tile_item0;
     int32_t* tile_nch;
-    uint32_t* n_items;            // [3]: items, producers X, singles Y
+    int32_t* tile_split;          // [n_tiles]: the split tiles (more than one chunk) in tile order
+    uint32_t* n_items;            // [4]: items, producers X, singles Y, split tiles
     float* scratch_Tc;
     float* scratch_C;
     float* scratch_Tend;
@@ -391,6 +392,7 @@ struct BlendArgs {
     uint32_t* flags;              // device flag word
     cudaEvent_t* ev_queue;        // 2 events around the main blend kernel (profiling), or NULL
     bool pre_zeroed;              // work (the plan's look-back words) and queue_sync already cleared
+    int num_sms;
 };
 size_t blend_plan_work_words(int64_t n_tiles);
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
