@@ -98,9 +98,10 @@ typedef struct {
     int32_t aa_compensate;   /* 1: opacities scaled by sqrt(det S' / det(S' + lowpass I))     */
     int32_t interpolate;     /* 1: parent/child interpolation (Sec. 4.2); 0: render the cut as is */
     float bg[3];             /* background colour                                              */
-    int32_t blend_chunk;     /* tile lists longer than this many entries are blended in chunks of
-                                this size by separate CTAs (64 .. 65536, default 384); the image
-                                does not depend on it beyond fp32 reassociation of T            */
+    int32_t blend_chunk;     /* a tile list of L > blend_chunk entries is blended as
+                                ceil(L / blend_chunk) chunks of near-equal length by separate
+                                CTAs (64 .. 65536, default 384); the image does not depend on
+                                it beyond fp32 reassociation of T                               */
 } h3dgs_render_opts;
 
 /* Counters of the most recent h3dgs_render (read with a stream synchronisation). */

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
     const float2 py = make_float2((float)pyi[0] + 0.5f, (float)pyi[1] + 0.5f);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 r = ranges[tile];
-    const int begin = r.x + it.y * chunk;     // first list entry of this item
+    const int begin = chunk_begin(r, nch, it.y);   // first list entry of this item
     float Tk[2] = {1.0f, 1.0f}, gk[2][3] = {{0, 0, 0}, {0, 0, 0}}, Sk[2][3] = {{0, 0, 0}, {0, 0, 0}};
     float gdk[2] = {0.0f, 0.0f}, SDk[2] = {0.0f, 0.0f};
     int stop[2] = {begin, begin};             // entries [begin, stop) are walked back to front

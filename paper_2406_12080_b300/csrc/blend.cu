@@ -9,8 +9,8 @@
 // The per-pixel decision quantities (dx, dy, exponent, alpha, T) use a fixed fp32 order.
 //
 // Street scenes put thousands of splats behind some pixels (near the vanishing point), so a
-// one-CTA-per-tile blend is bounded by its longest list.  Lists longer than `chunk` entries are
-// cut into chunks that run as separate CTAs ("items"):
+// one-CTA-per-tile blend is bounded by its longest list.  A list of L > `chunk` entries is cut into
+// ceil(L / chunk) chunks of near-equal length that run as separate CTAs ("items"):
 //   pass T    (split tiles only) each chunk computes the product of (1 - alpha) over its
 //             contributors, without the stop rule, giving every chunk its incoming transmittance
 //             T_in as a product of the earlier chunks' products;
@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     const bool main_pass = role != 0 || it.y == 0;
     const TileGeom2<TW, TH> g = tile_geom2<TW, TH>(cams, n_cams, tile);
     const int2 r = ranges[tile];
-    const int begin = r.x + it.y * chunk;
-    const int end = nch == 1 ? r.y : min(r.y, begin + chunk);
+    const int begin = chunk_begin(r, nch, it.y);
+    const int end = chunk_begin(r, nch, it.y + 1);
     const int64_t s0 = (int64_t)item * NT + g.slot0, s1 = (int64_t)item * NT + g.slot1;
     const int lane = threadIdx.x & 31;
     float2 T = make_float2(1.0f, 1.0f);

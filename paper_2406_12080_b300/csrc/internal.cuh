@@ -191,6 +191,12 @@ __device__ __forceinline__ uint32_t warp_mask(const float4 a, float cc, const fl
     return m;
 }
 
+// First list entry of chunk c when a tile's list [r.x, r.y) is split into nch chunks of near-equal
+// length (lengths differ by at most one; chunk nch ends at r.y).
+__device__ __forceinline__ int chunk_begin(int2 r, int nch, int c) {
+    return r.x + (int)(((int64_t)(r.y - r.x) * c) / nch);
+}
+
 // Programmatic dependent launch: a kernel launched with launch_dependent() may start while the
 // previous kernel of the stream is still running.  Such a kernel calls griddep_wait() (in every
 // block, before any early exit) before it reads anything an earlier kernel wrote or writes anything
