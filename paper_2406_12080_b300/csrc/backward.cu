@@ -254,21 +254,24 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
             // one approximate reciprocal per pixel instead of four divisions (values, not decisions)
             const float2 inv = make_float2(__fdividef(1.0f, 1.0f - alpha.x), __fdividef(1.0f, 1.0f - alpha.y));
             T = sel2(con0, con1, mul2(T, inv), T);
-            const float2 wgt = mul2(alpha, T);
+            // a pixel that does not take the splat gets weight 0 and alpha adjoint 0, so every gradient
+            // term below (each a product of one of the two with finite factors) is exactly 0 for it
+            const float2 wgt = sel2(con0, con1, mul2(alpha, T), f2(0.0f));
             const float2 gr = mul2(g0, wgt), gg = mul2(g1, wgt), gb = mul2(g2, wgt);
             float2 dal = mul2(g0, fma2(T, f2(c.x), mul2(f2(-1.0f), mul2(S0, inv))));
             dal = fma2(g1, fma2(T, f2(c.y), mul2(f2(-1.0f), mul2(S1, inv))), dal);
             dal = fma2(g2, fma2(T, f2(c.z), mul2(f2(-1.0f), mul2(S2, inv))), dal);
-            S0 = sel2(con0, con1, fma2(f2(c.x), wgt, S0), S0);
-            S1 = sel2(con0, con1, fma2(f2(c.y), wgt, S1), S1);
-            S2 = sel2(con0, con1, fma2(f2(c.z), wgt, S2), S2);
+            S0 = fma2(f2(c.x), wgt, S0);   // unchanged where wgt = 0
+            S1 = fma2(f2(c.y), wgt, S1);
+            S2 = fma2(f2(c.z), wgt, S2);
             float2 gz = f2(0.0f);
             if (DEPTH) {
                 const float zj = s_dz[j];
                 dal = fma2(gd2, fma2(T, f2(zj), mul2(f2(-1.0f), mul2(SD, inv))), dal);
                 gz = mul2(gd2, wgt);
-                SD = sel2(con0, con1, fma2(f2(zj), wgt, SD), SD);
+                SD = fma2(f2(zj), wgt, SD);
             }
+            dal = sel2(con0, con1, dal, f2(0.0f));
             const float2 dan = interp ? mul2(f2(1.0f - b.w), dal) : dal;
             const bool nl0 = xn.x < clampv, nl1 = xn.y < clampv;
             const float2 gon = sel2(nl0, nl1, mul2(dan, G), f2(0.0f));
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
             const float2 gu = mul2(f2(-1.0f), mul2(dp2, fma2(f2(2.0f * a.z), f2(dx), mul2(f2(a.w), dy))));
             const float2 gv = mul2(f2(-1.0f), mul2(dp2, fma2(f2(a.w), f2(dx), mul2(f2(2.0f * b.x), dy))));
             // both pixels' contributions of this splat (a pixel that does not take it adds zero)
-            auto sum2 = [&](float2 x) { return (con0 ? x.x : 0.0f) + (con1 ? x.y : 0.0f); };
+            auto sum2 = [](float2 x) { return x.x + x.y; };
             float v[16] = {sum2(gu), sum2(gv), sum2(gca), sum2(gcb), sum2(gcc), sum2(gon), sum2(gop), sum2(gr),
                            sum2(gg), sum2(gb), DEPTH ? sum2(gz) : 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const float sum = warp_reduce_scatter16(v, lane);
