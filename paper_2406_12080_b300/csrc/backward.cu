@@ -173,9 +173,13 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
     float2 T = make_float2(Tk[0], Tk[1]);
     const float2 g0 = make_float2(gk[0][0], gk[1][0]), g1 = make_float2(gk[0][1], gk[1][1]),
                  g2 = make_float2(gk[0][2], gk[1][2]);
-    float2 S0 = make_float2(Sk[0][0], Sk[1][0]), S1 = make_float2(Sk[0][1], Sk[1][1]), S2 = make_float2(Sk[0][2], Sk[1][2]);
+    const float2 S0 = make_float2(Sk[0][0], Sk[1][0]), S1 = make_float2(Sk[0][1], Sk[1][1]),
+                 S2 = make_float2(Sk[0][2], Sk[1][2]);
     const float2 gd2 = make_float2(gdk[0], gdk[1]);
-    float2 SD = make_float2(SDk[0], SDk[1]);
+    // B = sum_c g_c S_c (+ g_depth S_depth): the colour behind the current splat, S_c, enters the alpha
+    // adjoint only through this sum, which is carried instead of the channels
+    float2 B = fma2(g2, S2, fma2(g1, S1, mul2(g0, S0)));
+    if (DEPTH) B = fma2(gd2, make_float2(SDk[0], SDk[1]), B);
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
     atomicMax(&s_max, max(stop[0], stop[1]) - begin);
@@ -258,19 +262,15 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
             // term below (each a product of one of the two with finite factors) is exactly 0 for it
             const float2 wgt = sel2(con0, con1, mul2(alpha, T), f2(0.0f));
             const float2 gr = mul2(g0, wgt), gg = mul2(g1, wgt), gb = mul2(g2, wgt);
-            float2 dal = mul2(g0, fma2(T, f2(c.x), mul2(f2(-1.0f), mul2(S0, inv))));
-            dal = fma2(g1, fma2(T, f2(c.y), mul2(f2(-1.0f), mul2(S1, inv))), dal);
-            dal = fma2(g2, fma2(T, f2(c.z), mul2(f2(-1.0f), mul2(S2, inv))), dal);
-            S0 = fma2(f2(c.x), wgt, S0);   // unchanged where wgt = 0
-            S1 = fma2(f2(c.y), wgt, S1);
-            S2 = fma2(f2(c.z), wgt, S2);
+            // alpha adjoint, colour part: sum_c g_c (T col_c - S_c / (1 - alpha)) = T A - B / (1 - alpha)
+            float2 A = fma2(g2, f2(c.z), fma2(g1, f2(c.y), mul2(g0, f2(c.x))));
             float2 gz = f2(0.0f);
             if (DEPTH) {
-                const float zj = s_dz[j];
-                dal = fma2(gd2, fma2(T, f2(zj), mul2(f2(-1.0f), mul2(SD, inv))), dal);
+                A = fma2(gd2, f2(s_dz[j]), A);
                 gz = mul2(gd2, wgt);
-                SD = fma2(f2(zj), wgt, SD);
             }
+            float2 dal = fma2(T, A, mul2(B, mul2(inv, f2(-1.0f))));
+            B = fma2(A, wgt, B);   // unchanged where wgt = 0
             dal = sel2(con0, con1, dal, f2(0.0f));
             const float2 dan = interp ? mul2(f2(1.0f - b.w), dal) : dal;
             const bool nl0 = xn.x < clampv, nl1 = xn.y < clampv;
@@ -285,13 +285,15 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
                 dG = sel2(pl0, pl1, fma2(dap, f2(b.z), dG), dG);
             }
             const float2 dp2 = mul2(mul2(dG, G), f2(LN2));
-            const float2 dxx = f2(dx * dx);
-            const float2 gca = mul2(dp2, dxx), gcb = mul2(mul2(dp2, f2(dx)), dy), gcc = mul2(mul2(dp2, dy), dy);
-            const float2 gu = mul2(f2(-1.0f), mul2(dp2, fma2(f2(2.0f * a.z), f2(dx), mul2(f2(a.w), dy))));
-            const float2 gv = mul2(f2(-1.0f), mul2(dp2, fma2(f2(a.w), f2(dx), mul2(f2(2.0f * b.x), dy))));
+            // exponent p2 = ca dx^2 + cb dx dy + cc dy^2 with dx = px - u, dy = py - v: the conic gradients
+            // are dp2 dx^2, dp2 dx dy, dp2 dy^2, and the mean gradients -(2 ca P + cb Q), -(cb P + 2 cc Q)
+            // are linear in P = sum dp2 dx and Q = sum dp2 dy, which are reduced instead (the splat stage
+            // applies the conic once per splat)
+            const float2 P = mul2(dp2, f2(dx)), Q = mul2(dp2, dy);
+            const float2 gca = mul2(P, f2(dx)), gcb = mul2(P, dy), gcc = mul2(Q, dy);
             // both pixels' contributions of this splat (a pixel that does not take it adds zero)
             auto sum2 = [](float2 x) { return x.x + x.y; };
-            float v[16] = {sum2(gu), sum2(gv), sum2(gca), sum2(gcb), sum2(gcc), sum2(gon), sum2(gop), sum2(gr),
+            float v[16] = {sum2(P), sum2(Q), sum2(gca), sum2(gcb), sum2(gcc), sum2(gon), sum2(gop), sum2(gr),
                            sum2(gg), sum2(gb), DEPTH ? sum2(gz) : 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const float sum = warp_reduce_scatter16(v, lane);
             const int kk = (lane >> 1) & 15;
@@ -321,7 +323,8 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
     for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
         if (rect[m].x == 0xffffffffu) continue;  // culled
         const float* gs = sgrad + 12 * (int64_t)m;
-        const float gu = gs[0], gv = gs[1], gca = gs[2], gcb = gs[3], gcc = gs[4], gon = gs[5], gop = gs[6];
+        // gs: sum dp2 dx, sum dp2 dy, the three conic gradients, the two opacity gradients, colour, depth
+        const float sP = gs[0], sQ = gs[1], gca = gs[2], gcb = gs[3], gcc = gs[4], gon = gs[5], gop = gs[6];
         const float gz = gs[10];   // expected-depth channel: d L / d (view depth of the mean)
         const float grgb[3] = {gs[7], gs[8], gs[9]};
         const int k = find_cam(cut_offsets, n_cams, m);
@@ -387,6 +390,8 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         const float iD = 1.0f / D;
         const float comp = o.aa_compensate ? sqrtf(fmaxf(0.0f, det * iD)) : 1.0f;
         const float ca = cf * iD * KH, cb = bb * iD * KL, cq = af * iD * KH;
+        // mean (pixel-space) gradients from the reduced sums
+        const float gu = -fmaf(2.0f * ca, sP, cb * sQ), gv = -fmaf(cb, sP, 2.0f * cq * sQ);
         // ---- opacities
         const float on = h.opacity[n], op = use_p ? h.opacity[p] : 0.0f;
         const float d_on = gon * comp, d_op = gop * comp;
