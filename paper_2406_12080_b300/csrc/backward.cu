@@ -39,33 +39,53 @@ __device__ __forceinline__ float alpha_prime_grad(float ap, float K) {
     return __fdividef(ex2_approx(lg2_approx(1.0f - ap) * (__fdividef(1.0f, K) - 1.0f)), K);
 }
 
-// Warp reduce-scatter of 16 per-lane values (the last 6 are zero padding): after it, lanes 2k and
-// 2k+1 both hold the warp-wide sum of value k.  16 shuffles instead of 16 x 5.
-__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
+// Warp reduce-scatter of the per-lane gradient values of one splat: NV = 10 values (NV = 11 is done
+// as 12 with a zero).  Each level halves the values a lane carries by exchanging half of them with
+// the partner lane and adding; values left over at an odd count are reduced whole.  Afterwards the
+// warp-wide sum of value k is in the lane returned by the caller's write step: *k_out is the value
+// this lane writes (-1: none).  10 values: 14 shuffles; 12 values: 15.
+template <int NV>
+__device__ __forceinline__ float warp_reduce_scatter(const float* v, int lane, int* k_out) {
+    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+    auto xchg = [&](float lo, float hi, int off, bool upper) {
+        const float send = upper ? lo : hi, keep = upper ? hi : lo;
+        return keep + __shfl_xor_sync(0xffffffffu, send, off);
+    };
+    float y0, y1;
+    if (NV == 10) {
+        float w[5];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const bool hi = lane & 16;
-        const float send = hi ? v[i] : v[8 + i], keep = hi ? v[8 + i] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
+        for (int i = 0; i < 5; ++i) w[i] = xchg(v[i], v[5 + i], 16, b4);   // value 5 b4 + i
+        const float x0 = xchg(w[0], w[2], 8, b3);                           // 5 b4 + 2 b3
+        const float x1 = xchg(w[1], w[3], 8, b3);                           // 5 b4 + 2 b3 + 1
+        const float x2 = w[4] + __shfl_xor_sync(0xffffffffu, w[4], 8);      // 5 b4 + 4
+        y0 = xchg(x0, x1, 4, b2);                                           // 5 b4 + 2 b3 + b2
+        y1 = x2 + __shfl_xor_sync(0xffffffffu, x2, 4);
+    } else {
+        float w[6];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool hi = lane & 8;
-        const float send = hi ? v[i] : v[4 + i], keep = hi ? v[4 + i] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
+        for (int i = 0; i < 6; ++i) w[i] = xchg(v[i], i + 6 < NV ? v[6 + i] : 0.0f, 16, b4);   // 6 b4 + i
+        float x[3];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool hi = lane & 4;
-        const float send = hi ? v[i] : v[2 + i], keep = hi ? v[2 + i] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        for (int i = 0; i < 3; ++i) x[i] = xchg(w[i], w[3 + i], 8, b3);     // 6 b4 + 3 b3 + i
+        y0 = xchg(x[0], x[1], 4, b2);                                       // 6 b4 + 3 b3 + b2
+        y1 = x[2] + __shfl_xor_sync(0xffffffffu, x[2], 4);                  // 6 b4 + 3 b3 + 2
     }
-    {
-        const bool hi = lane & 2;
-        const float send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
+    y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
+    int k = -1;
+    float val = 0.0f;
+    if (NV == 10) {
+        if ((lane & 3) == 0) { k = 5 * b4 + 2 * b3 + b2; val = y0; }
+        else if ((lane & 15) == 1) { k = 5 * b4 + 4; val = y1; }
+    } else {
+        if ((lane & 3) == 0) { k = 6 * b4 + 3 * b3 + b2; val = y0; }
+        else if ((lane & 7) == 1) { k = 6 * b4 + 3 * b3 + 2; val = y1; }
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    *k_out = k < NV ? k : -1;
+    return val;
 }
 
 }  // namespace
@@ -293,11 +313,11 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
             const float2 gca = mul2(P, f2(dx)), gcb = mul2(P, dy), gcc = mul2(Q, dy);
             // both pixels' contributions of this splat (a pixel that does not take it adds zero)
             auto sum2 = [](float2 x) { return x.x + x.y; };
-            float v[16] = {sum2(P), sum2(Q), sum2(gca), sum2(gcb), sum2(gcc), sum2(gon), sum2(gop), sum2(gr),
-                           sum2(gg), sum2(gb), DEPTH ? sum2(gz) : 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const float sum = warp_reduce_scatter16(v, lane);
-            const int kk = (lane >> 1) & 15;
-            if (!(lane & 1) && kk < (DEPTH ? 11 : 10)) atomicAdd(sgrad + 12 * (int64_t)s_id[j] + kk, sum);
+            const float v[11] = {sum2(P), sum2(Q), sum2(gca), sum2(gcb), sum2(gcc), sum2(gon), sum2(gop), sum2(gr),
+                                 sum2(gg), sum2(gb), DEPTH ? sum2(gz) : 0.f};
+            int kk;
+            const float sum = warp_reduce_scatter<DEPTH ? 11 : 10>(v, lane, &kk);
+            if (kk >= 0) atomicAdd(sgrad + 12 * (int64_t)s_id[j] + kk, sum);
           }
         }
     }
