@@ -39,7 +39,8 @@ REF_BUDGET_S = 120.0
 #   dx, dy (2 FADD); exponent h = fma(ca, dx, cb dy), g = (cc dy) dy, p2 = fma(dx, h, g) (3 FMUL + 2 FFMA);
 #   alpha_n = min(clamp, o_n G) (FMUL + FMNMX); floor test (FSETP); T (1 - alpha) (FADD + FMUL); stop test
 #   (FSETP); w = alpha T (FMUL); colour (3 FFMA)  -> 22 flops (FFMA = 2) plus one MUFU (ex2).
-#   With t != 0: o_p G, min, 1 - ap, 1 + sqrt, divide, 1 - t, (1 - t) alpha_n, fma(t, a', .) -> +10 flops.
+#   With t != 0 (Eq. alphap, K = 2): o_p G, min, 1 - ap, 1 + sqrt, ap x reciprocal, 1 - t, (1 - t) alpha_n,
+#   fma(t, a', .) -> +10 flops plus two MUFU (sqrt, reciprocal); counted per evaluation of such a splat.
 FLOPS_PER_EVAL = 22
 FLOPS_PER_EVAL_T = 10
 # DRAM bytes (read + write) of one launch of the blend's main kernel at the 1080p corridor frame
@@ -305,6 +306,7 @@ def run_ours(args, rank, world, local):
         fwd_stages = {k: v / n_prof for k, v in stage_acc.items() if v > 0}
         st = dict(h3dgs.h3dgs_get_stats(ctx.ctx))
         st["n_evals"], st["n_evals_tpass"] = st_counts["n_evals"], st_counts["n_evals_tpass"]
+        st["n_evals_interp"] = st_counts["n_evals_interp"]
 
         # ---- fwd + bwd views/s
         grads = {k: torch.zeros_like(getattr(hier, k)) for k in ("mean", "scale", "rot", "opacity", "sh")}
@@ -460,8 +462,8 @@ def run_ours(args, rank, world, local):
     # ---- roofline of the dominant kernel: the blend's main kernel (FP32 issue-bound)
     peaks = measured_peaks()
     queue_ms = fwd_stages.get("blend_queue", 0.0)   # events around that kernel alone, on its stream
-    n_evals = int(st["n_evals"])
-    flops = n_evals * FLOPS_PER_EVAL
+    n_evals, n_evals_i = int(st["n_evals"]), int(st["n_evals_interp"])
+    flops = n_evals * FLOPS_PER_EVAL + n_evals_i * FLOPS_PER_EVAL_T
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     fp32_peak_tflops = 148 * 128 * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (queue_ms * 1e-3) / 1e12 if queue_ms > 0 else None
@@ -470,8 +472,10 @@ def run_ours(args, rank, world, local):
                 "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk == 384) else None,
                 "kernel_ms": queue_ms,
                 "peak_note": "148 SMs x 128 FP32 lanes x 2 (FFMA) x max SM clock from MEASURED_PEAKS.json",
-                "work_note": f"{FLOPS_PER_EVAL} FP32 flops per main-pass (pixel, splat) evaluation x {n_evals}; the "
-                             f"{int(st['n_evals_tpass'])} transmittance-pass evaluations of split tiles are not counted",
+                "work_note": f"{FLOPS_PER_EVAL} FP32 flops per main-pass (pixel, splat) evaluation x {n_evals}, "
+                             f"+{FLOPS_PER_EVAL_T} for the {n_evals_i} of them on splats with an interpolated parent "
+                             f"(t != 0: the transition alpha of Eq. alphap); the {int(st['n_evals_tpass'])} "
+                             f"transmittance-pass evaluations of split tiles are not counted",
                 "traffic_note": "DRAM read + write of one launch from an ncu capture of this kernel at this workload"}
     if calib:
         roofline["peak_calibrated"] = calib["fp32_tflops"]
@@ -497,7 +501,7 @@ def run_ours(args, rank, world, local):
     # frame-level roofline: the time every stage would take at its binding peak (HBM stages at the
     # measured copy bandwidth, the blend at the unit-count FP32 peak), summed, over the frame time
     ideal_ms = sum(b / (hbm * 1e9) * 1e3 for b in algo_bytes.values())
-    ideal_ms += FLOPS_PER_EVAL * n_evals / (fp32_peak_tflops * 1e12) * 1e3
+    ideal_ms += flops / (fp32_peak_tflops * 1e12) * 1e3
     frame_ms = total_ms / args.steps
     frame_roofline = {"frac": ideal_ms / frame_ms, "ideal_ms": ideal_ms, "frame_ms": frame_ms,
                       "note": "sum over cut, preprocess, sorts, duplication (algorithmic bytes at the measured HBM "
@@ -515,7 +519,7 @@ def run_ours(args, rank, world, local):
         "gaussians_per_s": M * value,
         "fwd_bwd": {"value": fb_value, "unit": "views/s", "ms_per_view": fb_ms / args.steps},
         "blend": {"items": int(st["n_items"]), "tile_chunk": int(opts.blend_chunk), "evals_main": n_evals,
-                  "evals_tpass": int(st["n_evals_tpass"])},
+                  "evals_main_interpolated": n_evals_i, "evals_tpass": int(st["n_evals_tpass"])},
         "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": 76 * len(cams),
                 "d2h_bytes_per_step": npix * 4, "serial_value": e2e_serial_value,
                 "note": "C-ABI calls from Python (not graph-captured), host clock; camera struct in, the whole "

@@ -121,6 +121,8 @@ typedef struct {
     int64_t n_evals_tpass; /* extra evaluations of the transmittance pass of split tiles
                              (likewise)                                          */
     int64_t n_items;      /* blend work items (tiles, split tiles count once per chunk) */
+    int64_t n_evals_interp; /* main-pass evaluations of splats with an interpolated parent
+                               (t != 0, Eq. alphap evaluated too; profiling level 2, else 0) */
 } h3dgs_stats;
 
 /* Per-stage device times of the most recent select_cut / render / render_backward, in ms,

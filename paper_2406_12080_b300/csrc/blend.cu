@@ -222,7 +222,7 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
                                             float clampv, float afloor, float tmin, float4* s_a, float4* s_b,
                                             float4* s_c, uint32_t* s_m, float* s_d, float4* s_box, float2& T, float2& C0,
                                             float2& C1, float2& C2, float2& Dp, int2& last, bool& done0, bool& done1,
-                                            unsigned int& evals) {
+                                            unsigned int& evals, unsigned int& evals_i) {
     constexpr int NT2 = TW * TH / 2, NW = NT2 / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int b0 = begin; b0 < end; b0 += NT2) {
@@ -268,7 +268,10 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
                 while (bits) {
                     const int j = base + __ffs(bits) - 1;
                     bits &= bits - 1;
-                    if (COUNT) evals += (unsigned)!done0 + (unsigned)!done1;
+                    if (COUNT) {
+                        evals += (unsigned)!done0 + (unsigned)!done1;
+                        if (s_b[j].w != 0.0f) evals_i += (unsigned)!done0 + (unsigned)!done1;
+                    }
                     const float2 alpha = pair_alpha2(g.px, g.py, s_a[j], s_b[j], &s_c[j], clampv);
                     const bool live0 = !done0 && alpha.x >= afloor, live1 = !done1 && alpha.y >= afloor;
                     if (!__any_sync(0xffffffffu, live0 || live1)) continue;   // no pixel of the warp takes it
@@ -335,10 +338,10 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     __shared__ uint32_t s_m[NT2];
     __shared__ float s_d[DEPTH ? NT2 : 1];
     __shared__ float4 s_box[NT2 / 32];
-    __shared__ unsigned int s_evals[2];
+    __shared__ unsigned int s_evals[3];
     __shared__ uint32_t s_k;
     if (threadIdx.x == 0) s_k = atomicAdd(ticket, 1u);
-    if (threadIdx.x < 2) s_evals[threadIdx.x] = 0;
+    if (threadIdx.x < 3) s_evals[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t k = s_k;
     const uint32_t X = counts[1], Y = counts[2];
@@ -369,19 +372,25 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     }
     float2 C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0, Dp = C0;
     int2 last = make_int2(-1, -1);
-    unsigned int evals = 0;
+    unsigned int evals = 0, evals_i = 0;
     bool done0 = !g.in0 || T.x < o.t_min, done1 = !g.in1 || T.y < o.t_min;
     if (main_pass)
         blend_walk2<TW, TH, true, COUNT, DEPTH, SAVE>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
                                                       o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp, last,
-                                                      done0, done1, evals);
+                                                      done0, done1, evals, evals_i);
     else
         blend_walk2<TW, TH, false, COUNT, false, false>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
                                                         o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp,
-                                                        last, done0, done1, evals);
+                                                        last, done0, done1, evals, evals_i);
     if (COUNT) {
-        for (int off = 16; off > 0; off >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, off);
-        if (lane == 0) atomicAdd(&s_evals[main_pass ? 0 : 1], evals);
+        for (int off = 16; off > 0; off >>= 1) {
+            evals += __shfl_down_sync(0xffffffffu, evals, off);
+            evals_i += __shfl_down_sync(0xffffffffu, evals_i, off);
+        }
+        if (lane == 0) {
+            atomicAdd(&s_evals[main_pass ? 0 : 1], evals);
+            if (main_pass) atomicAdd(&s_evals[2], evals_i);
+        }
     }
     if (role == 0) {
         // the product handed to the later chunks: 0 once the first chunk's walk stopped
@@ -410,7 +419,7 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     } else {
         __syncthreads();
     }
-    if (COUNT && threadIdx.x < 2 && s_evals[threadIdx.x])
+    if (COUNT && threadIdx.x < 3 && s_evals[threadIdx.x])
         atomicAdd(n_evals + threadIdx.x, (unsigned long long)s_evals[threadIdx.x]);
     if (role == 0) return;
     if (nch > 1) {
