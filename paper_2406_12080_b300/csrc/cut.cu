@@ -218,11 +218,11 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_write_kernel(const float4* __re
 // [b CS_TILE, (b + 1) CS_TILE), CS_IPT per thread at stride CUT_BLOCK (coalesced), counts the
 // selected ones per (step, warp), obtains the count of all earlier blocks and writes its ids in
 // ascending order with their weights.  The last block writes the offsets and the total.
-constexpr int CS_IPT = 8;
+constexpr int CS_IPT = 10;   // with at most 6 blocks of 256 per SM a 2M-node scan is one wave (8..16 measured, 10 fastest)
 constexpr int CS_GRP = 2;   // nodes whose loads are in flight together (2 measured fastest of 1, 2, 4, 8)
 constexpr int CS_TILE = CUT_BLOCK * CS_IPT;
 
-__global__ void __launch_bounds__(CUT_BLOCK) cut_single_kernel(const float4* __restrict__ rec, int64_t n,
+__global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* __restrict__ rec, int64_t n,
                                                                const h3dgs_camera raw, int64_t capacity,
                                                                int32_t* __restrict__ cut_ids, float* __restrict__ cut_t,
                                                                int64_t* __restrict__ cut_offsets,
@@ -231,6 +231,8 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_single_kernel(const float4* __r
     __shared__ uint32_t s_ticket;
     __shared__ unsigned long long s_slot, s_warp[CUT_BLOCK / 32];
     __shared__ uint32_t s_cnt[CS_IPT][CUT_BLOCK / 32];
+    __shared__ uint32_t s_word[CS_IPT][CUT_BLOCK / 32];   // per (step, warp): ballot of the selected nodes
+    __shared__ float s_tw[CS_IPT][CUT_BLOCK];             // per (step, thread): the node's parent weight
     const uint32_t b = lb_ticket(lb, &s_ticket);
     const int64_t base = (int64_t)b * CS_TILE;
     if (base >= n) return;
@@ -239,8 +241,6 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_single_kernel(const float4* __r
     cam.f = fmaxf(raw.fx, raw.fy);
     cam.tau = raw.tau;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t word[CS_IPT];
-    float tw[CS_IPT];
     // CS_GRP nodes at a time: their records are all requested, then their parents' records, so a
     // thread keeps 2 CS_GRP loads in flight instead of one dependent pair
 #pragma unroll
@@ -264,14 +264,18 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_single_kernel(const float4* __r
             const int64_t v = base + q * CUT_BLOCK + threadIdx.x;
             const int32_t p = __float_as_int(lo[k].w);
             bool sel = false;
-            tw[q] = 0.0f;
+            float tw = 0.0f;
             if (v < n) {
                 float en, ep;
                 sel = cut_test(cam, lo[k], hi[k], plo[k], phi[k], p >= 0, &en, &ep);
-                if (sel && p >= 0) tw[q] = parent_weight(cam.tau, en, ep);
+                if (sel && p >= 0) tw = parent_weight(cam.tau, en, ep);
             }
-            word[q] = __ballot_sync(0xffffffffu, sel);
-            if (lane == 0) s_cnt[q][warp] = __popc(word[q]);
+            const uint32_t word = __ballot_sync(0xffffffffu, sel);
+            s_tw[q][threadIdx.x] = tw;
+            if (lane == 0) {
+                s_cnt[q][warp] = __popc(word);
+                s_word[q][warp] = word;
+            }
         }
     }
     __syncthreads();
@@ -285,11 +289,12 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_single_kernel(const float4* __r
     const uint32_t lmask = (1u << lane) - 1u;
 #pragma unroll
     for (int q = 0; q < CS_IPT; ++q) {
-        if ((word[q] >> lane) & 1u) {
-            const int64_t pos = (int64_t)(prefix + s_cnt[q][warp]) + __popc(word[q] & lmask);
+        const uint32_t word = s_word[q][warp];
+        if ((word >> lane) & 1u) {
+            const int64_t pos = (int64_t)(prefix + s_cnt[q][warp]) + __popc(word & lmask);
             if (pos < capacity) {
                 cut_ids[pos] = (int32_t)(base + q * CUT_BLOCK + threadIdx.x);
-                if (cut_t) cut_t[pos] = tw[q];
+                if (cut_t) cut_t[pos] = s_tw[q][threadIdx.x];
             }
         }
     }
@@ -301,6 +306,10 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_single_kernel(const float4* __r
         cut_offsets[1] = total < capacity ? total : capacity;
         if (total > capacity) atomicOr(flags, FLAG_CUT_TRUNCATED);
     }
+}
+
+size_t cut_single_work_words(int64_t n) {
+    return LB_HEADER_WORDS + 2 * (size_t)((n + CS_TILE - 1) / CS_TILE);
 }
 
 cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const CutWork& w, int32_t* cut_ids,

@@ -290,6 +290,8 @@ struct CutWork {
     int64_t lb_words;
     h3dgs_camera cam0;       // single-camera pass: the raw camera (its derived values are computed in the kernel)
 };
+// Look-back words the single-camera cut needs for n nodes.
+size_t cut_single_work_words(int64_t n);
 cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const CutWork& w, int32_t* cut_ids,
                        float* cut_t, int64_t* cut_offsets, int64_t capacity, uint32_t* flags, cudaStream_t s);
 
