@@ -128,6 +128,8 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __re
                                                                 int32_t* __restrict__ tile_split,
                                                                 uint32_t* __restrict__ counts /* items, X, Y, Z */,
                                                                 Lookback lb) {
+    griddep_launch_dependents();
+    griddep_wait();
     __shared__ uint32_t s_ticket;
     __shared__ unsigned long long s_slot, s_warp[PL_THREADS / 32];
     const uint32_t b = lb_ticket(lb, &s_ticket);
@@ -333,6 +335,8 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
                                                                   int32_t* __restrict__ n_contrib,
                                                                   unsigned long long* __restrict__ n_evals,
                                                                   uint32_t* __restrict__ flags) {
+    griddep_launch_dependents();
+    griddep_wait();
     constexpr int NT = TW * TH, NT2 = NT / 2;
     __shared__ float4 s_a[NT2], s_b[NT2], s_c[NT2];
     __shared__ uint32_t s_m[NT2];
@@ -473,6 +477,8 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
                                                                 const float* __restrict__ exposure,
                                                                 float* __restrict__ T_final,
                                                                 int32_t* __restrict__ n_contrib) {
+    griddep_launch_dependents();
+    griddep_wait();
     constexpr int NT = TW * TH;
     const uint32_t Z = counts[3];
     for (uint32_t z = blockIdx.x; z < Z; z += gridDim.x) {
@@ -545,10 +551,10 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     if (!a.pre_zeroed) e = cudaMemsetAsync(a.work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)pblocks), s);
     if (e != cudaSuccess) return e;
     Lookback lb{reinterpret_cast<unsigned long long*>(a.work + LB_HEADER_WORDS), a.work, a.flags};
-    blend_plan_kernel<<<(unsigned)pblocks, PL_THREADS, 0, s>>>(a.ranges, a.n_tiles, a.chunk, a.tile_item0, a.tile_nch,
-                                                               a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons,
-                                                               a.tile_split, a.n_items,
-                                                               lb);
+    e = launch_dependent(blend_plan_kernel, dim3((unsigned)pblocks), dim3(PL_THREADS), s, a.ranges, a.n_tiles, a.chunk,
+                         a.tile_item0, a.tile_nch, a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons, a.tile_split,
+                         a.n_items, lb);
+    if (e != cudaSuccess) return e;
     Scratch sc{a.scratch_Tc, a.scratch_C, a.scratch_Tend, a.scratch_last, a.scratch_D};
     if (!a.pre_zeroed) e = cudaMemsetAsync(a.queue_sync, 0, sizeof(uint32_t) * (size_t)(a.n_tiles + 1), s);
     if (e != cudaSuccess) return e;
@@ -557,7 +563,7 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     // combine: one wave of blocks (a few per SM) over the split tiles
     const unsigned tg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.n_tiles, 8 * (int64_t)a.num_sms));
 #define QUEUE(TWV, THV, CNT, DEP, SAV)                                                                                \
-    blend_queue_kernel<TWV, THV, CNT, DEP, SAV><<<gq, TWV * THV / 2, 0, s>>>(                                         \
+    e = launch_dependent(blend_queue_kernel<TWV, THV, CNT, DEP, SAV>, dim3(gq), dim3(TWV * THV / 2), s,                \
         a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.items, a.q_prod, a.q_single, a.q_cons, a.n_items,         \
         a.tile_item0, a.tile_nch, a.chunk, sc, a.queue_sync, a.queue_sync + 1, a.images, a.depth, a.exposure,         \
         a.T_final, a.n_contrib, a.n_evals, a.flags)
@@ -571,10 +577,11 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
         } else {                                                                                                      \
             if (save) QUEUE(TWV, THV, false, false, true); else QUEUE(TWV, THV, false, false, false);                 \
         }                                                                                                             \
+        if (e != cudaSuccess) break;                                                                                  \
         if (a.ev_queue) cudaEventRecord(a.ev_queue[1], s);                                                            \
-        blend_combine_kernel<TWV, THV><<<tg, TWV * THV, 0, s>>>(a.cams, a.n_cams, a.o, a.n_items, a.tile_split,       \
-                                                                a.tile_item0, a.tile_nch, sc, a.images, a.depth,      \
-                                                                a.exposure, a.T_final, a.n_contrib);                  \
+        e = launch_dependent(blend_combine_kernel<TWV, THV>, dim3(tg), dim3(TWV * THV), s, a.cams, a.n_cams, a.o,     \
+                             a.n_items, a.tile_split, a.tile_item0, a.tile_nch, sc, a.images, a.depth, a.exposure,    \
+                             a.T_final, a.n_contrib);                                                                 \
     } while (0)
     const DevOpts& o = a.o;
     const bool save = a.T_final && a.n_contrib;   // per-pixel state for the adjoint (evaluations are not
@@ -587,6 +594,7 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     else return cudaErrorInvalidValue;
 #undef BL
 #undef QUEUE
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -36,6 +36,8 @@ cudaError_t launch_pack_records(const h3dgs_hierarchy& h, float4* rec, cudaStrea
 //   c_j = -(R_0j T_0 + R_1j T_1 + R_2j T_2)  as -fmaf(R_2j, T_2, fmaf(R_1j, T_1, R_0j * T_0)),
 //   f = max(fx, fy),  limx = (0.65 W) / fx,  limy = (0.65 H) / fy.
 __global__ void camera_setup_kernel(CamBatch b, DevCam* __restrict__ out) {
+    griddep_launch_dependents();
+    griddep_wait();
     const int i = threadIdx.x;
     if (i >= b.count) return;
     const h3dgs_camera& c = b.cam[i];
@@ -56,8 +58,7 @@ __global__ void camera_setup_kernel(CamBatch b, DevCam* __restrict__ out) {
 }
 
 cudaError_t launch_camera_setup(const CamBatch& b, const DevOpts*, DevCam* cams, cudaStream_t s) {
-    camera_setup_kernel<<<1, CAM_BATCH, 0, s>>>(b, cams);
-    return cudaGetLastError();
+    return launch_dependent(camera_setup_kernel, dim3(1), dim3(CAM_BATCH), s, b, cams);
 }
 
 // ------------------------------------------------------------------------------------ a1 + a2

@@ -93,6 +93,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
                                                          const float* __restrict__ cut_t,
                                                          const int64_t* __restrict__ cut_offsets, int64_t cap,
                                                          SplatBufs sb, uint32_t* __restrict__ flags) {
+    griddep_launch_dependents();
+    griddep_wait();
     __shared__ uint32_t s_hist[4][256];   // digit histograms of the depth keys, for the depth sort
     if (sb.depth_hist) {
         for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0;
@@ -295,8 +297,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
 cudaError_t launch_preprocess(const DevHier& h, const DevCam* cams, int n_cams, const DevOpts& o,
                               const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets, int64_t cap,
                               const SplatBufs& sb, uint32_t* flags, int grid, cudaStream_t s) {
-    preprocess_kernel<<<grid, 256, 0, s>>>(h, cams, n_cams, o, cut_ids, cut_t, cut_offsets, cap, sb, flags);
-    return cudaGetLastError();
+    return launch_dependent(preprocess_kernel, dim3(grid), dim3(256), s, h, cams, n_cams, o, cut_ids, cut_t, cut_offsets,
+                            cap, sb, flags);
 }
 
 // ---------------------------------------------------------------------------------- export (a3)

@@ -275,6 +275,8 @@ size_t radix_work_words(int64_t n_cap) {
 }
 
 __global__ void reset_kernel(ResetList r) {
+    griddep_launch_dependents();
+    griddep_wait();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     for (int k = 0; k < r.n; ++k) {
         uint32_t* p = r.p[k];
@@ -291,7 +293,8 @@ __global__ void reset_kernel(ResetList r) {
 
 cudaError_t launch_reset(const ResetList& r, int num_sms, cudaStream_t s) {
     if (r.n < 0 || r.n > 8) return cudaErrorInvalidValue;
-    reset_kernel<<<num_sms * 4, 256, 0, s>>>(r);
+    const cudaError_t e = launch_dependent(reset_kernel, dim3(num_sms * 4), dim3(256), s, r);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -359,6 +362,8 @@ __global__ void __launch_bounds__(PO_THREADS) pair_offsets_kernel(const uint32_t
                                                                   uint32_t* __restrict__ pair_off,
                                                                   uint32_t* __restrict__ seg_start, uint32_t seg_cap,
                                                                   uint32_t* __restrict__ total, Lookback lb) {
+    griddep_launch_dependents();
+    griddep_wait();
     __shared__ uint32_t s_ticket;
     __shared__ unsigned long long s_slot, s_warp[PO_THREADS / 32];
     const uint32_t b = lb_ticket(lb, &s_ticket);
@@ -408,9 +413,10 @@ cudaError_t launch_pair_offsets(const uint32_t* tiles, const uint32_t* order, co
         cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)blocks), s);
         if (e != cudaSuccess) return e;
     }
-    pair_offsets_kernel<<<(unsigned)blocks, PO_THREADS, 0, s>>>(tiles, order, n_dev, pair_off, seg_start,
-                                                                (uint32_t)std::min<int64_t>(seg_cap, 0xffffffffLL),
-                                                                total, lb);
+    const cudaError_t e = launch_dependent(pair_offsets_kernel, dim3((unsigned)blocks), dim3(PO_THREADS), s, tiles, order,
+                                           n_dev, pair_off, seg_start,
+                                           (uint32_t)std::min<int64_t>(seg_cap, 0xffffffffLL), total, lb);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -453,6 +459,8 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const DevCam* __restrict
                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                         uint32_t* __restrict__ hist, int hist_passes,
                                                         uint32_t* __restrict__ flags) {
+    griddep_launch_dependents();
+    griddep_wait();
     __shared__ uint32_t s_off[DUP_SEG + 1], s_m[DUP_SEG + 1], s_xy[DUP_SEG + 1], s_wtx[DUP_SEG + 1],
         s_tb[DUP_SEG + 1];
     __shared__ uint32_t s_hist[4][256];   // digit histograms of the tile keys for the tile sort
@@ -515,10 +523,9 @@ cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_
                              uint32_t* flags, cudaStream_t s) {
     const int64_t blocks = std::max<int64_t>(1, (cap_pairs + DUP_SEG - 1) / DUP_SEG);
     if (hist_passes < 0 || hist_passes > 4) return cudaErrorInvalidValue;
-    duplicate_kernel<<<(unsigned)blocks, 256, 0, s>>>(cams, n_cams, cut_offsets, sb, order, n_order, pair_off,
-                                                      seg_start, n_pairs, cap_pairs, n_pairs_kept, keys, vals, hist,
-                                                      hist_passes, flags);
-    return cudaGetLastError();
+    return launch_dependent(duplicate_kernel, dim3((unsigned)blocks), dim3(256), s, cams, n_cams, cut_offsets, sb, order,
+                            n_order, pair_off, seg_start, n_pairs, cap_pairs, n_pairs_kept, keys, vals, hist,
+                            hist_passes, flags);
 }
 
 // ------------------------------------------------------------------------------ ranges
@@ -527,6 +534,8 @@ cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_
 // range they were cleared to).
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev,
                               uint32_t n_tiles, int2* __restrict__ ranges) {
+    griddep_launch_dependents();
+    griddep_wait();
     const uint32_t n = *n_dev;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t k = __ldg(keys + i);
@@ -538,7 +547,8 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t*
 
 cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n_tiles, int2* ranges, int grid,
                           cudaStream_t s) {
-    ranges_kernel<<<grid, 256, 0, s>>>(keys, n_dev, (uint32_t)n_tiles, ranges);
+    const cudaError_t e = launch_dependent(ranges_kernel, dim3(grid), dim3(256), s, keys, n_dev, (uint32_t)n_tiles, ranges);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
