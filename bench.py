@@ -916,7 +916,7 @@ def run_reference(args, rank, world):
     cam = scene.cameras[0]
     # each step is one full frame; the run stops early once REF_BUDGET_S of timed work is done so that
     # the default --steps finishes within a few minutes (the steps actually timed are reported)
-    for _ in range(min(args.warmup, 1)):
+    for _ in range(args.warmup):
         oracle.render(cam, h, oracle.Opts())
     t0 = time.perf_counter()
     done = 0
@@ -929,7 +929,7 @@ def run_reference(args, rank, world):
     v = done / dt
     cores = oracle.num_threads()
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": world,
-            "steps": done, "steps_requested": args.steps, "warmup": min(args.warmup, 1),
+            "steps": done, "steps_requested": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / done,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"street corridor, {args.n_leaves} leaves, 1920x1080, tau={args.tau:g} px"},
