@@ -45,7 +45,7 @@ FLOPS_PER_EVAL = 22
 FLOPS_PER_EVAL_T = 10
 # DRAM bytes (read + write) of one launch of the blend's main kernel at the 1080p corridor frame
 # (16x16 tiles, chunk 384), from an ncu capture of the current kernel; None once the kernel changes
-BLEND_TRAFFIC_BYTES = 28.864e6 + 3.123e6
+BLEND_TRAFFIC_BYTES = 28.85e6 + 3.14e6
 
 
 def parse():

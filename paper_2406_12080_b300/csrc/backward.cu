@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
                                                                      const int2* __restrict__ items,
                                                                      const uint32_t* __restrict__ n_items,
                                                                      const int32_t* __restrict__ tile_item0,
-                                                                     const int32_t* __restrict__ tile_nch, int chunk,
+                                                                     const int32_t* __restrict__ tile_nch,
                                                                      const float* __restrict__ scC,
                                                                      const float* __restrict__ scTend,
                                                                      const int32_t* __restrict__ sclast,
@@ -571,7 +571,7 @@ cudaError_t launch_backward(const DevHier& h, const BlendArgs& a, const int32_t*
         const unsigned ig = (unsigned)a.item_cap;
 #define BWD(TWV, THV, DEP)                                                                                          \
     backward_blend_kernel<TWV, THV, DEP><<<ig, TWV * THV / 2, 0, s>>>(                                              \
-        a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.items, a.n_items, a.tile_item0, a.tile_nch, a.chunk,      \
+        a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.items, a.n_items, a.tile_item0, a.tile_nch,               \
         a.scratch_C, a.scratch_Tend, a.scratch_last, a.T_final, a.n_contrib, dL, dLdepth, a.exposure, a.scratch_D,    \
         splat_grad)
 #define BW(TWV, THV)                                                                                                \

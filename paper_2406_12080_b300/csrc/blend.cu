@@ -325,8 +325,8 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
                                                                   const uint32_t* __restrict__ q_cons,
                                                                   const uint32_t* __restrict__ counts,
                                                                   const int32_t* __restrict__ tile_item0,
-                                                                  const int32_t* __restrict__ tile_nch, int chunk,
-                                                                  Scratch sc, uint32_t* __restrict__ ticket,
+                                                                  const int32_t* __restrict__ tile_nch, Scratch sc,
+                                                                  uint32_t* __restrict__ ticket,
                                                                   uint32_t* __restrict__ tile_done,
                                                                   float* __restrict__ images,
                                                                   float* __restrict__ depth,
@@ -565,7 +565,7 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
 #define QUEUE(TWV, THV, CNT, DEP, SAV)                                                                                \
     e = launch_dependent(blend_queue_kernel<TWV, THV, CNT, DEP, SAV>, dim3(gq), dim3(TWV * THV / 2), s,                \
         a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.items, a.q_prod, a.q_single, a.q_cons, a.n_items,         \
-        a.tile_item0, a.tile_nch, a.chunk, sc, a.queue_sync, a.queue_sync + 1, a.images, a.depth, a.exposure,         \
+        a.tile_item0, a.tile_nch, sc, a.queue_sync, a.queue_sync + 1, a.images, a.depth, a.exposure,                  \
         a.T_final, a.n_contrib, a.n_evals, a.flags)
 #define BL(TWV, THV)                                                                                                  \
     do {                                                                                                              \
