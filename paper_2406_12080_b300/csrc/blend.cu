@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __
         int last = 0;
         // every chunk's scratch is read whether or not it is used, so the loads of successive chunks
         // do not wait on each other through the running transmittance
-#pragma unroll 4
+#pragma unroll 8
         for (int c = 0; c < nch; ++c) {
             const int64_t slot = (i0 + c) * NT + threadIdx.x;
             const float c0 = sc.C[3 * slot + 0], c1 = sc.C[3 * slot + 1], c2 = sc.C[3 * slot + 2];
