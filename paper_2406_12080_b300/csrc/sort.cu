@@ -37,6 +37,7 @@ constexpr unsigned long long ST_INC = 2ull << 62;   // look-back word: count of 
 constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
 constexpr int OS_SPIN_LIMIT = 1 << 20;       // re-reads of one look-back word before giving up
 constexpr int OS_LOOKBACK = 8;               // look-back words loaded per step
+constexpr int OS_GROUP = 16;                 // tiles per group of the grouped prefix (one-wave passes)
 constexpr int HG_IPT = 4;                    // keys per thread of the histogram kernel
 
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
@@ -46,6 +47,16 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
 }
 __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -139,6 +150,8 @@ __global__ void __launch_bounds__(OS_THREADS, 3) radix_onesweep_kernel(const uin
                                                                     const uint32_t* __restrict__ n_out, int shift,
                                                                     int drop, const uint32_t* __restrict__ hist,
                                                                     unsigned long long* __restrict__ status,
+                                                                    uint32_t* __restrict__ gtot,
+                                                                    uint32_t* __restrict__ gcnt,
                                                                     uint32_t* __restrict__ ticket,
                                                                     uint32_t* __restrict__ flags) {
     __shared__ uint32_t s_wcnt[OS_WARPS][256];
@@ -209,40 +222,83 @@ __global__ void __launch_bounds__(OS_THREADS, 3) radix_onesweep_kernel(const uin
     unsigned long long* st = status + (uint64_t)tile * 256;
     if (tile == 0) st_relaxed(st + d, ST_INC | cnt);
     else st_relaxed(st + d, ST_AGG | cnt);
-    const uint32_t lstart = block_exclusive_scan256(cnt, s_warp);
+    const uint32_t grp = tile / OS_GROUP;
+    if (gcnt) {   // grouped prefix: this tile's share of its group's digit totals
+        if (cnt) atomicAdd(gtot + (size_t)grp * 256 + d, cnt);
+        __threadfence();
+    }
+    const uint32_t lstart = block_exclusive_scan256(cnt, s_warp);   // (its barriers order the shares)
     s_lstart[d] = lstart;
     // global start of digit d over the whole input (exclusive scan of the pass histogram)
     const uint32_t gstart = block_exclusive_scan256(hist_d, s_warp);
-    // ---- decoupled look-back over earlier tiles for digit d: OS_LOOKBACK status words are loaded at
-    // once, then summed newest first until an inclusive one; a word not yet published is re-read
     unsigned long long excl = 0;
-    bool found = false;
-    for (int64_t j = (int64_t)tile - 1; j >= 0 && !found; j -= OS_LOOKBACK) {
-        unsigned long long v[OS_LOOKBACK];
+    if (gcnt) {
+        // ---- grouped prefix (every tile of the pass is resident, so all earlier tiles publish at about
+        // the same time): the digit totals of the complete earlier groups, then the counts of the
+        // earlier tiles of this group; all loads are independent, the waits are bounded
+        if (threadIdx.x == 0) atomicAdd(gcnt + grp, 1u);   // every share of this tile is in place
+        for (uint32_t g = threadIdx.x; g < grp; g += OS_THREADS) {
+            int spins = 0;
+            while (ld_acquire32(gcnt + g) < (uint32_t)OS_GROUP && spins < OS_SPIN_LIMIT)
+                if (++spins > 32) __nanosleep(64);
+            if (spins >= OS_SPIN_LIMIT) atomicOr(flags, FLAG_WAIT_TIMEOUT);   // result wrong, flagged
+        }
+        __syncthreads();
+        for (uint32_t g0 = 0; g0 < grp; g0 += 8) {
+            uint32_t v[8];
 #pragma unroll
-        for (int q = 0; q < OS_LOOKBACK; ++q) v[q] = (j - q >= 0) ? ld_relaxed(status + (uint64_t)(j - q) * 256 + d) : 0u;
+            for (int q = 0; q < 8; ++q) v[q] = g0 + q < grp ? ld_relaxed32(gtot + (size_t)(g0 + q) * 256 + d) : 0u;
 #pragma unroll
-        for (int q = 0; q < OS_LOOKBACK; ++q) {
-            if (found || j - q < 0) {
-                found = true;
-                continue;
-            }
+            for (int q = 0; q < 8; ++q) excl += v[q];
+        }
+        const uint32_t j0 = grp * OS_GROUP;
+        unsigned long long v[OS_GROUP - 1];
+#pragma unroll
+        for (int q = 0; q < OS_GROUP - 1; ++q) v[q] = j0 + q < tile ? ld_relaxed(status + (uint64_t)(j0 + q) * 256 + d) : 0u;
+#pragma unroll
+        for (int q = 0; q < OS_GROUP - 1; ++q) {
+            if (j0 + q >= tile) continue;
             unsigned long long x = v[q];
             int spins = 0;
             while ((x & (ST_AGG | ST_INC)) == 0 && spins < OS_SPIN_LIMIT) {
                 if (++spins > 32) __nanosleep(64);
-                x = ld_relaxed(status + (uint64_t)(j - q) * 256 + d);
+                x = ld_relaxed(status + (uint64_t)(j0 + q) * 256 + d);
             }
-            if ((x & (ST_AGG | ST_INC)) == 0) {   // gave up: the result is wrong, the flag says so
-                atomicOr(flags, FLAG_WAIT_TIMEOUT);
-                found = true;
-                continue;
-            }
-            excl += x & ST_VAL;
-            if (x & ST_INC) found = true;
+            if ((x & (ST_AGG | ST_INC)) == 0) atomicOr(flags, FLAG_WAIT_TIMEOUT);
+            else excl += x & ST_VAL;
         }
+    } else {
+        // ---- decoupled look-back over earlier tiles for digit d: OS_LOOKBACK status words are loaded
+        // at once, then summed newest first until an inclusive one; a word not yet published is re-read
+        bool found = false;
+        for (int64_t j = (int64_t)tile - 1; j >= 0 && !found; j -= OS_LOOKBACK) {
+            unsigned long long v[OS_LOOKBACK];
+#pragma unroll
+            for (int q = 0; q < OS_LOOKBACK; ++q)
+                v[q] = (j - q >= 0) ? ld_relaxed(status + (uint64_t)(j - q) * 256 + d) : 0u;
+#pragma unroll
+            for (int q = 0; q < OS_LOOKBACK; ++q) {
+                if (found || j - q < 0) {
+                    found = true;
+                    continue;
+                }
+                unsigned long long x = v[q];
+                int spins = 0;
+                while ((x & (ST_AGG | ST_INC)) == 0 && spins < OS_SPIN_LIMIT) {
+                    if (++spins > 32) __nanosleep(64);
+                    x = ld_relaxed(status + (uint64_t)(j - q) * 256 + d);
+                }
+                if ((x & (ST_AGG | ST_INC)) == 0) {   // gave up: the result is wrong, the flag says so
+                    atomicOr(flags, FLAG_WAIT_TIMEOUT);
+                    found = true;
+                    continue;
+                }
+                excl += x & ST_VAL;
+                if (x & ST_INC) found = true;
+            }
+        }
+        if (tile > 0) st_relaxed(st + d, ST_INC | (excl + cnt));
     }
-    if (tile > 0) st_relaxed(st + d, ST_INC | (excl + cnt));
     s_gdst[d] = (uint32_t)(gstart + excl);
     if (d == 255) s_cnt255 = cnt;
     __syncthreads();
@@ -269,9 +325,14 @@ __global__ void __launch_bounds__(OS_THREADS, 3) radix_onesweep_kernel(const uin
     }
 }
 
+// Workspace: header, the 64-bit look-back words [4 passes][tiles][256], then for the grouped prefix
+// [4 passes][groups][256] digit totals and [4 passes][groups] completion counters.
+static int64_t radix_max_tiles(int64_t n_cap) {
+    return std::max<int64_t>(1, (n_cap + OS_TILE_SMALL - 1) / OS_TILE_SMALL);
+}
 size_t radix_work_words(int64_t n_cap) {
-    const int64_t tiles = std::max<int64_t>(1, (n_cap + OS_TILE_SMALL - 1) / OS_TILE_SMALL);
-    return (size_t)(RADIX_HEADER_WORDS + 2 * 4 * tiles * 256);   // 64-bit look-back words
+    const int64_t tiles = radix_max_tiles(n_cap), groups = (tiles + OS_GROUP - 1) / OS_GROUP;
+    return (size_t)(RADIX_HEADER_WORDS + 2 * 4 * tiles * 256 + 4 * groups * 257);
 }
 
 __global__ void reset_kernel(ResetList r) {
@@ -315,10 +376,16 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
     uint32_t* tickets = w.work;            // [4]
     uint32_t* hist = w.work + 64;          // [4][256]
     unsigned long long* status = reinterpret_cast<unsigned long long*>(w.work + RADIX_HEADER_WORDS);
+    // grouped prefix when every tile of a pass is resident at once (3 blocks of 256 per SM)
+    const int64_t max_tiles = radix_max_tiles(n_cap), max_groups = (max_tiles + OS_GROUP - 1) / OS_GROUP;
+    const bool grouped = tiles <= 3 * (int64_t)w.num_sms;
+    uint32_t* gtot = w.work + RADIX_HEADER_WORDS + 2 * 4 * max_tiles * 256;   // [4][max_groups][256]
+    uint32_t* gcnt = gtot + 4 * max_groups * 256;                             // [4][max_groups]
     cudaError_t e = cudaSuccess;
     if (!pre_zeroed)
         e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * RADIX_HEADER_WORDS +
                                            sizeof(unsigned long long) * (size_t)passes * tiles * 256, s);
+    if (e == cudaSuccess && !pre_zeroed && grouped) e = cudaMemsetAsync(gtot, 0, sizeof(uint32_t) * 4 * max_groups * 257, s);
     if (e != cudaSuccess) return e;
     if (hist_pre) {
         hist = const_cast<uint32_t*>(hist_pre);   // counted by the producer of the keys, with *n_kept
@@ -338,7 +405,8 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
         e = launch_dependent(small ? radix_onesweep_kernel<OS_IPT_SMALL> : radix_onesweep_kernel<OS_IPT_LARGE>,
                              dim3((unsigned)tiles), dim3(OS_THREADS), s, ki, vi, to_a ? ka : kb, to_a ? va : vb,
                              p == 0 ? n_dev : n_kept, n_kept, 8 * p, (p == 0 && drop_max) ? 1 : 0, hist + 256 * p,
-                             status + (size_t)p * tiles * 256, tickets + p, w.flags);
+                             status + (size_t)p * tiles * 256, grouped ? gtot + (size_t)p * max_groups * 256 : nullptr,
+                             grouped ? gcnt + (size_t)p * max_groups : nullptr, tickets + p, w.flags);
         if (e != cudaSuccess) return e;
     }
     *result_in_a = (passes % 2) == 1;
