@@ -28,9 +28,9 @@ namespace h3dgs {
 
 constexpr int OS_THREADS = 256;                 // one thread per digit in the look-back
 constexpr int OS_WARPS = OS_THREADS / 32;
-constexpr int OS_IPT_SMALL = 8;                 // keys per thread when all tiles fit one wave
+constexpr int OS_IPT_SMALL = 7;                 // keys per thread when all tiles fit one wave (6..8 measured)
 constexpr int OS_IPT_LARGE = 15;                // keys per thread otherwise
-constexpr int OS_TILE_SMALL = OS_THREADS * OS_IPT_SMALL;   // 2048 keys per tile
+constexpr int OS_TILE_SMALL = OS_THREADS * OS_IPT_SMALL;   // 1792 keys per tile
 constexpr int OS_TILE_LARGE = OS_THREADS * OS_IPT_LARGE;   // 3840 keys per tile
 constexpr unsigned long long ST_AGG = 1ull << 62;   // look-back word: tile's own digit count
 constexpr unsigned long long ST_INC = 2ull << 62;   // look-back word: count of this and all earlier tiles
