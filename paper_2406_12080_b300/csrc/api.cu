@@ -620,6 +620,7 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
     CK(ensure(ctx->cut_bc, sizeof(uint32_t) * (size_t)w.blocks * n_cams), "cut counts");
     CK(ensure(ctx->cut_tot, sizeof(int64_t) * (size_t)(n_cams + 1)), "cut totals");
     w.lb_words = (int64_t)cut_single_work_words(N);
+    w.num_sms = ctx->num_sms;
     CK(ensure(ctx->cut_lb, sizeof(uint32_t) * (size_t)w.lb_words), "cut look-back");
     w.lb_work = P<uint32_t>(ctx->cut_lb);
     w.mask = P<uint32_t>(ctx->cut_mask);

@@ -310,17 +310,19 @@ __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* 
 }
 
 size_t cut_single_work_words(int64_t n) {
-    return LB_HEADER_WORDS + 2 * (size_t)((n + CS_TILE - 1) / CS_TILE);
+    return LB_HEADER_WORDS + lb_body_words((n + CS_TILE - 1) / CS_TILE);
 }
 
 cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const CutWork& w, int32_t* cut_ids,
                        float* cut_t, int64_t* cut_offsets, int64_t capacity, uint32_t* flags, cudaStream_t s) {
     if (n_cams == 1 && w.lb_work) {
         const int64_t blocks = (h.n + CS_TILE - 1) / CS_TILE;
-        if ((int64_t)LB_HEADER_WORDS + 2 * blocks > w.lb_words) return cudaErrorInvalidValue;
-        cudaError_t e = cudaMemsetAsync(w.lb_work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)blocks), s);
+        const size_t words = LB_HEADER_WORDS + lb_body_words(blocks);
+        if ((int64_t)words > w.lb_words) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(w.lb_work, 0, sizeof(uint32_t) * words, s);
         if (e != cudaSuccess) return e;
-        Lookback lb{reinterpret_cast<unsigned long long*>(w.lb_work + LB_HEADER_WORDS), w.lb_work, flags};
+        // grouped prefix when every block is resident (at most 6 blocks of 256 per SM)
+        const Lookback lb = lb_make(w.lb_work, blocks, blocks <= 6 * (int64_t)w.num_sms, flags);
         cut_single_kernel<<<(unsigned)blocks, CUT_BLOCK, 0, s>>>(h.rec, h.n, w.cam0, capacity, cut_ids, cut_t, cut_offsets,
                                                                  w.cam_totals, flags, lb);
         return cudaGetLastError();

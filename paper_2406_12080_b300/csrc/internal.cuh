@@ -289,6 +289,7 @@ struct CutWork {
     uint32_t* lb_work;       // single-camera pass: look-back workspace (NULL: use the three-pass path)
     int64_t lb_words;
     h3dgs_camera cam0;       // single-camera pass: the raw camera (its derived values are computed in the kernel)
+    int num_sms = 148;
 };
 // Look-back words the single-camera cut needs for n nodes.
 size_t cut_single_work_words(int64_t n);

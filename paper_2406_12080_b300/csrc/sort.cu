@@ -468,17 +468,19 @@ __global__ void __launch_bounds__(PO_THREADS) pair_offsets_kernel(const uint32_t
 }
 
 size_t pair_offsets_work_words(int64_t n_cap) {
-    return LB_HEADER_WORDS + 2 * (size_t)std::max<int64_t>(1, (n_cap + PO_TILE - 1) / PO_TILE);
+    return LB_HEADER_WORDS + lb_body_words(std::max<int64_t>(1, (n_cap + PO_TILE - 1) / PO_TILE));
 }
 
 cudaError_t launch_pair_offsets(const uint32_t* tiles, const uint32_t* order, const uint32_t* n_dev, int64_t n_cap,
                                 uint32_t* pair_off, uint32_t* seg_start, int64_t seg_cap, uint32_t* total,
                                 const SortWork& w, cudaStream_t s, bool pre_zeroed) {
     const int64_t blocks = std::max<int64_t>(1, (n_cap + PO_TILE - 1) / PO_TILE);
-    if ((size_t)(LB_HEADER_WORDS + 2 * blocks) > w.words) return cudaErrorInvalidValue;
-    Lookback lb{reinterpret_cast<unsigned long long*>(w.work + LB_HEADER_WORDS), w.work, w.flags};
+    const size_t words = LB_HEADER_WORDS + lb_body_words(blocks);
+    if (words > w.words) return cudaErrorInvalidValue;
+    // grouped prefix when every block is resident (a few blocks of 256 per SM)
+    const Lookback lb = lb_make(w.work, blocks, blocks <= 4 * (int64_t)w.num_sms, w.flags);
     if (!pre_zeroed) {
-        cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * (LB_HEADER_WORDS + 2 * (size_t)blocks), s);
+        cudaError_t e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t) * words, s);
         if (e != cudaSuccess) return e;
     }
     const cudaError_t e = launch_dependent(pair_offsets_kernel, dim3((unsigned)blocks), dim3(PO_THREADS), s, tiles, order,
