@@ -29,9 +29,9 @@ namespace h3dgs {
 constexpr int OS_THREADS = 256;                 // one thread per digit in the look-back
 constexpr int OS_WARPS = OS_THREADS / 32;
 constexpr int OS_IPT_SMALL = 7;                 // keys per thread when all tiles fit one wave (6..8 measured)
-constexpr int OS_IPT_LARGE = 15;                // keys per thread otherwise
+constexpr int OS_IPT_LARGE = 12;                // keys per thread otherwise (10..15 measured)
 constexpr int OS_TILE_SMALL = OS_THREADS * OS_IPT_SMALL;   // 1792 keys per tile
-constexpr int OS_TILE_LARGE = OS_THREADS * OS_IPT_LARGE;   // 3840 keys per tile
+constexpr int OS_TILE_LARGE = OS_THREADS * OS_IPT_LARGE;   // 3072 keys per tile
 constexpr unsigned long long ST_AGG = 1ull << 62;   // look-back word: tile's own digit count
 constexpr unsigned long long ST_INC = 2ull << 62;   // look-back word: count of this and all earlier tiles
 constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
@@ -376,9 +376,11 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
     uint32_t* tickets = w.work;            // [4]
     uint32_t* hist = w.work + 64;          // [4][256]
     unsigned long long* status = reinterpret_cast<unsigned long long*>(w.work + RADIX_HEADER_WORDS);
-    // grouped prefix when every tile of a pass is resident at once (3 blocks of 256 per SM)
+    // grouped prefix when the tiles of a pass are (about) all resident at once: 3 blocks of 256 per SM
+    // hold 3 x SMs tiles, and tiles beyond the keys actually present exit at once (the launch is
+    // sized by the capacity)
     const int64_t max_tiles = radix_max_tiles(n_cap), max_groups = (max_tiles + OS_GROUP - 1) / OS_GROUP;
-    const bool grouped = tiles <= 3 * (int64_t)w.num_sms;
+    const bool grouped = tiles <= 4 * (int64_t)w.num_sms;
     uint32_t* gtot = w.work + RADIX_HEADER_WORDS + 2 * 4 * max_tiles * 256;   // [4][max_groups][256]
     uint32_t* gcnt = gtot + 4 * max_groups * 256;                             // [4][max_groups]
     cudaError_t e = cudaSuccess;
