@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         const float dn = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
         const float x = dv[0] / dn, y = dv[1] / dn, zz = dv[2] / dn;
         const float xx = x * x, yy = y * y, z2 = zz * zz;
-        float Y[16], dY[16][3];
+        float Y[16];
         Y[0] = SH_C0;
         Y[1] = -SH_C1 * y; Y[2] = SH_C1 * zz; Y[3] = -SH_C1 * x;
         Y[4] = SH_C2A * x * y; Y[5] = -SH_C2A * y * zz; Y[6] = SH_C2B * (2.f * z2 - xx - yy);
@@ -478,20 +478,6 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         Y[11] = -SH_C3C * y * (4.f * z2 - xx - yy); Y[12] = SH_C3D * zz * (2.f * z2 - 3.f * xx - 3.f * yy);
         Y[13] = -SH_C3C * x * (4.f * z2 - xx - yy); Y[14] = SH_C3E * zz * (xx - yy);
         Y[15] = -SH_C3A * x * (xx - 3.f * yy);
-        for (int kk = 0; kk < 16; ++kk) dY[kk][0] = dY[kk][1] = dY[kk][2] = 0.f;
-        dY[1][1] = -SH_C1; dY[2][2] = SH_C1; dY[3][0] = -SH_C1;
-        dY[4][0] = SH_C2A * y; dY[4][1] = SH_C2A * x;
-        dY[5][1] = -SH_C2A * zz; dY[5][2] = -SH_C2A * y;
-        dY[6][0] = -2.f * SH_C2B * x; dY[6][1] = -2.f * SH_C2B * y; dY[6][2] = 4.f * SH_C2B * zz;
-        dY[7][0] = -SH_C2A * zz; dY[7][2] = -SH_C2A * x;
-        dY[8][0] = 2.f * SH_C2C * x; dY[8][1] = -2.f * SH_C2C * y;
-        dY[9][0] = -6.f * SH_C3A * x * y; dY[9][1] = -SH_C3A * (3.f * xx - 3.f * yy);
-        dY[10][0] = SH_C3B * y * zz; dY[10][1] = SH_C3B * x * zz; dY[10][2] = SH_C3B * x * y;
-        dY[11][0] = 2.f * SH_C3C * x * y; dY[11][1] = -SH_C3C * (4.f * z2 - xx - 3.f * yy); dY[11][2] = -8.f * SH_C3C * y * zz;
-        dY[12][0] = -6.f * SH_C3D * x * zz; dY[12][1] = -6.f * SH_C3D * y * zz; dY[12][2] = SH_C3D * (6.f * z2 - 3.f * xx - 3.f * yy);
-        dY[13][0] = -SH_C3C * (4.f * z2 - 3.f * xx - yy); dY[13][1] = 2.f * SH_C3C * x * y; dY[13][2] = -8.f * SH_C3C * x * zz;
-        dY[14][0] = 2.f * SH_C3E * zz * x; dY[14][1] = -2.f * SH_C3E * zz * y; dY[14][2] = SH_C3E * (xx - yy);
-        dY[15][0] = -SH_C3A * (3.f * xx - 3.f * yy); dY[15][1] = 6.f * SH_C3A * x * y;
         // SH rows as float4 (12 per node); loops fully unrolled so every Y / dY index is a constant
         const float4* shn4 = h.sh + (int64_t)12 * n;
         const float4* shp4 = h.sh + (int64_t)12 * (use_p ? p : n);
@@ -509,7 +495,11 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
 #pragma unroll
             for (int e = 0; e < 4; ++e) col[(4 * j4 + e) % 3] += vv[e] * Y[(4 * j4 + e) / 3];
         }
-        float ddir[3] = {0.f, 0.f, 0.f};
+        // wk[k] = sum over the channels that are not clamped of dL/dcolour x coefficient k (the colour's
+        // derivative along the view direction is then sum_k wk[k] dY_k)
+        float wk[16];
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) wk[kk] = 0.0f;
         const float wn = use_p ? omt : 1.0f;
         const bool leaf_n = h.child_count[n] == 0;
         const bool write_n = !(freeze_leaves && leaf_n);
@@ -530,14 +520,34 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
                 const int c = 4 * j4 + e, ch = c % 3;
                 const bool live = !(col[ch] < 0.0f);
                 g4[e] = live ? grgb[ch] * Y[c / 3] : 0.0f;
-                if (live)
-                    for (int jj = 0; jj < 3; ++jj) ddir[jj] += grgb[ch] * vv[e] * dY[c / 3][jj];
+                if (live) wk[c / 3] += grgb[ch] * vv[e];
             }
             if (g4[0] != 0.0f || g4[1] != 0.0f || g4[2] != 0.0f || g4[3] != 0.0f) {
                 if (write_n) red_add_v4(gout.sh + (int64_t)NSH * n + 4 * j4, wn * g4[0], wn * g4[1], wn * g4[2], wn * g4[3]);
                 if (use_p) red_add_v4(gout.sh + (int64_t)NSH * p + 4 * j4, t * g4[0], t * g4[1], t * g4[2], t * g4[3]);
             }
         }
+        // derivatives of the basis functions along x, y, z (built after the coefficient loops, so they
+        // are not held across them)
+        float dY[16][3];
+        for (int kk = 0; kk < 16; ++kk) dY[kk][0] = dY[kk][1] = dY[kk][2] = 0.f;
+        dY[1][1] = -SH_C1; dY[2][2] = SH_C1; dY[3][0] = -SH_C1;
+        dY[4][0] = SH_C2A * y; dY[4][1] = SH_C2A * x;
+        dY[5][1] = -SH_C2A * zz; dY[5][2] = -SH_C2A * y;
+        dY[6][0] = -2.f * SH_C2B * x; dY[6][1] = -2.f * SH_C2B * y; dY[6][2] = 4.f * SH_C2B * zz;
+        dY[7][0] = -SH_C2A * zz; dY[7][2] = -SH_C2A * x;
+        dY[8][0] = 2.f * SH_C2C * x; dY[8][1] = -2.f * SH_C2C * y;
+        dY[9][0] = -6.f * SH_C3A * x * y; dY[9][1] = -SH_C3A * (3.f * xx - 3.f * yy);
+        dY[10][0] = SH_C3B * y * zz; dY[10][1] = SH_C3B * x * zz; dY[10][2] = SH_C3B * x * y;
+        dY[11][0] = 2.f * SH_C3C * x * y; dY[11][1] = -SH_C3C * (4.f * z2 - xx - 3.f * yy); dY[11][2] = -8.f * SH_C3C * y * zz;
+        dY[12][0] = -6.f * SH_C3D * x * zz; dY[12][1] = -6.f * SH_C3D * y * zz; dY[12][2] = SH_C3D * (6.f * z2 - 3.f * xx - 3.f * yy);
+        dY[13][0] = -SH_C3C * (4.f * z2 - 3.f * xx - yy); dY[13][1] = 2.f * SH_C3C * x * y; dY[13][2] = -8.f * SH_C3C * x * zz;
+        dY[14][0] = 2.f * SH_C3E * zz * x; dY[14][1] = -2.f * SH_C3E * zz * y; dY[14][2] = SH_C3E * (xx - yy);
+        dY[15][0] = -SH_C3A * (3.f * xx - 3.f * yy); dY[15][1] = 6.f * SH_C3A * x * y;
+        float ddir[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kk = 1; kk < 16; ++kk)
+            for (int jj = 0; jj < 3; ++jj) ddir[jj] += wk[kk] * dY[kk][jj];
         const float dot = ddir[0] * x + ddir[1] * y + ddir[2] * zz;
         dmu[0] += (ddir[0] - x * dot) / dn;
         dmu[1] += (ddir[1] - y * dot) / dn;
