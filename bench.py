@@ -94,7 +94,11 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the sampled clock log (kept beside the run's other outputs when H3DGS_BENCH_LOG_DIR names a
+        # directory, else in the system's temporary directory)
+        import tempfile
+        log_dir = os.environ.get("H3DGS_BENCH_LOG_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(log_dir, f"h3dgs_clocks_gpu{gpu_index}.csv")
 
     def __enter__(self):
         try:
