@@ -731,7 +731,7 @@ def run_compaction(args, ctx, hier, stream, reps: int = 3):
 
 
 def run_streamed(args, hier, dev, stream, update_every: int = 2, cleanup_every: int = 100, max_age: int = 100):
-    """Out-of-core rendering along a drive down the street (Sec. 5.3): node attributes in page-locked
+    """Out-of-core rendering along a drive down the street (Sec. 6.3): node attributes in page-locked
     host memory, a device cache of rows; the cut is updated every 2 frames (transferring the nodes it
     needs) and a cleanup runs every 100 frames.  Reported like the paper's per-path table: cut size
     (#Render) and transferred nodes (#Trans) per frame, and frames/s, next to the same path with the

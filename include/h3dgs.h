@@ -8,7 +8,7 @@
  * (Sec. 4.2), interpolates each cut node with its parent (Sec. 4.2, Eq. t_interp and
  * Eq. alphap), and splats the result with a tile-based rasteriser (Sec. 3.1, Eq. alpha;
  * EWA low-pass of Sec. 5.1).  It also provides the adjoint used to optimise interior nodes
- * (Sec. 5.1, Sec. 6.3).
+ * (Sec. 5.1, Sec. 7.1, Sec. 7.3).
  *
  * Conventions shared by every call
  *   - All attribute, topology, output and gradient buffers are DEVICE pointers unless a
@@ -92,7 +92,7 @@ typedef struct {
     int32_t tile_w, tile_h;  /* screen tile in pixels: 16x16 (default), 8x8, 32x8, 8x32 or 16x8
                                 (both sides multiples of 8: a warp blends 8x8 pixels)          */
     float lowpass;           /* screen-space variance added to the 2D covariance, px^2 (0.3)    */
-    float alpha_clamp;       /* alpha upper clamp (0.99, Sec. 6.3)                              */
+    float alpha_clamp;       /* alpha upper clamp (0.99, Sec. 7.3)                              */
     float alpha_floor;       /* alpha below which a splat is skipped (1/255)                   */
     float t_min;             /* stop before transmittance would drop below this (1e-4)        */
     int32_t aa_compensate;   /* 1: opacities scaled by sqrt(det S' / det(S' + lowpass I))     */
@@ -190,7 +190,7 @@ h3dgs_status h3dgs_build_hierarchy(h3dgs_ctx* ctx, int64_t n_leaves, const float
                                    const h3dgs_node_arrays* out);
 
 /* Consolidated hierarchy over a chunked scene (the chunk-wise build and consolidation of large
- * captures, Sec. 5): the leaves are grouped into n_chunks chunks (chunk c = leaves
+ * captures, Sec. 6): the leaves are grouped into n_chunks chunks (chunk c = leaves
  * [chunk_offsets[c], chunk_offsets[c + 1]), host array of n_chunks + 1 ascending offsets starting at
  * 0); every chunk gets its own hierarchy exactly as h3dgs_build_hierarchy builds it from the chunk's
  * leaves alone, and a top tree built the same way over the chunk roots joins them (its leaf boxes
@@ -233,7 +233,7 @@ h3dgs_status h3dgs_compact_hierarchy(h3dgs_ctx* ctx, const h3dgs_camera* cams, i
  * The topology is trusted (not validated on the device). */
 h3dgs_status h3dgs_upload_hierarchy(h3dgs_ctx* ctx, const h3dgs_hierarchy* hier);
 
-/* Streamed (out-of-core) hierarchy (Sec. 5.3: the cut is updated every few frames by transferring
+/* Streamed (out-of-core) hierarchy (Sec. 6.3: the cut is updated every few frames by transferring
  * the nodes it needs from CPU RAM to the GPU; a cleanup runs every 100 frames).  Like
  * h3dgs_upload_hierarchy, but the attribute arrays (mean, scale, rot, opacity, sh) are PAGE-LOCKED
  * HOST arrays (cudaHostAlloc / cudaHostRegister; borrowed, same layouts) while the boxes and the
@@ -290,7 +290,10 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
  *   - hier->n_nodes must be at most H3DGS_NOALLOC_MAX_NODES; larger trees return
  *     H3DGS_ERR_CAPACITY without launching anything.
  *   - The first call on each device looks up the scratch array's device address; make that first
- *     call before any CUDA stream capture on that device.
+ *     call before any CUDA stream capture on that device.  The address belongs to the device's
+ *     current context: when that context changes (after cudaDeviceReset, or when the primary
+ *     context was released and created again) the next call looks it up again, so make that call
+ *     outside stream capture too.
  *   - All calls in the process share the scratch array: calls whose work overlaps on the GPU
  *     (other streams or host threads) race and must be serialised by the caller.
  *   - Work is issued on `cuda_stream` (cudaStream_t, NULL = legacy default stream) of the current
@@ -330,13 +333,13 @@ h3dgs_status h3dgs_render(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_ca
                           const int32_t* cut_ids, const float* cut_t, const int64_t* cut_offsets,
                           const h3dgs_render_opts* opts, float* images, int32_t save_for_backward);
 
-/* a8 -- adjoint of the most recent h3dgs_render(save_for_backward = 1) (Sec. 5.1, Sec. 6.3).
+/* a8 -- adjoint of the most recent h3dgs_render(save_for_backward = 1) (Sec. 5.1, Sec. 7.1, Sec. 7.3).
  * dL_dimages: device, same packing as `images`.  Gradients are ACCUMULATED into `grads`:
  * node n receives (1 - t) of the gradient of its interpolated mean/scale/rot/sh and its parent p
  * receives t of it (t is a constant); o_n and o_p receive the gradients of their own alpha terms,
  * including d alpha'/d alpha_p = (1/K)(1 - alpha_p)^(1/K - 1); an opacity gradient is zero where
- * its alpha is clamped (Sec. 6.3).  freeze_leaves = 1 leaves the rows of leaf nodes untouched
- * (stop-gradient on leaves, Sec. 6.3).  grads->rot and grads->sh must be 16-byte aligned (they are
+ * its alpha is clamped (Sec. 7.3).  freeze_leaves = 1 leaves the rows of leaf nodes untouched
+ * (stop-gradient on leaves, Sec. 7.1).  grads->rot and grads->sh must be 16-byte aligned (they are
  * updated with 4-float vector reductions).  Errors: STATE if no saved forward state, INVALID_ARG for
  * NULL or misaligned gradient arrays. */
 h3dgs_status h3dgs_render_backward(h3dgs_ctx* ctx, const float* dL_dimages, const h3dgs_grads* grads,
@@ -397,9 +400,6 @@ h3dgs_status h3dgs_debug_tile_lists(h3dgs_ctx* ctx, int32_t cam, int32_t* ranges
  * rect [m][4] = tile x0, x1, y0, y1 (inclusive), all -1 for culled entries; rgb [m][3]. */
 h3dgs_status h3dgs_debug_splats(h3dgs_ctx* ctx, float* rec, int32_t* rect, float* rgb, int64_t m);
 
-/* Copy the last render's per-pixel final transmittance and contributor count (the list position
- * after the last contributing splat) to HOST memory for all cameras (synchronous).  Only a render
- * with save_for_backward = 1 keeps this state. */
 /* Test hook for the failure path of the library's bounded waits between thread blocks (the
  * radix-sort and scan look-backs, the blend queue): runs one wait, with the same loop, on a device
  * word that nothing sets, giving up after `polls` polls (1 .. 2^20; each poll sleeps about 0.1 us
@@ -408,6 +408,11 @@ h3dgs_status h3dgs_debug_splats(h3dgs_ctx* ctx, float* rec, int32_t* rect, float
  * Errors: INVALID_ARG for polls out of range. */
 h3dgs_status h3dgs_debug_wait_timeout(h3dgs_ctx* ctx, int32_t polls);
 
+/* Copy the last render's per-pixel final transmittance and contributor count (the list position
+ * after the last contributing splat) to HOST memory for all cameras (synchronous); either output
+ * may be NULL.  Only a render with save_for_backward = 1 writes this state (after a forward-only
+ * render the arrays hold whatever the last saving render left).  n_pixels must equal the total
+ * pixel count of the last render's cameras (INVALID_ARG otherwise); STATE if nothing was rendered. */
 h3dgs_status h3dgs_debug_pixel_state(h3dgs_ctx* ctx, float* T_final, int32_t* n_contrib, int64_t n_pixels);
 
 #ifdef __cplusplus

@@ -257,7 +257,7 @@ def compact(cams, h: Hierarchy, tau_min: float, tau_max: float):
 
 def stream_trace(cams, h: Hierarchy, update_every: int = 2, cleanup_every: int = 100, max_age: int = 100,
                  interpolate: int = 1):
-    """Node residency of streamed rendering along a camera path (Sec. 5.3: the cut is updated every
+    """Node residency of streamed rendering along a camera path (Sec. 6.3: the cut is updated every
     few frames by transferring the nodes it needs from CPU RAM to the GPU; a cleanup runs every 100
     frames).  Frame f = 0, 1, ...:
       * if f % update_every == 0: the cut of cams[f]; the needed nodes are its nodes and the parents
@@ -417,6 +417,19 @@ def weighted_image_sum(cam, h: Hierarchy, fr: Frame, w: np.ndarray, opts: Opts, 
                                        _p(val, C.c_double), _p(fr.ranges, C.c_int32), _p(lists, C.c_int32),
                                        None if E is None else _p(E, C.c_float), _p(w, C.c_double),
                                        None if wd is None else _p(wd, C.c_double))
+
+
+def pair_alpha(fr: Frame, splat, px, py, opts: Opts):
+    """alpha of splat `splat[i]` of frame `fr` at pixel position (px[i], py[i]) in both tracks:
+    (fp32 decision track, fp64 value track)."""
+    s = np.ascontiguousarray(splat, np.int32)
+    x, y = _f64(px), _f64(py)
+    a32 = np.empty(len(s), np.float32)
+    a64 = np.empty(len(s), np.float64)
+    lib().or_pair_alpha(_p(fr.rec32, C.c_float), _p(fr.val64, C.c_double), C.c_int64(len(s)), _p(s, C.c_int32),
+                        _p(x, C.c_double), _p(y, C.c_double), C.c_float(opts.alpha_clamp), _p(a32, C.c_float),
+                        _p(a64, C.c_double))
+    return a32, a64
 
 
 def ellipsoid_area(s) -> float:

@@ -6,7 +6,7 @@
 // (Sec. 4.2, Eq. t_interp), attribute interpolation and transition opacity (Sec. 4.2,
 // Eq. alphap and its K-child form in Sec. 5.2), EWA-filtered splatting (Sec. 3.1 Eq. alpha,
 // Sec. 5.1), front-to-back blending, and the analytic adjoint used by hierarchy optimisation
-// (Sec. 5.1, Sec. 6.3).  Only the tests, the smoke check and the benchmark's CPU-baseline leg
+// (Sec. 5.1, Sec. 7.1, Sec. 7.3).  Only the tests, the smoke check and the benchmark's CPU-baseline leg
 // call it; the product library never links or loads it, and the two share no code.
 //
 // Two tracks are computed side by side:
@@ -1071,7 +1071,7 @@ void or_blend_bruteforce(const OrCamera* cam, const OrOpts* o, int64_t M, const 
 }  // extern "C"
 
 // ==========================================================================================
-// Adjoint (hierarchy optimisation, Sec. 5.1; manual alpha' derivative and clamp rule Sec. 6.3)
+// Adjoint (hierarchy optimisation, Sec. 5.1; manual alpha' derivative Sec. 7.1, clamp rule Sec. 7.3)
 // ==========================================================================================
 
 namespace {
@@ -1350,6 +1350,17 @@ double or_weighted_image_sum(const OrCamera* cam, const OrOpts* o, const float* 
     if (w_depth)
         for (size_t i = 0; i < dep.size(); ++i) s += w_depth[i] * dep[i];
     return s;
+}
+
+// The per-pixel alpha of both tracks at n (splat, pixel-centre) pairs, exposed so that the fp32
+// decision track can be checked against the fp64 value track: a32[i] = alpha_f of splat s[i]'s
+// record at (px[i], py[i]) (rounded to fp32 as the blend does), a64[i] = alpha_d there.
+void or_pair_alpha(const float* rec32, const double* val64, int64_t n, const int32_t* s, const double* px,
+                   const double* py, float clampv, float* a32, double* a64) {
+    for (int64_t i = 0; i < n; ++i) {
+        a32[i] = alpha_f(rec32 + 10 * (int64_t)s[i], (float)px[i], (float)py[i], clampv);
+        a64[i] = alpha_d(val64 + NVAL * (int64_t)s[i], px[i], py[i], (double)clampv);
+    }
 }
 
 // Ellipsoid surface area used by the merge weights (exposed for the closed-form test).

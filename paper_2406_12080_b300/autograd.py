@@ -3,7 +3,7 @@
 Hierarchy optimisation (Sec. 5.1 of the paper) renders random views at random target
 granularities tau and back-propagates into the interior nodes through the interpolation between
 a cut node and its parent.  The forward pass is `h3dgs_select_cut` + `h3dgs_render(save=1)`; the
-backward pass is `h3dgs_render_backward`.  Activations stay in torch (Sec. 6.3): scales are
+backward pass is `h3dgs_render_backward`.  Activations stay in torch (Sec. 7.3): scales are
 exp(raw), leaf opacities sigmoid(raw), interior opacities |raw| (the falloff may exceed 1);
 leaves can be frozen (stop-gradient).
 

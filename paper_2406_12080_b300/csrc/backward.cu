@@ -7,12 +7,12 @@
 // (u, v, conic, o_n', o_p', colour) is summed over the warp with shuffles and added to a per-splat
 // accumulator with one atomic per value per warp.  The alpha' chain uses the derivative of
 // Eq. alphap, d alpha'/d alpha_p = (1/K)(1 - alpha_p)^(1/K - 1); an opacity gradient is zero on a
-// clamped branch (Sec. 6.3).
+// clamped branch (Sec. 7.3).
 //
 // Stage 2, per cut entry: recompute the interpolated Gaussian and its projection and apply the
 // adjoint of SH colour, EWA projection (Sigma' = M M^T, M = J W R(q) diag(s)), the opacity
 // compensation and the quaternion normalisation, then scatter (1 - t) of the result to node n and
-// t to its parent p (t is a constant; Sec. 5.1).  Leaves are skipped when frozen (Sec. 6.3).
+// t to its parent p (t is a constant; Sec. 5.1).  Leaves are skipped when frozen (Sec. 7.1).
 #include "internal.cuh"
 
 namespace h3dgs {

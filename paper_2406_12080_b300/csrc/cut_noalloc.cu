@@ -143,10 +143,46 @@ __global__ void __launch_bounds__(NA_BLOCK) na_write_kernel(h3dgs_hierarchy h, h
     }
 }
 
-// device address of the scratch array, looked up once per device
+// Device address of the scratch array, looked up once per device and context: the address belongs
+// to the module loaded into the device's current context, so a new context (after a device reset,
+// or the primary context torn down and created again) needs a new look-up.
 constexpr int NA_MAX_DEVICES = 64;
-uint32_t* g_scratch_ptr[NA_MAX_DEVICES] = {};
+struct ScratchAddr {
+    void* ctx;
+    uint32_t* ptr;
+};
+ScratchAddr g_scratch[NA_MAX_DEVICES] = {};
 std::mutex g_scratch_mutex;
+
+// The driver's cuCtxGetCurrent, reached through the runtime (the library does not link libcuda).
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    return fn;
+}
+
+void* current_context() {
+    void* c = nullptr;
+    CtxGetCurrentFn fn = ctx_get_current();
+    if (!fn || fn(&c) != 0) return nullptr;
+    return c;
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t na_launch(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.stream = s;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 }  // namespace
 
@@ -168,14 +204,17 @@ extern "C" h3dgs_status h3dgs_select_cut_noalloc(const h3dgs_hierarchy* hier, co
     uint32_t* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mutex);
-        if (!g_scratch_ptr[dev]) {
-            // first call on this device (which is current): resolve the array's device address
+        void* ctx = current_context();
+        if (!g_scratch[dev].ptr || !ctx || ctx != g_scratch[dev].ctx) {
+            // first call on this device and context (which are current): resolve the array's device
+            // address (this also creates the primary context if none is current yet)
             uint32_t* p = nullptr;
             if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch) != cudaSuccess || !p)
                 return H3DGS_ERR_CUDA;
-            g_scratch_ptr[dev] = p;
+            g_scratch[dev].ptr = p;
+            g_scratch[dev].ctx = current_context();
         }
-        scratch = g_scratch_ptr[dev];
+        scratch = g_scratch[dev].ptr;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     const int64_t N = hier->n_nodes;
@@ -183,10 +222,13 @@ extern "C" h3dgs_status h3dgs_select_cut_noalloc(const h3dgs_hierarchy* hier, co
     const int64_t min_chunk = 8 * NA_BLOCK;   // at most ~N / 2048 blocks for small trees
     if (chunk < min_chunk) chunk = min_chunk;
     const int G = (int)((N + chunk - 1) / chunk);
-    na_mark_kernel<<<G, NA_BLOCK, 0, s>>>(*hier, *cam, chunk, scratch);
-    na_scan_kernel<<<1, 1024, 0, s>>>(G, capacity, scratch, cut_offsets);
-    na_write_kernel<<<G, NA_BLOCK, 0, s>>>(*hier, *cam, chunk, scratch, capacity, cut_ids, cut_t);
-    if (cudaGetLastError() != cudaSuccess) return H3DGS_ERR_CUDA;
+    // each launch reports its own status: an error left by the caller's earlier work is neither
+    // reported as this call's nor cleared
+    if (na_launch(na_mark_kernel, G, NA_BLOCK, s, *hier, *cam, chunk, scratch) != cudaSuccess ||
+        na_launch(na_scan_kernel, 1, 1024, s, G, capacity, scratch, cut_offsets) != cudaSuccess ||
+        na_launch(na_write_kernel, G, NA_BLOCK, s, *hier, *cam, chunk, (const uint32_t*)scratch, capacity, cut_ids,
+                  cut_t) != cudaSuccess)
+        return H3DGS_ERR_CUDA;
     if (total_out) {
         uint32_t tw[2];
         if (cudaMemcpyAsync(tw, scratch + NA_MASK_WORDS + NA_MAX_BLOCKS, sizeof(tw), cudaMemcpyDeviceToHost, s) !=

@@ -3,7 +3,7 @@
 // One thread per cut entry.  The entry's node n is interpolated with its parent p using the parent
 // weight t (Sec. 4.2): a = (1 - t) a_n + t a_p for mean, scale, rotation (then normalised) and SH,
 // computed as fmaf(t, a_p, (1 - t) a_n).  The parent's attributes are only read when t != 0,
-// which is why leaves cost about twice the bytes of interior cut nodes (Sec. 7.2).
+// which is why leaves cost about twice the bytes of interior cut nodes (Sec. 8.2).
 //
 // Projection is EWA splatting: Sigma' = J W Sigma W^T J^T with J the Jacobian of the pinhole map
 // at the mean (x/z, y/z clamped to 1.3 tan(half fov)).  Sigma' is evaluated as M M^T with

@@ -1,4 +1,4 @@
-// Streamed (out-of-core) rendering (Sec. 5.3: the cut is updated every few frames by transferring
+// Streamed (out-of-core) rendering (Sec. 6.3: the cut is updated every few frames by transferring
 // the nodes it needs from CPU RAM to the GPU, and a cleanup runs every 100 frames).
 //
 // Only the 32-byte cut records (boxes and topology) are resident for every node; node attributes

@@ -25,9 +25,10 @@ NINTERP = 62
 
 
 class H3dgsError(RuntimeError):
-    def __init__(self, status: int, msg: str):
+    def __init__(self, status: int, msg: str, total: int | None = None):
         super().__init__(f"h3dgs {STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
+        self.total = total      # the untruncated size, for CAPACITY errors that report one
 
 
 class h3dgs_camera(C.Structure):
@@ -276,7 +277,8 @@ def h3dgs_select_cut_noalloc(hier: "DeviceHierarchy", cam, cut_ids, cut_t, cut_o
     st = lib().h3dgs_select_cut_noalloc(C.byref(h), C.byref(camera_struct(cam)), _ptr(cut_ids), _ptr(cut_t),
                                         _ptr(cut_offsets), capacity, C.byref(tot) if want_total else None, stream)
     if st != H3DGS_OK:
-        raise H3dgsError(st, "h3dgs_select_cut_noalloc failed")
+        raise H3dgsError(st, "h3dgs_select_cut_noalloc failed",
+                         int(tot.value) if want_total and tot.value >= 0 else None)
     return int(tot.value) if want_total else None
 
 

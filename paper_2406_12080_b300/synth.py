@@ -13,7 +13,7 @@ Attribute distributions (identical for every scene):
   * SH degree 3: 48 coefficients ~ N(0, 0.3), laid out [k*3 + channel]
 
 Scene shapes follow the paper's capture description: a helmet rig at about
-1.7 m (Sec. 6.2), chunks of 50 x 50 m (Sec. 5), 2-8M leaves per chunk (Sec. 7).
+1.7 m (Sec. 7.2), chunks of 50 x 50 m (Sec. 6), 2-8M leaves per chunk (Sec. 8.1).
 """
 from __future__ import annotations
 

@@ -418,7 +418,7 @@ def test_alpha_floor_and_transmittance_stop():
     assert fr.n_contrib[16, 16] == 3
 
 
-# ------------------------------------------------------------------ adjoint (Sec. 5.1, Sec. 6.3)
+# ------------------------------------------------------------------ adjoint (Sec. 5.1, Sec. 7.1, Sec. 7.3)
 
 def _fd_scene():
     lv, cam = scenes.small_random_scene(n_leaves=40, res=(40, 32), seed=9, log_scale=-2.2)
@@ -480,7 +480,7 @@ def test_backward_matches_finite_differences():
 
 
 def test_backward_freeze_leaves_and_parent_share():
-    """Frozen leaves receive nothing (Sec. 6.3); a cut node with 0 < t < 1 sends gradient to its
+    """Frozen leaves receive nothing (Sec. 7.1); a cut node with 0 < t < 1 sends gradient to its
     parent, in proportion t : (1 - t) for the linearly interpolated SH coefficients."""
     h, cam = _fd_scene()
     opts = oracle.Opts()
@@ -500,3 +500,159 @@ def test_backward_freeze_leaves_and_parent_share():
         if sib in set(fr.ids.tolist()) or not leaf[sib]:
             continue
         np.testing.assert_allclose(g[p, 11:] * (1 - t), g[n, 11:] * t, rtol=1e-9, atol=1e-15)
+
+
+# ------------------------------------------------------------------ fp32 decision track (Sec. 3.1 Eq. alpha, Eq. alphap)
+#
+# The oracle takes every integer decision (tile rectangle, alpha floor, transmittance stop) in an
+# fp32 track (project_f / alpha_f: the conic pre-scaled to a base-2 exponent, fp32 arithmetic in a
+# fixed order) and every value in an fp64 track (project_d / alpha_d), which the tests above pin
+# by closed forms, a numeric Jacobian and finite differences.  The pins below tie the fp32 track
+# to the fp64 track at every (pixel, splat) pair of seeded scenes, binary and K-ary (K = 2, 3, 5)
+# transitions included, so that a dropped term, a wrong sign or a wrong base-2 factor in the
+# decision track fails them.
+
+_KH = float(np.float32(-0.72134752044448170))     # the decision track's -log2(e)/2
+_KL = float(np.float32(1.44269504088896341))      # and log2(e)
+
+
+def _box3(mean, scale, q):
+    R = _rotmat(q)
+    he = 3 * np.sqrt(((R * np.asarray(scale, np.float64)[None, :]) ** 2).sum(1))
+    return mean - he, mean + he
+
+
+def _kary_hierarchy(K, rng, depth=3.0):
+    """A root merged (Eq. merge) from K leaf children, leaf boxes the 3-sigma AABBs, the root box
+    their union: one K-child transition (Eq. alphap with K children, Sec. 5.2)."""
+    mean = np.c_[rng.uniform(-0.15, 0.15, K), rng.uniform(-0.15, 0.15, K), depth + rng.uniform(-0.1, 0.1, K)]
+    scale = np.exp(rng.normal(-3.0, 0.3, (K, 3)))
+    q = rng.normal(size=(K, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    rows = np.c_[mean, scale, q, rng.uniform(0.3, 0.95, K), rng.normal(0, 0.3, (K, 48))]
+    allr = np.vstack([oracle.merge_rows(rows)[None], rows]).astype(np.float32)
+    bmin = np.empty((K + 1, 3), np.float32)
+    bmax = np.empty((K + 1, 3), np.float32)
+    for i in range(K):
+        bmin[i + 1], bmax[i + 1] = _box3(mean[i], scale[i], q[i])
+    bmin[0], bmax[0] = bmin[1:].min(0), bmax[1:].max(0)
+    c = np.ascontiguousarray
+    return oracle.Hierarchy(c(allr[:, 0:3]), c(allr[:, 3:6]), c(allr[:, 6:10]), c(allr[:, 10]), c(allr[:, 11:59]),
+                            bmin, bmax, np.r_[-1, np.zeros(K)].astype(np.int32),
+                            np.r_[1, np.zeros(K)].astype(np.int32), np.r_[K, np.zeros(K)].astype(np.int32))
+
+
+def _decision_track_frames():
+    """Rendered frames of a 200-leaf binary scene at five tau and of K-child transitions at four tau
+    each, every one with splats at 0 < t < 1."""
+    opts = oracle.Opts()
+    lv, cam = scenes.small_random_scene(n_leaves=200, res=(96, 80), seed=11)
+    h = oracle.build_tree(lv)
+    eps = oracle.granularity(cam, h)
+    out = []
+    for tau in np.quantile(eps[h.child_count > 0], [0.1, 0.3, 0.5, 0.7, 0.9]):
+        c = synth.with_tau(cam, float(tau))
+        out.append((c, oracle.render(c, h, opts)))
+    rng = np.random.default_rng(5)
+    kcam = scenes.axis_camera(64, 64, 120.0)
+    for K in (2, 3, 5):
+        for _ in range(2):
+            hk = _kary_hierarchy(K, rng)
+            ek = oracle.granularity(kcam, hk)
+            assert ek[0] > ek[1:].max()
+            for tau in np.linspace(ek[1:].max(), ek[0], 6)[1:-1]:
+                c = synth.with_tau(kcam, float(tau))
+                fr = oracle.render(c, hk, opts)
+                assert list(fr.ids) == list(range(1, K + 1)) and np.all((fr.t > 0) & (fr.t < 1))
+                out.append((c, fr))
+    return opts, out
+
+
+def test_decision_track_records_match_value_track():
+    """Per visible splat: the base-2 pre-scaled conic (ca, cb, cc) of the decision record is
+    (-A/2, -B, -C/2) log2(e) of the value track's conic; centre, opacities, t, K and depth agree."""
+    _, frames = _decision_track_frames()
+    n_t = 0
+    for _, fr in frames:
+        vis = fr.rect[:, 0] >= 0
+        r, v = fr.rec32[vis].astype(np.float64), fr.val64[vis]
+        A, B, Cc = r[:, 2] / _KH, -r[:, 3] / _KL, r[:, 4] / _KH
+        scale = np.sqrt(v[:, 2] * v[:, 4])
+        assert np.all(v[:, 2] > 0) and np.all(v[:, 4] > 0)
+        np.testing.assert_array_less(np.abs(A - v[:, 2]), 1e-5 * v[:, 2])
+        np.testing.assert_array_less(np.abs(Cc - v[:, 4]), 1e-5 * v[:, 4])
+        np.testing.assert_array_less(np.abs(B - v[:, 3]), 1e-5 * scale)
+        np.testing.assert_array_less(np.abs(r[:, 0:2] - v[:, 0:2]), 1e-3)                 # pixels
+        np.testing.assert_array_less(np.abs(r[:, 5:7] - v[:, 5:7]), 1e-5 * np.abs(v[:, 5:7]) + 1e-30)
+        np.testing.assert_array_equal(r[:, 7], v[:, 7])                                     # t
+        np.testing.assert_array_equal(r[:, 8], v[:, 8])                                     # K
+        np.testing.assert_array_less(np.abs(r[:, 9] - v[:, 12]), 1e-6 * v[:, 12])          # depth
+        n_t += int(np.sum(r[:, 7] > 0))
+    assert n_t > 300
+
+
+def _rect_pairs(cam, fr, opts):
+    S, PX, PY = [], [], []
+    for i in np.nonzero(fr.rect[:, 0] >= 0)[0]:
+        x0, x1, y0, y1 = fr.rect[i]
+        xs = np.arange(x0 * opts.tile_w, min((x1 + 1) * opts.tile_w, cam.width))
+        ys = np.arange(y0 * opts.tile_h, min((y1 + 1) * opts.tile_h, cam.height))
+        X, Y = np.meshgrid(xs, ys)
+        S.append(np.full(X.size, i))
+        PX.append(X.ravel() + 0.5)
+        PY.append(Y.ravel() + 0.5)
+    return np.concatenate(S), np.concatenate(PX), np.concatenate(PY)
+
+
+def test_decision_alpha_matches_value_alpha():
+    """At every pixel of every splat's tile rectangle the fp32 alpha the decisions use equals the
+    fp64 alpha = (1-t) min(0.99, o_n G) + t (1 - (1 - min(0.99, o_p G))^(1/K)) within 1e-5 relative
+    wherever alpha >= 1e-3 (the oracle's ambiguity band around the 1/255 floor is 1e-5 relative, so
+    outside it both tracks take the same floor decision), for K = 2, 3 and 5."""
+    opts, frames = _decision_track_frames()
+    afl = opts.alpha_floor
+    seen_k = set()
+    n_pairs = 0
+    for cam, fr in frames:
+        S, PX, PY = _rect_pairs(cam, fr, opts)
+        a32, a64 = oracle.pair_alpha(fr, S, PX, PY, opts)
+        m = a64 >= 1e-3
+        np.testing.assert_array_less(np.abs(a32.astype(np.float64) - a64)[m], 1e-5 * a64[m])
+        clear = np.abs(a64 - afl) > 2e-5 * afl
+        np.testing.assert_array_equal((a32 >= np.float32(afl))[clear], (a64 >= afl)[clear])
+        tpos = fr.rec32[S, 7] > 0
+        seen_k |= set(np.unique(fr.rec32[S[tpos & m], 8]).astype(int).tolist())
+        n_pairs += int(m.sum())
+    assert {2, 3, 5} <= seen_k
+    assert n_pairs > 200_000
+
+
+def test_tile_rectangle_covers_the_three_sigma_footprint():
+    """The tile rectangle is the set of tiles of the square u +- r, v +- r with r = ceil(3 sqrt(
+    lambda_max)) of the filtered 2D covariance (eigenvalues by numpy from the value track's conic),
+    clamped to the grid; every pixel inside the 3-sigma ellipse lies in it."""
+    opts, frames = _decision_track_frames()
+    checked = 0
+    for cam, fr in frames:
+        TX, TY = oracle.tiles(cam, opts)
+        for i in np.nonzero(fr.rect[:, 0] >= 0)[0]:
+            v = fr.val64[i]
+            conic = np.array([[v[2], v[3]], [v[3], v[4]]])
+            lmax = np.linalg.eigvalsh(np.linalg.inv(conic)).max()
+            r3 = 3 * math.sqrt(lmax)
+            if abs(r3 - round(r3)) < 1e-4:
+                continue                     # radius on an integer: fp32 and fp64 may round apart
+            r = math.ceil(r3)
+            e = [(v[0] - r) / opts.tile_w, (v[0] + r) / opts.tile_w, (v[1] - r) / opts.tile_h, (v[1] + r) / opts.tile_h]
+            if any(abs(x - round(x)) < 1e-4 for x in e):
+                continue                     # square edge on a tile boundary
+            want = [max(math.floor(e[0]), 0), min(math.floor(e[1]), TX - 1),
+                    max(math.floor(e[2]), 0), min(math.floor(e[3]), TY - 1)]
+            assert list(fr.rect[i]) == want, (i, list(fr.rect[i]), want)
+            ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+            dx, dy = xs + 0.5 - v[0], ys + 0.5 - v[1]
+            inside = (conic[0, 0] * dx * dx + 2 * conic[0, 1] * dx * dy + conic[1, 1] * dy * dy) <= 9.0
+            tx, ty = xs[inside] // opts.tile_w, ys[inside] // opts.tile_h
+            assert np.all((tx >= want[0]) & (tx <= want[1]) & (ty >= want[2]) & (ty <= want[3]))
+            checked += 1
+    assert checked > 400

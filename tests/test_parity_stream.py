@@ -1,4 +1,4 @@
-"""Streamed hierarchy (h3dgs_upload_hierarchy_streamed, h3dgs_stream_update / _cleanup; Sec. 5.3)
+"""Streamed hierarchy (h3dgs_upload_hierarchy_streamed, h3dgs_stream_update / _cleanup; Sec. 6.3)
 against the oracle's residency trace and against the resident render.
 
 Bars: the number of nodes transferred by every update and the resident count after every cleanup

@@ -1,4 +1,4 @@
-"""Pins of the oracle's streaming residency trace (Sec. 5.3) by set arithmetic that does not go
+"""Pins of the oracle's streaming residency trace (Sec. 6.3) by set arithmetic that does not go
 through the trace: transfers of a static camera, the union of the needed sets without cleanup, and
 the residents after an aggressive cleanup."""
 import numpy as np

@@ -70,3 +70,48 @@ def test_noalloc_rejects_trees_beyond_its_scratch():
         h3dgs.h3dgs_select_cut_noalloc(dh, sc.cameras[0], ids, None, offs, 8,
                                        n_nodes=(1 << 24) + 1)
     assert e.value.status == 4   # H3DGS_ERR_CAPACITY, nothing launched
+
+
+def test_noalloc_truncates_at_capacity_and_reports_the_full_size():
+    """A capacity below the cut size: the first `capacity` ids are written, the end offset is clamped
+    to the capacity, and the call returns H3DGS_ERR_CAPACITY after storing the untruncated size."""
+    import torch
+    sc, h = scenes.tiny()
+    dh = gpu_path.upload(h)
+    cam = synth.with_tau(sc.cameras[0], 1.5)
+    ids, _, _ = gpu_path.context().select_cut([cam])
+    ids = ids.cpu().numpy()
+    cap = len(ids) // 3
+    assert cap > 32
+    ids2 = torch.full((cap + 16,), -7, dtype=torch.int32, device="cuda")
+    offs2 = torch.full((2,), -7, dtype=torch.int64, device="cuda")
+    with pytest.raises(h3dgs.H3dgsError) as e:
+        h3dgs.h3dgs_select_cut_noalloc(dh, cam, ids2, None, offs2, cap, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert e.value.status == 4           # H3DGS_ERR_CAPACITY
+    assert e.value.total == len(ids)
+    o = offs2.cpu().numpy()
+    assert o[0] == 0 and o[1] == cap
+    got = ids2.cpu().numpy()
+    np.testing.assert_array_equal(got[:cap], ids[:cap])
+    assert np.all(got[cap:] == -7)        # nothing written beyond the capacity
+
+
+def test_noalloc_without_total_does_not_synchronise_and_matches_after_a_sync():
+    import torch
+    sc, h = scenes.tiny()
+    dh = gpu_path.upload(h)
+    cam = synth.with_tau(sc.cameras[0], 4.0)
+    ids, t, offs = gpu_path.context().select_cut([cam])
+    cap = dh.n
+    ids2 = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    t2 = torch.full((cap,), -7.0, dtype=torch.float32, device="cuda")
+    offs2 = torch.full((2,), -7, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    assert h3dgs.h3dgs_select_cut_noalloc(dh, cam, ids2, t2, offs2, cap, stream.cuda_stream,
+                                          want_total=False) is None
+    stream.synchronize()
+    n = int(offs2[1].item())
+    assert n == len(ids) and int(offs2[0].item()) == 0
+    np.testing.assert_array_equal(ids2[:n].cpu().numpy(), ids.cpu().numpy())
+    np.testing.assert_array_equal(t2[:n].cpu().numpy().view(np.uint32), t.cpu().numpy().view(np.uint32))
