@@ -714,17 +714,53 @@ struct SplatF { float u, v, ca, cb, cc, on, op, t, K; float depth; int32_t rect[
 const float KH = -0.72134752044448170f;   // -0.5 * log2(e), rounded to fp32
 const float KL = 1.44269504088896341f;    //  log2(e), rounded to fp32
 
-SplatF project_f(const OrCamera& cam, const OrOpts& o, const float a[NINTERP]) {
+// Camera-space point of the decision track, x_c = R m + T per row as a compensated dot product
+// (Dot2 of Ogita, Rump & Oishi 2005): each product is split exactly into p + e with an FMA
+// (e = fmaf(a, b, -p)), partial sums are split exactly by Knuth's TwoSum, and the collected
+// errors are added back at the end.  The terms enter in the order R_i0 m_0, R_i1 m_1, R_i2 m_2,
+// T_i.  A plain fp32 dot product would lose the metre-scale camera-space coordinates of a
+// kilometre-scale scene to cancellation between R m and T; this one is as accurate as if it had
+// been evaluated in double the precision and rounded.
+float dot2_f(const float* r, float t, const float m[3]) {
+    auto twosum = [](float a, float b, float& err) {
+        const float x = a + b;
+        const float bv = x - a;
+        err = (a - (x - bv)) + (b - bv);
+        return x;
+    };
+    float acc = r[0] * m[0];
+    float comp = fmaf(r[0], m[0], -acc);
+    for (int j = 1; j < 3; ++j) {
+        const float prod = r[j] * m[j];
+        const float perr = fmaf(r[j], m[j], -prod);
+        float serr;
+        acc = twosum(acc, prod, serr);
+        comp = comp + (serr + perr);
+    }
+    float serr;
+    acc = twosum(acc, t, serr);
+    comp = comp + serr;
+    return acc + comp;
+}
+
+// x_c of cut node n with parent weight t: the node's and the parent's means mapped to camera space
+// (dot2_f) and interpolated there, xc = fmaf(t, x_p, (1 - t) x_n) -- the same point as the
+// transform of the interpolated mean, without rounding the km-scale interpolated mean to fp32.
+void view_point_f(const OrCamera& cam, const OrHier32& h, int64_t n, float t, float xc[3]) {
+    const int32_t p = h.parent[n];
+    const bool use_p = (t != 0.0f) && p >= 0;
+    for (int i = 0; i < 3; ++i) {
+        const float xn = dot2_f(cam.R + 3 * i, cam.T[i], h.mean + 3 * n);
+        if (!use_p) { xc[i] = xn; continue; }
+        const float xp = dot2_f(cam.R + 3 * i, cam.T[i], h.mean + 3 * (int64_t)p);
+        xc[i] = fmaf(t, xp, (1.0f - t) * xn);
+    }
+}
+
+SplatF project_f(const OrCamera& cam, const OrOpts& o, const float a[NINTERP], const float xc[3]) {
     SplatF s{};
     s.visible = false;
     const float* W = cam.R;
-    float xc[3];
-    for (int i = 0; i < 3; ++i) {
-        float acc = W[3 * i + 0] * a[0];
-        acc = fmaf(W[3 * i + 1], a[1], acc);
-        acc = fmaf(W[3 * i + 2], a[2], acc);
-        xc[i] = acc + cam.T[i];
-    }
     const float z = xc[2];
     if (!(z > cam.znear)) return s;
     const float xz = xc[0] / z, yz = xc[1] / z;
@@ -886,7 +922,9 @@ void or_preprocess(const OrCamera* cam, const OrOpts* o, const OrHier32* h, cons
         float ti = o->interpolate ? t[i] : 0.0f;
         interp_f(*h, ids[i], ti, a);
         interp_d(*h, *hd, ids[i], (double)ti, b);
-        SplatF sf = project_f(*cam, *o, a);
+        float xc[3];
+        view_point_f(*cam, *h, ids[i], ti, xc);
+        SplatF sf = project_f(*cam, *o, a, xc);
         float* r = rec32 + 10 * i;
         int32_t* rc = rect + 4 * i;
         if (!sf.visible) {

@@ -355,17 +355,14 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         const bool use_p = (t != 0.0f) && p >= 0;
         const float omt = 1.0f - t;
         // ---- interpolated attributes
-        float mu[3], s[3], ql[4];
+        float s[3], ql[4];
         const float4 qn4 = h.rot[n];
         float qv[4] = {qn4.x, qn4.y, qn4.z, qn4.w};
-        for (int d = 0; d < 3; ++d) { mu[d] = h.mean[3 * (int64_t)n + d]; s[d] = h.scale[3 * (int64_t)n + d]; }
+        for (int d = 0; d < 3; ++d) s[d] = h.scale[3 * (int64_t)n + d];
         if (use_p) {
             const float4 qp4 = h.rot[p];
             const float qpv[4] = {qp4.x, qp4.y, qp4.z, qp4.w};
-            for (int d = 0; d < 3; ++d) {
-                mu[d] = fmaf(t, h.mean[3 * (int64_t)p + d], omt * mu[d]);
-                s[d] = fmaf(t, h.scale[3 * (int64_t)p + d], omt * s[d]);
-            }
+            for (int d = 0; d < 3; ++d) s[d] = fmaf(t, h.scale[3 * (int64_t)p + d], omt * s[d]);
             for (int d = 0; d < 4; ++d) qv[d] = fmaf(t, qpv[d], omt * qv[d]);
         }
         for (int d = 0; d < 4; ++d) ql[d] = qv[d];
@@ -373,8 +370,15 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         const float q[4] = {ql[0] / qnorm, ql[1] / qnorm, ql[2] / qnorm, ql[3] / qnorm};
         // ---- forward recompute
         const float* W = cam.R;
+        // the camera-space mean exactly as the forward pass formed it (compensated transforms of the
+        // node's and the parent's means, interpolated in camera space)
         float xc[3];
-        for (int i = 0; i < 3; ++i) xc[i] = W[3 * i] * mu[0] + W[3 * i + 1] * mu[1] + W[3 * i + 2] * mu[2] + cam.T[i];
+        view_point(W, cam.T, h.mean[3 * (int64_t)n], h.mean[3 * (int64_t)n + 1], h.mean[3 * (int64_t)n + 2], xc);
+        if (use_p) {
+            float xp[3];
+            view_point(W, cam.T, h.mean[3 * (int64_t)p], h.mean[3 * (int64_t)p + 1], h.mean[3 * (int64_t)p + 2], xp);
+            for (int i = 0; i < 3; ++i) xc[i] = ffma(t, xp[i], fmul(fsub(1.0f, t), xc[i]));
+        }
         const float z = xc[2], iz = 1.0f / z;
         const float xz = xc[0] * iz, yz = xc[1] * iz;
         const bool x_in = xz > -cam.limx && xz < cam.limx, y_in = yz > -cam.limy && yz < cam.limy;
@@ -465,7 +469,12 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         float dql[4];
         for (int d = 0; d < 4; ++d) dql[d] = (dq[d] - q[d] * qdot) / qnorm;
         // ---- colour
-        float dv[3] = {mu[0] - cam.c[0], mu[1] - cam.c[1], mu[2] - cam.c[2]};
+        // view direction mean - c, as in the forward pass
+        float dv[3];
+        for (int j = 0; j < 3; ++j) {
+            const float dn = (h.mean[3 * (int64_t)n + j] - cam.ch[j]) - cam.cl[j];
+            dv[j] = use_p ? fmaf(t, (h.mean[3 * (int64_t)p + j] - cam.ch[j]) - cam.cl[j], omt * dn) : dn;
+        }
         const float dn = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
         const float x = dv[0] / dn, y = dv[1] / dn, zz = dv[2] / dn;
         const float xx = x * x, yy = y * y, z2 = zz * zz;

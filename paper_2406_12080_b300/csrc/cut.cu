@@ -47,6 +47,7 @@ __global__ void camera_setup_kernel(CamBatch b, DevCam* __restrict__ out) {
     d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
     d.width = c.width; d.height = c.height; d.znear = c.znear; d.tau = c.tau;
     camera_centre(c, d.c);
+    camera_centre_pair(c, d.ch, d.cl);
     d.f = fmaxf(c.fx, c.fy);
     d.limx = fdiv(fmul(0.65f, (float)c.width), c.fx);
     d.limy = fdiv(fmul(0.65f, (float)c.height), c.fy);

@@ -33,7 +33,8 @@ struct DevCam {
     float fx, fy, cx, cy;
     int32_t width, height;
     float znear, tau;
-    float c[3];        // camera centre  -R^T T
+    float c[3];        // camera centre  -R^T T (fixed fp32 order: the granularity's decisions)
+    float ch[3], cl[3];// the centre as an unevaluated sum ch + cl of a compensated dot product (values)
     float f;           // max(fx, fy)
     float limx, limy;  // 1.3 tan(half fov): clamp of x/z, y/z in the EWA Jacobian
     int32_t tiles_x, tiles_y;
@@ -81,6 +82,48 @@ __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b)
 __device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
 __device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// World -> camera transform of one point, x_c[i] = R_i . m + T_i, as a compensated dot product
+// (Ogita, Rump & Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26(6), 2005: Dot2,
+// with the products split exactly by an FMA and the sums by Knuth's TwoSum).  Large scenes keep
+// their coordinates in metres over kilometres, where fp32 resolves about 3e-5 m, while a splat a
+// metre in front of the camera needs camera-space coordinates far finer than that: the plain
+// fmaf chain loses them to cancellation between R m and T (up to 0.05 px at 720p for near splats);
+// Dot2 returns the point as if the dot product were evaluated in twice the working precision and
+// then rounded.  Fixed fp32 order: products (R_i0 m_0), (R_i1 m_1), (R_i2 m_2), then T_i.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = fadd(a, b);
+    const float z = fsub(s, a);
+    e = fadd(fsub(a, fsub(s, z)), fsub(b, z));
+}
+// r0 m0 + r1 m1 + r2 m2 + b as the unevaluated sum hi + lo (Dot2 before its final addition)
+__device__ __forceinline__ void dot2_pair(float r0, float r1, float r2, float b, float m0, float m1, float m2,
+                                          float& hi, float& lo) {
+    float p = fmul(r0, m0);
+    float err = ffma(r0, m0, -p);
+    const float rv[2] = {r1, r2}, mv[2] = {m1, m2};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float h = fmul(rv[j], mv[j]);
+        const float r = ffma(rv[j], mv[j], -h);
+        float q;
+        two_sum(p, h, p, q);
+        err = fadd(err, fadd(q, r));
+    }
+    float q;
+    two_sum(p, b, p, q);
+    hi = p;
+    lo = fadd(err, q);
+}
+__device__ __forceinline__ float dot2_row(const float* Ri, float Ti, float m0, float m1, float m2) {
+    float hi, lo;
+    dot2_pair(Ri[0], Ri[1], Ri[2], Ti, m0, m1, m2, hi, lo);
+    return fadd(hi, lo);
+}
+__device__ __forceinline__ void view_point(const float* R, const float* T, float m0, float m1, float m2, float xc[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) xc[i] = dot2_row(R + 3 * i, T[i], m0, m1, m2);
+}
+
 // Granularity (Sec. 4.2): projected size of the node's box, largest side over the distance from the
 // camera centre to the closest point of the box; +inf with the camera inside the box.
 // c = the camera centre, f = max(fx, fy).
@@ -108,6 +151,18 @@ __device__ __forceinline__ void camera_centre(const h3dgs_camera& cam, float c[3
         acc = ffma(cam.R[3 + j], cam.T[1], acc);
         acc = ffma(cam.R[6 + j], cam.T[2], acc);
         c[j] = -acc;
+    }
+}
+
+// The camera centre -R^T T as hi + lo pairs (compensated, for view directions of km-scale scenes):
+// a direction m - c is then (m - hi) - lo, exact to a few units in the last place of |m - c|.
+__device__ __forceinline__ void camera_centre_pair(const h3dgs_camera& cam, float hi[3], float lo[3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float h, l;
+        dot2_pair(cam.R[j], cam.R[3 + j], cam.R[6 + j], 0.0f, cam.T[0], cam.T[1], cam.T[2], h, l);
+        hi[j] = -h;
+        lo[j] = -l;
     }
 }
 

@@ -125,15 +125,20 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
             continue;
         }
         const Interp a = interp_geometry(h, rn, rp, use_p, t);
-        // ---- view transform
+        // ---- view transform: the node's and the parent's means are transformed separately (compensated)
+        // and interpolated in camera space, which equals transforming the interpolated mean but keeps
+        // the precision that a lerp of km-scale world coordinates would lose
         const float* W = cam.R;
         float xc[3];
+        view_point(W, cam.T, __ldg(h.mean + 3 * (int64_t)rn), __ldg(h.mean + 3 * (int64_t)rn + 1),
+                   __ldg(h.mean + 3 * (int64_t)rn + 2), xc);
+        if (use_p) {
+            float xp[3];
+            view_point(W, cam.T, __ldg(h.mean + 3 * (int64_t)rp), __ldg(h.mean + 3 * (int64_t)rp + 1),
+                       __ldg(h.mean + 3 * (int64_t)rp + 2), xp);
+            const float omt_v = fsub(1.0f, t);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            float acc = fmul(W[3 * i + 0], a.mean[0]);
-            acc = ffma(W[3 * i + 1], a.mean[1], acc);
-            acc = ffma(W[3 * i + 2], a.mean[2], acc);
-            xc[i] = fadd(acc, cam.T[i]);
+            for (int i = 0; i < 3; ++i) xc[i] = lerp_c(t, omt_v, xc[i], xp[i]);
         }
         const float z = xc[2];
         bool vis = z > cam.znear;
@@ -231,7 +236,15 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
         ++visible;
         // ---- view-dependent colour (value only), SH interpolated with the same weight
         const float omt = fsub(1.0f, t);
-        float dx = a.mean[0] - cam.c[0], dy = a.mean[1] - cam.c[1], dz = a.mean[2] - cam.c[2];
+        // direction from the camera centre to the (interpolated) mean: node and parent directions
+        // against the compensated centre, interpolated at metre scale
+        float dir[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float dn = (__ldg(h.mean + 3 * (int64_t)rn + j) - cam.ch[j]) - cam.cl[j];
+            dir[j] = use_p ? lerp_c(t, omt, dn, (__ldg(h.mean + 3 * (int64_t)rp + j) - cam.ch[j]) - cam.cl[j]) : dn;
+        }
+        float dx = dir[0], dy = dir[1], dz = dir[2];
         const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
         dx *= inv; dy *= inv; dz *= inv;
         float Y[16];

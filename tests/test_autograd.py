@@ -39,6 +39,7 @@ def test_autograd_gradients_match_the_oracle_through_the_activations(freeze):
     opts = oracle.Opts()
     fr = oracle.render(cam, h, opts)
     w = np.random.default_rng(3).normal(size=fr.image.shape)
+    w[:, fr.ambiguous] = 0.0
     (images * torch.from_numpy(w.reshape(-1).astype(np.float32)).cuda()).sum().backward()
     og = oracle.backward(cam, h, fr, w, opts, freeze_leaves=int(freeze))
     leaf = h.child_count == 0
@@ -51,8 +52,9 @@ def test_autograd_gradients_match_the_oracle_through_the_activations(freeze):
         g = getattr(params, name).grad.cpu().numpy().astype(np.float64).reshape(o.shape)
         scale = np.abs(o).max()
         assert scale > 0 or np.abs(g).max() == 0, name
-        if scale > 0:
-            assert np.abs(g - o).max() <= 2e-3 * scale, (name, np.abs(g - o).max() / scale)
+        if scale > 0:   # per element: the backward bar, the activations' chain rule in torch fp32 on top
+            excess = (np.abs(g - o) - 2e-3 * np.abs(o)) / scale
+            assert excess.max() <= 1e-5, (name, float(excess.max()))
     if freeze:
         for name in want:
             g = getattr(params, name).grad.cpu().numpy().reshape(h.n, -1)

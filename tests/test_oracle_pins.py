@@ -3,6 +3,7 @@
 Each test names the passage of the paper it checks and the independent fact used: a closed
 form, a Monte-Carlo estimate, brute force, an invariant, or a textbook routine (scipy).
 """
+import functools
 import itertools
 import math
 
@@ -602,6 +603,58 @@ def _rect_pairs(cam, fr, opts):
         PX.append(X.ravel() + 0.5)
         PY.append(Y.ravel() + 0.5)
     return np.concatenate(S), np.concatenate(PX), np.concatenate(PY)
+
+
+@functools.lru_cache(maxsize=None)
+def _street_frames():
+    """Two 320x180 views of a 100k-leaf street corridor: kilometre-scale world coordinates, metre-scale
+    camera-space ones (the large-scene setting of Sec. 6)."""
+    opts = oracle.Opts()
+    sc = synth.corridor_scene(seed=3, n_leaves=100_000)
+    h = oracle.build_tree(sc.leaves)
+    _, views = synth.optimisation_views(seed=3, width=320, height=180)
+    return opts, [(views[k], oracle.render(views[k], h, opts)) for k in (0, 5)]
+
+
+def _ulp(x):
+    return np.spacing(np.abs(np.asarray(x, np.float64)).astype(np.float32)).astype(np.float64)
+
+
+def _uv_resolution_bound(cam, fr, S, PX, PY):
+    """Relative alpha error that the fp32 representation of the splat's screen position alone allows:
+    |dp/du| du + |dp/dv| dv with p the natural exponent of the value track and du, dv four units in
+    the last place of fp32 screen coordinates (u = fx x/z + cx is resolved at the scale of the
+    image, max(|u|, width)), plus 2e-6 (1 + |p|) for the rounding of the exponent itself."""
+    v = fr.val64[S]
+    dx, dy = PX - v[:, 0], PY - v[:, 1]
+    A, B, Cc = v[:, 2], v[:, 3], v[:, 4]
+    p = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy
+    du = 4 * _ulp(np.maximum(np.abs(v[:, 0]), cam.width))
+    dv = 4 * _ulp(np.maximum(np.abs(v[:, 1]), cam.height))
+    return np.abs(A * dx + B * dy) * du + np.abs(B * dx + Cc * dy) * dv + 2e-6 * (1 + np.abs(p))
+
+
+def test_decision_track_keeps_metre_precision_in_kilometre_scenes():
+    """On a street corridor 1 km long the decision track's splat centres stay within a few fp32 units
+    in the last place of the exact ones (the world -> camera transform must not cancel the
+    kilometre-scale coordinates away), and its alpha matches the value track's alpha within the
+    resolution of fp32 screen coordinates at every pair with alpha >= 1e-3."""
+    opts, frames = _street_frames()
+    n_pairs = 0
+    for cam, fr in frames:
+        vis = fr.rect[:, 0] >= 0
+        r, v = fr.rec32[vis].astype(np.float64), fr.val64[vis]
+        np.testing.assert_array_less(np.abs(r[:, 0] - v[:, 0]), 4 * _ulp(np.maximum(np.abs(v[:, 0]), cam.width)))
+        np.testing.assert_array_less(np.abs(r[:, 1] - v[:, 1]), 4 * _ulp(np.maximum(np.abs(v[:, 1]), cam.height)))
+        np.testing.assert_array_less(np.abs(r[:, 9] - v[:, 12]), 4e-7 * v[:, 12])         # depth
+        assert np.sum(r[:, 7] > 0) > 5000
+        S, PX, PY = _rect_pairs(cam, fr, opts)
+        a32, a64 = oracle.pair_alpha(fr, S, PX, PY, opts)
+        m = a64 >= 1e-3
+        bound = _uv_resolution_bound(cam, fr, S, PX, PY)
+        np.testing.assert_array_less(np.abs(a32.astype(np.float64) - a64)[m], (bound * a64)[m])
+        n_pairs += int(m.sum())
+    assert n_pairs > 500_000
 
 
 def test_decision_alpha_matches_value_alpha():

@@ -11,7 +11,7 @@ import pytest
 import oracle
 from paper_2406_12080_b300 import h3dgs, synth
 from tests import gpu_path, scenes
-from tests.test_parity_backward import _check, _gpu_grads
+from tests.test_parity_backward import _check, _gpu_grads, loss_weight
 from tests.test_parity_forward import _compare
 
 pytestmark = pytest.mark.gpu
@@ -125,7 +125,7 @@ def test_backward_on_compacted_tree(compacted_tiny, tau):
     opts = oracle.Opts()
     dh = gpu_path.upload(oh)
     fr = oracle.render(cam, oh, opts)
-    w = np.random.default_rng(3).normal(size=fr.image.shape)
+    w = loss_weight(fr, 3)
     og = oracle.backward(cam, oh, fr, w, opts)
     gg = _gpu_grads(dh, cam, opts, w)
     _check(gg, og)

@@ -3,14 +3,14 @@ adjoint (h3dgs_render_backward_ex) with the oracle.
 
 Bars: images at the forward bar (2e-3 on unambiguous pixels); depth within 2e-3 of the frame's
 largest splat depth (the depth is a weighted mean of splat depths whose weights carry the colour's
-error); gradients at the backward bar (1e-3 of each attribute group's scale)."""
+error); gradients at the per-element backward bar of tests/test_parity_backward.py."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2406_12080_b300 import h3dgs, synth
 from tests import gpu_path, scenes
-from tests.test_parity_backward import _check
+from tests.test_parity_backward import _check, loss_weight
 
 pytestmark = pytest.mark.gpu
 IMG_TOL = 2e-3
@@ -68,7 +68,7 @@ def test_forward_batch_with_exposure_and_depth(chunk):
     for k, cam in enumerate(cams):
         ofr = oracle.render(cam, h, opts, exposure=E[k])
         amb = ofr.ambiguous
-        assert amb.mean() < 1e-3
+        assert amb.mean() < 2e-4
         err = np.abs(imgs[k] - ofr.image).max(axis=0)
         assert err[~amb].max() <= IMG_TOL, err[~amb].max()
         zmax = ofr.val64[ofr.rect[:, 0] >= 0, 12].max()
@@ -100,9 +100,9 @@ def test_backward_with_depth_and_exposure(tau, chunk):
     opts = oracle.Opts()
     E = _exposures(1, 2)
     fr = oracle.render(cam, h, opts, exposure=E[0])
-    rng = np.random.default_rng(3)
-    w = rng.normal(size=fr.image.shape)
-    wd = rng.normal(size=fr.depth.shape) * 0.05
+    w = loss_weight(fr, 3)
+    wd = np.random.default_rng(4).normal(size=fr.depth.shape) * 0.05
+    wd[fr.ambiguous] = 0.0
     og = oracle.backward(cam, h, fr, w, opts, dL_ddepth=wd, exposure=E[0])
     cut, Ed, images, depth = _render([cam], opts, E, chunk, save=1)
     grads = {k: torch.zeros_like(getattr(dh, k)) for k in ("mean", "scale", "rot", "opacity", "sh")}

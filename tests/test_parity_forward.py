@@ -4,7 +4,7 @@ Bars: bit-exact for the cut (ids and t), the interpolated fp32 attributes, the s
 (the decision track), tile rectangles and per-tile lists; images within 2e-3 max abs per channel
 on every pixel whose per-pixel decisions are unambiguous in fp32 (the oracle flags those within
 a 1e-5 relative band of the alpha floor or the transmittance stop), and the flagged fraction
-below 1e-3.  Full-size parity runs the 1M-leaf street corridor at 1920x1080.
+below 2e-4 (measured: at most 5e-5 on the test scenes).  Full-size parity runs the 1M-leaf street corridor at 1920x1080.
 """
 import numpy as np
 import pytest
@@ -48,7 +48,7 @@ def _compare(cam, h, dh, opts, cams_index=0, chunk=None):
     amb = ofr.ambiguous
     img = g.images[0]
     err = np.abs(img - ofr.image).max(axis=0)
-    assert amb.mean() < 1e-3
+    assert amb.mean() < 2e-4
     assert err[~amb].max() <= IMG_TOL, err[~amb].max()
     nc = g.n_contrib.reshape(cam.height, cam.width)
     np.testing.assert_array_equal(nc[~amb], ofr.n_contrib[~amb])
