@@ -123,6 +123,8 @@ typedef struct {
     int64_t n_items;      /* blend work items (tiles, split tiles count once per chunk) */
     int64_t n_evals_interp; /* main-pass evaluations of splats with an interpolated parent
                                (t != 0, Eq. alphap evaluated too; profiling level 2, else 0) */
+    int64_t n_contrib;    /* (pixel, splat) pairs whose colour was accumulated: alpha at or above the
+                             floor, before the transmittance stop (profiling level 2, else 0) */
 } h3dgs_stats;
 
 /* Per-stage device times of the most recent select_cut / render / render_backward, in ms,

@@ -38,12 +38,14 @@ template <typename T>
 T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
 
 // device counter block
-// C_EVALS, C_EVALS_T and C_EVALS_I occupy two words each (64-bit counters, in this order)
+// C_EVALS, C_EVALS_T, C_EVALS_I and C_CONTRIB occupy two words each (64-bit counters, in this order)
 // C_NSORTED: a zero word (the bounded-wait probe); C_NTSORT: unused
 // C_NITEMS: 4 words (items, producers, singles, split tiles).  C_FLAGS: render flags (cleared by every render);
 // C_CUTFLAGS: cut flags (cleared by every cut); the stats report both.
 enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NSORTED = 6,
-       C_NTSORT = 7, C_EVALS = 8, C_EVALS_T = 10, C_EVALS_I = 12, C_NITEMS = 14, C_CUTFLAGS = 18, C_COUNT = 19 };
+       C_NTSORT = 7, C_NITEMS = 14, C_CUTFLAGS = 18, C_EVALS = 20, C_EVALS_T = 22, C_EVALS_I = 24, C_CONTRIB = 26,
+       C_COUNT = 28 };
+constexpr int EVAL_WORDS = 8;   // the four 64-bit blend counters from C_EVALS on
 
 }  // namespace
 
@@ -742,14 +744,14 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
         rl.n = 5;
         rl.p[0] = cnt + C_FLAGS;    rl.words[0] = 1;
         rl.p[1] = cnt + C_NVISIBLE; rl.words[1] = 1;
-        rl.p[2] = cnt + C_EVALS;    rl.words[2] = 6;
+        rl.p[2] = cnt + C_EVALS;    rl.words[2] = EVAL_WORDS;
         rl.p[3] = P<uint32_t>(ctx->ranges); rl.words[3] = 2 * (uint64_t)ctx->n_tiles;
         rl.p[4] = base;             rl.words[4] = total;
         CK(launch_reset(rl, ctx->num_sms, s), "frame reset");
     } else {
         CK(cudaMemsetAsync(cnt + C_FLAGS, 0, sizeof(uint32_t), s), "memset");
         CK(cudaMemsetAsync(cnt + C_NVISIBLE, 0, sizeof(uint32_t), s), "memset");
-        CK(cudaMemsetAsync(cnt + C_EVALS, 0, 6 * sizeof(uint32_t), s), "memset");
+        CK(cudaMemsetAsync(cnt + C_EVALS, 0, EVAL_WORDS * sizeof(uint32_t), s), "memset");
         CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(int2) * (size_t)ctx->n_tiles, s), "memset");
         CK(ensure(ctx->hists, sizeof(uint32_t) * 2 * 4 * 256), "histograms");
         CK(cudaMemsetAsync(ctx->hists.p, 0, sizeof(uint32_t) * 2 * 4 * 256, s), "memset");
@@ -941,6 +943,8 @@ h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out) {
     out->n_evals_tpass = (int64_t)ev;
     std::memcpy(&ev, c + C_EVALS_I, sizeof(ev));
     out->n_evals_interp = (int64_t)ev;
+    std::memcpy(&ev, c + C_CONTRIB, sizeof(ev));
+    out->n_contrib = (int64_t)ev;
     out->n_items = c[C_NITEMS];
     return H3DGS_OK;
 }

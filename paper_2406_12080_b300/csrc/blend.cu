@@ -215,18 +215,31 @@ __device__ __forceinline__ void write_pixel(float* img, int64_t plane, float T, 
 // Walk of one item over list entries [begin, end) for this thread's two pixels.  MAIN: the exact
 // skip/stop rules with colour; otherwise the transmittance pass (product of (1 - alpha) over
 // contributors, no colour; a pixel is finished once T < t_min, after which nothing it could add
-// matters).  Branch-free per entry: the alpha of every live pixel is computed and applied through
-// selects; the paired fp32 instructions evaluate both pixels at once.  DEPTH: the expected depth Dp
-// is accumulated as a fourth channel.  SAVE: track the last contributor (kept for the adjoint).
+// matters).  DEPTH: the expected depth Dp is accumulated as a fourth channel.  SAVE: track the
+// last contributor (kept for the adjoint).
+//
+// The per-entry work is arranged to keep the per-pixel decisions off the critical ALU pipe while
+// producing bit-identical results to the direct formulation:
+//   * each pixel has a floor threshold fl (alpha_floor, or +inf once the pixel has stopped or lies
+//     outside the image), so one compare per pixel both applies the 1/255 skip and drops finished
+//     pixels;
+//   * a pixel that does not take the entry gets alpha_eff = 0, and T (1 - alpha_eff) = T and
+//     C + c alpha_eff T = C hold exactly, so T and the colours are updated with paired fp32
+//     arithmetic and no selects;
+//   * the transmittance stop can only happen at a pixel that takes the entry, at most once per
+//     pixel, so it is handled in a warp-uniform branch that is rarely entered: it freezes the
+//     pixel (fl = +inf), and in the main pass undoes the entry for it (stop before the splat).
 template <int TW, int TH, bool MAIN, bool COUNT, bool DEPTH, bool SAVE>
 __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const uint32_t* __restrict__ list,
                                             const float4* __restrict__ splat, int begin, int end, int list0,
                                             float clampv, float afloor, float tmin, float4* s_a, float4* s_b,
                                             float4* s_c, uint32_t* s_m, float* s_d, float4* s_box, float2& T, float2& C0,
                                             float2& C1, float2& C2, float2& Dp, int2& last, bool& done0, bool& done1,
-                                            unsigned int& evals, unsigned int& evals_i) {
+                                            unsigned int& evals, unsigned int& evals_i, unsigned int& contribs) {
     constexpr int NT2 = TW * TH / 2, NW = NT2 / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float INF = __int_as_float(0x7f800000);
+    float2 fl = make_float2(done0 ? INF : afloor, done1 ? INF : afloor);
     for (int b0 = begin; b0 < end; b0 += NT2) {
         // the warp's live pixels' bounding box (pixel centres): entries that cannot reach alpha_floor
         // inside it are skipped by the warp mask (its stopped pixels no longer matter)
@@ -275,31 +288,38 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
                         if (s_b[j].w != 0.0f) evals_i += (unsigned)!done0 + (unsigned)!done1;
                     }
                     const float2 alpha = pair_alpha2(g.px, g.py, s_a[j], s_b[j], &s_c[j], clampv);
-                    const bool live0 = !done0 && alpha.x >= afloor, live1 = !done1 && alpha.y >= afloor;
-                    if (!__any_sync(0xffffffffu, live0 || live1)) continue;   // no pixel of the warp takes it
-                    const float2 Tn = __fmul2_rn(T, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-alpha.x, -alpha.y)));
+                    bool take0 = alpha.x >= fl.x, take1 = alpha.y >= fl.y;
+                    if (!__any_sync(0xffffffffu, take0 || take1)) continue;   // no pixel of the warp takes it
+                    float2 ae = make_float2(take0 ? alpha.x : 0.0f, take1 ? alpha.y : 0.0f);
+                    float2 Tn = __fmul2_rn(T, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-ae.x, -ae.y)));
+                    const bool stop0 = take0 && Tn.x < tmin, stop1 = take1 && Tn.y < tmin;
+                    if (__any_sync(0xffffffffu, stop0 || stop1)) {
+                        // at most once per pixel: the pixel finishes here
+                        if (stop0) {
+                            done0 = true;
+                            fl.x = INF;
+                            if (MAIN) { ae.x = 0.0f; Tn.x = T.x; take0 = false; }
+                        }
+                        if (stop1) {
+                            done1 = true;
+                            fl.y = INF;
+                            if (MAIN) { ae.y = 0.0f; Tn.y = T.y; take1 = false; }
+                        }
+                    }
                     if (MAIN) {
-                        const bool stop0 = live0 && Tn.x < tmin, stop1 = live1 && Tn.y < tmin;
-                        const bool app0 = live0 && !stop0, app1 = live1 && !stop1;
-                        done0 = done0 || stop0;
-                        done1 = done1 || stop1;
-                        const float2 wt = __fmul2_rn(alpha, T);
-                        const float2 w = make_float2(app0 ? wt.x : 0.0f, app1 ? wt.y : 0.0f);
+                        const float2 w = __fmul2_rn(ae, T);
                         const float4 c = s_c[j];
                         C0 = __ffma2_rn(make_float2(c.x, c.x), w, C0);
                         C1 = __ffma2_rn(make_float2(c.y, c.y), w, C1);
                         C2 = __ffma2_rn(make_float2(c.z, c.z), w, C2);
                         if (DEPTH) Dp = __ffma2_rn(make_float2(s_d[j], s_d[j]), w, Dp);
-                        T = make_float2(app0 ? Tn.x : T.x, app1 ? Tn.y : T.y);
                         if (SAVE) {
                             const int pos = b0 + j + 1 - list0;
-                            last = make_int2(app0 ? pos : last.x, app1 ? pos : last.y);
+                            last = make_int2(take0 ? pos : last.x, take1 ? pos : last.y);
                         }
-                    } else {
-                        T = make_float2(live0 ? Tn.x : T.x, live1 ? Tn.y : T.y);
-                        done0 = done0 || (live0 && Tn.x < tmin);
-                        done1 = done1 || (live1 && Tn.y < tmin);
+                        if (COUNT) contribs += (unsigned)take0 + (unsigned)take1;
                     }
+                    T = Tn;
                 }
                 if (__all_sync(0xffffffffu, done0 && done1)) break;
             }
@@ -315,7 +335,7 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
 // DEPTH: also the expected depth (depth != NULL).  SAVE: also the per-pixel state the adjoint reads
 // (final transmittance, contributor count; T_final and n_contrib != NULL).
 template <int TW, int TH, bool COUNT, bool DEPTH, bool SAVE>
-__global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
+__global__ void __launch_bounds__(TW * TH / 2, 10) blend_queue_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
                                                                   const int2* __restrict__ ranges,
                                                                   const uint32_t* __restrict__ list,
                                                                   const float4* __restrict__ splat,
@@ -342,10 +362,10 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     __shared__ uint32_t s_m[NT2];
     __shared__ float s_d[DEPTH ? NT2 : 1];
     __shared__ float4 s_box[NT2 / 32];
-    __shared__ unsigned int s_evals[3];
+    __shared__ unsigned int s_evals[4];
     __shared__ uint32_t s_k;
     if (threadIdx.x == 0) s_k = atomicAdd(ticket, 1u);
-    if (threadIdx.x < 3) s_evals[threadIdx.x] = 0;
+    if (threadIdx.x < 4) s_evals[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t k = s_k;
     const uint32_t X = counts[1], Y = counts[2];
@@ -376,24 +396,28 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     }
     float2 C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0, Dp = C0;
     int2 last = make_int2(-1, -1);
-    unsigned int evals = 0, evals_i = 0;
+    unsigned int evals = 0, evals_i = 0, contribs = 0;
     bool done0 = !g.in0 || T.x < o.t_min, done1 = !g.in1 || T.y < o.t_min;
     if (main_pass)
         blend_walk2<TW, TH, true, COUNT, DEPTH, SAVE>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
                                                       o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp, last,
-                                                      done0, done1, evals, evals_i);
+                                                      done0, done1, evals, evals_i, contribs);
     else
         blend_walk2<TW, TH, false, COUNT, false, false>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
                                                         o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp,
-                                                        last, done0, done1, evals, evals_i);
+                                                        last, done0, done1, evals, evals_i, contribs);
     if (COUNT) {
         for (int off = 16; off > 0; off >>= 1) {
             evals += __shfl_down_sync(0xffffffffu, evals, off);
             evals_i += __shfl_down_sync(0xffffffffu, evals_i, off);
+            contribs += __shfl_down_sync(0xffffffffu, contribs, off);
         }
         if (lane == 0) {
             atomicAdd(&s_evals[main_pass ? 0 : 1], evals);
-            if (main_pass) atomicAdd(&s_evals[2], evals_i);
+            if (main_pass) {
+                atomicAdd(&s_evals[2], evals_i);
+                atomicAdd(&s_evals[3], contribs);
+            }
         }
     }
     if (role == 0) {
@@ -423,7 +447,7 @@ __global__ void __launch_bounds__(TW * TH / 2) blend_queue_kernel(const DevCam* 
     } else {
         __syncthreads();
     }
-    if (COUNT && threadIdx.x < 3 && s_evals[threadIdx.x])
+    if (COUNT && threadIdx.x < 4 && s_evals[threadIdx.x])
         atomicAdd(n_evals + threadIdx.x, (unsigned long long)s_evals[threadIdx.x]);
     if (role == 0) return;
     if (nch > 1) {

@@ -450,8 +450,8 @@ struct BlendArgs {
     float* scratch_D;             // per (item, pixel) expected depth of split tiles' chunks (depth only)
     float* T_final;
     int32_t* n_contrib;
-    unsigned long long* n_evals;  // [3]: main-pass evaluations, transmittance-pass evaluations, main-pass
-                                  // evaluations of splats with t != 0
+    unsigned long long* n_evals;  // [4]: main-pass evaluations, transmittance-pass evaluations, main-pass
+                                  // evaluations of splats with t != 0, applied contributions
     uint32_t* work;               // look-back workspace of the plan (LB_HEADER_WORDS + 2 per 1024 tiles)
     size_t work_words;
     uint32_t* flags;              // device flag word

@@ -62,7 +62,7 @@ class h3dgs_stats(C.Structure):
     _fields_ = [("n_cut", C.c_int64), ("n_visible", C.c_int64), ("n_pairs", C.c_int64),
                 ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("device_flags", C.c_uint32),
                 ("n_evals", C.c_int64), ("n_evals_tpass", C.c_int64), ("n_items", C.c_int64),
-                ("n_evals_interp", C.c_int64)]
+                ("n_evals_interp", C.c_int64), ("n_contrib", C.c_int64)]
 
 
 STAGES = ["cut", "preprocess", "depth_sort", "duplicate", "tile_sort", "ranges", "blend", "backward_blend",
