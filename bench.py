@@ -35,17 +35,30 @@ sys.path.insert(0, ROOT)
 METRIC = "1080p frames/s (cut+render) & fwd+bwd views/s; % of HBM/FP32 roofline"
 L2_FLUSH_BYTES = 256 << 20
 REF_BUDGET_S = 120.0
-# FP32 operations per evaluated (pixel, splat) pair in the blend kernel, from its op list:
-#   dx, dy (2 FADD); exponent h = fma(ca, dx, cb dy), g = (cc dy) dy, p2 = fma(dx, h, g) (3 FMUL + 2 FFMA);
-#   alpha_n = min(clamp, o_n G) (FMUL + FMNMX); floor test (FSETP); T (1 - alpha) (FADD + FMUL); stop test
-#   (FSETP); w = alpha T (FMUL); colour (3 FFMA)  -> 22 flops (FFMA = 2) plus one MUFU (ex2).
-#   With t != 0 (Eq. alphap, K = 2): o_p G, min, 1 - ap, 1 + sqrt, ap x reciprocal, 1 - t, (1 - t) alpha_n,
-#   fma(t, a', .) -> +10 flops plus two MUFU (sqrt, reciprocal); counted per evaluation of such a splat.
-FLOPS_PER_EVAL = 22
-FLOPS_PER_EVAL_T = 10
+# Algorithmic work of the blend and its adjoint: the op lists of the oracle's blend_pixel / alpha_f
+# and of its reverse walk in or_backward (Sec. 3.1 Eq. alpha; Eq. alphap), in their step order, counting
+# every fp32 add, subtract, multiply and divide as one flop and a fused multiply-add as two; compares,
+# min/max and selects are not flops, exp2 / log2 / sqrt / reciprocal are XU results.
+#   per evaluated (pixel, splat) pair: dx, dy (2); h = ca dx + cb dy (3); g = (cc dy) dy (2);
+#     p2 = dx h + g (2); o_n G (1)                                         -> 10 flops, 1 XU (exp2)
+#   + t != 0: o_p G (1); 1 - alpha_p, (.)^(1/K) as exp2(log2(.) / K), 1 - (.) (3); 1 - t, (1 - t) alpha_n,
+#     t alpha' + (.) (4)                                                   -> +8 flops, +2 XU
+#   + per contribution (the pair's colour is accumulated): T (1 - alpha) (2), alpha T (1), 3 colour FMAs (6)
+#                                                                          -> +9 flops
+BLEND_FLOPS_EVAL, BLEND_FLOPS_INTERP, BLEND_FLOPS_CONTRIB = 10, 8, 9
+BLEND_XU_EVAL, BLEND_XU_INTERP = 1, 2
+#   adjoint, per contributing pair (reverse walk, colour only): colour gradients a T g_c (9); alpha adjoint
+#     sum_c g_c (T c_c - S_c / (1 - alpha)) (18); colour behind S_c += c_c a T (9); dx, dy and the exponent
+#     (11); o_n G and its adjoint terms (5); exponent adjoint dG G and the conic and centre terms (22)
+#                                                                          -> 74 flops, 1 XU
+#     + t != 0: (1 - t) alpha adjoint (2); o_p G, d alpha'/d alpha_p = (1/K)(1 - alpha_p)^(1/K - 1), its
+#     product with t and the adjoint, o_p and G terms (12)                  -> +14 flops, +2 XU
+#   plus the recomputation of the pair's alpha (the adjoint keeps no per-pair state): the evaluation
+#   op list above, counted for contributing pairs only
+ADJ_FLOPS_CONTRIB, ADJ_FLOPS_CONTRIB_INTERP = 74 + BLEND_FLOPS_EVAL, 14 + BLEND_FLOPS_INTERP
 # DRAM bytes (read + write) of one launch of the blend's main kernel at the 1080p corridor frame
 # (16x16 tiles, chunk 384), from an ncu capture of the current kernel; None once the kernel changes
-BLEND_TRAFFIC_BYTES = 28.85e6 + 3.14e6
+BLEND_TRAFFIC_BYTES = 28.82e6 + 3.17e6
 
 
 def parse():
@@ -162,16 +175,21 @@ def cpu_oracle_time(scene, n_frames: int, budget_s: float = 25.0):
     cam = scene.cameras[0]
     times = []
     t_start = time.perf_counter()
+    amb = None
     for _ in range(max(1, n_frames)):
         t0 = time.perf_counter()
-        oracle.render(cam, h, oracle.Opts())
+        fr = oracle.render(cam, h, oracle.Opts())
         times.append(time.perf_counter() - t0)
+        amb = float(fr.ambiguous.mean())
         if time.perf_counter() - t_start > budget_s:
             break
     return {"value": len(times) / float(np.sum(times)), "unit": "frames/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"{len(times)} full 1920x1080 frames (cut + interpolate/project/SH + tile lists + blend), "
-                      f"fp64 values with fp32 decisions, OpenMP"}
+                      f"fp64 values with fp32 decisions, OpenMP",
+            "ambiguous_pixel_fraction": amb,
+            "ambiguous_note": "pixels of this frame whose fp32 alpha-floor or stop decision lies within 1e-5 "
+                              "(relative) of its threshold: excluded from the image parity bar (allowed: 2e-4)"}
 
 
 # ----------------------------------------------------------------------------------- our path
@@ -310,7 +328,12 @@ def run_ours(args, rank, world, local):
         fwd_stages = {k: v / n_prof for k, v in stage_acc.items() if v > 0}
         st = dict(h3dgs.h3dgs_get_stats(ctx.ctx))
         st["n_evals"], st["n_evals_tpass"] = st_counts["n_evals"], st_counts["n_evals_tpass"]
-        st["n_evals_interp"] = st_counts["n_evals_interp"]
+        for k in ("n_evals_interp", "n_contrib", "n_contrib_interp"):
+            st[k] = st_counts[k]
+        # visible splats with an interpolated parent (the adjoint's splat stage reads the parent's row too)
+        rec_dbg, rect_dbg, _ = h3dgs.h3dgs_debug_splats(ctx.ctx, int(st["n_cut"]))
+        st_counts["n_interp_visible"] = int(np.sum((rect_dbg[:, 0] >= 0) & (rec_dbg[:, 7] != 0)))
+        del rec_dbg, rect_dbg
 
         # ---- fwd + bwd views/s
         grads = {k: torch.zeros_like(getattr(hier, k)) for k in ("mean", "scale", "rot", "opacity", "sh")}
@@ -467,7 +490,9 @@ def run_ours(args, rank, world, local):
     peaks = measured_peaks()
     queue_ms = fwd_stages.get("blend_queue", 0.0)   # events around that kernel alone, on its stream
     n_evals, n_evals_i = int(st["n_evals"]), int(st["n_evals_interp"])
-    flops = n_evals * FLOPS_PER_EVAL + n_evals_i * FLOPS_PER_EVAL_T
+    n_contrib, n_contrib_i = int(st["n_contrib"]), int(st["n_contrib_interp"])
+    flops = n_evals * BLEND_FLOPS_EVAL + n_evals_i * BLEND_FLOPS_INTERP + n_contrib * BLEND_FLOPS_CONTRIB
+    xu_ops = n_evals * BLEND_XU_EVAL + n_evals_i * BLEND_XU_INTERP
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     fp32_peak_tflops = 148 * 128 * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (queue_ms * 1e-3) / 1e12 if queue_ms > 0 else None
@@ -476,17 +501,43 @@ def run_ours(args, rank, world, local):
                 "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk == 384) else None,
                 "kernel_ms": queue_ms,
                 "peak_note": "148 SMs x 128 FP32 lanes x 2 (FFMA) x max SM clock from MEASURED_PEAKS.json",
-                "work_note": f"{FLOPS_PER_EVAL} FP32 flops per main-pass (pixel, splat) evaluation x {n_evals}, "
-                             f"+{FLOPS_PER_EVAL_T} for the {n_evals_i} of them on splats with an interpolated parent "
-                             f"(t != 0: the transition alpha of Eq. alphap); the {int(st['n_evals_tpass'])} "
-                             f"transmittance-pass evaluations of split tiles are not counted",
+                "work_note": f"the oracle's op list: {BLEND_FLOPS_EVAL} flops per main-pass (pixel, splat) evaluation "
+                             f"x {n_evals}, +{BLEND_FLOPS_INTERP} for the {n_evals_i} on splats with an interpolated "
+                             f"parent (Eq. alphap), +{BLEND_FLOPS_CONTRIB} per accumulated contribution x {n_contrib}; "
+                             f"the {int(st['n_evals_tpass'])} transmittance-pass evaluations of split tiles are not "
+                             f"counted; compares, min and selects are not flops",
                 "traffic_note": "DRAM read + write of one launch from an ncu capture of this kernel at this workload"}
     if calib:
         roofline["peak_calibrated"] = calib["fp32_tflops"]
         roofline["frac_calibrated"] = (achieved / calib["fp32_tflops"]) if achieved else None
         roofline["ex2_gops_calibrated"] = calib["ex2_gops"]
+        roofline["xu_frac_calibrated"] = (xu_ops / (queue_ms * 1e-3) / 1e9 / calib["ex2_gops"]) if queue_ms > 0 else None
         roofline["calibration_note"] = ("fp32 paired-FMA and exp2 chain kernels filling every SM, run by "
                                         "h3dgs_measure_peaks on this GPU before the timed region")
+    # ---- adjoint (a8): the per-pixel stage against the FP32 peak with the oracle's op list, the per-splat
+    # stage against HBM (node and parent rows read, gradient rows reduced)
+    bb_ms, bs_ms = bwd_stages.get("backward_blend", 0.0), bwd_stages.get("backward_splat", 0.0)
+    adj_flops = n_contrib * ADJ_FLOPS_CONTRIB + n_contrib_i * ADJ_FLOPS_CONTRIB_INTERP
+    adj_achieved = adj_flops / (bb_ms * 1e-3) / 1e12 if bb_ms > 0 else None
+    n_vis, n_parent_rows = int(st["n_visible"]), int(st_counts.get("n_interp_visible", 0))
+    splat_bytes = n_vis * (236 + 59 * 4) + n_parent_rows * (236 + 59 * 4)
+    hbm_peak = float(peaks.get("hbm_gbs", 6442.9))
+    roofline_backward = {
+        "backward_blend": {"bound": "alu", "achieved": adj_achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                           "frac": (adj_achieved / fp32_peak_tflops) if adj_achieved else None,
+                           "frac_calibrated": (adj_achieved / calib["fp32_tflops"]) if (adj_achieved and calib) else None,
+                           "kernel_ms": bb_ms,
+                           "work_note": f"the oracle's adjoint op list: {ADJ_FLOPS_CONTRIB} flops per contributing "
+                                        f"(pixel, splat) pair x {n_contrib} (alpha recomputed + reverse step), "
+                                        f"+{ADJ_FLOPS_CONTRIB_INTERP} for the {n_contrib_i} with t != 0"},
+        "backward_splat": {"bound": "hbm", "achieved": splat_bytes / (bs_ms * 1e-3) / 1e9 if bs_ms > 0 else None,
+                           "peak": hbm_peak, "unit": "GB/s",
+                           "frac": (splat_bytes / (bs_ms * 1e-3) / 1e9 / hbm_peak) if bs_ms > 0 else None,
+                           "kernel_ms": bs_ms,
+                           "work_note": f"236 B attribute row read + 59 x 4 B gradient row reduced per visible cut "
+                                        f"entry ({n_vis}) and again for the parent of each of the {n_parent_rows} "
+                                        f"with t != 0"},
+    }
     hbm = float(peaks.get("hbm_gbs", 6442.9))
     stage_bw = {}
     M, V, Pn = int(st["n_cut"]), int(st["n_visible"]), int(st["n_pairs"])
@@ -523,7 +574,9 @@ def run_ours(args, rank, world, local):
         "gaussians_per_s": M * value,
         "fwd_bwd": {"value": fb_value, "unit": "views/s", "ms_per_view": fb_ms / args.steps},
         "blend": {"items": int(st["n_items"]), "tile_chunk": int(opts.blend_chunk), "evals_main": n_evals,
-                  "evals_main_interpolated": n_evals_i, "evals_tpass": int(st["n_evals_tpass"])},
+                  "evals_main_interpolated": n_evals_i, "evals_tpass": int(st["n_evals_tpass"]),
+                  "contributions": n_contrib, "contributions_interpolated": n_contrib_i,
+                  "flops": flops, "xu_ops": xu_ops},
         "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": 76 * len(cams),
                 "d2h_bytes_per_step": npix * 4, "serial_value": e2e_serial_value,
                 "note": "C-ABI calls from Python (not graph-captured), host clock; camera struct in, the whole "
@@ -531,6 +584,7 @@ def run_ours(args, rank, world, local):
                         "copy stream overlapping step k + 1 (two image buffers); serial_value: render then copy"},
         "stages_ms": {**fwd_stages, **bwd_stages}, "stage_bandwidth": stage_bw,
         "roofline": roofline,
+        "roofline_backward": roofline_backward,
         "frame_roofline": frame_roofline,
         "tile": args.tile,
         "gpu_launches": args.steps * launches,

@@ -115,7 +115,9 @@ typedef struct {
                               exceeded, bit 2: cut truncated to capacity, bit 3: a
                               bounded wait of one thread block on another (sort,
                               scan or blend queue) gave up: the frame is invalid,
-                              the context stays usable                            */
+                              the context stays usable; bit 7: a bounds check of a
+                              checked build (h3dgs_build_flags) failed: the file and
+                              line are in h3dgs_last_error                        */
     int64_t n_evals;      /* (pixel, splat) evaluations of the blend's main pass
                              (counted only at profiling level 2, else 0)        */
     int64_t n_evals_tpass; /* extra evaluations of the transmittance pass of split tiles
@@ -125,6 +127,7 @@ typedef struct {
                                (t != 0, Eq. alphap evaluated too; profiling level 2, else 0) */
     int64_t n_contrib;    /* (pixel, splat) pairs whose colour was accumulated: alpha at or above the
                              floor, before the transmittance stop (profiling level 2, else 0) */
+    int64_t n_contrib_interp; /* those of splats with an interpolated parent (t != 0; likewise) */
 } h3dgs_stats;
 
 /* Per-stage device times of the most recent select_cut / render / render_backward, in ms,
@@ -416,6 +419,15 @@ h3dgs_status h3dgs_debug_wait_timeout(h3dgs_ctx* ctx, int32_t polls);
  * render the arrays hold whatever the last saving render left).  n_pixels must equal the total
  * pixel count of the last render's cameras (INVALID_ARG otherwise); STATE if nothing was rendered. */
 h3dgs_status h3dgs_debug_pixel_state(h3dgs_ctx* ctx, float* T_final, int32_t* n_contrib, int64_t n_pixels);
+
+/* Build variant of the loaded library: H3DGS_BUILD_CHECKED when it was compiled with -DH3DGS_CHECK
+ * (libh3dgs_check.so): every index taken from data (parent and cut ids, list entries, radix staging
+ * slots and scatter destinations, work items) is range-checked before its access in the cut,
+ * preprocess, sort, blend and adjoint kernels; a failure skips the access, never traps, and sets
+ * bit 7 of h3dgs_stats.device_flags (the file and line in h3dgs_last_error).  A debug aid standing
+ * in for a memory checker; 0 for the default build, whose checks compile away. */
+#define H3DGS_BUILD_CHECKED 1
+int32_t h3dgs_build_flags(void);
 
 #ifdef __cplusplus
 }

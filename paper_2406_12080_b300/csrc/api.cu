@@ -38,14 +38,14 @@ template <typename T>
 T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
 
 // device counter block
-// C_EVALS, C_EVALS_T, C_EVALS_I and C_CONTRIB occupy two words each (64-bit counters, in this order)
+// C_EVALS, C_EVALS_T, C_EVALS_I, C_CONTRIB and C_CONTRIB_I occupy two words each (64-bit counters, in this order)
 // C_NSORTED: a zero word (the bounded-wait probe); C_NTSORT: unused
 // C_NITEMS: 4 words (items, producers, singles, split tiles).  C_FLAGS: render flags (cleared by every render);
 // C_CUTFLAGS: cut flags (cleared by every cut); the stats report both.
 enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NSORTED = 6,
        C_NTSORT = 7, C_NITEMS = 14, C_CUTFLAGS = 18, C_EVALS = 20, C_EVALS_T = 22, C_EVALS_I = 24, C_CONTRIB = 26,
-       C_COUNT = 28 };
-constexpr int EVAL_WORDS = 8;   // the four 64-bit blend counters from C_EVALS on
+       C_CONTRIB_I = 28, C_COUNT = 30 };
+constexpr int EVAL_WORDS = 10;   // the five 64-bit blend counters from C_EVALS on
 
 }  // namespace
 
@@ -220,6 +220,7 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images, float* de
     a.ranges = P<int2>(ctx->ranges);
     a.list = ctx->pairs_in_1 ? P<uint32_t>(ctx->pv1) : P<uint32_t>(ctx->pv0);
     a.splat = P<float4>(ctx->s_rec);
+    a.n_splats = P<uint32_t>(ctx->counters) + C_NSPLATS;
     a.chunk = ctx->opts.chunk;
     a.item_cap = ctx->item_cap;
     a.items = P<int2>(ctx->items);
@@ -945,6 +946,21 @@ h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out) {
     out->n_evals_interp = (int64_t)ev;
     std::memcpy(&ev, c + C_CONTRIB, sizeof(ev));
     out->n_contrib = (int64_t)ev;
+    std::memcpy(&ev, c + C_CONTRIB_I, sizeof(ev));
+    out->n_contrib_interp = (int64_t)ev;
+    // bounds-check words of a checked build (always zero otherwise); reading clears them
+    struct { const char* file; cudaError_t (*read)(uint32_t*, cudaStream_t); } readers[] = {
+        {"cut.cu", check_read_cut}, {"preprocess.cu", check_read_preprocess}, {"sort.cu", check_read_sort},
+        {"blend.cu", check_read_blend}, {"backward.cu", check_read_backward}};
+    for (const auto& r : readers) {
+        uint32_t w[2];
+        CK(r.read(w, ctx->stream), "read check words");
+        if (w[0]) {
+            out->device_flags |= FLAG_BOUNDS;
+            if (ctx->err.empty())
+                ctx->err = std::string("bounds check failed in ") + r.file + " line " + std::to_string(w[1]);
+        }
+    }
     out->n_items = c[C_NITEMS];
     return H3DGS_OK;
 }
@@ -1075,6 +1091,14 @@ h3dgs_status h3dgs_debug_pixel_state(h3dgs_ctx* ctx, float* T_final, int32_t* n_
     if (n_contrib) CK(cudaMemcpyAsync(n_contrib, ctx->n_contrib.p, 4 * n_pixels, cudaMemcpyDeviceToHost, ctx->stream), "read n");
     CK(cudaStreamSynchronize(ctx->stream), "debug sync");
     return H3DGS_OK;
+}
+
+int32_t h3dgs_build_flags(void) {
+#ifdef H3DGS_CHECK
+    return H3DGS_BUILD_CHECKED;
+#else
+    return 0;
+#endif
 }
 
 }  // extern "C"

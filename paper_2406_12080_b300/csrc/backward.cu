@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
                                                                      DevOpts o, const int2* __restrict__ ranges,
                                                                      const uint32_t* __restrict__ list,
                                                                      const float4* __restrict__ splat,
+                                                                     const uint32_t* __restrict__ n_spl,
                                                                      const int2* __restrict__ items,
                                                                      const uint32_t* __restrict__ n_items,
                                                                      const int32_t* __restrict__ tile_item0,
@@ -226,7 +227,8 @@ __global__ void __launch_bounds__(TW * TH / 2) backward_blend_kernel(const DevCa
         }
         __syncthreads();
         if ((int)threadIdx.x < n) {
-            const uint32_t s = __ldg(list + begin + first + threadIdx.x);
+            uint32_t s = __ldg(list + begin + first + threadIdx.x);
+            if (!H3DGS_IN(s, *n_spl)) s = 0;   // checked build only
             const float4 a = __ldg(splat + SPLAT_F4 * (int64_t)s);
             const float4 d = __ldg(splat + SPLAT_F4 * (int64_t)s + 3);
             s_id[threadIdx.x] = s;
@@ -350,9 +352,10 @@ __global__ void __launch_bounds__(128) backward_splat_kernel(DevHier h, const De
         const int k = find_cam(cut_offsets, n_cams, m);
         const DevCam& cam = cams[k];
         const int32_t n = cut_ids[m];
+        if (!H3DGS_IN(n, h.n)) continue;   // checked build only
         const float t = (o.interpolate && cut_t) ? cut_t[m] : 0.0f;
         const int32_t p = h.parent[n];
-        const bool use_p = (t != 0.0f) && p >= 0;
+        const bool use_p = (t != 0.0f) && p >= 0 && H3DGS_IN(p, h.n);
         const float omt = 1.0f - t;
         // ---- interpolated attributes
         float s[3], ql[4];
@@ -590,7 +593,7 @@ cudaError_t launch_backward(const DevHier& h, const BlendArgs& a, const int32_t*
         const unsigned ig = (unsigned)a.item_cap;
 #define BWD(TWV, THV, DEP)                                                                                          \
     backward_blend_kernel<TWV, THV, DEP><<<ig, TWV * THV / 2, 0, s>>>(                                              \
-        a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.items, a.n_items, a.tile_item0, a.tile_nch,               \
+        a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, n_splats, a.items, a.n_items, a.tile_item0, a.tile_nch,     \
         a.scratch_C, a.scratch_Tend, a.scratch_last, a.T_final, a.n_contrib, dL, dLdepth, a.exposure, a.scratch_D,    \
         splat_grad)
 #define BW(TWV, THV)                                                                                                \
@@ -618,5 +621,7 @@ cudaError_t launch_backward(const DevHier& h, const BlendArgs& a, const int32_t*
     if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }
+
+H3DGS_CHECK_READER(check_read_backward)
 
 }  // namespace h3dgs

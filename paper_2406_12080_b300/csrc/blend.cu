@@ -231,11 +231,13 @@ __device__ __forceinline__ void write_pixel(float* img, int64_t plane, float T, 
 //     pixel (fl = +inf), and in the main pass undoes the entry for it (stop before the splat).
 template <int TW, int TH, bool MAIN, bool COUNT, bool DEPTH, bool SAVE>
 __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const uint32_t* __restrict__ list,
-                                            const float4* __restrict__ splat, int begin, int end, int list0,
+                                            const float4* __restrict__ splat, const uint32_t* __restrict__ n_spl,
+                                            int begin, int end, int list0,
                                             float clampv, float afloor, float tmin, float4* s_a, float4* s_b,
                                             float4* s_c, uint32_t* s_m, float* s_d, float4* s_box, float2& T, float2& C0,
                                             float2& C1, float2& C2, float2& Dp, int2& last, bool& done0, bool& done1,
-                                            unsigned int& evals, unsigned int& evals_i, unsigned int& contribs) {
+                                            unsigned int& evals, unsigned int& evals_i, unsigned int& contribs,
+                                            unsigned int& contribs_i) {
     constexpr int NT2 = TW * TH / 2, NW = NT2 / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float INF = __int_as_float(0x7f800000);
@@ -259,7 +261,8 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
         if (__syncthreads_count(done0 && done1) == NT2) break;
         const int n = min(NT2, end - b0);
         if ((int)threadIdx.x < n) {
-            const uint32_t s = __ldg(list + b0 + threadIdx.x);
+            uint32_t s = __ldg(list + b0 + threadIdx.x);
+            if (!H3DGS_IN(s, *n_spl)) s = 0;   // checked build only
             const float4 a = __ldg(splat + SPLAT_F4 * (int64_t)s);
             const float4 bb = __ldg(splat + SPLAT_F4 * (int64_t)s + 1);
             const float4 d = __ldg(splat + SPLAT_F4 * (int64_t)s + 3);
@@ -289,7 +292,6 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
                     }
                     const float2 alpha = pair_alpha2(g.px, g.py, s_a[j], s_b[j], &s_c[j], clampv);
                     bool take0 = alpha.x >= fl.x, take1 = alpha.y >= fl.y;
-                    if (!__any_sync(0xffffffffu, take0 || take1)) continue;   // no pixel of the warp takes it
                     float2 ae = make_float2(take0 ? alpha.x : 0.0f, take1 ? alpha.y : 0.0f);
                     float2 Tn = __fmul2_rn(T, __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-ae.x, -ae.y)));
                     const bool stop0 = take0 && Tn.x < tmin, stop1 = take1 && Tn.y < tmin;
@@ -317,7 +319,10 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
                             const int pos = b0 + j + 1 - list0;
                             last = make_int2(take0 ? pos : last.x, take1 ? pos : last.y);
                         }
-                        if (COUNT) contribs += (unsigned)take0 + (unsigned)take1;
+                        if (COUNT) {
+                            contribs += (unsigned)take0 + (unsigned)take1;
+                            if (s_b[j].w != 0.0f) contribs_i += (unsigned)take0 + (unsigned)take1;
+                        }
                     }
                     T = Tn;
                 }
@@ -335,10 +340,11 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
 // DEPTH: also the expected depth (depth != NULL).  SAVE: also the per-pixel state the adjoint reads
 // (final transmittance, contributor count; T_final and n_contrib != NULL).
 template <int TW, int TH, bool COUNT, bool DEPTH, bool SAVE>
-__global__ void __launch_bounds__(TW * TH / 2, 10) blend_queue_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
+__global__ void __launch_bounds__(TW * TH / 2, 12) blend_queue_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
                                                                   const int2* __restrict__ ranges,
                                                                   const uint32_t* __restrict__ list,
                                                                   const float4* __restrict__ splat,
+                                                                  const uint32_t* __restrict__ n_spl,
                                                                   const int2* __restrict__ items,
                                                                   const uint32_t* __restrict__ q_prod,
                                                                   const uint32_t* __restrict__ q_single,
@@ -362,10 +368,10 @@ __global__ void __launch_bounds__(TW * TH / 2, 10) blend_queue_kernel(const DevC
     __shared__ uint32_t s_m[NT2];
     __shared__ float s_d[DEPTH ? NT2 : 1];
     __shared__ float4 s_box[NT2 / 32];
-    __shared__ unsigned int s_evals[4];
+    __shared__ unsigned int s_evals[5];
     __shared__ uint32_t s_k;
     if (threadIdx.x == 0) s_k = atomicAdd(ticket, 1u);
-    if (threadIdx.x < 4) s_evals[threadIdx.x] = 0;
+    if (threadIdx.x < 5) s_evals[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t k = s_k;
     const uint32_t X = counts[1], Y = counts[2];
@@ -375,6 +381,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 10) blend_queue_kernel(const DevC
     else if (k < X + Y) { role = 1; item = q_single[k - X]; }
     else if (k < 2 * X + Y) { role = 2; item = q_cons[k - X - Y]; }
     else return;
+    if (!H3DGS_IN(item, counts[0])) return;   // checked build only
     const int2 it = items[item];
     const int64_t tile = it.x;
     const int nch = tile_nch[tile];
@@ -396,27 +403,29 @@ __global__ void __launch_bounds__(TW * TH / 2, 10) blend_queue_kernel(const DevC
     }
     float2 C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0, Dp = C0;
     int2 last = make_int2(-1, -1);
-    unsigned int evals = 0, evals_i = 0, contribs = 0;
+    unsigned int evals = 0, evals_i = 0, contribs = 0, contribs_i = 0;
     bool done0 = !g.in0 || T.x < o.t_min, done1 = !g.in1 || T.y < o.t_min;
     if (main_pass)
-        blend_walk2<TW, TH, true, COUNT, DEPTH, SAVE>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
+        blend_walk2<TW, TH, true, COUNT, DEPTH, SAVE>(g, list, splat, n_spl, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
                                                       o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp, last,
-                                                      done0, done1, evals, evals_i, contribs);
+                                                      done0, done1, evals, evals_i, contribs, contribs_i);
     else
-        blend_walk2<TW, TH, false, COUNT, false, false>(g, list, splat, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
+        blend_walk2<TW, TH, false, COUNT, false, false>(g, list, splat, n_spl, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
                                                         o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp,
-                                                        last, done0, done1, evals, evals_i, contribs);
+                                                        last, done0, done1, evals, evals_i, contribs, contribs_i);
     if (COUNT) {
         for (int off = 16; off > 0; off >>= 1) {
             evals += __shfl_down_sync(0xffffffffu, evals, off);
             evals_i += __shfl_down_sync(0xffffffffu, evals_i, off);
             contribs += __shfl_down_sync(0xffffffffu, contribs, off);
+            contribs_i += __shfl_down_sync(0xffffffffu, contribs_i, off);
         }
         if (lane == 0) {
             atomicAdd(&s_evals[main_pass ? 0 : 1], evals);
             if (main_pass) {
                 atomicAdd(&s_evals[2], evals_i);
                 atomicAdd(&s_evals[3], contribs);
+                atomicAdd(&s_evals[4], contribs_i);
             }
         }
     }
@@ -447,7 +456,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 10) blend_queue_kernel(const DevC
     } else {
         __syncthreads();
     }
-    if (COUNT && threadIdx.x < 4 && s_evals[threadIdx.x])
+    if (COUNT && threadIdx.x < 5 && s_evals[threadIdx.x])
         atomicAdd(n_evals + threadIdx.x, (unsigned long long)s_evals[threadIdx.x]);
     if (role == 0) return;
     if (nch > 1) {
@@ -588,7 +597,8 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     const unsigned tg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.n_tiles, 8 * (int64_t)a.num_sms));
 #define QUEUE(TWV, THV, CNT, DEP, SAV)                                                                                \
     e = launch_dependent(blend_queue_kernel<TWV, THV, CNT, DEP, SAV>, dim3(gq), dim3(TWV * THV / 2), s,                \
-        a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.items, a.q_prod, a.q_single, a.q_cons, a.n_items,         \
+        a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.n_splats, a.items, a.q_prod, a.q_single, a.q_cons,        \
+        a.n_items,                                                                                                    \
         a.tile_item0, a.tile_nch, sc, a.queue_sync, a.queue_sync + 1, a.images, a.depth, a.exposure,                  \
         a.T_final, a.n_contrib, a.n_evals, a.flags)
 #define BL(TWV, THV)                                                                                                  \
@@ -621,5 +631,7 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
+
+H3DGS_CHECK_READER(check_read_blend)
 
 }  // namespace h3dgs

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_mark_kernel(const float4* __res
             lo = __ldg(rec + 2 * v);
             hi = __ldg(rec + 2 * v + 1);
             p = __float_as_int(lo.w);
-            if (p >= 0) {
+            if (p >= 0 && H3DGS_IN(p, n)) {
                 plo = __ldg(rec + 2 * (int64_t)p);
                 phi = __ldg(rec + 2 * (int64_t)p + 1);
             }
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_write_kernel(const float4* __re
                     const float4 lo = __ldg(rec + 2 * v), hi = __ldg(rec + 2 * v + 1);
                     const int32_t p = __float_as_int(lo.w);
                     float t = 0.0f;
-                    if (p >= 0) {
+                    if (p >= 0 && H3DGS_IN(p, n)) {
                         const float4 plo = __ldg(rec + 2 * (int64_t)p), phi = __ldg(rec + 2 * (int64_t)p + 1);
                         const float en = granularity(cam, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z);
                         const float ep = granularity(cam, plo.x, plo.y, plo.z, phi.x, phi.y, phi.z);
@@ -257,8 +257,9 @@ __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* 
 #pragma unroll
         for (int k = 0; k < CS_GRP; ++k) {
             const int32_t p = __float_as_int(lo[k].w);
-            plo[k] = p >= 0 ? __ldg(rec + 2 * (int64_t)p) : lo[k];
-            phi[k] = p >= 0 ? __ldg(rec + 2 * (int64_t)p + 1) : hi[k];
+            const bool pin = p >= 0 && H3DGS_IN(p, n);
+            plo[k] = pin ? __ldg(rec + 2 * (int64_t)p) : lo[k];
+            phi[k] = pin ? __ldg(rec + 2 * (int64_t)p + 1) : hi[k];
         }
 #pragma unroll
         for (int k = 0; k < CS_GRP; ++k) {
@@ -339,5 +340,7 @@ cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const C
                                                     w.cam_totals, capacity, cut_ids, cut_t);
     return cudaGetLastError();
 }
+
+H3DGS_CHECK_READER(check_read_cut)
 
 }  // namespace h3dgs

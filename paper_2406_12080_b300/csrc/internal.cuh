@@ -22,6 +22,50 @@ constexpr uint32_t FLAG_WAIT_TIMEOUT = 1u << 3;   // a bounded wait on another b
 constexpr uint32_t FLAG_BAD_TOPOLOGY = 1u << 4;   // a parent index not below its child's (compaction)
 constexpr uint32_t FLAG_NOT_RESIDENT = 1u << 5;   // streamed hierarchy: a cut node's attributes not in the cache
 constexpr uint32_t FLAG_CACHE_FULL = 1u << 6;     // streamed hierarchy: too few free cache slots for an update
+constexpr uint32_t FLAG_BOUNDS = 1u << 7;         // checked build: an index failed its bounds check
+
+// ---------------------------------------------------------------- debug bounds checks
+// A build with -DH3DGS_CHECK (paper_2406_12080_b300/build.py --check: libh3dgs_check.so) tests every
+// index that comes from data -- a parent id, a cut id, a list entry, a staging slot or a scatter
+// destination of the radix sort, a work item -- against the buffer it addresses before the access.  A
+// failed check records the source line in its translation unit's check word and the access is
+// skipped or redirected to element 0; nothing traps, so the context stays usable and the host reads
+// the words (h3dgs_get_stats: FLAG_BOUNDS, and the file and line in h3dgs_last_error).  The default
+// build compiles every check to `true`.
+#ifdef H3DGS_CHECK
+static __device__ uint32_t g_check_word[2];   // [0]: 1 once a check failed; [1]: the line of the first
+__device__ __forceinline__ bool check_in(int64_t i, int64_t n, int line) {
+    if (i >= 0 && i < n) return true;
+    if (atomicCAS(&g_check_word[0], 0u, 1u) == 0u) atomicExch(&g_check_word[1], (uint32_t)line);
+    return false;
+}
+#define H3DGS_IN(i, n) ::h3dgs::check_in((int64_t)(i), (int64_t)(n), __LINE__)
+#define H3DGS_CHECK_READER(name)                                                                              \
+    cudaError_t name(uint32_t out[2], cudaStream_t s) {                                                         \
+        cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_check_word, sizeof(uint32_t) * 2, 0,                  \
+                                                  cudaMemcpyDeviceToHost, s);                                    \
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);                                                     \
+        const uint32_t zero[2] = {0u, 0u};                                                                      \
+        if (e == cudaSuccess && out[0])                                                                         \
+            e = cudaMemcpyToSymbolAsync(g_check_word, zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);        \
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);                                                     \
+        return e;                                                                                               \
+    }
+#else
+#define H3DGS_IN(i, n) true
+#define H3DGS_CHECK_READER(name)                                                                              \
+    cudaError_t name(uint32_t out[2], cudaStream_t) {                                                           \
+        out[0] = out[1] = 0u;                                                                                   \
+        return cudaSuccess;                                                                                     \
+    }
+#endif
+// The check words of the checked translation units: out[0] = 1 if a check failed since the last read
+// (reading clears it), out[1] = the source line of the first failure.
+cudaError_t check_read_cut(uint32_t out[2], cudaStream_t s);
+cudaError_t check_read_preprocess(uint32_t out[2], cudaStream_t s);
+cudaError_t check_read_sort(uint32_t out[2], cudaStream_t s);
+cudaError_t check_read_blend(uint32_t out[2], cudaStream_t s);
+cudaError_t check_read_backward(uint32_t out[2], cudaStream_t s);
 constexpr int QUEUE_SPIN_LIMIT = 1 << 22;          // polls of the blend queue's per-tile counter
 
 // Per-camera data on the device.  Raw fields come from h3dgs_camera; the derived floats are
@@ -433,6 +477,7 @@ struct BlendArgs {
     uint32_t* q_cons;             // blend queue: consumer items (chunks 1 .. nch - 1 of split tiles)
     uint32_t* queue_sync;         // [1 + n_tiles]: queue ticket, per-tile finished-producer counters
     const float4* splat;
+    const uint32_t* n_splats;     // device: splat records written by the preprocess (bounds checks only)
     int chunk;
     int64_t item_cap;
     int2* items;
@@ -450,8 +495,9 @@ struct BlendArgs {
     float* scratch_D;             // per (item, pixel) expected depth of split tiles' chunks (depth only)
     float* T_final;
     int32_t* n_contrib;
-    unsigned long long* n_evals;  // [4]: main-pass evaluations, transmittance-pass evaluations, main-pass
-                                  // evaluations of splats with t != 0, applied contributions
+    unsigned long long* n_evals;  // [5]: main-pass evaluations, transmittance-pass evaluations, main-pass
+                                  // evaluations of splats with t != 0, applied contributions, those of
+                                  // splats with t != 0
     uint32_t* work;               // look-back workspace of the plan (LB_HEADER_WORDS + 2 per 1024 tiles)
     size_t work_words;
     uint32_t* flags;              // device flag word

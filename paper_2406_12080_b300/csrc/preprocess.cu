@@ -111,9 +111,15 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
         const int k = find_cam(cut_offsets, n_cams, m);
         const DevCam& cam = cams[k];
         const int32_t n = __ldg(cut_ids + m);
+        if (!H3DGS_IN(n, h.n)) {   // checked build only: a cut id outside the hierarchy
+            sb.tiles[m] = 0;
+            sb.depth_key[m] = 0xffffffffu;
+            sb.rect[m] = make_uint2(0xffffffffu, 0xffffffffu);
+            continue;
+        }
         const float t = (o.interpolate && cut_t) ? __ldg(cut_t + m) : 0.0f;
         const int32_t p = __ldg(h.parent + n);
-        const bool use_p = (t != 0.0f) && p >= 0;
+        const bool use_p = (t != 0.0f) && p >= 0 && H3DGS_IN(p, h.n);
         // attribute rows: the node ids, or the cache slots of a streamed hierarchy
         const int32_t rn = h.row_of ? __ldg(h.row_of + n) : n;
         const int32_t rp = (h.row_of && use_p) ? __ldg(h.row_of + p) : p;
@@ -360,5 +366,7 @@ cudaError_t launch_interpolate_export(const DevHier& h, int n_cams, const int32_
                                                                out, m_total);
     return cudaGetLastError();
 }
+
+H3DGS_CHECK_READER(check_read_preprocess)
 
 }  // namespace h3dgs

@@ -308,8 +308,10 @@ __global__ void __launch_bounds__(OS_THREADS, 3) radix_onesweep_kernel(const uin
         if (loc[i] != 0xffffffffu) {
             const uint32_t dd = (key[i] >> shift) & 255u;
             const uint32_t pos = s_lstart[dd] + s_wcnt[warp][dd] + loc[i];
-            s_keys[pos] = key[i];
-            s_vals[pos] = val[i];
+            if (H3DGS_IN(pos, OS_TILE)) {
+                s_keys[pos] = key[i];
+                s_vals[pos] = val[i];
+            }
         }
     }
     __syncthreads();
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(OS_THREADS, 3) radix_onesweep_kernel(const uin
         const uint32_t k = s_keys[j];
         const uint32_t dd = (k >> shift) & 255u;
         const uint32_t dst = s_gdst[dd] + (j - s_lstart[dd]);
-        if (dst < n_written) {
+        if (H3DGS_IN(dst, n_written) && dst < n_written) {
             kout[dst] = k;
             vout[dst] = s_vals[j];
         }
@@ -554,7 +556,8 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const DevCam* __restrict
     const int ne = (int)min(min(e1 - e0 + 1, (uint32_t)DUP_SEG + 1), V - e0);
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
         const uint32_t i = e0 + e;
-        const uint32_t m = __ldg(order + i);
+        uint32_t m = __ldg(order + i);
+        if (!H3DGS_IN(m, *sb.n_splats)) m = 0;   // checked build only
         const uint2 r = sb.rect[m];
         const int k = find_cam(cut_offsets, n_cams, m);
         s_off[e] = __ldg(pair_off + i);
@@ -623,5 +626,7 @@ cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
+
+H3DGS_CHECK_READER(check_read_sort)
 
 }  // namespace h3dgs

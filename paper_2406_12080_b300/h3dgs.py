@@ -15,7 +15,8 @@ from dataclasses import dataclass
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libh3dgs.so")
+# the library to load: H3DGS_LIB names another build (e.g. the bounds-checked libh3dgs_check.so)
+LIB_PATH = os.environ.get("H3DGS_LIB") or os.path.join(_PKG, "libh3dgs.so")
 HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "h3dgs.h")
 
 H3DGS_OK = 0
@@ -62,7 +63,8 @@ class h3dgs_stats(C.Structure):
     _fields_ = [("n_cut", C.c_int64), ("n_visible", C.c_int64), ("n_pairs", C.c_int64),
                 ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("device_flags", C.c_uint32),
                 ("n_evals", C.c_int64), ("n_evals_tpass", C.c_int64), ("n_items", C.c_int64),
-                ("n_evals_interp", C.c_int64), ("n_contrib", C.c_int64)]
+                ("n_evals_interp", C.c_int64), ("n_contrib", C.c_int64),
+                ("n_contrib_interp", C.c_int64)]
 
 
 STAGES = ["cut", "preprocess", "depth_sort", "duplicate", "tile_sort", "ranges", "blend", "backward_blend",
@@ -112,6 +114,7 @@ def lib():
             "h3dgs_debug_tile_lists": (i32, [vp, i32, vp, vp, i64, C.POINTER(i64)]),
             "h3dgs_debug_splats": (i32, [vp, vp, vp, vp, i64]),
             "h3dgs_debug_pixel_state": (i32, [vp, vp, vp, i64]),
+            "h3dgs_build_flags": (i32, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -162,6 +165,16 @@ def default_opts(**kw) -> h3dgs_render_opts:
 
 
 # ----------------------------------------------------------------------------- C entry points
+
+def h3dgs_last_error(ctx) -> str:
+    """The context's last error message ("" if none)."""
+    return lib().h3dgs_last_error(ctx).decode() if ctx else ""
+
+
+def h3dgs_build_flags() -> int:
+    """H3DGS_BUILD_CHECKED (1) for the bounds-checked debug build, else 0."""
+    return int(lib().h3dgs_build_flags())
+
 
 def _check(ctx, status):
     if status != H3DGS_OK:

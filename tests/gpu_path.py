@@ -65,6 +65,7 @@ def run(hier_dev, cams, oopts, debug=True, capacity=None, chunk=None) -> GpuFram
         fr.T_final, fr.n_contrib = h3dgs.h3dgs_debug_pixel_state(ctx.ctx, npix)
         fr.stats = h3dgs.h3dgs_get_stats(ctx.ctx)
         assert fr.stats["device_flags"] & 0x8 == 0, "a bounded inter-block wait timed out"
+        assert fr.stats["device_flags"] & 0x80 == 0, h3dgs.h3dgs_last_error(ctx.ctx)   # checked build only
     fr._images_dev = images
     fr._cut = cut
     return fr

@@ -43,6 +43,8 @@ def gpu_grads_batch(dh, cams, opts, ws, freeze=0, chunk=None):
     dl = torch.from_numpy(np.concatenate([np.ascontiguousarray(w, np.float32).reshape(-1) for w in ws])).cuda()
     h3dgs.h3dgs_render_backward(gpu_path.context().ctx, dl, grads, freeze)
     torch.cuda.synchronize()
+    flags = h3dgs.h3dgs_get_stats(gpu_path.context().ctx)["device_flags"]
+    assert flags & 0x88 == 0, (flags, h3dgs.h3dgs_last_error(gpu_path.context().ctx))
     del fr
     return np.concatenate([grads[k].cpu().numpy().reshape(dh.n, -1) for k in ("mean", "scale", "rot", "opacity", "sh")],
                           axis=1)
