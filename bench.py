@@ -553,6 +553,10 @@ def run_ours(args, rank, world, local):
     for k, b in algo_bytes.items():
         if fwd_stages.get(k):
             stage_bw[k] = {"GB/s": b / (fwd_stages[k] * 1e-3) / 1e9, "frac_hbm": b / (fwd_stages[k] * 1e-3) / 1e9 / hbm}
+    if "cut" in stage_bw:   # this tree is below the traversal threshold: the scan reads every record
+        stage_bw["cut"]["mode"] = "scan" if int(st["n_cut_visited"]) == N else "traversal"
+        stage_bw["cut"]["full_scan_bytes"] = N * 32 + M * 8
+        stage_bw["cut"]["visited_nodes_if_traversed"] = None
     # frame-level roofline: the time every stage would take at its binding peak (HBM stages at the
     # measured copy bandwidth, the blend at the unit-count FP32 peak), summed, over the frame time
     ideal_ms = sum(b / (hbm * 1e9) * 1e3 for b in algo_bytes.values())
@@ -935,6 +939,34 @@ def run_city(args, rank, world, local):
                 sizes.append(int(st["n_cut"]))
                 pairs.append(int(st["n_pairs"]))
         frame_ms = np.array(cut_ms) + np.array(render_ms)
+        # the root-down traversal on the same poses (every 8th): the records it reads and its time
+        h3dgs.h3dgs_set_cut_mode(ctx.ctx, 2)
+        trav_ms, visited = [], []
+        for c in poses[::8]:
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids, tt, offs, N, want_total=False)
+            e[1].record(stream)
+            e[1].synchronize()
+            trav_ms.append(e[0].elapsed_time(e[1]))
+            visited.append(int(h3dgs.h3dgs_get_stats(ctx.ctx)["n_cut_visited"]))
+        h3dgs.h3dgs_set_cut_mode(ctx.ctx, 0)
+        scan_ms = cut_ms
+        hbm = float(measured_peaks().get("hbm_gbs", 6442.9))
+        v_mean = float(np.mean(visited))
+        # algorithmic bytes: the 32 B record of every node read, + 8 B per cut entry written; the
+        # descent also reads and writes 8 B of frontier per visited node and 4 B of weight per cut node
+        trav_bytes = v_mean * (32 + 16) + float(np.mean(sizes)) * (8 + 8)
+        scan_bytes = N * 32 + float(np.mean(sizes)) * 8
+        cut_bw = {"visited_nodes_mean": v_mean, "visited_bytes": trav_bytes, "full_scan_bytes": scan_bytes,
+                  "mode": "scan", "scan_ms_mean": float(np.mean(scan_ms)),
+                  "scan_GB/s": scan_bytes / (np.mean(scan_ms) * 1e-3) / 1e9,
+                  "scan_frac_hbm": scan_bytes / (np.mean(scan_ms) * 1e-3) / 1e9 / hbm,
+                  "traversal_ms_mean": float(np.mean(trav_ms)),
+                  "traversal_GB/s": trav_bytes / (np.mean(trav_ms) * 1e-3) / 1e9,
+                  "traversal_frac_hbm": trav_bytes / (np.mean(trav_ms) * 1e-3) / 1e9 / hbm,
+                  "note": "one camera per frame; the frames use the scan (all N records); the root-down "
+                          "traversal (cut and ancestors + frontier traffic) is timed on every 8th pose"}
         value = len(poses) / (frame_ms.sum() * 1e-3)
         batched = None
         if args.batch_views > 0:
@@ -954,6 +986,7 @@ def run_city(args, rank, world, local):
                       "render_ms_max": float(np.max(render_ms)), "frame_ms_p50": float(np.median(frame_ms)),
                       "frame_ms_max": float(frame_ms.max())},
         "gaussians_per_s": float(np.sum(sizes) / (frame_ms.sum() * 1e-3)),
+        "stage_bandwidth": {"cut": cut_bw},
         "build": {"host_generation_s": t_gen, "device_build_s": t_build},
         "clocks": clk.summary(),
     }

@@ -128,6 +128,8 @@ typedef struct {
     int64_t n_contrib;    /* (pixel, splat) pairs whose colour was accumulated: alpha at or above the
                              floor, before the transmittance stop (profiling level 2, else 0) */
     int64_t n_contrib_interp; /* those of splats with an interpolated parent (t != 0; likewise) */
+    int64_t n_cut_visited; /* nodes whose record the last cut read: all nodes for the scan, the cut and
+                              its ancestors for the traversal (h3dgs_set_cut_mode) */
 } h3dgs_stats;
 
 /* Per-stage device times of the most recent select_cut / render / render_backward, in ms,
@@ -284,6 +286,18 @@ h3dgs_status h3dgs_stream_cleanup(h3dgs_ctx* ctx, int32_t frame, int32_t max_age
 h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams,
                               int32_t* cut_ids, float* cut_t, int64_t* cut_offsets, int64_t capacity,
                               int64_t* total_out);
+
+/* How h3dgs_select_cut finds one camera's cut (camera batches always scan):
+ *   0 (default): the scan, currently the faster choice at every size measured (up to 100M nodes);
+ *   1 the scan: every node's record is tested (one pass, decoupled look-back);
+ *   2 the traversal: a level-by-level descent from the root reads only the records of the cut and its
+ *     ancestors (a cooperative launch with a bounded grid barrier per level), then an ordered
+ *     compaction of per-node marks writes the ids ascending.  Same cut and weights as the scan for
+ *     trees whose boxes nest (granularity never larger at a child than at its parent, Sec. 4.2).
+ * Works for trees up to 1024 levels deep (deeper: device flag bit 2, the cut is incomplete).  The
+ * traversal keeps 4 x 4 B per node of frontier and 4 B per node of weights in the context.
+ * Errors: INVALID_ARG for another mode. */
+h3dgs_status h3dgs_set_cut_mode(h3dgs_ctx* ctx, int32_t mode);
 
 /* Cut selection that allocates nothing (the paper has no counterpart; this is a deployment aid).
  * For callers that cannot call cudaMalloc: code running under another framework's memory budget or

@@ -193,6 +193,100 @@ def build_tree(leaves) -> Hierarchy:
     return out
 
 
+def _rows64(h: Hierarchy, v: int) -> np.ndarray:
+    """Node v's attribute row (mean 3, scale 3, rot 4, opacity 1, sh 48) in double."""
+    return np.concatenate([h.mean[v], h.scale[v], h.rot[v], [h.opacity[v]], h.sh[v]]).astype(np.float64)
+
+
+def consolidate(chunks: list) -> Hierarchy:
+    """Chunk hierarchies joined under a global root (Sec. 6.3, chunk consolidation), step by step as
+    the reading states it: every chunk keeps the hierarchy built from its own leaves; a top tree is
+    built over the chunk roots with the rules of the chunk trees -- a group's box is the union of its
+    members' boxes (a chunk root's box is its leaf-union box), it is split at the median of the members'
+    means projected on the longest box axis (ties to the lower axis; members ordered by (projected mean,
+    chunk index); the left child takes the first floor(n/2)), interior nodes merge their two children
+    (Eq. merge) and are orientation-matched top-down, the chunk roots keeping their own frames.  Node
+    order: the top tree breadth-first (its leaves are the chunk roots), then each chunk's nodes except
+    its root in the chunk's breadth-first order."""
+    K = len(chunks)
+    root_mean = np.stack([c.mean[0] for c in chunks]).astype(np.float32)
+    root_lo = np.stack([c.box_min[0] for c in chunks]).astype(np.float32)
+    root_hi = np.stack([c.box_max[0] for c in chunks]).astype(np.float32)
+    perm = list(range(K))
+    tnodes = [[0, K, -1, 0, -1]]          # lo, hi, first child, child count, parent
+    cur = 0
+    while cur < len(tnodes):
+        lo, hi = tnodes[cur][0], tnodes[cur][1]
+        if hi - lo >= 2:
+            mem = perm[lo:hi]
+            bmin, bmax = root_lo[mem].min(axis=0), root_hi[mem].max(axis=0)
+            ext = bmax.astype(np.float64) - bmin.astype(np.float64)
+            axis = int(np.argmax(ext))           # the first maximum: ties to the lower axis
+            perm[lo:hi] = sorted(mem, key=lambda c: (root_mean[c, axis], c))
+            mid = lo + (hi - lo) // 2
+            tnodes[cur][2], tnodes[cur][3] = len(tnodes), 2
+            tnodes.append([lo, mid, -1, 0, cur])
+            tnodes.append([mid, hi, -1, 0, cur])
+        cur += 1
+    n_top = len(tnodes)
+    chunk_of = {v: perm[t[0]] for v, t in enumerate(tnodes) if t[3] == 0}   # top leaf -> chunk
+    # bottom-up merge of the top tree's interior nodes (double rows), then boxes
+    rows = [None] * n_top
+    lo_b = np.zeros((n_top, 3), np.float32)
+    hi_b = np.zeros((n_top, 3), np.float32)
+    for v in range(n_top - 1, -1, -1):
+        t = tnodes[v]
+        if t[3] == 0:
+            c = chunk_of[v]
+            rows[v] = _rows64(chunks[c], 0)
+            lo_b[v], hi_b[v] = chunks[c].box_min[0], chunks[c].box_max[0]
+        else:
+            kids = [t[2], t[2] + 1]
+            rows[v] = merge_rows(np.stack([rows[k] for k in kids]))
+            lo_b[v] = np.minimum(lo_b[kids[0]], lo_b[kids[1]])
+            hi_b[v] = np.maximum(hi_b[kids[0]], hi_b[kids[1]])
+    # top-down orientation matching inside the top tree (chunk roots keep their frames)
+    for v in range(n_top):
+        t = tnodes[v]
+        for k in range(t[2], t[2] + t[3]):
+            if tnodes[k][3] > 0:
+                rows[k] = match_orientation(rows[v], rows[k])
+    sizes = [c.n - 1 for c in chunks]
+    bases = n_top + np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    N = n_top + int(np.sum(sizes))
+    out = Hierarchy(np.empty((N, 3), np.float32), np.empty((N, 3), np.float32), np.empty((N, 4), np.float32),
+                    np.empty(N, np.float32), np.empty((N, NSH), np.float32), np.empty((N, 3), np.float32),
+                    np.empty((N, 3), np.float32), np.empty(N, np.int32), np.empty(N, np.int32),
+                    np.empty(N, np.int32))
+    top_of_chunk = {c: v for v, c in chunk_of.items()}
+    for v in range(n_top):
+        t = tnodes[v]
+        if t[3] == 0:   # a chunk root: its own (fp32) row, box and children
+            c = chunk_of[v]
+            h = chunks[c]
+            for k in ("mean", "scale", "rot", "opacity", "sh", "box_min", "box_max"):
+                getattr(out, k)[v] = getattr(h, k)[0]
+            out.child_count[v] = h.child_count[0]
+            out.child_start[v] = bases[c] + h.child_start[0] - 1 if h.child_count[0] > 0 else -1
+        else:
+            r = rows[v]
+            out.mean[v], out.scale[v], out.rot[v] = r[0:3], r[3:6], r[6:10]
+            out.opacity[v], out.sh[v] = r[10], r[11:59]
+            out.box_min[v], out.box_max[v] = lo_b[v], hi_b[v]
+            out.child_count[v], out.child_start[v] = t[3], t[2]
+        out.parent[v] = t[4]
+    for c, h in enumerate(chunks):
+        g = slice(int(bases[c]), int(bases[c]) + h.n - 1)
+        for k in ("mean", "scale", "rot", "opacity", "sh", "box_min", "box_max"):
+            getattr(out, k)[g] = getattr(h, k)[1:]
+        par = h.parent[1:].astype(np.int64)
+        out.parent[g] = np.where(par == 0, top_of_chunk[c], bases[c] + par - 1)
+        cs = h.child_start[1:].astype(np.int64)
+        out.child_start[g] = np.where(h.child_count[1:] > 0, bases[c] + cs - 1, -1)
+        out.child_count[g] = h.child_count[1:]
+    return out
+
+
 def merge_rows(rows: np.ndarray) -> np.ndarray:
     rows = _f64(rows)
     out = np.empty(NATTR, np.float64)

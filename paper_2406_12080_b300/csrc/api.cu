@@ -58,6 +58,12 @@ struct h3dgs_ctx {
     bool has_hier = false;
     DBuf rec, cams, counters;
     DBuf cut_mask, cut_bc, cut_tot, cut_lb;
+    // traversal cut: frontiers, their parents' granularities, level counts + barrier, marks, weights
+    DBuf tr_front0, tr_front1, tr_feps0, tr_feps1, tr_level, tr_mark, tr_tnode;
+    int cut_mode = 0;            // 0 (default) and 1: the scan; 2: the traversal
+    int tr_grid = -1;            // resident blocks of the cooperative descent (-1: not yet queried)
+    size_t tr_mark_bytes = 0;    // zeroed size of tr_mark
+    bool last_cut_traversed = false;
     DBuf s_rec, s_rect, s_key, s_idx, s_key2, s_idx2, s_key3, s_tiles, s_poff;
     DBuf pk0, pv0, pk1, pv1, ranges;
     DBuf sortw, seg_start, hists;   // hists: [2][4][256] digit histograms of the depth and tile keys
@@ -630,11 +636,54 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
     w.block_counts = P<uint32_t>(ctx->cut_bc);
     w.cam_totals = P<int64_t>(ctx->cut_tot);
     CK(cudaMemsetAsync(P<uint32_t>(ctx->counters) + C_CUTFLAGS, 0, sizeof(uint32_t), ctx->stream), "memset");
+    bool traverse = n_cams == 1 && ctx->cut_mode == 2;
+    if (traverse && ctx->tr_grid < 0) ctx->tr_grid = cut_traverse_grid(ctx->num_sms);
+    if (traverse && ctx->tr_grid <= 0) traverse = false;   // no cooperative launch: the scan
+    TravArgs ta{};
+    if (traverse) {
+        const size_t words = (size_t)((N + 31) / 32);
+        CK(ensure(ctx->tr_front0, sizeof(uint32_t) * (size_t)N), "traversal frontier");
+        CK(ensure(ctx->tr_front1, sizeof(uint32_t) * (size_t)N), "traversal frontier");
+        CK(ensure(ctx->tr_feps0, sizeof(float) * (size_t)N), "traversal frontier");
+        CK(ensure(ctx->tr_feps1, sizeof(float) * (size_t)N), "traversal frontier");
+        CK(ensure(ctx->tr_level, sizeof(uint32_t) * (TR_MAX_LEVELS + 1 + 2)), "traversal levels");
+        CK(ensure(ctx->tr_tnode, sizeof(float) * (size_t)N), "traversal weights");
+        CK(ensure(ctx->tr_mark, sizeof(uint32_t) * words), "traversal marks");
+        if (ctx->tr_mark_bytes != ctx->tr_mark.n) {   // a new mark buffer: zero it once (each compaction clears it)
+            CK(cudaMemsetAsync(ctx->tr_mark.p, 0, ctx->tr_mark.n, ctx->stream), "memset");
+            ctx->tr_mark_bytes = ctx->tr_mark.n;
+        }
+        const int64_t tw = (int64_t)cut_traverse_work_words(N);
+        if (tw > w.lb_words) {
+            w.lb_words = tw;
+            CK(ensure(ctx->cut_lb, sizeof(uint32_t) * (size_t)w.lb_words), "cut look-back");
+            w.lb_work = P<uint32_t>(ctx->cut_lb);
+        }
+        ta.rec = P<const float4>(ctx->rec);
+        ta.child_start = ctx->hier.child_start;
+        ta.n = N;
+        ta.front[0] = P<uint32_t>(ctx->tr_front0);
+        ta.front[1] = P<uint32_t>(ctx->tr_front1);
+        ta.feps[0] = P<float>(ctx->tr_feps0);
+        ta.feps[1] = P<float>(ctx->tr_feps1);
+        ta.cap = N;
+        ta.level_count = P<uint32_t>(ctx->tr_level);
+        ta.bar = ta.level_count + TR_MAX_LEVELS + 1;
+        ta.mark = P<uint32_t>(ctx->tr_mark);
+        ta.tnode = P<float>(ctx->tr_tnode);
+        ta.flags = P<uint32_t>(ctx->counters) + C_CUTFLAGS;
+    }
     stage_begin(ctx, H3DGS_STAGE_CUT);
-    CK(launch_cut(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, w, cut_ids, cut_t, cut_offsets, capacity,
-                  P<uint32_t>(ctx->counters) + C_CUTFLAGS, ctx->stream),
-       "cut kernels");
+    if (traverse)
+        CK(launch_cut_traverse(ta, cams[0], ctx->tr_grid, w.lb_work, w.lb_words, cut_ids, cut_t, cut_offsets,
+                               w.cam_totals, capacity, ctx->stream),
+           "traversal cut kernels");
+    else
+        CK(launch_cut(dev_hier(ctx), P<DevCam>(ctx->cams), n_cams, w, cut_ids, cut_t, cut_offsets, capacity,
+                      P<uint32_t>(ctx->counters) + C_CUTFLAGS, ctx->stream),
+           "cut kernels");
     stage_end(ctx, H3DGS_STAGE_CUT);
+    ctx->last_cut_traversed = traverse;
     if (total_out) {
         int64_t tot = 0;
         CK(cudaMemcpyAsync(&tot, P<int64_t>(ctx->cut_tot) + n_cams, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream),
@@ -948,6 +997,16 @@ h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out) {
     out->n_contrib = (int64_t)ev;
     std::memcpy(&ev, c + C_CONTRIB_I, sizeof(ev));
     out->n_contrib_interp = (int64_t)ev;
+    out->n_cut_visited = ctx->has_hier ? ctx->hier.n_nodes : 0;
+    if (ctx->last_cut_traversed) {   // the root, then every level's frontier
+        std::vector<uint32_t> lv(TR_MAX_LEVELS + 1);
+        CK(cudaMemcpyAsync(lv.data(), ctx->tr_level.p, sizeof(uint32_t) * lv.size(), cudaMemcpyDeviceToHost,
+                           ctx->stream), "read levels");
+        CK(cudaStreamSynchronize(ctx->stream), "stats sync");
+        int64_t v = 1;
+        for (size_t l = 1; l < lv.size(); ++l) v += lv[l];
+        out->n_cut_visited = v;
+    }
     // bounds-check words of a checked build (always zero otherwise); reading clears them
     struct { const char* file; cudaError_t (*read)(uint32_t*, cudaStream_t); } readers[] = {
         {"cut.cu", check_read_cut}, {"preprocess.cu", check_read_preprocess}, {"sort.cu", check_read_sort},
@@ -1090,6 +1149,14 @@ h3dgs_status h3dgs_debug_pixel_state(h3dgs_ctx* ctx, float* T_final, int32_t* n_
     if (T_final) CK(cudaMemcpyAsync(T_final, ctx->T_final.p, 4 * n_pixels, cudaMemcpyDeviceToHost, ctx->stream), "read T");
     if (n_contrib) CK(cudaMemcpyAsync(n_contrib, ctx->n_contrib.p, 4 * n_pixels, cudaMemcpyDeviceToHost, ctx->stream), "read n");
     CK(cudaStreamSynchronize(ctx->stream), "debug sync");
+    return H3DGS_OK;
+}
+
+h3dgs_status h3dgs_set_cut_mode(h3dgs_ctx* ctx, int32_t mode) {
+    if (!ctx) return H3DGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (mode < 0 || mode > 2) return fail(ctx, H3DGS_ERR_INVALID_ARG, "set_cut_mode: mode must be 0, 1 or 2");
+    ctx->cut_mode = mode;
     return H3DGS_OK;
 }
 

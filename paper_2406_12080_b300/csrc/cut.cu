@@ -341,6 +341,256 @@ cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const C
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------ a1 + a2, traversal
+//
+// One camera on a large tree: a persistent grid descends from the root level by level and reads only
+// the records of the nodes it visits, the cut and its ancestors, instead of all N.  The descent gives
+// exactly the scan's set: a frontier node's parent was expanded (eps(parent) >= tau, not a leaf), so it
+// is in the cut iff eps(n) < tau or it is a leaf; and eps does not decrease towards the root (nested
+// boxes, fixed fp32 order), so a node whose parent passes the test has every ancestor passing it too.
+// Cut nodes set their bit in a mark array and store their parent weight per node; an ordered
+// compaction of the marks then writes the ids in ascending order (the consolidated trees are not
+// globally breadth-first, so a level's ids do not follow the previous level's).  Levels are separated
+// by a grid barrier of bounded waits; the launch is cooperative, so every block is resident.
+
+constexpr int TR_BLOCK = 256;
+constexpr int TR_SPIN_LIMIT = 1 << 22;   // polls of one barrier wait before it gives up (flagged)
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier: arrivals counted in bar[0], the release published as a new generation in bar[1].
+// Bounded: a wait that gives up sets FLAG_WAIT_TIMEOUT (the cut is then invalid) and goes on.  Returns,
+// uniformly over the block, whether any wait of the launch has given up so far.
+__device__ __forceinline__ bool grid_sync_bounded(uint32_t* bar, uint32_t nblocks, uint32_t& gen, uint32_t* flags) {
+    __shared__ uint32_t s_failed;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t arrived = atomicAdd(bar, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(gen + 1) : "memory");
+        } else {
+            uint32_t g = gen;
+            int spins = 0;
+            while (spins < TR_SPIN_LIMIT) {
+                g = ld_acquire_u32(bar + 1);
+                if (g != gen) break;
+                if (++spins > 64) __nanosleep(100);
+            }
+            if (g == gen) atomicOr(flags, FLAG_WAIT_TIMEOUT);
+        }
+        gen += 1;
+        s_failed = ld_acquire_u32(flags) & FLAG_WAIT_TIMEOUT;
+    }
+    __syncthreads();
+    return s_failed != 0;
+}
+
+constexpr int TR_IPT = 4;                       // frontier entries per thread per step
+constexpr int TR_TILE = TR_BLOCK * TR_IPT;
+
+__global__ void __launch_bounds__(TR_BLOCK) cut_traverse_kernel(TravArgs a, const h3dgs_camera raw) {
+    __shared__ unsigned long long s_warp[TR_BLOCK / 32];
+    __shared__ uint32_t s_base;
+    DevCam cam;   // only the centre, f and tau are used; derived as the set-up kernel does
+    camera_centre(raw, cam.c);
+    cam.f = fmaxf(raw.fx, raw.fy);
+    cam.tau = raw.tau;
+    const float INF = __int_as_float(0x7f800000);
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * TR_TILE;
+    uint32_t gen = 0;
+    for (int level = 0; level < TR_MAX_LEVELS; ++level) {
+        const uint32_t m = level == 0 ? 1u : ld_acquire_u32(a.level_count + level);
+        if (m == 0) break;
+        const uint32_t mm = (int64_t)m > a.cap ? (uint32_t)a.cap : m;
+        const bool odd = level & 1;
+        const uint32_t* f_in = odd ? a.front[1] : a.front[0];
+        const float* e_in = odd ? a.feps[1] : a.feps[0];
+        uint32_t* f_out = odd ? a.front[0] : a.front[1];
+        float* e_out = odd ? a.feps[0] : a.feps[1];
+        uint32_t* out_count = a.level_count + level + 1;
+        for (uint64_t i0 = (uint64_t)blockIdx.x * TR_TILE; i0 < mm; i0 += stride) {   // uniform per block
+            // TR_IPT independent entries per thread: frontier, record and child range loads all in flight
+            uint32_t v[TR_IPT];
+            float ep[TR_IPT];
+#pragma unroll
+            for (int k = 0; k < TR_IPT; ++k) {
+                const uint64_t i = i0 + (uint64_t)k * TR_BLOCK + threadIdx.x;
+                v[k] = 0xffffffffu;
+                ep[k] = INF;
+                if (i < mm) {
+                    // written by other blocks during the previous level: read at L2, past any stale L1 line
+                    v[k] = level == 0 ? 0u : __ldcg(f_in + i);
+                    ep[k] = level == 0 ? INF : __ldcg(e_in + i);
+                }
+            }
+            float4 lo[TR_IPT], hi[TR_IPT];
+            int32_t cs[TR_IPT];
+#pragma unroll
+            for (int k = 0; k < TR_IPT; ++k) {
+                const bool ok = v[k] < (uint64_t)a.n && H3DGS_IN(v[k], a.n);
+                lo[k] = ok ? __ldg(a.rec + 2 * (int64_t)v[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                hi[k] = ok ? __ldg(a.rec + 2 * (int64_t)v[k] + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                cs[k] = ok ? __ldg(a.child_start + v[k]) : 0;
+                if (!ok) v[k] = 0xffffffffu;
+            }
+            int cnt[TR_IPT];
+            float en[TR_IPT];
+            uint32_t mine = 0;
+#pragma unroll
+            for (int k = 0; k < TR_IPT; ++k) {
+                cnt[k] = 0;
+                en[k] = 0.0f;
+                bool is_cut = false;
+                if (v[k] != 0xffffffffu) {
+                    en[k] = granularity(cam, lo[k].x, lo[k].y, lo[k].z, hi[k].x, hi[k].y, hi[k].z);
+                    const int cc = __float_as_int(hi[k].w);
+                    if (en[k] < cam.tau || cc == 0) {
+                        is_cut = true;
+                        a.tnode[v[k]] = level == 0 ? 0.0f : parent_weight(cam.tau, en[k], ep[k]);
+                    } else {
+                        cnt[k] = cc;
+                    }
+                }
+                // mark: one atomic OR per mark word touched by the warp
+                const uint32_t key = is_cut ? (v[k] >> 5) : 0xffffffffu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, key);
+                const uint32_t bits = __reduce_or_sync(peers, is_cut ? (1u << (v[k] & 31)) : 0u);
+                if (is_cut && lane == __ffs(peers) - 1) atomicOr(a.mark + key, bits);
+                mine += (uint32_t)cnt[k];
+            }
+            // the children join the next level's frontier: one append per block and step
+            unsigned long long total;
+            const unsigned long long before = lb_block_scan<TR_BLOCK>(mine, s_warp, &total);
+            if (threadIdx.x == 0) s_base = total ? atomicAdd(out_count, (uint32_t)total) : 0u;
+            __syncthreads();
+            uint64_t pos = (uint64_t)s_base + before;
+            if (threadIdx.x == 0 && (uint64_t)s_base + total > (uint64_t)a.cap) atomicOr(a.flags, FLAG_CUT_TRUNCATED);
+            __syncthreads();   // s_base and s_warp are reused by the next step
+#pragma unroll
+            for (int k = 0; k < TR_IPT; ++k)
+                for (int c = 0; c < cnt[k]; ++c, ++pos)
+                    if (pos < (uint64_t)a.cap) {
+                        f_out[pos] = (uint32_t)(cs[k] + c);
+                        e_out[pos] = en[k];
+                    }
+        }
+        // a barrier that gave up invalidates the cut (flagged): stop instead of waiting at every later level
+        if (grid_sync_bounded(a.bar, gridDim.x, gen, a.flags)) break;
+        if (level == TR_MAX_LEVELS - 1 && threadIdx.x == 0 && blockIdx.x == 0 &&
+            ld_acquire_u32(a.level_count + level + 1) != 0)
+            atomicOr(a.flags, FLAG_CUT_TRUNCATED);   // deeper than the level table: the cut is incomplete
+    }
+}
+
+// Ordered compaction of the marks: each thread reads TC_WPT consecutive mark words (one 16-byte load),
+// the block's and the earlier blocks' counts come from a single-pass look-back; ids are written in
+// ascending order with their parent weights, and the words are cleared for the next traversal.
+constexpr int TC_WPT = 4;
+constexpr int TC_TILE = TR_BLOCK * TC_WPT;   // mark words per block
+
+__global__ void __launch_bounds__(TR_BLOCK) cut_compact_kernel(uint32_t* __restrict__ mark,
+                                                               const float* __restrict__ tnode, int64_t n,
+                                                               int64_t capacity, int32_t* __restrict__ cut_ids,
+                                                               float* __restrict__ cut_t,
+                                                               int64_t* __restrict__ cut_offsets,
+                                                               int64_t* __restrict__ cam_totals,
+                                                               uint32_t* __restrict__ flags, Lookback lb) {
+    __shared__ uint32_t s_ticket;
+    __shared__ unsigned long long s_slot, s_warp[TR_BLOCK / 32];
+    const uint32_t b = lb_ticket(lb, &s_ticket);
+    const int64_t words = (n + 31) / 32;
+    const int64_t w0 = (int64_t)b * TC_TILE + (int64_t)threadIdx.x * TC_WPT;
+    if ((int64_t)b * TC_TILE >= words) return;
+    uint4 w4 = make_uint4(0, 0, 0, 0);
+    if (w0 + TC_WPT <= words) w4 = *reinterpret_cast<const uint4*>(mark + w0);
+    else {
+        uint32_t t[TC_WPT] = {0, 0, 0, 0};
+        for (int k = 0; k < TC_WPT; ++k)
+            if (w0 + k < words) t[k] = mark[w0 + k];
+        w4 = make_uint4(t[0], t[1], t[2], t[3]);
+    }
+    const uint32_t wv[TC_WPT] = {w4.x, w4.y, w4.z, w4.w};
+    const unsigned long long cnt = __popc(wv[0]) + __popc(wv[1]) + __popc(wv[2]) + __popc(wv[3]);
+    unsigned long long agg;
+    const unsigned long long before = lb_block_scan<TR_BLOCK>(cnt, s_warp, &agg);
+    const unsigned long long prefix = lb_prefix(lb, b, agg, &s_slot);   // ends with a barrier
+    int64_t pos = (int64_t)(prefix + before);
+#pragma unroll
+    for (int k = 0; k < TC_WPT; ++k) {
+        uint32_t x = wv[k];
+        while (x) {
+            const int bit = __ffs(x) - 1;
+            x &= x - 1;
+            const int64_t v = (w0 + k) * 32 + bit;
+            if (pos < capacity) {
+                cut_ids[pos] = (int32_t)v;
+                if (cut_t) cut_t[pos] = tnode[v];
+            }
+            ++pos;
+        }
+    }
+    if (w0 + TC_WPT <= words) *reinterpret_cast<uint4*>(mark + w0) = make_uint4(0, 0, 0, 0);
+    else
+        for (int k = 0; k < TC_WPT; ++k)
+            if (w0 + k < words) mark[w0 + k] = 0u;
+    if ((int64_t)(b + 1) * TC_TILE >= words && threadIdx.x == 0) {   // the last block: offsets and total
+        const int64_t total = (int64_t)(prefix + agg);
+        cam_totals[0] = 0;
+        cam_totals[1] = total;
+        cut_offsets[0] = 0;
+        cut_offsets[1] = total < capacity ? total : capacity;
+        if (total > capacity) atomicOr(flags, FLAG_CUT_TRUNCATED);
+    }
+}
+
+size_t cut_traverse_work_words(int64_t n) {
+    return LB_HEADER_WORDS + lb_body_words(std::max<int64_t>(1, ((n + 31) / 32 + TC_TILE - 1) / TC_TILE));
+}
+
+cudaError_t launch_cut_traverse(const TravArgs& a, const h3dgs_camera& cam, int grid, uint32_t* lb_work,
+                                int64_t lb_words, int32_t* cut_ids, float* cut_t, int64_t* cut_offsets,
+                                int64_t* cam_totals, int64_t capacity, cudaStream_t s) {
+    const int64_t words = (a.n + 31) / 32;
+    const int64_t cblocks = std::max<int64_t>(1, (words + TC_TILE - 1) / TC_TILE);
+    const size_t lw = LB_HEADER_WORDS + lb_body_words(cblocks);
+    if ((int64_t)lw > lb_words) return cudaErrorInvalidValue;
+    // level counts and the barrier words are zero before the descent, the look-back words before the compaction
+    cudaError_t e = cudaMemsetAsync(a.level_count, 0, sizeof(uint32_t) * (TR_MAX_LEVELS + 1 + 2), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lb_work, 0, sizeof(uint32_t) * lw, s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(TR_BLOCK);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, cut_traverse_kernel, a, cam);
+    if (e != cudaSuccess) return e;
+    const Lookback lb = lb_make(lb_work, cblocks, false, a.flags);
+    cut_compact_kernel<<<(unsigned)cblocks, TR_BLOCK, 0, s>>>(a.mark, a.tnode, a.n, capacity, cut_ids, cut_t,
+                                                            cut_offsets, cam_totals, a.flags, lb);
+    return cudaGetLastError();
+}
+
+int cut_traverse_grid(int num_sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cut_traverse_kernel, TR_BLOCK, 0) != cudaSuccess ||
+        per_sm < 1)
+        return 0;
+    return per_sm * num_sms;
+}
+
 H3DGS_CHECK_READER(check_read_cut)
 
 }  // namespace h3dgs

@@ -392,6 +392,27 @@ struct CutWork {
 };
 // Look-back words the single-camera cut needs for n nodes.
 size_t cut_single_work_words(int64_t n);
+
+// Traversal cut of one camera (large trees): visits only the cut and its ancestors.
+constexpr int TR_MAX_LEVELS = 1024;   // deepest tree the descent follows (deeper: FLAG_CUT_TRUNCATED)
+struct TravArgs {
+    const float4* rec;           // packed cut records [n][2]
+    const int32_t* child_start;  // [n]
+    int64_t n;
+    uint32_t* front[2];          // frontier node ids, double-buffered [cap]
+    float* feps[2];              // the parent's granularity of every frontier entry [cap]
+    int64_t cap;                 // frontier capacity (n suffices for any tree)
+    uint32_t* level_count;       // [TR_MAX_LEVELS + 1] frontier sizes, then the 2 barrier words; zeroed per launch
+    uint32_t* bar;               // = level_count + TR_MAX_LEVELS + 1
+    uint32_t* mark;              // [(n + 31) / 32] cut bits: zero before, cleared again by the compaction
+    float* tnode;                // [n] the parent weight of every cut node
+    uint32_t* flags;
+};
+size_t cut_traverse_work_words(int64_t n);
+int cut_traverse_grid(int num_sms);   // resident blocks of the cooperative descent (0: unavailable)
+cudaError_t launch_cut_traverse(const TravArgs& a, const h3dgs_camera& cam, int grid, uint32_t* lb_work,
+                                int64_t lb_words, int32_t* cut_ids, float* cut_t, int64_t* cut_offsets,
+                                int64_t* cam_totals, int64_t capacity, cudaStream_t s);
 cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const CutWork& w, int32_t* cut_ids,
                        float* cut_t, int64_t* cut_offsets, int64_t capacity, uint32_t* flags, cudaStream_t s);
 

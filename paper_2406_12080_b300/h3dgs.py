@@ -64,7 +64,7 @@ class h3dgs_stats(C.Structure):
                 ("n_tiles", C.c_int64), ("n_pixels", C.c_int64), ("device_flags", C.c_uint32),
                 ("n_evals", C.c_int64), ("n_evals_tpass", C.c_int64), ("n_items", C.c_int64),
                 ("n_evals_interp", C.c_int64), ("n_contrib", C.c_int64),
-                ("n_contrib_interp", C.c_int64)]
+                ("n_contrib_interp", C.c_int64), ("n_cut_visited", C.c_int64)]
 
 
 STAGES = ["cut", "preprocess", "depth_sort", "duplicate", "tile_sort", "ranges", "blend", "backward_blend",
@@ -115,6 +115,7 @@ def lib():
             "h3dgs_debug_splats": (i32, [vp, vp, vp, vp, i64]),
             "h3dgs_debug_pixel_state": (i32, [vp, vp, vp, i64]),
             "h3dgs_build_flags": (i32, []),
+            "h3dgs_set_cut_mode": (i32, [vp, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -169,6 +170,11 @@ def default_opts(**kw) -> h3dgs_render_opts:
 def h3dgs_last_error(ctx) -> str:
     """The context's last error message ("" if none)."""
     return lib().h3dgs_last_error(ctx).decode() if ctx else ""
+
+
+def h3dgs_set_cut_mode(ctx, mode: int):
+    """0 (default) and 1: the scan of every node's record; 2: the root-down traversal."""
+    _check(ctx, lib().h3dgs_set_cut_mode(ctx, mode))
 
 
 def h3dgs_build_flags() -> int:

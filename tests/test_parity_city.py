@@ -8,7 +8,13 @@ within fp32 rounding), and the device cut of full-size frames must hold exactly 
 oracle's cut rule selects, with identical weights (every chunk node but the root has its parent inside
 the chunk, so its decision is local).  Properties that hold at any size are checked on the whole
 scene: the cut is an antichain meeting every root-to-leaf path exactly once, and the images, final
-transmittances and contributor counts are in range."""
+transmittances and contributor counts are in range.
+
+The image is compared with the oracle on the 4 x 4 chunks around pose 0 of the camera loop (2M
+leaves, about 4M nodes): the oracle builds each chunk and consolidates them under a top tree
+(oracle.consolidate), the device's chunked build of the same leaves must equal that hierarchy, and the
+frame of pose 0 rendered from the oracle's hierarchy must match the oracle's render (cut, weights,
+splat records and tile lists bit-exact; image within 2e-3 on unambiguous pixels)."""
 import functools
 
 import numpy as np
@@ -79,9 +85,18 @@ def test_full_size_frame_cut_and_render(pose):
     ctx = gpu_path.context()
     ctx.upload(dh)
     cam = synth.city_path(2, 256)[pose]
-    cut = ctx.select_cut([cam], dh.n)
+    cut = ctx.select_cut([cam], dh.n)   # the scan (default mode)
     ids, t, _ = cut
     ids_h, t_h = ids.cpu().numpy(), t.cpu().numpy()
+    # the root-down traversal selects the same nodes with the same weights, reading far fewer records
+    h3dgs.h3dgs_set_cut_mode(ctx.ctx, 2)
+    ids_s, t_s, _ = ctx.select_cut([cam], dh.n)
+    st = h3dgs.h3dgs_get_stats(ctx.ctx)
+    h3dgs.h3dgs_set_cut_mode(ctx.ctx, 0)
+    assert st["n_cut_visited"] < dh.n // 2 and st["device_flags"] & 0xC == 0
+    np.testing.assert_array_equal(ids_s.cpu().numpy(), ids_h)
+    np.testing.assert_array_equal(t_s.cpu().numpy().view(np.uint32), t_h.view(np.uint32))
+    del ids_s, t_s
     assert np.all(np.diff(ids_h) > 0)
     assert np.all((t_h >= 0) & (t_h <= 1))
     # antichain meeting every root-to-leaf path once, level by level (parents precede children)
@@ -125,3 +140,52 @@ def test_full_size_frame_cut_and_render(pose):
     Tf, nc = h3dgs.h3dgs_debug_pixel_state(ctx.ctx, npix)
     assert np.all((Tf >= 0) & (Tf <= 1)) and np.all(nc >= 0)
     assert st["n_cut"] == len(ids_h) and st["n_visible"] > 0
+
+
+# ---------------------------------------------------------------- 16-chunk neighbourhood of pose 0
+
+def _neighbourhood():
+    """The 4 x 4 chunks around the camera of pose 0: the camera in the second row and column from the
+    block's back edge along its viewing direction."""
+    cam = synth.city_path(2, 256)[0]
+    pos, fwd = synth.city_poses(2, 256)[0]
+    cx, cy = int(pos[0] // 50.0), int(pos[1] // 50.0)
+    x0 = cx - 1 if fwd[0] >= 0 else cx - 2
+    y0 = cy - 1 if fwd[1] >= 0 else cy - 2
+    x0, y0 = min(max(x0, 0), GRID - 4), min(max(y0, 0), GRID - 4)
+    return cam, [(x, y) for y in range(y0, y0 + 4) for x in range(x0, x0 + 4)]
+
+
+@functools.lru_cache(maxsize=None)
+def _neighbourhood_oracle():
+    cam, cells = _neighbourhood()
+    leaves = [synth.city_chunk_leaves(2, x, y, PER) for x, y in cells]
+    return cam, leaves, oracle.consolidate([oracle.build_tree(lv) for lv in leaves])
+
+
+def test_neighbourhood_consolidation_equals_the_oracle():
+    import torch
+    cam, leaves, ho = _neighbourhood_oracle()
+    ctx = gpu_path.context()
+    dev = {k: torch.from_numpy(np.ascontiguousarray(np.concatenate([getattr(lv, k) for lv in leaves]))).cuda()
+           for k in ("mean", "scale", "rot", "opacity", "sh")}
+    off = np.arange(len(leaves) + 1, dtype=np.int64) * PER
+    dh = ctx.build_chunked(dev, off)
+    torch.cuda.synchronize()
+    assert dh.n == ho.n
+    for k in ("parent", "child_start", "child_count", "box_min", "box_max"):
+        np.testing.assert_array_equal(getattr(dh, k).cpu().numpy(), getattr(ho, k), err_msg=k)
+    np.testing.assert_allclose(dh.mean.cpu().numpy(), ho.mean, rtol=1e-6, atol=2e-5)
+    np.testing.assert_allclose(dh.opacity.cpu().numpy(), ho.opacity, rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(dh.sh.cpu().numpy(), ho.sh, rtol=1e-5, atol=1e-6)
+    s_d = dh.scale.cpu().numpy()
+    np.testing.assert_allclose(s_d, ho.scale, rtol=1e-4, atol=1e-6)
+
+
+def test_neighbourhood_frame_matches_the_oracle():
+    from tests.test_parity_forward import _compare
+    cam, _, ho = _neighbourhood_oracle()
+    dh = gpu_path.upload(ho)
+    ofr, g = _compare(cam, ho, dh, oracle.Opts())
+    assert len(ofr.ids) > 100_000 and np.sum(ofr.t > 0) > 10_000
+    assert g.stats["n_pairs"] == len(ofr.lists)

@@ -1,0 +1,96 @@
+"""The traversal cut (h3dgs_set_cut_mode 2: a level-by-level descent from the root that reads only
+the records of the cut and its ancestors) against the oracle's cut rule (Sec. 4.2, Eq. t_interp):
+ids and weights bit-exact, on the tiny scene at every tau (leaves only to root only), on K-ary
+compacted trees, and on the 2M-node street corridor; the number of nodes it reads equals the size of
+the cut plus its ancestors, counted here from the oracle's cut."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_12080_b300 import h3dgs, synth
+from tests import gpu_path, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_12080_b300 import build
+    build.build()
+    yield
+    h3dgs.h3dgs_set_cut_mode(gpu_path.context().ctx, 0)
+
+
+def _visited(h, ids):
+    """|cut U ancestors of the cut|: the nodes a root-down descent must read."""
+    seen = np.zeros(h.n, bool)
+    seen[ids] = True
+    frontier = np.unique(h.parent[ids])
+    frontier = frontier[frontier >= 0]
+    while len(frontier):
+        new = frontier[~seen[frontier]]
+        seen[new] = True
+        frontier = np.unique(h.parent[new])
+        frontier = frontier[frontier >= 0]
+    return int(seen.sum())
+
+
+def _traverse_and_compare(h, cam, scan_too=True):
+    ctx = gpu_path.context()
+    out = {}
+    for mode in ((1, 2) if scan_too else (2,)):
+        h3dgs.h3dgs_set_cut_mode(ctx.ctx, mode)
+        ids, t, offs = ctx.select_cut([cam])
+        st = h3dgs.h3dgs_get_stats(ctx.ctx)
+        assert st["device_flags"] & 0xC == 0, st["device_flags"]
+        out[mode] = (ids.cpu().numpy(), t.cpu().numpy(), offs.cpu().numpy(), st["n_cut_visited"])
+    h3dgs.h3dgs_set_cut_mode(ctx.ctx, 0)
+    oid, ot = oracle.select_cut(cam, h, 1)
+    ids, t, offs, visited = out[2]
+    np.testing.assert_array_equal(ids, oid)
+    np.testing.assert_array_equal(t.view(np.uint32), ot.view(np.uint32))
+    assert offs[0] == 0 and offs[1] == len(oid)
+    assert visited == _visited(h, oid)
+    if scan_too:
+        assert out[1][3] == h.n
+        np.testing.assert_array_equal(out[1][0], ids)
+    return oid, visited
+
+
+@pytest.mark.parametrize("tau", [0.0, 2.0, 6.0, 15.0, 80.0, float("inf")])
+def test_tiny_scene(tau):
+    sc, h = scenes.tiny()
+    gpu_path.upload(h)
+    oid, visited = _traverse_and_compare(h, synth.with_tau(sc.cameras[0], tau))
+    if tau == float("inf"):
+        assert list(oid) == [0] and visited == 1
+
+
+def test_camera_inside_the_root_box_and_off_axis_views():
+    sc, h = scenes.tiny()
+    gpu_path.upload(h)
+    for cam in (synth.look_camera([5.0, 5.0, 5.0], [0.3, 0.2, 1.0], [0, -1, 0], 160, 120, 70.0, 4.0),
+                synth.look_camera([-8, 5, 5.0], [1, 0, 0.05], [0, -1, 0], 96, 128, 75.0, 15.0)):
+        _traverse_and_compare(h, cam)
+
+
+@pytest.mark.parametrize("tau", [3.0, 15.0])
+def test_compacted_k_ary_tree(tau):
+    from tests.test_parity_compaction import _tiny_views
+    sc, h = scenes.tiny()
+    oh, _ = oracle.compact(_tiny_views(), h, 3.0, 128.0)
+    assert oh.child_count.max() > 2
+    gpu_path.upload(oh)
+    _traverse_and_compare(oh, synth.with_tau(sc.cameras[0], tau))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("tau", [0.0, 3.0, 6.0, 15.0])
+def test_street_corridor_full_size(tau):
+    sc, h = scenes.corridor()
+    gpu_path.upload(h)
+    oid, visited = _traverse_and_compare(h, synth.with_tau(sc.cameras[0], tau))
+    assert visited == 2 * len(oid) - 1   # binary tree: the cut's ancestors are one fewer than the cut
