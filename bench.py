@@ -941,6 +941,7 @@ def run_city(args, rank, world, local):
         frame_ms = np.array(cut_ms) + np.array(render_ms)
         # the root-down traversal on the same poses (every 8th): the records it reads and its time
         h3dgs.h3dgs_set_cut_mode(ctx.ctx, 2)
+        h3dgs.h3dgs_select_cut(ctx.ctx, [poses[0]], ids, tt, offs, N)   # sizes the traversal's buffers
         trav_ms, visited = [], []
         for c in poses[::8]:
             e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]

@@ -646,7 +646,7 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
         CK(ensure(ctx->tr_front1, sizeof(uint32_t) * (size_t)N), "traversal frontier");
         CK(ensure(ctx->tr_feps0, sizeof(float) * (size_t)N), "traversal frontier");
         CK(ensure(ctx->tr_feps1, sizeof(float) * (size_t)N), "traversal frontier");
-        CK(ensure(ctx->tr_level, sizeof(uint32_t) * (TR_MAX_LEVELS + 1 + 2)), "traversal levels");
+        CK(ensure(ctx->tr_level, sizeof(uint32_t) * TR_LEVEL_WORDS), "traversal levels");
         CK(ensure(ctx->tr_tnode, sizeof(float) * (size_t)N), "traversal weights");
         CK(ensure(ctx->tr_mark, sizeof(uint32_t) * words), "traversal marks");
         if (ctx->tr_mark_bytes != ctx->tr_mark.n) {   // a new mark buffer: zero it once (each compaction clears it)
@@ -668,7 +668,8 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
         ta.feps[1] = P<float>(ctx->tr_feps1);
         ta.cap = N;
         ta.level_count = P<uint32_t>(ctx->tr_level);
-        ta.bar = ta.level_count + TR_MAX_LEVELS + 1;
+        ta.inner = ta.level_count + TR_MAX_LEVELS + 1;
+        ta.bar = ta.level_count + TR_MAX_LEVELS + 2;
         ta.mark = P<uint32_t>(ctx->tr_mark);
         ta.tnode = P<float>(ctx->tr_tnode);
         ta.flags = P<uint32_t>(ctx->counters) + C_CUTFLAGS;
@@ -999,7 +1000,7 @@ h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out) {
     out->n_contrib_interp = (int64_t)ev;
     out->n_cut_visited = ctx->has_hier ? ctx->hier.n_nodes : 0;
     if (ctx->last_cut_traversed) {   // the root, then every level's frontier
-        std::vector<uint32_t> lv(TR_MAX_LEVELS + 1);
+        std::vector<uint32_t> lv(TR_MAX_LEVELS + 2);   // frontier sizes, then the inner visits
         CK(cudaMemcpyAsync(lv.data(), ctx->tr_level.p, sizeof(uint32_t) * lv.size(), cudaMemcpyDeviceToHost,
                            ctx->stream), "read levels");
         CK(cudaStreamSynchronize(ctx->stream), "stats sync");

@@ -392,12 +392,56 @@ __device__ __forceinline__ bool grid_sync_bounded(uint32_t* bar, uint32_t nblock
     return s_failed != 0;
 }
 
-constexpr int TR_IPT = 4;                       // frontier entries per thread per step
+constexpr int TR_IPT = 4;                       // frontier entries per thread per round
 constexpr int TR_TILE = TR_BLOCK * TR_IPT;
+
+// Visit up to TR_IPT nodes per thread: all their loads are issued first; a cut node sets its mark (one
+// atomic OR per mark word per warp) and its parent weight; an expanded node reports its child range.
+// Returns the thread's number of children.
+__device__ __forceinline__ uint32_t tr_visit(const TravArgs& a, const DevCam& cam, const uint32_t (&v)[TR_IPT],
+                                             const float (&ep)[TR_IPT], int (&cnt)[TR_IPT], int32_t (&cs)[TR_IPT],
+                                             float (&en)[TR_IPT], int lane) {
+    float4 lo[TR_IPT], hi[TR_IPT];
+    bool ok[TR_IPT];
+#pragma unroll
+    for (int k = 0; k < TR_IPT; ++k) {
+        ok[k] = v[k] < (uint64_t)a.n && H3DGS_IN(v[k], a.n);
+        lo[k] = ok[k] ? __ldg(a.rec + 2 * (int64_t)v[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        hi[k] = ok[k] ? __ldg(a.rec + 2 * (int64_t)v[k] + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        cs[k] = ok[k] ? __ldg(a.child_start + v[k]) : 0;
+    }
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < TR_IPT; ++k) {
+        cnt[k] = 0;
+        en[k] = 0.0f;
+        bool is_cut = false;
+        if (ok[k]) {
+            en[k] = granularity(cam, lo[k].x, lo[k].y, lo[k].z, hi[k].x, hi[k].y, hi[k].z);
+            const int cc = __float_as_int(hi[k].w);
+            if (en[k] < cam.tau || cc == 0) {
+                is_cut = true;
+                a.tnode[v[k]] = parent_weight(cam.tau, en[k], ep[k]);   // the root (ep = +inf): 0
+            } else {
+                cnt[k] = cc;
+            }
+        }
+        const uint32_t key = is_cut ? (v[k] >> 5) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        const uint32_t bits = __reduce_or_sync(peers, is_cut ? (1u << (v[k] & 31)) : 0u);
+        if (is_cut && lane == __ffs(peers) - 1) atomicOr(a.mark + key, bits);
+        mine += (uint32_t)cnt[k];
+    }
+    return mine;
+}
+
+constexpr int TR_CBUF = 2 * TR_TILE;            // children a block keeps in shared memory per round
 
 __global__ void __launch_bounds__(TR_BLOCK) cut_traverse_kernel(TravArgs a, const h3dgs_camera raw) {
     __shared__ unsigned long long s_warp[TR_BLOCK / 32];
     __shared__ uint32_t s_base;
+    __shared__ uint32_t s_cid[TR_CBUF];
+    __shared__ float s_ceps[TR_CBUF];
     DevCam cam;   // only the centre, f and tau are used; derived as the set-up kernel does
     camera_centre(raw, cam.c);
     cam.f = fmaxf(raw.fx, raw.fy);
@@ -406,18 +450,20 @@ __global__ void __launch_bounds__(TR_BLOCK) cut_traverse_kernel(TravArgs a, cons
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * TR_TILE;
     uint32_t gen = 0;
-    for (int level = 0; level < TR_MAX_LEVELS; ++level) {
-        const uint32_t m = level == 0 ? 1u : ld_acquire_u32(a.level_count + level);
+    // Each step takes the frontier (nodes whose parent was expanded, of any depth) and visits them and,
+    // inside the block, their children: only the grandchildren go to the next step's frontier, so a step
+    // descends two levels and one grid barrier separates steps.
+    for (int step = 0; step < TR_MAX_LEVELS; ++step) {
+        const uint32_t m = step == 0 ? 1u : ld_acquire_u32(a.level_count + step);
         if (m == 0) break;
         const uint32_t mm = (int64_t)m > a.cap ? (uint32_t)a.cap : m;
-        const bool odd = level & 1;
+        const bool odd = step & 1;
         const uint32_t* f_in = odd ? a.front[1] : a.front[0];
         const float* e_in = odd ? a.feps[1] : a.feps[0];
         uint32_t* f_out = odd ? a.front[0] : a.front[1];
         float* e_out = odd ? a.feps[0] : a.feps[1];
-        uint32_t* out_count = a.level_count + level + 1;
+        uint32_t* out_count = a.level_count + step + 1;
         for (uint64_t i0 = (uint64_t)blockIdx.x * TR_TILE; i0 < mm; i0 += stride) {   // uniform per block
-            // TR_IPT independent entries per thread: frontier, record and child range loads all in flight
             uint32_t v[TR_IPT];
             float ep[TR_IPT];
 #pragma unroll
@@ -426,75 +472,81 @@ __global__ void __launch_bounds__(TR_BLOCK) cut_traverse_kernel(TravArgs a, cons
                 v[k] = 0xffffffffu;
                 ep[k] = INF;
                 if (i < mm) {
-                    // written by other blocks during the previous level: read at L2, past any stale L1 line
-                    v[k] = level == 0 ? 0u : __ldcg(f_in + i);
-                    ep[k] = level == 0 ? INF : __ldcg(e_in + i);
+                    // written by other blocks during the previous step: read at L2, past any stale L1 line
+                    v[k] = step == 0 ? 0u : __ldcg(f_in + i);
+                    ep[k] = step == 0 ? INF : __ldcg(e_in + i);
                 }
-            }
-            float4 lo[TR_IPT], hi[TR_IPT];
-            int32_t cs[TR_IPT];
-#pragma unroll
-            for (int k = 0; k < TR_IPT; ++k) {
-                const bool ok = v[k] < (uint64_t)a.n && H3DGS_IN(v[k], a.n);
-                lo[k] = ok ? __ldg(a.rec + 2 * (int64_t)v[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                hi[k] = ok ? __ldg(a.rec + 2 * (int64_t)v[k] + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-                cs[k] = ok ? __ldg(a.child_start + v[k]) : 0;
-                if (!ok) v[k] = 0xffffffffu;
             }
             int cnt[TR_IPT];
+            int32_t cs[TR_IPT];
             float en[TR_IPT];
-            uint32_t mine = 0;
-#pragma unroll
-            for (int k = 0; k < TR_IPT; ++k) {
-                cnt[k] = 0;
-                en[k] = 0.0f;
-                bool is_cut = false;
-                if (v[k] != 0xffffffffu) {
-                    en[k] = granularity(cam, lo[k].x, lo[k].y, lo[k].z, hi[k].x, hi[k].y, hi[k].z);
-                    const int cc = __float_as_int(hi[k].w);
-                    if (en[k] < cam.tau || cc == 0) {
-                        is_cut = true;
-                        a.tnode[v[k]] = level == 0 ? 0.0f : parent_weight(cam.tau, en[k], ep[k]);
-                    } else {
-                        cnt[k] = cc;
-                    }
-                }
-                // mark: one atomic OR per mark word touched by the warp
-                const uint32_t key = is_cut ? (v[k] >> 5) : 0xffffffffu;
-                const uint32_t peers = __match_any_sync(0xffffffffu, key);
-                const uint32_t bits = __reduce_or_sync(peers, is_cut ? (1u << (v[k] & 31)) : 0u);
-                if (is_cut && lane == __ffs(peers) - 1) atomicOr(a.mark + key, bits);
-                mine += (uint32_t)cnt[k];
-            }
-            // the children join the next level's frontier: one append per block and step
+            uint32_t mine = tr_visit(a, cam, v, ep, cnt, cs, en, lane);
+            // children: the first TR_CBUF of the block into shared memory, any more to the next frontier
             unsigned long long total;
-            const unsigned long long before = lb_block_scan<TR_BLOCK>(mine, s_warp, &total);
-            if (threadIdx.x == 0) s_base = total ? atomicAdd(out_count, (uint32_t)total) : 0u;
+            unsigned long long pos = lb_block_scan<TR_BLOCK>(mine, s_warp, &total);
+            const uint32_t spill = total > (unsigned long long)TR_CBUF ? (uint32_t)(total - TR_CBUF) : 0u;
+            if (threadIdx.x == 0) s_base = spill ? atomicAdd(out_count, spill) : 0u;
             __syncthreads();
-            uint64_t pos = (uint64_t)s_base + before;
-            if (threadIdx.x == 0 && (uint64_t)s_base + total > (uint64_t)a.cap) atomicOr(a.flags, FLAG_CUT_TRUNCATED);
-            __syncthreads();   // s_base and s_warp are reused by the next step
 #pragma unroll
             for (int k = 0; k < TR_IPT; ++k)
-                for (int c = 0; c < cnt[k]; ++c, ++pos)
-                    if (pos < (uint64_t)a.cap) {
-                        f_out[pos] = (uint32_t)(cs[k] + c);
-                        e_out[pos] = en[k];
+                for (int c = 0; c < cnt[k]; ++c, ++pos) {
+                    if (pos < (unsigned long long)TR_CBUF) {
+                        s_cid[pos] = (uint32_t)(cs[k] + c);
+                        s_ceps[pos] = en[k];
+                    } else {
+                        const uint64_t g = (uint64_t)s_base + (pos - TR_CBUF);
+                        if (g < (uint64_t)a.cap) {
+                            f_out[g] = (uint32_t)(cs[k] + c);
+                            e_out[g] = en[k];
+                        }
                     }
+                }
+            if (threadIdx.x == 0 && spill && (uint64_t)s_base + spill > (uint64_t)a.cap)
+                atomicOr(a.flags, FLAG_CUT_TRUNCATED);
+            __syncthreads();
+            // the children kept in shared memory, TR_IPT per thread per round (consecutive ids per warp)
+            const uint32_t nc = total < (unsigned long long)TR_CBUF ? (uint32_t)total : (uint32_t)TR_CBUF;
+            if (threadIdx.x == 0 && nc) atomicAdd(a.inner, nc);   // nodes visited without a frontier entry
+            for (uint32_t r0 = 0; r0 < nc; r0 += TR_TILE) {   // uniform per block
+#pragma unroll
+                for (int k = 0; k < TR_IPT; ++k) {
+                    const uint32_t q = r0 + k * TR_BLOCK + threadIdx.x;
+                    v[k] = q < nc ? s_cid[q] : 0xffffffffu;
+                    ep[k] = q < nc ? s_ceps[q] : INF;
+                }
+                mine = tr_visit(a, cam, v, ep, cnt, cs, en, lane);
+                unsigned long long tot2;
+                unsigned long long p2 = lb_block_scan<TR_BLOCK>(mine, s_warp, &tot2);
+                if (threadIdx.x == 0) s_base = tot2 ? atomicAdd(out_count, (uint32_t)tot2) : 0u;
+                __syncthreads();
+                p2 += s_base;
+                if (threadIdx.x == 0 && (uint64_t)s_base + tot2 > (uint64_t)a.cap) atomicOr(a.flags, FLAG_CUT_TRUNCATED);
+#pragma unroll
+                for (int k = 0; k < TR_IPT; ++k)
+                    for (int c = 0; c < cnt[k]; ++c, ++p2)
+                        if (p2 < (uint64_t)a.cap) {
+                            f_out[p2] = (uint32_t)(cs[k] + c);
+                            e_out[p2] = en[k];
+                        }
+                __syncthreads();   // s_base and s_warp are reused
+            }
         }
-        // a barrier that gave up invalidates the cut (flagged): stop instead of waiting at every later level
+        // a barrier that gave up invalidates the cut (flagged): stop instead of waiting at every later step
         if (grid_sync_bounded(a.bar, gridDim.x, gen, a.flags)) break;
-        if (level == TR_MAX_LEVELS - 1 && threadIdx.x == 0 && blockIdx.x == 0 &&
-            ld_acquire_u32(a.level_count + level + 1) != 0)
-            atomicOr(a.flags, FLAG_CUT_TRUNCATED);   // deeper than the level table: the cut is incomplete
+        if (step == TR_MAX_LEVELS - 1 && threadIdx.x == 0 && blockIdx.x == 0 &&
+            ld_acquire_u32(a.level_count + step + 1) != 0)
+            atomicOr(a.flags, FLAG_CUT_TRUNCATED);   // deeper than the step table: the cut is incomplete
     }
 }
 
-// Ordered compaction of the marks: each thread reads TC_WPT consecutive mark words (one 16-byte load),
-// the block's and the earlier blocks' counts come from a single-pass look-back; ids are written in
-// ascending order with their parent weights, and the words are cleared for the next traversal.
-constexpr int TC_WPT = 4;
-constexpr int TC_TILE = TR_BLOCK * TC_WPT;   // mark words per block
+// Ordered compaction of the marks.  A block covers TC_TILE consecutive mark words, each warp TC_ROUNDS
+// rounds of 32 words (lane i holds word i of the round: coalesced loads).  The counts give every round
+// its output range (warp scans, a block scan over the warps, a single-pass look-back over the blocks);
+// the ids of a round are then written 32 consecutive slots at a time: the lane of slot s finds the
+// word holding it (binary search over the lanes' prefixes by shuffles) and its bit (__fns), so the
+// stores of a warp are contiguous.  The words are cleared for the next traversal.
+constexpr int TC_ROUNDS = 4;
+constexpr int TC_TILE = TR_BLOCK * TC_ROUNDS;   // mark words per block
 
 __global__ void __launch_bounds__(TR_BLOCK) cut_compact_kernel(uint32_t* __restrict__ mark,
                                                                const float* __restrict__ tnode, int64_t n,
@@ -507,40 +559,58 @@ __global__ void __launch_bounds__(TR_BLOCK) cut_compact_kernel(uint32_t* __restr
     __shared__ unsigned long long s_slot, s_warp[TR_BLOCK / 32];
     const uint32_t b = lb_ticket(lb, &s_ticket);
     const int64_t words = (n + 31) / 32;
-    const int64_t w0 = (int64_t)b * TC_TILE + (int64_t)threadIdx.x * TC_WPT;
     if ((int64_t)b * TC_TILE >= words) return;
-    uint4 w4 = make_uint4(0, 0, 0, 0);
-    if (w0 + TC_WPT <= words) w4 = *reinterpret_cast<const uint4*>(mark + w0);
-    else {
-        uint32_t t[TC_WPT] = {0, 0, 0, 0};
-        for (int k = 0; k < TC_WPT; ++k)
-            if (w0 + k < words) t[k] = mark[w0 + k];
-        w4 = make_uint4(t[0], t[1], t[2], t[3]);
-    }
-    const uint32_t wv[TC_WPT] = {w4.x, w4.y, w4.z, w4.w};
-    const unsigned long long cnt = __popc(wv[0]) + __popc(wv[1]) + __popc(wv[2]) + __popc(wv[3]);
-    unsigned long long agg;
-    const unsigned long long before = lb_block_scan<TR_BLOCK>(cnt, s_warp, &agg);
-    const unsigned long long prefix = lb_prefix(lb, b, agg, &s_slot);   // ends with a barrier
-    int64_t pos = (int64_t)(prefix + before);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t wbase = (int64_t)b * TC_TILE + (int64_t)warp * 32 * TC_ROUNDS;
+    uint32_t wv[TC_ROUNDS], incl[TC_ROUNDS], rtot[TC_ROUNDS];
+    uint32_t mine = 0;
 #pragma unroll
-    for (int k = 0; k < TC_WPT; ++k) {
-        uint32_t x = wv[k];
-        while (x) {
-            const int bit = __ffs(x) - 1;
-            x &= x - 1;
-            const int64_t v = (w0 + k) * 32 + bit;
-            if (pos < capacity) {
-                cut_ids[pos] = (int32_t)v;
-                if (cut_t) cut_t[pos] = tnode[v];
-            }
-            ++pos;
+    for (int r = 0; r < TC_ROUNDS; ++r) {
+        const int64_t w = wbase + r * 32 + lane;
+        wv[r] = w < words ? mark[w] : 0u;
+        incl[r] = __popc(wv[r]);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl[r], off);
+            if (lane >= off) incl[r] += y;
         }
+        rtot[r] = __shfl_sync(0xffffffffu, incl[r], 31);
+        mine += rtot[r];
     }
-    if (w0 + TC_WPT <= words) *reinterpret_cast<uint4*>(mark + w0) = make_uint4(0, 0, 0, 0);
-    else
-        for (int k = 0; k < TC_WPT; ++k)
-            if (w0 + k < words) mark[w0 + k] = 0u;
+    // block scan over the warps' totals (lane 0 of each warp contributes), then the look-back
+    unsigned long long agg;
+    const unsigned long long before = lb_block_scan<TR_BLOCK>(lane == 0 ? mine : 0u, s_warp, &agg);
+    const unsigned long long wpre = __shfl_sync(0xffffffffu, before, 0);
+    const unsigned long long prefix = lb_prefix(lb, b, agg, &s_slot);   // ends with a barrier
+    int64_t base = (int64_t)(prefix + wpre);
+#pragma unroll
+    for (int r = 0; r < TC_ROUNDS; ++r) {
+        const uint32_t ex = incl[r] - __popc(wv[r]);   // this lane's first slot within the round
+        for (uint32_t s0 = 0; s0 < rtot[r]; s0 += 32) {
+            const uint32_t slot = s0 + lane;
+            // owner: the last lane whose exclusive prefix is <= slot
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t e = __shfl_sync(0xffffffffu, ex, lo + step);
+                if (e <= slot) lo += step;
+            }
+            const uint32_t wo = __shfl_sync(0xffffffffu, wv[r], lo);
+            const uint32_t eo = __shfl_sync(0xffffffffu, ex, lo);
+            if (slot < rtot[r]) {
+                const int bit = (int)__fns(wo, 0u, (int)(slot - eo) + 1);   // -1 if absent (never)
+                const int64_t v = (wbase + r * 32 + lo) * 32 + bit;
+                const int64_t pos = base + slot;
+                if (pos < capacity && bit >= 0 && v < n && H3DGS_IN(v, n)) {
+                    cut_ids[pos] = (int32_t)v;
+                    if (cut_t) cut_t[pos] = tnode[v];
+                }
+            }
+        }
+        base += rtot[r];
+        const int64_t w = wbase + r * 32 + lane;
+        if (w < words && wv[r]) mark[w] = 0u;
+    }
     if ((int64_t)(b + 1) * TC_TILE >= words && threadIdx.x == 0) {   // the last block: offsets and total
         const int64_t total = (int64_t)(prefix + agg);
         cam_totals[0] = 0;
@@ -563,7 +633,7 @@ cudaError_t launch_cut_traverse(const TravArgs& a, const h3dgs_camera& cam, int 
     const size_t lw = LB_HEADER_WORDS + lb_body_words(cblocks);
     if ((int64_t)lw > lb_words) return cudaErrorInvalidValue;
     // level counts and the barrier words are zero before the descent, the look-back words before the compaction
-    cudaError_t e = cudaMemsetAsync(a.level_count, 0, sizeof(uint32_t) * (TR_MAX_LEVELS + 1 + 2), s);
+    cudaError_t e = cudaMemsetAsync(a.level_count, 0, sizeof(uint32_t) * TR_LEVEL_WORDS, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(lb_work, 0, sizeof(uint32_t) * lw, s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};

@@ -394,7 +394,9 @@ struct CutWork {
 size_t cut_single_work_words(int64_t n);
 
 // Traversal cut of one camera (large trees): visits only the cut and its ancestors.
-constexpr int TR_MAX_LEVELS = 1024;   // deepest tree the descent follows (deeper: FLAG_CUT_TRUNCATED)
+constexpr int TR_MAX_LEVELS = 1024;   // descent steps (two levels each; deeper trees: FLAG_CUT_TRUNCATED)
+// level table words: frontier sizes [TR_MAX_LEVELS + 1], the nodes visited inside blocks, 2 barrier words
+constexpr int TR_LEVEL_WORDS = TR_MAX_LEVELS + 1 + 1 + 2;
 struct TravArgs {
     const float4* rec;           // packed cut records [n][2]
     const int32_t* child_start;  // [n]
@@ -402,8 +404,9 @@ struct TravArgs {
     uint32_t* front[2];          // frontier node ids, double-buffered [cap]
     float* feps[2];              // the parent's granularity of every frontier entry [cap]
     int64_t cap;                 // frontier capacity (n suffices for any tree)
-    uint32_t* level_count;       // [TR_MAX_LEVELS + 1] frontier sizes, then the 2 barrier words; zeroed per launch
-    uint32_t* bar;               // = level_count + TR_MAX_LEVELS + 1
+    uint32_t* level_count;       // [TR_LEVEL_WORDS] frontier sizes per step, ...; zeroed per launch
+    uint32_t* inner;             // = level_count + TR_MAX_LEVELS + 1: nodes visited from shared memory
+    uint32_t* bar;               // = level_count + TR_MAX_LEVELS + 2: the grid barrier's 2 words
     uint32_t* mark;              // [(n + 31) / 32] cut bits: zero before, cleared again by the compaction
     float* tnode;                // [n] the parent weight of every cut node
     uint32_t* flags;
