@@ -189,3 +189,64 @@ def test_neighbourhood_frame_matches_the_oracle():
     ofr, g = _compare(cam, ho, dh, oracle.Opts())
     assert len(ofr.ids) > 100_000 and np.sum(ofr.t > 0) > 10_000
     assert g.stats["n_pairs"] == len(ofr.lists)
+
+
+# ---------------------------------------------------------------- C4: 32 mixed-resolution views at once
+
+def test_c4_batch_of_32_views_equals_single_views():
+    """32 cameras on the city loop, 8 each at 1280x720, 1920x1080, 2560x1440 and 3840x2160 with tau
+    cycling over 3, 6, 15, in one cut + render + adjoint: every image equals the camera rendered alone
+    bit for bit, and the node gradients equal the sum of the per-camera adjoints (fp32 reductions in
+    another order: the per-element bar of tests/test_parity_backward.py)."""
+    import torch
+    dh = _city()
+    ctx = gpu_path.context()
+    ctx.upload(dh)
+    cams = synth.city_views(2, 32)
+    N = dh.n
+    ids1 = torch.empty(N, dtype=torch.int32, device="cuda")
+    t1 = torch.empty(N, dtype=torch.float32, device="cuda")
+    offs1 = torch.empty(2, dtype=torch.int64, device="cuda")
+    sizes = [h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids1, t1, offs1, N) for c in cams]
+    cap = int(sum(sizes)) + 1024
+    ids = torch.empty(cap, dtype=torch.int32, device="cuda")
+    t = torch.empty(cap, dtype=torch.float32, device="cuda")
+    offs = torch.empty(len(cams) + 1, dtype=torch.int64, device="cuda")
+    assert h3dgs.h3dgs_select_cut(ctx.ctx, cams, ids, t, offs, cap) == sum(sizes)
+    npix = [3 * c.width * c.height for c in cams]
+    poff = np.concatenate([[0], np.cumsum(npix)])
+    opts = h3dgs.default_opts()
+    img_b = torch.empty(int(poff[-1]), dtype=torch.float32, device="cuda")
+    h3dgs.h3dgs_render(ctx.ctx, cams, ids, t, offs, opts, img_b, 1)
+    dl = torch.randn(int(poff[-1]), generator=torch.Generator(device="cuda").manual_seed(5), device="cuda")
+    keys = ("mean", "scale", "rot", "opacity", "sh")
+    gb = {k: torch.zeros_like(getattr(dh, k)) for k in keys}
+    h3dgs.h3dgs_render_backward(ctx.ctx, dl, gb, 1)
+    torch.cuda.synchronize()
+    assert h3dgs.h3dgs_get_stats(ctx.ctx)["device_flags"] == 0
+    gv = {k: torch.zeros_like(getattr(dh, k)) for k in keys}
+    img_v = torch.empty_like(img_b)
+    for k, c in enumerate(cams):
+        lo, hi = int(poff[k]), int(poff[k + 1])
+        h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids1, t1, offs1, N)
+        h3dgs.h3dgs_render(ctx.ctx, [c], ids1, t1, offs1, opts, img_v[lo:hi], 1)
+        h3dgs.h3dgs_render_backward(ctx.ctx, dl[lo:hi], gv, 1)   # accumulates
+    torch.cuda.synchronize()
+    assert torch.equal(img_b, img_v)
+    # the per-element bar, evaluated on the device (tens of millions of touched rows)
+    touched = 0
+    for k in keys:
+        a_all, b_all = gb[k].reshape(N, -1), gv[k].reshape(N, -1)
+        scale = b_all.abs().max().item()
+        assert scale > 0, k
+        excess, d2, b2, tk = 0.0, 0.0, 0.0, 0
+        for r0 in range(0, N, 8_000_000):   # row chunks bound the temporaries
+            a, b = a_all[r0:r0 + 8_000_000], b_all[r0:r0 + 8_000_000]
+            excess = max(excess, ((a - b).abs() - 1e-3 * b.abs()).max().item() / scale)
+            d2 += float(((a - b).double() ** 2).sum().item())
+            b2 += float((b.double() ** 2).sum().item())
+            tk += int((b.abs().amax(1) > 0).sum().item())
+        assert excess <= 1e-5, (k, excess)
+        assert d2 ** 0.5 <= 1e-3 * b2 ** 0.5, k
+        touched = max(touched, tk)
+    assert touched > 1_000_000
