@@ -58,7 +58,7 @@ BLEND_XU_EVAL, BLEND_XU_INTERP = 1, 2
 ADJ_FLOPS_CONTRIB, ADJ_FLOPS_CONTRIB_INTERP = 74 + BLEND_FLOPS_EVAL, 14 + BLEND_FLOPS_INTERP
 # DRAM bytes (read + write) of one launch of the blend's main kernel at the 1080p corridor frame
 # (16x16 tiles, chunk 384), from an ncu capture of the current kernel; None once the kernel changes
-BLEND_TRAFFIC_BYTES = 28.82e6 + 3.17e6
+BLEND_TRAFFIC_BYTES = 28.98e6 + 4.48e6
 
 
 def parse():
@@ -330,6 +330,17 @@ def run_ours(args, rank, world, local):
         st["n_evals"], st["n_evals_tpass"] = st_counts["n_evals"], st_counts["n_evals_tpass"]
         for k in ("n_evals_interp", "n_contrib", "n_contrib_interp"):
             st[k] = st_counts[k]
+        # the root-down traversal of the same frame: the records it reads and its time (the frame uses the scan)
+        h3dgs.h3dgs_set_cut_mode(ctx.ctx, 2)
+        h3dgs.h3dgs_select_cut(ctx.ctx, cams, ids, tt, offs, cap)   # sizes its buffers
+        trav_acc = []
+        for _ in range(n_prof):
+            h3dgs.h3dgs_select_cut(ctx.ctx, cams, ids, tt, offs, cap, want_total=False)
+            trav_acc.append(h3dgs.h3dgs_get_stage_times(ctx.ctx)["cut"])
+            flush.fill_(1.0)
+        st_counts["n_cut_visited_traversal"] = int(h3dgs.h3dgs_get_stats(ctx.ctx)["n_cut_visited"])
+        st_counts["traversal_ms"] = float(np.mean(trav_acc))
+        h3dgs.h3dgs_set_cut_mode(ctx.ctx, 0)
         # visible splats with an interpolated parent (the adjoint's splat stage reads the parent's row too)
         rec_dbg, rect_dbg, _ = h3dgs.h3dgs_debug_splats(ctx.ctx, int(st["n_cut"]))
         st_counts["n_interp_visible"] = int(np.sum((rect_dbg[:, 0] >= 0) & (rec_dbg[:, 7] != 0)))
@@ -504,8 +515,8 @@ def run_ours(args, rank, world, local):
                 "work_note": f"the oracle's op list: {BLEND_FLOPS_EVAL} flops per main-pass (pixel, splat) evaluation "
                              f"x {n_evals}, +{BLEND_FLOPS_INTERP} for the {n_evals_i} on splats with an interpolated "
                              f"parent (Eq. alphap), +{BLEND_FLOPS_CONTRIB} per accumulated contribution x {n_contrib}; "
-                             f"the {int(st['n_evals_tpass'])} transmittance-pass evaluations of split tiles are not "
-                             f"counted; compares, min and selects are not flops",
+                             f"the {int(st['n_evals_tpass'])} evaluations of the middle chunks' producer walks (extra work "
+                             f"of split tiles) are not counted; compares, min and selects are not flops",
                 "traffic_note": "DRAM read + write of one launch from an ncu capture of this kernel at this workload"}
     if calib:
         roofline["peak_calibrated"] = calib["fp32_tflops"]
@@ -553,10 +564,16 @@ def run_ours(args, rank, world, local):
     for k, b in algo_bytes.items():
         if fwd_stages.get(k):
             stage_bw[k] = {"GB/s": b / (fwd_stages[k] * 1e-3) / 1e9, "frac_hbm": b / (fwd_stages[k] * 1e-3) / 1e9 / hbm}
-    if "cut" in stage_bw:   # this tree is below the traversal threshold: the scan reads every record
-        stage_bw["cut"]["mode"] = "scan" if int(st["n_cut_visited"]) == N else "traversal"
-        stage_bw["cut"]["full_scan_bytes"] = N * 32 + M * 8
-        stage_bw["cut"]["visited_nodes_if_traversed"] = None
+    if "cut" in stage_bw:   # the frame's cut is the scan (all N records); the traversal is timed beside it
+        vis_n = int(st_counts.get("n_cut_visited_traversal", 0))
+        trav_bytes = vis_n * (32 + 16) + M * 16
+        stage_bw["cut"].update({
+            "mode": "scan", "full_scan_bytes": N * 32 + M * 8,
+            "traversal_visited_nodes": vis_n, "traversal_visited_bytes": trav_bytes,
+            "traversal_ms": st_counts.get("traversal_ms"),
+            "traversal_GB/s": trav_bytes / (st_counts["traversal_ms"] * 1e-3) / 1e9 if st_counts.get("traversal_ms") else None,
+            "note": "scan: 32 B record per node + 8 B out per cut entry; traversal: the cut and its ancestors' "
+                    "records + 16 B of frontier per visited node + 16 B per cut entry (marks, weights, ids)"})
     # frame-level roofline: the time every stage would take at its binding peak (HBM stages at the
     # measured copy bandwidth, the blend at the unit-count FP32 peak), summed, over the frame time
     ideal_ms = sum(b / (hbm * 1e9) * 1e3 for b in algo_bytes.values())

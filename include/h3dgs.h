@@ -120,7 +120,8 @@ typedef struct {
                               line are in h3dgs_last_error                        */
     int64_t n_evals;      /* (pixel, splat) evaluations of the blend's main pass
                              (counted only at profiling level 2, else 0)        */
-    int64_t n_evals_tpass; /* extra evaluations of the transmittance pass of split tiles
+    int64_t n_evals_tpass; /* extra evaluations: the walks of the middle chunks' producers
+                             of split tiles, which the consumers repeat while counting
                              (likewise)                                          */
     int64_t n_items;      /* blend work items (tiles, split tiles count once per chunk) */
     int64_t n_evals_interp; /* main-pass evaluations of splats with an interpolated parent

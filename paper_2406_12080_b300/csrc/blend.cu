@@ -11,12 +11,18 @@
 // Street scenes put thousands of splats behind some pixels (near the vanishing point), so a
 // one-CTA-per-tile blend is bounded by its longest list.  A list of L > `chunk` entries is cut into
 // ceil(L / chunk) chunks of near-equal length that run as separate CTAs ("items"):
-//   pass T    (split tiles only) each chunk computes the product of (1 - alpha) over its
-//             contributors, without the stop rule, giving every chunk its incoming transmittance
-//             T_in as a product of the earlier chunks' products;
-//   pass main every item walks its entries from T_in with the exact skip/stop rules; single-chunk
-//             tiles write the pixel directly, chunks of split tiles write (colour, T at the end,
-//             last contributor) to a per-(item, pixel) scratch kept for the adjoint;
+//   producers (chunks 0 .. nch - 2 of split tiles) walk their chunk from T = 1 with the exact
+//             skip/stop rules and hand on the chunk's product of (1 - alpha) over its contributors
+//             (0 if the walk stopped), so that every chunk's incoming transmittance T_in is a product
+//             of the earlier chunks' products; the local colour, end transmittance and last
+//             contributor go to a per-(item, pixel) scratch;
+//   consumers (chunks 1 .. nch - 1) and single-chunk tiles walk their entries from T_in with the
+//             exact rules.  A pixel of a middle chunk whose T_in times the chunk's product is above
+//             t_min by more than the rounding of the product cannot stop inside the chunk; there the
+//             walk from T_in takes the same decisions as the producer's walk from 1, and its colour,
+//             end transmittance and depth are the local ones times T_in, so the consumer takes those
+//             instead of walking.  Single-chunk tiles write the pixel directly, chunks of split tiles
+//             write (colour, T at the end, last contributor) to the scratch kept for the adjoint;
 //   combine   per pixel of a split tile: colour = sum of its chunks, T_final and the last
 //             contributor from the chunk where the walk stopped.
 // A chunk whose T_in is already below t_min adds nothing (the walk stopped in an earlier chunk).
@@ -108,8 +114,8 @@ __device__ __forceinline__ TileGeom2<TW, TH> tile_geom2(const DevCam* __restrict
 
 // The plan: chunk counts per tile, their exclusive scan (single pass, decoupled look-back), the full
 // (tile, chunk) item list (used by the combine and the adjoint) and the work queue of the blend:
-//   producers  chunks 0 .. nch - 2 of split tiles: chunk 0 is blended from T = 1 and hands on its
-//              (1 - alpha) product, the middle chunks compute their product only (transmittance pass);
+//   producers  chunks 0 .. nch - 2 of split tiles, blended from T = 1; each hands on its (1 - alpha)
+//              product;
 //   singles    tiles of one chunk;
 //   consumers  chunks 1 .. nch - 1 of split tiles, blended from the product of the earlier chunks.
 // Per tile the scan carries X = nch - 1 (split tiles) and Y = [nch == 1] packed in one word; the item
@@ -212,10 +218,8 @@ __device__ __forceinline__ void write_pixel(float* img, int64_t plane, float T, 
     }
 }
 
-// Walk of one item over list entries [begin, end) for this thread's two pixels.  MAIN: the exact
-// skip/stop rules with colour; otherwise the transmittance pass (product of (1 - alpha) over
-// contributors, no colour; a pixel is finished once T < t_min, after which nothing it could add
-// matters).  DEPTH: the expected depth Dp is accumulated as a fourth channel.  SAVE: track the
+// Walk of one item over list entries [begin, end) for this thread's two pixels with the exact
+// skip/stop rules.  DEPTH: the expected depth Dp is accumulated as a fourth channel.  SAVE: track the
 // last contributor (kept for the adjoint).
 //
 // The per-entry work is arranged to keep the per-pixel decisions off the critical ALU pipe while
@@ -228,8 +232,8 @@ __device__ __forceinline__ void write_pixel(float* img, int64_t plane, float T, 
 //     arithmetic and no selects;
 //   * the transmittance stop can only happen at a pixel that takes the entry, at most once per
 //     pixel, so it is handled in a warp-uniform branch that is rarely entered: it freezes the
-//     pixel (fl = +inf), and in the main pass undoes the entry for it (stop before the splat).
-template <int TW, int TH, bool MAIN, bool COUNT, bool DEPTH, bool SAVE>
+//     pixel (fl = +inf) and undoes the entry for it (stop before the splat).
+template <int TW, int TH, bool COUNT, bool DEPTH, bool SAVE>
 __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const uint32_t* __restrict__ list,
                                             const float4* __restrict__ splat, const uint32_t* __restrict__ n_spl,
                                             int begin, int end, int list0,
@@ -300,15 +304,15 @@ __device__ __forceinline__ void blend_walk2(const TileGeom2<TW, TH>& g, const ui
                         if (stop0) {
                             done0 = true;
                             fl.x = INF;
-                            if (MAIN) { ae.x = 0.0f; Tn.x = T.x; take0 = false; }
+                            ae.x = 0.0f; Tn.x = T.x; take0 = false;
                         }
                         if (stop1) {
                             done1 = true;
                             fl.y = INF;
-                            if (MAIN) { ae.y = 0.0f; Tn.y = T.y; take1 = false; }
+                            ae.y = 0.0f; Tn.y = T.y; take1 = false;
                         }
                     }
-                    if (MAIN) {
+                    {
                         const float2 w = __fmul2_rn(ae, T);
                         const float4 c = s_c[j];
                         C0 = __ffma2_rn(make_float2(c.x, c.x), w, C0);
@@ -385,7 +389,6 @@ __global__ void __launch_bounds__(TW * TH / 2, 12) blend_queue_kernel(const DevC
     const int2 it = items[item];
     const int64_t tile = it.x;
     const int nch = tile_nch[tile];
-    const bool main_pass = role != 0 || it.y == 0;
     const TileGeom2<TW, TH> g = tile_geom2<TW, TH>(cams, n_cams, tile);
     const int2 r = ranges[tile];
     const int begin = chunk_begin(r, nch, it.y);
@@ -393,6 +396,8 @@ __global__ void __launch_bounds__(TW * TH / 2, 12) blend_queue_kernel(const DevC
     const int64_t s0 = (int64_t)item * NT + g.slot0, s1 = (int64_t)item * NT + g.slot1;
     const int lane = threadIdx.x & 31;
     float2 T = make_float2(1.0f, 1.0f);
+    float2 Tc = T;                      // the producer's product of this chunk (middle chunks)
+    bool short0 = false, short1 = false;
     if (role == 2) {
         // wait for the tile's nch - 1 producers, then T_in = product of the earlier chunks' products
         if (threadIdx.x == 0) wait_geq(tile_done + tile, (uint32_t)(nch - 1), QUEUE_SPIN_LIMIT, flags);
@@ -400,19 +405,27 @@ __global__ void __launch_bounds__(TW * TH / 2, 12) blend_queue_kernel(const DevC
         const int64_t i0 = tile_item0[tile];
         for (int c = 0; c < it.y; ++c)
             T = __fmul2_rn(T, make_float2(__ldcg(sc.Tc + (i0 + c) * NT + g.slot0), __ldcg(sc.Tc + (i0 + c) * NT + g.slot1)));
+        if (it.y + 1 < nch) {
+            // T_in Tc >= t_min (1 + 4 len u) (u = 2^-24): the sequential products from T_in differ from
+            // T_in Tc by at most 2 len roundings, so no T (1 - alpha) of the chunk falls below t_min (a
+            // product the local walk stopped on is 0 and never passes)
+            Tc = make_float2(__ldcg(sc.Tc + s0), __ldcg(sc.Tc + s1));
+            const float thr = fmul(o.t_min, ffma((float)(end - begin), 2.384185791015625e-7f, 1.0f));
+            const float2 P = __fmul2_rn(T, Tc);
+            short0 = g.in0 && P.x >= thr;
+            short1 = g.in1 && P.y >= thr;
+        }
     }
     float2 C0 = make_float2(0.0f, 0.0f), C1 = C0, C2 = C0, Dp = C0;
     int2 last = make_int2(-1, -1);
     unsigned int evals = 0, evals_i = 0, contribs = 0, contribs_i = 0;
-    bool done0 = !g.in0 || T.x < o.t_min, done1 = !g.in1 || T.y < o.t_min;
-    if (main_pass)
-        blend_walk2<TW, TH, true, COUNT, DEPTH, SAVE>(g, list, splat, n_spl, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
-                                                      o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp, last,
-                                                      done0, done1, evals, evals_i, contribs, contribs_i);
-    else
-        blend_walk2<TW, TH, false, COUNT, false, false>(g, list, splat, n_spl, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
-                                                        o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp,
-                                                        last, done0, done1, evals, evals_i, contribs, contribs_i);
+    // while counting, every pixel walks (the counts are those of the sequential walk) and the shortcut's
+    // values replace the walk's afterwards, so that the image does not depend on the counting
+    const float2 Tin = T;
+    bool done0 = !g.in0 || T.x < o.t_min || (!COUNT && short0), done1 = !g.in1 || T.y < o.t_min || (!COUNT && short1);
+    blend_walk2<TW, TH, COUNT, DEPTH, SAVE>(g, list, splat, n_spl, begin, end, r.x, o.alpha_clamp, o.alpha_floor,
+                                            o.t_min, s_a, s_b, s_c, s_m, s_d, s_box, T, C0, C1, C2, Dp, last, done0,
+                                            done1, evals, evals_i, contribs, contribs_i);
     if (COUNT) {
         for (int off = 16; off > 0; off >>= 1) {
             evals += __shfl_down_sync(0xffffffffu, evals, off);
@@ -420,9 +433,12 @@ __global__ void __launch_bounds__(TW * TH / 2, 12) blend_queue_kernel(const DevC
             contribs += __shfl_down_sync(0xffffffffu, contribs, off);
             contribs_i += __shfl_down_sync(0xffffffffu, contribs_i, off);
         }
+        // the middle producers' walks are repeated by their consumers while counting: counted apart,
+        // as extra work
+        const bool counted = role != 0 || it.y == 0;
         if (lane == 0) {
-            atomicAdd(&s_evals[main_pass ? 0 : 1], evals);
-            if (main_pass) {
+            atomicAdd(&s_evals[counted ? 0 : 1], evals);
+            if (counted) {
                 atomicAdd(&s_evals[2], evals_i);
                 atomicAdd(&s_evals[3], contribs);
                 atomicAdd(&s_evals[4], contribs_i);
@@ -430,26 +446,22 @@ __global__ void __launch_bounds__(TW * TH / 2, 12) blend_queue_kernel(const DevC
         }
     }
     if (role == 0) {
-        // the product handed to the later chunks: 0 once the first chunk's walk stopped
-        if (!main_pass) {
-            sc.Tc[s0] = T.x;
-            sc.Tc[s1] = T.y;
-        } else {
-            sc.C[3 * s0 + 0] = C0.x; sc.C[3 * s0 + 1] = C1.x; sc.C[3 * s0 + 2] = C2.x;
-            sc.C[3 * s1 + 0] = C0.y; sc.C[3 * s1 + 1] = C1.y; sc.C[3 * s1 + 2] = C2.y;
-            sc.Tend[s0] = T.x;
-            sc.Tend[s1] = T.y;
-            if (SAVE) {
-                sc.last[s0] = last.x;
-                sc.last[s1] = last.y;
-            }
-            if (DEPTH) {
-                sc.D[s0] = Dp.x;
-                sc.D[s1] = Dp.y;
-            }
-            sc.Tc[s0] = (done0 && g.in0) ? 0.0f : T.x;
-            sc.Tc[s1] = (done1 && g.in1) ? 0.0f : T.y;
+        // the local walk (the first chunk's is final) and the product handed to the later chunks:
+        // 0 once the walk stopped
+        sc.C[3 * s0 + 0] = C0.x; sc.C[3 * s0 + 1] = C1.x; sc.C[3 * s0 + 2] = C2.x;
+        sc.C[3 * s1 + 0] = C0.y; sc.C[3 * s1 + 1] = C1.y; sc.C[3 * s1 + 2] = C2.y;
+        sc.Tend[s0] = T.x;
+        sc.Tend[s1] = T.y;
+        if (SAVE) {
+            sc.last[s0] = last.x;
+            sc.last[s1] = last.y;
         }
+        if (DEPTH) {
+            sc.D[s0] = Dp.x;
+            sc.D[s1] = Dp.y;
+        }
+        sc.Tc[s0] = (done0 && g.in0) ? 0.0f : T.x;
+        sc.Tc[s1] = (done1 && g.in1) ? 0.0f : T.y;
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(tile_done + tile, 1u);
@@ -460,6 +472,29 @@ __global__ void __launch_bounds__(TW * TH / 2, 12) blend_queue_kernel(const DevC
         atomicAdd(n_evals + threadIdx.x, (unsigned long long)s_evals[threadIdx.x]);
     if (role == 0) return;
     if (nch > 1) {
+        // pixels that take the producer's walk: its local values times T_in (without counting, T still
+        // holds T_in there)
+        const float2 T0 = COUNT ? Tin : T;
+        // checked build, while counting: the walk from T_in did not stop and ended on the producer's
+        // last contributor
+        if (COUNT && short0) H3DGS_HOLDS(!done0 && (!SAVE || last.x == __ldcg(sc.last + s0)));
+        if (COUNT && short1) H3DGS_HOLDS(!done1 && (!SAVE || last.y == __ldcg(sc.last + s1)));
+        if (short0) {
+            C0.x = fmul(T0.x, __ldcg(sc.C + 3 * s0 + 0));
+            C1.x = fmul(T0.x, __ldcg(sc.C + 3 * s0 + 1));
+            C2.x = fmul(T0.x, __ldcg(sc.C + 3 * s0 + 2));
+            if (SAVE) last.x = __ldcg(sc.last + s0);
+            if (DEPTH) Dp.x = fmul(T0.x, __ldcg(sc.D + s0));
+            T.x = fmul(T0.x, Tc.x);
+        }
+        if (short1) {
+            C0.y = fmul(T0.y, __ldcg(sc.C + 3 * s1 + 0));
+            C1.y = fmul(T0.y, __ldcg(sc.C + 3 * s1 + 1));
+            C2.y = fmul(T0.y, __ldcg(sc.C + 3 * s1 + 2));
+            if (SAVE) last.y = __ldcg(sc.last + s1);
+            if (DEPTH) Dp.y = fmul(T0.y, __ldcg(sc.D + s1));
+            T.y = fmul(T0.y, Tc.y);
+        }
         sc.C[3 * s0 + 0] = C0.x; sc.C[3 * s0 + 1] = C1.x; sc.C[3 * s0 + 2] = C2.x;
         sc.C[3 * s1 + 0] = C0.y; sc.C[3 * s1 + 1] = C1.y; sc.C[3 * s1 + 2] = C2.y;
         sc.Tend[s0] = T.x;

@@ -29,7 +29,8 @@ constexpr uint32_t FLAG_BOUNDS = 1u << 7;         // checked build: an index fai
 // index that comes from data -- a parent id, a cut id, a list entry, a staging slot or a scatter
 // destination of the radix sort, a work item -- against the buffer it addresses before the access.  A
 // failed check records the source line in its translation unit's check word and the access is
-// skipped or redirected to element 0; nothing traps, so the context stays usable and the host reads
+// skipped or redirected to element 0; a few invariants are tested the same way (H3DGS_HOLDS); nothing
+// traps, so the context stays usable and the host reads
 // the words (h3dgs_get_stats: FLAG_BOUNDS, and the file and line in h3dgs_last_error).  The default
 // build compiles every check to `true`.
 #ifdef H3DGS_CHECK
@@ -40,6 +41,8 @@ __device__ __forceinline__ bool check_in(int64_t i, int64_t n, int line) {
     return false;
 }
 #define H3DGS_IN(i, n) ::h3dgs::check_in((int64_t)(i), (int64_t)(n), __LINE__)
+// an invariant that the kernel relies on (recorded like a failed range check)
+#define H3DGS_HOLDS(c) ::h3dgs::check_in((c) ? 0 : -1, 1, __LINE__)
 #define H3DGS_CHECK_READER(name)                                                                              \
     cudaError_t name(uint32_t out[2], cudaStream_t s) {                                                         \
         cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_check_word, sizeof(uint32_t) * 2, 0,                  \
@@ -53,6 +56,7 @@ __device__ __forceinline__ bool check_in(int64_t i, int64_t n, int line) {
     }
 #else
 #define H3DGS_IN(i, n) true
+#define H3DGS_HOLDS(c) true
 #define H3DGS_CHECK_READER(name)                                                                              \
     cudaError_t name(uint32_t out[2], cudaStream_t) {                                                           \
         out[0] = out[1] = 0u;                                                                                   \
@@ -519,7 +523,7 @@ struct BlendArgs {
     float* scratch_D;             // per (item, pixel) expected depth of split tiles' chunks (depth only)
     float* T_final;
     int32_t* n_contrib;
-    unsigned long long* n_evals;  // [5]: main-pass evaluations, transmittance-pass evaluations, main-pass
+    unsigned long long* n_evals;  // [5]: main-pass evaluations, middle producers' evaluations, main-pass
                                   // evaluations of splats with t != 0, applied contributions, those of
                                   // splats with t != 0
     uint32_t* work;               // look-back workspace of the plan (LB_HEADER_WORDS + 2 per 1024 tiles)

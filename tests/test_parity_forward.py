@@ -183,3 +183,37 @@ def test_one_tile_with_twenty_thousand_splats():
     ofr, g = _compare(cam, h, dh, oracle.Opts())
     lengths = ofr.ranges[:, 1] - ofr.ranges[:, 0]
     assert lengths.max() > 16384
+
+
+
+@pytest.mark.parametrize("which,chunk", [("tiny", 64), ("tiny", 100), ("full_size_corridor", 64),
+                                         ("full_size_corridor", None)])
+def test_middle_chunk_shortcut_and_counting(which, chunk):
+    """Consumers of middle chunks take the producer's local walk times T_in at the pixels that cannot stop
+    inside the chunk.  While counting (profiling level 2) every consumer walks all its pixels and then
+    takes the same values, so the outputs are bit-identical with and without counting; in the checked
+    build the counting kernel also verifies that each such walk did not stop and ended on the producer's
+    last contributor (bit 7 of the device flags, asserted clear by gpu_path.run)."""
+    from paper_2406_12080_b300 import h3dgs
+    sc, h = scenes.tiny() if which == "tiny" else scenes.corridor()
+    dh = gpu_path.upload(h)
+    cam = synth.with_tau(sc.cameras[0], 2.0 if which == "tiny" else 6.0)
+    ctx = gpu_path.context()
+    runs = []
+    for prof in (0, 2):
+        h3dgs.h3dgs_set_profiling(ctx.ctx, prof)
+        try:
+            g = gpu_path.run(dh, [cam], oracle.Opts(), chunk=chunk)
+        finally:
+            h3dgs.h3dgs_set_profiling(ctx.ctx, 0)
+        runs.append(g)
+    a, b = runs
+    ranges, _ = gpu_path.tile_lists(0, int(b.stats["n_tiles"]))
+    lens = ranges[:, 1] - ranges[:, 0]
+    c = chunk or 384
+    middle = bool(np.any(lens > 2 * c))       # tiles of three or more chunks
+    assert middle or chunk != 64
+    assert (b.stats["n_evals_tpass"] > 0) == middle
+    np.testing.assert_array_equal(a.images[0].view(np.uint32), b.images[0].view(np.uint32))
+    np.testing.assert_array_equal(a.T_final.view(np.uint32), b.T_final.view(np.uint32))
+    np.testing.assert_array_equal(a.n_contrib, b.n_contrib)

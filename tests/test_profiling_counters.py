@@ -6,7 +6,8 @@ and the counts respect bounds that any correct blend satisfies.
   (the oracle's lists).
 * Evaluations of splats with an interpolated parent (t != 0, where the transition alpha of Eq. alphap
   is evaluated too) are a subset of the main-pass ones, and there are none with interpolation off.
-* The transmittance pass runs only for split tiles: none when the chunk exceeds every list.
+* The middle chunks' producer walks (counted apart) exist only for split tiles: none when the chunk
+  exceeds every list.
 """
 import numpy as np
 import pytest
