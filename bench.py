@@ -344,7 +344,16 @@ def run_ours(args, rank, world, local):
         # visible splats with an interpolated parent (the adjoint's splat stage reads the parent's row too)
         rec_dbg, rect_dbg, _ = h3dgs.h3dgs_debug_splats(ctx.ctx, int(st["n_cut"]))
         st_counts["n_interp_visible"] = int(np.sum((rect_dbg[:, 0] >= 0) & (rec_dbg[:, 7] != 0)))
-        del rec_dbg, rect_dbg
+        # the frame's entries and the distinct parents the interpolation reads (of all entries with
+        # t != 0 for the geometry, of the visible ones for opacity, K and SH)
+        m_cut = int(st["n_cut"])
+        vis_m = rect_dbg[:m_cut, 0] >= 0
+        cut_np = ids[:m_cut].cpu().numpy()
+        par_np = hier.parent.cpu().numpy()[cut_np]
+        interp_m = (tt[:m_cut].cpu().numpy() != 0) & (par_np >= 0)
+        st_counts["n_parents_geom"] = int(np.unique(par_np[interp_m]).size)
+        st_counts["n_parents_vis"] = int(np.unique(par_np[interp_m & vis_m]).size)
+        del rec_dbg, rect_dbg, cut_np, par_np
 
         # ---- fwd + bwd views/s
         grads = {k: torch.zeros_like(getattr(hier, k)) for k in ("mean", "scale", "rot", "opacity", "sh")}
@@ -552,36 +561,60 @@ def run_ours(args, rank, world, local):
     hbm = float(peaks.get("hbm_gbs", 6442.9))
     stage_bw = {}
     M, V, Pn = int(st["n_cut"]), int(st["n_visible"]), int(st["n_pairs"])
-    # algorithmic bytes: cut reads 32 B of records per node (+ the parent's, half of them cached) and writes
-    # 8 B per cut entry; preprocess reads the node and parent attributes (236 + 16 B) and writes 64 B of
-    # record + 16 B of key/count/rect per entry; each radix pass reads and writes 8 B per key/value pair;
-    # duplicate reads 16 B per visible splat and writes 8 B per pair
-    algo_bytes = {"cut": N * 32 + N * 32 // 2 + M * 8,
-                  "preprocess": M * (236 + 16) + M * 80,
-                  "depth_sort": 4 * V * 16,
+    visited = int(st_counts.get("n_cut_visited_traversal", 0)) or N
+    Ug, Uv = int(st_counts.get("n_parents_geom", 0)), int(st_counts.get("n_parents_vis", 0))
+    # algorithmic bytes per stage (the least the method moves):
+    #   cut         the records of the visited nodes (the cut and its ancestors), 32 B each, + 8 B (id, t)
+    #               out per cut entry
+    #   preprocess  per entry its id, t, parent id and geometry (mean, scale, rot: 52 B) and per distinct
+    #               interpolated parent the geometry (40 B); per visible entry opacity + SH (196 B) and per
+    #               distinct parent of a visible interpolated entry opacity, K and SH (200 B); out 80 B
+    #               (record 64, rect, key, tile count) per visible entry and 16 B per culled one
+    #   sorts       one read and one write of each 8 B key/value pair (the LSD passes move that per pass:
+    #               `pass_bytes`)
+    #   duplicate   16 B read per visible splat, 8 B written per pair
+    algo_bytes = {"cut": visited * 32 + M * 8,
+                  "preprocess": M * 52 + Ug * 40 + V * 196 + Uv * 200 + V * 80 + (M - V) * 16,
+                  "depth_sort": V * 16,
                   "duplicate": V * 16 + Pn * 8,
-                  "tile_sort": 2 * Pn * 16}
+                  "tile_sort": Pn * 16}
+    # bytes the implementation moves (the kernel's own efficiency): the scan reads the records of the
+    # tiles its bound test keeps
+    scan_read = int(st.get("n_cut_visited", N))
+    impl_bytes = {**algo_bytes, "cut": scan_read * 32 + M * 8, "depth_sort": 4 * V * 16, "tile_sort": 2 * Pn * 16}
     for k, b in algo_bytes.items():
         if fwd_stages.get(k):
-            stage_bw[k] = {"GB/s": b / (fwd_stages[k] * 1e-3) / 1e9, "frac_hbm": b / (fwd_stages[k] * 1e-3) / 1e9 / hbm}
+            sec = fwd_stages[k] * 1e-3
+            stage_bw[k] = {"algorithmic_bytes": b, "algorithmic_GB/s": b / sec / 1e9,
+                           "frac_hbm": b / sec / 1e9 / hbm}
+            if impl_bytes[k] != b:
+                stage_bw[k].update({"pass_bytes": impl_bytes[k], "pass_GB/s": impl_bytes[k] / sec / 1e9,
+                                    "pass_frac_hbm": impl_bytes[k] / sec / 1e9 / hbm})
+    if "preprocess" in stage_bw:
+        stage_bw["preprocess"].update({"distinct_parents_geometry": Ug, "distinct_parents_visible": Uv})
     if "cut" in stage_bw:   # the frame's cut is the scan (all N records); the traversal is timed beside it
         vis_n = int(st_counts.get("n_cut_visited_traversal", 0))
         trav_bytes = vis_n * (32 + 16) + M * 16
         stage_bw["cut"].update({
-            "mode": "scan", "full_scan_bytes": N * 32 + M * 8,
-            "traversal_visited_nodes": vis_n, "traversal_visited_bytes": trav_bytes,
+            "mode": "scan", "visited_nodes": vis_n, "scan_read_nodes": scan_read,
+            "traversal_visited_bytes": trav_bytes,
             "traversal_ms": st_counts.get("traversal_ms"),
             "traversal_GB/s": trav_bytes / (st_counts["traversal_ms"] * 1e-3) / 1e9 if st_counts.get("traversal_ms") else None,
-            "note": "scan: 32 B record per node + 8 B out per cut entry; traversal: the cut and its ancestors' "
+            "note": "algorithmic: the visited nodes' records + 8 B per cut entry; pass (the scan): the "
+                    "records of the tiles kept by its bound test + 8 B per cut entry; traversal: the visited "
                     "records + 16 B of frontier per visited node + 16 B per cut entry (marks, weights, ids)"})
     # frame-level roofline: the time every stage would take at its binding peak (HBM stages at the
-    # measured copy bandwidth, the blend at the unit-count FP32 peak), summed, over the frame time
+    # measured copy bandwidth with their algorithmic bytes, the blend at the unit-count FP32 peak),
+    # summed, over the frame time
     ideal_ms = sum(b / (hbm * 1e9) * 1e3 for b in algo_bytes.values())
     ideal_ms += flops / (fp32_peak_tflops * 1e12) * 1e3
     frame_ms = total_ms / args.steps
     frame_roofline = {"frac": ideal_ms / frame_ms, "ideal_ms": ideal_ms, "frame_ms": frame_ms,
+                      "frac_with_pass_bytes": (ideal_ms + sum((impl_bytes[k] - algo_bytes[k]) / (hbm * 1e9) * 1e3
+                                                              for k in algo_bytes)) / frame_ms,
                       "note": "sum over cut, preprocess, sorts, duplication (algorithmic bytes at the measured HBM "
-                              "copy rate) and blend (main-pass flops at the FP32 peak), divided by the frame time"}
+                              "copy rate) and blend (main-pass flops at the FP32 peak), divided by the frame time; "
+                              "frac_with_pass_bytes counts the scan's and the LSD passes' bytes instead"}
     clocks = clk.summary()
     out = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -940,7 +973,7 @@ def run_city(args, rank, world, local):
             h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids, tt, offs, N, want_total=False)
             h3dgs.h3dgs_render(ctx.ctx, [c], ids, tt, offs, opts, images, 0, cam_array=a)
         torch.cuda.synchronize()
-        cut_ms, render_ms, sizes, pairs = [], [], [], []
+        cut_ms, render_ms, sizes, pairs, scan_read = [], [], [], [], []
         with ClockSampler(local) as clk:
             for c, a in zip(poses, arrs):
                 e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -955,6 +988,7 @@ def run_city(args, rank, world, local):
                 render_ms.append(e[1].elapsed_time(e[2]))
                 sizes.append(int(st["n_cut"]))
                 pairs.append(int(st["n_pairs"]))
+                scan_read.append(int(st["n_cut_visited"]))
         frame_ms = np.array(cut_ms) + np.array(render_ms)
         # the root-down traversal on the same poses (every 8th): the records it reads and its time
         h3dgs.h3dgs_set_cut_mode(ctx.ctx, 2)
@@ -972,19 +1006,27 @@ def run_city(args, rank, world, local):
         scan_ms = cut_ms
         hbm = float(measured_peaks().get("hbm_gbs", 6442.9))
         v_mean = float(np.mean(visited))
-        # algorithmic bytes: the 32 B record of every node read, + 8 B per cut entry written; the
-        # descent also reads and writes 8 B of frontier per visited node and 4 B of weight per cut node
+        # algorithmic bytes: the 32 B record of every visited node (the cut and its ancestors), + 8 B per
+        # cut entry written; the scan reads the records of the tiles its bound test keeps, the descent
+        # also reads and writes 8 B of frontier per visited node and 4 B of weight per cut node
+        algo_bytes = v_mean * 32 + float(np.mean(sizes)) * 8
         trav_bytes = v_mean * (32 + 16) + float(np.mean(sizes)) * (8 + 8)
-        scan_bytes = N * 32 + float(np.mean(sizes)) * 8
-        cut_bw = {"visited_nodes_mean": v_mean, "visited_bytes": trav_bytes, "full_scan_bytes": scan_bytes,
+        scan_bytes = float(np.mean(scan_read)) * 32 + float(np.mean(sizes)) * 8
+        cut_bw = {"visited_nodes_mean": v_mean, "algorithmic_bytes": algo_bytes,
+                  "algorithmic_GB/s": algo_bytes / (np.mean(scan_ms) * 1e-3) / 1e9,
+                  "algorithmic_frac_hbm": algo_bytes / (np.mean(scan_ms) * 1e-3) / 1e9 / hbm,
+                  "scan_read_nodes_mean": float(np.mean(scan_read)), "scan_bytes": scan_bytes,
+                  "full_scan_bytes": N * 32 + float(np.mean(sizes)) * 8, "traversal_bytes": trav_bytes,
                   "mode": "scan", "scan_ms_mean": float(np.mean(scan_ms)),
                   "scan_GB/s": scan_bytes / (np.mean(scan_ms) * 1e-3) / 1e9,
                   "scan_frac_hbm": scan_bytes / (np.mean(scan_ms) * 1e-3) / 1e9 / hbm,
                   "traversal_ms_mean": float(np.mean(trav_ms)),
                   "traversal_GB/s": trav_bytes / (np.mean(trav_ms) * 1e-3) / 1e9,
                   "traversal_frac_hbm": trav_bytes / (np.mean(trav_ms) * 1e-3) / 1e9 / hbm,
-                  "note": "one camera per frame; the frames use the scan (all N records); the root-down "
-                          "traversal (cut and ancestors + frontier traffic) is timed on every 8th pose"}
+                  "note": "one camera per frame; the frames use the scan (every record of the 256-node rows "
+                          "whose parents' granularity bound reaches tau; algorithmic_GB/s is the visited nodes' "
+                          "records over the scan's time); the root-down traversal (cut and ancestors + "
+                          "frontier traffic) is timed on every 8th pose"}
         value = len(poses) / (frame_ms.sum() * 1e-3)
         batched = None
         if args.batch_views > 0:

@@ -129,8 +129,11 @@ typedef struct {
     int64_t n_contrib;    /* (pixel, splat) pairs whose colour was accumulated: alpha at or above the
                              floor, before the transmittance stop (profiling level 2, else 0) */
     int64_t n_contrib_interp; /* those of splats with an interpolated parent (t != 0; likewise) */
-    int64_t n_cut_visited; /* nodes whose record the last cut read: all nodes for the scan, the cut and
-                              its ancestors for the traversal (h3dgs_set_cut_mode) */
+    int64_t n_cut_visited; /* nodes whose record the last cut read: for the one-camera scan all nodes
+                              except those of the 256-node rows it skipped (a row is skipped when a
+                              bound on its nodes' parents' granularity is below tau, so none of its
+                              nodes can be in the cut), for a camera batch all nodes, for the
+                              traversal the cut and its ancestors (h3dgs_set_cut_mode) */
 } h3dgs_stats;
 
 /* Per-stage device times of the most recent select_cut / render / render_backward, in ms,

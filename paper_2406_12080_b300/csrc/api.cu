@@ -41,9 +41,10 @@ T* P(DBuf& b) { return reinterpret_cast<T*>(b.p); }
 // C_EVALS, C_EVALS_T, C_EVALS_I, C_CONTRIB and C_CONTRIB_I occupy two words each (64-bit counters, in this order)
 // C_NSORTED: a zero word (the bounded-wait probe); C_NTSORT: unused
 // C_NITEMS: 4 words (items, producers, singles, split tiles).  C_FLAGS: render flags (cleared by every render);
-// C_CUTFLAGS: cut flags (cleared by every cut); the stats report both.
+// C_CUTFLAGS: cut flags (cleared by every cut); the stats report both.  C_CUTSKIP: nodes in the rows
+// the one-camera scan skipped (cleared by every cut).
 enum { C_FLAGS = 0, C_NSPLATS = 1, C_NVISIBLE = 2, C_NPAIRS = 3, C_NPAIRS_KEPT = 4, C_NSORTED = 6,
-       C_NTSORT = 7, C_NITEMS = 14, C_CUTFLAGS = 18, C_EVALS = 20, C_EVALS_T = 22, C_EVALS_I = 24, C_CONTRIB = 26,
+       C_NTSORT = 7, C_NITEMS = 14, C_CUTFLAGS = 18, C_CUTSKIP = 19, C_EVALS = 20, C_EVALS_T = 22, C_EVALS_I = 24, C_CONTRIB = 26,
        C_CONTRIB_I = 28, C_COUNT = 30 };
 constexpr int EVAL_WORDS = 10;   // the five 64-bit blend counters from C_EVALS on
 
@@ -56,7 +57,7 @@ struct h3dgs_ctx {
     int num_sms = 148;
     h3dgs_hierarchy hier{};
     bool has_hier = false;
-    DBuf rec, cams, counters;
+    DBuf rec, rec_tb, cams, counters;
     DBuf cut_mask, cut_bc, cut_tot, cut_lb;
     // traversal cut: frontiers, their parents' granularities, level counts + barrier, marks, weights
     DBuf tr_front0, tr_front1, tr_feps0, tr_feps1, tr_level, tr_mark, tr_tnode;
@@ -186,6 +187,7 @@ DevHier dev_hier(h3dgs_ctx* ctx) {
     h.parent = ctx->hier.parent;
     h.child_count = ctx->hier.child_count;
     h.rec = P<const float4>(ctx->rec);
+    h.row_bound = P<const float4>(ctx->rec_tb);
     h.row_of = nullptr;
     if (ctx->streamed) {
         h.mean = ctx->st.mean;
@@ -317,7 +319,7 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
     if (!ctx) return H3DGS_OK;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    DBuf* bufs[] = {&ctx->rec, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot, &ctx->cut_lb,
+    DBuf* bufs[] = {&ctx->rec, &ctx->rec_tb, &ctx->cams, &ctx->counters, &ctx->cut_mask, &ctx->cut_bc, &ctx->cut_tot, &ctx->cut_lb,
                     &ctx->s_rec, &ctx->s_rect, &ctx->s_key, &ctx->s_idx, &ctx->s_key2, &ctx->s_idx2,
                     &ctx->s_key3, &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1,
                     &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->hists, &ctx->fw, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
@@ -503,6 +505,8 @@ h3dgs_status h3dgs_upload_hierarchy(h3dgs_ctx* ctx, const h3dgs_hierarchy* h) {
     CK(cudaSetDevice(ctx->device), "set device");
     CK(ensure(ctx->rec, sizeof(float4) * 2 * (size_t)h->n_nodes), "record buffer");
     CK(launch_pack_records(*h, P<float4>(ctx->rec), ctx->stream), "pack records");
+    CK(ensure(ctx->rec_tb, sizeof(float4) * 2 * (size_t)cut_row_count(h->n_nodes)), "row bounds");
+    CK(launch_cut_row_bounds(P<const float4>(ctx->rec), h->n_nodes, P<float4>(ctx->rec_tb), ctx->stream), "row bounds");
     ctx->hier = *h;
     ctx->has_hier = true;
     ctx->streamed = false;
@@ -549,6 +553,8 @@ h3dgs_status h3dgs_upload_hierarchy_streamed(h3dgs_ctx* ctx, const h3dgs_hierarc
     CK(ensure(ctx->st_count, 16), "stream tables");
     CK(ensure(ctx->rec, sizeof(float4) * 2 * N), "record buffer");
     CK(launch_pack_records(*h, P<float4>(ctx->rec), ctx->stream), "pack records");
+    CK(ensure(ctx->rec_tb, sizeof(float4) * 2 * (size_t)cut_row_count(h->n_nodes)), "row bounds");
+    CK(launch_cut_row_bounds(P<const float4>(ctx->rec), h->n_nodes, P<float4>(ctx->rec_tb), ctx->stream), "row bounds");
     StreamState& st = ctx->st;
     st.n_nodes = h->n_nodes;
     st.cap = cache_nodes;
@@ -635,7 +641,9 @@ h3dgs_status h3dgs_select_cut(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t 
     w.mask = P<uint32_t>(ctx->cut_mask);
     w.block_counts = P<uint32_t>(ctx->cut_bc);
     w.cam_totals = P<int64_t>(ctx->cut_tot);
-    CK(cudaMemsetAsync(P<uint32_t>(ctx->counters) + C_CUTFLAGS, 0, sizeof(uint32_t), ctx->stream), "memset");
+    // the cut's flags and its count of nodes in skipped tiles
+    CK(cudaMemsetAsync(P<uint32_t>(ctx->counters) + C_CUTFLAGS, 0, 2 * sizeof(uint32_t), ctx->stream), "memset");
+    w.skipped_nodes = P<uint32_t>(ctx->counters) + C_CUTSKIP;
     bool traverse = n_cams == 1 && ctx->cut_mode == 2;
     if (traverse && ctx->tr_grid < 0) ctx->tr_grid = cut_traverse_grid(ctx->num_sms);
     if (traverse && ctx->tr_grid <= 0) traverse = false;   // no cooperative launch: the scan
@@ -998,7 +1006,8 @@ h3dgs_status h3dgs_get_stats(h3dgs_ctx* ctx, h3dgs_stats* out) {
     out->n_contrib = (int64_t)ev;
     std::memcpy(&ev, c + C_CONTRIB_I, sizeof(ev));
     out->n_contrib_interp = (int64_t)ev;
-    out->n_cut_visited = ctx->has_hier ? ctx->hier.n_nodes : 0;
+    // the scan reads every record except those of the rows its bound test skipped
+    out->n_cut_visited = ctx->has_hier ? ctx->hier.n_nodes - (int64_t)c[C_CUTSKIP] : 0;
     if (ctx->last_cut_traversed) {   // the root, then every level's frontier
         std::vector<uint32_t> lv(TR_MAX_LEVELS + 2);   // frontier sizes, then the inner visits
         CK(cudaMemcpyAsync(lv.data(), ctx->tr_level.p, sizeof(uint32_t) * lv.size(), cudaMemcpyDeviceToHost,

@@ -223,13 +223,73 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_write_kernel(const float4* __re
 constexpr int CS_IPT = 10;   // with at most 6 blocks of 256 per SM a 2M-node scan is one wave (8..16 measured, 10 fastest)
 constexpr int CS_GRP = 2;   // nodes whose loads are in flight together (2 measured fastest of 1, 2, 4, 8)
 constexpr int CS_TILE = CUT_BLOCK * CS_IPT;
+//
+// Rows (CUT_BLOCK consecutive node ids, one step of a tile) that cannot hold a cut node are skipped
+// without reading their records.  A node is only in the cut if eps(parent) >= tau (or it is the
+// root).  Per row the upload stores the union box U of its nodes' parents and their largest side S
+// (cut_row_bounds_kernel); every parent p then has eps(p) = f size_p / dist(c, box_p) <= f S / dist(c, U),
+// since box_p lies inside U.  When that bound is below tau by a margin of 1e-4 (relative), far above
+// the rounding of the bound and of the fp32 eps(p) the test would compute, no node of the row is
+// selected.  A row holding any node of the cut or its ancestors is always read, so the scan reads at
+// least what a root-down traversal visits; far chunks of a city lose most of their deep rows.
+constexpr int CUT_ROW = CUT_BLOCK;
+
+__global__ void __launch_bounds__(CUT_ROW) cut_row_bounds_kernel(const float4* __restrict__ rec, int64_t n,
+                                                                 float4* __restrict__ rb) {
+    __shared__ float s_r[CUT_ROW / 32][8];
+    const float INF = __int_as_float(0x7f800000);
+    float v[8] = {INF, INF, INF, 0.0f, -INF, -INF, -INF, 0.0f};   // U.lo, S, U.hi, no-skip flag
+    const int64_t i = (int64_t)blockIdx.x * CUT_ROW + threadIdx.x;
+    if (i < n) {
+        const int32_t p = __float_as_int(__ldg(rec + 2 * i).w);
+        if (p < 0 || p >= n) {   // the root (or an invalid parent): never skipped
+            v[7] = 1.0f;
+        } else {
+            const float4 lo = __ldg(rec + 2 * (int64_t)p), hi = __ldg(rec + 2 * (int64_t)p + 1);
+            const float s = fmaxf(fmaxf(fsub(hi.x, lo.x), fsub(hi.y, lo.y)), fsub(hi.z, lo.z));
+            if (isnan(lo.x) || isnan(lo.y) || isnan(lo.z) || isnan(hi.x) || isnan(hi.y) || isnan(hi.z) || isnan(s))
+                v[7] = 1.0f;
+            v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = s; v[4] = hi.x; v[5] = hi.y; v[6] = hi.z;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float o = __shfl_xor_sync(0xffffffffu, v[k], off);
+            v[k] = (k < 3) ? fminf(v[k], o) : fmaxf(v[k], o);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 8; ++k) s_r[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < CUT_ROW / 32; ++w)
+            for (int k = 0; k < 8; ++k) v[k] = (k < 3) ? fminf(v[k], s_r[w][k]) : fmaxf(v[k], s_r[w][k]);
+        rb[2 * blockIdx.x] = make_float4(v[0], v[1], v[2], v[3]);
+        rb[2 * blockIdx.x + 1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+}
+
+int64_t cut_row_count(int64_t n) { return (n + CUT_ROW - 1) / CUT_ROW; }
+
+cudaError_t launch_cut_row_bounds(const float4* rec, int64_t n, float4* rb, cudaStream_t s) {
+    const int64_t rows = cut_row_count(n);
+    if (rows <= 0) return cudaSuccess;
+    if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;
+    cut_row_bounds_kernel<<<(unsigned)rows, CUT_ROW, 0, s>>>(rec, n, rb);
+    return cudaGetLastError();
+}
 
 __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* __restrict__ rec, int64_t n,
+                                                               const float4* __restrict__ rb,
                                                                const h3dgs_camera raw, int64_t capacity,
                                                                int32_t* __restrict__ cut_ids, float* __restrict__ cut_t,
                                                                int64_t* __restrict__ cut_offsets,
                                                                int64_t* __restrict__ cam_totals,
-                                                               uint32_t* __restrict__ flags, Lookback lb) {
+                                                               uint32_t* __restrict__ flags,
+                                                               uint32_t* __restrict__ skipped, Lookback lb) {
     __shared__ uint32_t s_ticket;
     __shared__ unsigned long long s_slot, s_warp[CUT_BLOCK / 32];
     __shared__ uint32_t s_cnt[CS_IPT][CUT_BLOCK / 32];
@@ -243,41 +303,63 @@ __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* 
     cam.f = fmaxf(raw.fx, raw.fy);
     cam.tau = raw.tau;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // CS_GRP nodes at a time: their records are all requested, then their parents' records, so a
-    // thread keeps 2 CS_GRP loads in flight instead of one dependent pair
-#pragma unroll
-    for (int g = 0; g < CS_IPT; g += CS_GRP) {
-        float4 lo[CS_GRP], hi[CS_GRP], plo[CS_GRP], phi[CS_GRP];
-#pragma unroll
-        for (int k = 0; k < CS_GRP; ++k) {
-            const int64_t v = base + (g + k) * CUT_BLOCK + threadIdx.x;
-            lo[k] = v < n ? __ldg(rec + 2 * v) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-            hi[k] = v < n ? __ldg(rec + 2 * v + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    // rows of this tile whose bound test shows they hold no cut node (one bit per step, uniform)
+    __shared__ uint32_t s_skip;
+    if (warp == 0) {
+        bool sk = false;
+        const int64_t row = (int64_t)b * CS_IPT + lane;
+        if (rb && lane < CS_IPT && base + (int64_t)lane * CUT_ROW < n) {
+            const float4 u0 = __ldg(rb + 2 * row), u1 = __ldg(rb + 2 * row + 1);
+            const float dx = fmaxf(fmaxf(u0.x - cam.c[0], cam.c[0] - u1.x), 0.0f);
+            const float dy = fmaxf(fmaxf(u0.y - cam.c[1], cam.c[1] - u1.y), 0.0f);
+            const float dz = fmaxf(fmaxf(u0.z - cam.c[2], cam.c[2] - u1.z), 0.0f);
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            sk = u1.w == 0.0f && d2 > 0.0f && cam.f * u0.w < cam.tau * (1.0f - 1e-4f) * sqrtf(d2);
+            if (sk && skipped) atomicAdd(skipped, (uint32_t)min((int64_t)CUT_ROW, n - (base + (int64_t)lane * CUT_ROW)));
         }
+        const uint32_t m = __ballot_sync(0xffffffffu, sk);
+        if (lane == 0) s_skip = m;
+    }
+    __syncthreads();
+    const uint32_t skip = s_skip;
+    {
+        // CS_GRP nodes at a time: their records are all requested, then their parents' records, so a
+        // thread keeps 2 CS_GRP loads in flight instead of one dependent pair
 #pragma unroll
-        for (int k = 0; k < CS_GRP; ++k) {
-            const int32_t p = __float_as_int(lo[k].w);
-            const bool pin = p >= 0 && H3DGS_IN(p, n);
-            plo[k] = pin ? __ldg(rec + 2 * (int64_t)p) : lo[k];
-            phi[k] = pin ? __ldg(rec + 2 * (int64_t)p + 1) : hi[k];
-        }
+        for (int g = 0; g < CS_IPT; g += CS_GRP) {
+            float4 lo[CS_GRP], hi[CS_GRP], plo[CS_GRP], phi[CS_GRP];
 #pragma unroll
-        for (int k = 0; k < CS_GRP; ++k) {
-            const int q = g + k;
-            const int64_t v = base + q * CUT_BLOCK + threadIdx.x;
-            const int32_t p = __float_as_int(lo[k].w);
-            bool sel = false;
-            float tw = 0.0f;
-            if (v < n) {
-                float en, ep;
-                sel = cut_test(cam, lo[k], hi[k], plo[k], phi[k], p >= 0, &en, &ep);
-                if (sel && p >= 0) tw = parent_weight(cam.tau, en, ep);
+            for (int k = 0; k < CS_GRP; ++k) {
+                const int64_t v = base + (g + k) * CUT_BLOCK + threadIdx.x;
+                const bool rd = v < n && !((skip >> (g + k)) & 1u);
+                lo[k] = rd ? __ldg(rec + 2 * v) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+                hi[k] = rd ? __ldg(rec + 2 * v + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            const uint32_t word = __ballot_sync(0xffffffffu, sel);
-            s_tw[q][threadIdx.x] = tw;
-            if (lane == 0) {
-                s_cnt[q][warp] = __popc(word);
-                s_word[q][warp] = word;
+#pragma unroll
+            for (int k = 0; k < CS_GRP; ++k) {
+                const int32_t p = __float_as_int(lo[k].w);
+                const bool pin = p >= 0 && H3DGS_IN(p, n);
+                plo[k] = pin ? __ldg(rec + 2 * (int64_t)p) : lo[k];
+                phi[k] = pin ? __ldg(rec + 2 * (int64_t)p + 1) : hi[k];
+            }
+#pragma unroll
+            for (int k = 0; k < CS_GRP; ++k) {
+                const int q = g + k;
+                const int64_t v = base + q * CUT_BLOCK + threadIdx.x;
+                const int32_t p = __float_as_int(lo[k].w);
+                bool sel = false;
+                float tw = 0.0f;
+                if (v < n && !((skip >> q) & 1u)) {
+                    float en, ep;
+                    sel = cut_test(cam, lo[k], hi[k], plo[k], phi[k], p >= 0, &en, &ep);
+                    if (sel && p >= 0) tw = parent_weight(cam.tau, en, ep);
+                }
+                const uint32_t word = __ballot_sync(0xffffffffu, sel);
+                s_tw[q][threadIdx.x] = tw;
+                if (lane == 0) {
+                    s_cnt[q][warp] = __popc(word);
+                    s_word[q][warp] = word;
+                }
             }
         }
     }
@@ -325,8 +407,9 @@ cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const C
         if (e != cudaSuccess) return e;
         // grouped prefix when every block is resident (at most 6 blocks of 256 per SM)
         const Lookback lb = lb_make(w.lb_work, blocks, blocks <= 6 * (int64_t)w.num_sms, flags);
-        cut_single_kernel<<<(unsigned)blocks, CUT_BLOCK, 0, s>>>(h.rec, h.n, w.cam0, capacity, cut_ids, cut_t, cut_offsets,
-                                                                 w.cam_totals, flags, lb);
+        cut_single_kernel<<<(unsigned)blocks, CUT_BLOCK, 0, s>>>(h.rec, h.n, h.row_bound, w.cam0, capacity, cut_ids,
+                                                                 cut_t, cut_offsets, w.cam_totals, flags,
+                                                                 w.skipped_nodes, lb);
         return cudaGetLastError();
     }
     const size_t smem = sizeof(uint32_t) * (size_t)n_cams;

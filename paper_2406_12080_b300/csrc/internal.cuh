@@ -42,7 +42,7 @@ __device__ __forceinline__ bool check_in(int64_t i, int64_t n, int line) {
 }
 #define H3DGS_IN(i, n) ::h3dgs::check_in((int64_t)(i), (int64_t)(n), __LINE__)
 // an invariant that the kernel relies on (recorded like a failed range check)
-#define H3DGS_HOLDS(c) ::h3dgs::check_in((c) ? 0 : -1, 1, __LINE__)
+#define H3DGS_HOLDS(c) ((void)::h3dgs::check_in((c) ? 0 : -1, 1, __LINE__))
 #define H3DGS_CHECK_READER(name)                                                                              \
     cudaError_t name(uint32_t out[2], cudaStream_t s) {                                                         \
         cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_check_word, sizeof(uint32_t) * 2, 0,                  \
@@ -56,7 +56,7 @@ __device__ __forceinline__ bool check_in(int64_t i, int64_t n, int line) {
     }
 #else
 #define H3DGS_IN(i, n) true
-#define H3DGS_HOLDS(c) true
+#define H3DGS_HOLDS(c) ((void)0)
 #define H3DGS_CHECK_READER(name)                                                                              \
     cudaError_t name(uint32_t out[2], cudaStream_t) {                                                           \
         out[0] = out[1] = 0u;                                                                                   \
@@ -116,6 +116,8 @@ struct DevHier {
     const int32_t* parent;
     const int32_t* child_count;
     const float4* rec;     // packed cut records [N][2]: {box_min.xyz, parent}, {box_max.xyz, child_count}
+    const float4* row_bound;  // per row of 256 nodes of the one-camera scan [rows][2]: {parents' union box
+                              // min, their largest side}, {union box max, 1 if the row is never skipped}, or NULL
     const int32_t* row_of; // attribute row of each node (streamed hierarchy: its cache slot, -1 if absent), or
                            // NULL: the node id
 };
@@ -381,6 +383,9 @@ __device__ __forceinline__ int find_cam(const int64_t* __restrict__ offs, int n_
 // ---------------------------------------------------------------- launchers (host side)
 // cut.cu
 cudaError_t launch_pack_records(const h3dgs_hierarchy& h, float4* rec, cudaStream_t s);
+// Per row of 256 nodes of the one-camera scan: the parents' union box and largest side (see cut.cu).
+int64_t cut_row_count(int64_t n);
+cudaError_t launch_cut_row_bounds(const float4* rec, int64_t n, float4* rb, cudaStream_t s);
 cudaError_t launch_camera_setup(const CamBatch& b, const DevOpts* opts, DevCam* cams, cudaStream_t s);
 struct CutWork {
     uint32_t* mask;          // [n_cams][words]
@@ -393,6 +398,7 @@ struct CutWork {
     int64_t lb_words;
     h3dgs_camera cam0;       // single-camera pass: the raw camera (its derived values are computed in the kernel)
     int num_sms = 148;
+    uint32_t* skipped_nodes = nullptr;   // single-camera pass: nodes of the rows skipped by the bound test
 };
 // Look-back words the single-camera cut needs for n nodes.
 size_t cut_single_work_words(int64_t n);

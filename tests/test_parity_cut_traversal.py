@@ -2,7 +2,9 @@
 the records of the cut and its ancestors) against the oracle's cut rule (Sec. 4.2, Eq. t_interp):
 ids and weights bit-exact, on the tiny scene at every tau (leaves only to root only), on K-ary
 compacted trees, and on the 2M-node street corridor; the number of nodes it reads equals the size of
-the cut plus its ancestors, counted here from the oracle's cut."""
+the cut plus its ancestors, counted here from the oracle's cut.  The scan (mode 1) selects the same
+and reads at least those records: it skips only rows of 256 nodes whose nodes all have a parent
+below tau."""
 import numpy as np
 import pytest
 
@@ -54,17 +56,20 @@ def _traverse_and_compare(h, cam, scan_too=True):
     np.testing.assert_array_equal(t.view(np.uint32), ot.view(np.uint32))
     assert offs[0] == 0 and offs[1] == len(oid)
     assert visited == _visited(h, oid)
+    scan_read = None
     if scan_too:
-        assert out[1][3] == h.n
+        scan_read = out[1][3]
+        assert visited <= scan_read <= h.n
         np.testing.assert_array_equal(out[1][0], ids)
-    return oid, visited
+        np.testing.assert_array_equal(out[1][1].view(np.uint32), t.view(np.uint32))
+    return oid, visited, scan_read
 
 
 @pytest.mark.parametrize("tau", [0.0, 2.0, 6.0, 15.0, 80.0, float("inf")])
 def test_tiny_scene(tau):
     sc, h = scenes.tiny()
     gpu_path.upload(h)
-    oid, visited = _traverse_and_compare(h, synth.with_tau(sc.cameras[0], tau))
+    oid, visited, _ = _traverse_and_compare(h, synth.with_tau(sc.cameras[0], tau))
     if tau == float("inf"):
         assert list(oid) == [0] and visited == 1
 
@@ -92,5 +97,23 @@ def test_compacted_k_ary_tree(tau):
 def test_street_corridor_full_size(tau):
     sc, h = scenes.corridor()
     gpu_path.upload(h)
-    oid, visited = _traverse_and_compare(h, synth.with_tau(sc.cameras[0], tau))
+    oid, visited, _ = _traverse_and_compare(h, synth.with_tau(sc.cameras[0], tau))
     assert visited == 2 * len(oid) - 1   # binary tree: the cut's ancestors are one fewer than the cut
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("tau,max_read", [(3.0, 1.0), (6.0, 0.4), (15.0, 0.1)])
+def test_scan_skips_rows_below_the_cut(tau, max_read):
+    """From high above the street most rows of the deep levels have every parent below tau: the scan
+    skips them unread (a bound of their parents' granularity from the union box and the largest side)
+    and still selects the oracle's cut and weights bit for bit.  (A row holding any child of an
+    expanded node is read; at tau = 3 nearly every row holds one.)"""
+    sc, h = scenes.corridor()
+    gpu_path.upload(h)
+    lo, hi = h.box_min[0].astype(np.float64), h.box_max[0].astype(np.float64)
+    centre = 0.5 * (lo + hi)
+    pos = centre + np.array([0.0, 0.0, 0.6 * float(np.max(hi - lo))])
+    cam = synth.look_camera(pos, [0.05, 0.0, -1.0], [1.0, 0.0, 0.0], 1920, 1080, 60.0, tau)
+    oid, visited, scan_read = _traverse_and_compare(h, cam)
+    assert len(oid) > 1000
+    assert scan_read <= max_read * h.n
