@@ -217,10 +217,11 @@ __global__ void __launch_bounds__(CUT_BLOCK) cut_write_kernel(const float4* __re
 }
 
 // One camera: a single pass with decoupled look-back.  Block b (ticket order) tests nodes
-// [b CS_TILE, (b + 1) CS_TILE), CS_IPT per thread at stride CUT_BLOCK (coalesced), counts the
+// [b T, (b + 1) T) (T = IPT CUT_BLOCK), IPT per thread at stride CUT_BLOCK (coalesced), counts the
 // selected ones per (step, warp), obtains the count of all earlier blocks and writes its ids in
 // ascending order with their weights.  The last block writes the offsets and the total.
 constexpr int CS_IPT = 10;   // with at most 6 blocks of 256 per SM a 2M-node scan is one wave (8..16 measured, 10 fastest)
+constexpr int CS_IPT_LARGE = 20;   // nodes per thread when the scan takes several waves (fewer, longer blocks)
 constexpr int CS_GRP = 2;   // nodes whose loads are in flight together (2 measured fastest of 1, 2, 4, 8)
 constexpr int CS_TILE = CUT_BLOCK * CS_IPT;
 //
@@ -282,6 +283,7 @@ cudaError_t launch_cut_row_bounds(const float4* rec, int64_t n, float4* rb, cuda
     return cudaGetLastError();
 }
 
+template <int IPT>
 __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* __restrict__ rec, int64_t n,
                                                                const float4* __restrict__ rb,
                                                                const h3dgs_camera raw, int64_t capacity,
@@ -292,11 +294,11 @@ __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* 
                                                                uint32_t* __restrict__ skipped, Lookback lb) {
     __shared__ uint32_t s_ticket;
     __shared__ unsigned long long s_slot, s_warp[CUT_BLOCK / 32];
-    __shared__ uint32_t s_cnt[CS_IPT][CUT_BLOCK / 32];
-    __shared__ uint32_t s_word[CS_IPT][CUT_BLOCK / 32];   // per (step, warp): ballot of the selected nodes
-    __shared__ float s_tw[CS_IPT][CUT_BLOCK];             // per (step, thread): the node's parent weight
+    __shared__ uint32_t s_cnt[IPT][CUT_BLOCK / 32];
+    __shared__ uint32_t s_word[IPT][CUT_BLOCK / 32];   // per (step, warp): ballot of the selected nodes
+    __shared__ float s_tw[IPT][CUT_BLOCK];             // per (step, thread): the node's parent weight
     const uint32_t b = lb_ticket(lb, &s_ticket);
-    const int64_t base = (int64_t)b * CS_TILE;
+    const int64_t base = (int64_t)b * (CUT_BLOCK * IPT);
     if (base >= n) return;
     DevCam cam;   // only the centre, f and tau are used; derived as the set-up kernel does
     camera_centre(raw, cam.c);
@@ -307,8 +309,8 @@ __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* 
     __shared__ uint32_t s_skip;
     if (warp == 0) {
         bool sk = false;
-        const int64_t row = (int64_t)b * CS_IPT + lane;
-        if (rb && lane < CS_IPT && base + (int64_t)lane * CUT_ROW < n) {
+        const int64_t row = (int64_t)b * IPT + lane;
+        if (rb && lane < IPT && base + (int64_t)lane * CUT_ROW < n) {
             const float4 u0 = __ldg(rb + 2 * row), u1 = __ldg(rb + 2 * row + 1);
             const float dx = fmaxf(fmaxf(u0.x - cam.c[0], cam.c[0] - u1.x), 0.0f);
             const float dy = fmaxf(fmaxf(u0.y - cam.c[1], cam.c[1] - u1.y), 0.0f);
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* 
         // CS_GRP nodes at a time: their records are all requested, then their parents' records, so a
         // thread keeps 2 CS_GRP loads in flight instead of one dependent pair
 #pragma unroll
-        for (int g = 0; g < CS_IPT; g += CS_GRP) {
+        for (int g = 0; g < IPT; g += CS_GRP) {
             float4 lo[CS_GRP], hi[CS_GRP], plo[CS_GRP], phi[CS_GRP];
 #pragma unroll
             for (int k = 0; k < CS_GRP; ++k) {
@@ -366,14 +368,14 @@ __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* 
     __syncthreads();
     // exclusive scan of the (step, warp) counts in step-major order = ascending node order
     unsigned long long mine = 0;
-    if (threadIdx.x < CS_IPT * (CUT_BLOCK / 32)) mine = (&s_cnt[0][0])[threadIdx.x];
+    if (threadIdx.x < IPT * (CUT_BLOCK / 32)) mine = (&s_cnt[0][0])[threadIdx.x];
     unsigned long long agg;
     const unsigned long long ex = lb_block_scan<CUT_BLOCK>(mine, s_warp, &agg);
-    if (threadIdx.x < CS_IPT * (CUT_BLOCK / 32)) (&s_cnt[0][0])[threadIdx.x] = (uint32_t)ex;
+    if (threadIdx.x < IPT * (CUT_BLOCK / 32)) (&s_cnt[0][0])[threadIdx.x] = (uint32_t)ex;
     const unsigned long long prefix = lb_prefix(lb, b, agg, &s_slot);   // ends with a barrier
     const uint32_t lmask = (1u << lane) - 1u;
 #pragma unroll
-    for (int q = 0; q < CS_IPT; ++q) {
+    for (int q = 0; q < IPT; ++q) {
         const uint32_t word = s_word[q][warp];
         if ((word >> lane) & 1u) {
             const int64_t pos = (int64_t)(prefix + s_cnt[q][warp]) + __popc(word & lmask);
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* 
             }
         }
     }
-    if (base + CS_TILE >= n && threadIdx.x == 0) {   // the last block: offsets and total
+    if (base + (CUT_BLOCK * IPT) >= n && threadIdx.x == 0) {   // the last block: offsets and total
         const int64_t total = (int64_t)(prefix + agg);
         cam_totals[0] = 0;
         cam_totals[1] = total;
@@ -400,16 +402,24 @@ size_t cut_single_work_words(int64_t n) {
 cudaError_t launch_cut(const DevHier& h, const DevCam* cams, int n_cams, const CutWork& w, int32_t* cut_ids,
                        float* cut_t, int64_t* cut_offsets, int64_t capacity, uint32_t* flags, cudaStream_t s) {
     if (n_cams == 1 && w.lb_work) {
-        const int64_t blocks = (h.n + CS_TILE - 1) / CS_TILE;
+        // one wave of small tiles where they all fit (at most 6 blocks of 256 per SM), else longer tiles
+        const bool large = (h.n + CS_TILE - 1) / CS_TILE > 6 * (int64_t)w.num_sms;
+        const int64_t tile = (int64_t)CUT_BLOCK * (large ? CS_IPT_LARGE : CS_IPT);
+        const int64_t blocks = (h.n + tile - 1) / tile;
         const size_t words = LB_HEADER_WORDS + lb_body_words(blocks);
         if ((int64_t)words > w.lb_words) return cudaErrorInvalidValue;
         cudaError_t e = cudaMemsetAsync(w.lb_work, 0, sizeof(uint32_t) * words, s);
         if (e != cudaSuccess) return e;
         // grouped prefix when every block is resident (at most 6 blocks of 256 per SM)
         const Lookback lb = lb_make(w.lb_work, blocks, blocks <= 6 * (int64_t)w.num_sms, flags);
-        cut_single_kernel<<<(unsigned)blocks, CUT_BLOCK, 0, s>>>(h.rec, h.n, h.row_bound, w.cam0, capacity, cut_ids,
-                                                                 cut_t, cut_offsets, w.cam_totals, flags,
-                                                                 w.skipped_nodes, lb);
+        if (large)
+            cut_single_kernel<CS_IPT_LARGE><<<(unsigned)blocks, CUT_BLOCK, 0, s>>>(
+                h.rec, h.n, h.row_bound, w.cam0, capacity, cut_ids, cut_t, cut_offsets, w.cam_totals, flags,
+                w.skipped_nodes, lb);
+        else
+            cut_single_kernel<CS_IPT><<<(unsigned)blocks, CUT_BLOCK, 0, s>>>(
+                h.rec, h.n, h.row_bound, w.cam0, capacity, cut_ids, cut_t, cut_offsets, w.cam_totals, flags,
+                w.skipped_nodes, lb);
         return cudaGetLastError();
     }
     const size_t smem = sizeof(uint32_t) * (size_t)n_cams;
