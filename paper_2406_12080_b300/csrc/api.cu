@@ -70,7 +70,7 @@ struct h3dgs_ctx {
     DBuf sortw, seg_start, hists;   // hists: [2][4][256] digit histograms of the depth and tile keys
     DBuf fw;                        // fixed-capacity frame workspace (all cleared by one launch per render)
     DBuf T_final, n_contrib, splat_grad;
-    DBuf items, q_prod, q_single, q_cons, queue_sync, tile_item0, tile_nch, tile_split, sc_Tc, sc_C, sc_Tend, sc_last, sc_D;
+    DBuf items, q_prod, q_single, q_cons, queue_sync, tile_item0, tile_nch, sc_Tc, sc_C, sc_Tend, sc_last, sc_D;
     DBuf exposure;   // copy of the last render's exposure affines [n_cams][12]
     // streamed hierarchy (attributes in host memory, a device cache of rows)
     bool streamed = false;
@@ -238,7 +238,6 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images, float* de
     a.queue_sync = P<uint32_t>(ctx->queue_sync);
     a.tile_item0 = P<int32_t>(ctx->tile_item0);
     a.tile_nch = P<int32_t>(ctx->tile_nch);
-    a.tile_split = P<int32_t>(ctx->tile_split);
     a.num_sms = ctx->num_sms;
     a.n_items = P<uint32_t>(ctx->counters) + C_NITEMS;
     a.scratch_Tc = P<float>(ctx->sc_Tc);
@@ -324,7 +323,7 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
                     &ctx->s_key3, &ctx->s_tiles, &ctx->s_poff, &ctx->pk0, &ctx->pv0, &ctx->pk1, &ctx->pv1,
                     &ctx->ranges, &ctx->sortw, &ctx->seg_start, &ctx->hists, &ctx->fw, &ctx->T_final, &ctx->n_contrib, &ctx->splat_grad,
                     &ctx->items, &ctx->q_prod, &ctx->q_single, &ctx->q_cons, &ctx->queue_sync,
-                    &ctx->tile_item0, &ctx->tile_nch, &ctx->tile_split, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
+                    &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
                     &ctx->sc_last, &ctx->sc_D, &ctx->exposure, &ctx->st_mean, &ctx->st_scale, &ctx->st_rot,
                     &ctx->st_opacity, &ctx->st_sh, &ctx->st_slot_of, &ctx->st_node_of, &ctx->st_stamp,
                     &ctx->st_free, &ctx->st_missing, &ctx->st_count};
@@ -786,7 +785,7 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
         auto r64 = [](size_t w) { return (w + 63) / 64 * 64; };
         const size_t wd = r64(radix_work_words(capM)), wt = r64(radix_work_words(capP));
         const size_t wpo = r64(pair_offsets_work_words(capM)), wpl = r64(blend_plan_work_words(ctx->n_tiles));
-        const size_t wq = r64((size_t)ctx->n_tiles + 1), wh = 2 * 4 * 256;
+        const size_t wq = r64(2 * (size_t)ctx->n_tiles + 1), wh = 2 * 4 * 256;
         const size_t total = wd + wt + wpo + wpl + wq + wh;
         CK(ensure(ctx->fw, sizeof(uint32_t) * total), "frame workspace");
         uint32_t* base = P<uint32_t>(ctx->fw);
@@ -894,10 +893,9 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
         CK(ensure(ctx->q_prod, sizeof(uint32_t) * (size_t)icap), "blend queue");
         CK(ensure(ctx->q_cons, sizeof(uint32_t) * (size_t)icap), "blend queue");
         CK(ensure(ctx->q_single, sizeof(uint32_t) * (size_t)ctx->n_tiles), "blend queue");
-        CK(ensure(ctx->queue_sync, sizeof(uint32_t) * (size_t)(ctx->n_tiles + 1)), "blend queue");
+        CK(ensure(ctx->queue_sync, sizeof(uint32_t) * (size_t)(2 * ctx->n_tiles + 1)), "blend queue");
         CK(ensure(ctx->tile_item0, sizeof(int32_t) * (size_t)ctx->n_tiles), "blend items");
         CK(ensure(ctx->tile_nch, sizeof(int32_t) * (size_t)ctx->n_tiles), "blend items");
-        CK(ensure(ctx->tile_split, sizeof(int32_t) * (size_t)ctx->n_tiles), "blend items");
         CK(ensure(ctx->sc_Tc, sizeof(float) * (size_t)icap * NT), "blend scratch");
         CK(ensure(ctx->sc_C, 3 * sizeof(float) * (size_t)icap * NT), "blend scratch");
         CK(ensure(ctx->sc_Tend, sizeof(float) * (size_t)icap * NT), "blend scratch");

@@ -23,8 +23,9 @@
 //             end transmittance and depth are the local ones times T_in, so the consumer takes those
 //             instead of walking.  Single-chunk tiles write the pixel directly, chunks of split tiles
 //             write (colour, T at the end, last contributor) to the scratch kept for the adjoint;
-//   combine   per pixel of a split tile: colour = sum of its chunks, T_final and the last
-//             contributor from the chunk where the walk stopped.
+//   combine   by the consumer of each split tile's last chunk, after a bounded wait on the tile's other
+//             consumers (all taken before it): per pixel, colour = sum of the chunks, T_final and the
+//             last contributor from the chunk where the walk stopped.
 // A chunk whose T_in is already below t_min adds nothing (the walk stopped in an earlier chunk).
 //
 // Optional outputs (appendix, depth regularisation and exposure optimisation): the expected depth
@@ -113,7 +114,7 @@ __device__ __forceinline__ TileGeom2<TW, TH> tile_geom2(const DevCam* __restrict
 // ------------------------------------------------------------------------------------ plan
 
 // The plan: chunk counts per tile, their exclusive scan (single pass, decoupled look-back), the full
-// (tile, chunk) item list (used by the combine and the adjoint) and the work queue of the blend:
+// (tile, chunk) item list (used by the blend and the adjoint) and the work queue of the blend:
 //   producers  chunks 0 .. nch - 2 of split tiles, blended from T = 1; each hands on its (1 - alpha)
 //              product;
 //   singles    tiles of one chunk;
@@ -131,7 +132,6 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __re
                                                                 uint32_t* __restrict__ q_prod,
                                                                 uint32_t* __restrict__ q_single,
                                                                 uint32_t* __restrict__ q_cons,
-                                                                int32_t* __restrict__ tile_split,
                                                                 uint32_t* __restrict__ counts /* items, X, Y, Z */,
                                                                 Lookback lb) {
     griddep_launch_dependents();
@@ -166,7 +166,6 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __re
             const int64_t offF = t + offX;
             tile_item0[t] = (int32_t)offF;
             tile_nch[t] = n;
-            if (n > 1) tile_split[t - offY] = (int32_t)t;   // offY singles before t
             for (int c = 0; c < n; ++c) {
                 const int64_t it = offF + c;
                 if (it >= item_cap) break;
@@ -358,6 +357,7 @@ __global__ void __launch_bounds__(TW * TH / 2, 12) blend_queue_kernel(const DevC
                                                                   const int32_t* __restrict__ tile_nch, Scratch sc,
                                                                   uint32_t* __restrict__ ticket,
                                                                   uint32_t* __restrict__ tile_done,
+                                                                  uint32_t* __restrict__ cons_done,
                                                                   float* __restrict__ images,
                                                                   float* __restrict__ depth,
                                                                   const float* __restrict__ exposure,
@@ -507,6 +507,56 @@ __global__ void __launch_bounds__(TW * TH / 2, 12) blend_queue_kernel(const DevC
             sc.D[s0] = Dp.x;
             sc.D[s1] = Dp.y;
         }
+        if (it.y + 1 < nch) {   // a middle chunk: counted as finished for the tile's last chunk
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(cons_done + tile, 1u);
+            return;
+        }
+        // the tile's last chunk combines: its other consumers were all taken before it, so the bounded
+        // wait ends; per pixel the colour is the sum of the chunks in chunk order, T_final and the last
+        // contributor come from the last chunk whose walk ran (a chunk with T_in below t_min did not)
+        if (threadIdx.x == 0) wait_geq(cons_done + tile, (uint32_t)(nch - 2), QUEUE_SPIN_LIMIT, flags);
+        __syncthreads();
+        const DevCam& cam = *g.cam;
+        const int64_t plane = (int64_t)cam.width * cam.height;
+        const float* E = exposure ? exposure + 12 * (g.cam - cams) : nullptr;
+        const int64_t i0 = tile_item0[tile];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (!(k ? g.in1 : g.in0)) continue;
+            const int slot = k ? g.slot1 : g.slot0;
+            const int py = k ? g.py_i1 : g.py_i0;
+            float c0s = 0.0f, c1s = 0.0f, c2s = 0.0f, Ds = 0.0f, Tt = 1.0f, Tin = 1.0f;
+            int lst = 0;
+#pragma unroll 8
+            for (int c = 0; c < nch; ++c) {
+                const int64_t sl = (i0 + c) * NT + slot;
+                const float c0 = __ldcg(sc.C + 3 * sl + 0), c1 = __ldcg(sc.C + 3 * sl + 1), c2 = __ldcg(sc.C + 3 * sl + 2);
+                const float te = __ldcg(sc.Tend + sl), tc = __ldcg(sc.Tc + sl);   // Tc of the last chunk is not used
+                const bool run = !(Tin < o.t_min);
+                c0s += run ? c0 : 0.0f;
+                c1s += run ? c1 : 0.0f;
+                c2s += run ? c2 : 0.0f;
+                Tt = run ? te : Tt;
+                if (DEPTH) {
+                    const float dd = __ldcg(sc.D + sl);
+                    Ds += run ? dd : 0.0f;
+                }
+                if (SAVE) {
+                    const int32_t l = __ldcg(sc.last + sl);
+                    if (run && l >= 0) lst = l;
+                }
+                if (c + 1 < nch) Tin = fmul(Tin, tc);
+            }
+            const int64_t pix = cam.pix_base + (int64_t)py * cam.width + g.px_i;
+            write_pixel(images + 3 * cam.pix_base + (int64_t)py * cam.width + g.px_i, plane, Tt, c0s, c1s, c2s, o, E);
+            if (DEPTH) depth[pix] = Ds;
+            if (SAVE) {
+                T_final[pix] = Tt;
+                n_contrib[pix] = lst;
+            }
+        }
         return;
     }
     const DevCam& cam = *g.cam;
@@ -532,72 +582,6 @@ __global__ void __launch_bounds__(TW * TH / 2, 12) blend_queue_kernel(const DevC
     }
 }
 
-// Split tiles: per pixel, sum the chunks' colours; T_final and the last contributor come from the
-// last chunk whose walk ran (a chunk with T_in below t_min did not run).  One wave of blocks walks
-// the plan's list of split tiles (counts[3] of them), one pixel per thread.
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) blend_combine_kernel(const DevCam* __restrict__ cams, int n_cams, DevOpts o,
-                                                                const uint32_t* __restrict__ counts,
-                                                                const int32_t* __restrict__ tile_split,
-                                                                const int32_t* __restrict__ tile_item0,
-                                                                const int32_t* __restrict__ tile_nch, Scratch sc,
-                                                                float* __restrict__ images, float* __restrict__ depth,
-                                                                const float* __restrict__ exposure,
-                                                                float* __restrict__ T_final,
-                                                                int32_t* __restrict__ n_contrib) {
-    griddep_launch_dependents();
-    griddep_wait();
-    constexpr int NT = TW * TH;
-    const uint32_t Z = counts[3];
-    for (uint32_t z = blockIdx.x; z < Z; z += gridDim.x) {
-        const int64_t tile = tile_split[z];
-        const int nch = tile_nch[tile];
-        // one pixel per thread, row-major in the tile (the scratch's pixel order)
-        int lo = 0, hi = n_cams - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (cams[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
-        }
-        const DevCam& cam = cams[lo];
-        const int local = (int)(tile - cam.tile_base);
-        const int px_i = (local % cam.tiles_x) * TW + (int)threadIdx.x % TW;
-        const int py_i = (local / cam.tiles_x) * TH + (int)threadIdx.x / TW;
-        if (px_i >= cam.width || py_i >= cam.height) continue;
-        const int64_t i0 = tile_item0[tile];
-        float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f, T = 1.0f, Tin = 1.0f;
-        int last = 0;
-        // every chunk's scratch is read whether or not it is used, so the loads of successive chunks
-        // do not wait on each other through the running transmittance
-#pragma unroll 8
-        for (int c = 0; c < nch; ++c) {
-            const int64_t slot = (i0 + c) * NT + threadIdx.x;
-            const float c0 = sc.C[3 * slot + 0], c1 = sc.C[3 * slot + 1], c2 = sc.C[3 * slot + 2];
-            const float te = sc.Tend[slot], tc = sc.Tc[slot];   // Tc of the last chunk is not used
-            const bool run = !(Tin < o.t_min);
-            C0 += run ? c0 : 0.0f;
-            C1 += run ? c1 : 0.0f;
-            C2 += run ? c2 : 0.0f;
-            T = run ? te : T;
-            if (depth) {
-                const float dd = sc.D[slot];
-                D += run ? dd : 0.0f;
-            }
-            if (n_contrib) {
-                const int32_t l = sc.last[slot];
-                if (run && l >= 0) last = l;
-            }
-            if (c + 1 < nch) Tin = fmul(Tin, tc);
-        }
-        const int64_t pix = cam.pix_base + (int64_t)py_i * cam.width + px_i;
-        const int64_t plane = (int64_t)cam.width * cam.height;
-        write_pixel(images + 3 * cam.pix_base + (int64_t)py_i * cam.width + px_i, plane, T, C0, C1, C2, o,
-                    exposure ? exposure + 12 * lo : nullptr);
-        if (depth) depth[pix] = D;
-        if (T_final) T_final[pix] = T;
-        if (n_contrib) n_contrib[pix] = last;
-    }
-}
-
 __global__ void wait_probe_kernel(const uint32_t* word, int polls, uint32_t* flags) {
     if (threadIdx.x == 0) wait_geq(word, 1u, polls, flags);
 }
@@ -620,21 +604,20 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     Lookback lb{reinterpret_cast<unsigned long long*>(a.work + LB_HEADER_WORDS), a.work, a.flags};
     e = launch_dependent(blend_plan_kernel, dim3((unsigned)pblocks), dim3(PL_THREADS), s, a.ranges, a.n_tiles, a.chunk,
-                         a.tile_item0, a.tile_nch, a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons, a.tile_split,
+                         a.tile_item0, a.tile_nch, a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons,
                          a.n_items, lb);
     if (e != cudaSuccess) return e;
     Scratch sc{a.scratch_Tc, a.scratch_C, a.scratch_Tend, a.scratch_last, a.scratch_D};
-    if (!a.pre_zeroed) e = cudaMemsetAsync(a.queue_sync, 0, sizeof(uint32_t) * (size_t)(a.n_tiles + 1), s);
+    if (!a.pre_zeroed) e = cudaMemsetAsync(a.queue_sync, 0, sizeof(uint32_t) * (size_t)(2 * a.n_tiles + 1), s);
     if (e != cudaSuccess) return e;
     // queue length 2 X + Y <= 2 item_cap - n_tiles
     const unsigned gq = (unsigned)std::max<int64_t>(1, 2 * a.item_cap - a.n_tiles);
-    // combine: one wave of blocks (a few per SM) over the split tiles
-    const unsigned tg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.n_tiles, 8 * (int64_t)a.num_sms));
 #define QUEUE(TWV, THV, CNT, DEP, SAV)                                                                                \
     e = launch_dependent(blend_queue_kernel<TWV, THV, CNT, DEP, SAV>, dim3(gq), dim3(TWV * THV / 2), s,                \
         a.cams, a.n_cams, a.o, a.ranges, a.list, a.splat, a.n_splats, a.items, a.q_prod, a.q_single, a.q_cons,        \
         a.n_items,                                                                                                    \
-        a.tile_item0, a.tile_nch, sc, a.queue_sync, a.queue_sync + 1, a.images, a.depth, a.exposure,                  \
+        a.tile_item0, a.tile_nch, sc, a.queue_sync, a.queue_sync + 1, a.queue_sync + 1 + a.n_tiles, a.images,        \
+        a.depth, a.exposure,                                                                                          \
         a.T_final, a.n_contrib, a.n_evals, a.flags)
 #define BL(TWV, THV)                                                                                                  \
     do {                                                                                                              \
@@ -648,9 +631,6 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
         }                                                                                                             \
         if (e != cudaSuccess) break;                                                                                  \
         if (a.ev_queue) cudaEventRecord(a.ev_queue[1], s);                                                            \
-        e = launch_dependent(blend_combine_kernel<TWV, THV>, dim3(tg), dim3(TWV * THV), s, a.cams, a.n_cams, a.o,     \
-                             a.n_items, a.tile_split, a.tile_item0, a.tile_nch, sc, a.images, a.depth, a.exposure,    \
-                             a.T_final, a.n_contrib);                                                                 \
     } while (0)
     const DevOpts& o = a.o;
     const bool save = a.T_final && a.n_contrib;   // per-pixel state for the adjoint (evaluations are not

@@ -509,7 +509,8 @@ struct BlendArgs {
     uint32_t* q_prod;             // blend queue: producer items (chunks 0 .. nch - 2 of split tiles)
     uint32_t* q_single;           // blend queue: single-chunk tiles
     uint32_t* q_cons;             // blend queue: consumer items (chunks 1 .. nch - 1 of split tiles)
-    uint32_t* queue_sync;         // [1 + n_tiles]: queue ticket, per-tile finished-producer counters
+    uint32_t* queue_sync;         // [1 + 2 n_tiles]: queue ticket, per-tile finished-producer counters, per-tile
+                                  // finished middle-consumer counters
     const float4* splat;
     const uint32_t* n_splats;     // device: splat records written by the preprocess (bounds checks only)
     int chunk;
@@ -517,7 +518,6 @@ struct BlendArgs {
     int2* items;
     int32_t* tile_item0;
     int32_t* tile_nch;
-    int32_t* tile_split;          // [n_tiles]: the split tiles (more than one chunk) in tile order
     uint32_t* n_items;            // [4]: items, producers X, singles Y, split tiles
     float* scratch_Tc;
     float* scratch_C;
