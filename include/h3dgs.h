@@ -144,7 +144,8 @@ typedef enum {
     H3DGS_STAGE_DEPTH_SORT,     /* a5: depth radix sort of the splats                */
     H3DGS_STAGE_DUPLICATE,      /* a5: pair-offset scan and (tile, splat) emission   */
     H3DGS_STAGE_TILE_SORT,      /* a5: stable radix sort of the pairs by tile        */
-    H3DGS_STAGE_RANGES,         /* a6: tile ranges                                   */
+    H3DGS_STAGE_RANGES,         /* a6: tile ranges (marked by the tile sort's last pass:
+                                   0; the stage is kept for the layout of the times) */
     H3DGS_STAGE_BLEND,          /* a7: per-tile blend                                */
     H3DGS_STAGE_BACKWARD_BLEND, /* a8: reverse per-tile blend                        */
     H3DGS_STAGE_BACKWARD_SPLAT, /* a8: projection/interpolation adjoint and scatter  */

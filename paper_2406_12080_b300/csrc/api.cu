@@ -877,14 +877,11 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
     // histograms counted by the duplication; every pair is kept
     CK(radix_sort_pairs(P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), P<uint32_t>(ctx->pk1), P<uint32_t>(ctx->pv1),
                         P<uint32_t>(ctx->pk0), P<uint32_t>(ctx->pv0), cnt + C_NPAIRS_KEPT, capP, tbits, false,
-                        cnt + C_NPAIRS_KEPT, sw_t, &in_a, s, tile_hist, prezero),
+                        cnt + C_NPAIRS_KEPT, sw_t, &in_a, s, tile_hist, prezero,
+                        reinterpret_cast<uint32_t*>(P<int2>(ctx->ranges)), ctx->n_tiles),
        "tile sort");
     stage_end(ctx, H3DGS_STAGE_TILE_SORT);
-    const bool in1 = in_a;
-    const uint32_t* tile_keys = in1 ? P<uint32_t>(ctx->pk1) : P<uint32_t>(ctx->pk0);
-    stage_begin(ctx, H3DGS_STAGE_RANGES);
-    CK(launch_ranges(tile_keys, cnt + C_NPAIRS_KEPT, ctx->n_tiles, P<int2>(ctx->ranges), grid, s), "ranges");
-    stage_end(ctx, H3DGS_STAGE_RANGES);
+    const bool in1 = in_a;   // the tile sort's last pass also marked the tile ranges (decoded by the plan)
     stage_begin(ctx, H3DGS_STAGE_BLEND);
     {
         const int NT = o.tile_w * o.tile_h;

@@ -113,7 +113,7 @@ __device__ __forceinline__ TileGeom2<TW, TH> tile_geom2(const DevCam* __restrict
 
 // ------------------------------------------------------------------------------------ plan
 
-// The plan: chunk counts per tile, their exclusive scan (single pass, decoupled look-back), the full
+// The plan: the tile ranges decoded, chunk counts per tile, their exclusive scan (single pass, decoupled look-back), the full
 // (tile, chunk) item list (used by the blend and the adjoint) and the work queue of the blend:
 //   producers  chunks 0 .. nch - 2 of split tiles, blended from T = 1; each hands on its (1 - alpha)
 //              product;
@@ -125,7 +125,7 @@ constexpr int PL_THREADS = 256;
 constexpr int PL_IPT = 1;   // one tile per thread: 32 blocks at 1080p (4 tiles per thread left 8 blocks)
 constexpr int PL_TILE = PL_THREADS * PL_IPT;
 
-__global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __restrict__ ranges, int64_t n_tiles,
+__global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(int2* __restrict__ ranges, int64_t n_tiles,
                                                                 int chunk, int32_t* __restrict__ tile_item0,
                                                                 int32_t* __restrict__ tile_nch,
                                                                 int2* __restrict__ items, int64_t item_cap,
@@ -148,7 +148,11 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(const int2* __re
         const int64_t t = base + (int64_t)threadIdx.x * PL_IPT + q;
         nch[q] = 0;
         if (t < n_tiles) {
-            const int2 r = ranges[t];
+            // the tile sort leaves {~first, last + 1} ({0, 0} for a tile without pairs): decoded here,
+            // in place, for the blend and the adjoint
+            int2 r = ranges[t];
+            r = r.y == 0 ? make_int2(0, 0) : make_int2(~r.x, r.y);
+            ranges[t] = r;
             const int len = r.y - r.x;
             nch[q] = len <= chunk ? 1 : (len + chunk - 1) / chunk;
             sum += ((unsigned long long)(nch[q] - 1) << 31) | (unsigned long long)(nch[q] == 1);

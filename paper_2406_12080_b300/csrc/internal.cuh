@@ -464,10 +464,14 @@ size_t radix_work_words(int64_t n_cap);
 // counted by the producer of the keys, with *n_kept already holding the number of kept keys; NULL:
 // the sort counts them itself.
 // pre_zeroed: the workspace (radix_work_words(n_cap) words) was cleared by the caller.
+// ranges ([n_ranges][2], zeroed by the caller; NULL: not wanted): for every key value k < n_ranges
+// present, {~first, last + 1} of its positions in the sorted output (the first position bit-inverted,
+// so that an absent key stays {0, 0}; decode with ~).
 cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ka, uint32_t* va, uint32_t* kb,
                              uint32_t* vb, const uint32_t* n_dev, int64_t n_cap, int bits, bool drop_max,
                              uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s,
-                             const uint32_t* hist_pre = nullptr, bool pre_zeroed = false);
+                             const uint32_t* hist_pre = nullptr, bool pre_zeroed = false, uint32_t* ranges = nullptr,
+                             int64_t n_ranges = 0);
 // Zeroes up to 8 regions of 32-bit words in one launch (the per-frame clears of the render).
 struct ResetList {
     int n = 0;
@@ -492,8 +496,6 @@ cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_
                              const uint32_t* seg_start, const uint32_t* n_pairs, int64_t cap_pairs,
                              uint32_t* n_pairs_kept, uint32_t* keys, uint32_t* vals, uint32_t* hist, int hist_passes,
                              uint32_t* flags, cudaStream_t s);
-cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n_tiles, int2* ranges, int grid,
-                          cudaStream_t s);
 
 // blend.cu
 // Everything the chunked blend and its adjoint share.  Items are (tile, chunk) pairs; tiles with at
@@ -504,7 +506,7 @@ struct BlendArgs {
     int n_cams;
     int64_t n_tiles;
     DevOpts o;
-    const int2* ranges;
+    int2* ranges;                 // as the tile sort leaves them ({~first, last + 1}); the plan decodes them
     const uint32_t* list;
     uint32_t* q_prod;             // blend queue: producer items (chunks 0 .. nch - 2 of split tiles)
     uint32_t* q_single;           // blend queue: single-chunk tiles

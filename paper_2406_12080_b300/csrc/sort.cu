@@ -8,7 +8,8 @@
 //   3. every splat writes one (tile id, cut position) pair per covered tile;
 //   4. the pairs are sorted stably by tile id (ceil(log2 tiles) bits, 2 passes at 1080p), which
 //      keeps each tile's entries in depth order;
-//   5. tile ranges are read off the sorted tile ids.
+//   5. tile ranges are marked by the last pass of that sort (the first and last position of each run
+//      of equal tile ids in its staging).
 //
 // The radix sort is an LSD "onesweep" sort with 8-bit digits: one kernel computes the digit
 // histograms of every pass, then one kernel per pass ranks a tile of keys stably in shared memory,
@@ -153,7 +154,9 @@ __global__ void __launch_bounds__(OS_THREADS, 3) radix_onesweep_kernel(const uin
                                                                     uint32_t* __restrict__ gtot,
                                                                     uint32_t* __restrict__ gcnt,
                                                                     uint32_t* __restrict__ ticket,
-                                                                    uint32_t* __restrict__ flags) {
+                                                                    uint32_t* __restrict__ flags,
+                                                                    uint32_t* __restrict__ ranges,
+                                                                    uint32_t n_ranges) {
     __shared__ uint32_t s_wcnt[OS_WARPS][256];
     __shared__ uint32_t s_lstart[256];    // first staging slot of each digit in this tile
     __shared__ uint32_t s_gdst[256];      // global destination of each digit's first key of this tile
@@ -323,6 +326,13 @@ __global__ void __launch_bounds__(OS_THREADS, 3) radix_onesweep_kernel(const uin
         if (H3DGS_IN(dst, n_written) && dst < n_written) {
             kout[dst] = k;
             vout[dst] = s_vals[j];
+            // the last pass of a sort whose keys were already ordered on the lower digits: equal keys
+            // are neighbours in the staging, so the first and last of every run mark the key's range
+            // (first stored inverted, so that zero means untouched; see radix_sort_pairs)
+            if (ranges && k < n_ranges) {
+                if (j == 0 || s_keys[j - 1] != k) atomicMax(ranges + 2 * (size_t)k, ~dst);
+                if (j + 1 == kept || s_keys[j + 1] != k) atomicMax(ranges + 2 * (size_t)k + 1, dst + 1);
+            }
         }
     }
 }
@@ -364,7 +374,7 @@ cudaError_t launch_reset(const ResetList& r, int num_sms, cudaStream_t s) {
 cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* ka, uint32_t* va, uint32_t* kb,
                              uint32_t* vb, const uint32_t* n_dev, int64_t n_cap, int bits, bool drop_max,
                              uint32_t* n_kept, const SortWork& w, bool* result_in_a, cudaStream_t s,
-                             const uint32_t* hist_pre, bool pre_zeroed) {
+                             const uint32_t* hist_pre, bool pre_zeroed, uint32_t* ranges, int64_t n_ranges) {
     *result_in_a = false;
     if (n_cap <= 0) return hist_pre ? cudaSuccess : cudaMemsetAsync(n_kept, 0, sizeof(uint32_t), s);
     if (n_cap > 0xffffffffLL || bits < 1 || bits > 32) return cudaErrorInvalidValue;
@@ -410,7 +420,8 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t*
                              dim3((unsigned)tiles), dim3(OS_THREADS), s, ki, vi, to_a ? ka : kb, to_a ? va : vb,
                              p == 0 ? n_dev : n_kept, n_kept, 8 * p, (p == 0 && drop_max) ? 1 : 0, hist + 256 * p,
                              status + (size_t)p * tiles * 256, grouped ? gtot + (size_t)p * max_groups * 256 : nullptr,
-                             grouped ? gcnt + (size_t)p * max_groups : nullptr, tickets + p, w.flags);
+                             grouped ? gcnt + (size_t)p * max_groups : nullptr, tickets + p, w.flags,
+                             p + 1 == passes ? ranges : nullptr, (uint32_t)std::min<int64_t>(n_ranges, 0xffffffffLL));
         if (e != cudaSuccess) return e;
     }
     *result_in_a = (passes % 2) == 1;
@@ -601,30 +612,6 @@ cudaError_t launch_duplicate(const DevCam* cams, int n_cams, const int64_t* cut_
     return launch_dependent(duplicate_kernel, dim3((unsigned)blocks), dim3(256), s, cams, n_cams, cut_offsets, sb, order,
                             n_order, pair_off, seg_start, n_pairs, cap_pairs, n_pairs_kept, keys, vals, hist,
                             hist_passes, flags);
-}
-
-// ------------------------------------------------------------------------------ ranges
-//
-// ranges[t] = [first, last + 1) of tile id t in the sorted keys (tiles without pairs keep the zero
-// range they were cleared to).
-__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev,
-                              uint32_t n_tiles, int2* __restrict__ ranges) {
-    griddep_launch_dependents();
-    griddep_wait();
-    const uint32_t n = *n_dev;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t k = __ldg(keys + i);
-        if (k >= n_tiles) continue;   // only after a failed sort (flagged)
-        if (i == 0 || __ldg(keys + i - 1) != k) ranges[k].x = (int)i;
-        if (i + 1 == n || __ldg(keys + i + 1) != k) ranges[k].y = (int)(i + 1);
-    }
-}
-
-cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* n_dev, int64_t n_tiles, int2* ranges, int grid,
-                          cudaStream_t s) {
-    const cudaError_t e = launch_dependent(ranges_kernel, dim3(grid), dim3(256), s, keys, n_dev, (uint32_t)n_tiles, ranges);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
 }
 
 H3DGS_CHECK_READER(check_read_sort)
