@@ -57,8 +57,8 @@ BLEND_XU_EVAL, BLEND_XU_INTERP = 1, 2
 #   op list above, counted for contributing pairs only
 ADJ_FLOPS_CONTRIB, ADJ_FLOPS_CONTRIB_INTERP = 74 + BLEND_FLOPS_EVAL, 14 + BLEND_FLOPS_INTERP
 # DRAM bytes (read + write) of one launch of the blend's main kernel at the 1080p corridor frame
-# (16x16 tiles, chunk 384), from an ncu capture of the current kernel; None once the kernel changes
-BLEND_TRAFFIC_BYTES = 29.83e6 + 5.66e6
+# (16x16 tiles, chunk 320), from an ncu capture of the current kernel; None once the kernel changes
+BLEND_TRAFFIC_BYTES = 30.91e6 + 6.05e6
 
 
 def parse():
@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--tau", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--chunk", type=int, default=384, help="blend chunk (list entries per CTA)")
+    ap.add_argument("--chunk", type=int, default=320, help="blend chunk (list entries per CTA)")
     ap.add_argument("--tile", default="16x16", help="screen tile WxH")
     ap.add_argument("--batch-views", type=int, default=32, help="cameras of the batched multi-view section (0: skip)")
     ap.add_argument("--opt-leaves", type=int, default=2_000_000,
@@ -518,7 +518,7 @@ def run_ours(args, rank, world, local):
     achieved = flops / (queue_ms * 1e-3) / 1e12 if queue_ms > 0 else None
     roofline = {"kernel": "blend_queue_kernel<16,16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": (achieved / fp32_peak_tflops) if achieved else None,
-                "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk == 384) else None,
+                "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk == 320) else None,
                 "kernel_ms": queue_ms,
                 "peak_note": "148 SMs x 128 FP32 lanes x 2 (FFMA) x max SM clock from MEASURED_PEAKS.json",
                 "work_note": f"the oracle's op list: {BLEND_FLOPS_EVAL} flops per main-pass (pixel, splat) evaluation "
@@ -805,7 +805,7 @@ def run_optimisation(args, dev, stream):
     return out
 
 
-def run_compaction(args, ctx, hier, stream, reps: int = 3):
+def run_compaction(args, ctx, hier, stream, reps: int = 7):
     """Hierarchy compaction (Sec. 5.2) of the resident hierarchy for training views along the street.
 
     The call is synchronous (one host read per level of the new tree) and allocates its scratch, so
@@ -835,7 +835,7 @@ def run_compaction(args, ctx, hier, stream, reps: int = 3):
             "ms": ms, "nodes_per_s": N / (ms * 1e-3), "view_node_tests_per_s": N * len(views) / (ms * 1e-3),
             "n_in": N, "n_out": int(m), "max_children": int(cc.max().item()),
             "wide_nodes": int((cc > 2).sum().item()),
-            "note": "host clock around the synchronous call (best of 3), including its scratch allocation"}
+            "note": "host clock around the synchronous call (best of 7), including its scratch allocation"}
 
 
 def run_streamed(args, hier, dev, stream, update_every: int = 2, cleanup_every: int = 100, max_age: int = 100):

@@ -100,7 +100,7 @@ typedef struct {
     float bg[3];             /* background colour                                              */
     int32_t blend_chunk;     /* a tile list of L > blend_chunk entries is blended as
                                 ceil(L / blend_chunk) chunks of near-equal length by separate
-                                CTAs (64 .. 65536, default 384); the image does not depend on
+                                CTAs (64 .. 65536, default 320); the image does not depend on
                                 it beyond fp32 reassociation of T                               */
 } h3dgs_render_opts;
 

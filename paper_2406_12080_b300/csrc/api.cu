@@ -205,7 +205,7 @@ DevOpts dev_opts(const h3dgs_render_opts& o) {
     d.tile_w = o.tile_w; d.tile_h = o.tile_h; d.lowpass = o.lowpass; d.alpha_clamp = o.alpha_clamp;
     d.alpha_floor = o.alpha_floor; d.t_min = o.t_min; d.aa_compensate = o.aa_compensate;
     d.interpolate = o.interpolate;
-    d.chunk = o.blend_chunk > 0 ? o.blend_chunk : 384;
+    d.chunk = o.blend_chunk > 0 ? o.blend_chunk : 320;
     for (int i = 0; i < 3; ++i) d.bg[i] = o.bg[i];
     return d;
 }
@@ -348,7 +348,7 @@ void h3dgs_default_opts(h3dgs_render_opts* o) {
     o->aa_compensate = 1;
     o->interpolate = 1;
     o->bg[0] = o->bg[1] = o->bg[2] = 0.0f;
-    o->blend_chunk = 384;
+    o->blend_chunk = 320;
 }
 
 h3dgs_status h3dgs_reserve(h3dgs_ctx* ctx, int64_t max_splats, int64_t max_pairs) {

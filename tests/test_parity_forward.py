@@ -210,7 +210,7 @@ def test_middle_chunk_shortcut_and_counting(which, chunk):
     a, b = runs
     ranges, _ = gpu_path.tile_lists(0, int(b.stats["n_tiles"]))
     lens = ranges[:, 1] - ranges[:, 0]
-    c = chunk or 384
+    c = chunk or 320
     middle = bool(np.any(lens > 2 * c))       # tiles of three or more chunks
     assert middle or chunk != 64
     assert (b.stats["n_evals_tpass"] > 0) == middle
