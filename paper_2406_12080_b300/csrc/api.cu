@@ -141,7 +141,9 @@ h3dgs_status check_cams(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams
 }
 
 // Upload cameras with their tile grids; fills the ctx bookkeeping vectors.
-h3dgs_status setup_cameras(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams, int tile_w, int tile_h) {
+// defer (nullable): a single batch is returned there for a later launch to set up, instead of launched
+h3dgs_status setup_cameras(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_cams, int tile_w, int tile_h,
+                           CamBatch* defer = nullptr) {
     CK(ensure(ctx->cams, sizeof(DevCam) * (size_t)n_cams), "camera buffer");
     ctx->cams_host.assign(cams, cams + n_cams);
     ctx->tile_base.resize(n_cams);
@@ -170,6 +172,10 @@ h3dgs_status setup_cameras(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n_c
             b.tiles_y[i] = ctx->tiles_y[first + i];
             b.tile_base[i] = ctx->tile_base[first + i];
             b.pix_base[i] = ctx->pix_base[first + i];
+        }
+        if (defer && n_cams <= CAM_BATCH) {
+            *defer = b;
+            break;
         }
         CK(launch_camera_setup(b, nullptr, P<DevCam>(ctx->cams), ctx->stream), "camera set-up");
     }
@@ -746,7 +752,10 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
     if ((reinterpret_cast<uintptr_t>(exposure) & 3u) || (reinterpret_cast<uintptr_t>(depth) & 3u))
         return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: misaligned depth or exposure array");
     CK(cudaSetDevice(ctx->device), "set device");
-    st = setup_cameras(ctx, cams, n_cams, opts->tile_w, opts->tile_h);
+    // with fixed capacities the frame's reset launch also sets up a single batch of cameras
+    CamBatch deferred;
+    deferred.count = 0;
+    st = setup_cameras(ctx, cams, n_cams, opts->tile_w, opts->tile_h, ctx->fixed ? &deferred : nullptr);
     if (st != H3DGS_OK) return st;
     if (ctx->n_tiles > 0xffffffffLL) return fail(ctx, H3DGS_ERR_INVALID_ARG, "render: too many tiles");
     cudaStream_t s = ctx->stream;
@@ -805,6 +814,10 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
         rl.p[2] = cnt + C_EVALS;    rl.words[2] = EVAL_WORDS;
         rl.p[3] = P<uint32_t>(ctx->ranges); rl.words[3] = 2 * (uint64_t)ctx->n_tiles;
         rl.p[4] = base;             rl.words[4] = total;
+        if (deferred.count > 0) {
+            rl.cams = P<DevCam>(ctx->cams);
+            rl.cb = deferred;
+        }
         CK(launch_reset(rl, ctx->num_sms, s), "frame reset");
     } else {
         CK(cudaMemsetAsync(cnt + C_FLAGS, 0, sizeof(uint32_t), s), "memset");

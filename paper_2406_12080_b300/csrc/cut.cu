@@ -32,30 +32,10 @@ cudaError_t launch_pack_records(const h3dgs_hierarchy& h, float4* rec, cudaStrea
     return cudaGetLastError();
 }
 
-// Camera set-up: copies the raw cameras and derives, in a fixed fp32 order,
-//   c_j = -(R_0j T_0 + R_1j T_1 + R_2j T_2)  as -fmaf(R_2j, T_2, fmaf(R_1j, T_1, R_0j * T_0)),
-//   f = max(fx, fy),  limx = (0.65 W) / fx,  limy = (0.65 H) / fy.
 __global__ void camera_setup_kernel(CamBatch b, DevCam* __restrict__ out) {
     griddep_launch_dependents();
     griddep_wait();
-    const int i = threadIdx.x;
-    if (i >= b.count) return;
-    const h3dgs_camera& c = b.cam[i];
-    DevCam d;
-    for (int k = 0; k < 9; ++k) d.R[k] = c.R[k];
-    for (int k = 0; k < 3; ++k) d.T[k] = c.T[k];
-    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
-    d.width = c.width; d.height = c.height; d.znear = c.znear; d.tau = c.tau;
-    camera_centre(c, d.c);
-    camera_centre_pair(c, d.ch, d.cl);
-    d.f = fmaxf(c.fx, c.fy);
-    d.limx = fdiv(fmul(0.65f, (float)c.width), c.fx);
-    d.limy = fdiv(fmul(0.65f, (float)c.height), c.fy);
-    d.tiles_x = b.tiles_x[i];
-    d.tiles_y = b.tiles_y[i];
-    d.tile_base = b.tile_base[i];
-    d.pix_base = b.pix_base[i];
-    out[b.first + i] = d;
+    if ((int)threadIdx.x < b.count) setup_camera(b, threadIdx.x, out);
 }
 
 cudaError_t launch_camera_setup(const CamBatch& b, const DevOpts*, DevCam* cams, cudaStream_t s) {

@@ -370,6 +370,28 @@ __device__ __forceinline__ bool wait_geq(const uint32_t* p, uint32_t want, int l
     return false;
 }
 
+// Camera set-up of camera i of a batch: copies the raw camera and derives, in a fixed fp32 order,
+//   c_j = -(R_0j T_0 + R_1j T_1 + R_2j T_2)  as -fmaf(R_2j, T_2, fmaf(R_1j, T_1, R_0j * T_0)),
+//   f = max(fx, fy),  limx = (0.65 W) / fx,  limy = (0.65 H) / fy.
+__device__ __forceinline__ void setup_camera(const CamBatch& b, int i, DevCam* __restrict__ out) {
+    const h3dgs_camera& c = b.cam[i];
+    DevCam d;
+    for (int k = 0; k < 9; ++k) d.R[k] = c.R[k];
+    for (int k = 0; k < 3; ++k) d.T[k] = c.T[k];
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    d.width = c.width; d.height = c.height; d.znear = c.znear; d.tau = c.tau;
+    camera_centre(c, d.c);
+    camera_centre_pair(c, d.ch, d.cl);
+    d.f = fmaxf(c.fx, c.fy);
+    d.limx = fdiv(fmul(0.65f, (float)c.width), c.fx);
+    d.limy = fdiv(fmul(0.65f, (float)c.height), c.fy);
+    d.tiles_x = b.tiles_x[i];
+    d.tiles_y = b.tiles_y[i];
+    d.tile_base = b.tile_base[i];
+    d.pix_base = b.pix_base[i];
+    out[b.first + i] = d;
+}
+
 // Camera index of global entry m given the per-camera offsets (binary search, n_cams small).
 __device__ __forceinline__ int find_cam(const int64_t* __restrict__ offs, int n_cams, int64_t m) {
     int lo = 0, hi = n_cams - 1;
@@ -477,6 +499,8 @@ struct ResetList {
     int n = 0;
     uint32_t* p[8];
     uint64_t words[8];
+    DevCam* cams = nullptr;   // non-NULL: the launch also sets up the cameras of `cb` (one batch)
+    CamBatch cb;
 };
 cudaError_t launch_reset(const ResetList& r, int num_sms, cudaStream_t s);
 size_t pair_offsets_work_words(int64_t n_cap);

@@ -350,6 +350,7 @@ size_t radix_work_words(int64_t n_cap) {
 __global__ void reset_kernel(ResetList r) {
     griddep_launch_dependents();
     griddep_wait();
+    if (r.cams && blockIdx.x == 0 && (int)threadIdx.x < r.cb.count) setup_camera(r.cb, threadIdx.x, r.cams);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     for (int k = 0; k < r.n; ++k) {
         uint32_t* p = r.p[k];
