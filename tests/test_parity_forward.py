@@ -217,3 +217,37 @@ def test_middle_chunk_shortcut_and_counting(which, chunk):
     np.testing.assert_array_equal(a.images[0].view(np.uint32), b.images[0].view(np.uint32))
     np.testing.assert_array_equal(a.T_final.view(np.uint32), b.T_final.view(np.uint32))
     np.testing.assert_array_equal(a.n_contrib, b.n_contrib)
+
+
+@pytest.mark.parametrize("which", ["single", "batch"])
+def test_reserved_capacities_render_the_same_frame(which):
+    """With fixed capacities (h3dgs_reserve) one launch clears the frame's counters and workspaces and
+    sets up the cameras, and the sorts and the plan use pre-zeroed workspaces; the frame must be the one
+    the unreserved path renders, bit for bit (images, per-pixel state, tile lists)."""
+    from paper_2406_12080_b300 import h3dgs
+    sc, h = scenes.tiny()
+    dh = gpu_path.upload(h)
+    base = sc.cameras[0]
+    cams = [synth.with_tau(base, 2.0)] if which == "single" else [
+        synth.with_tau(base, 6.0),
+        synth.look_camera([5, 5, -12.0], [0.1, 0, 1], [0, -1, 0], 200, 150, 60.0, 3.0),
+        synth.look_camera([-8, 5, 5.0], [1, 0, 0.05], [0, -1, 0], 96, 128, 75.0, 15.0)]
+    o = oracle.Opts()
+    a = gpu_path.run(dh, cams, o, chunk=64)
+    tiles = [int(np.prod(oracle.tiles(c, o))) for c in cams]
+    la = [gpu_path.tile_lists(k, n) for k, n in enumerate(tiles)]
+    ctx = gpu_path.context()
+    try:
+        h3dgs.h3dgs_reserve(ctx.ctx, len(a.cut_ids) + 64, 4 * int(a.stats["n_pairs"]) + 1024)
+        b = gpu_path.run(dh, cams, o, chunk=64)
+        lb = [gpu_path.tile_lists(k, n) for k, n in enumerate(tiles)]
+    finally:
+        h3dgs.h3dgs_reserve(ctx.ctx, 0, 0)
+    assert b.stats["device_flags"] == 0
+    for ia, ib in zip(a.images, b.images):
+        np.testing.assert_array_equal(ia.view(np.uint32), ib.view(np.uint32))
+    np.testing.assert_array_equal(a.T_final.view(np.uint32), b.T_final.view(np.uint32))
+    np.testing.assert_array_equal(a.n_contrib, b.n_contrib)
+    for (ra, ia), (rb, ib) in zip(la, lb):
+        np.testing.assert_array_equal(ra, rb)
+        np.testing.assert_array_equal(ia, ib)
