@@ -57,7 +57,8 @@ BLEND_XU_EVAL, BLEND_XU_INTERP = 1, 2
 #   op list above, counted for contributing pairs only
 ADJ_FLOPS_CONTRIB, ADJ_FLOPS_CONTRIB_INTERP = 74 + BLEND_FLOPS_EVAL, 14 + BLEND_FLOPS_INTERP
 # DRAM bytes (read + write) of one launch of the blend's main kernel at the 1080p corridor frame
-# (16x16 tiles, chunk 320), from an ncu capture of the current kernel; None once the kernel changes
+# (16x16 tiles, the automatic chunk: 320 at this frame), from an ncu capture of the current kernel; None once
+# the kernel changes
 BLEND_TRAFFIC_BYTES = 30.91e6 + 6.05e6
 
 
@@ -71,7 +72,7 @@ def parse():
     ap.add_argument("--tau", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--chunk", type=int, default=320, help="blend chunk (list entries per CTA)")
+    ap.add_argument("--chunk", type=int, default=0, help="blend chunk (list entries per CTA; 0: automatic)")
     ap.add_argument("--tile", default="16x16", help="screen tile WxH")
     ap.add_argument("--batch-views", type=int, default=32, help="cameras of the batched multi-view section (0: skip)")
     ap.add_argument("--opt-leaves", type=int, default=2_000_000,
@@ -518,7 +519,7 @@ def run_ours(args, rank, world, local):
     achieved = flops / (queue_ms * 1e-3) / 1e12 if queue_ms > 0 else None
     roofline = {"kernel": "blend_queue_kernel<16,16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": (achieved / fp32_peak_tflops) if achieved else None,
-                "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk == 320) else None,
+                "traffic": BLEND_TRAFFIC_BYTES if (args.tile == "16x16" and args.chunk in (0, 320)) else None,
                 "kernel_ms": queue_ms,
                 "peak_note": "148 SMs x 128 FP32 lanes x 2 (FFMA) x max SM clock from MEASURED_PEAKS.json",
                 "work_note": f"the oracle's op list: {BLEND_FLOPS_EVAL} flops per main-pass (pixel, splat) evaluation "
@@ -959,7 +960,7 @@ def run_city(args, rank, world, local):
         offs = torch.empty(2, dtype=torch.int64, device=dev)
         npix = 3 * poses[0].width * poses[0].height
         images = torch.empty(npix, dtype=torch.float32, device=dev)
-        opts = h3dgs.default_opts()
+        opts = h3dgs.default_opts(blend_chunk=args.chunk)
         # size the fixed workspace from every 8th pose, then time every pose with events
         h3dgs.h3dgs_reserve(ctx.ctx, 0, 0)
         mmax = pmax = 0

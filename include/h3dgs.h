@@ -100,8 +100,10 @@ typedef struct {
     float bg[3];             /* background colour                                              */
     int32_t blend_chunk;     /* a tile list of L > blend_chunk entries is blended as
                                 ceil(L / blend_chunk) chunks of near-equal length by separate
-                                CTAs (64 .. 65536, default 320); the image does not depend on
-                                it beyond fp32 reassociation of T                               */
+                                CTAs (64 .. 65536); 0 (the default): automatic per frame, 320
+                                while the frame's mean list length is at most 450 entries, no
+                                split above; the image does not depend on it beyond fp32
+                                reassociation of T                                              */
 } h3dgs_render_opts;
 
 /* Counters of the most recent h3dgs_render (read with a stream synchronisation). */

@@ -14,7 +14,7 @@ import os
 from . import h3dgs
 
 TILES = ((16, 16), (32, 8), (16, 8), (8, 32))
-CHUNKS = (256, 320, 384, 512, 1024)
+CHUNKS = (256, 320, 384, 512, 1024, 65536)
 CACHE_PATH = os.environ.get("H3DGS_TUNE_CACHE",
                             os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.json"))
 

@@ -211,7 +211,7 @@ DevOpts dev_opts(const h3dgs_render_opts& o) {
     d.tile_w = o.tile_w; d.tile_h = o.tile_h; d.lowpass = o.lowpass; d.alpha_clamp = o.alpha_clamp;
     d.alpha_floor = o.alpha_floor; d.t_min = o.t_min; d.aa_compensate = o.aa_compensate;
     d.interpolate = o.interpolate;
-    d.chunk = o.blend_chunk > 0 ? o.blend_chunk : 320;
+    d.chunk = o.blend_chunk > 0 ? o.blend_chunk : 0;   // 0: automatic (the plan picks it per frame)
     for (int i = 0; i < 3; ++i) d.bg[i] = o.bg[i];
     return d;
 }
@@ -236,6 +236,7 @@ static BlendArgs blend_args(h3dgs_ctx* ctx, int n_cams, float* images, float* de
     a.splat = P<float4>(ctx->s_rec);
     a.n_splats = P<uint32_t>(ctx->counters) + C_NSPLATS;
     a.chunk = ctx->opts.chunk;
+    a.n_pairs = P<uint32_t>(ctx->counters) + C_NPAIRS_KEPT;
     a.item_cap = ctx->item_cap;
     a.items = P<int2>(ctx->items);
     a.q_prod = P<uint32_t>(ctx->q_prod);
@@ -354,7 +355,7 @@ void h3dgs_default_opts(h3dgs_render_opts* o) {
     o->aa_compensate = 1;
     o->interpolate = 1;
     o->bg[0] = o->bg[1] = o->bg[2] = 0.0f;
-    o->blend_chunk = 320;
+    o->blend_chunk = 0;
 }
 
 h3dgs_status h3dgs_reserve(h3dgs_ctx* ctx, int64_t max_splats, int64_t max_pairs) {
@@ -898,7 +899,7 @@ h3dgs_status h3dgs_render_ex(h3dgs_ctx* ctx, const h3dgs_camera* cams, int32_t n
     stage_begin(ctx, H3DGS_STAGE_BLEND);
     {
         const int NT = o.tile_w * o.tile_h;
-        const int64_t icap = ctx->n_tiles + capP / o.chunk + 1;
+        const int64_t icap = ctx->n_tiles + capP / (o.chunk > 0 ? o.chunk : BLEND_AUTO_CHUNK) + 1;
         CK(ensure(ctx->items, sizeof(int2) * (size_t)icap), "blend items");
         CK(ensure(ctx->q_prod, sizeof(uint32_t) * (size_t)icap), "blend queue");
         CK(ensure(ctx->q_cons, sizeof(uint32_t) * (size_t)icap), "blend queue");

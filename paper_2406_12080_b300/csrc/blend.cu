@@ -126,7 +126,8 @@ constexpr int PL_IPT = 1;   // one tile per thread: 32 blocks at 1080p (4 tiles 
 constexpr int PL_TILE = PL_THREADS * PL_IPT;
 
 __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(int2* __restrict__ ranges, int64_t n_tiles,
-                                                                int chunk, int32_t* __restrict__ tile_item0,
+                                                                int chunk, const uint32_t* __restrict__ n_pairs,
+                                                                int32_t* __restrict__ tile_item0,
                                                                 int32_t* __restrict__ tile_nch,
                                                                 int2* __restrict__ items, int64_t item_cap,
                                                                 uint32_t* __restrict__ q_prod,
@@ -138,6 +139,13 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(int2* __restrict
     griddep_wait();
     __shared__ uint32_t s_ticket;
     __shared__ unsigned long long s_slot, s_warp[PL_THREADS / 32];
+    // the automatic chunk: with the split threshold of the frame, longer lists go in chunks of
+    // BLEND_AUTO_CHUNK
+    int split_min = chunk;
+    if (chunk <= 0) {
+        chunk = BLEND_AUTO_CHUNK;
+        split_min = blend_auto_split(*n_pairs, n_tiles);
+    }
     const uint32_t b = lb_ticket(lb, &s_ticket);
     const int64_t base = (int64_t)b * PL_TILE;
     if (base >= n_tiles) return;
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(PL_THREADS) blend_plan_kernel(int2* __restrict
             r = r.y == 0 ? make_int2(0, 0) : make_int2(~r.x, r.y);
             ranges[t] = r;
             const int len = r.y - r.x;
-            nch[q] = len <= chunk ? 1 : (len + chunk - 1) / chunk;
+            nch[q] = len <= split_min ? 1 : (len + chunk - 1) / chunk;
             sum += ((unsigned long long)(nch[q] - 1) << 31) | (unsigned long long)(nch[q] == 1);
         }
     }
@@ -608,7 +616,7 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     Lookback lb{reinterpret_cast<unsigned long long*>(a.work + LB_HEADER_WORDS), a.work, a.flags};
     e = launch_dependent(blend_plan_kernel, dim3((unsigned)pblocks), dim3(PL_THREADS), s, a.ranges, a.n_tiles, a.chunk,
-                         a.tile_item0, a.tile_nch, a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons,
+                         a.n_pairs, a.tile_item0, a.tile_nch, a.items, a.item_cap, a.q_prod, a.q_single, a.q_cons,
                          a.n_items, lb);
     if (e != cudaSuccess) return e;
     Scratch sc{a.scratch_Tc, a.scratch_C, a.scratch_Tend, a.scratch_last, a.scratch_D};

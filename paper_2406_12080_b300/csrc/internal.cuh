@@ -296,6 +296,22 @@ __device__ __forceinline__ uint32_t warp_mask(const float4 a, float cc, const fl
     return m;
 }
 
+// The automatic blend chunk.  Splitting long lists into chunks shortens the critical path of a frame
+// whose long lists are few among many short ones (a street view: lists of thousands of entries near
+// the vanishing point, a mean of 94 to 165 per tile), but costs the producer/consumer hand-over, the
+// scratch and a tail of consumers at the end of the queue, which is all loss when nearly every list
+// is long (the 100M-node city at 1080p: a mean of 1115).  Measured with the split threshold at
+// gamma x (pairs per resident CTA): the corridor is fastest when every list above 320 is split (1080p
+// 0.454 ms, 4K 0.745 ms; 0.497 / 0.842 ms with gamma = 2), the city without any split (render
+// 1.81 ms; 2.41 ms split at 320).  The rule: split at BLEND_AUTO_CHUNK while the frame's mean list
+// length is at most BLEND_AUTO_MEAN_MAX, do not split above it.
+constexpr int BLEND_AUTO_CHUNK = 320;
+constexpr int BLEND_AUTO_MEAN_MAX = 450;
+constexpr int BLEND_NO_SPLIT = 0x7fffffff;
+__host__ __device__ inline int blend_auto_split(uint32_t n_pairs, int64_t n_tiles) {
+    return (int64_t)n_pairs <= (int64_t)BLEND_AUTO_MEAN_MAX * n_tiles ? BLEND_AUTO_CHUNK : BLEND_NO_SPLIT;
+}
+
 // First list entry of chunk c when a tile's list [r.x, r.y) is split into nch chunks of near-equal
 // length (lengths differ by at most one; chunk nch ends at r.y).
 __device__ __forceinline__ int chunk_begin(int2 r, int nch, int c) {
@@ -539,7 +555,8 @@ struct BlendArgs {
                                   // finished middle-consumer counters
     const float4* splat;
     const uint32_t* n_splats;     // device: splat records written by the preprocess (bounds checks only)
-    int chunk;
+    int chunk;                    // list entries per item, or 0: automatic (see blend_auto_chunk)
+    const uint32_t* n_pairs;      // device: the frame's pairs (the automatic chunk)
     int64_t item_cap;
     int2* items;
     int32_t* tile_item0;

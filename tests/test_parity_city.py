@@ -143,6 +143,9 @@ def test_full_size_frame_cut_and_render(pose):
     Tf, nc = h3dgs.h3dgs_debug_pixel_state(ctx.ctx, npix)
     assert np.all((Tf >= 0) & (Tf <= 1)) and np.all(nc >= 0)
     assert st["n_cut"] == len(ids_h) and st["n_visible"] > 0
+    # the automatic blend chunk: a frame whose mean list length is above 450 splits no tile list
+    assert st["n_pairs"] > 450 * st["n_tiles"]
+    assert st["n_items"] == st["n_tiles"]
 
 
 # ---------------------------------------------------------------- 16-chunk neighbourhood of pose 0
@@ -200,7 +203,9 @@ def test_c4_batch_of_32_views_equals_single_views():
     """32 cameras on the city loop, 8 each at 1280x720, 1920x1080, 2560x1440 and 3840x2160 with tau
     cycling over 3, 6, 15, in one cut + render + adjoint: every image equals the camera rendered alone
     bit for bit, and the node gradients equal the sum of the per-camera adjoints (fp32 reductions in
-    another order: the per-element bar of tests/test_parity_backward.py)."""
+    another order: the per-element bar of tests/test_parity_backward.py).  The blend chunk is explicit:
+    the automatic one depends on the frame's total work (the batch would split no list, a single view
+    at 320), and chunked walks reassociate T."""
     import torch
     dh = _city()
     ctx = gpu_path.context()
@@ -218,7 +223,7 @@ def test_c4_batch_of_32_views_equals_single_views():
     assert h3dgs.h3dgs_select_cut(ctx.ctx, cams, ids, t, offs, cap) == sum(sizes)
     npix = [3 * c.width * c.height for c in cams]
     poff = np.concatenate([[0], np.cumsum(npix)])
-    opts = h3dgs.default_opts()
+    opts = h3dgs.default_opts(blend_chunk=320)
     img_b = torch.empty(int(poff[-1]), dtype=torch.float32, device="cuda")
     h3dgs.h3dgs_render(ctx.ctx, cams, ids, t, offs, opts, img_b, 1)
     dl = torch.randn(int(poff[-1]), generator=torch.Generator(device="cuda").manual_seed(5), device="cuda")

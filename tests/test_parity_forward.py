@@ -251,3 +251,17 @@ def test_reserved_capacities_render_the_same_frame(which):
     for (ra, ia), (rb, ib) in zip(la, lb):
         np.testing.assert_array_equal(ra, rb)
         np.testing.assert_array_equal(ia, ib)
+
+
+def test_automatic_chunk_splits_a_light_frame_at_320():
+    """The default (automatic) blend chunk of the 1080p corridor frame (mean list length 165, below 450)
+    is 320: the plan cuts each list of L > 320 entries into ceil(L / 320) chunks."""
+    sc, h = scenes.corridor()
+    dh = gpu_path.upload(h)
+    cam = synth.with_tau(sc.cameras[0], 6.0)
+    g = gpu_path.run(dh, [cam], oracle.Opts())          # default options: the automatic chunk
+    TX, TY = oracle.tiles(cam, oracle.Opts())
+    ranges, _ = gpu_path.tile_lists(0, TX * TY)
+    lens = ranges[:, 1] - ranges[:, 0]
+    want = int(np.sum(np.where(lens <= 320, 1, (lens + 319) // 320)))
+    assert g.stats["n_items"] == want > TX * TY
