@@ -991,6 +991,17 @@ def run_city(args, rank, world, local):
                 pairs.append(int(st["n_pairs"]))
                 scan_read.append(int(st["n_cut_visited"]))
         frame_ms = np.array(cut_ms) + np.array(render_ms)
+        # per-stage device times (profiling events) on every 16th pose, outside the timed loop
+        h3dgs.h3dgs_set_profiling(ctx.ctx, 1)
+        stage_acc, n_st = {}, 0
+        for c, a in list(zip(poses, arrs))[::16]:
+            h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids, tt, offs, N, want_total=False)
+            h3dgs.h3dgs_render(ctx.ctx, [c], ids, tt, offs, opts, images, 0, cam_array=a)
+            for k, v in h3dgs.h3dgs_get_stage_times(ctx.ctx).items():
+                stage_acc[k] = stage_acc.get(k, 0.0) + v
+            n_st += 1
+        h3dgs.h3dgs_set_profiling(ctx.ctx, 0)
+        city_stages = {k: v / n_st for k, v in stage_acc.items() if v > 0}
         # the root-down traversal on the same poses (every 8th): the records it reads and its time
         h3dgs.h3dgs_set_cut_mode(ctx.ctx, 2)
         h3dgs.h3dgs_select_cut(ctx.ctx, [poses[0]], ids, tt, offs, N)   # sizes the traversal's buffers
@@ -1048,6 +1059,7 @@ def run_city(args, rank, world, local):
                       "frame_ms_max": float(frame_ms.max())},
         "gaussians_per_s": float(np.sum(sizes) / (frame_ms.sum() * 1e-3)),
         "stage_bandwidth": {"cut": cut_bw},
+        "stages_ms": city_stages,
         "build": {"host_generation_s": t_gen, "device_build_s": t_build},
         "clocks": clk.summary(),
     }

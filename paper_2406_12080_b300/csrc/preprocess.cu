@@ -130,7 +130,6 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
             sb.rect[m] = make_uint2(0xffffffffu, 0xffffffffu);
             continue;
         }
-        const Interp a = interp_geometry(h, rn, rp, use_p, t);
         // ---- view transform: the node's and the parent's means are transformed separately (compensated)
         // and interpolated in camera space, which equals transforming the interpolated mean but keeps
         // the precision that a lerp of km-scale world coordinates would lose
@@ -151,6 +150,9 @@ __global__ void __launch_bounds__(256) preprocess_kernel(DevHier h, const DevCam
         float u = 0, v = 0, ca = 0, cb = 0, cc = 0, comp = 0, sxx = 0, syy = 0;
         int rx0 = 0, rx1 = -1, ry0 = 0, ry1 = -1;
         if (vis) {
+            // scale and rotation only for entries in front of the near plane (half the surroundings of a
+            // street or city view lie behind the camera)
+            const Interp a = interp_geometry(h, rn, rp, use_p, t);
             const float xz = fdiv(xc[0], z), yz = fdiv(xc[1], z);
             u = ffma(cam.fx, xz, cam.cx);
             v = ffma(cam.fy, yz, cam.cy);
