@@ -52,7 +52,9 @@ __device__ __forceinline__ bool cut_test(const DevCam& cam, const float4 lo, con
     const bool leaf = __float_as_int(hi.w) == 0;
     float ep = __int_as_float(0x7f800000);
     bool parent_ok = true;
-    if (has_parent) {
+    // the parent's granularity only decides nodes that pass their own test (eps(n) < tau or a leaf);
+    // the others are not selected whatever it is (ep_out is then not meaningful and not used)
+    if (has_parent && ((en < cam.tau) || leaf)) {
         ep = granularity(cam, plo.x, plo.y, plo.z, phi.x, phi.y, phi.z);
         parent_ok = ep >= cam.tau;
     }
