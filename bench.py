@@ -961,10 +961,11 @@ def run_city(args, rank, world, local):
         npix = 3 * poses[0].width * poses[0].height
         images = torch.empty(npix, dtype=torch.float32, device=dev)
         opts = h3dgs.default_opts(blend_chunk=args.chunk)
-        # size the fixed workspace from every 8th pose, then time every pose with events
+        # size the fixed workspace from 32 poses spread over the loop (every pose of a short loop), then
+        # time every pose with events
         h3dgs.h3dgs_reserve(ctx.ctx, 0, 0)
         mmax = pmax = 0
-        for c in poses[::8]:
+        for c in poses[::max(1, len(poses) // 32)]:
             mmax = max(mmax, h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids, tt, offs, N))
             h3dgs.h3dgs_render(ctx.ctx, [c], ids, tt, offs, opts, images, 0)
             pmax = max(pmax, h3dgs.h3dgs_get_stats(ctx.ctx)["n_pairs"])
