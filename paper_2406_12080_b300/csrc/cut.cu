@@ -354,6 +354,12 @@ __global__ void __launch_bounds__(CUT_BLOCK, 6) cut_single_kernel(const float4* 
     unsigned long long agg;
     const unsigned long long ex = lb_block_scan<CUT_BLOCK>(mine, s_warp, &agg);
     if (threadIdx.x < IPT * (CUT_BLOCK / 32)) (&s_cnt[0][0])[threadIdx.x] = (uint32_t)ex;
+    // a block with nothing to write publishes its count without waiting for its prefix (the block
+    // holding the last node still waits: it writes the offsets and the total)
+    if (agg == 0 && base + (int64_t)CUT_BLOCK * IPT < n) {
+        lb_publish(lb, b, 0ull);
+        return;
+    }
     const unsigned long long prefix = lb_prefix(lb, b, agg, &s_slot);   // ends with a barrier
     const uint32_t lmask = (1u << lane) - 1u;
 #pragma unroll

@@ -70,6 +70,19 @@ __device__ __forceinline__ uint32_t lb_ticket(const Lookback& lb, uint32_t* s_sl
 
 // Exclusive prefix of block b from its aggregate agg (all threads call it; the result is the same in
 // every thread).  s_slot: one shared 64-bit word.
+// Publishes block b's aggregate without waiting for its prefix (thread 0; for a block that writes
+// nothing).  Later blocks sum it on their way back as they sum any published aggregate.
+__device__ __forceinline__ void lb_publish(const Lookback& lb, uint32_t b, unsigned long long agg) {
+    if (threadIdx.x != 0) return;
+    lb_store(lb.status + b, (b == 0 ? LB_INC : LB_AGG) | agg);
+    if (lb.gsum) {
+        const uint32_t g = b / LB_GROUP;
+        atomicAdd(lb.gsum + g, agg);
+        __threadfence();
+        atomicAdd(lb.gcnt + g, 1u);
+    }
+}
+
 __device__ __forceinline__ unsigned long long lb_prefix(const Lookback& lb, uint32_t b, unsigned long long agg,
                                                         unsigned long long* s_slot) {
     if (threadIdx.x == 0) lb_store(lb.status + b, (b == 0 ? LB_INC : LB_AGG) | agg);
