@@ -333,7 +333,8 @@ h3dgs_status h3dgs_destroy(h3dgs_ctx* ctx) {
                     &ctx->tile_item0, &ctx->tile_nch, &ctx->sc_Tc, &ctx->sc_C, &ctx->sc_Tend,
                     &ctx->sc_last, &ctx->sc_D, &ctx->exposure, &ctx->st_mean, &ctx->st_scale, &ctx->st_rot,
                     &ctx->st_opacity, &ctx->st_sh, &ctx->st_slot_of, &ctx->st_node_of, &ctx->st_stamp,
-                    &ctx->st_free, &ctx->st_missing, &ctx->st_count};
+                    &ctx->st_free, &ctx->st_missing, &ctx->st_count, &ctx->tr_front0, &ctx->tr_front1,
+                    &ctx->tr_feps0, &ctx->tr_feps1, &ctx->tr_level, &ctx->tr_mark, &ctx->tr_tnode};
     for (DBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& e : ctx->ev)

@@ -117,3 +117,33 @@ def test_scan_skips_rows_below_the_cut(tau, max_read):
     oid, visited, scan_read = _traverse_and_compare(h, cam)
     assert len(oid) > 1000
     assert scan_read <= max_read * h.n
+
+
+@pytest.mark.slow
+def test_destroy_returns_every_device_buffer():
+    """A context that ran the traversal cut and a render gives all its device memory back when it is
+    destroyed: the free memory the driver reports returns to its level before the context (the same
+    work ran once before, so that loading the kernels' code is not counted)."""
+    import torch
+    sc, h = scenes.corridor()
+    dh = h3dgs.DeviceHierarchy.from_arrays(h)
+    cam = sc.cameras[0]
+
+    def run_once():
+        ctx = h3dgs.Context(torch.cuda.current_device())
+        ctx.upload(dh)
+        h3dgs.h3dgs_set_cut_mode(ctx.ctx, 2)
+        cut = ctx.select_cut([cam])
+        img = ctx.render([cam], cut)
+        torch.cuda.synchronize()
+        assert h3dgs.h3dgs_get_stats(ctx.ctx)["device_flags"] == 0
+        del cut, img
+        ctx.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+    run_once()
+    free0 = torch.cuda.mem_get_info()[0]
+    run_once()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 < 8 << 20, (free0 - free1) / 2**20
