@@ -7,6 +7,7 @@ H3DGS_ERR_NO_DEVICE) on machines without a GPU.
 from __future__ import annotations
 
 import argparse
+import fcntl
 import os
 import shutil
 import subprocess
@@ -49,6 +50,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if not force and not _stale(lib):
         return lib
     os.makedirs(bdir, exist_ok=True)
+    # one build at a time per build folder (every rank of a multi-GPU run calls this): a caller that
+    # waited for the lock finds the library fresh and returns
+    with open(os.path.join(bdir, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        if not force and not _stale(lib):
+            return lib
+        return _compile(lib, bdir, check, verbose, ptxas_verbose)
+
+
+def _compile(lib: str, bdir: str, check: bool, verbose: bool, ptxas_verbose: bool) -> str:
     extra = (["-Xptxas", "-v"] if ptxas_verbose else []) + (["-DH3DGS_CHECK"] if check else [])
     objs = [os.path.join(bdir, src.replace(".cu", ".o")) for src in SOURCES]
     cmds = [[nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj] for src, obj in zip(SOURCES, objs)]

@@ -41,3 +41,41 @@ def test_null_context_and_no_device(L):
     out = C.c_void_p()
     assert L.h3dgs_create(C.byref(out), 0, None) == 7   # H3DGS_ERR_NO_DEVICE
     assert not out.value
+
+
+def test_concurrent_builds_compile_once(tmp_path, monkeypatch):
+    """Two callers of build() at once (every rank of a multi-GPU run calls it) while the library is
+    missing: one compiles and links, the other waits for the build folder's lock, then finds the
+    library fresh and returns it (the compiler is replaced by a stub that writes its output)."""
+    import threading
+    import time
+    lib = tmp_path / "libh3dgs.so"
+    monkeypatch.setattr(build, "LIB", str(lib))
+    monkeypatch.setattr(build, "BUILD_DIR", str(tmp_path / "_build"))
+    monkeypatch.setattr(build, "nvcc", lambda: "nvcc")
+    links, errors = [], []
+
+    def stub(cmd):
+        out = cmd[cmd.index("-o") + 1]
+        if "-shared" in cmd:
+            links.append(out)
+            time.sleep(0.3)   # the other caller arrives while this one links
+        with open(out, "w") as f:
+            f.write("stub")
+        return 0
+
+    monkeypatch.setattr(build.subprocess, "check_call", stub)
+
+    def call():
+        try:
+            assert build.build() == str(lib)
+        except Exception as e:   # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=call) for _ in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    assert len(links) == 1 and lib.exists()
