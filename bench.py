@@ -91,6 +91,22 @@ def parse():
     return ap.parse_args()
 
 
+def rank_max(x, world, dev):
+    """The largest value of x over the ranks (x itself on one rank): a timing of the whole job."""
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_barrier(world):
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -387,6 +403,7 @@ def run_ours(args, rank, world, local):
             fb_run()
             flush.fill_(1.0)
         torch.cuda.synchronize()
+        rank_barrier(world)
         fb_ms = 0.0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for _ in range(args.steps):
@@ -396,6 +413,7 @@ def run_ours(args, rank, world, local):
             flush.fill_(1.0)
             e1.synchronize()
             fb_ms += e0.elapsed_time(e1)
+        fb_ms = rank_max(fb_ms, world, dev)
         fb_value = world * args.steps / (fb_ms / 1e3)
 
         # ---- expected-depth output and exposure affine (appendix): forward frame, and forward + adjoint
@@ -453,12 +471,13 @@ def run_ours(args, rank, world, local):
             frame()
             host_img.copy_(images, non_blocking=True)
         stream.synchronize()
+        rank_barrier(world)
         t0 = time.perf_counter()
         for _ in range(args.steps):
             frame()
             host_img.copy_(images, non_blocking=True)
         stream.synchronize()
-        e2e_serial_value = world * args.steps / (time.perf_counter() - t0)
+        e2e_serial_value = world * args.steps / rank_max(time.perf_counter() - t0, world, dev)
 
         dev_imgs = [images, torch.empty_like(images)]
         host_imgs = [host_img, torch.empty(npix, dtype=torch.float32, pin_memory=True)]
@@ -482,12 +501,13 @@ def run_ours(args, rank, world, local):
             pipelined(k)
         copy_stream.synchronize()
         stream.synchronize()
+        rank_barrier(world)
         t0 = time.perf_counter()
         for k in range(args.steps):
             pipelined(k)
         copy_stream.synchronize()
         stream.synchronize()
-        e2e_s = time.perf_counter() - t0
+        e2e_s = rank_max(time.perf_counter() - t0, world, dev)
         e2e_value = world * args.steps / e2e_s
         assert torch.equal(host_imgs[(args.steps - 1) & 1].to(dev), ref_img), "read-back differs from the frame"
 
@@ -948,6 +968,9 @@ def run_city(args, rank, world, local):
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.Stream(dev)
     ctx = h3dgs.Context(local, stream)
     with torch.cuda.stream(stream):
@@ -975,6 +998,7 @@ def run_city(args, rank, world, local):
             h3dgs.h3dgs_select_cut(ctx.ctx, [c], ids, tt, offs, N, want_total=False)
             h3dgs.h3dgs_render(ctx.ctx, [c], ids, tt, offs, opts, images, 0, cam_array=a)
         torch.cuda.synchronize()
+        rank_barrier(world)
         cut_ms, render_ms, sizes, pairs, scan_read = [], [], [], [], []
         with ClockSampler(local) as clk:
             for c, a in zip(poses, arrs):
@@ -1040,7 +1064,8 @@ def run_city(args, rank, world, local):
                           "whose parents' granularity bound reaches tau; algorithmic_GB/s is the visited nodes' "
                           "records over the scan's time); the root-down traversal (cut and ancestors + "
                           "frontier traffic) is timed on every 8th pose"}
-        value = len(poses) / (frame_ms.sum() * 1e-3)
+        loop_ms = rank_max(frame_ms.sum(), world, dev)   # the slowest rank's loop
+        value = world * len(poses) / (loop_ms * 1e-3)
         batched = None
         if args.batch_views > 0:
             flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -1058,7 +1083,7 @@ def run_city(args, rank, world, local):
                       "cut_ms_max": float(np.max(cut_ms)), "render_ms_mean": float(np.mean(render_ms)),
                       "render_ms_max": float(np.max(render_ms)), "frame_ms_p50": float(np.median(frame_ms)),
                       "frame_ms_max": float(frame_ms.max())},
-        "gaussians_per_s": float(np.sum(sizes) / (frame_ms.sum() * 1e-3)),
+        "gaussians_per_s": float(world * np.sum(sizes) / (loop_ms * 1e-3)),
         "stage_bandwidth": {"cut": cut_bw},
         "stages_ms": city_stages,
         "build": {"host_generation_s": t_gen, "device_build_s": t_build},
@@ -1066,6 +1091,9 @@ def run_city(args, rank, world, local):
     }
     if batched is not None:
         out["batched"] = batched
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
     return out if rank == 0 else None
 
 

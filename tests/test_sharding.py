@@ -67,3 +67,33 @@ def test_gradient_allreduce_on_two_gloo_ranks():
         np.testing.assert_array_equal(out[r]["mean"], np.full((5, 3), 3.0))
         np.testing.assert_array_equal(out[r]["sh"], np.arange(10.0).reshape(2, 5) * 3)
         np.testing.assert_array_equal(out[r]["opacity"], [1.0])
+
+
+def _timing_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        bench.rank_barrier(world)
+        q.put((rank, bench.rank_max([2.5, 7.0][rank], world, "cpu"), bench.rank_max(rank, 1, "cpu")))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_times_the_slowest_rank():
+    """The bench's job timings on two gloo ranks: every rank receives the largest of the ranks' times
+    (the whole job's), and one rank keeps its own."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_timing_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = {r: (a, b) for r, a, b in (q.get(timeout=120) for _ in procs)}
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out == {0: (7.0, 0.0), 1: (7.0, 1.0)}
