@@ -76,3 +76,39 @@ def city_device(ctx, grid=20, per=125_000, seed=2):
             for k in leaves:
                 leaves[k][c * per:(c + 1) * per].copy_(torch.from_numpy(getattr(lv, k)))
     return leaves, np.arange(K + 1, dtype=np.int64) * per
+
+
+@functools.lru_cache(maxsize=None)
+def two_corridors(n_leaves=1_000_000):
+    """Two copies of the corridor hierarchy under a new root (the second one shifted along x by the
+    street's length; 4M nodes at the default size, a scan of several waves).  Ids:
+    0 the new root, 1 and 2 the copies' roots, then the rest of the first copy, then of the second."""
+    import oracle
+    _, h = corridor(n_leaves)
+    n = h.n
+    shift = np.zeros(3, np.float32)
+    shift[0] = float(h.box_max[0][0] - h.box_min[0][0]) * 1.05
+    ida = np.concatenate([[1], np.arange(3, n + 2)])            # new id of the first copy's node i
+    idb = np.concatenate([[2], np.arange(n + 2, 2 * n + 1)])    # and of the second copy's
+
+    def cat(a, b_shift=None):
+        b = a if b_shift is None else a + b_shift
+        return np.ascontiguousarray(np.concatenate([a[:1], a[:1], b[:1], a[1:], b[1:]]))
+
+    def topo(idm, arr_par, arr_cs):
+        par = np.where(arr_par >= 0, idm[np.maximum(arr_par, 0)], 0).astype(np.int32)
+        cs = np.where(h.child_count > 0, idm[np.minimum(arr_cs, n - 1)], 0).astype(np.int32)
+        return par, cs
+
+    pa, ca = topo(ida, h.parent, h.child_start)
+    pb, cb = topo(idb, h.parent, h.child_start)
+    parent = np.concatenate([[-1], pa[:1], pb[:1], pa[1:], pb[1:]]).astype(np.int32)
+    child_start = np.concatenate([[1], ca[:1], cb[:1], ca[1:], cb[1:]]).astype(np.int32)
+    child_count = np.concatenate([[2], h.child_count[:1], h.child_count[:1], h.child_count[1:],
+                                  h.child_count[1:]]).astype(np.int32)
+    bmin = cat(h.box_min, shift)
+    bmax = cat(h.box_max, shift)
+    bmin[0] = np.minimum(h.box_min[0], h.box_min[0] + shift)
+    bmax[0] = np.maximum(h.box_max[0], h.box_max[0] + shift)
+    return oracle.Hierarchy(cat(h.mean, shift), cat(h.scale), cat(h.rot), cat(h.opacity), cat(h.sh), bmin, bmax,
+                            parent, child_start, child_count)

@@ -256,6 +256,37 @@ def test_cut_special_cases_and_invariants():
         assert np.all(t[~inner] == 0)
 
 
+
+@pytest.mark.parametrize("tau", [3.0, 15.0])
+def test_cut_rule_is_local_under_a_joined_root(tau):
+    """The cut rule is local (Sec. 4.2: a node is in the cut iff its granularity is below tau and its
+    parent's is not, or it is a leaf under an expanded parent), so joining two copies of a tree
+    under a new root that is expanded leaves each copy's cut and weights as the copy's own (the test
+    tree of the several-wave scan, here at 100k leaves).  The joined tree is checked for a valid
+    hierarchy first: every node but the root is one child of its parent, parents come before their
+    children, and child boxes nest in their parent's."""
+    sc, h1 = scenes.corridor(100_000)
+    h = scenes.two_corridors(100_000)
+    n1 = h1.n
+    assert h.n == 2 * n1 + 1
+    par, cs, cc = h.parent, h.child_start, h.child_count
+    assert par[0] == -1 and np.all(par[1:] < np.arange(1, h.n))
+    inner = np.flatnonzero(cc > 0)
+    kids = np.concatenate([cs[inner] + k for k in range(2)])
+    assert np.all(cc[inner] == 2)
+    np.testing.assert_array_equal(np.sort(kids), np.arange(1, h.n))   # each non-root node once
+    assert np.all(par[kids] == np.concatenate([inner, inner]))
+    assert np.all(h.box_min[1:] >= h.box_min[par[1:]]) and np.all(h.box_max[1:] <= h.box_max[par[1:]])
+    cam = synth.with_tau(sc.cameras[0], tau)
+    ids, t = oracle.select_cut(cam, h)
+    o1, t1 = oracle.select_cut(cam, h1)
+    assert 0 not in ids and 1 not in ids      # the new root and the first copy's root are expanded
+    first = (ids >= 3) & (ids < n1 + 2)       # the first copy's nodes other than its root: id - 2
+    np.testing.assert_array_equal(ids[first] - 2, o1)
+    np.testing.assert_array_equal(t[first].view(np.uint32), t1.view(np.uint32))
+    second = ids >= n1 + 2                    # the second copy, shifted down the street
+    assert second.sum() > 0 and first.sum() + second.sum() == len(ids)
+
 def test_granularity_is_projected_box_size():
     """eps(n) = f * (largest box side) / (distance to the box); check against a direct fp64
     evaluation of the worst-case projected size of a box edge seen head-on."""

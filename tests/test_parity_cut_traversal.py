@@ -6,8 +6,6 @@ several waves); the number of nodes it reads equals the size of the cut plus its
 here from the oracle's cut.  The scan (mode 1) selects the same and reads at least those records: it
 skips only rows of 256 nodes whose nodes all have a parent below tau.  Destroying a context that ran
 the traversal returns all its device memory."""
-import functools
-
 import numpy as np
 import pytest
 
@@ -123,41 +121,6 @@ def test_scan_skips_rows_below_the_cut(tau, max_read):
 
 
 
-@functools.lru_cache(maxsize=None)
-def _two_corridors():
-    """Two copies of the 2M-node corridor under a new root (the second one shifted along x by the
-    street's length): a 4M-node tree, whose scan takes several waves of its longer tiles.  Ids:
-    0 the new root, 1 and 2 the copies' roots, then the rest of the first copy, then of the second."""
-    _, h = scenes.corridor()
-    n = h.n
-    shift = np.zeros(3, np.float32)
-    shift[0] = float(h.box_max[0][0] - h.box_min[0][0]) * 1.05
-    ida = np.concatenate([[1], np.arange(3, n + 2)])            # new id of the first copy's node i
-    idb = np.concatenate([[2], np.arange(n + 2, 2 * n + 1)])    # and of the second copy's
-
-    def cat(a, b_shift=None):
-        b = a if b_shift is None else a + b_shift
-        return np.ascontiguousarray(np.concatenate([a[:1], a[:1], b[:1], a[1:], b[1:]]))
-
-    def topo(idm, arr_par, arr_cs):
-        par = np.where(arr_par >= 0, idm[np.maximum(arr_par, 0)], 0).astype(np.int32)
-        cs = np.where(h.child_count > 0, idm[np.minimum(arr_cs, n - 1)], 0).astype(np.int32)
-        return par, cs
-
-    pa, ca = topo(ida, h.parent, h.child_start)
-    pb, cb = topo(idb, h.parent, h.child_start)
-    parent = np.concatenate([[-1], pa[:1], pb[:1], pa[1:], pb[1:]]).astype(np.int32)
-    child_start = np.concatenate([[1], ca[:1], cb[:1], ca[1:], cb[1:]]).astype(np.int32)
-    child_count = np.concatenate([[2], h.child_count[:1], h.child_count[:1], h.child_count[1:],
-                                  h.child_count[1:]]).astype(np.int32)
-    bmin = cat(h.box_min, shift)
-    bmax = cat(h.box_max, shift)
-    bmin[0] = np.minimum(h.box_min[0], h.box_min[0] + shift)
-    bmax[0] = np.maximum(h.box_max[0], h.box_max[0] + shift)
-    return oracle.Hierarchy(cat(h.mean, shift), cat(h.scale), cat(h.rot), cat(h.opacity), cat(h.sh), bmin, bmax,
-                            parent, child_start, child_count)
-
-
 @pytest.mark.slow
 @pytest.mark.parametrize("tau", [3.0, 6.0, 15.0])
 def test_scan_of_several_waves(tau):
@@ -165,7 +128,7 @@ def test_scan_of_several_waves(tau):
     chained by the look-back, the row skipping): the default mode, the forced scan and the traversal
     all select the oracle's nodes and weights bit for bit, over both copies of the street."""
     sc, _ = scenes.corridor()
-    h = _two_corridors()
+    h = scenes.two_corridors()
     assert h.n == 2 * scenes.corridor()[1].n + 1
     gpu_path.upload(h)
     cam = synth.with_tau(sc.cameras[0], tau)
