@@ -257,6 +257,44 @@ def test_cut_special_cases_and_invariants():
 
 
 
+
+@pytest.mark.parametrize("seed", range(12))
+def test_cut_invariants_on_random_trees_and_cameras(seed):
+    """The cut (Sec. 4.2) on seeded random trees of 1 to 300 leaves, seen from random positions
+    (outside and inside the leaves' cube, any direction) at random tau, including 0 and infinity:
+    ids ascending, equal to the recursive descent from the root, every root-to-leaf path meets the
+    cut once, weights in [0, 1].  At tau = 0 the cut is the leaves; at tau = infinity it is the root
+    when the camera is outside the root's box, and otherwise the nodes of finite granularity
+    closest to the root (a box holding the camera is at distance 0: infinitely coarse)."""
+    rng = np.random.default_rng([seed, 77])
+    n_leaves = int(rng.choice([1, 2, 3, 17, 64, 300]))
+    sc = synth.tiny_scene(seed=100 + seed, n_leaves=n_leaves)
+    h = oracle.build_tree(sc.leaves)
+    assert h.n == 2 * n_leaves - 1
+    for k in range(4):
+        pos = rng.uniform(-15.0, 25.0, 3) if k % 2 else rng.uniform(2.0, 8.0, 3)
+        fwd = rng.normal(size=3)
+        up = np.cross(fwd, rng.normal(size=3))
+        for tau in (0.0, float(np.exp(rng.uniform(np.log(0.1), np.log(500.0)))), float("inf")):
+            cam = synth.look_camera(pos, fwd, up, 160, 120, float(rng.uniform(30, 100)), tau)
+            ids, t = oracle.select_cut(cam, h)
+            assert np.all(np.diff(ids) > 0)
+            np.testing.assert_array_equal(ids, oracle.select_cut_descent(cam, h))
+            assert _paths_hit_once(h, ids)
+            assert np.all((t >= 0) & (t <= 1))
+            if tau == 0.0:
+                np.testing.assert_array_equal(ids, np.flatnonzero(h.child_count == 0))
+            if tau == float("inf"):
+                inside = np.all(pos >= h.box_min[0]) and np.all(pos <= h.box_max[0])
+                if not inside:
+                    np.testing.assert_array_equal(ids, [0])
+                    assert t[0] == 0
+                else:
+                    eps = oracle.granularity(cam, h)
+                    cut_leaf = h.child_count[ids] == 0
+                    assert np.all(np.isfinite(eps[ids]) | cut_leaf)
+                    assert not np.isfinite(eps[0]) and 0 not in ids
+
 @pytest.mark.parametrize("tau", [3.0, 15.0])
 def test_cut_rule_is_local_under_a_joined_root(tau):
     """The cut rule is local (Sec. 4.2: a node is in the cut iff its granularity is below tau and its
