@@ -463,6 +463,26 @@ def test_tiled_equals_bruteforce_over_tile_shapes():
         assert fr.image.max() > 0.1
 
 
+
+@pytest.mark.parametrize("seed", range(8))
+def test_tiled_equals_bruteforce_on_random_scenes(seed):
+    """The tiled blend (depth sort, tile lists, per-tile front-to-back walk) equals the per-pixel
+    brute force over every splat on seeded random scenes at several tau (so that interpolated
+    splats, t != 0, take part) and a random tile shape."""
+    rng = np.random.default_rng([seed, 55])
+    lv, cam = scenes.small_random_scene(n_leaves=int(rng.integers(8, 120)), seed=1000 + seed, res=(61, 37),
+                                        log_scale=float(rng.uniform(-3.0, -2.0)))
+    h = oracle.build_tree(lv)
+    tw, th = [(16, 16), (8, 8), (32, 8), (8, 32)][int(rng.integers(4))]
+    opts = oracle.Opts(tile_w=tw, tile_h=th)
+    n_interp = 0
+    for tau in (0.0, 2.0, 6.0, 20.0):
+        fr = oracle.render(synth.with_tau(cam, tau), h, opts)
+        bf = oracle.blend_bruteforce(synth.with_tau(cam, tau), fr, opts)
+        np.testing.assert_allclose(fr.image, bf, atol=1e-13)
+        n_interp += int(np.sum(fr.t != 0))
+    assert n_interp > 0
+
 def test_alpha_floor_and_transmittance_stop():
     """A splat whose alpha never reaches 1/255 changes nothing; the transmittance stop halts
     BEFORE the splat that would take T below 1e-4, so nothing behind it is added."""
