@@ -112,3 +112,20 @@ def two_corridors(n_leaves=1_000_000):
     bmax[0] = np.maximum(h.box_max[0], h.box_max[0] + shift)
     return oracle.Hierarchy(cat(h.mean, shift), cat(h.scale), cat(h.rot), cat(h.opacity), cat(h.sh), bmin, bmax,
                             parent, child_start, child_count)
+
+
+def random_case(seed):
+    """A seeded random scene (50, 500 or 4096 leaves in a 10 m cube) and camera: inside the cube
+    looking anywhere, or outside looking at it; random ragged resolution, field of view and tau."""
+    rng = np.random.default_rng([seed, 91])
+    n_leaves = int(rng.choice([50, 500, 4096]))
+    sc = synth.tiny_scene(seed=200 + seed, n_leaves=n_leaves)
+    import oracle
+    h = oracle.build_tree(sc.leaves)
+    inside = bool(rng.integers(2))
+    pos = rng.uniform(2.0, 8.0, 3) if inside else np.array([5.0, 5.0, 5.0]) + rng.normal(size=3) * 12.0
+    fwd = rng.normal(size=3) if inside else np.array([5.0, 5.0, 5.0]) - pos
+    up = np.cross(fwd, rng.normal(size=3))
+    w, hgt = int(rng.integers(150, 330)), int(rng.integers(100, 260))
+    tau = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
+    return h, synth.look_camera(pos, fwd, up, w, hgt, float(rng.uniform(40, 90)), tau)

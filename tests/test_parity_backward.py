@@ -116,6 +116,20 @@ def test_backward_tiny_scene(tau, chunk):
     _check(gg, og)
 
 
+
+@pytest.mark.parametrize("seed", range(10))
+def test_backward_random_scenes_and_cameras(seed):
+    """The adjoint on the forward path's seeded random scenes and cameras (inside or outside the
+    scene, ragged resolutions, one frame that sees nothing)."""
+    h, cam = scenes.random_case(seed)
+    opts = oracle.Opts()
+    dh = gpu_path.upload(h)
+    fr = oracle.render(cam, h, opts)
+    w = loss_weight(fr, 10 + seed)
+    og = oracle.backward(cam, h, fr, w, opts)
+    gg = _gpu_grads(dh, cam, opts, w)
+    _check(gg, og)
+
 def test_backward_options():
     sc, h = scenes.tiny()
     cam = synth.with_tau(sc.cameras[0], 6.0)

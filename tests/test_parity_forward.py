@@ -67,27 +67,11 @@ def test_tiny_scene_all_stages(tau):
 
 
 
-def _random_case(seed):
-    """A seeded random scene (50, 500 or 4096 leaves in a 10 m cube) and camera: inside the cube
-    looking anywhere, or outside looking at it; random ragged resolution, field of view and tau."""
-    rng = np.random.default_rng([seed, 91])
-    n_leaves = int(rng.choice([50, 500, 4096]))
-    sc = synth.tiny_scene(seed=200 + seed, n_leaves=n_leaves)
-    h = oracle.build_tree(sc.leaves)
-    inside = bool(rng.integers(2))
-    pos = rng.uniform(2.0, 8.0, 3) if inside else np.array([5.0, 5.0, 5.0]) + rng.normal(size=3) * 12.0
-    fwd = rng.normal(size=3) if inside else np.array([5.0, 5.0, 5.0]) - pos
-    up = np.cross(fwd, rng.normal(size=3))
-    w, hgt = int(rng.integers(150, 330)), int(rng.integers(100, 260))
-    tau = float(np.exp(rng.uniform(np.log(0.5), np.log(50.0))))
-    return h, synth.look_camera(pos, fwd, up, w, hgt, float(rng.uniform(40, 90)), tau)
-
-
 @pytest.mark.parametrize("seed", range(10))
 def test_random_scenes_and_cameras(seed):
     """Every bar of the forward path on seeded random scenes and cameras (one of them sees
     nothing)."""
-    h, cam = _random_case(seed)
+    h, cam = scenes.random_case(seed)
     dh = gpu_path.upload(h)
     ofr, g = _compare(cam, h, dh, oracle.Opts())
     assert g.stats["n_cut"] == len(ofr.ids) and g.stats["n_pairs"] == len(ofr.lists)
