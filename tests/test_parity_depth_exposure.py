@@ -77,6 +77,28 @@ def test_forward_batch_with_exposure_and_depth(chunk):
         assert ofr.depth.max() > 0.5 * zmax * 0.1
 
 
+
+@pytest.mark.parametrize("seed", range(10))
+def test_depth_and_exposure_on_random_scenes_and_cameras(seed):
+    """The expected depth and an exposure affine on the forward path's seeded random scenes and
+    cameras (one of them sees nothing: background only, depth zero)."""
+    h, cam = scenes.random_case(seed)
+    gpu_path.upload(h)
+    opts = oracle.Opts(bg=(0.1, 0.3, 0.2))
+    E = _exposures(1, 20 + seed)
+    cut, Ed, images, depth = _render([cam], opts, E)
+    img = _split(images.cpu().numpy(), [cam], 3)[0]
+    dep = _split(depth.cpu().numpy(), [cam], 1)[0]
+    ofr = oracle.render(cam, h, opts, exposure=E[0])
+    amb = ofr.ambiguous
+    assert amb.mean() < 2e-4
+    err = np.abs(img - ofr.image).max(axis=0)
+    assert err[~amb].max() <= IMG_TOL, err[~amb].max()
+    vis = ofr.rect[:, 0] >= 0
+    zmax = float(ofr.val64[vis, 12].max()) if vis.any() else 0.0
+    derr = np.abs(dep - ofr.depth)
+    assert derr[~amb].max() <= IMG_TOL * max(zmax, 1e-6), (derr[~amb].max(), zmax)
+
 def test_plain_render_is_unchanged_by_the_extended_entry_point():
     import torch
     sc, h = scenes.tiny()
