@@ -51,6 +51,20 @@ def test_noalloc_cut_matches_context_cut_on_consecutive_calls():
         np.testing.assert_array_equal(t2.view(np.uint32), t.view(np.uint32))
 
 
+
+@pytest.mark.parametrize("seed", range(10))
+def test_noalloc_cut_on_random_scenes_and_cameras(seed):
+    """On the forward path's seeded random scenes and cameras the allocation-free cut equals the
+    oracle's cut rule, ids and weights bit for bit."""
+    import oracle
+    h, cam = scenes.random_case(seed)
+    dh = gpu_path.upload(h)
+    _, (ids2, t2, offs2, total) = _both(dh, cam)
+    oid, ot = oracle.select_cut(cam, h, 1)
+    assert total == len(oid) == offs2[1]
+    np.testing.assert_array_equal(ids2, oid)
+    np.testing.assert_array_equal(t2.view(np.uint32), ot.view(np.uint32))
+
 def test_noalloc_cut_on_the_two_million_node_corridor():
     sc, h = scenes.corridor()
     dh = gpu_path.upload(h)
