@@ -70,6 +70,28 @@ def test_matches_the_brute_force_procedure(small, tau_min, tau_max):
     assert [int(p) for p in out.parent[1:]] == [new_of_old[up[o]] for o in order[1:]]
 
 
+
+@pytest.mark.parametrize("seed", range(8))
+def test_matches_the_brute_force_procedure_on_random_trees(seed):
+    """The same equality on seeded random trees (5 to 80 leaves), camera sets (1 to 4 orbit views at
+    random distances) and tau ranges drawn inside the interior nodes' granularities (so that nodes
+    are removed and wider nodes made)."""
+    rng = np.random.default_rng([seed, 31])
+    n_leaves = int(rng.choice([5, 17, 40, 80]))
+    lv, _ = scenes.small_random_scene(n_leaves=n_leaves, seed=500 + seed, cube=1.0, dist=3.0)
+    h = oracle.build_tree(lv)
+    cams = synth.orbit_views([0.0, 0.0, 3.0], float(rng.uniform(2.0, 8.0)), int(rng.integers(1, 5)), 64, 48,
+                             seed=int(rng.integers(1000)))
+    eps = np.concatenate([oracle.granularity(c, h)[h.child_count > 0] for c in cams])
+    tau_min = float(np.quantile(eps[np.isfinite(eps)], rng.uniform(0.05, 0.6)))
+    tau_max = tau_min * float(2 ** rng.integers(1, 6))
+    out, old = oracle.compact(cams, h, tau_min, tau_max)
+    order, up = _brute_force(cams, h, tau_min, tau_max)
+    assert old.tolist() == order
+    new_of_old = {o: i for i, o in enumerate(order)}
+    assert out.parent[0] == -1
+    assert [int(p) for p in out.parent[1:]] == [new_of_old[up[o]] for o in order[1:]]
+
 def test_brute_force_case_removes_nodes_and_makes_wider_nodes(small):
     h, cams = small
     out, old = oracle.compact(cams, h, 1.0, 64.0)
